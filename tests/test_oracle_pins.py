@@ -1,0 +1,350 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values printed
+in the paper (tests/golden), closed forms, brute force, exact discrete identities,
+invariants and symmetries.  A plausible slip in the oracle (a dropped term, a sign,
+an index, a transposed operand) fails at least one of them.
+"""
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+from scipy.special import expit
+
+import workloads as W
+from oracle import flame, poisson
+from oracle import step as S
+from oracle.operators import V, Grid
+from oracle.convergence import observed_order, richardson_order, gci
+
+from conftest import golden
+
+
+def _l2(a, g):
+    return float(np.sqrt(np.sum(a * a) * g.dV))
+
+
+def _tg_run(n, dt, t_end, want_star=False):
+    prm, geo, f = W.taylor_green(n, dt)
+    pb = S.Problem(prm, geo)
+    st = S.initial_state(pb, f["v"], f["Z"], f["H"])
+    nsteps = int(round(t_end / dt))
+    for _ in range(nsteps - 1):
+        st = S.advance(pb, st)
+    new, star = S.advance(pb, st, return_star=True)
+    return pb, new, star
+
+
+# ---------------------------------------------------------------------------
+# Table 2: predictor-corrector local truncation error, 50x50, t = 1.3
+# ---------------------------------------------------------------------------
+def test_taylor_green_table2_lte():
+    rows = golden("taylor_green_table2.txt")
+    want = {(float(r[1]), r[2]): float(r[3]) for r in rows}
+    got = {}
+    for dt in (4e-3, 2e-3):
+        pb, new, star = _tg_run(50, dt, 1.3, want_star=True)
+        g = pb.g
+        got[(dt, "P")] = _l2(V(star["P"], g) - V(new.P, g), g)
+        got[(dt, "v1")] = _l2(V(star["v"][0], g) - V(new.v[0], g), g)
+        got[(dt, "v2")] = _l2(V(star["v"][1], g) - V(new.v[1], g), g)
+    for key, ref in want.items():
+        assert got[key] == pytest.approx(ref, rel=2e-3), (key, got[key], ref)
+    for var in ("P", "v1", "v2"):
+        assert observed_order(got[(4e-3, var)], got[(2e-3, var)], 2.0) == pytest.approx(3.0, abs=0.02)
+
+
+# ---------------------------------------------------------------------------
+# Table 1: error against the exact solution, 40x40, dt = 5e-5, t = 1.3
+# ---------------------------------------------------------------------------
+@pytest.mark.slow
+def test_taylor_green_table1_spatial():
+    rows = golden("taylor_green_table1.txt")
+    dt = 5e-5
+    pb, new, _ = _tg_run(40, dt, 1.3)
+    g = pb.g
+    u, v, p = W.taylor_green_exact(40, new.t)
+    p_num = V(new.P, g) / dt
+    got = {("v1", "L2"): _l2(V(new.v[0], g) - u, g),
+           ("v1", "Linf"): float(np.abs(V(new.v[0], g) - u).max()),
+           ("v2", "L2"): _l2(V(new.v[1], g) - v, g),
+           ("p", "L2"): _l2(p_num - p, g)}
+    tol = {("v1", "L2"): 2e-3, ("v2", "L2"): 2e-3, ("v1", "Linf"): 1e-2, ("p", "L2"): 1e-2}
+    for r in rows:
+        key = (r[2], r[3])
+        assert got[key] == pytest.approx(float(r[4]), rel=tol[key]), (key, got[key], r[4])
+
+
+# ---------------------------------------------------------------------------
+# Flame sheet: Eq 3.41 is the integral of the regularised slope (Eqs 3.39-3.40)
+# ---------------------------------------------------------------------------
+def test_flame_closed_form_matches_integral():
+    fp = flame.derived_parameters(0.055, 7.0, 0.5, 1e-3)
+    S_, k = fp["S"], fp["k"]
+    # regularised slope, written with the logistic function (= (1 + tanh x)/2)
+    slope = lambda z: -(1.0 / S_ + 1.0) * expit(2.0 * k * (z - 1.0)) + 1.0
+    for Z in (-0.5, 0.0, 0.3, 0.9, 1.0, 1.2, 2.5, 10.0, S_ + 1.0, 25.0):
+        integral = quad(slope, 1.0, Z, limit=200, epsabs=1e-13, epsrel=1e-13)[0]
+        assert flame.F_eps_unshifted(np.array(Z), S_, k) == pytest.approx(integral, abs=1e-11)
+
+
+def test_flame_levels_and_sharp_limit():
+    fp = flame.derived_parameters(0.055, 7.0, 0.5, 1e-3)
+    S_, Q, k = fp["S"], fp["Q"], fp["k"]
+    H_inf = 1.0 + (S_ + 1.0) / Q
+    # far from the flame the translated F_eps is the piecewise-linear F (Eq 3.37)
+    far = np.array([-2.0, -1.0, 1.0 - 6.0 / k, 1.0 + 6.0 / k, 5.0, S_ + 1.0, 30.0])
+    far = far[np.abs(k * (far - 1.0)) > 5.0]
+    err = np.abs(flame.F_eps(far, S_, k) - flame.F_sharp(far, S_))
+    assert np.all(err < (S_ + 1.0) / (2 * S_ * k) * np.exp(-2 * np.abs(k * (far - 1.0))) * 1.01 + 1e-14)
+    # oxidiser and fuel streams at T = 1, adiabatic flame temperature = density ratio
+    assert flame.temperature(np.array(0.0), np.array(H_inf), fp) == pytest.approx(1.0, abs=1e-5)
+    assert flame.temperature(np.array(S_ + 1.0), np.array(H_inf), fp) == pytest.approx(1.0, abs=1e-6)
+    T_sharp_flame = Q / (S_ + 1.0) * (flame.F_sharp(np.array(1.0), S_) + H_inf)
+    assert T_sharp_flame == pytest.approx(7.0, rel=1e-14)
+    # the regularised peak is lower (text after Eq 3.41) and tends to 7 as k grows
+    peaks = []
+    for tol in (1e-3, 1e-6, 1e-12):
+        fpt = flame.derived_parameters(0.055, 7.0, 0.5, tol)
+        peaks.append(float(flame.temperature(np.array(1.0), np.array(H_inf), fpt)))
+    assert peaks[0] < peaks[1] < peaks[2] < 7.0
+    assert 7.0 - peaks[2] < 0.5 * (7.0 - peaks[0])
+    # slope continuity: a centred difference of F_eps reproduces Eq 3.39
+    Z = np.linspace(0.0, 3.0, 31)
+    d = 1e-5
+    fd = (flame.F_eps(Z + d, S_, k) - flame.F_eps(Z - d, S_, k)) / (2 * d)
+    want = -(1.0 / S_ + 1.0) * expit(2 * k * (Z - 1.0)) + 1.0
+    assert np.max(np.abs(fd - want)) < 1e-7
+
+
+# ---------------------------------------------------------------------------
+# Poisson: transform solve == brute-force augmented dense solve
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,periodic", [((8, 6), (True, True)), ((8, 6), (True, False)),
+                                        ((7, 10), (False, False)), ((6, 4, 5), (False, True, False)),
+                                        ((4, 6, 4), (True, True, True))])
+def test_poisson_transform_equals_dense(n, periodic):
+    rng = np.random.Generator(np.random.PCG64(7))
+    g = Grid(n, [1.0 + 0.1 * d for d in range(len(n))])
+    b = rng.normal(size=tuple(reversed(n)))
+    P_fft = poisson.solve(b, g, periodic)
+    P_dense, lam = poisson.dense_solve(b, g, periodic)
+    assert lam == pytest.approx(b.mean(), abs=1e-12)
+    assert np.max(np.abs(P_fft - P_dense)) < 1e-11 * np.max(np.abs(P_dense))
+    assert abs(P_fft.mean()) < 1e-13
+    # the discrete equation holds: L P = b - mean(b)
+    assert np.max(np.abs(poisson.apply(P_fft, g, periodic) - (b - b.mean()))) < 1e-10
+
+
+def test_poisson_eigenvalues_closed_form():
+    # a single separable mode is an eigenvector of L with eigenvalue
+    # -(2 - 2cos(theta))/h^2 summed over directions
+    g = Grid((12, 10), (1.0, 2.0))
+    x = (np.arange(12) + 0.5) / 12
+    y = (np.arange(10) + 0.5) * 0.2
+    kx, ky = 3, 2
+    mode = np.cos(2 * np.pi * kx * x)[None, :] * np.cos(np.pi * ky * y / 2.0)[:, None]
+    lam = -(2 - 2 * np.cos(2 * np.pi * kx / 12)) / (1 / 12) ** 2 - (2 - 2 * np.cos(np.pi * ky / 10)) / 0.2 ** 2
+    out = poisson.apply(mode, g, (True, False))
+    assert np.max(np.abs(out - lam * mode)) < 1e-10 * abs(lam)
+
+
+# ---------------------------------------------------------------------------
+# Discrete continuity (Eq 3.24 with S_m, Eq 3.33) after each projection
+# ---------------------------------------------------------------------------
+def _continuity_residual(pb, prev, new, dt):
+    g = pb.g
+    rho1, rho0 = V(new.rho, g), V(prev.rho, g)
+    if prev.rho_prev is None:
+        drho = (rho1 - rho0) / dt
+    else:
+        drho = (3 * rho1 - 4 * rho0 + V(prev.rho_prev, g)) / (2 * dt)
+    div = 0.0
+    for j in range(g.dim):
+        Fj = V(new.F[j], g, face=j)
+        a = g.ax(j)
+        hi = np.take(Fj, range(1, g.n[j] + 1), axis=a)
+        lo = np.take(Fj, range(0, g.n[j]), axis=a)
+        div = div + (hi - lo) / g.h[j]
+    Sm = pb.ibm["Sm"] if pb.ibm is not None else 0.0
+    return drho + div - Sm, np.max(np.abs(drho)) + np.max(np.abs(Sm))
+
+
+@pytest.mark.parametrize("case", ["blobs", "slot"])
+def test_divergence_constraint_and_mass(case):
+    if case == "blobs":
+        prm, geo, f = W.periodic_blobs(32)
+    else:
+        prm, geo, f = W.slot_burner(32, 64)
+    pb = S.Problem(prm, geo)
+    g = pb.g
+    st = S.initial_state(pb, f["v"], f["Z"], f["H"])
+    m0 = float(np.sum(V(st.rho, g)) * g.dV)
+    for k in range(12):
+        prev = st
+        st = S.advance(pb, st)
+        res, scale = _continuity_residual(pb, prev, st, prm["dt"])
+        assert np.max(np.abs(res)) < 1e-9 * max(scale, 1.0), (k, np.max(np.abs(res)))
+    if case == "blobs":
+        # enclosed system: total mass fixed by Eq 2.40
+        m = float(np.sum(V(st.rho, g)) * g.dV)
+        assert m == pytest.approx(m0, rel=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Enclosed box: p0 from the mass constraint (Eq 2.40) obeys the ODE of Eq 2.38
+# ---------------------------------------------------------------------------
+def _p0_gap(n, dt, t_end):
+    prm, geo, f = W.periodic_blobs(n)
+    prm["dt"] = dt
+    pb = S.Problem(prm, geo)
+    g = pb.g
+    st = S.initial_state(pb, f["v"], f["Z"], f["H"])
+    for _ in range(int(round(t_end / dt))):
+        st = S.advance(pb, st)
+    p0n, p0m1, p0m2 = st.p0_hist
+    dp0 = (3 * p0n - 4 * p0m1 + p0m2) / (2 * dt)
+    Z, kap, h = V(st.Z, g), V(st.kappa, g), g.h[0]
+
+    def div_k_grad(phi):
+        out = 0.0
+        for ax in (0, 1):
+            kf = 0.5 * (kap + np.roll(kap, -1, axis=ax))
+            fl = kf * (np.roll(phi, -1, axis=ax) - phi) / h
+            out = out + (fl - np.roll(fl, 1, axis=ax)) / h
+        return out
+    fp = pb.fp
+    Np = (-1.0 / fp["S"] - 1.0) * expit(2 * fp["k"] * (Z - 1.0)) + 1.0   # Eq 3.35c
+    # Eq 2.38, periodic enclosure of volume 1: boundary integrals vanish
+    rhs = prm["gamma"] * fp["Q"] / (fp["S"] + 1.0) / pb.Pe * float(np.sum(Np * div_k_grad(Z)) * g.dV)
+    return abs(dp0 - rhs) / abs(rhs)
+
+
+def test_enclosed_p0_follows_ode():
+    gap64 = _p0_gap(64, 2e-5, 2e-3)
+    gap128 = _p0_gap(128, 5e-6, 2e-3)
+    assert gap64 < 1e-2
+    assert gap128 < 0.4 * gap64            # converges (about second order)
+
+
+# ---------------------------------------------------------------------------
+# Invariants and symmetry
+# ---------------------------------------------------------------------------
+def test_open_system_keeps_uniform_excess_enthalpy_and_mirror_symmetry():
+    prm, geo, f = W.slot_burner(32, 64)
+    pb = S.Problem(prm, geo)
+    g = pb.g
+    st = S.initial_state(pb, f["v"], f["Z"], f["H"])
+    H_inf = prm["inflow_H"]
+    for _ in range(15):
+        st = S.advance(pb, st)
+    # Le = 1, open system, H_ib = H_inf: H stays uniform (Eqs 2.45, 3.32)
+    assert np.max(np.abs(V(st.H, g) - H_inf)) < 1e-13
+    # x-mirror symmetry about x = 0.5 of the slot burner
+    u, v, Z, P = V(st.v[0], g), V(st.v[1], g), V(st.Z, g), V(st.P, g)
+    su = np.max(np.abs(u)) + 1e-30
+    assert np.max(np.abs(u + u[:, ::-1])) < 1e-9 * su
+    assert np.max(np.abs(v - v[:, ::-1])) < 1e-9 * np.max(np.abs(v))
+    assert np.max(np.abs(Z - Z[:, ::-1])) < 1e-9 * np.max(np.abs(Z))
+    assert np.max(np.abs(P - P[:, ::-1])) < 1e-8 * np.max(np.abs(P))
+
+
+def test_uniform_scalars_stay_uniform_under_any_flow():
+    prm, geo, f = W.periodic_blobs(24)
+    prm["closed_system"] = 0
+    f["Z"] = np.full_like(f["Z"], 0.4)
+    pb = S.Problem(prm, geo)
+    g = pb.g
+    st = S.initial_state(pb, f["v"], f["Z"], f["H"])
+    for _ in range(5):
+        st = S.advance(pb, st)
+    assert np.max(np.abs(V(st.Z, g) - 0.4)) < 1e-13
+    assert np.max(np.abs(V(st.H, g) - f["H"][0, 0])) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Immersed boundary mass source: discrete integral equals the prescribed flow
+# ---------------------------------------------------------------------------
+def test_ibm_integrated_mass_source():
+    from oracle.ibm import build
+    for n in (64, 128, 256):
+        prm, geo, _ = W.slot_burner(n, 2 * n)
+        g = Grid(prm["n"][:2], prm["L"][:2])
+        ib = build(g, geo)
+        total = float(np.sum(ib["Sm"]) * g.dV)
+        # continuous ejected mass flow: integral of rho_b U_b (1 - (x/a)^2) over |x| < a
+        a = geo["half"][0] + np.sqrt(geo["Da_ib"])
+        exact = geo["rho_b"] * geo["U_b"] * 4.0 * a / 3.0
+        assert abs(total - exact) < 2.0 * (1.0 / n) ** 2 * geo["U_b"] / a + 1e-14 * exact
+    # radial ejection: 2D form of Eq 4.19 -> flow 2 pi (R+s) rho_b U_b
+    g = Grid((256, 256), (1.0, 1.0))
+    geo = dict(kind=2, center=[0.5, 0.5], radius=0.1, Da_ib=1e-4, rho_b=1.0, U_b=1.0,
+               Z_ib=18.0, H_ib=1.2)
+    ib = build(g, geo)
+    total = float(np.sum(ib["Sm"]) * g.dV)
+    assert total == pytest.approx(2 * np.pi * 0.11, rel=2e-2)
+
+
+# ---------------------------------------------------------------------------
+# Verification formulas (Eqs 4.1-4.3) on a sequence with a known order
+# ---------------------------------------------------------------------------
+def test_convergence_formulas():
+    f = lambda h: 3.0 + 0.7 * h ** 2
+    assert observed_order(0.7 * 0.1 ** 2, 0.7 * 0.05 ** 2, 2.0) == pytest.approx(2.0)
+    assert richardson_order(f(0.2), f(0.1), f(0.05), 2.0) == pytest.approx(2.0)
+    assert gci(f(0.1), f(0.05), 2.0, 2.0) == pytest.approx(1.25 * abs((f(0.1) - f(0.05)) / f(0.05)) / 3.0)
+
+
+def test_variable_density_richardson_order():
+    """Three-level order (Eq 4.2) of a variable-density enclosed run without an
+    exact solution: the integral of Z^2 after a fixed time on 16^2, 32^2, 64^2."""
+    vals = []
+    for n in (16, 32, 64):
+        prm, geo, f = W.periodic_blobs(n)
+        prm["dt"] = 2.5e-5
+        pb = S.Problem(prm, geo)
+        g = pb.g
+        # a smooth initial state (one Fourier mode in Z, Taylor-Green velocity)
+        x, y = W.cell_centres((n, n), (1.0, 1.0))
+        Z0 = 2.0 + 1.5 * np.cos(2 * np.pi * x) * np.cos(2 * np.pi * y)
+        u0 = 0.1 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+        v0 = -0.1 * np.cos(2 * np.pi * x) * np.sin(2 * np.pi * y)
+        st = S.initial_state(pb, [u0, v0], Z0, f["H"])
+        for _ in range(80):
+            st = S.advance(pb, st)
+        vals.append(float(np.sum(V(st.Z, g) ** 2) * g.dV))
+    b = richardson_order(vals[0], vals[1], vals[2], 2.0)
+    assert 1.7 < b < 2.4, b
+
+
+# ---------------------------------------------------------------------------
+# Penalisation (Eqs 3.30-3.32): a body filling a periodic box relaxes v, Z, H
+# exponentially towards the targets; the discrete decay converges at second order
+# ---------------------------------------------------------------------------
+def _brinkman(dt, t_end=1.0):
+    prm, _, _ = W.taylor_green(8, dt)
+    prm.update(Re=50.0, Pr=0.5)              # Pe = 25
+    Da = 0.02
+    geo = dict(kind=W.IBM_SPHERE, center=[0.5, 0.5, 0.0], radius=10.0, Da_ib=Da, rho_b=1.0,
+               U_b=0.0, Z_ib=0.5, H_ib=3.0)
+    pb = S.Problem(prm, geo)
+    g = pb.g
+    ones = np.ones((8, 8))
+    st = S.initial_state(pb, [0.3 * ones, -0.2 * ones], 2.0 * ones, 1.0 * ones)
+    for _ in range(int(round(t_end / dt))):
+        st = S.advance(pb, st)
+    Pe = prm["Re"] * prm["Pr"]
+    lam_v = prm["Pr"] / (Pe * Da)            # Eq 3.30 with kappa = rho = 1
+    lam_s = 1.0 / (Pe * Da)                  # Eqs 3.31-3.32 with Le = 1
+    ev = abs(float(np.mean(V(st.v[0], g))) - 0.3 * np.exp(-lam_v * t_end))
+    eZ = abs(float(np.mean(V(st.Z, g))) - (0.5 + 1.5 * np.exp(-lam_s * t_end)))
+    eH = abs(float(np.mean(V(st.H, g))) - (3.0 - 2.0 * np.exp(-lam_s * t_end)))
+    return ev, eZ, eH
+
+
+def test_penalisation_relaxation_rates():
+    e1 = _brinkman(0.02)
+    e2 = _brinkman(0.01)
+    for a, b in zip(e1, e2):
+        assert a < 2e-3
+        assert observed_order(a, b, 2.0) == pytest.approx(2.0, abs=0.15)

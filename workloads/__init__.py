@@ -1,0 +1,221 @@
+"""Seeded synthetic workloads (input recipes) shared by the tests, the bench and
+the oracle checks.
+
+This module only builds inputs: the parameter record, the body description and
+the initial fields.  It holds none of the solver's arithmetic -- the state
+relation, the boundary treatment, the mask, the fluxes and the Poisson solve
+are implemented separately by the oracle and by the CUDA path.
+
+Conventions of the recipes (paper variables; Eqs 2.34-2.37, 4.21):
+  S = 1/Z_st - 1, Q = (ratio - 1)(S + 1)  so that the flame (Z = 1) temperature
+  is the density ratio; ambient air and fuel at T = 1, hence
+  H_inf = H_ib = 1 + (S+1)/Q ("zero excess enthalpy"), Z_air = 0, Z_fuel = S + 1.
+Initial fields are interior arrays of shape (n_y, n_x) / (n_z, n_y, n_x), x fastest.
+
+Workloads
+  taylor_green(n, dt)   Taylor-Green vortex (Eqs 4.4-4.6), constant density.
+  periodic_blobs(...)   2D doubly periodic enclosed box, 8 Gaussian mixture-fraction
+                        blobs, solenoidal random velocity (rms 0.1), 64x64.
+  slot_burner(...)      2D planar slot burner, 256x512 on [0,1]x[0,2].
+  sphere_burner(...)    3D spherical porous burner, 192^3 on [0,1]^3.
+"""
+
+import numpy as np
+
+PERIODIC, INFLOW, OUTFLOW, WALL, SLIP = 0, 1, 2, 3, 4
+IBM_NONE, IBM_SLOT, IBM_SPHERE = 0, 1, 2
+FP64, MIXED = 0, 1
+
+SEED = 20260101
+
+
+def _base_params():
+    return dict(
+        dim=2, n=[0, 0, 1], L=[1.0, 1.0, 1.0],
+        bc=[[PERIODIC, PERIODIC], [PERIODIC, PERIODIC], [PERIODIC, PERIODIC]],
+        inflow_v=[0.0, 0.0, 0.0], inflow_Z=0.0, inflow_H=0.0,
+        Re=100.0, Pr=0.7, inv_Fr2=0.0, Le_F=1.0, Le_O=1.0, gamma=1.4, sigma=0.7,
+        Z_st=0.055, density_ratio=7.0, eps_reg=0.5, tol_reg=1e-3,
+        closed_system=0, incompressible=0, dt=0.0,
+        precision=FP64, poisson_rtol=1e-10, poisson_max_iter=200)
+
+
+def paper_scalars(Z_st, ratio):
+    """(S, Q, H_inf, Z_fuel) of the recipe conventions above."""
+    S = 1.0 / Z_st - 1.0
+    Q = (ratio - 1.0) * (S + 1.0)
+    return S, Q, 1.0 + (S + 1.0) / Q, S + 1.0
+
+
+def cell_centres(n, L):
+    """Coordinates of interior cell centres, one array per direction."""
+    dim = len(n)
+    axes = [(np.arange(n[d]) + 0.5) * (L[d] / n[d]) for d in range(dim)]
+    grids = np.meshgrid(*reversed(axes), indexing="ij")     # (z), y, x order
+    return list(reversed(grids))                             # x, y, (z)
+
+
+def stable_dt(n, L, Re, Pr, ratio, sigma, U, cfl, Da_ib=None, dim=2):
+    """Fixed time step of a run: CFL-scaled minimum of the convective limit,
+    the explicit-diffusion limit at the hottest, lightest state (kappa = T_f^sigma,
+    rho = 1/T_f) and, with a body, the penalisation limit dt <= Re Da_ib."""
+    h = min(L[d] / n[d] for d in range(dim))
+    T_f = ratio
+    kap_max = T_f ** sigma
+    rho_min = 1.0 / T_f
+    lim = [h / U, h * h * Re * min(1.0, Pr) * rho_min / (2.0 * dim * kap_max)]
+    if Da_ib is not None:
+        lim.append(Re * Da_ib * rho_min / kap_max)
+    return cfl * min(lim)
+
+
+def _solenoidal_2d(rng, n, L, kmax, rms):
+    """delta_2-curl of a random periodic streamfunction (modes 0 < |k| <= kmax),
+    scaled to the requested rms speed."""
+    x, y = cell_centres(n, L)
+    psi = np.zeros(x.shape)
+    for kx in range(-kmax, kmax + 1):
+        for ky in range(-kmax, kmax + 1):
+            k2 = kx * kx + ky * ky
+            if k2 == 0 or k2 > kmax * kmax:
+                continue
+            amp = rng.normal() / np.sqrt(k2)
+            ph = rng.uniform(0.0, 2.0 * np.pi)
+            psi += amp * np.cos(2.0 * np.pi * (kx * x / L[0] + ky * y / L[1]) + ph)
+    hx, hy = L[0] / n[0], L[1] / n[1]
+    u = (np.roll(psi, -1, axis=0) - np.roll(psi, 1, axis=0)) / (2.0 * hy)
+    v = -(np.roll(psi, -1, axis=1) - np.roll(psi, 1, axis=1)) / (2.0 * hx)
+    s = rms / np.sqrt(np.mean(u * u + v * v))
+    return u * s, v * s
+
+
+def taylor_green(n=50, dt=4e-3, Re=100.0):
+    """Taylor-Green vortex on the unit periodic square (Sec. 4.2): exact
+    velocity of Eqs 4.4-4.5 at t = 0; constant density."""
+    prm = _base_params()
+    prm.update(dim=2, n=[n, n, 1], L=[1.0, 1.0, 1.0], Re=Re, Pr=1.0, incompressible=1, dt=dt,
+               poisson_rtol=1e-13)
+    x, y = cell_centres((n, n), (1.0, 1.0))
+    u = np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    v = -np.cos(2 * np.pi * x) * np.sin(2 * np.pi * y)
+    fields = dict(v=[u, v], Z=np.zeros_like(u), H=np.ones_like(u))
+    return prm, None, fields
+
+
+def taylor_green_exact(n, t, Re=100.0):
+    """Eqs 4.4-4.6 at the cell centres."""
+    x, y = cell_centres((n, n), (1.0, 1.0))
+    e1 = np.exp(-8 * np.pi ** 2 * t / Re)
+    e2 = np.exp(-16 * np.pi ** 2 * t / Re)
+    u = np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) * e1
+    v = -np.cos(2 * np.pi * x) * np.sin(2 * np.pi * y) * e1
+    p = 0.25 * (np.cos(4 * np.pi * x) + np.cos(4 * np.pi * y)) * e2
+    return u, v, p
+
+
+def periodic_blobs(n=64, seed=SEED, cfl=0.4, nblobs=8):
+    """2D doubly periodic enclosed box: Z_c = clip(sum of 8 Gaussian blobs, 0, 1)
+    with amplitude U[0.3,1], width U[0.05,0.15] L, centre U[0,1)^2 (minimum-image
+    periodic distance); H = H_inf; velocity the delta_2-curl of a random
+    streamfunction (|k| <= 4) scaled to rms 0.1; Z_st = 0.055, density ratio 7,
+    Le = 1, Re = 100, Pr = 0.7; enclosed (p0 from the mass constraint)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    prm = _base_params()
+    ny = nx = n
+    prm.update(dim=2, n=[nx, ny, 1], L=[1.0, 1.0, 1.0], Re=100.0, Pr=0.7, closed_system=1)
+    S, Q, H_inf, Z_fuel = paper_scalars(prm["Z_st"], prm["density_ratio"])
+    x, y = cell_centres((nx, ny), (1.0, 1.0))
+    Zc = np.zeros(x.shape)
+    for _ in range(nblobs):
+        a = rng.uniform(0.3, 1.0)
+        s = rng.uniform(0.05, 0.15)
+        cx, cy = rng.uniform(0.0, 1.0, size=2)
+        dx = (x - cx + 0.5) % 1.0 - 0.5
+        dy = (y - cy + 0.5) % 1.0 - 0.5
+        Zc += a * np.exp(-(dx * dx + dy * dy) / (2.0 * s * s))
+    Zc = np.clip(Zc, 0.0, 1.0)
+    u, v = _solenoidal_2d(rng, (nx, ny), (1.0, 1.0), 4, 0.1)
+    Umax = float(np.max(np.sqrt(u * u + v * v)))
+    prm["dt"] = stable_dt((nx, ny), (1.0, 1.0), prm["Re"], prm["Pr"], prm["density_ratio"],
+                          prm["sigma"], Umax, cfl)
+    fields = dict(v=[u, v], Z=Z_fuel * Zc, H=np.full(x.shape, H_inf))
+    return prm, None, fields
+
+
+def slot_burner(nx=256, ny=512, cfl=0.4, Re=200.0, profile=None, U_coflow=0.2):
+    """2D planar slot burner: [0,1] x [0,2], periodic in x; bottom inflow of air
+    (v = (0, U_coflow), Z = 0, H = H_inf) outside the burner foot; top outflow.
+    Immersed rectangular burner 0.1 x 0.3 standing on the bottom boundary at
+    x = 0.5 (centre (0.5, 0.15), half-sizes (0.05, 0.15)), ejecting fuel
+    (Z = S+1, T = 1) through its top face with a parabolic mass-flux profile of
+    peak U_b = 1; Da_ib = 1e-4.  Initial state: fuel at rest inside the
+    (unshifted) burner box, falling off outside it as a Gaussian of the distance
+    to the box (width max(0.04, 10 dy)), and coflow air far from it."""
+    prm = _base_params()
+    prm.update(dim=2, n=[nx, ny, 1], L=[1.0, 2.0, 1.0], Re=Re, Pr=0.7,
+               bc=[[PERIODIC, PERIODIC], [INFLOW, OUTFLOW], [PERIODIC, PERIODIC]],
+               inflow_v=[0.0, U_coflow, 0.0])
+    S, Q, H_inf, Z_fuel = paper_scalars(prm["Z_st"], prm["density_ratio"])
+    prm.update(inflow_Z=0.0, inflow_H=H_inf)
+    Da = 1e-4
+    geo = dict(kind=IBM_SLOT, center=[0.5, 0.15, 0.0], half=[0.05, 0.15, 0.0], radius=0.0,
+               Da_ib=Da, rho_b=1.0, U_b=1.0, Z_ib=Z_fuel, H_ib=H_inf,
+               profile=None if profile is None else list(profile))
+    x, y = cell_centres((nx, ny), (1.0, 2.0))
+    # distance to the (unshifted) burner box; Gaussian fall-off of the fuel
+    # outside it, wide enough (>= 10 cells) that the Z = 1 flame is resolved
+    dx = np.maximum(np.abs(x - 0.5) - 0.05, 0.0)
+    dy = np.maximum(y - 0.3, 0.0)
+    dist = np.sqrt(dx * dx + dy * dy)
+    w = max(0.04, 10.0 * 2.0 / ny)
+    shape = np.exp(-dist * dist / (2.0 * w * w))
+    u = np.zeros(x.shape)
+    v = U_coflow * (1.0 - shape)
+    Z = Z_fuel * shape
+    H = np.full(x.shape, H_inf)
+    prm["dt"] = stable_dt((nx, ny), (1.0, 2.0), Re, prm["Pr"], prm["density_ratio"],
+                          prm["sigma"], 1.0, cfl, Da_ib=Da)
+    return prm, geo, dict(v=[u, v], Z=Z, H=H)
+
+
+def sphere_burner(n=192, cfl=0.4, Re=150.0, seed=SEED, rms=0.01):
+    """3D spherical porous burner: [0,1]^3, outflow on all sides; sphere of
+    radius 0.1 at the centre ejecting fuel radially with U_b = 1; quiescent air
+    plus a seeded solenoidal perturbation of rms 0.01 (delta_2-curl of a random
+    vector potential with modes |k| <= 3); fuel inside the sphere, falling off
+    outside it as a Gaussian of the distance (width max(0.04, 10 dx))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    prm = _base_params()
+    prm.update(dim=3, n=[n, n, n], L=[1.0, 1.0, 1.0], Re=Re, Pr=0.7,
+               bc=[[OUTFLOW, OUTFLOW]] * 3)
+    S, Q, H_inf, Z_fuel = paper_scalars(prm["Z_st"], prm["density_ratio"])
+    prm.update(inflow_Z=0.0, inflow_H=H_inf)
+    Da = 1e-4
+    geo = dict(kind=IBM_SPHERE, center=[0.5, 0.5, 0.5], half=[0.0, 0.0, 0.0], radius=0.1,
+               Da_ib=Da, rho_b=1.0, U_b=1.0, Z_ib=Z_fuel, H_ib=H_inf, profile=None)
+    x, y, z = cell_centres((n, n, n), (1.0, 1.0, 1.0))
+    h = 1.0 / n
+    A = [np.zeros(x.shape) for _ in range(3)]
+    for c in range(3):
+        for _ in range(6):
+            k = rng.integers(-3, 4, size=3)
+            if not k.any():
+                continue
+            ph = rng.uniform(0, 2 * np.pi)
+            A[c] += rng.normal() * np.cos(2 * np.pi * (k[0] * x + k[1] * y + k[2] * z) + ph)
+
+    def d2(a, d):
+        ax = 2 - d
+        return (np.roll(a, -1, axis=ax) - np.roll(a, 1, axis=ax)) / (2 * h)
+    u = d2(A[2], 1) - d2(A[1], 2)
+    v = d2(A[0], 2) - d2(A[2], 0)
+    w = d2(A[1], 0) - d2(A[0], 1)
+    s = rms / np.sqrt(np.mean(u * u + v * v + w * w))
+    r = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)
+    dist = np.maximum(r - 0.1, 0.0)
+    w = max(0.04, 10.0 / n)
+    Z = Z_fuel * np.exp(-dist * dist / (2.0 * w * w))
+    H = np.full(x.shape, H_inf)
+    prm["dt"] = stable_dt((n, n, n), (1.0, 1.0, 1.0), Re, prm["Pr"], prm["density_ratio"],
+                          prm["sigma"], 1.0, cfl, Da_ib=Da, dim=3)
+    return prm, geo, dict(v=[u * s, v * s, w * s], Z=Z, H=H)
