@@ -84,7 +84,7 @@ class Boundary:
                 elif what == "H":
                     dirichlet = self.inflow_H
                 elif what == "kappa":
-                    dirichlet = kappa_in
+                    dirichlet = kappa_in if kappa_in is not None else 0.0   # no inflow side
                 else:
                     dirichlet = self.inflow_v[comp]
                 mirror_in = 2.0 * dirichlet - a1                     # Eq 3.43 (Phi = inflow)
