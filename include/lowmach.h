@@ -1,0 +1,224 @@
+/*
+ * lowmach.h -- C ABI of the GB300 (sm_103a) implementation of one time step of
+ * the low-Mach-number flame-sheet solver of Severino, Fachini, Gennaro,
+ * Rodriguez & Souza, "Numerical method for strongly variable-density flows at
+ * low Mach number: flame-sheet regularisation and a mass-flux immersed boundary
+ * method" (arXiv 2603.01727).
+ *
+ * The method (paper Secs 2.4-3.6): zero-Mach-number reacting flow in the
+ * Burke-Schumann limit with unknowns v, Z, H, P = p dt and p0(t); a
+ * predictor (Adams-Bashforth 2) / corrector (Adams-Moulton 2) fractional step
+ * (Eqs 3.1-3.19) on a collocated Cartesian grid with auxiliary interface mass
+ * fluxes (Eqs 3.20-3.26); a Poisson equation for P per stage (Eqs 3.9, 3.17,
+ * 3.24); Brinkman-penalised immersed bodies with a mass source (Eqs 3.29-3.33);
+ * and the regularised flame-sheet state relation (Eqs 3.34-3.42).
+ *
+ * Conventions shared by every entry point
+ *   - All floating-point data is IEEE binary64 unless stated otherwise.
+ *   - Cell fields are x-fastest arrays of the interior cells only, n[0]*n[1]
+ *     (2D) or n[0]*n[1]*n[2] (3D) entries: index i + n0*(j + n1*k).
+ *     Interface (face) fields along direction d have n[d]+1 entries along d
+ *     and n entries along the others, x fastest.
+ *   - Device memory is never allocated by the library.  The caller passes one
+ *     device workspace of at least sim_workspace_size() bytes (256-byte
+ *     aligned) to sim_create and keeps it alive until sim_destroy.
+ *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *     void*; NULL = legacy default stream).  sim_step returns after enqueueing
+ *     the work and checking the previous step's device status word.
+ *   - Errors are returned as sim_status codes; nothing aborts or throws
+ *     across the ABI; sim_last_error() gives a human-readable reason.
+ */
+#ifndef LOWMACH_H
+#define LOWMACH_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sim sim_t;
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_EINVAL = -1,     /* invalid argument or unsupported configuration            */
+    SIM_ENOMEM = -2,     /* workspace smaller than sim_workspace_size()              */
+    SIM_ECUDA = -3,      /* a CUDA runtime call failed                               */
+    SIM_ENOCONV = -4,    /* a Poisson solve hit poisson_max_iter before rtol         */
+    SIM_ENAN = -5,       /* a non-finite value appeared in the state                 */
+    SIM_EUNSTABLE = -6,  /* dt violates the explicit penalisation limit dt < Re Da_ib */
+    SIM_ESTATE = -7      /* call out of order (e.g. step before the fields are set)  */
+} sim_status;
+
+/* Boundary kinds of a domain side (paper Sec. 3.6, Eqs 3.43-3.46). */
+enum {
+    SIM_BC_PERIODIC = 0, /* Eq 3.45; both sides of a direction must be periodic       */
+    SIM_BC_INFLOW = 1,   /* Dirichlet v, Z, H (Eq 3.43); known mass flux rho_in v_in  */
+    SIM_BC_OUTFLOW = 2,  /* zero-gradient v, Z, H (Eq 3.44); extrapolated mass flux,
+                            shifted uniformly to close the global mass balance
+                            (text after Eq 4.22)                                      */
+    SIM_BC_WALL = 3,     /* no-slip v = 0, zero-gradient Z, H, zero mass flux        */
+    SIM_BC_SLIP = 4      /* symmetry plane (Eqs 4.22a-b): v_n = 0, zero-gradient rest */
+};
+
+enum { SIM_FP64 = 0, SIM_MIXED = 1 };
+enum { SIM_IBM_NONE = 0, SIM_IBM_SLOT = 1, SIM_IBM_SPHERE = 2 };
+
+/* Run parameters (paper notation, Eqs 2.42-2.50). */
+typedef struct {
+    int dim;                 /* 2 or 3                                                  */
+    int n[3];                /* interior cells per direction (n[2] ignored in 2D)       */
+    double L[3];             /* domain lengths; uniform spacing h_d = L_d / n_d         */
+    int bc[3][2];            /* SIM_BC_* of the low / high side of each direction       */
+    double inflow_v[3];      /* Dirichlet velocity of SIM_BC_INFLOW sides               */
+    double inflow_Z;         /* Dirichlet rescaled mixture fraction of inflow sides     */
+    double inflow_H;         /* Dirichlet excess enthalpy of inflow sides               */
+    double Re, Pr;           /* Reynolds (Re = Pe/Pr) and Prandtl numbers               */
+    double inv_Fr2;          /* 1/Fr^2 of the buoyancy term (Eq 3.8b)                   */
+    double Le_F, Le_O;       /* fuel / oxidiser Lewis numbers (Eq 3.35)                 */
+    double gamma;            /* ratio of specific heats (zeta, text after Eq 2.45)      */
+    double sigma;            /* transport exponent, kappa = T^sigma (Eq 2.50)           */
+    double Z_st;             /* stoichiometric conventional mixture fraction: S = 1/Z_st - 1 */
+    double density_ratio;    /* flame / ambient temperature: Q = (ratio - 1)(S + 1)     */
+    double eps_reg, tol_reg; /* regularisation: k = ln((1-tol)/tol) / (2 eps) (Eq 3.34)  */
+    int closed_system;       /* 1: p0 from the mass constraint (Eq 2.40); 0: p0 = 1 (Eq 2.41) */
+    int incompressible;      /* 1: T = rho = kappa = p0 = 1 (constant-density runs)     */
+    double dt;               /* fixed time step (> 0)                                   */
+    int precision;           /* SIM_FP64 (only value accepted by this version)          */
+    double poisson_rtol;     /* stop when ||r||_2 / ||f||_2 <= rtol (0 < rtol < 1)      */
+    int poisson_max_iter;    /* PCG iteration cap (>= 1)                                */
+} sim_params_t;
+
+/* Immersed burner (paper Sec. 3.4; Eqs 3.30-3.33, 4.19-4.21).  The mask is the
+ * set of cells whose centre lies within sqrt(Da_ib) of the body (shifted
+ * characteristic function).  SLOT: box [center-half, center+half] ejecting
+ * through its +x_2 face with U(x_1) = U_b [1 - ((x_1-c_1)/(half_1+s))^2]_+ times
+ * the piecewise-linear interpolant of profile[0..n_profile-1] sampled uniformly
+ * over the shifted width (profile may be NULL); v_ib = (0, U (x_2-y_lo)/(y_hi-y_lo)),
+ * S_m = rho_b U / (n_col h_2) on the n_col masked cells of each column.
+ * SPHERE (circle in 2D): v_ib = U_b (x-c)/r, S_m = (dim-1) rho_b U_b / r. */
+typedef struct {
+    int kind;                /* SIM_IBM_*                                              */
+    double center[3];
+    double half[3];          /* SLOT half-sizes                                        */
+    double radius;           /* SPHERE radius                                          */
+    double Da_ib;            /* immersed-boundary Darcy number (> 0)                   */
+    double rho_b, U_b;       /* ejected density and velocity scale                     */
+    double Z_ib, H_ib;       /* body targets in the paper's variables (Eq 4.21)        */
+    int n_profile;           /* number of profile samples (0: none)                    */
+    const double *profile;   /* host pointer, copied during the call                   */
+} sim_ibm_t;
+
+/* Field identifiers for sim_fields. */
+enum {
+    SIM_FIELD_U = 0, SIM_FIELD_V = 1, SIM_FIELD_W = 2,   /* velocity components        */
+    SIM_FIELD_Z = 3, SIM_FIELD_H = 4,                     /* transported scalars        */
+    SIM_FIELD_T = 5, SIM_FIELD_RHO = 6,                   /* state relation outputs     */
+    SIM_FIELD_P = 7,                                      /* P = p dt, zero mean        */
+    SIM_FIELD_FX = 8, SIM_FIELD_FY = 9, SIM_FIELD_FZ = 10,/* interface mass fluxes (faces) */
+    SIM_FIELD_CHI = 11,                                   /* mask (0/1 as double)       */
+    SIM_FIELD_SM = 12,                                    /* mass source S_m            */
+    SIM_FIELD_KAPPA = 13
+};
+enum { SIM_GET = 0, SIM_SET = 1 };
+
+/* Scalars for sim_query. */
+enum {
+    SIM_Q_TIME = 0, SIM_Q_DT = 1, SIM_Q_P0 = 2, SIM_Q_STEPS = 3,
+    SIM_Q_ITERS_PRED = 4, SIM_Q_ITERS_CORR = 5,     /* PCG iterations of the last step */
+    SIM_Q_RESID_PRED = 6, SIM_Q_RESID_CORR = 7,     /* final ||r||/||f|| of the last step */
+    SIM_Q_MASS = 8, SIM_Q_NCELLS = 9, SIM_Q_MG_LEVELS = 10,
+    SIM_Q_KERNEL_LAUNCHES = 11                      /* kernels enqueued by the last sim_step */
+};
+
+/* Bytes of device workspace sim_create needs for these parameters. */
+sim_status sim_workspace_size(const sim_params_t *prm, size_t *bytes);
+
+/* Validate prm, derive S, Q, k, Pe, zeta, N_F, N_O (paper Eqs 2.34-2.37, 3.34),
+ * lay out every device array inside d_workspace and build the multigrid
+ * hierarchy of the pressure solver.  No body until sim_set_ibm_geometry; no
+ * state until the fields U, V, (W,) Z, H are set with sim_fields. */
+sim_status sim_create(const sim_params_t *prm, void *d_workspace, size_t workspace_bytes,
+                      void *cuda_stream, sim_t **out);
+
+/* Set (or with geo == NULL / kind == SIM_IBM_NONE, clear) the immersed body:
+ * computes chi, v_ib and S_m on the device (paper Sec. 3.4).  Returns
+ * SIM_EUNSTABLE if dt >= Re Da_ib (explicit penalisation limit, text after
+ * Eq 3.30).  Must precede the first sim_step after the fields are set. */
+sim_status sim_set_ibm_geometry(sim_t *sim, const sim_ibm_t *geo);
+
+/* Copy a field between the library and buf (interior cells / faces, layout
+ * above).  dir = SIM_GET copies out, SIM_SET copies in (only U, V, W, Z, H may
+ * be set; setting them starts a new run at t = 0 from those fields: T, rho,
+ * kappa, F^0 and the mass are derived at the next sim_step).  on_device = 1:
+ * buf is a device pointer, else a host pointer.  Synchronous with respect to
+ * the host for on_device = 0. */
+sim_status sim_fields(sim_t *sim, int field_id, void *buf, int dir, int on_device);
+
+/* Advance nsteps time steps (predictor + corrector each, Eqs 3.1-3.19).  The
+ * first step of a run uses Euler in the predictor (text after Eq 3.19). */
+sim_status sim_step(sim_t *sim, int nsteps);
+
+/* Wait for the enqueued work and return the device status: SIM_ENOCONV if a
+ * Poisson solve did not reach rtol, SIM_ENAN if a non-finite value appeared. */
+sim_status sim_sync(sim_t *sim);
+
+/* Read one scalar (SIM_Q_*); synchronises the stream. */
+sim_status sim_query(sim_t *sim, int what, double *out);
+
+/* Restart state (checkpoint / resume): every array and scalar the next step
+ * reads -- v, Z, H, T, kappa, rho^n and rho^(n-1), the interface fluxes F^n, the
+ * stored residuals of the last predictor, P, p0 history, mass, step counter and
+ * time -- in one opaque little-endian blob of sim_state_size() bytes with a
+ * header that identifies the grid.  save copies the blob out (synchronises);
+ * load copies it in and the next sim_step continues from it exactly as if the
+ * run had never stopped (SIM_EINVAL if the header does not match this grid).
+ * buf is a device pointer when on_device = 1, else a host pointer. */
+sim_status sim_state_size(const sim_t *sim, size_t *bytes);
+sim_status sim_state_save(sim_t *sim, void *buf, int on_device);
+sim_status sim_state_load(sim_t *sim, const void *buf, int on_device);
+
+/* Kernel timing support: enqueue `reps` back-to-back launches of one kernel of
+ * the next step with that step's arguments (no synchronisation), so a caller
+ * can bracket them with CUDA events on the stream.  Only scratch of the step is
+ * written (stage temporaries, Krylov and multigrid vectors), never the state.
+ * kernel: SIM_K_* below.  Returns SIM_ESTATE before the first step. */
+enum {
+    SIM_K_RESIDUAL = 0,   /* predictor stencil pass (residuals + AB2 update)      */
+    SIM_K_SMOOTH = 1,     /* one red-black Gauss-Seidel colour on the fine level  */
+    SIM_K_MATVEC = 2,     /* CG operator application + dot product, fine level    */
+    SIM_K_RESTRICT = 3,   /* fine-level residual + restriction to level 1         */
+    SIM_K_STATE = 4,      /* flame-sheet state relation                           */
+    SIM_K_PROJECT = 5     /* interface fluxes + cell velocities (projection)      */
+};
+sim_status sim_time_kernel(sim_t *sim, int kernel, int reps);
+
+/* Reason of the last failing call on this handle (static storage of the handle). */
+const char *sim_last_error(const sim_t *sim);
+
+void sim_destroy(sim_t *sim);
+
+/* ---------------------------------------------------------------------------
+ * Stand-alone pressure solve (the step's dominant kernel, paper Eqs 3.9/3.24):
+ * zero-mean P with sum_d delta_1(delta_1 P/delta_1 x_d)/delta_1 x_d = b - mean(b)
+ * on a uniform grid; periodic[d] != 0 selects a periodic direction, else
+ * homogeneous Neumann (known boundary mass flux, Sec. 3.3).  Multigrid-
+ * preconditioned conjugate gradients to ||r||_2/||f||_2 <= rtol; P holds the
+ * warm start on entry.  d_b and d_P are device arrays of n0*n1(*n2) doubles.
+ * The workspace (device, >= sim_poisson_workspace_size bytes, 256-byte
+ * aligned) holds the multigrid hierarchy and the Krylov vectors.  iters and
+ * rel_resid (host pointers, may be NULL) receive the iteration count and the
+ * final relative residual; the call synchronises the stream.
+ * Returns SIM_ENOCONV if max_iter was reached first.
+ * ------------------------------------------------------------------------- */
+sim_status sim_poisson_workspace_size(int dim, const int n[3], const int periodic[3],
+                                      size_t *bytes);
+sim_status sim_poisson_solve(int dim, const int n[3], const double h[3], const int periodic[3],
+                             const double *d_b, double *d_P, double rtol, int max_iter,
+                             void *d_workspace, size_t workspace_bytes, void *cuda_stream,
+                             int *iters, double *rel_resid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOWMACH_H */

@@ -1,0 +1,110 @@
+// Shared device-side definitions of the sm_103a path: grid geometry, the
+// padded field layout, physical constants of a run and block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lm {
+
+constexpr int kMaxDim = 3;
+
+enum BcKind : int { BC_PERIODIC = 0, BC_INFLOW = 1, BC_OUTFLOW = 2, BC_WALL = 3, BC_SLIP = 4 };
+
+// Grid geometry.  Cell fields live in a padded array with one ghost layer on
+// each side of every active direction (ghost index 0 and n+1, interior 1..n),
+// x fastest.  In 2D the z extent is 1 and has no ghosts.
+struct Geom {
+    int dim;
+    int n[3];        // interior cells (n[2] = 1 in 2D)
+    int p[3];        // padded extents
+    long long s[3];  // strides of the padded array (s[0] = 1)
+    long long npad;  // padded cells
+    long long ncell; // interior cells
+    double h[3];     // spacing
+    double ih[3];    // 1 / h
+    double ih2[3];   // 1 / h^2
+    double dV;       // cell volume
+    int periodic[3];
+};
+
+// Interior linear index t (x fastest over the interior) -> padded index.
+__host__ __device__ inline long long pad_index(const Geom& g, long long t) {
+    int i = (int)(t % g.n[0]);
+    long long r = t / g.n[0];
+    int j = (int)(r % g.n[1]);
+    int k = (int)(r / g.n[1]);
+    long long kz = (g.dim == 3) ? (k + 1) : 0;
+    return (long long)(i + 1) + (long long)(j + 1) * g.s[1] + kz * g.s[2];
+}
+
+__host__ __device__ inline void interior_coords(const Geom& g, long long t, int c[3]) {
+    c[0] = (int)(t % g.n[0]);
+    long long r = t / g.n[0];
+    c[1] = (int)(r % g.n[1]);
+    c[2] = (int)(r / g.n[1]);
+}
+
+// Physical constants of a run (paper notation), derived once on the host.
+struct Phys {
+    double S, Q, k, Pe, PrPe, zeta;   // Eqs 2.34-2.37, 3.34; PrPe = Pr/Pe
+    double Le_F, Le_O, N_F, N_O;       // Eqs 3.35a-b
+    double sigma, inv_Fr2;
+    double Fshift;                     // level translation of F_eps (text after Eq 3.41)
+    double kappa_in, rho_in_T;         // inflow transport coefficient, inflow temperature
+    double inflow_v[3], inflow_Z, inflow_H;
+    int incompressible, closed;
+};
+
+// ---------------------------------------------------------------------------
+// Deterministic block reduction (fixed tree for a fixed block size).
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ inline double block_sum(double v, double* smem /* NT/32 doubles */) {
+    static_assert(NT % 32 == 0 && NT <= 1024, "block size");
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) smem[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (l < NT / 32) ? smem[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if (l == 0) smem[0] = r;
+    }
+    __syncthreads();
+    r = smem[0];
+    __syncthreads();
+    return r;
+}
+
+// Sum of npart partial sums, every thread of the block gets the same value
+// (same order of additions in every block, so the result is bitwise identical).
+template <int NT>
+__device__ inline double sum_partials(const double* part, int npart, double* smem) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < npart; i += NT) v += part[i];
+    return block_sum<NT>(v, smem);
+}
+
+constexpr int kThreads = 256;     // block size of the stencil / vector kernels
+constexpr int kMaxPartials = 2048; // capacity of a partial-sum buffer
+
+inline int blocks_for(long long n, int nt = kThreads) {
+    long long b = (n + nt - 1) / nt;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// Grid-stride launch bounded by the partial-sum capacity.
+inline int reduce_blocks(long long n, int nt = kThreads) {
+    long long b = (n + nt - 1) / nt;
+    if (b > kMaxPartials) b = kMaxPartials;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace lm

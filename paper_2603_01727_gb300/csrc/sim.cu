@@ -1,0 +1,1116 @@
+// C ABI of the low-Mach flame-sheet step (include/lowmach.h) and the host-side
+// orchestration of one time step: the predictor / corrector launch sequence of
+// paper Sec. 3.1 (Eqs 3.1-3.19), CUDA-graph capture of a whole step with one
+// conditional while node per pressure solve, and the t = 0 initialisation.
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/lowmach.h"
+#include "poisson.cuh"
+#include "step.cuh"
+
+using namespace lm;
+
+namespace {
+
+constexpr int kMaxProfile = 4096;
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct sim {
+    sim_params_t prm;
+    Geom g;
+    Phys ph;
+    cudaStream_t stream;   // caller's stream (work is enqueued here)
+    cudaStream_t cap;      // private stream used for graph capture
+    cudaStream_t side;     // private stream used to capture while-node bodies
+
+    double* v[3];
+    double* vs[3];
+    double *Z, *H, *Zs, *Hs, *T, *kap;
+    double* rho[3];
+    double* mom[3];
+    double* F[3];
+    double* R[2][5];
+    double* vib[3];
+    double *Sm, *U;
+    double *P, *b, *io;
+    double* part;
+    double* part2;
+    double* sc;
+    double* profile;
+    int* status;
+    uint8_t* chi;
+    uint8_t* kind[3][2];
+
+    PoissonPlan pp;
+    std::vector<double> minv;
+    Bnd bnd;
+    double eA, eB, eC;
+
+    int ibm_active;
+    double Z_ib, H_ib, Da;
+
+    int fields_set;        // bit mask of U, V, W, Z, H set since create
+    bool need_init;
+    long long nstep;
+    int rho_base;
+    double t;
+
+    int launches_last;
+    int launches_fixed_graph[6];
+    int body_launches;
+    cudaGraphExec_t gexec[6];
+    bool gvalid[6];
+    int use_graph;
+
+    char err[512];
+};
+
+namespace {
+
+sim_status fail(sim_t* s, sim_status st, const char* fmt, ...) {
+    if (s) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(s->err, sizeof(s->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return fail(s, SIM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+Geom make_geom(const sim_params_t* p) {
+    Geom g;
+    std::memset(&g, 0, sizeof(g));
+    g.dim = p->dim;
+    for (int d = 0; d < 3; ++d) {
+        const bool act = d < p->dim;
+        g.n[d] = act ? p->n[d] : 1;
+        g.p[d] = act ? p->n[d] + 2 : 1;
+        g.h[d] = act ? p->L[d] / p->n[d] : 1.0;
+        g.ih[d] = 1.0 / g.h[d];
+        g.ih2[d] = g.ih[d] * g.ih[d];
+        g.periodic[d] = act ? (p->bc[d][0] == SIM_BC_PERIODIC) : 0;
+    }
+    g.s[0] = 1;
+    g.s[1] = g.p[0];
+    g.s[2] = (long long)g.p[0] * g.p[1];
+    g.npad = (long long)g.p[0] * g.p[1] * g.p[2];
+    g.ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    g.dV = 1.0;
+    for (int d = 0; d < p->dim; ++d) g.dV *= g.h[d];
+    return g;
+}
+
+double host_temperature(const Phys& ph, double z, double h) {
+    const double x = ph.k * (z - 1.0);
+    const double ax = std::fabs(x);
+    const double F =
+        (-(ph.S + 1.0) * (ax + std::log1p(std::exp(-2.0 * ax))) / ph.k + (ph.S - 1.0) * (z - 1.0)) / (2.0 * ph.S);
+    return ph.Q / (ph.S + 1.0) * (F + h);
+}
+
+Phys make_phys(const sim_params_t* p) {
+    Phys ph;
+    std::memset(&ph, 0, sizeof(ph));
+    ph.S = 1.0 / p->Z_st - 1.0;                                  // Eq 2.34 with Z_st
+    ph.Q = (p->density_ratio - 1.0) * (ph.S + 1.0);              // flame temperature = ratio
+    ph.k = std::log((1.0 - p->tol_reg) / p->tol_reg) / (2.0 * p->eps_reg);  // text after Eq 3.34
+    ph.Pe = p->Re * p->Pr;
+    ph.PrPe = p->Pr / ph.Pe;
+    ph.zeta = (ph.S + 1.0) * (p->gamma - 1.0) / (p->gamma * ph.Q);
+    ph.Le_F = p->Le_F;
+    ph.Le_O = p->Le_O;
+    ph.N_F = (1.0 - p->Le_F) / (ph.S * p->Le_F);
+    ph.N_O = (p->Le_O - 1.0) / p->Le_O;
+    ph.sigma = p->sigma;
+    ph.inv_Fr2 = p->inv_Fr2;
+    for (int d = 0; d < 3; ++d) ph.inflow_v[d] = p->inflow_v[d];
+    ph.inflow_Z = p->inflow_Z;
+    ph.inflow_H = p->inflow_H;
+    ph.incompressible = p->incompressible;
+    ph.closed = p->closed_system && !p->incompressible;
+    bool inflow = false;
+    for (int d = 0; d < p->dim; ++d)
+        for (int q = 0; q < 2; ++q) inflow |= (p->bc[d][q] == SIM_BC_INFLOW);
+    if (p->incompressible) {
+        ph.rho_in_T = 1.0;
+        ph.kappa_in = 1.0;
+    } else if (inflow) {
+        ph.rho_in_T = host_temperature(ph, p->inflow_Z, p->inflow_H);
+        ph.kappa_in = std::pow(ph.rho_in_T, p->sigma);
+    } else {
+        ph.rho_in_T = 1.0;
+        ph.kappa_in = 1.0;
+    }
+    return ph;
+}
+
+const char* validate(const sim_params_t* p) {
+    if (!p) return "null parameters";
+    if (p->dim != 2 && p->dim != 3) return "dim must be 2 or 3";
+    for (int d = 0; d < p->dim; ++d) {
+        if (p->n[d] < 4) return "every extent must be >= 4 cells";
+        if (!(p->L[d] > 0.0)) return "domain lengths must be > 0";
+        for (int q = 0; q < 2; ++q)
+            if (p->bc[d][q] < SIM_BC_PERIODIC || p->bc[d][q] > SIM_BC_SLIP) return "unknown boundary kind";
+        if ((p->bc[d][0] == SIM_BC_PERIODIC) != (p->bc[d][1] == SIM_BC_PERIODIC))
+            return "a periodic side needs a periodic partner";
+    }
+    if (!(p->dt > 0.0)) return "dt must be > 0";
+    if (!(p->Re > 0.0) || !(p->Pr > 0.0)) return "Re and Pr must be > 0";
+    if (!p->incompressible) {
+        if (!(p->Z_st > 0.0 && p->Z_st < 1.0)) return "Z_st must lie in (0, 1)";
+        if (!(p->density_ratio > 1.0)) return "density_ratio must be > 1";
+        if (!(p->eps_reg > 0.0)) return "eps_reg must be > 0";
+        if (!(p->tol_reg > 0.0 && p->tol_reg < 0.5)) return "tol_reg must lie in (0, 0.5)";
+        if (!(p->Le_F > 0.0 && p->Le_O > 0.0)) return "Lewis numbers must be > 0";
+        if (!(p->gamma > 1.0)) return "gamma must be > 1";
+    }
+    if (!(p->poisson_rtol > 0.0 && p->poisson_rtol < 1.0)) return "poisson_rtol must lie in (0, 1)";
+    if (p->poisson_max_iter < 1) return "poisson_max_iter must be >= 1";
+    if (p->precision != SIM_FP64) return "this build implements precision = SIM_FP64 only";
+    if (p->closed_system) {
+        for (int d = 0; d < p->dim; ++d)
+            for (int q = 0; q < 2; ++q)
+                if (p->bc[d][q] == SIM_BC_INFLOW || p->bc[d][q] == SIM_BC_OUTFLOW)
+                    return "an enclosed system cannot have inflow or outflow sides";
+    }
+    return nullptr;
+}
+
+// Walk the workspace layout; with s != nullptr assign the pointers.
+size_t layout(const sim_params_t* p, sim_t* s, char* base) {
+    const Geom g = make_geom(p);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* ptr = base ? base + off : nullptr;
+        off += a256(bytes);
+        return ptr;
+    };
+    const size_t fpad = sizeof(double) * (size_t)g.npad;
+    const size_t fcmp = sizeof(double) * (size_t)g.ncell;
+    long long maxface = 0;
+    for (int d = 0; d < g.dim; ++d) {
+        long long m = g.ncell / g.n[d] * (g.n[d] + 1);
+        if (m > maxface) maxface = m;
+    }
+    long long maxslab = 0;
+    for (int d = 0; d < 3; ++d) {
+        const int a = (d == 0) ? 1 : 0, b = (d == 2) ? 1 : 2;
+        const long long m = (long long)g.p[a] * g.p[b];
+        if (m > maxslab) maxslab = m;
+    }
+    const int D = g.dim;
+    sim_t tmp;
+    sim_t* t = s ? s : &tmp;
+    auto F = [&](double** dst) { *dst = (double*)take(fpad); };
+    for (int d = 0; d < D; ++d) F(&t->v[d]);
+    for (int d = 0; d < D; ++d) F(&t->vs[d]);
+    F(&t->Z); F(&t->H); F(&t->Zs); F(&t->Hs); F(&t->T); F(&t->kap);
+    for (int r = 0; r < 3; ++r) F(&t->rho[r]);
+    for (int d = 0; d < D; ++d) F(&t->mom[d]);
+    for (int d = 0; d < D; ++d) F(&t->F[d]);
+    for (int k = 0; k < 2; ++k) {
+        for (int d = 0; d < D; ++d) F(&t->R[k][d]);
+        F(&t->R[k][3]);
+        F(&t->R[k][4]);
+    }
+    for (int d = 0; d < D; ++d) F(&t->vib[d]);
+    F(&t->Sm);
+    F(&t->U);
+    {
+        double* q = (double*)take(fcmp);
+        if (s) s->P = q;
+        q = (double*)take(fcmp);
+        if (s) s->b = q;
+        q = (double*)take(sizeof(double) * (size_t)(maxface > g.ncell ? maxface : g.ncell));
+        if (s) s->io = q;
+        q = (double*)take(sizeof(double) * kMaxPartials);
+        if (s) s->part = q;
+        q = (double*)take(sizeof(double) * kMaxPartials);
+        if (s) s->part2 = q;
+        q = (double*)take(sizeof(double) * SC_NSCAL);
+        if (s) s->sc = q;
+        q = (double*)take(sizeof(double) * kMaxProfile);
+        if (s) s->profile = q;
+        int* st = (int*)take(sizeof(int) * 8);
+        if (s) s->status = st;
+        uint8_t* c = (uint8_t*)take((size_t)g.npad);
+        if (s) s->chi = c;
+        for (int d = 0; d < 3; ++d)
+            for (int q2 = 0; q2 < 2; ++q2) {
+                uint8_t* k = (uint8_t*)take((size_t)maxslab);
+                if (s) s->kind[d][q2] = k;
+            }
+    }
+    const char* err = nullptr;
+    int periodic[3] = {g.periodic[0], g.periodic[1], g.periodic[2]};
+    const size_t pb = poisson_plan_bytes(g.dim, g.n, periodic, nullptr, nullptr, &err);
+    if (pb == 0) return 0;
+    off += a256(pb);
+    return off;
+}
+
+char* poisson_ws(const sim_params_t* p, char* base) {
+    // the Poisson plan sits at the end of the layout
+    const Geom g = make_geom(p);
+    const char* err = nullptr;
+    int periodic[3] = {g.periodic[0], g.periodic[1], g.periodic[2]};
+    const size_t pb = a256(poisson_plan_bytes(g.dim, g.n, periodic, nullptr, nullptr, &err));
+    return base + layout(p, nullptr, nullptr) - pb;
+}
+
+// --------------------------- launch sequences -------------------------------
+void ghost(sim_t* s, std::initializer_list<std::pair<double*, int>> fields, cudaStream_t st, int* L) {
+    GhostJob job;
+    std::memset(&job, 0, sizeof(job));
+    for (auto& f : fields) {
+        job.f[job.nf] = f.first;
+        job.what[job.nf] = f.second;
+        ++job.nf;
+    }
+    launch_ghost(s->g, s->bnd, s->ph, job, st, L);
+}
+
+void ghost_v(sim_t* s, double* const* v, cudaStream_t st, int* L) {
+    GhostJob job;
+    std::memset(&job, 0, sizeof(job));
+    for (int d = 0; d < s->g.dim; ++d) {
+        job.f[d] = v[d];
+        job.what[d] = GW_V0 + d;
+    }
+    job.nf = s->g.dim;
+    launch_ghost(s->g, s->bnd, s->ph, job, st, L);
+}
+
+cudaError_t enqueue_init(sim_t* s, cudaStream_t st) {
+    int L = 0;
+    const Geom& g = s->g;
+    double* rho0 = s->rho[s->rho_base];
+    ghost_v(s, s->v, st, &L);
+    ghost(s, {{s->Z, GW_Z}, {s->H, GW_H}}, st, &L);
+    Phys ph0 = s->ph;
+    ph0.closed = 0;                                      // p0^0 = 1
+    launch_state(g, ph0, s->Z, s->H, s->T, rho0, s->kap, s->sc, SC_P0_N, s->part, s->status, st, &L);
+    ghost(s, {{s->kap, GW_KAPPA}}, st, &L);
+    launch_sum(g, rho0, s->part, st, &L);
+    launch_store_sum(s->part, reduce_grid(g), g.dV, s->sc + SC_MASS, st, &L);
+    launch_momentum(g, rho0, s->v, s->mom, st, &L);
+    FluxArgs fa;
+    std::memset(&fa, 0, sizeof(fa));
+    for (int d = 0; d < g.dim; ++d) {
+        fa.mom[d] = s->mom[d];
+        fa.F[d] = s->F[d];
+    }
+    fa.sc = s->sc;
+    fa.p0_slot = SC_P0_N;
+    fa.part = s->part;
+    fa.correct = 0;
+    launch_flux_rhs(g, s->ph, s->bnd, fa, st, &L);
+    cudaError_t e = cudaMemsetAsync(s->P, 0, sizeof(double) * (size_t)g.ncell, st);
+    if (e != cudaSuccess) return e;
+    double ones[3] = {1.0, 1.0, 1.0};
+    e = cudaMemcpyAsync(s->sc + SC_P0_NM1, ones, sizeof(double) * 2, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(s->status, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(st);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Pressure solve of one stage; graph mode adds a conditional while node.
+cudaError_t enqueue_poisson(sim_t* s, cudaStream_t st, bool graph, int iter_slot, int* L, int* body_launch) {
+    PoissonPlan* pl = &s->pp;
+    pl->launches = 0;
+    cudaError_t e = poisson_enqueue_prologue(pl, s->b, s->P, st);
+    if (e != cudaSuccess) return e;
+    if (!graph) {
+        e = poisson_enqueue_ctrl_init(pl, st, 0ULL, 0);
+        if (e != cudaSuccess) return e;
+        int done = 0;
+        for (int guard = 0; guard <= pl->max_iter + 1; ++guard) {
+            e = cudaMemcpyAsync(&done, pl->ictl + PI_DONE, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return e;
+            if (done) break;
+            const int before = pl->launches;
+            e = poisson_enqueue_body(pl, s->P, st, 0ULL);
+            if (e != cudaSuccess) return e;
+            *body_launch = pl->launches - before;
+        }
+    } else {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t graph_h;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph_h, &deps, nullptr, &ndeps);
+        if (e != cudaSuccess) return e;
+        cudaGraphConditionalHandle h;
+        e = cudaGraphConditionalHandleCreate(&h, graph_h, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) return e;
+        e = poisson_enqueue_ctrl_init(pl, st, (unsigned long long)h, 1);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph_h, &deps, nullptr, &ndeps);
+        if (e != cudaSuccess) return e;
+        std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, graph_h, dv.data(), nullptr, dv.size(), &np);
+        if (e != cudaSuccess) return e;
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(s->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return e;
+        const int before = pl->launches;
+        e = poisson_enqueue_body(pl, s->P, s->side, (unsigned long long)h);
+        cudaGraph_t body_out = body;
+        cudaError_t e2 = cudaStreamEndCapture(s->side, &body_out);
+        if (e != cudaSuccess) return e;
+        if (e2 != cudaSuccess) return e2;
+        *body_launch = pl->launches - before;
+        e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e != cudaSuccess) return e;
+    }
+    e = poisson_enqueue_epilogue(pl, s->P, st);
+    if (e != cudaSuccess) return e;
+    // record iterations / residual and fold non-convergence into the status word;
+    // in graph mode the body is counted per executed iteration at query time
+    *L += graph ? pl->launches - *body_launch : pl->launches;
+    launch_copy_scalar(pl->scal + PS_ITERS, s->sc + iter_slot, 1, st, L);
+    launch_copy_scalar(pl->scal + PS_RELRES, s->sc + iter_slot + 1, 1, st, L);
+    launch_or_status(pl->ictl + PI_NOCONV, ST_NOCONV, s->status, st, L);
+    return cudaGetLastError();
+}
+
+struct Roles {
+    double *rho_n, *rho_prev, *rho_new;
+    double* Rn[5];
+    double* Rp[5];
+};
+
+Roles roles(sim_t* s, long long n) {
+    Roles r;
+    const int b = s->rho_base;
+    r.rho_n = s->rho[b];
+    r.rho_new = s->rho[(b + 1) % 3];
+    r.rho_prev = s->rho[(b + 2) % 3];
+    for (int k = 0; k < 5; ++k) {
+        r.Rn[k] = s->R[n & 1][k];
+        r.Rp[k] = s->R[(n + 1) & 1][k];
+    }
+    return r;
+}
+
+ResidArgs resid_common(sim_t* s) {
+    ResidArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.chi = s->chi;
+    for (int d = 0; d < s->g.dim; ++d) a.vib[d] = s->vib[d];
+    a.Z_ib = s->Z_ib;
+    a.H_ib = s->H_ib;
+    a.inv_Da = s->ibm_active ? 1.0 / s->Da : 0.0;
+    a.ibm = s->ibm_active;
+    a.sc = s->sc;
+    a.dt = s->prm.dt;
+    return a;
+}
+
+// Enqueue step number n (predictor + corrector).  graph: being captured on st.
+cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int* L, int* body) {
+    const Geom& g = s->g;
+    const int D = g.dim;
+    const double dt = s->prm.dt;
+    Roles r = roles(s, n);
+
+    // ---------------- predictor ----------------
+    ResidArgs a = resid_common(s);
+    for (int d = 0; d < D; ++d) {
+        a.v[d] = s->v[d];
+        a.vb[d] = s->v[d];
+        a.F[d] = s->F[d];
+        a.mo[d] = s->mom[d];
+    }
+    a.Z = s->Z;
+    a.H = s->H;
+    a.rho = r.rho_n;
+    a.kap = s->kap;
+    a.Zb = s->Z;
+    a.Hb = s->H;
+    a.rhob = r.rho_n;
+    for (int k = 0; k < 5; ++k) {
+        a.Rst[k] = r.Rn[k];
+        a.Rrd[k] = r.Rp[k];
+    }
+    a.Zo = s->Zs;
+    a.Ho = s->Hs;
+    a.mode = (n == 0) ? MODE_PRED_EULER : MODE_PRED_AB2;
+    a.p0a = SC_P0_N;
+    a.p0b = SC_P0_NM1;
+    a.p0c = SC_P0_NM2;
+    if (n == 0) {
+        a.wden = 0.0;
+    } else if (n == 1) {
+        a.w0 = 1.0; a.w1 = -1.0; a.w2 = 0.0; a.wden = dt;
+    } else {
+        a.w0 = 3.0; a.w1 = -4.0; a.w2 = 1.0; a.wden = 2.0 * dt;
+    }
+    launch_residual(g, s->ph, a, st, L);
+    ghost(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}}, st, L);
+    launch_state(g, s->ph, s->Zs, s->Hs, s->T, r.rho_new, s->kap, s->sc, SC_P0_STAR, s->part, s->status, st, L);
+    ghost(s, {{s->kap, GW_KAPPA}}, st, L);
+
+    FluxArgs fa;
+    std::memset(&fa, 0, sizeof(fa));
+    for (int d = 0; d < D; ++d) {
+        fa.mom[d] = s->mom[d];
+        fa.F[d] = s->F[d];
+    }
+    fa.rho_new = r.rho_new;
+    fa.rho_n = r.rho_n;
+    fa.rho_prev = r.rho_prev;
+    fa.Sm = s->ibm_active ? s->Sm : nullptr;
+    if (n == 0) {
+        fa.bdf_c0 = 1.0; fa.bdf_c1 = -1.0; fa.bdf_c2 = 0.0; fa.bdf_den = dt;
+    } else {
+        fa.bdf_c0 = 3.0; fa.bdf_c1 = -4.0; fa.bdf_c2 = 1.0; fa.bdf_den = 2.0 * dt;
+    }
+    fa.sc = s->sc;
+    fa.p0_slot = SC_P0_STAR;
+    fa.part = s->part;
+    fa.b = s->b;
+    fa.correct = 1;
+    launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
+    cudaError_t e = enqueue_poisson(s, st, graph, SC_ITERS_PRED, L, body);
+    if (e != cudaSuccess) return e;
+    ProjArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    for (int d = 0; d < D; ++d) {
+        pa.F[d] = s->F[d];
+        pa.mom[d] = s->mom[d];
+        pa.v[d] = s->vs[d];
+    }
+    pa.P = s->P;
+    pa.rho = r.rho_new;
+    pa.eA = s->eA;
+    pa.eB = s->eB;
+    pa.eC = s->eC;
+    launch_project(g, pa, st, L);
+    ghost_v(s, s->vs, st, L);
+
+    // ---------------- corrector ----------------
+    ResidArgs c = resid_common(s);
+    for (int d = 0; d < D; ++d) {
+        c.v[d] = s->vs[d];
+        c.vb[d] = s->v[d];
+        c.F[d] = s->F[d];
+        c.mo[d] = s->mom[d];
+    }
+    c.Z = s->Zs;
+    c.H = s->Hs;
+    c.rho = r.rho_new;      // rho* (overwritten by rho^{n+1} below, after this kernel)
+    c.kap = s->kap;         // kappa*
+    c.Zb = s->Z;
+    c.Hb = s->H;
+    c.rhob = r.rho_n;
+    for (int k = 0; k < 5; ++k) c.Rrd[k] = r.Rn[k];
+    c.Zo = s->Z;
+    c.Ho = s->H;
+    c.mode = MODE_CORR;
+    c.p0a = SC_P0_STAR;
+    c.p0b = SC_P0_N;
+    c.p0c = SC_P0_NM1;
+    if (n == 0) {
+        c.w0 = 1.0; c.w1 = -1.0; c.w2 = 0.0; c.wden = dt;
+    } else {
+        c.w0 = 3.0; c.w1 = -4.0; c.w2 = 1.0; c.wden = 2.0 * dt;
+    }
+    launch_residual(g, s->ph, c, st, L);
+    ghost(s, {{s->Z, GW_Z}, {s->H, GW_H}}, st, L);
+    launch_state(g, s->ph, s->Z, s->H, s->T, r.rho_new, s->kap, s->sc, SC_P0_NEW, s->part, s->status, st, L);
+    ghost(s, {{s->kap, GW_KAPPA}}, st, L);
+    fa.p0_slot = SC_P0_NEW;
+    launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
+    e = enqueue_poisson(s, st, graph, SC_ITERS_CORR, L, body);
+    if (e != cudaSuccess) return e;
+    for (int d = 0; d < D; ++d) pa.v[d] = s->v[d];
+    launch_project(g, pa, st, L);
+    ghost_v(s, s->v, st, L);
+    launch_rotate_p0(s->sc, st, L);
+    return cudaGetLastError();
+}
+
+void after_step(sim_t* s) {
+    s->rho_base = (s->rho_base + 1) % 3;
+    s->nstep += 1;
+    s->t += s->prm.dt;
+}
+
+sim_status capture_phase(sim_t* s, int phase) {
+    int L = 0, body = 0;
+    CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeRelaxed));
+    cudaError_t e = enqueue_step(s, s->nstep, s->cap, true, &L, &body);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s->cap, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(s, SIM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
+    if (e2 != cudaSuccess) return fail(s, SIM_ECUDA, "end capture: %s", cudaGetErrorString(e2));
+    e = cudaGraphInstantiate(&s->gexec[phase], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(s, SIM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    s->gvalid[phase] = true;
+    s->launches_fixed_graph[phase] = L;
+    s->body_launches = body;
+    return SIM_OK;
+}
+
+sim_status check_device_status(sim_t* s) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (st & ST_NAN) return fail(s, SIM_ENAN, "non-finite or non-positive temperature in the state");
+    if (st & ST_NOCONV) return fail(s, SIM_ENOCONV, "a pressure solve did not reach poisson_rtol in %d iterations",
+                                    s->prm.poisson_max_iter);
+    return SIM_OK;
+}
+
+}  // namespace
+
+// ============================== C ABI ========================================
+extern "C" {
+
+sim_status sim_workspace_size(const sim_params_t* prm, size_t* bytes) {
+    if (!bytes) return SIM_EINVAL;
+    if (validate(prm)) return SIM_EINVAL;
+    const size_t b = layout(prm, nullptr, nullptr);
+    if (b == 0) return SIM_EINVAL;
+    *bytes = b;
+    return SIM_OK;
+}
+
+sim_status sim_create(const sim_params_t* prm, void* d_workspace, size_t workspace_bytes, void* cuda_stream,
+                      sim_t** out) {
+    if (!out) return SIM_EINVAL;
+    *out = nullptr;
+    const char* bad = validate(prm);
+    if (bad) return SIM_EINVAL;
+    const size_t need = layout(prm, nullptr, nullptr);
+    if (need == 0) return SIM_EINVAL;
+    if (!d_workspace || workspace_bytes < need) return SIM_ENOMEM;
+    if (((uintptr_t)d_workspace & 255) != 0) return SIM_EINVAL;
+    sim_t* s = new sim_t();   // value-initialised: every plain member starts at zero
+    s->prm = *prm;
+    s->g = make_geom(prm);
+    s->ph = make_phys(prm);
+    s->stream = (cudaStream_t)cuda_stream;
+    {
+        // LOWMACH_NO_GRAPH=1 keeps every step on the host-driven launch path
+        const char* ng = std::getenv("LOWMACH_NO_GRAPH");
+        s->use_graph = !(ng && ng[0] == '1');
+    }
+    layout(prm, s, (char*)d_workspace);
+    for (int d = 0; d < 3; ++d)
+        for (int q = 0; q < 2; ++q) {
+            s->bnd.kind[d][q] = s->kind[d][q];
+            s->bnd.bc[d][q] = (d < prm->dim) ? prm->bc[d][q] : SIM_BC_PERIODIC;
+        }
+    // Eq 3.28 on the first three cell centres of a side (uniform spacing)
+    {
+        const double h = 1.0;
+        const double x0 = -0.5 * h, x1 = 0.5 * h, x2 = 1.5 * h, x3 = 2.5 * h;
+        s->eA = (x2 - x0) * (x3 - x0) / ((x2 - x1) * (x3 - x1));
+        s->eB = (x1 - x0) * (x3 - x0) / ((x1 - x2) * (x3 - x2));
+        s->eC = (x1 - x0) * (x2 - x0) / ((x1 - x3) * (x2 - x3));
+    }
+    const char* err = nullptr;
+    int periodic[3] = {s->g.periodic[0], s->g.periodic[1], s->g.periodic[2]};
+    char* pws = poisson_ws(prm, (char*)d_workspace);
+    const int* nn = s->g.n;
+    if (!poisson_plan_init(&s->pp, prm->dim, nn, s->g.h, periodic, prm->poisson_rtol, prm->poisson_max_iter, pws,
+                           (size_t)((char*)d_workspace + need - pws), &s->minv, &err)) {
+        delete s;
+        return SIM_EINVAL;
+    }
+    sim_status st = SIM_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete s;
+        return SIM_ECUDA;
+    }
+    if (!poisson_upload_coarse(&s->pp, s->minv, s->stream, &err)) {
+        sim_destroy(s);
+        return SIM_ECUDA;
+    }
+    // no body yet: boundary kinds from the sides alone
+    int bc[3][2];
+    for (int d = 0; d < 3; ++d)
+        for (int q = 0; q < 2; ++q) bc[d][q] = s->bnd.bc[d][q];
+    e = cudaMemsetAsync(s->sc, 0, sizeof(double) * SC_NSCAL, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->status, 0, sizeof(int) * 8, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->chi, 0, (size_t)s->g.npad, s->stream);
+    if (e == cudaSuccess) {
+        launch_bkinds(s->g, bc, nullptr, s->kind, s->part, s->sc, s->stream);
+        e = cudaStreamSynchronize(s->stream);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        sim_destroy(s);
+        return SIM_ECUDA;
+    }
+    s->need_init = true;
+    *out = s;
+    return st;
+}
+
+sim_status sim_set_ibm_geometry(sim_t* s, const sim_ibm_t* geo) {
+    if (!s) return SIM_EINVAL;
+    int bc[3][2];
+    for (int d = 0; d < 3; ++d)
+        for (int q = 0; q < 2; ++q) bc[d][q] = s->bnd.bc[d][q];
+    for (int k = 0; k < 6; ++k)
+        if (s->gvalid[k]) {
+            cudaGraphExecDestroy(s->gexec[k]);
+            s->gvalid[k] = false;
+        }
+    if (!geo || geo->kind == SIM_IBM_NONE) {
+        s->ibm_active = 0;
+        CK(cudaMemsetAsync(s->chi, 0, (size_t)s->g.npad, s->stream));
+        launch_bkinds(s->g, bc, nullptr, s->kind, s->part, s->sc, s->stream);
+        CK(cudaStreamSynchronize(s->stream));
+        CK(cudaGetLastError());
+        return SIM_OK;
+    }
+    if (geo->kind != SIM_IBM_SLOT && geo->kind != SIM_IBM_SPHERE)
+        return fail(s, SIM_EINVAL, "unknown body kind %d", geo->kind);
+    if (!(geo->Da_ib > 0.0)) return fail(s, SIM_EINVAL, "Da_ib must be > 0");
+    if (geo->n_profile < 0 || geo->n_profile > kMaxProfile || (geo->n_profile > 0 && !geo->profile) ||
+        geo->n_profile == 1)
+        return fail(s, SIM_EINVAL, "profile must have 0 or 2..%d samples", kMaxProfile);
+    if (s->prm.dt >= s->prm.Re * geo->Da_ib)
+        return fail(s, SIM_EUNSTABLE, "dt = %g >= Re Da_ib = %g (explicit penalisation limit)", s->prm.dt,
+                    s->prm.Re * geo->Da_ib);
+    IbmDev b;
+    std::memset(&b, 0, sizeof(b));
+    b.kind = geo->kind;
+    for (int d = 0; d < 3; ++d) {
+        b.c[d] = geo->center[d];
+        b.half[d] = geo->half[d];
+    }
+    b.radius = geo->radius;
+    b.s = std::sqrt(geo->Da_ib);
+    b.rho_b = geo->rho_b;
+    b.U_b = geo->U_b;
+    b.n_profile = geo->n_profile;
+    if (geo->n_profile > 0) {
+        CK(cudaMemcpyAsync(s->profile, geo->profile, sizeof(double) * geo->n_profile, cudaMemcpyHostToDevice,
+                           s->stream));
+        b.profile = s->profile;
+    }
+    launch_ibm(s->g, b, s->chi, s->vib, s->U, s->Sm, s->stream);
+    launch_bkinds(s->g, bc, s->chi, s->kind, s->part, s->sc, s->stream);
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    s->ibm_active = 1;
+    s->Z_ib = geo->Z_ib;
+    s->H_ib = geo->H_ib;
+    s->Da = geo->Da_ib;
+    return SIM_OK;
+}
+
+sim_status sim_fields(sim_t* s, int id, void* buf, int dir, int on_device) {
+    if (!s || !buf) return SIM_EINVAL;
+    const Geom& g = s->g;
+    const int D = g.dim;
+    cudaStream_t st = s->stream;
+    const cudaMemcpyKind h2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind d2h = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t cells = sizeof(double) * (size_t)g.ncell;
+    if (dir == SIM_SET) {
+        double* dst = nullptr;
+        int bit = 0;
+        if (id >= SIM_FIELD_U && id <= SIM_FIELD_W) {
+            if (id - SIM_FIELD_U >= D) return fail(s, SIM_EINVAL, "no W component in 2D");
+            dst = s->v[id - SIM_FIELD_U];
+            bit = 1 << id;
+        } else if (id == SIM_FIELD_Z) {
+            dst = s->Z;
+            bit = 1 << 3;
+        } else if (id == SIM_FIELD_H) {
+            dst = s->H;
+            bit = 1 << 4;
+        } else {
+            return fail(s, SIM_EINVAL, "field %d cannot be set (only U, V, W, Z, H)", id);
+        }
+        CK(cudaMemcpyAsync(s->io, buf, cells, h2d, st));
+        launch_unpack(g, s->io, dst, st);
+        CK(cudaGetLastError());
+        if (!on_device) CK(cudaStreamSynchronize(st));
+        s->fields_set |= bit;
+        s->need_init = true;
+        return SIM_OK;
+    }
+    if (dir != SIM_GET) return fail(s, SIM_EINVAL, "dir must be SIM_GET or SIM_SET");
+    size_t bytes = cells;
+    if (id >= SIM_FIELD_U && id <= SIM_FIELD_W) {
+        if (id - SIM_FIELD_U >= D) return fail(s, SIM_EINVAL, "no W component in 2D");
+        launch_pack(g, s->v[id - SIM_FIELD_U], s->io, -1, st);
+    } else if (id == SIM_FIELD_Z) {
+        launch_pack(g, s->Z, s->io, -1, st);
+    } else if (id == SIM_FIELD_H) {
+        launch_pack(g, s->H, s->io, -1, st);
+    } else if (id == SIM_FIELD_T) {
+        launch_pack(g, s->T, s->io, -1, st);
+    } else if (id == SIM_FIELD_RHO) {
+        launch_pack(g, s->rho[s->rho_base], s->io, -1, st);
+    } else if (id == SIM_FIELD_KAPPA) {
+        launch_pack(g, s->kap, s->io, -1, st);
+    } else if (id == SIM_FIELD_P) {
+        CK(cudaMemcpyAsync(s->io, s->P, cells, cudaMemcpyDeviceToDevice, st));
+    } else if (id >= SIM_FIELD_FX && id <= SIM_FIELD_FZ) {
+        const int d = id - SIM_FIELD_FX;
+        if (d >= D) return fail(s, SIM_EINVAL, "no z faces in 2D");
+        launch_pack(g, s->F[d], s->io, d, st);
+        bytes = sizeof(double) * (size_t)(g.ncell / g.n[d] * (g.n[d] + 1));
+    } else if (id == SIM_FIELD_CHI) {
+        launch_u8_to_double(g, s->chi, s->io, st);
+    } else if (id == SIM_FIELD_SM) {
+        if (s->ibm_active)
+            launch_pack(g, s->Sm, s->io, -1, st);
+        else
+            CK(cudaMemsetAsync(s->io, 0, cells, st));
+    } else {
+        return fail(s, SIM_EINVAL, "unknown field %d", id);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(buf, s->io, bytes, d2h, st));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return SIM_OK;
+}
+
+sim_status sim_step(sim_t* s, int nsteps) {
+    if (!s || nsteps < 0) return SIM_EINVAL;
+    const int need = (s->g.dim == 3) ? 0x1f : 0x1b;
+    if ((s->fields_set & need) != need) return fail(s, SIM_ESTATE, "set U, V, (W,) Z, H before stepping");
+    if (s->need_init) {
+        CK(enqueue_init(s, s->stream));
+        s->need_init = false;
+        s->nstep = 0;
+        s->rho_base = 0;
+        s->t = 0.0;
+        for (int k = 0; k < 6; ++k)
+            if (s->gvalid[k]) {
+                cudaGraphExecDestroy(s->gexec[k]);
+                s->gvalid[k] = false;
+            }
+    }
+    for (int it = 0; it < nsteps; ++it) {
+        const long long n = s->nstep;
+        if (n < 2 || !s->use_graph) {
+            int L = 0, body = 0;
+            CK(enqueue_step(s, n, s->stream, false, &L, &body));
+            s->launches_last = L;
+        } else {
+            // the launch sequence depends on n only through the rotating roles
+            const int phase = (int)(n % 6);
+            if (!s->gvalid[phase]) {
+                sim_status st = capture_phase(s, phase);
+                if (st != SIM_OK) return st;
+            }
+            CK(cudaGraphLaunch(s->gexec[phase], s->stream));
+            s->launches_last = -(s->launches_fixed_graph[phase] + 1);  // resolved by sim_query
+        }
+        after_step(s);
+    }
+    return SIM_OK;
+}
+
+sim_status sim_sync(sim_t* s) {
+    if (!s) return SIM_EINVAL;
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    return check_device_status(s);
+}
+
+sim_status sim_query(sim_t* s, int what, double* out) {
+    if (!s || !out) return SIM_EINVAL;
+    CK(cudaStreamSynchronize(s->stream));
+    auto dev = [&](int slot, double* v) -> sim_status {
+        CK(cudaMemcpy(v, s->sc + slot, sizeof(double), cudaMemcpyDeviceToHost));
+        return SIM_OK;
+    };
+    switch (what) {
+        case SIM_Q_TIME: *out = s->t; return SIM_OK;
+        case SIM_Q_DT: *out = s->prm.dt; return SIM_OK;
+        case SIM_Q_P0: return dev(SC_P0_N, out);
+        case SIM_Q_STEPS: *out = (double)s->nstep; return SIM_OK;
+        case SIM_Q_ITERS_PRED: return dev(SC_ITERS_PRED, out);
+        case SIM_Q_RESID_PRED: return dev(SC_RELRES_PRED, out);
+        case SIM_Q_ITERS_CORR: return dev(SC_ITERS_CORR, out);
+        case SIM_Q_RESID_CORR: return dev(SC_RELRES_CORR, out);
+        case SIM_Q_MASS: return dev(SC_MASS, out);
+        case SIM_Q_NCELLS: *out = (double)s->g.ncell; return SIM_OK;
+        case SIM_Q_MG_LEVELS: *out = (double)s->pp.nlev; return SIM_OK;
+        case SIM_Q_KERNEL_LAUNCHES: {
+            if (s->launches_last >= 0) {
+                *out = (double)s->launches_last;
+                return SIM_OK;
+            }
+            double ip = 0, ic = 0;
+            sim_status st = dev(SC_ITERS_PRED, &ip);
+            if (st != SIM_OK) return st;
+            st = dev(SC_ITERS_CORR, &ic);
+            if (st != SIM_OK) return st;
+            *out = (double)(-s->launches_last - 1) + (ip + ic) * s->body_launches;
+            return SIM_OK;
+        }
+        default: return fail(s, SIM_EINVAL, "unknown query %d", what);
+    }
+}
+
+sim_status sim_time_kernel(sim_t* s, int kernel, int reps) {
+    if (!s || reps < 0) return SIM_EINVAL;
+    if (s->need_init || s->nstep < 1) return fail(s, SIM_ESTATE, "time kernels after the first step");
+    const Geom& g = s->g;
+    const int D = g.dim;
+    const long long n = s->nstep;
+    Roles r = roles(s, n);
+    int L = 0;
+    for (int it = 0; it < reps; ++it) {
+        switch (kernel) {
+            case SIM_K_RESIDUAL: {
+                ResidArgs a = resid_common(s);
+                for (int d = 0; d < D; ++d) {
+                    a.v[d] = s->v[d];
+                    a.vb[d] = s->v[d];
+                    a.F[d] = s->F[d];
+                    a.mo[d] = s->mom[d];
+                }
+                a.Z = s->Z;
+                a.H = s->H;
+                a.rho = r.rho_n;
+                a.kap = s->kap;
+                a.Zb = s->Z;
+                a.Hb = s->H;
+                a.rhob = r.rho_n;
+                for (int k = 0; k < 5; ++k) {
+                    a.Rst[k] = r.Rn[k];
+                    a.Rrd[k] = r.Rp[k];
+                }
+                a.Zo = s->Zs;
+                a.Ho = s->Hs;
+                a.mode = MODE_PRED_AB2;
+                a.p0a = SC_P0_N;
+                a.p0b = SC_P0_NM1;
+                a.p0c = SC_P0_NM2;
+                a.w0 = 3.0; a.w1 = -4.0; a.w2 = 1.0; a.wden = 2.0 * s->prm.dt;
+                launch_residual(g, s->ph, a, s->stream, &L);
+                break;
+            }
+            case SIM_K_SMOOTH: CK(poisson_launch_single(&s->pp, 0, s->stream)); break;
+            case SIM_K_MATVEC: CK(poisson_launch_single(&s->pp, 1, s->stream)); break;
+            case SIM_K_RESTRICT: CK(poisson_launch_single(&s->pp, 2, s->stream)); break;
+            case SIM_K_STATE: {
+                // T, kappa of Z*, H* into residual scratch (the next predictor rewrites it)
+                Phys ph = s->ph;
+                ph.closed = 0;
+                launch_state(g, ph, s->Zs, s->Hs, r.Rn[3], r.rho_new, r.Rn[4], s->sc, SC_P0_STAR, s->part,
+                             s->status, s->stream, &L);
+                break;
+            }
+            case SIM_K_PROJECT: {
+                ProjArgs pa;
+                std::memset(&pa, 0, sizeof(pa));
+                for (int d = 0; d < D; ++d) {
+                    pa.F[d] = r.Rn[d];   // residual scratch stands in for the interface fluxes
+                    pa.mom[d] = s->mom[d];
+                    pa.v[d] = s->vs[d];
+                }
+                pa.P = s->pp.z;          // Krylov scratch as the pressure argument
+                pa.rho = r.rho_n;
+                pa.eA = s->eA;
+                pa.eB = s->eB;
+                pa.eC = s->eC;
+                launch_project(g, pa, s->stream, &L);
+                break;
+            }
+            default: return fail(s, SIM_EINVAL, "unknown kernel id %d", kernel);
+        }
+    }
+    CK(cudaGetLastError());
+    return SIM_OK;
+}
+
+// ----------------------------- restart state ---------------------------------
+namespace {
+struct StateHeader {
+    char magic[8];
+    int version, dim, n[3], rho_base;
+    long long nstep;
+    double t, dt;
+    int ibm_active, pad_;
+};
+
+// Segments of the restart blob: (device pointer, bytes), in a fixed order.
+std::vector<std::pair<void*, size_t>> state_segments(sim_t* s) {
+    const Geom& g = s->g;
+    const size_t fpad = sizeof(double) * (size_t)g.npad;
+    std::vector<std::pair<void*, size_t>> seg;
+    for (int d = 0; d < g.dim; ++d) seg.push_back({s->v[d], fpad});
+    seg.push_back({s->Z, fpad});
+    seg.push_back({s->H, fpad});
+    seg.push_back({s->T, fpad});
+    seg.push_back({s->kap, fpad});
+    for (int r = 0; r < 3; ++r) seg.push_back({s->rho[r], fpad});
+    for (int d = 0; d < g.dim; ++d) seg.push_back({s->F[d], fpad});
+    for (int k = 0; k < 2; ++k) {
+        for (int d = 0; d < g.dim; ++d) seg.push_back({s->R[k][d], fpad});
+        seg.push_back({s->R[k][3], fpad});
+        seg.push_back({s->R[k][4], fpad});
+    }
+    seg.push_back({s->P, sizeof(double) * (size_t)g.ncell});
+    seg.push_back({s->sc, sizeof(double) * SC_NSCAL});
+    seg.push_back({s->status, sizeof(int) * 8});
+    return seg;
+}
+
+size_t state_bytes(sim_t* s) {
+    size_t b = a256(sizeof(StateHeader));
+    for (auto& q : state_segments(s)) b += a256(q.second);
+    return b;
+}
+}  // namespace
+
+sim_status sim_state_size(const sim_t* cs, size_t* bytes) {
+    if (!cs || !bytes) return SIM_EINVAL;
+    *bytes = state_bytes(const_cast<sim_t*>(cs));
+    return SIM_OK;
+}
+
+sim_status sim_state_save(sim_t* s, void* buf, int on_device) {
+    if (!s || !buf) return SIM_EINVAL;
+    if (s->need_init) return fail(s, SIM_ESTATE, "no state yet: step once after setting the fields");
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "LMSTATE", 8);
+    h.version = 1;
+    h.dim = s->g.dim;
+    for (int d = 0; d < 3; ++d) h.n[d] = s->g.n[d];
+    h.rho_base = s->rho_base;
+    h.nstep = s->nstep;
+    h.t = s->t;
+    h.dt = s->prm.dt;
+    h.ibm_active = s->ibm_active;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    char* out = (char*)buf;
+    CK(cudaMemcpyAsync(out, &h, sizeof(h), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s->stream));
+    size_t off = a256(sizeof(StateHeader));
+    for (auto& q : state_segments(s)) {
+        CK(cudaMemcpyAsync(out + off, q.first, q.second, k, s->stream));
+        off += a256(q.second);
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+sim_status sim_state_load(sim_t* s, const void* buf, int on_device) {
+    if (!s || !buf) return SIM_EINVAL;
+    StateHeader h;
+    if (on_device)
+        CK(cudaMemcpy(&h, buf, sizeof(h), cudaMemcpyDeviceToHost));
+    else
+        std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, "LMSTATE", 8) != 0 || h.version != 1 || h.dim != s->g.dim || h.dt != s->prm.dt ||
+        h.n[0] != s->g.n[0] || h.n[1] != s->g.n[1] || h.n[2] != s->g.n[2] || h.ibm_active != s->ibm_active)
+        return fail(s, SIM_EINVAL, "restart blob does not match this simulation");
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const char* in = (const char*)buf;
+    size_t off = a256(sizeof(StateHeader));
+    for (auto& q : state_segments(s)) {
+        CK(cudaMemcpyAsync(q.first, in + off, q.second, k, s->stream));
+        off += a256(q.second);
+    }
+    if (!on_device) CK(cudaStreamSynchronize(s->stream));
+    s->rho_base = h.rho_base;
+    s->nstep = h.nstep;
+    s->t = h.t;
+    s->need_init = false;
+    s->fields_set = 0x1f;
+    return SIM_OK;
+}
+
+const char* sim_last_error(const sim_t* s) { return s ? s->err : "null handle"; }
+
+void sim_destroy(sim_t* s) {
+    if (!s) return;
+    for (int k = 0; k < 6; ++k)
+        if (s->gvalid[k]) cudaGraphExecDestroy(s->gexec[k]);
+    if (s->cap) cudaStreamDestroy(s->cap);
+    if (s->side) cudaStreamDestroy(s->side);
+    delete s;
+}
+
+// ----------------------- stand-alone pressure solve --------------------------
+sim_status sim_poisson_workspace_size(int dim, const int n[3], const int periodic[3], size_t* bytes) {
+    if (!n || !periodic || !bytes || (dim != 2 && dim != 3)) return SIM_EINVAL;
+    for (int d = 0; d < dim; ++d)
+        if (n[d] < 2) return SIM_EINVAL;
+    int nn[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
+    const char* err = nullptr;
+    const size_t b = poisson_plan_bytes(dim, nn, periodic, nullptr, nullptr, &err);
+    if (b == 0) return SIM_EINVAL;
+    *bytes = b;
+    return SIM_OK;
+}
+
+sim_status sim_poisson_solve(int dim, const int n[3], const double h[3], const int periodic[3], const double* d_b,
+                             double* d_P, double rtol, int max_iter, void* d_workspace, size_t workspace_bytes,
+                             void* cuda_stream, int* iters, double* rel_resid) {
+    if (!n || !h || !periodic || !d_b || !d_P || !d_workspace || (dim != 2 && dim != 3)) return SIM_EINVAL;
+    if (!(rtol > 0.0 && rtol < 1.0) || max_iter < 1) return SIM_EINVAL;
+    int nn[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
+    double hh[3] = {h[0], h[1], dim == 3 ? h[2] : 1.0};
+    int per[3] = {periodic[0] != 0, periodic[1] != 0, dim == 3 ? (periodic[2] != 0) : 0};
+    for (int d = 0; d < dim; ++d)
+        if (nn[d] < 2 || !(hh[d] > 0.0)) return SIM_EINVAL;
+    const char* err = nullptr;
+    const size_t need = poisson_plan_bytes(dim, nn, per, nullptr, nullptr, &err);
+    if (need == 0) return SIM_EINVAL;
+    if (workspace_bytes < need) return SIM_ENOMEM;
+    PoissonPlan pl;
+    std::vector<double> minv;
+    if (!poisson_plan_init(&pl, dim, nn, hh, per, rtol, max_iter, d_workspace, workspace_bytes, &minv, &err))
+        return SIM_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!poisson_upload_coarse(&pl, minv, st, &err)) return SIM_ECUDA;
+    cudaError_t e = poisson_solve_host_loop(&pl, d_b, d_P, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return SIM_ECUDA;
+    double sc[PS_NSCAL];
+    int ic[PI_NINT];
+    if (cudaMemcpy(sc, pl.scal, sizeof(sc), cudaMemcpyDeviceToHost) != cudaSuccess) return SIM_ECUDA;
+    if (cudaMemcpy(ic, pl.ictl, sizeof(ic), cudaMemcpyDeviceToHost) != cudaSuccess) return SIM_ECUDA;
+    if (iters) *iters = (int)sc[PS_ITERS];
+    if (rel_resid) *rel_resid = sc[PS_RELRES];
+    return ic[PI_NOCONV] ? SIM_ENOCONV : SIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// Kernels of one predictor / corrector stage (everything but the Poisson
+// solve) and their host launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace lm {
+
+// Device scalar slots of a simulation.
+enum : int {
+    SC_P0_N = 0, SC_P0_NM1 = 1, SC_P0_NM2 = 2, SC_P0_STAR = 3, SC_P0_NEW = 4,
+    SC_MASS = 5, SC_OUT_AREA = 6,
+    SC_ITERS_PRED = 8, SC_RELRES_PRED = 9, SC_ITERS_CORR = 10, SC_RELRES_CORR = 11,
+    SC_NSCAL = 32
+};
+// Device status bits (int word).
+enum : int { ST_NOCONV = 1, ST_NAN = 2 };
+
+enum Mode : int { MODE_PRED_EULER = 0, MODE_PRED_AB2 = 1, MODE_CORR = 2 };
+
+// Boundary description on the device: per direction and side, the kind of
+// every position of the full padded slab (uint8), plus ghost-fill job lists.
+struct Bnd {
+    const uint8_t* kind[3][2];
+    int bc[3][2];
+};
+
+// What a ghost-filled field is: scalar Z, H, kappa, or velocity component c.
+enum GhostWhat : int { GW_Z = 0, GW_H = 1, GW_KAPPA = 2, GW_V0 = 3 };
+constexpr int kMaxGhostFields = 6;
+struct GhostJob {
+    double* f[kMaxGhostFields];
+    int what[kMaxGhostFields];
+    int nf;
+};
+
+struct ResidArgs {
+    const double* v[3];
+    const double* Z;
+    const double* H;
+    const double* rho;
+    const double* kap;
+    const double* F[3];
+    const double* Zb;
+    const double* Hb;
+    const double* rhob;
+    const double* vb[3];
+    double* Rst[5];          // stored residuals (v0, v1, v2, Z, H)
+    const double* Rrd[5];    // previous (AB2) or level-n (corrector) residuals
+    double* Zo;
+    double* Ho;
+    double* mo[3];
+    const uint8_t* chi;
+    const double* vib[3];
+    double Z_ib, H_ib, inv_Da;
+    int ibm;
+    const double* sc;
+    int p0a, p0b, p0c;
+    double w0, w1, w2, wden;  // dp0/dt = (w0 sc[a] + w1 sc[b] + w2 sc[c]) / wden (wden = 0: zero)
+    int mode;
+    double dt;
+};
+
+struct FluxArgs {
+    const double* mom[3];    // provisional momentum (padded layout, interior valid)
+    double* F[3];            // out: interface fluxes (padded face layout)
+    const double* rho_new;
+    const double* rho_n;
+    const double* rho_prev;
+    const double* Sm;        // may be null
+    double bdf_c0, bdf_c1, bdf_c2, bdf_den;  // d_t rho = (c0 new + c1 n + c2 prev) / den
+    const double* sc;
+    int p0_slot;             // p0 of the stage (inflow density p0 / T_in)
+    double* part;            // partial sums of the global mass balance
+    double* b;               // right-hand side (compact)
+    int correct;             // 1: shift outflow fluxes, build b; 0: fluxes only (t = 0)
+};
+
+struct ProjArgs {
+    double* F[3];
+    const double* P;         // compact
+    const double* mom[3];
+    const double* rho;
+    double* v[3];
+    double eA, eB, eC;       // quadratic extrapolation coefficients (Eq 3.28)
+};
+
+void launch_ghost(const Geom& g, const Bnd& bnd, const Phys& ph, const GhostJob& job, cudaStream_t s,
+                  int* launches);
+void launch_state(const Geom& g, const Phys& ph, const double* Z, const double* H, double* T,
+                  double* rho, double* kap, double* sc, int p0_slot, double* part, int* status,
+                  cudaStream_t s, int* launches);
+void launch_residual(const Geom& g, const Phys& ph, const ResidArgs& a, cudaStream_t s, int* launches);
+void launch_flux_rhs(const Geom& g, const Phys& ph, const Bnd& bnd, const FluxArgs& a, cudaStream_t s,
+                     int* launches);
+void launch_project(const Geom& g, const ProjArgs& a, cudaStream_t s, int* launches);
+void launch_momentum(const Geom& g, const double* rho, double* const v[3], double* mom[3], cudaStream_t s,
+                     int* launches);
+void launch_sum(const Geom& g, const double* x, double* part, cudaStream_t s, int* launches);
+void launch_store_sum(const double* part, int np, double scale, double* dst, cudaStream_t s, int* launches);
+void launch_rotate_p0(double* sc, cudaStream_t s, int* launches);
+void launch_copy_scalar(const double* src, double* dst, int n, cudaStream_t s, int* launches);
+void launch_or_status(const int* src_flag, int bit, int* status, cudaStream_t s, int* launches);
+
+// Immersed body and boundary kinds (set-up time).
+struct IbmDev {
+    int kind;
+    double c[3], half[3], radius, s, rho_b, U_b;
+    const double* profile;  // device copy (may be null)
+    int n_profile;
+};
+void launch_ibm(const Geom& g, const IbmDev& b, uint8_t* chi, double* vib[3], double* U, double* Sm,
+                cudaStream_t s);
+void launch_bkinds(const Geom& g, const int bc[3][2], const uint8_t* chi, uint8_t* kind[3][2],
+                   double* part, double* sc, cudaStream_t s);
+
+// Pack / unpack between the padded layout and compact interior / face arrays.
+void launch_pack(const Geom& g, const double* padded, double* compact, int face_dir, cudaStream_t s);
+void launch_unpack(const Geom& g, const double* compact, double* padded, cudaStream_t s);
+void launch_u8_to_double(const Geom& g, const uint8_t* padded, double* compact, cudaStream_t s);
+
+int reduce_grid(const Geom& g);
+
+}  // namespace lm
