@@ -1,0 +1,432 @@
+"""Benchmark of one time step of the low-Mach flame-sheet solver on a GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                    [--config slot|sphere|blobs] [--precision fp64|mixed|both]
+
+A "step" is one predictor + corrector time step (both pressure solves to a
+relative residual of 1e-10) of the 2D 256x512 planar slot-burner flame: seeded
+synthetic inputs from ``workloads`` (the paper uses no public dataset).  The
+metric is cell-steps/s: interior cells x steps / device time.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
+the simulation's stream; before each timed step a 256 MiB buffer is written to
+flush the 129 MB L2 (the flush is outside the events).  Under torchrun every
+rank runs an independent replica (the method is not sharded across GPUs);
+the reported time is the maximum over ranks and ``value`` counts the cells of
+all ranks ("scaling": "weak").
+
+Extra keys of the JSON line: ``roofline`` for the dominant kernel (average
+launch duration from CUDA events around back-to-back launches of that kernel
+with the step's own arguments, algorithmic bytes or flops per launch from the
+kernel's data model), ``cpu_baseline`` (the FP64 oracle on a bounded sample of
+the same workload, on the host cores), ``e2e`` (the same metric through the C
+ABI with the restart state loaded from and saved to pinned host memory every
+step), ``clocks`` (nvidia-smi samples taken during the timed region) and
+``gpu_launches`` (kernels of this library enqueued in the timed region).
+"""
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "cell-steps/s incl. Poisson to 1e-10 (mixed vs FP64, same GPU); HBM GB/s % peak"
+UNIT = "cell-steps/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="slot", choices=["slot", "sphere", "blobs"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    """(prm, geo, fields, config description)."""
+    if name == "slot":
+        prm, geo, f = W.slot_burner(256, 512)
+        cfg = {"workload": "2D 256x512 planar slot-burner diffusion flame (immersed 0.1x0.3 burner, "
+                           "parabolic fuel mass flux peak Re=200, coflow 0.2, density ratio 7, Z_st=0.055, "
+                           "outflow top)", "grid": [256, 512]}
+    elif name == "sphere":
+        prm, geo, f = W.sphere_burner(192)
+        cfg = {"workload": "3D 192^3 spherical porous burner (IBM sphere r=0.1L, radial fuel mass flux "
+                           "Re=150, quiescent air, density ratio 7, 1% perturbations, outflow all sides)",
+               "grid": [192, 192, 192]}
+    else:
+        prm, geo, f = W.periodic_blobs(64)
+        cfg = {"workload": "2D 64x64 doubly periodic enclosed box, 8 Gaussian Z blobs, Re=100",
+               "grid": [64, 64]}
+    prm["poisson_rtol"] = 1e-10
+    cfg["poisson_rtol"] = 1e-10
+    return prm, geo, f, cfg
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (independent replicas)
+# ---------------------------------------------------------------------------
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda_ok() else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device.index])
+        else:
+            pg.barrier()
+
+
+def reduce_max(pg, x, device=None):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device if device is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(pg, x, device=None):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device if device is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# data model of the kernels (algorithmic bytes / flops per launch)
+# ---------------------------------------------------------------------------
+def kernel_models(prm, mixed):
+    """Algorithmic traffic (bytes) and arithmetic (flops) per launch of the
+    kernels timed by sim_time_kernel, from the fields each one must read and
+    write once (ghost layers ignored).  w = bytes of a smoother / stencil word."""
+    dim = prm["dim"]
+    N = float(np.prod(prm["n"][:dim]))
+    w = 4.0 if mixed else 8.0
+    nb = 2 * dim                        # neighbours of the compact operator
+    m = {}
+    # one red-black colour: read all of u and the colour's f, write the colour's u
+    m["smooth"] = dict(id=1, bytes=N * w + 0.5 * N * w + 0.5 * N * w, flops=0.5 * N * (2 * nb + 2))
+    # operator application + dot product: read p, write q (FP64 Krylov vectors)
+    m["matvec"] = dict(id=2, bytes=2 * N * 8.0, flops=N * (2 * nb + 3))
+    # fine residual + restriction: read u, f, write r; read r, write coarse f
+    m["restrict"] = dict(id=3, bytes=3 * N * w + N * w + N / 2 ** dim * w, flops=N * (2 * nb + 3) + N * 2.0)
+    # predictor stencil pass: reads v, Z, H, rho, kappa, F (dim faces), chi-data, R^(n-1);
+    # writes R^n, Z*, H*, rho v~ (the data model of the stage kernel)
+    reads = dim + 2 + 2 + dim + (dim + 2) + (dim + 1) + dim   # v Z H rho kap F Rprev vib+chi rho_b v_b
+    writes = (dim + 2) + 2 + dim
+    m["residual"] = dict(id=0, bytes=(reads + writes) * N * 8.0, flops=N * (60.0 * dim * dim))
+    m["state"] = dict(id=4, bytes=5 * N * 8.0, flops=N * 40.0)
+    m["project"] = dict(id=5, bytes=(1 + 2 * dim + 1 + dim) * N * 8.0, flops=N * 8.0 * dim)
+    return m
+
+
+# ---------------------------------------------------------------------------
+# the GB300 arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, precision, world, rank, local, pg):
+    import torch
+    from paper_2603_01727_gb300 import lowmach as LM
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    prm, geo, f, cfg = workload(args.config)
+    prm["precision"] = LM.SIM_MIXED if precision == "mixed" else LM.SIM_FP64
+    stream = torch.cuda.current_stream(device)
+    sim = LM.Simulation(prm, geo, device=device, stream=stream)
+    sim.set_fields(f)
+    ncell = int(sim.query(LM.SIM_Q_NCELLS))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    sim.step(max(args.warmup, 3))
+    sim.sync()
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    launches = 0
+    iters = []
+    clocks = Clocks(device.index)
+    barrier(pg, device)
+    torch.cuda.synchronize(device)
+    clocks.start()
+    for k in range(K):
+        flush.zero_()
+        starts[k].record(stream)
+        sim.step(1)
+        ends[k].record(stream)
+        launches += int(sim.query(LM.SIM_Q_KERNEL_LAUNCHES))    # synchronises (outside the events)
+        iters.append(sim.query(LM.SIM_Q_ITERS_PRED) + sim.query(LM.SIM_Q_ITERS_CORR))
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    sim.sync()
+    barrier(pg, device)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms_max = reduce_max(pg, ms, device)
+    cells_all = reduce_sum(pg, float(ncell) * K, device)
+    value = cells_all / (ms_max * 1e-3)
+    resid = max(sim.query(LM.SIM_Q_RESID_PRED), sim.query(LM.SIM_Q_RESID_CORR))
+
+    # ---- per-kernel timing (the step's own arguments, back-to-back launches)
+    models = kernel_models(prm, precision == "mixed")
+    reps = 200
+    ktimes = {}
+    for name, mdl in models.items():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sim.time_kernel(mdl["id"], 5)
+        flush.zero_()
+        e0.record(stream)
+        sim.time_kernel(mdl["id"], reps)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        ktimes[name] = e0.elapsed_time(e1) * 1e-3 / reps
+    sim.sync()
+
+    out = dict(value=value, ms_per_step=ms_max / K, launches=launches, iters_per_step=float(np.mean(iters)),
+               relres=resid, clocks=clk, ktimes=ktimes, models=models, ncell=ncell, cfg=cfg, sim=sim,
+               prm=prm, geo=geo, f=f)
+    return out
+
+
+def e2e_gpu(args, precision, res, device):
+    """Same metric through the C ABI with host buffers: every step loads the
+    restart state from pinned host memory, steps once and saves the state back
+    to pinned host memory (wall clock around the three calls)."""
+    import torch
+    sim = res["sim"]
+    nbytes = sim.state_size()
+    hin = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    hout = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    sim.state_save(hin)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    K = max(10, min(args.steps, 100))
+    total = 0.0
+    for k in range(K):
+        flush.zero_()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        sim.state_load(hin)
+        sim.step(1)
+        sim.state_save(hout)          # synchronises
+        total += time.perf_counter() - t0
+        hin, hout = hout, hin
+    sim.sync()
+    return {"value": res["ncell"] * K / total, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "steps": K}
+
+
+def roofline(res, peaks, precision):
+    """Roofline entry of the kernel with the largest share of the step."""
+    share = {}
+    # launches of each kernel class per step (model of the launch sequence)
+    it = res["iters_per_step"]
+    nlev = res["sim"].query(10)
+    per_step = {"smooth": 3 * it, "matvec": it, "restrict": it, "residual": 2, "state": 2, "project": 2}
+    for k, t in res["ktimes"].items():
+        share[k] = t * per_step[k] / (res["ms_per_step"] * 1e-3)
+    top = max(share, key=share.get)
+    t = res["ktimes"][top]
+    m = res["models"][top]
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    gbs = m["bytes"] / t / 1e9
+    fp64_tflops = FP64_PEAK_TFLOPS
+    tfl = m["flops"] / t / 1e12
+    if precision == "fp64" and tfl / fp64_tflops > gbs / hbm:
+        rl = {"bound": "alu", "achieved": tfl, "peak": fp64_tflops, "unit": "TFLOP/s (fp64)",
+              "frac": tfl / fp64_tflops}
+    else:
+        rl = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
+    rl.update(kernel=top, launch_us=t * 1e6, share_of_step=share[top], traffic=None,
+              peak_source="MEASURED_PEAKS.json hbm_gbs (burst copy)" if rl["bound"] == "hbm"
+              else "nominal GB300 FP64 rate (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)",
+              shares={k: round(v, 4) for k, v in share.items()}, nlev=nlev)
+    return rl
+
+
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12    # 1.26 TFLOP/s
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the --impl reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(config, nsteps, budget_s):
+    """Cell-steps/s of the FP64 oracle on this host: ``nsteps`` steps (or as
+    many as fit in ``budget_s`` seconds) of the workload from its initial state."""
+    from oracle import step as S
+    prm, geo, f, cfg = workload(config)
+    pb = S.Problem(prm, geo)
+    st = S.initial_state(pb, f["v"], f["Z"], f["H"])
+    ncell = int(np.prod(prm["n"][:prm["dim"]]))
+    t0 = time.perf_counter()
+    done = 0
+    while done < nsteps:
+        st = S.advance(pb, st)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return ncell * done / dt, done, dt
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    prm, geo, f, cfg = workload(args.config)
+    # warm-up: W oracle steps (bounded)
+    oracle_rate(args.config, max(1, min(args.warmup, 3)), 30.0)
+    rate, done, secs = oracle_rate(args.config, max(1, args.steps), 60.0)
+    sample = f"{done} oracle steps of the workload from its initial state ({secs:.1f} s)"
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": done, "warmup": args.warmup, "ms_per_step": secs * 1e3 / done, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": cfg,
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_init(args)
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+    import torch
+    device = torch.device("cuda", local)
+    precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    from paper_2603_01727_gb300 import lowmach as LM
+    results = {}
+    for p in precs:
+        try:
+            results[p] = run_gpu(args, p, world, rank, local, pg)
+        except LM.SimError as e:
+            if p == "mixed" and e.status == LM.SIM_EINVAL and args.precision == "both":
+                continue      # mixed precision not built into this library
+            raise
+    head = "mixed" if "mixed" in results else "fp64"
+    res = results[head]
+    peaks = load_peaks()
+    rl = roofline(res, peaks, head)
+    e2e = None if args.no_e2e else e2e_gpu(args, head, res, device)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, done, secs = oracle_rate(args.config, 200, 20.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} FP64 oracle steps of the same workload from its initial state "
+                         f"({secs:.1f} s, numpy/scipy single-threaded)"}
+    if rank != 0:
+        return
+    cfg = dict(res["cfg"])
+    cfg.update(precision=head, l2="flushed before every timed step (256 MiB write outside the events)",
+               parallelism=f"replicas x{world}")
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64",
+            "data": "synthetic (seeded workloads module)", "config": cfg, "roofline": rl,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": res["clocks"], "gpu_launches": res["launches"],
+            "poisson_iters_per_step": res["iters_per_step"], "poisson_relres": res["relres"]}
+    for p, r in results.items():
+        line[p] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "iters_per_step": r["iters_per_step"],
+                   "kernel_us": {k: round(v * 1e6, 3) for k, v in r["ktimes"].items()}}
+    if "mixed" in results and "fp64" in results:
+        line["mixed_over_fp64"] = results["mixed"]["value"] / results["fp64"]["value"]
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

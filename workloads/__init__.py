@@ -213,8 +213,8 @@ def sphere_burner(n=192, cfl=0.4, Re=150.0, seed=SEED, rms=0.01):
     s = rms / np.sqrt(np.mean(u * u + v * v + w * w))
     r = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)
     dist = np.maximum(r - 0.1, 0.0)
-    w = max(0.04, 10.0 / n)
-    Z = Z_fuel * np.exp(-dist * dist / (2.0 * w * w))
+    width = max(0.04, 10.0 / n)
+    Z = Z_fuel * np.exp(-dist * dist / (2.0 * width * width))
     H = np.full(x.shape, H_inf)
     prm["dt"] = stable_dt((n, n, n), (1.0, 1.0, 1.0), Re, prm["Pr"], prm["density_ratio"],
                           prm["sigma"], 1.0, cfl, Da_ib=Da, dim=3)
