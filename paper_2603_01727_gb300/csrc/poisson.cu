@@ -309,10 +309,12 @@ __global__ void k_ctrl_beta(double* scal, const int* ictl, const double* prz, co
 }
 
 __global__ void k_update_p(const double* __restrict__ z, double* __restrict__ p, const double* scal,
-                           long long N) {
+                           const int* ictl, long long N) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
-    p[t] = (z[t] - scal[PS_MEANZ]) + scal[PS_BETA] * p[t];
+    // first iteration: p = z (p holds no previous direction, whatever its bits)
+    const double zc = z[t] - scal[PS_MEANZ];
+    p[t] = (ictl[PI_IT] == 0) ? zc : zc + scal[PS_BETA] * p[t];
 }
 
 template <int DIM>
@@ -639,7 +641,7 @@ static void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditiona
     vcycle<DIM>(pl, s);
     k_dot_rz<<<rb, NT, 0, s>>>(pl->r, pl->z, pl->N, pl->part0, pl->part1);
     k_ctrl_beta<<<1, NT, 0, s>>>(pl->scal, pl->ictl, pl->part0, pl->part1, rb, pl->N);
-    k_update_p<<<nb, NT, 0, s>>>(pl->z, pl->p, pl->scal, pl->N);
+    k_update_p<<<nb, NT, 0, s>>>(pl->z, pl->p, pl->scal, pl->ictl, pl->N);
     k_matvec_dot<DIM><<<rb, NT, 0, s>>>(pl->lev[0], pl->p, pl->q, pl->part0);
     k_update_xr<<<rb, NT, 0, s>>>(x, pl->r, pl->p, pl->q, pl->N, pl->scal, pl->part0, rb, pl->part1);
     k_ctrl_conv<<<1, NT, 0, s>>>(pl->scal, pl->ictl, pl->part1, rb, pl->rtol, pl->max_iter, h, use_graph);
