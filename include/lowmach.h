@@ -218,6 +218,35 @@ sim_status sim_poisson_solve(int dim, const int n[3], const double h[3], const i
                              void *d_workspace, size_t workspace_bytes, void *cuda_stream,
                              int *iters, double *rel_resid);
 
+/* ---------------------------------------------------------------------------
+ * Pressure solve without any allocation (no counterpart in the paper; an
+ * interface convenience).  Same operator, arguments, results and status codes
+ * as sim_poisson_solve, minus the workspace: the scratch lives in one static
+ * device array of SIM_NOALLOC_SCRATCH_BYTES inside this library, held on every
+ * GPU that loads the library until the process exits.
+ *
+ * For callers that cannot call cudaMalloc or lend a workspace: a plug-in whose
+ * host application owns all device memory, a process under a fixed device
+ * memory budget, or a latency-critical loop that cannot take the implicit
+ * device synchronisation of cudaMalloc / cudaFree.  The call itself allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * - The first call on a device looks up the array's device address with that
+ *   device current (one-time set-up); make that first call before any stream
+ *   capture on the device.
+ * - Returns SIM_ENOMEM, before touching the GPU, when the grid needs more than
+ *   SIM_NOALLOC_SCRATCH_BYTES of scratch (sim_poisson_workspace_size gives the
+ *   need; about 40 bytes per cell, e.g. 2D grids up to roughly 400 000 cells).
+ * - Every call shares the one array: the used part is cleared at the start of
+ *   each call, and calls that overlap on the GPU (different streams, or other
+ *   host threads) race on it -- serialise them.
+ * - Synchronises cuda_stream before returning (like sim_poisson_solve).
+ * ------------------------------------------------------------------------- */
+#define SIM_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+sim_status sim_poisson_solve_noalloc(int dim, const int n[3], const double h[3], const int periodic[3],
+                                     const double *d_b, double *d_P, double rtol, int max_iter,
+                                     void *cuda_stream, int *iters, double *rel_resid);
+
 #ifdef __cplusplus
 }
 #endif

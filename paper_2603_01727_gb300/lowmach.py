@@ -83,6 +83,7 @@ def load():
         "sim_state_load": ([VP, VP, I], I),
         "sim_poisson_workspace_size": ([I, P(I), P(I), P(SZ)], I),
         "sim_poisson_solve": ([I, P(I), P(D), P(I), VP, VP, D, I, VP, SZ, VP, P(I), P(D)], I),
+        "sim_poisson_solve_noalloc": ([I, P(I), P(D), P(I), VP, VP, D, I, VP, P(I), P(D)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -97,7 +98,7 @@ def exported_symbols():
             "sim_sync", "sim_query", "sim_last_error", "sim_destroy", "sim_time_kernel", "sim_state_size",
             "sim_state_save",
             "sim_state_load", "sim_poisson_workspace_size",
-            "sim_poisson_solve"]
+            "sim_poisson_solve", "sim_poisson_solve_noalloc"]
 
 
 class SimError(RuntimeError):
@@ -285,5 +286,25 @@ def poisson_solve(b, P, h, periodic, rtol=1e-12, max_iter=200, stream=None):
     status = lib.sim_poisson_solve(dim, n, hh, per, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(P.data_ptr()),
                                    float(rtol), int(max_iter), ctypes.c_void_p(ptr), ctypes.c_size_t(sz.value),
                                    ctypes.c_void_p(st.cuda_stream), ctypes.byref(it), ctypes.byref(rr))
+    _check(lib, status)
+    return it.value, rr.value
+
+
+def poisson_solve_noalloc(b, P, h, periodic, rtol=1e-12, max_iter=200, stream=None):
+    """Same as poisson_solve, through sim_poisson_solve_noalloc: the library
+    uses its own static device scratch, so nothing is allocated for the call
+    (the caller still owns b and P).  Returns (iterations, relative residual)."""
+    import torch
+    lib = load()
+    dim = b.dim()
+    n = (ctypes.c_int * 3)(*([int(s) for s in reversed(b.shape)] + [1] * (3 - dim)))
+    per = (ctypes.c_int * 3)(*([int(bool(x)) for x in periodic] + [0] * (3 - dim)))
+    hh = (ctypes.c_double * 3)(*([float(x) for x in h] + [1.0] * (3 - dim)))
+    st = stream if stream is not None else torch.cuda.current_stream(b.device)
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    status = lib.sim_poisson_solve_noalloc(dim, n, hh, per, ctypes.c_void_p(b.data_ptr()),
+                                           ctypes.c_void_p(P.data_ptr()), float(rtol), int(max_iter),
+                                           ctypes.c_void_p(st.cuda_stream), ctypes.byref(it), ctypes.byref(rr))
     _check(lib, status)
     return it.value, rr.value
