@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-kernel-timing", action="store_true",
+                    help="skip the per-kernel timing (keeps an ncu launch list to the steps alone)")
     return ap.parse_args()
 
 
@@ -254,7 +256,7 @@ def run_gpu(args, precision, world, rank, local, pg):
     models = kernel_models(prm, precision == "mixed")
     reps = 200
     ktimes = {}
-    for name, mdl in models.items():
+    for name, mdl in ([] if args.no_kernel_timing else models.items()):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         sim.time_kernel(mdl["id"], 5)
@@ -399,7 +401,7 @@ def main():
     head = "mixed" if "mixed" in results else "fp64"
     res = results[head]
     peaks = load_peaks()
-    rl = roofline(res, peaks, head)
+    rl = roofline(res, peaks, head) if res["ktimes"] else None
     e2e = None if args.no_e2e else e2e_gpu(args, head, res, device)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
