@@ -185,19 +185,23 @@ class Clocks:
 # ---------------------------------------------------------------------------
 def kernel_models(prm, mixed):
     """Algorithmic traffic (bytes) and arithmetic (flops) per launch of the
-    kernels timed by sim_time_kernel, from the fields each one must read and
-    write once (ghost layers ignored).  w = bytes of a smoother / stencil word."""
+    kernels timed by sim_time_kernel, from the arrays each one must read and
+    write once (ghost layers and shared-memory halos ignored).  w = bytes of a
+    multigrid word (4 in the mixed path, 8 in FP64); Krylov vectors are FP64."""
     dim = prm["dim"]
     N = float(np.prod(prm["n"][:dim]))
     w = 4.0 if mixed else 8.0
     nb = 2 * dim                        # neighbours of the compact operator
     m = {}
-    # one red-black colour: read all of u and the colour's f, write the colour's u
-    m["smooth"] = dict(id=1, bytes=N * w + 0.5 * N * w + 0.5 * N * w, flops=0.5 * N * (2 * nb + 2))
-    # operator application + dot product: read p, write q (FP64 Krylov vectors)
-    m["matvec"] = dict(id=2, bytes=2 * N * 8.0, flops=N * (2 * nb + 3))
-    # fine residual + restriction: read u, f, write r; read r, write coarse f
-    m["restrict"] = dict(id=3, bytes=3 * N * w + N * w + N / 2 ** dim * w, flops=N * (2 * nb + 3) + N * 2.0)
+    # fine level down: read r, write u_pre and the coarse right-hand side;
+    # red (1 flop), black (2nb+1), residual (2nb+2), restriction (2 x 4^d / 2^d)
+    m["mg_down"] = dict(id=1, bytes=8 * N + w * N + w * N / 2 ** dim,
+                        flops=N * (0.5 + 0.5 * (2 * nb + 1) + (2 * nb + 2) + 2.0 * 2 ** dim))
+    # CG: p = z - mean + beta p_old, q = A p, p.q: read z, p_old; write p, q
+    m["cg_matvec"] = dict(id=2, bytes=w * N + 3 * 8 * N, flops=N * (2 + 2 * nb + 2 + 2))
+    # fine level up: read u_pre, r, coarse u; write z; r.z and sum z
+    m["mg_up"] = dict(id=3, bytes=w * N + 8 * N + w * N / 2 ** dim + w * N,
+                      flops=N * (2 * 2 ** dim + (2 * nb + 1) + 4))
     # predictor stencil pass: reads v, Z, H, rho, kappa, F (dim faces), chi-data, R^(n-1);
     # writes R^n, Z*, H*, rho v~ (the data model of the stage kernel)
     reads = dim + 2 + 2 + dim + (dim + 2) + (dim + 1) + dim   # v Z H rho kap F Rprev vib+chi rho_b v_b
@@ -205,6 +209,7 @@ def kernel_models(prm, mixed):
     m["residual"] = dict(id=0, bytes=(reads + writes) * N * 8.0, flops=N * (60.0 * dim * dim))
     m["state"] = dict(id=4, bytes=5 * N * 8.0, flops=N * 40.0)
     m["project"] = dict(id=5, bytes=(1 + 2 * dim + 1 + dim) * N * 8.0, flops=N * 8.0 * dim)
+    m["mg_tail"] = dict(id=6, bytes=0.0, flops=0.0)
     return m
 
 
@@ -307,17 +312,19 @@ def roofline(res, peaks, precision):
     # launches of each kernel class per step (model of the launch sequence)
     it = res["iters_per_step"]
     nlev = res["sim"].query(10)
-    per_step = {"smooth": 3 * it, "matvec": it, "restrict": it, "residual": 2, "state": 2, "project": 2}
+    per_step = {"mg_down": it, "cg_matvec": it, "mg_up": it, "mg_tail": it, "residual": 2, "state": 2,
+                "project": 2}
     for k, t in res["ktimes"].items():
         share[k] = t * per_step[k] / (res["ms_per_step"] * 1e-3)
-    top = max(share, key=share.get)
+    top = max((k for k in share if res["models"][k]["bytes"] > 0), key=share.get)
     t = res["ktimes"][top]
     m = res["models"][top]
     hbm = peaks.get("hbm_gbs", 6800.0)
     gbs = m["bytes"] / t / 1e9
     fp64_tflops = FP64_PEAK_TFLOPS
     tfl = m["flops"] / t / 1e12
-    if precision == "fp64" and tfl / fp64_tflops > gbs / hbm:
+    fp64_kernel = (precision == "fp64") or top in ("cg_matvec", "residual", "state", "project")
+    if fp64_kernel and tfl / fp64_tflops > gbs / hbm:
         rl = {"bound": "alu", "achieved": tfl, "peak": fp64_tflops, "unit": "TFLOP/s (fp64)",
               "frac": tfl / fp64_tflops}
     else:

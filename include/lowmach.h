@@ -84,7 +84,9 @@ typedef struct {
     int closed_system;       /* 1: p0 from the mass constraint (Eq 2.40); 0: p0 = 1 (Eq 2.41) */
     int incompressible;      /* 1: T = rho = kappa = p0 = 1 (constant-density runs)     */
     double dt;               /* fixed time step (> 0)                                   */
-    int precision;           /* SIM_FP64 (only value accepted by this version)          */
+    int precision;           /* SIM_FP64: every kernel in FP64.  SIM_MIXED: multigrid
+                                preconditioner in FP32 inside the FP64 CG (the CG
+                                residual and the stopping test stay FP64)              */
     double poisson_rtol;     /* stop when ||r||_2 / ||f||_2 <= rtol (0 < rtol < 1)      */
     int poisson_max_iter;    /* PCG iteration cap (>= 1)                                */
 } sim_params_t;
@@ -184,12 +186,13 @@ sim_status sim_state_load(sim_t *sim, const void *buf, int on_device);
  * written (stage temporaries, Krylov and multigrid vectors), never the state.
  * kernel: SIM_K_* below.  Returns SIM_ESTATE before the first step. */
 enum {
-    SIM_K_RESIDUAL = 0,   /* predictor stencil pass (residuals + AB2 update)      */
-    SIM_K_SMOOTH = 1,     /* one red-black Gauss-Seidel colour on the fine level  */
-    SIM_K_MATVEC = 2,     /* CG operator application + dot product, fine level    */
-    SIM_K_RESTRICT = 3,   /* fine-level residual + restriction to level 1         */
-    SIM_K_STATE = 4,      /* flame-sheet state relation                           */
-    SIM_K_PROJECT = 5     /* interface fluxes + cell velocities (projection)      */
+    SIM_K_RESIDUAL = 0,   /* predictor stencil pass (residuals + AB2 update)             */
+    SIM_K_MG_DOWN = 1,    /* fine level: red, black, residual, restriction (one kernel)  */
+    SIM_K_CG_MATVEC = 2,  /* CG direction update + operator application + dot product   */
+    SIM_K_MG_UP = 3,      /* fine level: prolongation-add, black, red (one kernel)        */
+    SIM_K_STATE = 4,      /* flame-sheet state relation                                  */
+    SIM_K_PROJECT = 5,    /* interface fluxes + cell velocities (projection)             */
+    SIM_K_MG_TAIL = 6     /* coarse multigrid levels in one thread block                 */
 };
 sim_status sim_time_kernel(sim_t *sim, int kernel, int reps);
 

@@ -16,14 +16,29 @@ constexpr int kMaxLevels = 16;
 constexpr long long kMaxCoarse = 1024;   // cells of the directly-solved coarsest level
 constexpr long long kCoarsenAbove = 64;  // keep coarsening while a level has more cells
 
+// Geometry and operator coefficients of one multigrid level, in the
+// multigrid's arithmetic type T.  A = -L: (A u)_c = diag_c u_c - sum w_d u_nb.
+// diag / invd are indexed by the neighbour-count class c_0 + 3 c_1 + 9 c_2,
+// c_d in {0, 1, 2} = neighbours that exist along d (Neumann sides drop one).
+template <class T>
+struct LvT {
+    int n[3];
+    int per[3];
+    int N;
+    T w[3];
+    T diag[27];
+    T invd[27];
+};
+
+// Host view of a level: shape plus its device arrays.
 struct MgLevel {
     int n[3];
     int periodic[3];
-    double h[3], ih2[3];
     long long N;
-    double* u;   // correction (level >= 1)
-    double* f;   // right-hand side (level >= 1)
-    double* r;   // residual scratch
+    double h[3], ih2[3];
+    void* upre;   // pre-smoothed correction   (T, levels 1 .. top-1; level 0: plan u0pre)
+    void* upost;  // post-smoothed correction  (T, levels 1 .. top; level top: tail output)
+    void* f;      // right-hand side            (T, levels 1 .. top)
 };
 
 // Device scalars of one solve (indices into PoissonPlan::scal).
@@ -36,58 +51,74 @@ enum : int {
     PS_MEANB = 5,
     PS_ITERS = 6,     // iterations done (as a double, for reporting)
     PS_RELRES = 7,    // sqrt(rr/ff) at exit
+    PS_ALPHA = 8,
+    PS_MEANX = 9,
     PS_NSCAL = 16
 };
 enum : int { PI_IT = 0, PI_DONE = 1, PI_NOCONV = 2, PI_ZERO = 3, PI_NINT = 8 };
+constexpr int kNumCounters = 8;          // last-block counters (one per reducing kernel kind)
 
 struct PoissonPlan {
     int dim;
     int nlev;
+    int top;              // first level of the single-block tail (levels top .. nlev-1)
+    int mg_fp32;          // 1: multigrid in FP32, else FP64
     MgLevel lev[kMaxLevels];
     long long N;          // fine cells
-    double* r;            // Krylov vectors on the fine level
-    double* z;
-    double* p;
+    double* r;            // FP64 Krylov vectors on the fine level
+    double* p[2];         // search direction, double-buffered by iteration parity
     double* q;
-    double* part0;        // partial sums
+    void* z;              // preconditioned residual (T)
+    void* u0pre;          // pre-smoothed fine-level correction (T)
+    double* part0;        // partial sums (npart entries each)
     double* part1;
     double* part2;
+    int npart;
     double* scal;         // PS_* scalars
     int* ictl;            // PI_* integer control words
-    double* Minv;         // dense inverse of the coarsest operator (+ J/N)
+    unsigned int* cnt;    // last-block counters
+    void* levtab;         // LvT<T>[nlev] on the device (tail)
+    double* Minv;         // dense pseudo-inverse of the coarsest operator
+    float* Minv_f;        // the same in FP32
     long long Nc;
+    size_t tail_smem;     // dynamic shared memory of the tail kernel
+    int tail_off_u[kMaxLevels], tail_off_f[kMaxLevels], tail_off_r;   // tail smem offsets (elements)
     double rtol;
     int max_iter;
     int launches;         // kernels enqueued by the last enqueue (host-side count)
+    size_t levtab_bytes;
+    unsigned char levtab_host[kMaxLevels * sizeof(LvT<double>)];   // host copy of levtab
 };
 
-// Level shapes and workspace bytes for a grid (no allocation).
-size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int* nlev_out,
+// Workspace bytes for a grid (no allocation).
+size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg_fp32, int* nlev_out,
                           long long* Nc_out, const char** err);
 
 // Carve a plan out of ws (256-byte aligned, >= poisson_plan_bytes) and compute
-// the coarsest-level inverse on the host (returned in minv_host).  h is the
-// fine spacing.
-bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[3],
-                       const int periodic[3], double rtol, int max_iter, void* ws,
-                       size_t ws_bytes, std::vector<double>* minv_host, const char** err);
+// the coarsest-level inverse and the level tables on the host.
+bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[3], const int periodic[3],
+                       int mg_fp32, double rtol, int max_iter, void* ws, size_t ws_bytes,
+                       std::vector<double>* minv_host, const char** err);
 
-// Copy the coarsest inverse into the plan's device buffer (synchronises s).
+// Copy the host-prepared tables into the plan's device buffers (synchronises s).
 bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& minv_host, cudaStream_t s,
                            const char** err);
 
 // Enqueue the pieces of a solve of L x = b - mean(b) (b, x: device arrays of N
-// doubles; x holds the warm start).  The PCG loop body sets the conditional of
-// a while node when graph_handle != 0 (the body is then being captured into
-// that node's body graph); with graph_handle == 0 the loop is host-driven.
-cudaError_t poisson_enqueue_prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s);
-cudaError_t poisson_enqueue_ctrl_init(PoissonPlan* pl, cudaStream_t s, unsigned long long graph_handle,
-                                      int use_graph);
-cudaError_t poisson_enqueue_body(PoissonPlan* pl, double* x, cudaStream_t s,
-                                 unsigned long long graph_handle);
-cudaError_t poisson_enqueue_epilogue(PoissonPlan* pl, double* x, cudaStream_t s);
-// Single kernels of the fine level for timing: 0 = one smoother colour,
-// 1 = operator application + dot, 2 = residual + restriction to level 1.
+// doubles; x holds the warm start).  The convergence test of the prologue and
+// of each iteration sets the conditional of a while node when graph_handle != 0
+// (the body is then being captured into that node's body graph); with
+// graph_handle == 0 the loop is host-driven.
+cudaError_t poisson_enqueue_prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s,
+                                     unsigned long long graph_handle);
+cudaError_t poisson_enqueue_body(PoissonPlan* pl, double* x, cudaStream_t s, unsigned long long graph_handle);
+// Zero-mean x; optionally report iterations / relative residual into
+// rep[0], rep[1] and OR status_bit into *status on non-convergence.
+cudaError_t poisson_enqueue_epilogue(PoissonPlan* pl, double* x, cudaStream_t s, double* rep, int* status,
+                                     int status_bit);
+// Single kernels for timing (scratch only): 0 = fine-level down sweep,
+// 1 = CG direction update + operator application, 2 = fine-level up sweep,
+// 3 = coarse-level tail.
 cudaError_t poisson_launch_single(PoissonPlan* pl, int which, cudaStream_t s);
 // Host-driven complete solve (prologue, body until done, epilogue).
 cudaError_t poisson_solve_host_loop(PoissonPlan* pl, const double* b, double* x, cudaStream_t s);

@@ -182,7 +182,7 @@ const char* validate(const sim_params_t* p) {
     }
     if (!(p->poisson_rtol > 0.0 && p->poisson_rtol < 1.0)) return "poisson_rtol must lie in (0, 1)";
     if (p->poisson_max_iter < 1) return "poisson_max_iter must be >= 1";
-    if (p->precision != SIM_FP64) return "this build implements precision = SIM_FP64 only";
+    if (p->precision != SIM_FP64 && p->precision != SIM_MIXED) return "precision must be SIM_FP64 or SIM_MIXED";
     if (p->closed_system) {
         for (int d = 0; d < p->dim; ++d)
             for (int q = 0; q < 2; ++q)
@@ -259,7 +259,7 @@ size_t layout(const sim_params_t* p, sim_t* s, char* base) {
     }
     const char* err = nullptr;
     int periodic[3] = {g.periodic[0], g.periodic[1], g.periodic[2]};
-    const size_t pb = poisson_plan_bytes(g.dim, g.n, periodic, nullptr, nullptr, &err);
+    const size_t pb = poisson_plan_bytes(g.dim, g.n, periodic, p->precision == SIM_MIXED, nullptr, nullptr, &err);
     if (pb == 0) return 0;
     off += a256(pb);
     return off;
@@ -270,7 +270,8 @@ char* poisson_ws(const sim_params_t* p, char* base) {
     const Geom g = make_geom(p);
     const char* err = nullptr;
     int periodic[3] = {g.periodic[0], g.periodic[1], g.periodic[2]};
-    const size_t pb = a256(poisson_plan_bytes(g.dim, g.n, periodic, nullptr, nullptr, &err));
+    const size_t pb = a256(poisson_plan_bytes(g.dim, g.n, periodic, p->precision == SIM_MIXED, nullptr, nullptr,
+                                              &err));
     return base + layout(p, nullptr, nullptr) - pb;
 }
 
@@ -332,14 +333,14 @@ cudaError_t enqueue_init(sim_t* s, cudaStream_t st) {
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// Pressure solve of one stage; graph mode adds a conditional while node.
+// Pressure solve of one stage; graph mode adds a conditional while node whose
+// condition the prologue and every iteration set on the device.
 cudaError_t enqueue_poisson(sim_t* s, cudaStream_t st, bool graph, int iter_slot, int* L, int* body_launch) {
     PoissonPlan* pl = &s->pp;
     pl->launches = 0;
-    cudaError_t e = poisson_enqueue_prologue(pl, s->b, s->P, st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     if (!graph) {
-        e = poisson_enqueue_ctrl_init(pl, st, 0ULL, 0);
+        e = poisson_enqueue_prologue(pl, s->b, s->P, st, 0ULL);
         if (e != cudaSuccess) return e;
         int done = 0;
         for (int guard = 0; guard <= pl->max_iter + 1; ++guard) {
@@ -362,7 +363,7 @@ cudaError_t enqueue_poisson(sim_t* s, cudaStream_t st, bool graph, int iter_slot
         cudaGraphConditionalHandle h;
         e = cudaGraphConditionalHandleCreate(&h, graph_h, 1, cudaGraphCondAssignDefault);
         if (e != cudaSuccess) return e;
-        e = poisson_enqueue_ctrl_init(pl, st, (unsigned long long)h, 1);
+        e = poisson_enqueue_prologue(pl, s->b, s->P, st, (unsigned long long)h);
         if (e != cudaSuccess) return e;
         e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph_h, &deps, nullptr, &ndeps);
         if (e != cudaSuccess) return e;
@@ -388,14 +389,12 @@ cudaError_t enqueue_poisson(sim_t* s, cudaStream_t st, bool graph, int iter_slot
         e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
         if (e != cudaSuccess) return e;
     }
-    e = poisson_enqueue_epilogue(pl, s->P, st);
+    // zero mean; iterations / residual into the step's scalar slots and
+    // non-convergence into the status word
+    e = poisson_enqueue_epilogue(pl, s->P, st, s->sc + iter_slot, s->status, ST_NOCONV);
     if (e != cudaSuccess) return e;
-    // record iterations / residual and fold non-convergence into the status word;
     // in graph mode the body is counted per executed iteration at query time
     *L += graph ? pl->launches - *body_launch : pl->launches;
-    launch_copy_scalar(pl->scal + PS_ITERS, s->sc + iter_slot, 1, st, L);
-    launch_copy_scalar(pl->scal + PS_RELRES, s->sc + iter_slot + 1, 1, st, L);
-    launch_or_status(pl->ictl + PI_NOCONV, ST_NOCONV, s->status, st, L);
     return cudaGetLastError();
 }
 
@@ -644,7 +643,8 @@ sim_status sim_create(const sim_params_t* prm, void* d_workspace, size_t workspa
     int periodic[3] = {s->g.periodic[0], s->g.periodic[1], s->g.periodic[2]};
     char* pws = poisson_ws(prm, (char*)d_workspace);
     const int* nn = s->g.n;
-    if (!poisson_plan_init(&s->pp, prm->dim, nn, s->g.h, periodic, prm->poisson_rtol, prm->poisson_max_iter, pws,
+    if (!poisson_plan_init(&s->pp, prm->dim, nn, s->g.h, periodic, prm->precision == SIM_MIXED, prm->poisson_rtol,
+                           prm->poisson_max_iter, pws,
                            (size_t)((char*)d_workspace + need - pws), &s->minv, &err)) {
         delete s;
         return SIM_EINVAL;
@@ -925,9 +925,10 @@ sim_status sim_time_kernel(sim_t* s, int kernel, int reps) {
                 launch_residual(g, s->ph, a, s->stream, &L);
                 break;
             }
-            case SIM_K_SMOOTH: CK(poisson_launch_single(&s->pp, 0, s->stream)); break;
-            case SIM_K_MATVEC: CK(poisson_launch_single(&s->pp, 1, s->stream)); break;
-            case SIM_K_RESTRICT: CK(poisson_launch_single(&s->pp, 2, s->stream)); break;
+            case SIM_K_MG_DOWN: CK(poisson_launch_single(&s->pp, 0, s->stream)); break;
+            case SIM_K_CG_MATVEC: CK(poisson_launch_single(&s->pp, 1, s->stream)); break;
+            case SIM_K_MG_UP: CK(poisson_launch_single(&s->pp, 2, s->stream)); break;
+            case SIM_K_MG_TAIL: CK(poisson_launch_single(&s->pp, 3, s->stream)); break;
             case SIM_K_STATE: {
                 // T, kappa of Z*, H* into residual scratch (the next predictor rewrites it)
                 Phys ph = s->ph;
@@ -944,7 +945,7 @@ sim_status sim_time_kernel(sim_t* s, int kernel, int reps) {
                     pa.mom[d] = s->mom[d];
                     pa.v[d] = s->vs[d];
                 }
-                pa.P = s->pp.z;          // Krylov scratch as the pressure argument
+                pa.P = s->pp.q;          // Krylov scratch as the pressure argument
                 pa.rho = r.rho_n;
                 pa.eA = s->eA;
                 pa.eB = s->eB;
@@ -1075,7 +1076,7 @@ sim_status sim_poisson_workspace_size(int dim, const int n[3], const int periodi
         if (n[d] < 2) return SIM_EINVAL;
     int nn[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
     const char* err = nullptr;
-    const size_t b = poisson_plan_bytes(dim, nn, periodic, nullptr, nullptr, &err);
+    const size_t b = poisson_plan_bytes(dim, nn, periodic, 0, nullptr, nullptr, &err);
     if (b == 0) return SIM_EINVAL;
     *bytes = b;
     return SIM_OK;
@@ -1092,12 +1093,12 @@ sim_status sim_poisson_solve(int dim, const int n[3], const double h[3], const i
     for (int d = 0; d < dim; ++d)
         if (nn[d] < 2 || !(hh[d] > 0.0)) return SIM_EINVAL;
     const char* err = nullptr;
-    const size_t need = poisson_plan_bytes(dim, nn, per, nullptr, nullptr, &err);
+    const size_t need = poisson_plan_bytes(dim, nn, per, 0, nullptr, nullptr, &err);
     if (need == 0) return SIM_EINVAL;
     if (workspace_bytes < need) return SIM_ENOMEM;
     PoissonPlan pl;
     std::vector<double> minv;
-    if (!poisson_plan_init(&pl, dim, nn, hh, per, rtol, max_iter, d_workspace, workspace_bytes, &minv, &err))
+    if (!poisson_plan_init(&pl, dim, nn, hh, per, 0, rtol, max_iter, d_workspace, workspace_bytes, &minv, &err))
         return SIM_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (!poisson_upload_coarse(&pl, minv, st, &err)) return SIM_ECUDA;

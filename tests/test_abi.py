@@ -69,7 +69,7 @@ def test_invalid_parameters_rejected_without_gpu(lib_path):
     sz = ctypes.c_size_t()
     p = L.params_struct(prm)
     assert lib.sim_workspace_size(ctypes.byref(p), ctypes.byref(sz)) == L.SIM_OK
-    for key, val in [("dt", 0.0), ("dim", 4), ("poisson_rtol", 2.0), ("precision", 7)]:
+    for key, val in [("dt", 0.0), ("dim", 4), ("poisson_rtol", 2.0), ("precision", 7), ("precision", -1)]:
         bad = dict(prm)
         bad[key] = val
         assert lib.sim_workspace_size(ctypes.byref(L.params_struct(bad)), ctypes.byref(sz)) == L.SIM_EINVAL

@@ -171,6 +171,29 @@ def test_slot_burner_full_size_timing_tolerance():
 
 
 # ---------------------------------------------------------------------------
+# Mixed precision: FP32 multigrid preconditioner inside the FP64 CG.  The CG
+# residual and its stopping test stay FP64, so the converged fields keep the
+# FP64 parity bound.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["blobs", "slot", "sphere"])
+def test_mixed_multigrid_keeps_fp64_parity(case):
+    if case == "blobs":
+        prm, geo, f = W.periodic_blobs(64)
+        steps = 30
+    elif case == "slot":
+        prm, geo, f = W.slot_burner(64, 128)
+        steps = 20
+    else:
+        prm, geo, f = W.sphere_burner(24)
+        steps = 6
+    prm["poisson_rtol"] = 1e-12
+    prm["precision"] = W.MIXED
+    pb, st = oracle_run(prm, geo, f, steps)
+    sim = gpu_run(prm, geo, f, steps)
+    compare(sim, oracle_fields(pb, st), 1e-9)
+
+
+# ---------------------------------------------------------------------------
 # Execution paths and error handling
 # ---------------------------------------------------------------------------
 def test_graph_and_eager_paths_agree_bitwise(monkeypatch):
