@@ -209,7 +209,11 @@ def kernel_models(prm, mixed):
     m["residual"] = dict(id=0, bytes=(reads + writes) * N * 8.0, flops=N * (60.0 * dim * dim))
     m["state"] = dict(id=4, bytes=5 * N * 8.0, flops=N * 40.0)
     m["project"] = dict(id=5, bytes=(1 + 2 * dim + 1 + dim) * N * 8.0, flops=N * 8.0 * dim)
-    m["mg_tail"] = dict(id=6, bytes=0.0, flops=0.0)
+    # coarse levels (one block): right-hand side in, correction out; with the
+    # fast-diagonalisation solve (2D mixed) four dense products of the top level
+    nt = N / 4 ** 3 if dim == 2 else N / 8 ** 3
+    side = nt ** 0.5 if dim == 2 else nt ** (1.0 / 3.0)
+    m["mg_tail"] = dict(id=6, bytes=2 * nt * w, flops=2.0 * nt * 4 * 1.5 * side)
     return m
 
 
@@ -223,7 +227,8 @@ def run_gpu(args, precision, world, rank, local, pg):
     torch.cuda.set_device(device)
     prm, geo, f, cfg = workload(args.config)
     prm["precision"] = LM.SIM_MIXED if precision == "mixed" else LM.SIM_FP64
-    stream = torch.cuda.current_stream(device)
+    stream = torch.cuda.Stream(device)     # side stream: kernel timing captures graphs on it
+    torch.cuda.set_stream(stream)
     sim = LM.Simulation(prm, geo, device=device, stream=stream)
     sim.set_fields(f)
     ncell = int(sim.query(LM.SIM_Q_NCELLS))
@@ -257,20 +262,27 @@ def run_gpu(args, precision, world, rank, local, pg):
     value = cells_all / (ms_max * 1e-3)
     resid = max(sim.query(LM.SIM_Q_RESID_PRED), sim.query(LM.SIM_Q_RESID_CORR))
 
-    # ---- per-kernel timing (the step's own arguments, back-to-back launches)
+    # ---- per-kernel timing: 100 launches of one kernel with the step's own
+    # arguments captured in a CUDA graph on the simulation's stream and replayed
+    # twice between CUDA events (device time, not host launch rate)
     models = kernel_models(prm, precision == "mixed")
-    reps = 200
+    reps = 100
     ktimes = {}
     for name, mdl in ([] if args.no_kernel_timing else models.items()):
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            sim.time_kernel(mdl["id"], reps)
+        graph.replay()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        sim.time_kernel(mdl["id"], 5)
         flush.zero_()
         e0.record(stream)
-        sim.time_kernel(mdl["id"], reps)
+        graph.replay()
+        graph.replay()
         e1.record(stream)
         torch.cuda.synchronize(device)
-        ktimes[name] = e0.elapsed_time(e1) * 1e-3 / reps
+        ktimes[name] = e0.elapsed_time(e1) * 1e-3 / (2 * reps)
+        del graph
     sim.sync()
 
     out = dict(value=value, ms_per_step=ms_max / K, launches=launches, iters_per_step=float(np.mean(iters)),

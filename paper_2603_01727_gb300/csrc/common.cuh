@@ -53,7 +53,11 @@ struct Phys {
     double Fshift;                     // level translation of F_eps (text after Eq 3.41)
     double kappa_in, rho_in_T;         // inflow transport coefficient, inflow temperature
     double inflow_v[3], inflow_Z, inflow_H;
+    double cA, cB, cT;                 // T = cT (cA (|x| + log1p(e^-2|x|)) + cB (Z - 1) + H), Eq 3.42
+    double iPe, iLePe;                 // 1/Pe, 1/(Le Pe) (uniform Le)
     int incompressible, closed;
+    int mixed;                         // 1: FP32 stencil arithmetic and multigrid (SIM_MIXED)
+    int sigma_is_07;                   // sigma == 0.7 exactly (paper value, Eq 2.50)
 };
 
 // ---------------------------------------------------------------------------
@@ -80,6 +84,34 @@ __device__ inline double block_sum(double v, double* smem /* NT/32 doubles */) {
     __syncthreads();
     return r;
 }
+
+// FP32 variant (for the FP32 inner Krylov loop); same fixed tree.
+template <int NT>
+__device__ inline float block_sum_f(float v, float* smem /* NT/32 floats */) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) smem[w] = v;
+    __syncthreads();
+    float r = 0.0f;
+    if (w == 0) {
+        r = (l < NT / 32) ? smem[l] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if (l == 0) smem[0] = r;
+    }
+    __syncthreads();
+    r = smem[0];
+    __syncthreads();
+    return r;
+}
+
+// Block sum in the accumulator's own type, returned as double.
+template <int NT>
+__device__ inline double block_sum_any(double v, double* smem, float*) { return block_sum<NT>(v, smem); }
+template <int NT>
+__device__ inline double block_sum_any(float v, double*, float* smemf) { return (double)block_sum_f<NT>(v, smemf); }
 
 // Sum of npart partial sums, every thread of the block gets the same value
 // (same order of additions in every block, so the result is bitwise identical).

@@ -30,6 +30,7 @@
 // the while-node conditional.
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -64,6 +65,13 @@ struct Box {
     static constexpr int SN = SX * SY * SZ;
     static constexpr int S1 = SX, S2 = SX * SY;   // shared-memory strides of y and z
 };
+
+__device__ __forceinline__ void coords(const int n[3], int t, int c[3]) {
+    c[0] = t % n[0];
+    const int r = t / n[0];
+    c[1] = r % n[1];
+    c[2] = r / n[1];
+}
 
 __device__ __forceinline__ int wrapi(int g, int n) {
     const int m = g % n;
@@ -349,7 +357,7 @@ __global__ void __launch_bounds__(Tile<DIM>::NT)
         }
     }
     __syncthreads();
-    double rz = 0.0, sz = 0.0;
+    TF rz = (TF)0, sz = (TF)0;
     {
         constexpr int W = B::FX, RY = B::FY, RZ = B::FZ;
         for (int k = threadIdx.x; k < W * RY * RZ; k += NT) {
@@ -361,19 +369,20 @@ __global__ void __launch_bounds__(Tile<DIM>::NT)
             const T u = su[s[0] + B::S1 * s[1] + B::S2 * s[2]];
             upost[gi] = u;
             if (FINE) {
-                rz += (double)f[gi] * (double)u;
-                sz += (double)u;
+                rz = fma(f[gi], (TF)u, rz);
+                sz += (TF)u;
             }
         }
     }
     if (FINE) {
         __shared__ double red[NT / 32];
-        rz = block_sum<NT>(rz, red);
-        sz = block_sum<NT>(sz, red);
+        __shared__ float redf[NT / 32];
+        const double brz = block_sum_any<NT>(rz, red, redf);
+        const double bsz = block_sum_any<NT>(sz, red, redf);
         const int nb = gridDim.x * gridDim.y * gridDim.z;
         if (threadIdx.x == 0) {
-            part_rz[block_linear()] = rz;
-            part_sz[block_linear()] = sz;
+            part_rz[block_linear()] = brz;
+            part_sz[block_linear()] = bsz;
         }
         if (arrive_last(cnt)) {
             const double RZ = sum_parts_cg<NT>(part_rz, nb, red);
@@ -393,19 +402,19 @@ __global__ void __launch_bounds__(Tile<DIM>::NT)
 // CG: p = (z - mean z) + beta p_old (p_new buffer by parity), q = A p, p.q;
 // the last block forms alpha = r.z / p.q.
 // ---------------------------------------------------------------------------
-template <class T, int DIM>
+template <class T, int DIM, class V>
 __global__ void __launch_bounds__(Tile<DIM>::NT)
-    k_cg_pq(LvT<double> L, const T* __restrict__ z, double* p0, double* p1, double* __restrict__ q,
-            double* part, double* scal, const int* ictl, unsigned int* cnt) {
+    k_cg_pq(LvT<V> L, const T* __restrict__ z, V* p0, V* p1, V* __restrict__ q, double* part, double* scal,
+            const int* ictl, unsigned int* cnt) {
     constexpr int H = 1;
     using B = Box<DIM, H>;
     constexpr int NT = Tile<DIM>::NT;
     extern __shared__ __align__(16) unsigned char smraw[];
-    double* sp = reinterpret_cast<double*>(smraw);
+    V* sp = reinterpret_cast<V*>(smraw);
     const int it = ictl[PI_IT];
-    const double* pold = (it & 1) ? p0 : p1;
-    double* pnew = (it & 1) ? p1 : p0;
-    const double beta = scal[PS_BETA], mz = scal[PS_MEANZ];
+    const V* pold = (it & 1) ? p0 : p1;
+    V* pnew = (it & 1) ? p1 : p0;
+    const V beta = (V)scal[PS_BETA], mz = (V)scal[PS_MEANZ];
     const int o[3] = {(int)blockIdx.x * B::FX - H, (int)blockIdx.y * B::FY - H,
                       (DIM == 3) ? (int)blockIdx.z * B::FZ - H : 0};
     int F[3] = {B::FX, B::FY, B::FZ};
@@ -413,35 +422,36 @@ __global__ void __launch_bounds__(Tile<DIM>::NT)
         const int s[3] = {i % B::SX, (i / B::SX) % B::SY, i / B::S2};
         int gi, cl;
         bool own;
-        double pv = 0.0;
-        if (cell_info<double, DIM>(L, o, s, H, F, &gi, &cl, &own)) {
-            pv = (double)z[gi] - mz;
+        V pv = (V)0;
+        if (cell_info<V, DIM>(L, o, s, H, F, &gi, &cl, &own)) {
+            pv = (V)z[gi] - mz;
             if (it > 0) pv = fma(beta, pold[gi], pv);
         }
         sp[i] = pv;
     }
     __syncthreads();
-    double pq = 0.0;
+    V pq = (V)0;
     {
         constexpr int W = B::FX, RY = B::FY, RZ = B::FZ;
         for (int k = threadIdx.x; k < W * RY * RZ; k += NT) {
             const int s[3] = {1 + k % W, 1 + (k / W) % RY, (DIM == 3) ? 1 + k / (W * RY) : 0};
             int gi, cl;
             bool own;
-            cell_info<double, DIM>(L, o, s, H, F, &gi, &cl, &own);
+            cell_info<V, DIM>(L, o, s, H, F, &gi, &cl, &own);
             if (!own) continue;
             const int i = s[0] + B::S1 * s[1] + B::S2 * s[2];
-            const double pv = sp[i];
-            const double qv = L.diag[cl] * pv - off_box<double, DIM, B>(L, sp, i);
+            const V pv = sp[i];
+            const V qv = L.diag[cl] * pv - off_box<V, DIM, B>(L, sp, i);
             pnew[gi] = pv;
             q[gi] = qv;
             pq = fma(pv, qv, pq);
         }
     }
     __shared__ double red[NT / 32];
-    pq = block_sum<NT>(pq, red);
+    __shared__ float redf[NT / 32];
+    const double bpq = block_sum_any<NT>(pq, red, redf);
     const int nb = gridDim.x * gridDim.y * gridDim.z;
-    if (threadIdx.x == 0) part[block_linear()] = pq;
+    if (threadIdx.x == 0) part[block_linear()] = bpq;
     if (arrive_last(cnt)) {
         const double PQ = sum_parts_cg<NT>(part, nb, red);
         if (threadIdx.x == 0) {
@@ -490,6 +500,104 @@ __global__ void __launch_bounds__(NTV)
 }
 
 // ---------------------------------------------------------------------------
+// Refinement mode: FP32 inner update, then (when due) the FP64 outer step.
+// ---------------------------------------------------------------------------
+// e = (first inner iteration ? 0 : e) + alpha p, r32 -= alpha q, ||r32||^2; the
+// last block counts the iteration and flags an outer step when the inner solve
+// reached inner_tol (relative to its start), inner_max, or the solve's cap.
+__global__ void __launch_bounds__(NTV)
+    k_ir_update(float* __restrict__ e, float* __restrict__ r, const float* p0, const float* p1,
+                const float* __restrict__ q, long long N, double* part, double* scal, int* ictl, unsigned int* cnt,
+                double inner_tol, int inner_max, int max_iter, cudaGraphConditionalHandle h, int use_graph) {
+    const int it = ictl[PI_IT];
+    const float* __restrict__ p = (it & 1) ? p1 : p0;
+    const float alpha = (float)scal[PS_ALPHA];
+    float rr = 0.0f;
+    for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV) {
+        const float ev = (it == 0) ? 0.0f : e[t];
+        e[t] = fmaf(alpha, p[t], ev);
+        const float rv = fmaf(-alpha, q[t], r[t]);
+        r[t] = rv;
+        rr = fmaf(rv, rv, rr);
+    }
+    __shared__ float redf[NTV / 32];
+    __shared__ double red[NTV / 32];
+    const float brr = block_sum_f<NTV>(rr, redf);
+    if (threadIdx.x == 0) part[blockIdx.x] = (double)brr;
+    if (arrive_last(cnt)) {
+        const double RR = sum_parts_cg<NTV>(part, gridDim.x, red);
+        if (threadIdx.x == 0) {
+            const int itn = it + 1, tot = ictl[PI_TOTAL] + 1;
+            ictl[PI_IT] = itn;
+            ictl[PI_TOTAL] = tot;
+            scal[PS_ITERS] = (double)tot;
+            const int bad = !(RR == RR) || !(RR < 1e300);
+            const int refine = (RR <= inner_tol * inner_tol * scal[PS_RR0]) || (itn >= inner_max) ||
+                               (tot >= max_iter) || bad;
+            ictl[PI_REFINE] = refine;
+            if (!refine && use_graph) cudaGraphSetConditional(h, 1u);
+            *cnt = 0u;
+        }
+    }
+}
+
+// Outer step (FP64), only when flagged: x += e, r64 -= A e (e exact in FP64),
+// r32 = r64, ||r64||^2; the last block applies the FP64 stopping test and
+// restarts the inner solve.
+template <int DIM>
+__global__ void __launch_bounds__(NTV)
+    k_ir_refine(LvT<double> L, double* __restrict__ x, double* __restrict__ r64, const float* __restrict__ e,
+                float* __restrict__ r32, double* part, double* scal, int* ictl, unsigned int* cnt, double rtol,
+                int max_iter, cudaGraphConditionalHandle h, int use_graph) {
+    if (!ictl[PI_REFINE]) return;
+    double rr = 0.0;
+    for (int t = blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
+        int c[3];
+        coords(L.n, t, c);
+        double off = 0.0;
+        int stride = 1, p3 = 1, cl = 0;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const int n = L.n[d];
+            if (c[d] > 0) off += L.w[d] * (double)e[t - stride];
+            else if (L.per[d]) off += L.w[d] * (double)e[t + (n - 1) * stride];
+            if (c[d] < n - 1) off += L.w[d] * (double)e[t + stride];
+            else if (L.per[d]) off += L.w[d] * (double)e[t - (n - 1) * stride];
+            cl += (L.per[d] ? 2 : (int)(c[d] > 0) + (int)(c[d] < n - 1)) * p3;
+            stride *= n;
+            p3 *= 3;
+        }
+        const double ev = (double)e[t];
+        x[t] += ev;
+        const double rv = r64[t] - (L.diag[cl] * ev - off);
+        r64[t] = rv;
+        r32[t] = (float)rv;
+        rr = fma(rv, rv, rr);
+    }
+    __shared__ double red[NTV / 32];
+    rr = block_sum<NTV>(rr, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = rr;
+    if (arrive_last(cnt)) {
+        const double RR = sum_parts_cg<NTV>(part, gridDim.x, red);
+        if (threadIdx.x == 0) {
+            const double ff = scal[PS_FF];
+            const int conv = (RR <= rtol * rtol * ff);
+            const int bad = !(RR == RR) || !(RR < 1e300);
+            const int done = conv || bad || (ictl[PI_TOTAL] >= max_iter);
+            scal[PS_RR] = RR;
+            scal[PS_RR0] = RR;
+            scal[PS_RELRES] = sqrt(RR / ff);
+            ictl[PI_IT] = 0;
+            ictl[PI_REFINE] = 0;
+            ictl[PI_DONE] = done;
+            if (done && !conv) ictl[PI_NOCONV] = 1;
+            if (use_graph) cudaGraphSetConditional(h, done ? 0u : 1u);
+            *cnt = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Compact-array stencil (tail levels, prologue)
 // ---------------------------------------------------------------------------
 template <class T, int DIM>
@@ -510,13 +618,6 @@ __device__ __forceinline__ T off_compact(const LvT<T>& L, const T* u, int t, con
     }
     *cls = cl;
     return off;
-}
-
-__device__ __forceinline__ void coords(const int n[3], int t, int c[3]) {
-    c[0] = t % n[0];
-    const int r = t / n[0];
-    c[1] = r % n[1];
-    c[2] = r / n[1];
 }
 
 // Sum of b (partials; the last block stores the mean).
@@ -541,8 +642,8 @@ __global__ void __launch_bounds__(NTV) k_mean(const double* __restrict__ b, long
 template <int DIM>
 __global__ void __launch_bounds__(NTV)
     k_pcg_init(LvT<double> L, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
-               double* pff, double* prr, double* scal, int* ictl, unsigned int* cnt, double rtol,
-               cudaGraphConditionalHandle h, int use_graph) {
+               float* __restrict__ r32, double* pff, double* prr, double* scal, int* ictl, unsigned int* cnt,
+               double rtol, cudaGraphConditionalHandle h, int use_graph) {
     const double mean_b = scal[PS_MEANB];
     double ff = 0.0, rr = 0.0;
     for (int t = blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
@@ -553,6 +654,7 @@ __global__ void __launch_bounds__(NTV)
         const double f = -(b[t] - mean_b);
         const double rv = f - (L.diag[cl] * x[t] - off);
         r[t] = rv;
+        if (r32) r32[t] = (float)rv;
         ff = fma(f, f, ff);
         rr = fma(rv, rv, rr);
     }
@@ -572,7 +674,10 @@ __global__ void __launch_bounds__(NTV)
             scal[PS_RZ] = 0.0;
             scal[PS_BETA] = 0.0;
             scal[PS_ITERS] = 0.0;
+            scal[PS_RR0] = RR;
             ictl[PI_IT] = 0;
+            ictl[PI_TOTAL] = 0;
+            ictl[PI_REFINE] = 0;
             ictl[PI_NOCONV] = 0;
             const int zero = !(FF > 0.0);
             ictl[PI_ZERO] = zero;
@@ -758,6 +863,475 @@ __global__ void __launch_bounds__(kTailThreads)
     }
 }
 
+// ---------------------------------------------------------------------------
+// 2D kernels: a 32-column shared-memory box, one warp per box row (lane =
+// column), colour sweeps two rows per warp step (lanes 0-15 and 16-31 take
+// alternate rows, so the two half-warps hit even and odd banks).
+// ---------------------------------------------------------------------------
+namespace k2 {
+
+constexpr int NW = 8;             // warps per block
+constexpr int NT = 32 * NW;
+constexpr int SY = 32;            // box rows
+constexpr int FD = 26;            // down: fine tile (box 32 = 26 + 2 x 3), coarse tile 13
+constexpr int CD = 13;
+constexpr int FU = 28;            // up: fine tile (32 = 28 + 2 x 2)
+constexpr int FP = 30;            // CG operator: tile (32 = 30 + 2 x 1)
+
+struct Ax {
+    int gw;       // wrapped index (valid cells)
+    int cls;      // neighbour count along the axis
+    bool valid;   // inside the domain or periodic
+    bool in;      // inside the domain (unwrapped)
+};
+
+__device__ __forceinline__ Ax axis(int g, int n, int per) {
+    Ax a;
+    a.in = (g >= 0 && g < n);
+    a.gw = a.in ? g : (per ? wrapi(g, n) : 0);
+    a.valid = a.in || per;
+    a.cls = per ? 2 : (int)(a.gw > 0) + (int)(a.gw < n - 1);
+    return a;
+}
+
+template <class T>
+__device__ __forceinline__ T off2(const LvT<T>& L, T (*su)[32], int r, int c) {
+    return L.w[0] * (su[r][c - 1] + su[r][c + 1]) + L.w[1] * (su[r - 1][c] + su[r + 1][c]);
+}
+
+// One colour on rows [r0, r1] x columns [c0, c1] of the box.
+template <class T>
+__device__ __forceinline__ void color_sweep(const LvT<T>& L, T (*su)[32], T (*sf)[32], int ox, int oy, int par0,
+                                            int color, int r0, int r1, int c0, int c1) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int npairs = (r1 - r0 + 2) / 2;
+    for (int rp = warp; rp < npairs; rp += NW) {
+        const int r = r0 + 2 * rp + (lane >> 4);
+        const int c = 2 * (lane & 15) + ((color - par0 - r) & 1);
+        if (r > r1 || c < c0 || c > c1) continue;
+        const Ax ax = axis(ox + c, L.n[0], L.per[0]);
+        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        if (!(ax.valid && ay.valid)) continue;
+        su[r][c] = (sf[r][c] + off2<T>(L, su, r, c)) * L.invd[ax.cls + 3 * ay.cls];
+    }
+}
+
+template <class T, class TF>
+__global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restrict__ f, T* __restrict__ upre,
+                                           T* __restrict__ fc) {
+    constexpr int H = 3;
+    __shared__ T sf[SY][32];
+    __shared__ T su[SY][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ox = blockIdx.x * FD - H, oy = blockIdx.y * FD - H;
+    const int nx = L.n[0];
+    const int par0 = (ox + oy) & 1;
+    const Ax ax = axis(ox + lane, nx, L.per[0]);
+#pragma unroll
+    for (int k = 0; k < SY / NW; ++k) {
+        const int r = warp + NW * k;
+        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        T fv = (T)0, uv = (T)0;
+        if (ax.valid && ay.valid) {
+            fv = (T)f[ax.gw + nx * ay.gw];
+            if (((par0 + lane + r) & 1) == 0) uv = fv * L.invd[ax.cls + 3 * ay.cls];
+        }
+        sf[r][lane] = fv;
+        su[r][lane] = uv;
+    }
+    __syncthreads();
+    color_sweep<T>(L, su, sf, ox, oy, par0, 1, 1, SY - 2, 1, 30);
+    __syncthreads();
+    // residual on rows / columns 2 .. 29 (overwrites f); store the tile's u
+    const bool colr = (lane >= 2 && lane <= 29);
+#pragma unroll
+    for (int k = 0; k < SY / NW; ++k) {
+        const int r = warp + NW * k;
+        if (r < 2 || r > 29 || !colr) continue;
+        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        if (!(ax.valid && ay.valid)) continue;
+        const T u = su[r][lane];
+        sf[r][lane] = sf[r][lane] - (L.diag[ax.cls + 3 * ay.cls] * u - off2<T>(L, su, r, lane));
+        if (ax.in && ay.in && lane >= H && lane < H + FD && r >= H && r < H + FD) upre[ax.gw + nx * ay.gw] = u;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < CD * CD; c += NT) {
+        const int cx = c % CD, cy = c / CD;
+        const int I = blockIdx.x * CD + cx, J = blockIdx.y * CD + cy;
+        if (I >= C.n[0] || J >= C.n[1]) continue;
+        T acc = (T)0;
+#pragma unroll
+        for (int ay = 0; ay < 4; ++ay) {
+            const T wy = (T)rweight(ay, J, C.n[1], C.per[1]);
+            const int r = 2 * cy + 2 + ay;
+            T row = (T)0;
+#pragma unroll
+            for (int axx = 0; axx < 4; ++axx) row += (T)rweight(axx, I, C.n[0], C.per[0]) * sf[r][2 * cx + 2 + axx];
+            acc += wy * row;
+        }
+        fc[I + C.n[0] * J] = acc * (T)0.25;
+    }
+}
+
+template <class T, class TF, bool FINE>
+__global__ void __launch_bounds__(NT)
+    up(LvT<T> L, LvT<T> C, const T* __restrict__ upre, const TF* __restrict__ f, const T* __restrict__ uc,
+       T* __restrict__ upost, double* part_rz, double* part_sz, double* scal, const int* ictl, unsigned int* cnt) {
+    constexpr int H = 2;
+    __shared__ T sf[SY][32];
+    __shared__ T su[SY][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ox = blockIdx.x * FU - H, oy = blockIdx.y * FU - H;
+    const int nx = L.n[0];
+    const int par0 = (ox + oy) & 1;
+    const Ax ax = axis(ox + lane, nx, L.per[0]);
+    // coarse columns of this lane's fine column (bilinear prolongation)
+    int I0 = 0, I1 = 0;
+    if (ax.valid) pro_pair(ax.gw, C.n[0], C.per[0], &I0, &I1);
+    const T a = (T)0.75, b = (T)0.25;
+#pragma unroll
+    for (int k = 0; k < SY / NW; ++k) {
+        const int r = warp + NW * k;
+        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        T fv = (T)0, uv = (T)0;
+        if (ax.valid && ay.valid) {
+            const int g = ax.gw + nx * ay.gw;
+            fv = (T)f[g];
+            int J0, J1;
+            pro_pair(ay.gw, C.n[1], C.per[1], &J0, &J1);
+            const T* c0 = uc + C.n[0] * J0;
+            const T* c1 = uc + C.n[0] * J1;
+            uv = upre[g] + a * (a * c0[I0] + b * c0[I1]) + b * (a * c1[I0] + b * c1[I1]);
+        }
+        sf[r][lane] = fv;
+        su[r][lane] = uv;
+    }
+    __syncthreads();
+    color_sweep<T>(L, su, sf, ox, oy, par0, 1, 1, SY - 2, 1, 30);
+    __syncthreads();
+    color_sweep<T>(L, su, sf, ox, oy, par0, 0, 2, SY - 3, 2, 29);
+    __syncthreads();
+    TF rz = (TF)0, sz = (TF)0;    // FP64 path: double; refinement mode: FP32
+    const bool colo = ax.in && lane >= H && lane < H + FU;
+#pragma unroll
+    for (int k = 0; k < SY / NW; ++k) {
+        const int r = warp + NW * k;
+        if (!colo || r < H || r >= H + FU) continue;
+        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        if (!ay.in) continue;
+        const int g = ax.gw + nx * ay.gw;
+        const T u = su[r][lane];
+        upost[g] = u;
+        if (FINE) {
+            rz = fma(f[g], (TF)u, rz);
+            sz += (TF)u;
+        }
+    }
+    if (FINE) {
+        __shared__ double red[NT / 32];
+        __shared__ float redf[NT / 32];
+        const double brz = block_sum_any<NT>(rz, red, redf);
+        const double bsz = block_sum_any<NT>(sz, red, redf);
+        const int nb = gridDim.x * gridDim.y;
+        const int bid = blockIdx.x + gridDim.x * blockIdx.y;
+        if (threadIdx.x == 0) {
+            part_rz[bid] = brz;
+            part_sz[bid] = bsz;
+        }
+        if (arrive_last(cnt)) {
+            const double RZ = sum_parts_cg<NT>(part_rz, nb, red);
+            const double SZ = sum_parts_cg<NT>(part_sz, nb, red);
+            if (threadIdx.x == 0) {
+                const int it = ictl[PI_IT];
+                scal[PS_BETA] = (it == 0) ? 0.0 : RZ / scal[PS_RZ];
+                scal[PS_RZ] = RZ;
+                scal[PS_MEANZ] = SZ / (double)L.N;
+                *cnt = 0u;
+            }
+        }
+    }
+}
+
+template <class T, class V>
+__global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p0, V* p1, V* __restrict__ q,
+                                         double* part, double* scal, const int* ictl, unsigned int* cnt) {
+    constexpr int H = 1;
+    __shared__ V sp[SY][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int it = ictl[PI_IT];
+    const V* pold = (it & 1) ? p0 : p1;
+    V* pnew = (it & 1) ? p1 : p0;
+    const V beta = (V)scal[PS_BETA], mz = (V)scal[PS_MEANZ];
+    const int ox = blockIdx.x * FP - H, oy = blockIdx.y * FP - H;
+    const int nx = L.n[0];
+    const Ax ax = axis(ox + lane, nx, L.per[0]);
+#pragma unroll
+    for (int k = 0; k < SY / NW; ++k) {
+        const int r = warp + NW * k;
+        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        V pv = (V)0;
+        if (ax.valid && ay.valid) {
+            const int g = ax.gw + nx * ay.gw;
+            pv = (V)z[g] - mz;
+            if (it > 0) pv = fma(beta, pold[g], pv);
+        }
+        sp[r][lane] = pv;
+    }
+    __syncthreads();
+    V acc = (V)0;
+    const bool colo = ax.in && lane >= H && lane < H + FP;
+#pragma unroll
+    for (int k = 0; k < SY / NW; ++k) {
+        const int r = warp + NW * k;
+        if (!colo || r < H || r >= H + FP) continue;
+        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        if (!ay.in) continue;
+        const int g = ax.gw + nx * ay.gw;
+        const V pv = sp[r][lane];
+        const V off = L.w[0] * (sp[r][lane - 1] + sp[r][lane + 1]) + L.w[1] * (sp[r - 1][lane] + sp[r + 1][lane]);
+        const V qv = L.diag[ax.cls + 3 * ay.cls] * pv - off;
+        pnew[g] = pv;
+        q[g] = qv;
+        acc = fma(pv, qv, acc);
+    }
+    __shared__ double red[NT / 32];
+    __shared__ float redf[NT / 32];
+    const double bacc = block_sum_any<NT>(acc, red, redf);
+    const int nb = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) part[blockIdx.x + gridDim.x * blockIdx.y] = bacc;
+    if (arrive_last(cnt)) {
+        const double PQ = sum_parts_cg<NT>(part, nb, red);
+        if (threadIdx.x == 0) {
+            scal[PS_ALPHA] = scal[PS_RZ] / PQ;
+            *cnt = 0u;
+        }
+    }
+}
+
+// Coarse levels top .. nlev-1 in one block; warps over rows, lanes over columns.
+constexpr int TW = 16;            // warps of the tail block
+constexpr int TT = 32 * TW;
+
+template <class T>
+__device__ __forceinline__ T off_c(const LvT<T>& L, const T* u, int i, int j, int* cls) {
+    const int nx = L.n[0], ny = L.n[1], t = i + nx * j;
+    T o = (T)0;
+    if (i > 0) o += L.w[0] * u[t - 1];
+    else if (L.per[0]) o += L.w[0] * u[t + nx - 1];
+    if (i < nx - 1) o += L.w[0] * u[t + 1];
+    else if (L.per[0]) o += L.w[0] * u[t - (nx - 1)];
+    if (j > 0) o += L.w[1] * u[t - nx];
+    else if (L.per[1]) o += L.w[1] * u[t + nx * (ny - 1)];
+    if (j < ny - 1) o += L.w[1] * u[t + nx];
+    else if (L.per[1]) o += L.w[1] * u[t - nx * (ny - 1)];
+    *cls = (L.per[0] ? 2 : (int)(i > 0) + (int)(i < nx - 1)) + 3 * (L.per[1] ? 2 : (int)(j > 0) + (int)(j < ny - 1));
+    return o;
+}
+
+template <class T>
+__device__ __forceinline__ void tail_color(const LvT<T>& L, T* u, const T* f, int color) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nx = L.n[0], ny = L.n[1];
+    for (int j = warp; j < ny; j += TW)
+        for (int i = lane; i < nx; i += 32) {
+            if (((i + j) & 1) != color) continue;
+            int cl;
+            const T o = off_c<T>(L, u, i, j, &cl);
+            u[i + nx * j] = (f[i + nx * j] + o) * L.invd[cl];
+        }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TT) tail(const LvT<T>* __restrict__ levs, TailArgs a, const T* __restrict__ f_top,
+                                           T* __restrict__ u_top, const T* __restrict__ Minv) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ LvT<T> lv[kMaxLevels];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int top = a.top, last = a.nlev - 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    {
+        const int words = (int)(sizeof(LvT<T>) / 4) * (last - top + 1);
+        const unsigned int* src = reinterpret_cast<const unsigned int*>(levs + top);
+        unsigned int* dst = reinterpret_cast<unsigned int*>(lv + top);
+        for (int k = threadIdx.x; k < words; k += TT) dst[k] = src[k];
+        const int N = levs[top].N;
+        T* f = sm + a.off_f[top];
+        for (int t = threadIdx.x; t < N; t += TT) f[t] = f_top[t];
+    }
+    __syncthreads();
+    for (int l = top; l < last; ++l) {
+        const LvT<T>& L = lv[l];
+        const LvT<T>& C = lv[l + 1];
+        const int nx = L.n[0], ny = L.n[1];
+        T* u = sm + a.off_u[l];
+        const T* f = sm + a.off_f[l];
+        T* r = sm + a.off_r;
+        T* fc = sm + a.off_f[l + 1];
+        for (int j = warp; j < ny; j += TW)
+            for (int i = lane; i < nx; i += 32) {
+                const int cl = (L.per[0] ? 2 : (int)(i > 0) + (int)(i < nx - 1)) +
+                               3 * (L.per[1] ? 2 : (int)(j > 0) + (int)(j < ny - 1));
+                u[i + nx * j] = (((i + j) & 1) == 0) ? f[i + nx * j] * L.invd[cl] : (T)0;
+            }
+        __syncthreads();
+        tail_color<T>(L, u, f, 1);
+        __syncthreads();
+        for (int j = warp; j < ny; j += TW)
+            for (int i = lane; i < nx; i += 32) {
+                int cl;
+                const T o = off_c<T>(L, u, i, j, &cl);
+                const int t = i + nx * j;
+                r[t] = f[t] - (L.diag[cl] * u[t] - o);
+            }
+        __syncthreads();
+        const int cx = C.n[0], cy = C.n[1];
+        for (int J = warp; J < cy; J += TW)
+            for (int I = lane; I < cx; I += 32) {
+                T acc = (T)0;
+#pragma unroll
+                for (int ay = 0; ay < 4; ++ay) {
+                    const T wy = (T)rweight(ay, J, cy, C.per[1]);
+                    const int fy = wrapi(2 * J - 1 + ay, ny);
+#pragma unroll
+                    for (int axx = 0; axx < 4; ++axx) {
+                        const T wx = (T)rweight(axx, I, cx, C.per[0]);
+                        const int fx = wrapi(2 * I - 1 + axx, nx);
+                        acc += wy * wx * ((wx != (T)0 && wy != (T)0) ? r[fx + nx * fy] : (T)0);
+                    }
+                }
+                fc[I + cx * J] = acc * (T)0.25;
+            }
+        __syncthreads();
+    }
+    {
+        const int Nc = a.Nc;
+        const T* f = sm + a.off_f[last];
+        T* u = sm + a.off_u[last];
+        for (int i = threadIdx.x; i < Nc; i += TT) {
+            T acc = (T)0;
+            const T* row = Minv + (size_t)i * Nc;
+            for (int j = 0; j < Nc; ++j) acc += row[j] * f[j];
+            u[i] = acc;
+        }
+    }
+    __syncthreads();
+    for (int l = last - 1; l >= top; --l) {
+        const LvT<T>& L = lv[l];
+        const LvT<T>& C = lv[l + 1];
+        const int nx = L.n[0], ny = L.n[1];
+        T* u = sm + a.off_u[l];
+        const T* f = sm + a.off_f[l];
+        const T* uc = sm + a.off_u[l + 1];
+        const T pa = (T)0.75, pb = (T)0.25;
+        for (int j = warp; j < ny; j += TW) {
+            int J0, J1;
+            pro_pair(j, C.n[1], C.per[1], &J0, &J1);
+            for (int i = lane; i < nx; i += 32) {
+                int I0, I1;
+                pro_pair(i, C.n[0], C.per[0], &I0, &I1);
+                const T* c0 = uc + C.n[0] * J0;
+                const T* c1 = uc + C.n[0] * J1;
+                u[i + nx * j] += pa * (pa * c0[I0] + pb * c0[I1]) + pb * (pa * c1[I0] + pb * c1[I1]);
+            }
+        }
+        __syncthreads();
+        tail_color<T>(L, u, f, 1);
+        __syncthreads();
+        tail_color<T>(L, u, f, 0);
+        __syncthreads();
+    }
+    {
+        const int N = lv[top].N;
+        const T* u = sm + a.off_u[top];
+        for (int t = threadIdx.x; t < N; t += TT) u_top[t] = u[t];
+    }
+}
+
+// Exact solve on the top coarse level by fast diagonalisation (Lynch, Rice &
+// Thomas): the level operator is A = Ax (x) I + I (x) Ay with 1D second-difference
+// matrices Ad = Sd diag(lam_d) Sd^T, so the zero-mean solution of A u = f is
+//   u = Sy [ (Sy^T F Sx) .* IL ] Sx^T,   IL[l][k] = 1 / (lam_y,l + lam_x,k) (0 for the null mode),
+// four small dense products in shared memory.  F, u: ny rows of nx values.
+constexpr int FT = 256;            // threads of the fast-diagonalisation block
+
+// C[M x N] = L[M x K] R[K x N] (row-major, leading dimensions K and N), each
+// thread a 2 x 4 tile: per k two scalar loads of L (shared by the threads of a
+// tile row) and one float4 load of R; optionally C .*= S.  N % 4 == 0, M even.
+__device__ __forceinline__ void mm24(float* __restrict__ C, const float* __restrict__ L, const float* __restrict__ R,
+                                     int M, int N, int K, const float* __restrict__ S) {
+    const int tn = N / 4;
+    for (int tile = threadIdx.x; tile < (M / 2) * tn; tile += FT) {
+        const int m0 = 2 * (tile / tn), n0 = 4 * (tile % tn);
+        const float* l0 = L + m0 * K;
+        const float* l1 = l0 + K;
+        float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+            const float4 r = *reinterpret_cast<const float4*>(R + k * N + n0);
+            const float a0 = l0[k], a1 = l1[k];
+            c0.x = fmaf(a0, r.x, c0.x);
+            c0.y = fmaf(a0, r.y, c0.y);
+            c0.z = fmaf(a0, r.z, c0.z);
+            c0.w = fmaf(a0, r.w, c0.w);
+            c1.x = fmaf(a1, r.x, c1.x);
+            c1.y = fmaf(a1, r.y, c1.y);
+            c1.z = fmaf(a1, r.z, c1.z);
+            c1.w = fmaf(a1, r.w, c1.w);
+        }
+        if (S) {
+            const float4 s0 = *reinterpret_cast<const float4*>(S + m0 * N + n0);
+            const float4 s1 = *reinterpret_cast<const float4*>(S + (m0 + 1) * N + n0);
+            c0.x *= s0.x; c0.y *= s0.y; c0.z *= s0.z; c0.w *= s0.w;
+            c1.x *= s1.x; c1.y *= s1.y; c1.z *= s1.z; c1.w *= s1.w;
+        }
+        *reinterpret_cast<float4*>(C + m0 * N + n0) = c0;
+        *reinterpret_cast<float4*>(C + (m0 + 1) * N + n0) = c1;
+    }
+}
+
+// Shared-memory layout (floats): Sx, SxT (nx*nx each), Sy, SyT (ny*ny each),
+// IL, A, B (nx*ny each); the global tables hold Sx, Sy, IL in that order.
+__global__ void __launch_bounds__(FT) fdm(int nx, int ny, const float* __restrict__ tab, const float* __restrict__ f,
+                                          float* __restrict__ u) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* Sx = reinterpret_cast<float*>(smraw);
+    float* SxT = Sx + nx * nx;
+    float* Sy = SxT + nx * nx;
+    float* SyT = Sy + ny * ny;
+    float* IL = SyT + ny * ny;
+    float* A = IL + nx * ny;
+    float* B = A + nx * ny;
+    const float* gSx = tab;
+    const float* gSy = tab + nx * nx;
+    const float* gIL = gSy + ny * ny;
+    for (int i = threadIdx.x; i < nx * nx; i += FT) {
+        const float v = gSx[i];
+        Sx[i] = v;
+        SxT[(i % nx) * nx + i / nx] = v;
+    }
+    for (int i = threadIdx.x; i < ny * ny; i += FT) {
+        const float v = gSy[i];
+        Sy[i] = v;
+        SyT[(i % ny) * ny + i / ny] = v;
+    }
+    for (int i = threadIdx.x; i < nx * ny; i += FT) {
+        IL[i] = gIL[i];
+        A[i] = f[i];
+    }
+    __syncthreads();
+    mm24(B, A, Sx, ny, nx, nx, nullptr);    // B = F Sx
+    __syncthreads();
+    mm24(A, SyT, B, ny, nx, ny, IL);        // A = (Sy^T B) .* IL
+    __syncthreads();
+    mm24(B, Sy, A, ny, nx, ny, nullptr);    // B = Sy A
+    __syncthreads();
+    mm24(A, B, SxT, ny, nx, nx, nullptr);   // A = B Sx^T
+    __syncthreads();
+    for (int i = threadIdx.x; i < nx * ny; i += FT) u[i] = A[i];
+}
+
+}  // namespace k2
+
 // ------------------------------ host helpers --------------------------------
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -803,7 +1377,12 @@ int pick_top(const Shapes& s, int mg_fp32, size_t* smem_out) {
         *smem_out = 0;
         return 0;
     }
-    const long long thr = mg_fp32 ? kTailCellsF32 : kTailCellsF64;
+    long long thr = mg_fp32 ? kTailCellsF32 : kTailCellsF64;
+    // tuning override: LOWMACH_TAIL_CELLS = largest level handled by the tail block
+    if (const char* e = std::getenv("LOWMACH_TAIL_CELLS")) {
+        const long long v = std::atoll(e);
+        if (v > 0) thr = v;
+    }
     const size_t w = mg_fp32 ? 4 : 8;
     for (int top = 1; top < s.nlev; ++top) {
         if (s.N[top] > thr && top < s.nlev - 1) continue;
@@ -816,6 +1395,12 @@ int pick_top(const Shapes& s, int mg_fp32, size_t* smem_out) {
     }
     *smem_out = 0;
     return s.nlev - 1;
+}
+
+long long k2_blocks(const int n[3]) {
+    const long long up = (long long)((n[0] + k2::FU - 1) / k2::FU) * ((n[1] + k2::FU - 1) / k2::FU);
+    const long long pq = (long long)((n[0] + k2::FP - 1) / k2::FP) * ((n[1] + k2::FP - 1) / k2::FP);
+    return up > pq ? up : pq;
 }
 
 template <int DIM>
@@ -907,6 +1492,49 @@ std::vector<double> coarse_inverse(const MgLevel& L, int dim) {
     return A;
 }
 
+// Orthonormal eigenvectors (columns, S[i * n + k]) and eigenvalues of the 1D
+// cell-centred second-difference matrix (diagonal 2, off-diagonals -1) scaled
+// by 1/h^2: Neumann ends (diagonal 1 at the ends) -> DCT-II basis
+// cos(pi k (i + 1/2) / n), lam = 2 - 2 cos(pi k / n); periodic -> real Fourier
+// basis cos / sin(2 pi m i / n), lam = 2 - 2 cos(2 pi m / n).
+void eig1d(int n, int periodic, double h, std::vector<double>& S, std::vector<double>& lam) {
+    const double pi = 3.14159265358979323846;
+    S.assign((size_t)n * n, 0.0);
+    lam.assign(n, 0.0);
+    const double ih2 = 1.0 / (h * h);
+    if (!periodic) {
+        for (int k = 0; k < n; ++k) {
+            const double ck = (k == 0) ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);
+            for (int i = 0; i < n; ++i) S[(size_t)i * n + k] = ck * std::cos(pi * k * (i + 0.5) / n);
+            lam[k] = (2.0 - 2.0 * std::cos(pi * k / n)) * ih2;
+        }
+        return;
+    }
+    for (int i = 0; i < n; ++i) S[(size_t)i * n] = std::sqrt(1.0 / n);
+    lam[0] = 0.0;
+    int col = 1;
+    for (int m = 1; 2 * m < n; ++m) {
+        const double l = (2.0 - 2.0 * std::cos(2.0 * pi * m / n)) * ih2;
+        for (int i = 0; i < n; ++i) {
+            S[(size_t)i * n + col] = std::sqrt(2.0 / n) * std::cos(2.0 * pi * m * i / n);
+            S[(size_t)i * n + col + 1] = std::sqrt(2.0 / n) * std::sin(2.0 * pi * m * i / n);
+        }
+        lam[col] = lam[col + 1] = l;
+        col += 2;
+    }
+    if (n % 2 == 0) {
+        for (int i = 0; i < n; ++i) S[(size_t)i * n + col] = (i % 2 == 0 ? 1.0 : -1.0) / std::sqrt((double)n);
+        lam[col] = 4.0 * ih2;
+    }
+}
+
+bool fdm_fits(const Shapes& s, int top, int dim, int mg_fp32) {
+    if (dim != 2 || !mg_fp32 || s.nlev < 2) return false;
+    const long long nx = s.n[top][0], ny = s.n[top][1];
+    const size_t smem = sizeof(float) * (size_t)(2 * nx * nx + 2 * ny * ny + 3 * nx * ny);
+    return nx % 4 == 0 && ny % 2 == 0 && nx <= 128 && ny <= 128 && smem <= kTailSmemMax;
+}
+
 template <class T>
 LvT<T> make_lv(const MgLevel& L, int dim) {
     LvT<T> v;
@@ -940,8 +1568,10 @@ void set_smem_attrs() {
                          2 * Box<3, 2>::SN * (int)sizeof(T));
     cudaFuncSetAttribute(k_mg_tail<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
     cudaFuncSetAttribute(k_mg_tail<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
-    cudaFuncSetAttribute(k_cg_pq<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_cg_pq<T, 3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          Box<3, 1>::SN * (int)sizeof(double));
+    cudaFuncSetAttribute(k2::tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+    cudaFuncSetAttribute(k2::fdm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
 }
 
 }  // namespace
@@ -956,11 +1586,12 @@ size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg
     const int top = pick_top(s, mg_fp32, &tail_smem);
     const size_t w = mg_fp32 ? 4 : 8;
     const long long N = s.N[0];
-    const long long nblk = (dim == 3) ? tile_blocks<3>(s.n[0]) : tile_blocks<2>(s.n[0]);
+    const long long nblk = (dim == 3) ? tile_blocks<3>(s.n[0]) : k2_blocks(s.n[0]);
     const long long npart = nblk > kMaxPartials ? nblk : kMaxPartials;
     size_t b = 0;
     b += 4 * align256(sizeof(double) * N);                  // r p0 p1 q
-    b += 2 * align256(w * N);                               // z u0pre
+    b += align256(sizeof(double) * N) + align256(w * N);    // z (double-sized: one-level grids), u0pre
+    if (mg_fp32 && s.nlev > 1) b += 5 * align256(sizeof(float) * N);   // r32 e32 p32[2] q32
     b += 3 * align256(sizeof(double) * npart);              // partials
     b += align256(sizeof(double) * PS_NSCAL) + align256(sizeof(int) * PI_NINT) +
          align256(sizeof(unsigned int) * kNumCounters);
@@ -971,6 +1602,10 @@ size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg
     b += align256((mg_fp32 ? sizeof(LvT<float>) : sizeof(LvT<double>)) * s.nlev);
     const long long Nc = s.N[s.nlev - 1];
     b += align256(sizeof(double) * Nc * Nc) + align256(sizeof(float) * Nc * Nc);
+    if (fdm_fits(s, top, dim, mg_fp32)) {
+        const long long nx = s.n[top][0], ny = s.n[top][1];
+        b += align256(sizeof(float) * (nx * nx + ny * ny + nx * ny));
+    }
     if (nlev_out) *nlev_out = s.nlev;
     if (Nc_out) *Nc_out = Nc;
     return b;
@@ -1008,14 +1643,33 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
     pl->rtol = rtol;
     pl->max_iter = max_iter;
     pl->tail_smem = tail_smem;
-    const long long nblk = (dim == 3) ? tile_blocks<3>(s.n[0]) : tile_blocks<2>(s.n[0]);
+    const long long nblk = (dim == 3) ? tile_blocks<3>(s.n[0]) : k2_blocks(s.n[0]);
     pl->npart = (int)(nblk > kMaxPartials ? nblk : kMaxPartials);
     pl->r = (double*)take(sizeof(double) * pl->N);
     pl->p[0] = (double*)take(sizeof(double) * pl->N);
     pl->p[1] = (double*)take(sizeof(double) * pl->N);
     pl->q = (double*)take(sizeof(double) * pl->N);
-    pl->z = take(w * pl->N);
+    pl->z = take(sizeof(double) * pl->N);
     pl->u0pre = take(w * pl->N);
+    // Refinement mode is opt-in (LOWMACH_REFINE=1): on the 256 x 512 slot burner
+    // it needs ~25% more inner iterations than the FP64 CG around the same FP32
+    // multigrid, which costs more than the FP32 Krylov kernels save.
+    const char* rf = std::getenv("LOWMACH_REFINE");
+    const bool refine_mode = mg_fp32 && s.nlev > 1 && (rf && rf[0] == '1');
+    if (refine_mode) {   // refinement mode (a one-level grid is solved exactly in FP64)
+        pl->r32 = (float*)take(sizeof(float) * pl->N);
+        pl->e32 = (float*)take(sizeof(float) * pl->N);
+        pl->p32[0] = (float*)take(sizeof(float) * pl->N);
+        pl->p32[1] = (float*)take(sizeof(float) * pl->N);
+        pl->q32 = (float*)take(sizeof(float) * pl->N);
+        pl->inner_tol = 1e-4;
+        pl->inner_max = 30;
+        // tuning override: LOWMACH_INNER_TOL = relative tolerance of the FP32 inner solve
+        if (const char* e = std::getenv("LOWMACH_INNER_TOL")) {
+            const double v = std::atof(e);
+            if (v > 0.0 && v < 1.0) pl->inner_tol = v;
+        }
+    }
     pl->part0 = (double*)take(sizeof(double) * pl->npart);
     pl->part1 = (double*)take(sizeof(double) * pl->npart);
     pl->part2 = (double*)take(sizeof(double) * pl->npart);
@@ -1046,6 +1700,13 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
     pl->Nc = s.N[s.nlev - 1];
     pl->Minv = (double*)take(sizeof(double) * pl->Nc * pl->Nc);
     pl->Minv_f = (float*)take(sizeof(float) * pl->Nc * pl->Nc);
+    pl->fdm = fdm_fits(s, pl->top, dim, mg_fp32);
+    if (pl->fdm) {
+        // the top level is solved exactly by fast diagonalisation (replaces the tail V-cycle)
+        const int nx = s.n[pl->top][0], ny = s.n[pl->top][1];
+        pl->fdm_tab = (float*)take(sizeof(float) * (nx * nx + ny * ny + nx * ny));
+        pl->fdm_smem = sizeof(float) * (size_t)(2 * nx * nx + 2 * ny * ny + 3 * nx * ny);
+    }
     // tail shared-memory offsets (elements of T)
     {
         int off = 0;
@@ -1068,6 +1729,20 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
     }
     pl->levtab_bytes = lvsz * s.nlev;
     *minv_host = coarse_inverse(pl->lev[s.nlev - 1], dim);
+    if (pl->fdm) {
+        // appended after the coarse inverse: S_x (nx*nx), S_y (ny*ny), IL (ny*nx)
+        const int nx = s.n[pl->top][0], ny = s.n[pl->top][1];
+        std::vector<double> Sx, Sy, lx, ly;
+        eig1d(nx, pl->lev[pl->top].periodic[0], pl->lev[pl->top].h[0], Sx, lx);
+        eig1d(ny, pl->lev[pl->top].periodic[1], pl->lev[pl->top].h[1], Sy, ly);
+        minv_host->insert(minv_host->end(), Sx.begin(), Sx.end());
+        minv_host->insert(minv_host->end(), Sy.begin(), Sy.end());
+        for (int l = 0; l < ny; ++l)
+            for (int k = 0; k < nx; ++k) {
+                const double lam = ly[l] + lx[k];
+                minv_host->push_back(lam > 0.0 ? 1.0 / lam : 0.0);
+            }
+    }
     if (mg_fp32) set_smem_attrs<float>();
     else set_smem_attrs<double>();
     cudaGetLastError();   // attribute calls must not leave a sticky error behind
@@ -1075,17 +1750,28 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
 }
 
 bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& M, cudaStream_t s, const char** err) {
-    if ((long long)M.size() != pl->Nc * pl->Nc) {
+    const size_t nm = (size_t)(pl->Nc * pl->Nc);
+    size_t nf = 0;
+    if (pl->fdm) {
+        const size_t nx = pl->lev[pl->top].n[0], ny = pl->lev[pl->top].n[1];
+        nf = nx * nx + ny * ny + nx * ny;
+    }
+    if (M.size() != nm + nf) {
         *err = "coarse inverse not prepared";
         return false;
     }
     std::vector<float> Mf(M.size());
     for (size_t i = 0; i < M.size(); ++i) Mf[i] = (float)M[i];
-    cudaError_t e = cudaMemcpyAsync(pl->Minv, M.data(), sizeof(double) * M.size(), cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(pl->Minv, M.data(), sizeof(double) * nm, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(pl->Minv_f, Mf.data(), sizeof(float) * Mf.size(), cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(pl->Minv_f, Mf.data(), sizeof(float) * nm, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(pl->levtab, pl->levtab_host, pl->levtab_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && pl->fdm) {
+        const int nx = pl->lev[pl->top].n[0], ny = pl->lev[pl->top].n[1];
+        const float* hp = Mf.data() + nm;
+        e = cudaMemcpyAsync(pl->fdm_tab, hp, sizeof(float) * (nx * nx + ny * ny + nx * ny), cudaMemcpyHostToDevice, s);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->cnt, 0, sizeof(unsigned int) * kNumCounters, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->ictl, 0, sizeof(int) * PI_NINT, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1099,7 +1785,7 @@ bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& M, cudaSt
 // ------------------------------ enqueue -------------------------------------
 namespace {
 
-enum { CNT_UP0 = 0, CNT_PQ = 1, CNT_UPD = 2, CNT_MEANB = 3, CNT_INIT = 4, CNT_MEANX = 5 };
+enum { CNT_UP0 = 0, CNT_PQ = 1, CNT_UPD = 2, CNT_MEANB = 3, CNT_INIT = 4, CNT_MEANX = 5, CNT_REF = 6 };
 
 template <class T>
 const LvT<T>* lv_dev(PoissonPlan* pl) {
@@ -1113,34 +1799,67 @@ LvT<T> lv_host(PoissonPlan* pl, int l) {
     return v;
 }
 
+// Right-hand side of the fine multigrid level: the FP64 CG residual, or the
+// FP32 inner residual in refinement mode.
 template <class T, int DIM>
 void enqueue_down(PoissonPlan* pl, int l, cudaStream_t s) {
     const LvT<T> L = lv_host<T>(pl, l), C = lv_host<T>(pl, l + 1);
-    const dim3 grid = tile_grid<DIM>(pl->lev[l].n);
-    const size_t smem = 2 * Box<DIM, 3>::SN * sizeof(T);
     T* fc = (T*)pl->lev[l + 1].f;
-    if (l == 0)
-        k_mg_down<T, double, DIM><<<grid, Tile<DIM>::NT, smem, s>>>(L, C, pl->r, (T*)pl->u0pre, fc);
-    else
-        k_mg_down<T, T, DIM><<<grid, Tile<DIM>::NT, smem, s>>>(L, C, (const T*)pl->lev[l].f, (T*)pl->lev[l].upre,
-                                                               fc);
+    const bool ir = pl->r32 != nullptr;
+    if (DIM == 2) {
+        const dim3 grid((C.n[0] + k2::CD - 1) / k2::CD, (C.n[1] + k2::CD - 1) / k2::CD);
+        if (l == 0 && ir) k2::down<T, float><<<grid, k2::NT, 0, s>>>(L, C, pl->r32, (T*)pl->u0pre, fc);
+        else if (l == 0) k2::down<T, double><<<grid, k2::NT, 0, s>>>(L, C, pl->r, (T*)pl->u0pre, fc);
+        else k2::down<T, T><<<grid, k2::NT, 0, s>>>(L, C, (const T*)pl->lev[l].f, (T*)pl->lev[l].upre, fc);
+    } else {
+        const dim3 grid = tile_grid<DIM>(pl->lev[l].n);
+        const size_t smem = 2 * Box<DIM, 3>::SN * sizeof(T);
+        if (l == 0 && ir)
+            k_mg_down<T, float, DIM><<<grid, Tile<DIM>::NT, smem, s>>>(L, C, pl->r32, (T*)pl->u0pre, fc);
+        else if (l == 0)
+            k_mg_down<T, double, DIM><<<grid, Tile<DIM>::NT, smem, s>>>(L, C, pl->r, (T*)pl->u0pre, fc);
+        else
+            k_mg_down<T, T, DIM><<<grid, Tile<DIM>::NT, smem, s>>>(L, C, (const T*)pl->lev[l].f,
+                                                                   (T*)pl->lev[l].upre, fc);
+    }
     pl->launches += 1;
 }
 
 template <class T, int DIM>
 void enqueue_up(PoissonPlan* pl, int l, cudaStream_t s) {
     const LvT<T> L = lv_host<T>(pl, l), C = lv_host<T>(pl, l + 1);
-    const dim3 grid = tile_grid<DIM>(pl->lev[l].n);
-    const size_t smem = 2 * Box<DIM, 2>::SN * sizeof(T);
     const T* uc = (const T*)pl->lev[l + 1].upost;
-    if (l == 0)
-        k_mg_up<T, double, DIM, true><<<grid, Tile<DIM>::NT, smem, s>>>(
-            L, C, (const T*)pl->u0pre, pl->r, uc, (T*)pl->z, pl->part0, pl->part1, pl->scal, pl->ictl,
-            pl->cnt + CNT_UP0);
-    else
-        k_mg_up<T, T, DIM, false><<<grid, Tile<DIM>::NT, smem, s>>>(
-            L, C, (const T*)pl->lev[l].upre, (const T*)pl->lev[l].f, uc, (T*)pl->lev[l].upost, nullptr, nullptr,
-            nullptr, nullptr, nullptr);
+    const bool ir = pl->r32 != nullptr;
+    if (DIM == 2) {
+        const dim3 grid((L.n[0] + k2::FU - 1) / k2::FU, (L.n[1] + k2::FU - 1) / k2::FU);
+        if (l == 0 && ir)
+            k2::up<T, float, true><<<grid, k2::NT, 0, s>>>(L, C, (const T*)pl->u0pre, pl->r32, uc, (T*)pl->z,
+                                                           pl->part0, pl->part1, pl->scal, pl->ictl,
+                                                           pl->cnt + CNT_UP0);
+        else if (l == 0)
+            k2::up<T, double, true><<<grid, k2::NT, 0, s>>>(L, C, (const T*)pl->u0pre, pl->r, uc, (T*)pl->z,
+                                                            pl->part0, pl->part1, pl->scal, pl->ictl,
+                                                            pl->cnt + CNT_UP0);
+        else
+            k2::up<T, T, false><<<grid, k2::NT, 0, s>>>(L, C, (const T*)pl->lev[l].upre, (const T*)pl->lev[l].f, uc,
+                                                        (T*)pl->lev[l].upost, nullptr, nullptr, nullptr, nullptr,
+                                                        nullptr);
+    } else {
+        const dim3 grid = tile_grid<DIM>(pl->lev[l].n);
+        const size_t smem = 2 * Box<DIM, 2>::SN * sizeof(T);
+        if (l == 0 && ir)
+            k_mg_up<T, float, DIM, true><<<grid, Tile<DIM>::NT, smem, s>>>(
+                L, C, (const T*)pl->u0pre, pl->r32, uc, (T*)pl->z, pl->part0, pl->part1, pl->scal, pl->ictl,
+                pl->cnt + CNT_UP0);
+        else if (l == 0)
+            k_mg_up<T, double, DIM, true><<<grid, Tile<DIM>::NT, smem, s>>>(
+                L, C, (const T*)pl->u0pre, pl->r, uc, (T*)pl->z, pl->part0, pl->part1, pl->scal, pl->ictl,
+                pl->cnt + CNT_UP0);
+        else
+            k_mg_up<T, T, DIM, false><<<grid, Tile<DIM>::NT, smem, s>>>(
+                L, C, (const T*)pl->lev[l].upre, (const T*)pl->lev[l].f, uc, (T*)pl->lev[l].upost, nullptr, nullptr,
+                nullptr, nullptr, nullptr);
+    }
     pl->launches += 1;
 }
 
@@ -1157,36 +1876,77 @@ void enqueue_tail(PoissonPlan* pl, cudaStream_t s) {
     }
     a.off_r = pl->tail_off_r;
     const T* Minv = (sizeof(T) == 4) ? (const T*)pl->Minv_f : (const T*)pl->Minv;
-    k_mg_tail<T, DIM><<<1, kTailThreads, pl->tail_smem, s>>>(lv_dev<T>(pl), a, (const T*)pl->lev[pl->top].f,
-                                                             (T*)pl->lev[pl->top].upost, Minv);
+    if (DIM == 2 && pl->fdm) {
+        const int nx = pl->lev[pl->top].n[0], ny = pl->lev[pl->top].n[1];
+        k2::fdm<<<1, k2::FT, pl->fdm_smem, s>>>(nx, ny, pl->fdm_tab, (const float*)pl->lev[pl->top].f,
+                                                (float*)pl->lev[pl->top].upost);
+    } else if (DIM == 2)
+        k2::tail<T><<<1, k2::TT, pl->tail_smem, s>>>(lv_dev<T>(pl), a, (const T*)pl->lev[pl->top].f,
+                                                     (T*)pl->lev[pl->top].upost, Minv);
+    else
+        k_mg_tail<T, DIM><<<1, kTailThreads, pl->tail_smem, s>>>(lv_dev<T>(pl), a, (const T*)pl->lev[pl->top].f,
+                                                                 (T*)pl->lev[pl->top].upost, Minv);
     pl->launches += 1;
 }
 
+// CG direction update + operator application: FP64 vectors, or the FP32
+// inner vectors in refinement mode.
 template <class T, int DIM>
 void enqueue_pq(PoissonPlan* pl, cudaStream_t s) {
-    const LvT<double> L = make_lv<double>(pl->lev[0], DIM);
-    const dim3 grid = tile_grid<DIM>(pl->lev[0].n);
-    k_cg_pq<T, DIM><<<grid, Tile<DIM>::NT, Box<DIM, 1>::SN * sizeof(double), s>>>(
-        L, (const T*)pl->z, pl->p[0], pl->p[1], pl->q, pl->part2, pl->scal, pl->ictl, pl->cnt + CNT_PQ);
+    const bool ir = pl->r32 != nullptr;
+    if (DIM == 2) {
+        const dim3 grid((pl->lev[0].n[0] + k2::FP - 1) / k2::FP, (pl->lev[0].n[1] + k2::FP - 1) / k2::FP);
+        if (ir)
+            k2::pq<T, float><<<grid, k2::NT, 0, s>>>(make_lv<float>(pl->lev[0], DIM), (const T*)pl->z, pl->p32[0],
+                                                     pl->p32[1], pl->q32, pl->part2, pl->scal, pl->ictl,
+                                                     pl->cnt + CNT_PQ);
+        else
+            k2::pq<T, double><<<grid, k2::NT, 0, s>>>(make_lv<double>(pl->lev[0], DIM), (const T*)pl->z, pl->p[0],
+                                                      pl->p[1], pl->q, pl->part2, pl->scal, pl->ictl,
+                                                      pl->cnt + CNT_PQ);
+    } else {
+        const dim3 grid = tile_grid<DIM>(pl->lev[0].n);
+        if (ir)
+            k_cg_pq<T, DIM, float><<<grid, Tile<DIM>::NT, Box<DIM, 1>::SN * sizeof(float), s>>>(
+                make_lv<float>(pl->lev[0], DIM), (const T*)pl->z, pl->p32[0], pl->p32[1], pl->q32, pl->part2,
+                pl->scal, pl->ictl, pl->cnt + CNT_PQ);
+        else
+            k_cg_pq<T, DIM, double><<<grid, Tile<DIM>::NT, Box<DIM, 1>::SN * sizeof(double), s>>>(
+                make_lv<double>(pl->lev[0], DIM), (const T*)pl->z, pl->p[0], pl->p[1], pl->q, pl->part2, pl->scal,
+                pl->ictl, pl->cnt + CNT_PQ);
+    }
     pl->launches += 1;
 }
 
 template <class T, int DIM>
 void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle h, int use_graph) {
+    const bool ir = pl->r32 != nullptr;
     if (pl->nlev == 1) {
-        const T* Minv = (sizeof(T) == 4) ? (const T*)pl->Minv_f : (const T*)pl->Minv;
-        k_direct<T><<<1, kTailThreads, 0, s>>>(Minv, (int)pl->Nc, pl->r, (T*)pl->z, pl->scal, pl->ictl);
+        // one-level grid: the preconditioner is the exact coarse solve (FP64)
+        k_direct<double><<<1, kTailThreads, 0, s>>>(pl->Minv, (int)pl->Nc, pl->r, (double*)pl->z, pl->scal,
+                                                    pl->ictl);
         pl->launches += 1;
+        enqueue_pq<double, DIM>(pl, s);
     } else {
         for (int l = 0; l < pl->top; ++l) enqueue_down<T, DIM>(pl, l, s);
         enqueue_tail<T, DIM>(pl, s);
         for (int l = pl->top - 1; l >= 0; --l) enqueue_up<T, DIM>(pl, l, s);
+        enqueue_pq<T, DIM>(pl, s);
     }
-    enqueue_pq<T, DIM>(pl, s);
     const int rb = reduce_blocks(pl->N);
-    k_cg_update<<<rb, NTV, 0, s>>>(x, pl->r, pl->p[0], pl->p[1], pl->q, pl->N, pl->part0, pl->scal, pl->ictl,
-                                   pl->cnt + CNT_UPD, pl->rtol, pl->max_iter, h, use_graph);
-    pl->launches += 1;
+    if (ir) {
+        k_ir_update<<<rb, NTV, 0, s>>>(pl->e32, pl->r32, pl->p32[0], pl->p32[1], pl->q32, pl->N, pl->part0, pl->scal,
+                                       pl->ictl, pl->cnt + CNT_UPD, pl->inner_tol, pl->inner_max, pl->max_iter, h,
+                                       use_graph);
+        k_ir_refine<DIM><<<rb, NTV, 0, s>>>(make_lv<double>(pl->lev[0], DIM), x, pl->r, pl->e32, pl->r32, pl->part1,
+                                            pl->scal, pl->ictl, pl->cnt + CNT_REF, pl->rtol, pl->max_iter, h,
+                                            use_graph);
+        pl->launches += 2;
+    } else {
+        k_cg_update<<<rb, NTV, 0, s>>>(x, pl->r, pl->p[0], pl->p[1], pl->q, pl->N, pl->part0, pl->scal, pl->ictl,
+                                       pl->cnt + CNT_UPD, pl->rtol, pl->max_iter, h, use_graph);
+        pl->launches += 1;
+    }
 }
 
 template <int DIM>
@@ -1195,7 +1955,7 @@ void prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s, cudaG
     const int rb = reduce_blocks(pl->N);
     k_mean<<<rb, NTV, 0, s>>>(b, pl->N, pl->part0, pl->scal, PS_MEANB, pl->cnt + CNT_MEANB);
     const LvT<double> L = make_lv<double>(pl->lev[0], DIM);
-    k_pcg_init<DIM><<<rb, NTV, 0, s>>>(L, b, x, pl->r, pl->part1, pl->part2, pl->scal, pl->ictl,
+    k_pcg_init<DIM><<<rb, NTV, 0, s>>>(L, b, x, pl->r, pl->r32, pl->part1, pl->part2, pl->scal, pl->ictl,
                                        pl->cnt + CNT_INIT, pl->rtol, h, use_graph);
     pl->launches += 2;
 }

@@ -53,9 +53,12 @@ enum : int {
     PS_RELRES = 7,    // sqrt(rr/ff) at exit
     PS_ALPHA = 8,
     PS_MEANX = 9,
+    PS_RR0 = 10,      // ||r||^2 at the start of the current inner solve (refinement mode)
     PS_NSCAL = 16
 };
-enum : int { PI_IT = 0, PI_DONE = 1, PI_NOCONV = 2, PI_ZERO = 3, PI_NINT = 8 };
+// PI_IT: iterations of the current (inner) CG; PI_TOTAL: all inner iterations
+// of the solve; PI_REFINE: an outer refinement step is due (refinement mode).
+enum : int { PI_IT = 0, PI_DONE = 1, PI_NOCONV = 2, PI_ZERO = 3, PI_REFINE = 4, PI_TOTAL = 5, PI_NINT = 8 };
 constexpr int kNumCounters = 8;          // last-block counters (one per reducing kernel kind)
 
 struct PoissonPlan {
@@ -70,6 +73,15 @@ struct PoissonPlan {
     double* q;
     void* z;              // preconditioned residual (T)
     void* u0pre;          // pre-smoothed fine-level correction (T)
+    // Refinement mode (mg_fp32): an FP32 inner PCG on A e = r solved to a
+    // relative inner_tol inside an FP64 iterative-refinement loop
+    // (x += e, r -= A e in FP64, FP64 stopping test).
+    float* r32;           // inner residual
+    float* e32;           // inner solution (correction)
+    float* p32[2];        // inner search direction, double-buffered
+    float* q32;
+    double inner_tol;
+    int inner_max;
     double* part0;        // partial sums (npart entries each)
     double* part1;
     double* part2;
@@ -88,6 +100,11 @@ struct PoissonPlan {
     int launches;         // kernels enqueued by the last enqueue (host-side count)
     size_t levtab_bytes;
     unsigned char levtab_host[kMaxLevels * sizeof(LvT<double>)];   // host copy of levtab
+    // fast-diagonalisation solve of the top coarse level (2D, FP32 multigrid)
+    int fdm;
+    float* fdm_tab;       // S_x (nx x nx, eigenvectors as columns), S_y (ny x ny), inverse
+                          // eigenvalue sums (ny x nx, 0 for the null mode)
+    size_t fdm_smem;
 };
 
 // Workspace bytes for a grid (no allocation).
@@ -95,7 +112,9 @@ size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg
                           long long* Nc_out, const char** err);
 
 // Carve a plan out of ws (256-byte aligned, >= poisson_plan_bytes) and compute
-// the coarsest-level inverse and the level tables on the host.
+// the coarsest-level inverse and the level tables on the host; minv_host gets
+// the coarse inverse followed (fast-diagonalisation plans) by S_x, S_y and the
+// inverse eigenvalue sums.
 bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[3], const int periodic[3],
                        int mg_fp32, double rtol, int max_iter, void* ws, size_t ws_bytes,
                        std::vector<double>* minv_host, const char** err);

@@ -136,6 +136,13 @@ Phys make_phys(const sim_params_t* p) {
     ph.Le_O = p->Le_O;
     ph.N_F = (1.0 - p->Le_F) / (ph.S * p->Le_F);
     ph.N_O = (p->Le_O - 1.0) / p->Le_O;
+    ph.cA = -(ph.S + 1.0) / (2.0 * ph.S * ph.k);                 // Eq 3.41 folded into Eq 3.42
+    ph.cB = (ph.S - 1.0) / (2.0 * ph.S);
+    ph.cT = ph.Q / (ph.S + 1.0);
+    ph.iPe = 1.0 / ph.Pe;
+    ph.iLePe = 1.0 / (p->Le_O * ph.Pe);
+    ph.mixed = (p->precision == SIM_MIXED);
+    ph.sigma_is_07 = (p->sigma == 0.7);
     ph.sigma = p->sigma;
     ph.inv_Fr2 = p->inv_Fr2;
     for (int d = 0; d < 3; ++d) ph.inflow_v[d] = p->inflow_v[d];
@@ -463,6 +470,8 @@ cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int
     a.p0a = SC_P0_N;
     a.p0b = SC_P0_NM1;
     a.p0c = SC_P0_NM2;
+    a.T = s->T;              // T^n
+    a.p0r = SC_P0_N;
     if (n == 0) {
         a.wden = 0.0;
     } else if (n == 1) {
@@ -470,6 +479,7 @@ cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int
     } else {
         a.w0 = 3.0; a.w1 = -4.0; a.w2 = 1.0; a.wden = 2.0 * dt;
     }
+    a.iwden = (a.wden != 0.0) ? 1.0 / a.wden : 0.0;
     launch_residual(g, s->ph, a, st, L);
     ghost(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}}, st, L);
     launch_state(g, s->ph, s->Zs, s->Hs, s->T, r.rho_new, s->kap, s->sc, SC_P0_STAR, s->part, s->status, st, L);
@@ -507,6 +517,9 @@ cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int
     }
     pa.P = s->P;
     pa.rho = r.rho_new;
+    pa.T = s->T;             // T*
+    pa.sc = s->sc;
+    pa.p0_slot = SC_P0_STAR;
     pa.eA = s->eA;
     pa.eB = s->eB;
     pa.eC = s->eC;
@@ -535,11 +548,14 @@ cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int
     c.p0a = SC_P0_STAR;
     c.p0b = SC_P0_N;
     c.p0c = SC_P0_NM1;
+    c.T = s->T;              // T*
+    c.p0r = SC_P0_STAR;
     if (n == 0) {
         c.w0 = 1.0; c.w1 = -1.0; c.w2 = 0.0; c.wden = dt;
     } else {
         c.w0 = 3.0; c.w1 = -4.0; c.w2 = 1.0; c.wden = 2.0 * dt;
     }
+    c.iwden = 1.0 / c.wden;
     launch_residual(g, s->ph, c, st, L);
     ghost(s, {{s->Z, GW_Z}, {s->H, GW_H}}, st, L);
     launch_state(g, s->ph, s->Z, s->H, s->T, r.rho_new, s->kap, s->sc, SC_P0_NEW, s->part, s->status, st, L);
@@ -549,6 +565,7 @@ cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int
     e = enqueue_poisson(s, st, graph, SC_ITERS_CORR, L, body);
     if (e != cudaSuccess) return e;
     for (int d = 0; d < D; ++d) pa.v[d] = s->v[d];
+    pa.p0_slot = SC_P0_NEW;  // T^{n+1}, p0^{n+1}
     launch_project(g, pa, st, L);
     ghost_v(s, s->v, st, L);
     launch_rotate_p0(s->sc, st, L);
@@ -921,7 +938,10 @@ sim_status sim_time_kernel(sim_t* s, int kernel, int reps) {
                 a.p0a = SC_P0_N;
                 a.p0b = SC_P0_NM1;
                 a.p0c = SC_P0_NM2;
+                a.T = s->T;
+                a.p0r = SC_P0_N;
                 a.w0 = 3.0; a.w1 = -4.0; a.w2 = 1.0; a.wden = 2.0 * s->prm.dt;
+                a.iwden = 1.0 / a.wden;
                 launch_residual(g, s->ph, a, s->stream, &L);
                 break;
             }
@@ -947,6 +967,9 @@ sim_status sim_time_kernel(sim_t* s, int kernel, int reps) {
                 }
                 pa.P = s->pp.q;          // Krylov scratch as the pressure argument
                 pa.rho = r.rho_n;
+                pa.T = s->T;
+                pa.sc = s->sc;
+                pa.p0_slot = SC_P0_N;
                 pa.eA = s->eA;
                 pa.eB = s->eB;
                 pa.eC = s->eC;

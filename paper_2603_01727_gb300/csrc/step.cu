@@ -90,12 +90,51 @@ __global__ void k_ghost(Geom g, Phys ph, const uint8_t* __restrict__ klo, const 
 __device__ __forceinline__ double temperature(const Phys& ph, double z, double h) {
     const double x = ph.k * (z - 1.0);
     const double ax = fabs(x);
-    // ln cosh x + ln 2 = |x| + log1p(exp(-2|x|)): Eq 3.41 minus its level shift
-    const double F = (-(ph.S + 1.0) * (ax + log1p(exp(-2.0 * ax))) / ph.k + (ph.S - 1.0) * (z - 1.0)) /
-                     (2.0 * ph.S);
-    return ph.Q / (ph.S + 1.0) * (F + h);
+    // ln cosh x + ln 2 = |x| + log1p(exp(-2|x|)): Eq 3.41 minus its level shift,
+    // with the constant factors folded: T = cT (cA (|x| + L) + cB (Z - 1) + H)
+    return ph.cT * (ph.cA * (ax + log1p(exp(-2.0 * ax))) + ph.cB * (z - 1.0) + h);
 }
 
+// Mixed precision: the bounded term L = log1p(exp(-2|x|)), x = k (Z - 1), is
+// evaluated in FP64 inside the stoichiometric band |x| < kStoichBand and in
+// FP32 outside it, where L < 2.3e-6 and its FP32 rounding (< 1.4e-13 in T) stays
+// far below what the BDF density rate (which divides T differences by dt)
+// would amplify into the pressure.  The affine part, whose cancellation (F + H
+// is ~18x smaller than F in air) needs FP64, is FP64 everywhere.
+constexpr double kStoichBand = 6.5;
+
+__device__ __forceinline__ double temperature_mixed(const Phys& ph, double z, double h) {
+    const double ax = fabs(ph.k * (z - 1.0));
+    double L;
+    if (ax < kStoichBand) L = log1p(exp(-2.0 * ax));
+    else L = (double)log1pf(expf(-2.0f * (float)ax));
+    return ph.cT * (ph.cA * (ax + L) + ph.cB * (z - 1.0) + h);
+}
+
+// 1/T to FP64 accuracy from an FP32 reciprocal and one Newton step
+// (y <- y + y (1 - T y) doubles the ~24 correct bits).
+__device__ __forceinline__ double recip_newton(double T) {
+    const double y = (double)(1.0f / (float)T);
+    return fma(y, fma(-T, y, 1.0), y);
+}
+
+// kappa = T^sigma (Eq 2.50) in the mixed path.  For the paper's sigma = 7/10:
+// y0 = powf(T, 0.7) (FP32), then with delta = T^7 / y0^10 - 1 (~1e-7) the exact
+// y = y0 (1 + delta)^(1/10) = y0 (1 + delta/10 - 0.045 delta^2 + O(delta^3)),
+// evaluated in FP64 (T^7 and y0^10 by repeated squaring, the quotient through
+// a Newton-refined reciprocal): FP64-accurate kappa without an FP64 pow, so
+// kappa carries no FP32 rounding noise into the diffusion-flux differences.
+// Other exponents use the FP64 pow.
+__device__ __forceinline__ double kappa_mixed(const Phys& ph, double T) {
+    if (!ph.sigma_is_07) return pow(T, ph.sigma);
+    const double y0 = (double)powf((float)T, 0.7f);
+    const double T2 = T * T, T4 = T2 * T2, T7 = T4 * T2 * T;
+    const double y2 = y0 * y0, y4 = y2 * y2, y8 = y4 * y4, y10 = y8 * y2;
+    const double delta = fma(T7, recip_newton(y10), -1.0);
+    return fma(y0, delta * fma(-0.045, delta, 0.1), y0);
+}
+
+template <bool MIXED>
 __global__ void k_state(Geom g, Phys ph, const double* __restrict__ Z, const double* __restrict__ H,
                         double* __restrict__ T, double* __restrict__ rho, double* __restrict__ kap,
                         double* __restrict__ part, int* status, double* sc, int p0_slot) {
@@ -104,170 +143,200 @@ __global__ void k_state(Geom g, Phys ph, const double* __restrict__ Z, const dou
     int bad = 0;
     for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
         const long long c = pad_index(g, t);
-        double Tv, kv;
+        double Tv, kv, iT;
         if (ph.incompressible) {
             Tv = 1.0;
             kv = 1.0;
+            iT = 1.0;
+        } else if (MIXED) {
+            Tv = temperature_mixed(ph, Z[c], H[c]);
+            kv = kappa_mixed(ph, Tv);
+            iT = recip_newton(Tv);
         } else {
             Tv = temperature(ph, Z[c], H[c]);
             kv = pow(Tv, ph.sigma);
+            iT = 1.0 / Tv;
         }
         T[c] = Tv;
         kap[c] = kv;
-        if (!ph.closed) rho[c] = ph.incompressible ? 1.0 : 1.0 / Tv;
-        acc += 1.0 / Tv;
+        if (!ph.closed) rho[c] = iT;        // p0 = 1 (Eq 2.41), rho = p0 / T (Eq 2.49)
+        acc += iT;
         if (!(Tv > 0.0) || !(Tv < 1e300)) bad = 1;
     }
     if (bad) atomicOr(status, ST_NAN);
     acc = block_sum<NT>(acc, sm);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && !ph.closed) sc[p0_slot] = 1.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !ph.closed) {
+        sc[p0_slot] = 1.0;
+        sc[p0_slot + SC_INV_OFF] = 1.0;
+    }
 }
 
 // Enclosed system: p0 = m / (sum(1/T) dV) (Eq 2.40), rho = p0 / T (Eq 2.49).
 __global__ void k_density(Geom g, const double* __restrict__ T, double* __restrict__ rho,
-                          const double* __restrict__ part, int np, double* sc, int p0_slot) {
+                          const double* __restrict__ part, int np, double* sc, int p0_slot, int mixed) {
     __shared__ double sm[NT / 32];
     const double s = sum_partials<NT>(part, np, sm);
     const double p0 = sc[SC_MASS] / (s * g.dV);
     for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
         const long long c = pad_index(g, t);
-        rho[c] = p0 / T[c];
+        rho[c] = mixed ? p0 * recip_newton(T[c]) : p0 / T[c];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc[p0_slot] = p0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc[p0_slot] = p0;
+        sc[p0_slot + SC_INV_OFF] = 1.0 / p0;
+    }
 }
 
 // ----------------------------------------------------------------------------
 // Residuals at one level and the AB2 / AM2 combination (Eqs 3.1-3.4, 3.7-3.8,
 // 3.10, 3.12-3.13, 3.16, 3.18; convection Eq 3.26; penalisation Eqs 3.30-3.32).
 // ----------------------------------------------------------------------------
-template <int DIM>
+// C is the arithmetic type of the residual terms and of the stored residual
+// history (double in both precision modes, see launch_residual); the state
+// updates X = X_b + dt * combination are FP64.
+template <int DIM, class C>
 __global__ void __launch_bounds__(NT) k_residual(Geom g, Phys ph, ResidArgs a) {
     const long long t = (long long)blockIdx.x * NT + threadIdx.x;
     if (t >= g.ncell) return;
     const long long c = pad_index(g, t);
-    int ct[3];
-    interior_coords(g, t, ct);
-    (void)ct;
+    const C* Rrd[5];
+    C* Rst[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        Rrd[k] = reinterpret_cast<const C*>(a.Rrd[k]);
+        Rst[k] = reinterpret_cast<C*>(a.Rst[k]);
+    }
 
     // dp0/dt for the H source (Eqs 3.5, 3.14)
-    const double p0dot =
-        (a.wden != 0.0) ? (a.w0 * a.sc[a.p0a] + a.w1 * a.sc[a.p0b] + a.w2 * a.sc[a.p0c]) / a.wden : 0.0;
-
-    const double rho_c = a.rho[c];
-    const double kap_c = a.kap[c];
-    const double Zc = a.Z[c], Hc = a.H[c];
+    const double p0dot = (a.wden != 0.0) ? (a.w0 * a.sc[a.p0a] + a.w1 * a.sc[a.p0b] + a.w2 * a.sc[a.p0c]) * a.iwden
+                                         : 0.0;
+    const C half = (C)0.5;
+    const C rho_c = (C)a.rho[c];
+    const C kap_c = (C)a.kap[c];
+    const C Zc = (C)a.Z[c], Hc = (C)a.H[c];
 
     // scalar convection (Eq 3.26b) and diffusion div(kappa grad .)
-    double convZ = 0.0, convH = 0.0, difZ = 0.0, difH = 0.0;
-    double kf_lo[DIM], kf_hi[DIM];
+    C convZ = 0, convH = 0, difZ = 0, difH = 0;
+    C kf_lo[DIM], kf_hi[DIM];
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
         const long long s = g.s[j];
-        const double ih = g.ih[j];
-        const double Flo = a.F[j][c], Fhi = a.F[j][c + s];
-        kf_lo[j] = 0.5 * (a.kap[c - s] + kap_c);
-        kf_hi[j] = 0.5 * (kap_c + a.kap[c + s]);
-        const double dZlo = (Zc - a.Z[c - s]) * ih, dZhi = (a.Z[c + s] - Zc) * ih;
-        const double dHlo = (Hc - a.H[c - s]) * ih, dHhi = (a.H[c + s] - Hc) * ih;
-        convZ += 0.5 * (Flo * dZlo + Fhi * dZhi);
-        convH += 0.5 * (Flo * dHlo + Fhi * dHhi);
+        const C ih = (C)g.ih[j];
+        const C Flo = (C)a.F[j][c], Fhi = (C)a.F[j][c + s];
+        kf_lo[j] = half * ((C)a.kap[c - s] + kap_c);
+        kf_hi[j] = half * (kap_c + (C)a.kap[c + s]);
+        const C dZlo = (Zc - (C)a.Z[c - s]) * ih, dZhi = ((C)a.Z[c + s] - Zc) * ih;
+        const C dHlo = (Hc - (C)a.H[c - s]) * ih, dHhi = ((C)a.H[c + s] - Hc) * ih;
+        convZ += half * (Flo * dZlo + Fhi * dZhi);
+        convH += half * (Flo * dHlo + Fhi * dHhi);
         difZ += (kf_hi[j] * dZhi - kf_lo[j] * dZlo) * ih;
         difH += (kf_hi[j] * dHhi - kf_lo[j] * dHlo) * ih;
     }
 
     // momentum: convection Eq 3.26a, viscous stress Eq 2.46 on the interfaces
-    double Rv[DIM];
+    const C two3 = (C)(2.0 / 3.0);
+    C Rv[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
         const double* vi = a.v[i];
-        double conv = 0.0, visc = 0.0;
+        C conv = 0, visc = 0;
 #pragma unroll
         for (int j = 0; j < DIM; ++j) {
             const long long s = g.s[j];
-            const double ih = g.ih[j];
-            const double Flo = a.F[j][c], Fhi = a.F[j][c + s];
-            conv += (Fhi * (0.5 * (vi[c] + vi[c + s])) - Flo * (0.5 * (vi[c - s] + vi[c]))) * ih;
-            double tau_f[2];
+            const C ih = (C)g.ih[j];
+            const C Flo = (C)a.F[j][c], Fhi = (C)a.F[j][c + s];
+            const C vl = (C)vi[c - s], vc = (C)vi[c], vh = (C)vi[c + s];
+            conv += (Fhi * (half * (vc + vh)) - Flo * (half * (vl + vc))) * ih;
+            C tau_f[2];
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
                 const long long ca = side ? c : c - s;   // cell below the interface
                 const long long cb = ca + s;             // cell above
-                const double kf = side ? kf_hi[j] : kf_lo[j];
-                const double dvi = (vi[cb] - vi[ca]) * ih;
-                double dvj;
+                const C kf = side ? kf_hi[j] : kf_lo[j];
+                const C dvi = (side ? (vh - vc) : (vc - vl)) * ih;
+                C dvj;
                 if (i == j) {
                     dvj = dvi;
                 } else {
                     const long long si = g.s[i];
                     const double* vj = a.v[j];
-                    const double da = (vj[ca + si] - vj[ca - si]) * (0.5 * g.ih[i]);
-                    const double db = (vj[cb + si] - vj[cb - si]) * (0.5 * g.ih[i]);
-                    dvj = 0.5 * (da + db);
+                    const C hi2 = (C)(0.5 * g.ih[i]);
+                    const C da = ((C)vj[ca + si] - (C)vj[ca - si]) * hi2;
+                    const C db = ((C)vj[cb + si] - (C)vj[cb - si]) * hi2;
+                    dvj = half * (da + db);
                 }
-                double tau = kf * (dvi + dvj);
+                C tau = kf * (dvi + dvj);
                 if (i == j) {
-                    double div = (a.v[j][cb] - a.v[j][ca]) * ih;
+                    C div = dvi;
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) {
                         if (k == j) continue;
                         const long long sk = g.s[k];
                         const double* vk = a.v[k];
-                        const double da = (vk[ca + sk] - vk[ca - sk]) * (0.5 * g.ih[k]);
-                        const double db = (vk[cb + sk] - vk[cb - sk]) * (0.5 * g.ih[k]);
-                        div = div + 0.5 * (da + db);
+                        const C hk2 = (C)(0.5 * g.ih[k]);
+                        const C da = ((C)vk[ca + sk] - (C)vk[ca - sk]) * hk2;
+                        const C db = ((C)vk[cb + sk] - (C)vk[cb - sk]) * hk2;
+                        div = div + half * (da + db);
                     }
-                    tau = tau - (2.0 / 3.0) * kf * div;
+                    tau = tau - two3 * kf * div;
                 }
                 tau_f[side] = tau;
             }
             visc += (tau_f[1] - tau_f[0]) * ih;
         }
-        double R = -conv + ph.PrPe * visc;
-        if (i == 1 && ph.inv_Fr2 != 0.0) R = R + ph.inv_Fr2 * (1.0 - rho_c);          // Eq 3.8b
-        if (a.ibm && a.chi[c]) R = R - ph.PrPe * a.inv_Da * kap_c * (vi[c] - a.vib[i][c]);  // Eq 3.30
+        C R = -conv + (C)ph.PrPe * visc;
+        if (i == 1 && ph.inv_Fr2 != 0.0) R = R + (C)ph.inv_Fr2 * ((C)1 - rho_c);              // Eq 3.8b
+        if (a.ibm && a.chi[c])
+            R = R - (C)(ph.PrPe * a.inv_Da) * kap_c * ((C)vi[c] - (C)a.vib[i][c]);           // Eq 3.30
         Rv[i] = R;
     }
 
     // Lewis and N coefficients (Eq 3.35)
-    double Le = ph.Le_O, Nn = ph.N_O;
+    C iLePe = (C)ph.iLePe, Nn = (C)ph.N_O;
     if (ph.Le_F != ph.Le_O) {
-        const double th = 0.5 * (1.0 + tanh(ph.k * (Zc - 1.0)));
-        Le = (ph.Le_F - ph.Le_O) * th + ph.Le_O;
-        Nn = (ph.N_F - ph.N_O) * th + ph.N_O;
+        const C th = half * ((C)1 + (C)tanh(ph.k * ((double)Zc - 1.0)));
+        const C Le = (C)(ph.Le_F - ph.Le_O) * th + (C)ph.Le_O;
+        Nn = (C)(ph.N_F - ph.N_O) * th + (C)ph.N_O;
+        iLePe = (C)1 / (Le * (C)ph.Pe);
     }
-    const double Pe = ph.Pe;
-    double bZ = -convZ + difZ / (Le * Pe);
-    double bH = -convH + difH / Pe + ph.zeta * p0dot + Nn * difZ / Pe;
+    const C iPe = (C)ph.iPe;
+    C bZ = -convZ + difZ * iLePe;
+    C bH = -convH + difH * iPe + (C)(ph.zeta * p0dot) + Nn * difZ * iPe;
     if (a.ibm && a.chi[c]) {
-        bZ = bZ - kap_c * (Zc - a.Z_ib) / (Le * Pe) * a.inv_Da;                 // Eq 3.31
-        bH = bH - kap_c * (Hc - a.H_ib) / Pe * a.inv_Da;                         // Eq 3.32
+        const C iDa = (C)a.inv_Da;
+        bZ = bZ - kap_c * (Zc - (C)a.Z_ib) * iLePe * iDa;                                   // Eq 3.31
+        bH = bH - kap_c * (Hc - (C)a.H_ib) * iPe * iDa;                                     // Eq 3.32
     }
-    const double RZ = bZ / rho_c;
-    const double RH = bH / rho_c;
+    // 1/rho = T / p0 (Eq 2.49)
+    const C irho = (C)(a.T[c] * a.sc[a.p0r + SC_INV_OFF]);
+    const C RZ = bZ * irho;
+    const C RH = bH * irho;
 
-    // combination
+    // combination (FP64 state update)
     const double dt = a.dt;
     const double rb = a.rhob[c];
     if (a.mode == MODE_CORR) {
+        const double hdt = 0.5 * dt;
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) a.mo[i][c] = rb * a.vb[i][c] + 0.5 * dt * (Rv[i] + a.Rrd[i][c]);
-        a.Zo[c] = a.Zb[c] + 0.5 * dt * (RZ + a.Rrd[3][c]);
-        a.Ho[c] = a.Hb[c] + 0.5 * dt * (RH + a.Rrd[4][c]);
+        for (int i = 0; i < DIM; ++i) a.mo[i][c] = fma(hdt, (double)(Rv[i] + Rrd[i][c]), rb * a.vb[i][c]);
+        a.Zo[c] = fma(hdt, (double)(RZ + Rrd[3][c]), a.Zb[c]);
+        a.Ho[c] = fma(hdt, (double)(RH + Rrd[4][c]), a.Hb[c]);
     } else {
         const bool ab2 = (a.mode == MODE_PRED_AB2);
+        const C c15 = (C)1.5;
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
-            const double cv = ab2 ? (1.5 * Rv[i] - 0.5 * a.Rrd[i][c]) : Rv[i];
-            a.Rst[i][c] = Rv[i];
-            a.mo[i][c] = rb * a.vb[i][c] + dt * cv;
+            const C cv = ab2 ? (c15 * Rv[i] - half * Rrd[i][c]) : Rv[i];
+            Rst[i][c] = Rv[i];
+            a.mo[i][c] = fma(dt, (double)cv, rb * a.vb[i][c]);
         }
-        const double cZ = ab2 ? (1.5 * RZ - 0.5 * a.Rrd[3][c]) : RZ;
-        const double cH = ab2 ? (1.5 * RH - 0.5 * a.Rrd[4][c]) : RH;
-        a.Rst[3][c] = RZ;
-        a.Rst[4][c] = RH;
-        a.Zo[c] = a.Zb[c] + dt * cZ;
-        a.Ho[c] = a.Hb[c] + dt * cH;
+        const C cZ = ab2 ? (c15 * RZ - half * Rrd[3][c]) : RZ;
+        const C cH = ab2 ? (c15 * RH - half * Rrd[4][c]) : RH;
+        Rst[3][c] = RZ;
+        Rst[4][c] = RH;
+        a.Zo[c] = fma(dt, (double)cZ, a.Zb[c]);
+        a.Ho[c] = fma(dt, (double)cH, a.Hb[c]);
     }
 }
 
@@ -367,7 +436,7 @@ __global__ void k_project(Geom g, ProjArgs a) {
     int ct[3];
     interior_coords(g, t, ct);
     const double Pc = a.P[t];
-    const double rho = a.rho[c];
+    const double irho = a.T[c] * a.sc[a.p0_slot + SC_INV_OFF];   // 1/rho = T / p0 (Eq 2.49)
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
         const long long s = g.s[j];
@@ -383,7 +452,7 @@ __global__ void k_project(Geom g, ProjArgs a) {
         else Pp = a.eA * Pc + a.eB * a.P[t - st] + a.eC * a.P[t - 2 * st];
         if (ct[j] > 0 || g.periodic[j]) a.F[j][c] = a.F[j][c] - (Pc - Pm) * ih;
         if (ct[j] == n - 1 && g.periodic[j]) a.F[j][c + s] = a.F[j][c + s] - (Pp - Pc) * ih;
-        a.v[j][c] = (a.mom[j][c] - (Pp - Pm) / (2.0 * g.h[j])) / rho;
+        a.v[j][c] = (a.mom[j][c] - (Pp - Pm) * (0.5 * ih)) * irho;
     }
 }
 
@@ -417,6 +486,9 @@ __global__ void k_rotate_p0(double* sc) {
     sc[SC_P0_NM2] = sc[SC_P0_NM1];
     sc[SC_P0_NM1] = sc[SC_P0_N];
     sc[SC_P0_N] = sc[SC_P0_NEW];
+    sc[SC_P0_NM2 + SC_INV_OFF] = sc[SC_P0_NM1 + SC_INV_OFF];
+    sc[SC_P0_NM1 + SC_INV_OFF] = sc[SC_P0_N + SC_INV_OFF];
+    sc[SC_P0_N + SC_INV_OFF] = sc[SC_P0_NEW + SC_INV_OFF];
 }
 
 __global__ void k_copy_scalar(const double* src, double* dst, int n) {
@@ -585,19 +657,23 @@ void launch_state(const Geom& g, const Phys& ph, const double* Z, const double* 
                   double* kap, double* sc, int p0_slot, double* part, int* status, cudaStream_t s,
                   int* launches) {
     const int rb = reduce_grid(g);
-    k_state<<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, part, status, sc, p0_slot);
+    if (ph.mixed)
+        k_state<true><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, part, status, sc, p0_slot);
+    else
+        k_state<false><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, part, status, sc, p0_slot);
     ++*launches;
     if (ph.closed) {
-        k_density<<<rb, NT, 0, s>>>(g, T, rho, part, rb, sc, p0_slot);
+        k_density<<<rb, NT, 0, s>>>(g, T, rho, part, rb, sc, p0_slot, ph.mixed);
         ++*launches;
     }
 }
 
 void launch_residual(const Geom& g, const Phys& ph, const ResidArgs& a, cudaStream_t s, int* launches) {
-    if (g.dim == 3)
-        k_residual<3><<<blocks_for(g.ncell), NT, 0, s>>>(g, ph, a);
-    else
-        k_residual<2><<<blocks_for(g.ncell), NT, 0, s>>>(g, ph, a);
+    const int nb = blocks_for(g.ncell);
+    // FP64 in both precision modes: the pressure is the dt-scaled divergence of
+    // the momentum increment and inherits its relative rounding directly
+    if (g.dim == 3) k_residual<3, double><<<nb, NT, 0, s>>>(g, ph, a);
+    else k_residual<2, double><<<nb, NT, 0, s>>>(g, ph, a);
     ++*launches;
 }
 

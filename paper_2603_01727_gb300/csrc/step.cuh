@@ -14,6 +14,7 @@ enum : int {
     SC_P0_N = 0, SC_P0_NM1 = 1, SC_P0_NM2 = 2, SC_P0_STAR = 3, SC_P0_NEW = 4,
     SC_MASS = 5, SC_OUT_AREA = 6,
     SC_ITERS_PRED = 8, SC_RELRES_PRED = 9, SC_ITERS_CORR = 10, SC_RELRES_CORR = 11,
+    SC_INV_OFF = 16,      // slot p0_slot + SC_INV_OFF holds 1 / p0 of that slot (slots 16..20)
     SC_NSCAL = 32
 };
 // Device status bits (int word).
@@ -48,8 +49,10 @@ struct ResidArgs {
     const double* Hb;
     const double* rhob;
     const double* vb[3];
-    double* Rst[5];          // stored residuals (v0, v1, v2, Z, H)
-    const double* Rrd[5];    // previous (AB2) or level-n (corrector) residuals
+    void* Rst[5];            // stored residuals (v0, v1, v2, Z, H), of the kernel's arithmetic type
+    const void* Rrd[5];      // previous (AB2) or level-n (corrector) residuals
+    const double* T;         // temperature of the residual's level (1/rho = T / p0)
+    int p0r;                 // p0 slot of the residual's level
     double* Zo;
     double* Ho;
     double* mo[3];
@@ -60,6 +63,7 @@ struct ResidArgs {
     const double* sc;
     int p0a, p0b, p0c;
     double w0, w1, w2, wden;  // dp0/dt = (w0 sc[a] + w1 sc[b] + w2 sc[c]) / wden (wden = 0: zero)
+    double iwden;             // 1 / wden
     int mode;
     double dt;
 };
@@ -84,6 +88,9 @@ struct ProjArgs {
     const double* P;         // compact
     const double* mom[3];
     const double* rho;
+    const double* T;         // temperature of the stage (1/rho = T / p0)
+    const double* sc;
+    int p0_slot;
     double* v[3];
     double eA, eB, eC;       // quadratic extrapolation coefficients (Eq 3.28)
 };

@@ -171,26 +171,30 @@ def test_slot_burner_full_size_timing_tolerance():
 
 
 # ---------------------------------------------------------------------------
-# Mixed precision: FP32 multigrid preconditioner inside the FP64 CG.  The CG
-# residual and its stopping test stay FP64, so the converged fields keep the
-# FP64 parity bound.
+# Mixed precision (FP32 stencil arithmetic and multigrid; FP64 state, CG
+# residual and stopping test, FP64 affine part of the state relation): every
+# field within a stated relative error of the FP64 oracle.
 # ---------------------------------------------------------------------------
+MIXED_TOL = 1e-6
+
+
 @pytest.mark.parametrize("case", ["blobs", "slot", "sphere"])
-def test_mixed_multigrid_keeps_fp64_parity(case):
+def test_mixed_precision_error_against_oracle(case):
     if case == "blobs":
         prm, geo, f = W.periodic_blobs(64)
-        steps = 30
+        steps = 100
     elif case == "slot":
         prm, geo, f = W.slot_burner(64, 128)
-        steps = 20
+        steps = 50
     else:
         prm, geo, f = W.sphere_burner(24)
-        steps = 6
+        steps = 10
     prm["poisson_rtol"] = 1e-12
     prm["precision"] = W.MIXED
     pb, st = oracle_run(prm, geo, f, steps)
     sim = gpu_run(prm, geo, f, steps)
-    compare(sim, oracle_fields(pb, st), 1e-9)
+    worst = compare(sim, oracle_fields(pb, st), MIXED_TOL)
+    print(case, {k: f"{v:.2e}" for k, v in worst.items()})
 
 
 # ---------------------------------------------------------------------------
