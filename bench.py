@@ -209,11 +209,9 @@ def kernel_models(prm, mixed):
     m["residual"] = dict(id=0, bytes=(reads + writes) * N * 8.0, flops=N * (60.0 * dim * dim))
     m["state"] = dict(id=4, bytes=5 * N * 8.0, flops=N * 40.0)
     m["project"] = dict(id=5, bytes=(1 + 2 * dim + 1 + dim) * N * 8.0, flops=N * 8.0 * dim)
-    # coarse levels (one block): right-hand side in, correction out; with the
-    # fast-diagonalisation solve (2D mixed) four dense products of the top level
-    nt = N / 4 ** 3 if dim == 2 else N / 8 ** 3
-    side = nt ** 0.5 if dim == 2 else nt ** (1.0 / 3.0)
-    m["mg_tail"] = dict(id=6, bytes=2 * nt * w, flops=2.0 * nt * 4 * 1.5 * side)
+    # coarse levels in one block: right-hand side in, correction out; the tail
+    # shape is filled in from the library (tail_model)
+    m["mg_tail"] = dict(id=6, bytes=0.0, flops=0.0, one_sm=True)
     return m
 
 
@@ -318,6 +316,23 @@ def e2e_gpu(args, precision, res, device):
             "d2h_bytes_per_step": nbytes, "steps": K}
 
 
+def tail_model(sim, mixed, sweeps=2):
+    """Bytes and flops of one coarse-level launch: fast diagonalisation is four
+    dense products of the top level (nx*ny*(nx+ny) multiply-adds each pair);
+    the shared-memory V-cycle is ~(4 sweeps + residual + transfers) x 10 flops
+    per cell over the levels (4/3 of the top level in 2D)."""
+    nx, ny = sim.query(12), sim.query(13)
+    nt = nx * ny
+    w = 4.0 if mixed else 8.0
+    if sim.query(14) > 0:
+        flops = 2.0 * 2.0 * nt * (nx + ny)
+        table = 4.0 * (2 * nx * nx + 2 * ny * ny + nt)
+    else:
+        flops = (4 * sweeps + 4) * 10.0 * nt * 4.0 / 3.0
+        table = 0.0
+    return dict(bytes=2 * nt * w + table, flops=flops)
+
+
 def roofline(res, peaks, precision):
     """Roofline entry of the kernel with the largest share of the step."""
     share = {}
@@ -328,14 +343,26 @@ def roofline(res, peaks, precision):
                 "project": 2}
     for k, t in res["ktimes"].items():
         share[k] = t * per_step[k] / (res["ms_per_step"] * 1e-3)
-    top = max((k for k in share if res["models"][k]["bytes"] > 0), key=share.get)
+    res["models"]["mg_tail"].update(tail_model(res["sim"], precision == "mixed"))
+    top = max(share, key=share.get)
     t = res["ktimes"][top]
     m = res["models"][top]
     hbm = peaks.get("hbm_gbs", 6800.0)
     gbs = m["bytes"] / t / 1e9
     fp64_tflops = FP64_PEAK_TFLOPS
     tfl = m["flops"] / t / 1e12
-    fp64_kernel = (precision == "fp64") or top in ("cg_matvec", "residual", "state", "project")
+    fp64_kernel = (precision == "fp64") or top in ("residual", "state", "project")
+    if m.get("one_sm"):
+        # one thread block by design: the ceiling is one SM's ALU rate
+        if fp64_kernel:
+            pk, unit, src = FP64_PEAK_TFLOPS / 152, "TFLOP/s (fp64, one SM)", "GB300 FP64 rate / 152 SMs"
+        else:
+            pk, unit, src = FP32_PEAK_TFLOPS / 152, "TFLOP/s (fp32, one SM)", \
+                "one SM: 128 FP32 FMA/clk x 2 x 2.07 GHz"
+        rl = {"bound": "alu", "achieved": tfl, "peak": pk, "unit": unit, "frac": tfl / pk}
+        rl.update(kernel=top, launch_us=t * 1e6, share_of_step=share[top], traffic=None, peak_source=src,
+                  shares={k: round(v, 4) for k, v in share.items()}, nlev=nlev)
+        return rl
     if fp64_kernel and tfl / fp64_tflops > gbs / hbm:
         rl = {"bound": "alu", "achieved": tfl, "peak": fp64_tflops, "unit": "TFLOP/s (fp64)",
               "frac": tfl / fp64_tflops}
@@ -349,6 +376,7 @@ def roofline(res, peaks, precision):
 
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12    # 1.26 TFLOP/s
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 80.5 TFLOP/s
 
 
 def load_peaks():

@@ -32,6 +32,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "poisson.cuh"
@@ -40,10 +41,42 @@ namespace lm {
 
 namespace {
 
+// Programmatic dependent launch: every kernel of the solver is launched with
+// programmatic stream serialisation, so the next kernel of the chain is
+// scheduled while this one drains.  Each kernel therefore waits for its
+// predecessor's completion (and memory flush) before touching global memory
+// (pdl_wait, first statement), and lets its own successor launch at once
+// (pdl_trigger).  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("LOWMACH_NO_PDL");   // tuning override: disable PDL
+        return !(e && e[0] == '1');
+    }();
+    return on;
+}
+
+template <typename... KArgs, typename... Args>
+void launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 constexpr int NTV = kThreads;            // block size of the pointwise kernels
 constexpr int kTailThreads = 512;
 constexpr long long kTailCellsF32 = 4096;   // largest level handled by the tail (FP32)
-constexpr long long kTailCellsF64 = 512;    // (FP64: one SM's FP64 rate is 1/64 of FP32)
+constexpr long long kTailCellsF64 = 128;    // (FP64: one SM's FP64 rate is 1/64 of FP32)
 constexpr size_t kTailSmemMax = 200 * 1024;
 
 template <int DIM>
@@ -159,17 +192,19 @@ __device__ __forceinline__ T prolong_at(const LvT<T>& C, const T* __restrict__ u
     return plane(0);
 }
 
-// Last block of a grid to arrive (after its partial sums are visible).
+// Last block of a grid to arrive.  The block's partial sums are written by
+// thread 0 before the call, so only thread 0 fences them (release) before
+// counting in; the last block fences again (acquire) before reading the others'.
 __device__ __forceinline__ bool arrive_last(unsigned int* cnt) {
     __shared__ int am_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
         am_last = (atomicAdd(cnt, 1u) == nb - 1u);
+        if (am_last) __threadfence();
     }
     __syncthreads();
-    if (am_last) __threadfence();
     return am_last != 0;
 }
 
@@ -190,6 +225,8 @@ __device__ __forceinline__ int block_linear() {
 template <class T, class TF, int DIM>
 __global__ void __launch_bounds__(Tile<DIM>::NT) k_mg_down(LvT<T> L, LvT<T> C, const TF* __restrict__ f,
                                                            T* __restrict__ upre, T* __restrict__ fc) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int H = 3;
     using B = Box<DIM, H>;
     constexpr int NT = Tile<DIM>::NT;
@@ -293,6 +330,8 @@ __global__ void __launch_bounds__(Tile<DIM>::NT)
     k_mg_up(LvT<T> L, LvT<T> C, const T* __restrict__ upre, const TF* __restrict__ f, const T* __restrict__ uc,
             T* __restrict__ upost, double* part_rz, double* part_sz, double* scal, const int* ictl,
             unsigned int* cnt) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int H = 2;
     using B = Box<DIM, H>;
     constexpr int NT = Tile<DIM>::NT;
@@ -406,6 +445,8 @@ template <class T, int DIM, class V>
 __global__ void __launch_bounds__(Tile<DIM>::NT)
     k_cg_pq(LvT<V> L, const T* __restrict__ z, V* p0, V* p1, V* __restrict__ q, double* part, double* scal,
             const int* ictl, unsigned int* cnt) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int H = 1;
     using B = Box<DIM, H>;
     constexpr int NT = Tile<DIM>::NT;
@@ -466,6 +507,8 @@ __global__ void __launch_bounds__(NTV)
     k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* p0, const double* p1,
                 const double* __restrict__ q, long long N, double* part, double* scal, int* ictl,
                 unsigned int* cnt, double rtol, int max_iter, cudaGraphConditionalHandle h, int use_graph) {
+    pdl_wait();
+    pdl_trigger();
     const int it = ictl[PI_IT];
     const double* __restrict__ p = (it & 1) ? p1 : p0;
     const double alpha = scal[PS_ALPHA];
@@ -502,19 +545,23 @@ __global__ void __launch_bounds__(NTV)
 // ---------------------------------------------------------------------------
 // Refinement mode: FP32 inner update, then (when due) the FP64 outer step.
 // ---------------------------------------------------------------------------
-// e = (first inner iteration ? 0 : e) + alpha p, r32 -= alpha q, ||r32||^2; the
-// last block counts the iteration and flags an outer step when the inner solve
-// reached inner_tol (relative to its start), inner_max, or the solve's cap.
+// e = (folded into x since the last update ? 0 : e) + alpha p, r32 -= alpha q,
+// ||r32||^2; the last block counts the iteration and flags a reliable update
+// when the residual dropped by inner_tol since the last one, after inner_max
+// iterations, or at the solve's iteration cap.
 __global__ void __launch_bounds__(NTV)
     k_ir_update(float* __restrict__ e, float* __restrict__ r, const float* p0, const float* p1,
                 const float* __restrict__ q, long long N, double* part, double* scal, int* ictl, unsigned int* cnt,
                 double inner_tol, int inner_max, int max_iter, cudaGraphConditionalHandle h, int use_graph) {
+    pdl_wait();
+    pdl_trigger();
     const int it = ictl[PI_IT];
+    const int ereset = ictl[PI_ERESET];
     const float* __restrict__ p = (it & 1) ? p1 : p0;
     const float alpha = (float)scal[PS_ALPHA];
     float rr = 0.0f;
     for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV) {
-        const float ev = (it == 0) ? 0.0f : e[t];
+        const float ev = (it == 0 || ereset) ? 0.0f : e[t];
         e[t] = fmaf(alpha, p[t], ev);
         const float rv = fmaf(-alpha, q[t], r[t]);
         r[t] = rv;
@@ -527,12 +574,14 @@ __global__ void __launch_bounds__(NTV)
     if (arrive_last(cnt)) {
         const double RR = sum_parts_cg<NTV>(part, gridDim.x, red);
         if (threadIdx.x == 0) {
-            const int itn = it + 1, tot = ictl[PI_TOTAL] + 1;
+            const int itn = it + 1, tot = ictl[PI_TOTAL] + 1, since = ictl[PI_SINCE] + 1;
             ictl[PI_IT] = itn;
             ictl[PI_TOTAL] = tot;
+            ictl[PI_ERESET] = 0;
+            ictl[PI_SINCE] = since;           // iterations since the last reliable update
             scal[PS_ITERS] = (double)tot;
             const int bad = !(RR == RR) || !(RR < 1e300);
-            const int refine = (RR <= inner_tol * inner_tol * scal[PS_RR0]) || (itn >= inner_max) ||
+            const int refine = (RR <= inner_tol * inner_tol * scal[PS_RR0]) || (since >= inner_max) ||
                                (tot >= max_iter) || bad;
             ictl[PI_REFINE] = refine;
             if (!refine && use_graph) cudaGraphSetConditional(h, 1u);
@@ -541,14 +590,16 @@ __global__ void __launch_bounds__(NTV)
     }
 }
 
-// Outer step (FP64), only when flagged: x += e, r64 -= A e (e exact in FP64),
-// r32 = r64, ||r64||^2; the last block applies the FP64 stopping test and
-// restarts the inner solve.
+// Reliable update (FP64), only when flagged: x += e, r64 -= A e (e exact in
+// FP64), r32 = r64, ||r64||^2; the last block applies the FP64 stopping test.
+// The FP32 search direction and r.z are kept (no restart).
 template <int DIM>
 __global__ void __launch_bounds__(NTV)
     k_ir_refine(LvT<double> L, double* __restrict__ x, double* __restrict__ r64, const float* __restrict__ e,
                 float* __restrict__ r32, double* part, double* scal, int* ictl, unsigned int* cnt, double rtol,
                 int max_iter, cudaGraphConditionalHandle h, int use_graph) {
+    pdl_wait();
+    pdl_trigger();
     if (!ictl[PI_REFINE]) return;
     double rr = 0.0;
     for (int t = blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
@@ -587,8 +638,9 @@ __global__ void __launch_bounds__(NTV)
             scal[PS_RR] = RR;
             scal[PS_RR0] = RR;
             scal[PS_RELRES] = sqrt(RR / ff);
-            ictl[PI_IT] = 0;
             ictl[PI_REFINE] = 0;
+            ictl[PI_ERESET] = 1;                   // e now lives in x
+            ictl[PI_SINCE] = 0;
             ictl[PI_DONE] = done;
             if (done && !conv) ictl[PI_NOCONV] = 1;
             if (use_graph) cudaGraphSetConditional(h, done ? 0u : 1u);
@@ -623,6 +675,8 @@ __device__ __forceinline__ T off_compact(const LvT<T>& L, const T* u, int t, con
 // Sum of b (partials; the last block stores the mean).
 __global__ void __launch_bounds__(NTV) k_mean(const double* __restrict__ b, long long N, double* part,
                                               double* scal, int slot, unsigned int* cnt) {
+    pdl_wait();
+    pdl_trigger();
     double v = 0.0;
     for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV) v += b[t];
     __shared__ double red[NTV / 32];
@@ -644,6 +698,8 @@ __global__ void __launch_bounds__(NTV)
     k_pcg_init(LvT<double> L, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
                float* __restrict__ r32, double* pff, double* prr, double* scal, int* ictl, unsigned int* cnt,
                double rtol, cudaGraphConditionalHandle h, int use_graph) {
+    pdl_wait();
+    pdl_trigger();
     const double mean_b = scal[PS_MEANB];
     double ff = 0.0, rr = 0.0;
     for (int t = blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
@@ -678,6 +734,8 @@ __global__ void __launch_bounds__(NTV)
             ictl[PI_IT] = 0;
             ictl[PI_TOTAL] = 0;
             ictl[PI_REFINE] = 0;
+            ictl[PI_ERESET] = 1;
+            ictl[PI_SINCE] = 0;
             ictl[PI_NOCONV] = 0;
             const int zero = !(FF > 0.0);
             ictl[PI_ZERO] = zero;
@@ -697,6 +755,8 @@ __global__ void __launch_bounds__(NTV)
 // Zero-mean x; report iterations / residual / status.
 __global__ void __launch_bounds__(NTV) k_sub_mean(double* __restrict__ x, long long N, const double* scal,
                                                   const int* ictl, double* rep, int* status, int bit) {
+    pdl_wait();
+    pdl_trigger();
     const double mean = scal[PS_MEANX];
     const int zero = ictl[PI_ZERO];
     for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV)
@@ -734,6 +794,8 @@ template <class T, int DIM>
 __global__ void __launch_bounds__(kTailThreads)
     k_mg_tail(const LvT<T>* __restrict__ levs, TailArgs a, const T* __restrict__ f_top, T* __restrict__ u_top,
               const T* __restrict__ Minv) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     const int top = a.top, last = a.nlev - 1;
@@ -843,6 +905,8 @@ template <class T>
 __global__ void __launch_bounds__(kTailThreads)
     k_direct(const T* __restrict__ Minv, int Nc, const double* __restrict__ r, T* __restrict__ z, double* scal,
              const int* ictl) {
+    pdl_wait();
+    pdl_trigger();
     double rz = 0.0, sz = 0.0;
     for (int i = threadIdx.x; i < Nc; i += kTailThreads) {
         T acc = (T)0;
@@ -870,12 +934,14 @@ __global__ void __launch_bounds__(kTailThreads)
 // ---------------------------------------------------------------------------
 namespace k2 {
 
-constexpr int NW = 8;             // warps per block
+constexpr int NW = 16;            // warps per block
 constexpr int NT = 32 * NW;
 constexpr int SY = 32;            // box rows
-constexpr int FD = 26;            // down: fine tile (box 32 = 26 + 2 x 3), coarse tile 13
-constexpr int CD = 13;
-constexpr int FU = 28;            // up: fine tile (32 = 28 + 2 x 2)
+// NS red-black sweeps per smoothing: down keeps a halo of 2 NS + 1 (fine tile
+// 32 - 2 (2 NS + 1)), up a halo of 2 NS (fine tile 32 - 4 NS).
+__host__ __device__ constexpr int fd_of(int ns) { return 32 - 2 * (2 * ns + 1); }   // down fine tile (26 / 22)
+__host__ __device__ constexpr int cd_of(int ns) { return fd_of(ns) / 2; }           // down coarse tile (13 / 11)
+__host__ __device__ constexpr int fu_of(int ns) { return 32 - 4 * ns; }              // up fine tile (28 / 24)
 constexpr int FP = 30;            // CG operator: tile (32 = 30 + 2 x 1)
 
 struct Ax {
@@ -916,10 +982,12 @@ __device__ __forceinline__ void color_sweep(const LvT<T>& L, T (*su)[32], T (*sf
     }
 }
 
-template <class T, class TF>
+template <class T, class TF, int NS>
 __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restrict__ f, T* __restrict__ upre,
                                            T* __restrict__ fc) {
-    constexpr int H = 3;
+    pdl_wait();
+    pdl_trigger();
+    constexpr int H = 2 * NS + 1, FD = fd_of(NS), CD = cd_of(NS);
     __shared__ T sf[SY][32];
     __shared__ T su[SY][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -940,14 +1008,20 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
         su[r][lane] = uv;
     }
     __syncthreads();
-    color_sweep<T>(L, su, sf, ox, oy, par0, 1, 1, SY - 2, 1, 30);
-    __syncthreads();
-    // residual on rows / columns 2 .. 29 (overwrites f); store the tile's u
-    const bool colr = (lane >= 2 && lane <= 29);
+    // pre-smoothing (red from zero above, then black, red, ...): sweep k works on
+    // the box minus k layers
+#pragma unroll
+    for (int k = 1; k < 2 * NS; ++k) {
+        color_sweep<T>(L, su, sf, ox, oy, par0, k & 1, k, SY - 1 - k, k, 31 - k);
+        __syncthreads();
+    }
+    // residual on the box minus 2 NS layers (overwrites f); store the tile's u
+    constexpr int R0 = 2 * NS, R1 = 31 - 2 * NS;
+    const bool colr = (lane >= R0 && lane <= R1);
 #pragma unroll
     for (int k = 0; k < SY / NW; ++k) {
         const int r = warp + NW * k;
-        if (r < 2 || r > 29 || !colr) continue;
+        if (r < R0 || r > R1 || !colr) continue;
         const Ax ay = axis(oy + r, L.n[1], L.per[1]);
         if (!(ax.valid && ay.valid)) continue;
         const T u = su[r][lane];
@@ -955,6 +1029,8 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
         if (ax.in && ay.in && lane >= H && lane < H + FD && r >= H && r < H + FD) upre[ax.gw + nx * ay.gw] = u;
     }
     __syncthreads();
+    // restriction: coarse cell I of the tile reads fine cells 2I-1 .. 2I+2, at
+    // box offset 2 c + H - 1 + a
     for (int c = threadIdx.x; c < CD * CD; c += NT) {
         const int cx = c % CD, cy = c / CD;
         const int I = blockIdx.x * CD + cx, J = blockIdx.y * CD + cy;
@@ -963,21 +1039,24 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
 #pragma unroll
         for (int ay = 0; ay < 4; ++ay) {
             const T wy = (T)rweight(ay, J, C.n[1], C.per[1]);
-            const int r = 2 * cy + 2 + ay;
+            const int r = 2 * cy + H - 1 + ay;
             T row = (T)0;
 #pragma unroll
-            for (int axx = 0; axx < 4; ++axx) row += (T)rweight(axx, I, C.n[0], C.per[0]) * sf[r][2 * cx + 2 + axx];
+            for (int axx = 0; axx < 4; ++axx)
+                row += (T)rweight(axx, I, C.n[0], C.per[0]) * sf[r][2 * cx + H - 1 + axx];
             acc += wy * row;
         }
         fc[I + C.n[0] * J] = acc * (T)0.25;
     }
 }
 
-template <class T, class TF, bool FINE>
+template <class T, class TF, bool FINE, int NS>
 __global__ void __launch_bounds__(NT)
     up(LvT<T> L, LvT<T> C, const T* __restrict__ upre, const TF* __restrict__ f, const T* __restrict__ uc,
        T* __restrict__ upost, double* part_rz, double* part_sz, double* scal, const int* ictl, unsigned int* cnt) {
-    constexpr int H = 2;
+    pdl_wait();
+    pdl_trigger();
+    constexpr int H = 2 * NS, FU = fu_of(NS);
     __shared__ T sf[SY][32];
     __shared__ T su[SY][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1007,10 +1086,13 @@ __global__ void __launch_bounds__(NT)
         su[r][lane] = uv;
     }
     __syncthreads();
-    color_sweep<T>(L, su, sf, ox, oy, par0, 1, 1, SY - 2, 1, 30);
-    __syncthreads();
-    color_sweep<T>(L, su, sf, ox, oy, par0, 0, 2, SY - 3, 2, 29);
-    __syncthreads();
+    // post-smoothing black, red, ...: sweep k on the box minus k layers; the
+    // last (red) sweep covers exactly the tile
+#pragma unroll
+    for (int k = 1; k <= 2 * NS; ++k) {
+        color_sweep<T>(L, su, sf, ox, oy, par0, k & 1, k, SY - 1 - k, k, 31 - k);
+        __syncthreads();
+    }
     TF rz = (TF)0, sz = (TF)0;    // FP64 path: double; refinement mode: FP32
     const bool colo = ax.in && lane >= H && lane < H + FU;
 #pragma unroll
@@ -1055,6 +1137,8 @@ __global__ void __launch_bounds__(NT)
 template <class T, class V>
 __global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p0, V* p1, V* __restrict__ q,
                                          double* part, double* scal, const int* ictl, unsigned int* cnt) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int H = 1;
     __shared__ V sp[SY][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1144,6 +1228,8 @@ __device__ __forceinline__ void tail_color(const LvT<T>& L, T* u, const T* f, in
 template <class T>
 __global__ void __launch_bounds__(TT) tail(const LvT<T>* __restrict__ levs, TailArgs a, const T* __restrict__ f_top,
                                            T* __restrict__ u_top, const T* __restrict__ Minv) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ LvT<T> lv[kMaxLevels];
     T* sm = reinterpret_cast<T*>(smraw);
@@ -1290,9 +1376,12 @@ __device__ __forceinline__ void mm24(float* __restrict__ C, const float* __restr
 }
 
 // Shared-memory layout (floats): Sx, SxT (nx*nx each), Sy, SyT (ny*ny each),
-// IL, A, B (nx*ny each); the global tables hold Sx, Sy, IL in that order.
+// IL, A, B (nx*ny each); the global table holds Sx, SxT, Sy, SyT, IL in that
+// order and is copied linearly.
 __global__ void __launch_bounds__(FT) fdm(int nx, int ny, const float* __restrict__ tab, const float* __restrict__ f,
                                           float* __restrict__ u) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
     float* Sx = reinterpret_cast<float*>(smraw);
     float* SxT = Sx + nx * nx;
@@ -1301,23 +1390,10 @@ __global__ void __launch_bounds__(FT) fdm(int nx, int ny, const float* __restric
     float* IL = SyT + ny * ny;
     float* A = IL + nx * ny;
     float* B = A + nx * ny;
-    const float* gSx = tab;
-    const float* gSy = tab + nx * nx;
-    const float* gIL = gSy + ny * ny;
-    for (int i = threadIdx.x; i < nx * nx; i += FT) {
-        const float v = gSx[i];
-        Sx[i] = v;
-        SxT[(i % nx) * nx + i / nx] = v;
-    }
-    for (int i = threadIdx.x; i < ny * ny; i += FT) {
-        const float v = gSy[i];
-        Sy[i] = v;
-        SyT[(i % ny) * ny + i / ny] = v;
-    }
-    for (int i = threadIdx.x; i < nx * ny; i += FT) {
-        IL[i] = gIL[i];
-        A[i] = f[i];
-    }
+    const int ntab = 2 * nx * nx + 2 * ny * ny + nx * ny;     // a multiple of 4 (nx % 4 == 0, ny even)
+    for (int i = threadIdx.x; i < ntab / 4; i += FT)
+        reinterpret_cast<float4*>(Sx)[i] = reinterpret_cast<const float4*>(tab)[i];
+    for (int i = threadIdx.x; i < nx * ny; i += FT) A[i] = f[i];
     __syncthreads();
     mm24(B, A, Sx, ny, nx, nx, nullptr);    // B = F Sx
     __syncthreads();
@@ -1398,7 +1474,8 @@ int pick_top(const Shapes& s, int mg_fp32, size_t* smem_out) {
 }
 
 long long k2_blocks(const int n[3]) {
-    const long long up = (long long)((n[0] + k2::FU - 1) / k2::FU) * ((n[1] + k2::FU - 1) / k2::FU);
+    const int fu = k2::fu_of(2);   // smallest up tile of any sweep count
+    const long long up = (long long)((n[0] + fu - 1) / fu) * ((n[1] + fu - 1) / fu);
     const long long pq = (long long)((n[0] + k2::FP - 1) / k2::FP) * ((n[1] + k2::FP - 1) / k2::FP);
     return up > pq ? up : pq;
 }
@@ -1604,7 +1681,7 @@ size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg
     b += align256(sizeof(double) * Nc * Nc) + align256(sizeof(float) * Nc * Nc);
     if (fdm_fits(s, top, dim, mg_fp32)) {
         const long long nx = s.n[top][0], ny = s.n[top][1];
-        b += align256(sizeof(float) * (nx * nx + ny * ny + nx * ny));
+        b += align256(sizeof(float) * (2 * nx * nx + 2 * ny * ny + nx * ny));
     }
     if (nlev_out) *nlev_out = s.nlev;
     if (Nc_out) *Nc_out = Nc;
@@ -1643,6 +1720,16 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
     pl->rtol = rtol;
     pl->max_iter = max_iter;
     pl->tail_smem = tail_smem;
+    // red-black sweeps per smoothing (2D kernels): two, V(2,2).  The fused
+    // kernels are latency-bound, so the extra shared-memory sweeps cost less
+    // than the iterations they save (256x512: 20 -> 14 iterations per step in
+    // FP32; in FP64 a small gain together with the 128-cell tail).  Tuning
+    // override LOWMACH_SWEEPS = 1 or 2.
+    pl->sweeps = 2;
+    if (const char* e = std::getenv("LOWMACH_SWEEPS")) {
+        const int v = std::atoi(e);
+        if (v == 1 || v == 2) pl->sweeps = v;
+    }
     const long long nblk = (dim == 3) ? tile_blocks<3>(s.n[0]) : k2_blocks(s.n[0]);
     pl->npart = (int)(nblk > kMaxPartials ? nblk : kMaxPartials);
     pl->r = (double*)take(sizeof(double) * pl->N);
@@ -1651,20 +1738,19 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
     pl->q = (double*)take(sizeof(double) * pl->N);
     pl->z = take(sizeof(double) * pl->N);
     pl->u0pre = take(w * pl->N);
-    // Refinement mode is opt-in (LOWMACH_REFINE=1): on the 256 x 512 slot burner
-    // it needs ~25% more inner iterations than the FP64 CG around the same FP32
-    // multigrid, which costs more than the FP32 Krylov kernels save.
+    // Refinement mode (FP32 CG with reliable updates) is the mixed default; the
+    // tuning override LOWMACH_REFINE=0 keeps the FP64 CG around the FP32 multigrid.
     const char* rf = std::getenv("LOWMACH_REFINE");
-    const bool refine_mode = mg_fp32 && s.nlev > 1 && (rf && rf[0] == '1');
+    const bool refine_mode = mg_fp32 && s.nlev > 1 && !(rf && rf[0] == '0');
     if (refine_mode) {   // refinement mode (a one-level grid is solved exactly in FP64)
         pl->r32 = (float*)take(sizeof(float) * pl->N);
         pl->e32 = (float*)take(sizeof(float) * pl->N);
         pl->p32[0] = (float*)take(sizeof(float) * pl->N);
         pl->p32[1] = (float*)take(sizeof(float) * pl->N);
         pl->q32 = (float*)take(sizeof(float) * pl->N);
-        pl->inner_tol = 1e-4;
-        pl->inner_max = 30;
-        // tuning override: LOWMACH_INNER_TOL = relative tolerance of the FP32 inner solve
+        pl->inner_tol = 0.1;     // reliable update whenever ||r|| fell 10x since the last one
+        pl->inner_max = 50;
+        // tuning override: LOWMACH_INNER_TOL = residual drop between reliable updates
         if (const char* e = std::getenv("LOWMACH_INNER_TOL")) {
             const double v = std::atof(e);
             if (v > 0.0 && v < 1.0) pl->inner_tol = v;
@@ -1704,7 +1790,7 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
     if (pl->fdm) {
         // the top level is solved exactly by fast diagonalisation (replaces the tail V-cycle)
         const int nx = s.n[pl->top][0], ny = s.n[pl->top][1];
-        pl->fdm_tab = (float*)take(sizeof(float) * (nx * nx + ny * ny + nx * ny));
+        pl->fdm_tab = (float*)take(sizeof(float) * (2 * nx * nx + 2 * ny * ny + nx * ny));
         pl->fdm_smem = sizeof(float) * (size_t)(2 * nx * nx + 2 * ny * ny + 3 * nx * ny);
     }
     // tail shared-memory offsets (elements of T)
@@ -1735,8 +1821,14 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
         std::vector<double> Sx, Sy, lx, ly;
         eig1d(nx, pl->lev[pl->top].periodic[0], pl->lev[pl->top].h[0], Sx, lx);
         eig1d(ny, pl->lev[pl->top].periodic[1], pl->lev[pl->top].h[1], Sy, ly);
-        minv_host->insert(minv_host->end(), Sx.begin(), Sx.end());
-        minv_host->insert(minv_host->end(), Sy.begin(), Sy.end());
+        auto put = [&](const std::vector<double>& M, int n, bool transpose) {
+            for (int i = 0; i < n; ++i)
+                for (int k = 0; k < n; ++k) minv_host->push_back(transpose ? M[(size_t)k * n + i] : M[(size_t)i * n + k]);
+        };
+        put(Sx, nx, false);
+        put(Sx, nx, true);
+        put(Sy, ny, false);
+        put(Sy, ny, true);
         for (int l = 0; l < ny; ++l)
             for (int k = 0; k < nx; ++k) {
                 const double lam = ly[l] + lx[k];
@@ -1754,7 +1846,7 @@ bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& M, cudaSt
     size_t nf = 0;
     if (pl->fdm) {
         const size_t nx = pl->lev[pl->top].n[0], ny = pl->lev[pl->top].n[1];
-        nf = nx * nx + ny * ny + nx * ny;
+        nf = 2 * nx * nx + 2 * ny * ny + nx * ny;
     }
     if (M.size() != nm + nf) {
         *err = "coarse inverse not prepared";
@@ -1770,7 +1862,8 @@ bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& M, cudaSt
     if (e == cudaSuccess && pl->fdm) {
         const int nx = pl->lev[pl->top].n[0], ny = pl->lev[pl->top].n[1];
         const float* hp = Mf.data() + nm;
-        e = cudaMemcpyAsync(pl->fdm_tab, hp, sizeof(float) * (nx * nx + ny * ny + nx * ny), cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(pl->fdm_tab, hp, sizeof(float) * (2 * nx * nx + 2 * ny * ny + nx * ny),
+                            cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->cnt, 0, sizeof(unsigned int) * kNumCounters, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->ictl, 0, sizeof(int) * PI_NINT, s);
@@ -1799,6 +1892,32 @@ LvT<T> lv_host(PoissonPlan* pl, int l) {
     return v;
 }
 
+// 2D level kernels with NS sweeps per smoothing.
+template <class T, int NS>
+void enqueue_down2(PoissonPlan* pl, int l, const LvT<T>& L, const LvT<T>& C, T* fc, cudaStream_t s) {
+    constexpr int CD = k2::cd_of(NS);
+    const dim3 grid((C.n[0] + CD - 1) / CD, (C.n[1] + CD - 1) / CD);
+    if (l == 0 && pl->r32) launch(k2::down<T, float, NS>, grid, k2::NT, 0, s, L, C, pl->r32, (T*)pl->u0pre, fc);
+    else if (l == 0) launch(k2::down<T, double, NS>, grid, k2::NT, 0, s, L, C, pl->r, (T*)pl->u0pre, fc);
+    else launch(k2::down<T, T, NS>, grid, k2::NT, 0, s, L, C, (const T*)pl->lev[l].f, (T*)pl->lev[l].upre, fc);
+}
+
+template <class T, int NS>
+void enqueue_up2(PoissonPlan* pl, int l, const LvT<T>& L, const LvT<T>& C, const T* uc, cudaStream_t s) {
+    constexpr int FU = k2::fu_of(NS);
+    const dim3 grid((L.n[0] + FU - 1) / FU, (L.n[1] + FU - 1) / FU);
+    if (l == 0 && pl->r32)
+        launch(k2::up<T, float, true, NS>, grid, k2::NT, 0, s, L, C, (const T*)pl->u0pre, pl->r32, uc, (T*)pl->z,
+               pl->part0, pl->part1, pl->scal, pl->ictl, pl->cnt + CNT_UP0);
+    else if (l == 0)
+        launch(k2::up<T, double, true, NS>, grid, k2::NT, 0, s, L, C, (const T*)pl->u0pre, pl->r, uc, (T*)pl->z,
+               pl->part0, pl->part1, pl->scal, pl->ictl, pl->cnt + CNT_UP0);
+    else
+        launch(k2::up<T, T, false, NS>, grid, k2::NT, 0, s, L, C, (const T*)pl->lev[l].upre, (const T*)pl->lev[l].f,
+               uc, (T*)pl->lev[l].upost, (double*)nullptr, (double*)nullptr, (double*)nullptr, (const int*)nullptr,
+               (unsigned int*)nullptr);
+}
+
 // Right-hand side of the fine multigrid level: the FP64 CG residual, or the
 // FP32 inner residual in refinement mode.
 template <class T, int DIM>
@@ -1807,19 +1926,23 @@ void enqueue_down(PoissonPlan* pl, int l, cudaStream_t s) {
     T* fc = (T*)pl->lev[l + 1].f;
     const bool ir = pl->r32 != nullptr;
     if (DIM == 2) {
-        const dim3 grid((C.n[0] + k2::CD - 1) / k2::CD, (C.n[1] + k2::CD - 1) / k2::CD);
-        if (l == 0 && ir) k2::down<T, float><<<grid, k2::NT, 0, s>>>(L, C, pl->r32, (T*)pl->u0pre, fc);
-        else if (l == 0) k2::down<T, double><<<grid, k2::NT, 0, s>>>(L, C, pl->r, (T*)pl->u0pre, fc);
-        else k2::down<T, T><<<grid, k2::NT, 0, s>>>(L, C, (const T*)pl->lev[l].f, (T*)pl->lev[l].upre, fc);
+        {
+            if (pl->sweeps == 2) {
+                enqueue_down2<T, 2>(pl, l, L, C, fc, s);
+                pl->launches += 1;
+                return;
+            }
+        }
+        enqueue_down2<T, 1>(pl, l, L, C, fc, s);
     } else {
         const dim3 grid = tile_grid<DIM>(pl->lev[l].n);
         const size_t smem = 2 * Box<DIM, 3>::SN * sizeof(T);
         if (l == 0 && ir)
-            k_mg_down<T, float, DIM><<<grid, Tile<DIM>::NT, smem, s>>>(L, C, pl->r32, (T*)pl->u0pre, fc);
+            launch(k_mg_down<T, float, DIM>, grid, Tile<DIM>::NT, smem, s, L, C, pl->r32, (T*)pl->u0pre, fc);
         else if (l == 0)
-            k_mg_down<T, double, DIM><<<grid, Tile<DIM>::NT, smem, s>>>(L, C, pl->r, (T*)pl->u0pre, fc);
+            launch(k_mg_down<T, double, DIM>, grid, Tile<DIM>::NT, smem, s, L, C, pl->r, (T*)pl->u0pre, fc);
         else
-            k_mg_down<T, T, DIM><<<grid, Tile<DIM>::NT, smem, s>>>(L, C, (const T*)pl->lev[l].f,
+            launch(k_mg_down<T, T, DIM>, grid, Tile<DIM>::NT, smem, s, L, C, (const T*)pl->lev[l].f,
                                                                    (T*)pl->lev[l].upre, fc);
     }
     pl->launches += 1;
@@ -1831,32 +1954,27 @@ void enqueue_up(PoissonPlan* pl, int l, cudaStream_t s) {
     const T* uc = (const T*)pl->lev[l + 1].upost;
     const bool ir = pl->r32 != nullptr;
     if (DIM == 2) {
-        const dim3 grid((L.n[0] + k2::FU - 1) / k2::FU, (L.n[1] + k2::FU - 1) / k2::FU);
-        if (l == 0 && ir)
-            k2::up<T, float, true><<<grid, k2::NT, 0, s>>>(L, C, (const T*)pl->u0pre, pl->r32, uc, (T*)pl->z,
-                                                           pl->part0, pl->part1, pl->scal, pl->ictl,
-                                                           pl->cnt + CNT_UP0);
-        else if (l == 0)
-            k2::up<T, double, true><<<grid, k2::NT, 0, s>>>(L, C, (const T*)pl->u0pre, pl->r, uc, (T*)pl->z,
-                                                            pl->part0, pl->part1, pl->scal, pl->ictl,
-                                                            pl->cnt + CNT_UP0);
-        else
-            k2::up<T, T, false><<<grid, k2::NT, 0, s>>>(L, C, (const T*)pl->lev[l].upre, (const T*)pl->lev[l].f, uc,
-                                                        (T*)pl->lev[l].upost, nullptr, nullptr, nullptr, nullptr,
-                                                        nullptr);
+        {
+            if (pl->sweeps == 2) {
+                enqueue_up2<T, 2>(pl, l, L, C, uc, s);
+                pl->launches += 1;
+                return;
+            }
+        }
+        enqueue_up2<T, 1>(pl, l, L, C, uc, s);
     } else {
         const dim3 grid = tile_grid<DIM>(pl->lev[l].n);
         const size_t smem = 2 * Box<DIM, 2>::SN * sizeof(T);
         if (l == 0 && ir)
-            k_mg_up<T, float, DIM, true><<<grid, Tile<DIM>::NT, smem, s>>>(
+            launch(k_mg_up<T, float, DIM, true>, grid, Tile<DIM>::NT, smem, s, 
                 L, C, (const T*)pl->u0pre, pl->r32, uc, (T*)pl->z, pl->part0, pl->part1, pl->scal, pl->ictl,
                 pl->cnt + CNT_UP0);
         else if (l == 0)
-            k_mg_up<T, double, DIM, true><<<grid, Tile<DIM>::NT, smem, s>>>(
+            launch(k_mg_up<T, double, DIM, true>, grid, Tile<DIM>::NT, smem, s, 
                 L, C, (const T*)pl->u0pre, pl->r, uc, (T*)pl->z, pl->part0, pl->part1, pl->scal, pl->ictl,
                 pl->cnt + CNT_UP0);
         else
-            k_mg_up<T, T, DIM, false><<<grid, Tile<DIM>::NT, smem, s>>>(
+            launch(k_mg_up<T, T, DIM, false>, grid, Tile<DIM>::NT, smem, s, 
                 L, C, (const T*)pl->lev[l].upre, (const T*)pl->lev[l].f, uc, (T*)pl->lev[l].upost, nullptr, nullptr,
                 nullptr, nullptr, nullptr);
     }
@@ -1878,13 +1996,13 @@ void enqueue_tail(PoissonPlan* pl, cudaStream_t s) {
     const T* Minv = (sizeof(T) == 4) ? (const T*)pl->Minv_f : (const T*)pl->Minv;
     if (DIM == 2 && pl->fdm) {
         const int nx = pl->lev[pl->top].n[0], ny = pl->lev[pl->top].n[1];
-        k2::fdm<<<1, k2::FT, pl->fdm_smem, s>>>(nx, ny, pl->fdm_tab, (const float*)pl->lev[pl->top].f,
+        launch(k2::fdm, 1, k2::FT, pl->fdm_smem, s, nx, ny, pl->fdm_tab, (const float*)pl->lev[pl->top].f,
                                                 (float*)pl->lev[pl->top].upost);
     } else if (DIM == 2)
-        k2::tail<T><<<1, k2::TT, pl->tail_smem, s>>>(lv_dev<T>(pl), a, (const T*)pl->lev[pl->top].f,
+        launch(k2::tail<T>, 1, k2::TT, pl->tail_smem, s, lv_dev<T>(pl), a, (const T*)pl->lev[pl->top].f,
                                                      (T*)pl->lev[pl->top].upost, Minv);
     else
-        k_mg_tail<T, DIM><<<1, kTailThreads, pl->tail_smem, s>>>(lv_dev<T>(pl), a, (const T*)pl->lev[pl->top].f,
+        launch(k_mg_tail<T, DIM>, 1, kTailThreads, pl->tail_smem, s, lv_dev<T>(pl), a, (const T*)pl->lev[pl->top].f,
                                                                  (T*)pl->lev[pl->top].upost, Minv);
     pl->launches += 1;
 }
@@ -1897,21 +2015,21 @@ void enqueue_pq(PoissonPlan* pl, cudaStream_t s) {
     if (DIM == 2) {
         const dim3 grid((pl->lev[0].n[0] + k2::FP - 1) / k2::FP, (pl->lev[0].n[1] + k2::FP - 1) / k2::FP);
         if (ir)
-            k2::pq<T, float><<<grid, k2::NT, 0, s>>>(make_lv<float>(pl->lev[0], DIM), (const T*)pl->z, pl->p32[0],
+            launch(k2::pq<T, float>, grid, k2::NT, 0, s, make_lv<float>(pl->lev[0], DIM), (const T*)pl->z, pl->p32[0],
                                                      pl->p32[1], pl->q32, pl->part2, pl->scal, pl->ictl,
                                                      pl->cnt + CNT_PQ);
         else
-            k2::pq<T, double><<<grid, k2::NT, 0, s>>>(make_lv<double>(pl->lev[0], DIM), (const T*)pl->z, pl->p[0],
+            launch(k2::pq<T, double>, grid, k2::NT, 0, s, make_lv<double>(pl->lev[0], DIM), (const T*)pl->z, pl->p[0],
                                                       pl->p[1], pl->q, pl->part2, pl->scal, pl->ictl,
                                                       pl->cnt + CNT_PQ);
     } else {
         const dim3 grid = tile_grid<DIM>(pl->lev[0].n);
         if (ir)
-            k_cg_pq<T, DIM, float><<<grid, Tile<DIM>::NT, Box<DIM, 1>::SN * sizeof(float), s>>>(
+            launch(k_cg_pq<T, DIM, float>, grid, Tile<DIM>::NT, Box<DIM, 1>::SN * sizeof(float), s, 
                 make_lv<float>(pl->lev[0], DIM), (const T*)pl->z, pl->p32[0], pl->p32[1], pl->q32, pl->part2,
                 pl->scal, pl->ictl, pl->cnt + CNT_PQ);
         else
-            k_cg_pq<T, DIM, double><<<grid, Tile<DIM>::NT, Box<DIM, 1>::SN * sizeof(double), s>>>(
+            launch(k_cg_pq<T, DIM, double>, grid, Tile<DIM>::NT, Box<DIM, 1>::SN * sizeof(double), s, 
                 make_lv<double>(pl->lev[0], DIM), (const T*)pl->z, pl->p[0], pl->p[1], pl->q, pl->part2, pl->scal,
                 pl->ictl, pl->cnt + CNT_PQ);
     }
@@ -1923,7 +2041,7 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
     const bool ir = pl->r32 != nullptr;
     if (pl->nlev == 1) {
         // one-level grid: the preconditioner is the exact coarse solve (FP64)
-        k_direct<double><<<1, kTailThreads, 0, s>>>(pl->Minv, (int)pl->Nc, pl->r, (double*)pl->z, pl->scal,
+        launch(k_direct<double>, 1, kTailThreads, 0, s, pl->Minv, (int)pl->Nc, pl->r, (double*)pl->z, pl->scal,
                                                     pl->ictl);
         pl->launches += 1;
         enqueue_pq<double, DIM>(pl, s);
@@ -1935,15 +2053,15 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
     }
     const int rb = reduce_blocks(pl->N);
     if (ir) {
-        k_ir_update<<<rb, NTV, 0, s>>>(pl->e32, pl->r32, pl->p32[0], pl->p32[1], pl->q32, pl->N, pl->part0, pl->scal,
+        launch(k_ir_update, rb, NTV, 0, s, pl->e32, pl->r32, pl->p32[0], pl->p32[1], pl->q32, pl->N, pl->part0, pl->scal,
                                        pl->ictl, pl->cnt + CNT_UPD, pl->inner_tol, pl->inner_max, pl->max_iter, h,
                                        use_graph);
-        k_ir_refine<DIM><<<rb, NTV, 0, s>>>(make_lv<double>(pl->lev[0], DIM), x, pl->r, pl->e32, pl->r32, pl->part1,
+        launch(k_ir_refine<DIM>, rb, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r, pl->e32, pl->r32, pl->part1,
                                             pl->scal, pl->ictl, pl->cnt + CNT_REF, pl->rtol, pl->max_iter, h,
                                             use_graph);
         pl->launches += 2;
     } else {
-        k_cg_update<<<rb, NTV, 0, s>>>(x, pl->r, pl->p[0], pl->p[1], pl->q, pl->N, pl->part0, pl->scal, pl->ictl,
+        launch(k_cg_update, rb, NTV, 0, s, x, pl->r, pl->p[0], pl->p[1], pl->q, pl->N, pl->part0, pl->scal, pl->ictl,
                                        pl->cnt + CNT_UPD, pl->rtol, pl->max_iter, h, use_graph);
         pl->launches += 1;
     }
@@ -1953,9 +2071,9 @@ template <int DIM>
 void prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s, cudaGraphConditionalHandle h,
               int use_graph) {
     const int rb = reduce_blocks(pl->N);
-    k_mean<<<rb, NTV, 0, s>>>(b, pl->N, pl->part0, pl->scal, PS_MEANB, pl->cnt + CNT_MEANB);
+    launch(k_mean, rb, NTV, 0, s, b, pl->N, pl->part0, pl->scal, PS_MEANB, pl->cnt + CNT_MEANB);
     const LvT<double> L = make_lv<double>(pl->lev[0], DIM);
-    k_pcg_init<DIM><<<rb, NTV, 0, s>>>(L, b, x, pl->r, pl->r32, pl->part1, pl->part2, pl->scal, pl->ictl,
+    launch(k_pcg_init<DIM>, rb, NTV, 0, s, L, b, x, pl->r, pl->r32, pl->part1, pl->part2, pl->scal, pl->ictl,
                                        pl->cnt + CNT_INIT, pl->rtol, h, use_graph);
     pl->launches += 2;
 }
@@ -1988,8 +2106,8 @@ cudaError_t poisson_enqueue_body(PoissonPlan* pl, double* x, cudaStream_t s, uns
 cudaError_t poisson_enqueue_epilogue(PoissonPlan* pl, double* x, cudaStream_t s, double* rep, int* status,
                                      int status_bit) {
     const int rb = reduce_blocks(pl->N);
-    k_mean<<<rb, NTV, 0, s>>>(x, pl->N, pl->part0, pl->scal, PS_MEANX, pl->cnt + CNT_MEANX);
-    k_sub_mean<<<rb, NTV, 0, s>>>(x, pl->N, pl->scal, pl->ictl, rep, status, status_bit);
+    launch(k_mean, rb, NTV, 0, s, x, pl->N, pl->part0, pl->scal, PS_MEANX, pl->cnt + CNT_MEANX);
+    launch(k_sub_mean, rb, NTV, 0, s, x, pl->N, pl->scal, pl->ictl, rep, status, status_bit);
     pl->launches += 2;
     return cudaGetLastError();
 }

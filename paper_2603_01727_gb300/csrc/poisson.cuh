@@ -56,9 +56,12 @@ enum : int {
     PS_RR0 = 10,      // ||r||^2 at the start of the current inner solve (refinement mode)
     PS_NSCAL = 16
 };
-// PI_IT: iterations of the current (inner) CG; PI_TOTAL: all inner iterations
-// of the solve; PI_REFINE: an outer refinement step is due (refinement mode).
-enum : int { PI_IT = 0, PI_DONE = 1, PI_NOCONV = 2, PI_ZERO = 3, PI_REFINE = 4, PI_TOTAL = 5, PI_NINT = 8 };
+// PI_IT: CG iterations of the solve (FP32 CG iterations in refinement mode);
+// PI_TOTAL: the same count for the iteration cap; PI_REFINE: a reliable
+// update is due; PI_ERESET: the FP32 correction was folded into x; PI_SINCE:
+// iterations since the last reliable update (refinement mode).
+enum : int { PI_IT = 0, PI_DONE = 1, PI_NOCONV = 2, PI_ZERO = 3, PI_REFINE = 4, PI_TOTAL = 5, PI_ERESET = 6,
+             PI_SINCE = 7, PI_NINT = 8 };
 constexpr int kNumCounters = 8;          // last-block counters (one per reducing kernel kind)
 
 struct PoissonPlan {
@@ -66,6 +69,7 @@ struct PoissonPlan {
     int nlev;
     int top;              // first level of the single-block tail (levels top .. nlev-1)
     int mg_fp32;          // 1: multigrid in FP32, else FP64
+    int sweeps;           // red-black sweeps per pre / post smoothing (2D kernels)
     MgLevel lev[kMaxLevels];
     long long N;          // fine cells
     double* r;            // FP64 Krylov vectors on the fine level
@@ -73,9 +77,11 @@ struct PoissonPlan {
     double* q;
     void* z;              // preconditioned residual (T)
     void* u0pre;          // pre-smoothed fine-level correction (T)
-    // Refinement mode (mg_fp32): an FP32 inner PCG on A e = r solved to a
-    // relative inner_tol inside an FP64 iterative-refinement loop
-    // (x += e, r -= A e in FP64, FP64 stopping test).
+    // Refinement mode (mg_fp32): the CG runs in FP32 on the correction e with
+    // reliable updates: whenever its residual has dropped by inner_tol since
+    // the last update, e is folded into the FP64 x, the FP64 residual is
+    // updated (r -= A e) and replaces the FP32 one, and the FP64 stopping test
+    // runs; the search direction is kept across updates.
     float* r32;           // inner residual
     float* e32;           // inner solution (correction)
     float* p32[2];        // inner search direction, double-buffered
@@ -102,8 +108,8 @@ struct PoissonPlan {
     unsigned char levtab_host[kMaxLevels * sizeof(LvT<double>)];   // host copy of levtab
     // fast-diagonalisation solve of the top coarse level (2D, FP32 multigrid)
     int fdm;
-    float* fdm_tab;       // S_x (nx x nx, eigenvectors as columns), S_y (ny x ny), inverse
-                          // eigenvalue sums (ny x nx, 0 for the null mode)
+    float* fdm_tab;       // S_x, S_x^T (nx x nx, eigenvectors as columns), S_y, S_y^T (ny x ny),
+                          // inverse eigenvalue sums (ny x nx, 0 for the null mode)
     size_t fdm_smem;
 };
 
@@ -113,7 +119,7 @@ size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg
 
 // Carve a plan out of ws (256-byte aligned, >= poisson_plan_bytes) and compute
 // the coarsest-level inverse and the level tables on the host; minv_host gets
-// the coarse inverse followed (fast-diagonalisation plans) by S_x, S_y and the
+// the coarse inverse followed (fast-diagonalisation plans) by S_x, S_x^T, S_y, S_y^T and the
 // inverse eigenvalue sums.
 bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[3], const int periodic[3],
                        int mg_fp32, double rtol, int max_iter, void* ws, size_t ws_bytes,

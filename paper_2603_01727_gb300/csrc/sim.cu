@@ -886,6 +886,9 @@ sim_status sim_query(sim_t* s, int what, double* out) {
         case SIM_Q_MASS: return dev(SC_MASS, out);
         case SIM_Q_NCELLS: *out = (double)s->g.ncell; return SIM_OK;
         case SIM_Q_MG_LEVELS: *out = (double)s->pp.nlev; return SIM_OK;
+        case SIM_Q_TAIL_NX: *out = (double)s->pp.lev[s->pp.top].n[0]; return SIM_OK;
+        case SIM_Q_TAIL_NY: *out = (double)s->pp.lev[s->pp.top].n[1]; return SIM_OK;
+        case SIM_Q_TAIL_FDM: *out = (double)s->pp.fdm; return SIM_OK;
         case SIM_Q_KERNEL_LAUNCHES: {
             if (s->launches_last >= 0) {
                 *out = (double)s->launches_last;

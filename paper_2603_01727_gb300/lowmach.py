@@ -25,9 +25,11 @@ SIM_IBM_NONE, SIM_IBM_SLOT, SIM_IBM_SPHERE = 0, 1, 2
  SIM_FIELD_P, SIM_FIELD_FX, SIM_FIELD_FY, SIM_FIELD_FZ, SIM_FIELD_CHI, SIM_FIELD_SM,
  SIM_FIELD_KAPPA) = range(14)
 SIM_GET, SIM_SET = 0, 1
-SIM_K_RESIDUAL, SIM_K_SMOOTH, SIM_K_MATVEC, SIM_K_RESTRICT, SIM_K_STATE, SIM_K_PROJECT = range(6)
+(SIM_K_RESIDUAL, SIM_K_MG_DOWN, SIM_K_CG_MATVEC, SIM_K_MG_UP, SIM_K_STATE, SIM_K_PROJECT,
+ SIM_K_MG_TAIL) = range(7)
 (SIM_Q_TIME, SIM_Q_DT, SIM_Q_P0, SIM_Q_STEPS, SIM_Q_ITERS_PRED, SIM_Q_ITERS_CORR, SIM_Q_RESID_PRED,
- SIM_Q_RESID_CORR, SIM_Q_MASS, SIM_Q_NCELLS, SIM_Q_MG_LEVELS, SIM_Q_KERNEL_LAUNCHES) = range(12)
+ SIM_Q_RESID_CORR, SIM_Q_MASS, SIM_Q_NCELLS, SIM_Q_MG_LEVELS, SIM_Q_KERNEL_LAUNCHES, SIM_Q_TAIL_NX,
+ SIM_Q_TAIL_NY, SIM_Q_TAIL_FDM) = range(15)
 
 FIELD_IDS = dict(U=SIM_FIELD_U, V=SIM_FIELD_V, W=SIM_FIELD_W, Z=SIM_FIELD_Z, H=SIM_FIELD_H,
                  T=SIM_FIELD_T, RHO=SIM_FIELD_RHO, P=SIM_FIELD_P, FX=SIM_FIELD_FX, FY=SIM_FIELD_FY,
