@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="slot", choices=["slot", "sphere", "blobs"])
+    ap.add_argument("--config", default="slot", choices=["slot", "sphere", "blobs", "batch"])
+    ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -74,6 +75,12 @@ def workload(name):
         cfg = {"workload": "3D 192^3 spherical porous burner (IBM sphere r=0.1L, radial fuel mass flux "
                            "Re=150, quiescent air, density ratio 7, 1% perturbations, outflow all sides)",
                "grid": [192, 192, 192]}
+    elif name == "batch":
+        # the oracle's sample of the batched workload: its first flame
+        prm, geo, f = W.batched_flames(1)[0]
+        cfg = {"workload": "256 independent 2D slot-burner flames in one CUDA graph per step, grids uniform "
+                           "from {64x128, 96x192, 128x256}, inlet Re~U[50,400], Z_st~U[0.04,0.08], density "
+                           "ratio~U[4,8]", "grids": [list(g) for g in W.BATCH_GRIDS]}
     else:
         prm, geo, f = W.periodic_blobs(64)
         cfg = {"workload": "2D 64x64 doubly periodic enclosed box, 8 Gaussian Z blobs, Re=100",
@@ -289,6 +296,89 @@ def run_gpu(args, precision, world, rank, local, pg):
     return out
 
 
+def step_bytes_model(dim, iters, mixed):
+    """Algorithmic HBM bytes per cell and step (each array read / written once
+    per kernel): two stages of stencil (~30 FP64 words), state relation (5),
+    fluxes and right-hand side (12) and projection (8); per CG iteration the
+    multigrid down / up sweeps of the fine level and the Krylov kernels (~15
+    words of the multigrid type plus 4 Krylov words, x 4/3 for the coarser
+    levels in 2D, 8/7 in 3D)."""
+    stage = 2 * (30 + 5 + 12 + 8) * 8.0
+    w = 4.0 if mixed else 8.0
+    per_it = (15 * w + 4 * w) * (4.0 / 3.0 if dim == 2 else 8.0 / 7.0)
+    return stage + iters * per_it
+
+
+def run_gpu_batch(args, precision, world, rank, local, pg):
+    """C5: independent flames advanced by one batch graph per step."""
+    import torch
+    from paper_2603_01727_gb300 import lowmach as LM, autotune
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(stream)
+    flames = W.batched_flames(args.batch_size, precision=LM.SIM_MIXED if precision == "mixed" else LM.SIM_FP64)
+    for prm, _, _ in flames:
+        prm["poisson_rtol"] = 1e-10
+    # autotune each grid size once (first flame of that size)
+    tuned, tables = {}, {}
+    for prm, geo, f in flames:
+        key = tuple(prm["n"][:2])
+        if key not in tuned:
+            tuned[key], tab = autotune.tune(prm, geo, f, copies=8, device=device)
+            tables["x".join(map(str, key))] = {f"sweeps{a}_tail{b}": round(v, 4) for (a, b), v in tab.items()}
+    sims = []
+    for prm, geo, f in flames:
+        s = LM.Simulation(autotune.apply(prm, tuned[tuple(prm["n"][:2])]), geo, device=device, stream=stream)
+        s.set_fields(f)
+        sims.append(s)
+    batch = LM.Batch(sims, stream=stream)
+    ncell = batch.cells()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    batch.step(max(args.warmup, 8))           # eager start-up and every rotation phase's graph
+    batch.sync()
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    launches, iters = 0, []
+    clocks = Clocks(device.index)
+    barrier(pg, device)
+    torch.cuda.synchronize(device)
+    clocks.start()
+    for k in range(K):
+        flush.zero_()
+        starts[k].record(stream)
+        batch.step(1)
+        ends[k].record(stream)
+        batch.sync()
+        launches += sum(int(s.query(LM.SIM_Q_KERNEL_LAUNCHES)) for s in sims)
+        iters.append(float(np.mean([s.query(LM.SIM_Q_ITERS_PRED) + s.query(LM.SIM_Q_ITERS_CORR) for s in sims])))
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    barrier(pg, device)
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    ms_max = reduce_max(pg, ms, device)
+    cells_all = reduce_sum(pg, float(ncell) * K, device)
+    value = cells_all / (ms_max * 1e-3)
+    relres = max(max(s.query(LM.SIM_Q_RESID_PRED), s.query(LM.SIM_Q_RESID_CORR)) for s in sims)
+    it = float(np.mean(iters))
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bytes_step = step_bytes_model(2, it, precision == "mixed") * ncell
+    gbs = bytes_step / (ms / K * 1e-3) / 1e9
+    rl = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+          "kernel": "whole batched step (all kernels of all flames; model bytes per cell-step "
+                    f"{bytes_step / ncell:.0f} B)", "traffic": None,
+          "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"}
+    cfg = workload("batch")[3]
+    cfg.update(flames=len(sims), cells=ncell, autotuned={"x".join(map(str, k)): list(v) for k, v in tuned.items()},
+               autotune_ms=tables)
+    out = dict(value=value, ms_per_step=ms_max / K, launches=launches, iters_per_step=it, relres=relres, clocks=clk,
+               ktimes={}, models={}, ncell=ncell, cfg=cfg, sim=None, roofline=rl)
+    batch.close()
+    return out
+
+
 def e2e_gpu(args, precision, res, device):
     """Same metric through the C ABI with host buffers: every step loads the
     restart state from pinned host memory, steps once and saves the state back
@@ -440,7 +530,8 @@ def main():
     results = {}
     for p in precs:
         try:
-            results[p] = run_gpu(args, p, world, rank, local, pg)
+            runner = run_gpu_batch if args.config == "batch" else run_gpu
+            results[p] = runner(args, p, world, rank, local, pg)
         except LM.SimError as e:
             if p == "mixed" and e.status == LM.SIM_EINVAL and args.precision == "both":
                 continue      # mixed precision not built into this library
@@ -448,8 +539,8 @@ def main():
     head = "mixed" if "mixed" in results else "fp64"
     res = results[head]
     peaks = load_peaks()
-    rl = roofline(res, peaks, head) if res["ktimes"] else None
-    e2e = None if args.no_e2e else e2e_gpu(args, head, res, device)
+    rl = roofline(res, peaks, head) if res["ktimes"] else res.get("roofline")
+    e2e = None if (args.no_e2e or res["sim"] is None) else e2e_gpu(args, head, res, device)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, done, secs = oracle_rate(args.config, 200, 20.0)

@@ -89,6 +89,12 @@ typedef struct {
                                 residual and the stopping test stay FP64)              */
     double poisson_rtol;     /* stop when ||r||_2 / ||f||_2 <= rtol (0 < rtol < 1)      */
     int poisson_max_iter;    /* PCG iteration cap (>= 1)                                */
+    /* Multigrid tuning (0 = library default): red-black sweeps per pre / post
+     * smoothing of the 2D fused kernels (1 or 2), and the largest level (cells)
+     * handled by the one-block coarse solve.  Results depend on them only
+     * through the iteration count (the stopping test is unchanged). */
+    int mg_sweeps;
+    int mg_tail_cells;
 } sim_params_t;
 
 /* Immersed burner (paper Sec. 3.4; Eqs 3.30-3.33, 4.19-4.21).  The mask is the
@@ -202,6 +208,29 @@ sim_status sim_time_kernel(sim_t *sim, int kernel, int reps);
 const char *sim_last_error(const sim_t *sim);
 
 void sim_destroy(sim_t *sim);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent simulations (many flames, e.g. of uneven grid sizes).
+ * One CUDA graph per step holds every simulation's whole step as an
+ * independent branch (forked streams at capture), so their latency-bound
+ * kernel chains run concurrently on the GPU.  The paper has no counterpart:
+ * each simulation is the paper's step unchanged; only the launching differs.
+ *   create:  sims (host array of n distinct handles, n >= 1) is copied; the
+ *            simulations stay owned by the caller and must outlive the batch.
+ *            Work is enqueued on cuda_stream.
+ *   step:    advances every simulation nsteps steps; the first two steps of a
+ *            run go through each simulation's own launch path, later ones one
+ *            batch graph launch per step.  The simulations must be in lockstep
+ *            (SIM_ESTATE otherwise).  Do not call a member simulation's own
+ *            functions while a batch step may be in flight: sim_batch_sync first.
+ *   sync:    waits and returns the first failing member's device status.
+ * ------------------------------------------------------------------------- */
+typedef struct sim_batch sim_batch_t;
+sim_status sim_batch_create(sim_t *const *sims, int n, void *cuda_stream, sim_batch_t **out);
+sim_status sim_batch_step(sim_batch_t *batch, int nsteps);
+sim_status sim_batch_sync(sim_batch_t *batch);
+const char *sim_batch_last_error(const sim_batch_t *batch);
+void sim_batch_destroy(sim_batch_t *batch);
 
 /* ---------------------------------------------------------------------------
  * Stand-alone pressure solve (the step's dominant kernel, paper Eqs 3.9/3.24):

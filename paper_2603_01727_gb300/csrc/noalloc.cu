@@ -68,7 +68,7 @@ extern "C" sim_status sim_poisson_solve_noalloc(int dim, const int n[3], const d
     for (int d = 0; d < dim; ++d)
         if (nn[d] < 2 || !(hh[d] > 0.0)) return SIM_EINVAL;
     const char* err = nullptr;
-    const size_t need = poisson_plan_bytes(dim, nn, per, 0, nullptr, nullptr, &err);
+    const size_t need = poisson_plan_bytes(dim, nn, per, 0, 0, nullptr, nullptr, &err);
     if (need == 0) return SIM_EINVAL;
     if (need > kNoAllocScratchBytes) return SIM_ENOMEM;   // grid too large for the static scratch
 
@@ -79,7 +79,7 @@ extern "C" sim_status sim_poisson_solve_noalloc(int dim, const int n[3], const d
     if (cudaMemsetAsync(ws, 0, need, st) != cudaSuccess) return SIM_ECUDA;
     PoissonPlan pl;
     std::vector<double> minv;
-    if (!poisson_plan_init(&pl, dim, nn, hh, per, 0, rtol, max_iter, ws, kNoAllocScratchBytes, &minv, &err))
+    if (!poisson_plan_init(&pl, dim, nn, hh, per, 0, 0, 0, rtol, max_iter, ws, kNoAllocScratchBytes, &minv, &err))
         return SIM_EINVAL;
     if (!poisson_upload_coarse(&pl, minv, st, &err)) return SIM_ECUDA;
     cudaError_t e = poisson_solve_host_loop(&pl, d_b, d_P, st);

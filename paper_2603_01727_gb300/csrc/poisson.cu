@@ -1448,14 +1448,15 @@ bool make_shapes(int dim, const int n[3], Shapes* s, const char** err) {
     return true;
 }
 
-int pick_top(const Shapes& s, int mg_fp32, size_t* smem_out) {
+int pick_top(const Shapes& s, int mg_fp32, long long tail_cells, size_t* smem_out) {
     if (s.nlev == 1) {
         *smem_out = 0;
         return 0;
     }
     long long thr = mg_fp32 ? kTailCellsF32 : kTailCellsF64;
-    // tuning override: LOWMACH_TAIL_CELLS = largest level handled by the tail block
-    if (const char* e = std::getenv("LOWMACH_TAIL_CELLS")) {
+    if (tail_cells > 0) {
+        thr = tail_cells;
+    } else if (const char* e = std::getenv("LOWMACH_TAIL_CELLS")) {   // tuning override
         const long long v = std::atoll(e);
         if (v > 0) thr = v;
     }
@@ -1654,13 +1655,13 @@ void set_smem_attrs() {
 }  // namespace
 
 // ------------------------------ plan ----------------------------------------
-size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg_fp32, int* nlev_out,
-                          long long* Nc_out, const char** err) {
+size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg_fp32, int tail_cells,
+                          int* nlev_out, long long* Nc_out, const char** err) {
     (void)periodic;
     Shapes s;
     if (!make_shapes(dim, n, &s, err)) return 0;
     size_t tail_smem = 0;
-    const int top = pick_top(s, mg_fp32, &tail_smem);
+    const int top = pick_top(s, mg_fp32, tail_cells, &tail_smem);
     const size_t w = mg_fp32 ? 4 : 8;
     const long long N = s.N[0];
     const long long nblk = (dim == 3) ? tile_blocks<3>(s.n[0]) : k2_blocks(s.n[0]);
@@ -1689,11 +1690,11 @@ size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg
 }
 
 bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[3], const int periodic[3],
-                       int mg_fp32, double rtol, int max_iter, void* ws, size_t ws_bytes,
-                       std::vector<double>* minv_host, const char** err) {
+                       int mg_fp32, int sweeps, int tail_cells, double rtol, int max_iter, void* ws,
+                       size_t ws_bytes, std::vector<double>* minv_host, const char** err) {
     Shapes s;
     if (!make_shapes(dim, n, &s, err)) return false;
-    const size_t need = poisson_plan_bytes(dim, n, periodic, mg_fp32, nullptr, nullptr, err);
+    const size_t need = poisson_plan_bytes(dim, n, periodic, mg_fp32, tail_cells, nullptr, nullptr, err);
     if (need == 0) return false;
     if (ws_bytes < need) {
         *err = "poisson workspace too small";
@@ -1714,7 +1715,7 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
     size_t tail_smem = 0;
     pl->dim = dim;
     pl->nlev = s.nlev;
-    pl->top = pick_top(s, mg_fp32, &tail_smem);
+    pl->top = pick_top(s, mg_fp32, tail_cells, &tail_smem);
     pl->mg_fp32 = mg_fp32;
     pl->N = s.N[0];
     pl->rtol = rtol;
@@ -1726,7 +1727,9 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
     // FP32; in FP64 a small gain together with the 128-cell tail).  Tuning
     // override LOWMACH_SWEEPS = 1 or 2.
     pl->sweeps = 2;
-    if (const char* e = std::getenv("LOWMACH_SWEEPS")) {
+    if (sweeps == 1 || sweeps == 2) {
+        pl->sweeps = sweeps;
+    } else if (const char* e = std::getenv("LOWMACH_SWEEPS")) {
         const int v = std::atoi(e);
         if (v == 1 || v == 2) pl->sweeps = v;
     }

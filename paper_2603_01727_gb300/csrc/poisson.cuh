@@ -114,16 +114,17 @@ struct PoissonPlan {
 };
 
 // Workspace bytes for a grid (no allocation).
-size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg_fp32, int* nlev_out,
-                          long long* Nc_out, const char** err);
+// tail_cells (and sweeps below): multigrid tuning, 0 = default.
+size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg_fp32, int tail_cells,
+                          int* nlev_out, long long* Nc_out, const char** err);
 
 // Carve a plan out of ws (256-byte aligned, >= poisson_plan_bytes) and compute
 // the coarsest-level inverse and the level tables on the host; minv_host gets
 // the coarse inverse followed (fast-diagonalisation plans) by S_x, S_x^T, S_y, S_y^T and the
 // inverse eigenvalue sums.
 bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[3], const int periodic[3],
-                       int mg_fp32, double rtol, int max_iter, void* ws, size_t ws_bytes,
-                       std::vector<double>* minv_host, const char** err);
+                       int mg_fp32, int sweeps, int tail_cells, double rtol, int max_iter, void* ws,
+                       size_t ws_bytes, std::vector<double>* minv_host, const char** err);
 
 // Copy the host-prepared tables into the plan's device buffers (synchronises s).
 bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& minv_host, cudaStream_t s,

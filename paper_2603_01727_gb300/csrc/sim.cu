@@ -189,6 +189,8 @@ const char* validate(const sim_params_t* p) {
     }
     if (!(p->poisson_rtol > 0.0 && p->poisson_rtol < 1.0)) return "poisson_rtol must lie in (0, 1)";
     if (p->poisson_max_iter < 1) return "poisson_max_iter must be >= 1";
+    if (p->mg_sweeps < 0 || p->mg_sweeps > 2) return "mg_sweeps must be 0 (default), 1 or 2";
+    if (p->mg_tail_cells < 0) return "mg_tail_cells must be >= 0";
     if (p->precision != SIM_FP64 && p->precision != SIM_MIXED) return "precision must be SIM_FP64 or SIM_MIXED";
     if (p->closed_system) {
         for (int d = 0; d < p->dim; ++d)
@@ -266,7 +268,7 @@ size_t layout(const sim_params_t* p, sim_t* s, char* base) {
     }
     const char* err = nullptr;
     int periodic[3] = {g.periodic[0], g.periodic[1], g.periodic[2]};
-    const size_t pb = poisson_plan_bytes(g.dim, g.n, periodic, p->precision == SIM_MIXED, nullptr, nullptr, &err);
+    const size_t pb = poisson_plan_bytes(g.dim, g.n, periodic, p->precision == SIM_MIXED, p->mg_tail_cells, nullptr, nullptr, &err);
     if (pb == 0) return 0;
     off += a256(pb);
     return off;
@@ -277,8 +279,8 @@ char* poisson_ws(const sim_params_t* p, char* base) {
     const Geom g = make_geom(p);
     const char* err = nullptr;
     int periodic[3] = {g.periodic[0], g.periodic[1], g.periodic[2]};
-    const size_t pb = a256(poisson_plan_bytes(g.dim, g.n, periodic, p->precision == SIM_MIXED, nullptr, nullptr,
-                                              &err));
+    const size_t pb = a256(poisson_plan_bytes(g.dim, g.n, periodic, p->precision == SIM_MIXED, p->mg_tail_cells,
+                                              nullptr, nullptr, &err));
     return base + layout(p, nullptr, nullptr) - pb;
 }
 
@@ -660,7 +662,8 @@ sim_status sim_create(const sim_params_t* prm, void* d_workspace, size_t workspa
     int periodic[3] = {s->g.periodic[0], s->g.periodic[1], s->g.periodic[2]};
     char* pws = poisson_ws(prm, (char*)d_workspace);
     const int* nn = s->g.n;
-    if (!poisson_plan_init(&s->pp, prm->dim, nn, s->g.h, periodic, prm->precision == SIM_MIXED, prm->poisson_rtol,
+    if (!poisson_plan_init(&s->pp, prm->dim, nn, s->g.h, periodic, prm->precision == SIM_MIXED, prm->mg_sweeps,
+                           prm->mg_tail_cells, prm->poisson_rtol,
                            prm->poisson_max_iter, pws,
                            (size_t)((char*)d_workspace + need - pws), &s->minv, &err)) {
         delete s;
@@ -1102,7 +1105,7 @@ sim_status sim_poisson_workspace_size(int dim, const int n[3], const int periodi
         if (n[d] < 2) return SIM_EINVAL;
     int nn[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
     const char* err = nullptr;
-    const size_t b = poisson_plan_bytes(dim, nn, periodic, 0, nullptr, nullptr, &err);
+    const size_t b = poisson_plan_bytes(dim, nn, periodic, 0, 0, nullptr, nullptr, &err);
     if (b == 0) return SIM_EINVAL;
     *bytes = b;
     return SIM_OK;
@@ -1119,12 +1122,12 @@ sim_status sim_poisson_solve(int dim, const int n[3], const double h[3], const i
     for (int d = 0; d < dim; ++d)
         if (nn[d] < 2 || !(hh[d] > 0.0)) return SIM_EINVAL;
     const char* err = nullptr;
-    const size_t need = poisson_plan_bytes(dim, nn, per, 0, nullptr, nullptr, &err);
+    const size_t need = poisson_plan_bytes(dim, nn, per, 0, 0, nullptr, nullptr, &err);
     if (need == 0) return SIM_EINVAL;
     if (workspace_bytes < need) return SIM_ENOMEM;
     PoissonPlan pl;
     std::vector<double> minv;
-    if (!poisson_plan_init(&pl, dim, nn, hh, per, 0, rtol, max_iter, d_workspace, workspace_bytes, &minv, &err))
+    if (!poisson_plan_init(&pl, dim, nn, hh, per, 0, 0, 0, rtol, max_iter, d_workspace, workspace_bytes, &minv, &err))
         return SIM_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (!poisson_upload_coarse(&pl, minv, st, &err)) return SIM_ECUDA;
@@ -1138,6 +1141,168 @@ sim_status sim_poisson_solve(int dim, const int n[3], const double h[3], const i
     if (iters) *iters = (int)sc[PS_ITERS];
     if (rel_resid) *rel_resid = sc[PS_RELRES];
     return ic[PI_NOCONV] ? SIM_ENOCONV : SIM_OK;
+}
+
+// ------------------------------ batches --------------------------------------
+// Many independent simulations advanced by one CUDA graph per step: each
+// simulation's whole step (its kernels and its two pressure-solve while nodes)
+// is captured on its own forked stream, so the graph holds one independent
+// branch per simulation and the GPU runs their latency-bound chains
+// concurrently.  Simulations must step in lockstep (same step count).
+}  // extern "C"
+
+struct sim_batch {
+    std::vector<sim_t*> sims;
+    cudaStream_t stream;         // caller's stream (the batch graph runs here)
+    cudaStream_t cap;            // capture origin
+    cudaEvent_t fork;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t gexec[6];
+    bool gvalid[6];
+    char err[512];
+};
+
+namespace {
+
+sim_status bfail(sim_batch_t* b, sim_status st, const char* fmt, ...) {
+    if (b) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b->err, sizeof(b->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define BCK(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return bfail(b, SIM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+void batch_drop_graphs(sim_batch_t* b) {
+    for (int k = 0; k < 6; ++k)
+        if (b->gvalid[k]) {
+            cudaGraphExecDestroy(b->gexec[k]);
+            b->gvalid[k] = false;
+        }
+}
+
+sim_status batch_capture(sim_batch_t* b, int phase) {
+    BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+    cudaError_t e = cudaEventRecord(b->fork, b->cap);
+    for (size_t i = 0; i < b->sims.size() && e == cudaSuccess; ++i) {
+        sim_t* s = b->sims[i];
+        e = cudaStreamWaitEvent(s->cap, b->fork, 0);
+        int L = 0, body = 0;
+        if (e == cudaSuccess) e = enqueue_step(s, s->nstep, s->cap, true, &L, &body);
+        s->launches_fixed_graph[phase] = L;
+        s->body_launches = body;
+        if (e == cudaSuccess) e = cudaEventRecord(b->join[i], s->cap);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return bfail(b, SIM_ECUDA, "batch capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->gexec[phase], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(b, SIM_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    b->gvalid[phase] = true;
+    return SIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sim_status sim_batch_create(sim_t* const* sims, int n, void* cuda_stream, sim_batch_t** out) {
+    if (!out || !sims || n < 1) return SIM_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j)
+            if (!sims[i] || sims[i] == sims[j]) return SIM_EINVAL;
+    sim_batch_t* b = new sim_batch();
+    b->sims.assign(sims, sims + n);
+    b->stream = (cudaStream_t)cuda_stream;
+    b->join.assign((size_t)n, nullptr);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        sim_batch_destroy(b);
+        return SIM_ECUDA;
+    }
+    *out = b;
+    return SIM_OK;
+}
+
+sim_status sim_batch_step(sim_batch_t* b, int nsteps) {
+    if (!b || nsteps < 0) return SIM_EINVAL;
+    // set-up and the first two (eager) steps go through each simulation's own path
+    for (sim_t* s : b->sims) {
+        const int need = (s->g.dim == 3) ? 0x1f : 0x1b;
+        if ((s->fields_set & need) != need) return bfail(b, SIM_ESTATE, "a simulation has no fields set");
+        if (s->need_init) batch_drop_graphs(b);
+    }
+    int done = 0;
+    while (done < nsteps && (b->sims[0]->need_init || b->sims[0]->nstep < 2)) {
+        for (sim_t* s : b->sims) {
+            const sim_status st = sim_step(s, 1);
+            if (st != SIM_OK) return bfail(b, st, "simulation step: %s", s->err);
+        }
+        ++done;
+    }
+    if (done == nsteps) return SIM_OK;
+    const long long n0 = b->sims[0]->nstep;
+    const int rb0 = b->sims[0]->rho_base;
+    for (sim_t* s : b->sims)
+        if (s->nstep != n0 || s->rho_base != rb0 || s->need_init)
+            return bfail(b, SIM_ESTATE, "the simulations of a batch must step in lockstep");
+    // the batch stream follows each simulation's stream, and vice versa at the end
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+        BCK(cudaEventRecord(b->join[i], b->sims[i]->stream));
+        BCK(cudaStreamWaitEvent(b->stream, b->join[i], 0));
+    }
+    for (; done < nsteps; ++done) {
+        const int phase = (int)(b->sims[0]->nstep % 6);
+        if (!b->gvalid[phase]) {
+            const sim_status st = batch_capture(b, phase);
+            if (st != SIM_OK) return st;
+        }
+        BCK(cudaGraphLaunch(b->gexec[phase], b->stream));
+        for (sim_t* s : b->sims) {
+            s->launches_last = -(s->launches_fixed_graph[phase] + 1);
+            after_step(s);
+        }
+    }
+    BCK(cudaEventRecord(b->fork, b->stream));
+    for (sim_t* s : b->sims) BCK(cudaStreamWaitEvent(s->stream, b->fork, 0));
+    return SIM_OK;
+}
+
+sim_status sim_batch_sync(sim_batch_t* b) {
+    if (!b) return SIM_EINVAL;
+    BCK(cudaStreamSynchronize(b->stream));
+    for (sim_t* s : b->sims) {
+        const sim_status st = sim_sync(s);
+        if (st != SIM_OK) return bfail(b, st, "%s", s->err);
+    }
+    return SIM_OK;
+}
+
+const char* sim_batch_last_error(const sim_batch_t* b) { return b ? b->err : "null handle"; }
+
+void sim_batch_destroy(sim_batch_t* b) {
+    if (!b) return;
+    batch_drop_graphs(b);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
 }
 
 }  // extern "C"

@@ -47,7 +47,8 @@ class SimParams(ctypes.Structure):
                 ("tol_reg", ctypes.c_double), ("closed_system", ctypes.c_int),
                 ("incompressible", ctypes.c_int), ("dt", ctypes.c_double),
                 ("precision", ctypes.c_int), ("poisson_rtol", ctypes.c_double),
-                ("poisson_max_iter", ctypes.c_int)]
+                ("poisson_max_iter", ctypes.c_int), ("mg_sweeps", ctypes.c_int),
+                ("mg_tail_cells", ctypes.c_int)]
 
 
 class SimIbm(ctypes.Structure):
@@ -86,6 +87,11 @@ def load():
         "sim_poisson_workspace_size": ([I, P(I), P(I), P(SZ)], I),
         "sim_poisson_solve": ([I, P(I), P(D), P(I), VP, VP, D, I, VP, SZ, VP, P(I), P(D)], I),
         "sim_poisson_solve_noalloc": ([I, P(I), P(D), P(I), VP, VP, D, I, VP, P(I), P(D)], I),
+        "sim_batch_create": ([P(VP), I, VP, P(VP)], I),
+        "sim_batch_step": ([VP, I], I),
+        "sim_batch_sync": ([VP], I),
+        "sim_batch_last_error": ([VP], ctypes.c_char_p),
+        "sim_batch_destroy": ([VP], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -100,7 +106,8 @@ def exported_symbols():
             "sim_sync", "sim_query", "sim_last_error", "sim_destroy", "sim_time_kernel", "sim_state_size",
             "sim_state_save",
             "sim_state_load", "sim_poisson_workspace_size",
-            "sim_poisson_solve", "sim_poisson_solve_noalloc"]
+            "sim_poisson_solve", "sim_poisson_solve_noalloc", "sim_batch_create", "sim_batch_step",
+            "sim_batch_sync", "sim_batch_last_error", "sim_batch_destroy"]
 
 
 class SimError(RuntimeError):
@@ -123,6 +130,8 @@ def params_struct(prm):
         setattr(p, k, float(prm[k]))
     for k in ("closed_system", "incompressible", "precision", "poisson_max_iter"):
         setattr(p, k, int(prm[k]))
+    p.mg_sweeps = int(prm.get("mg_sweeps", 0))
+    p.mg_tail_cells = int(prm.get("mg_tail_cells", 0))
     return p
 
 
@@ -310,3 +319,46 @@ def poisson_solve_noalloc(b, P, h, periodic, rtol=1e-12, max_iter=200, stream=No
                                            ctypes.c_void_p(st.cuda_stream), ctypes.byref(it), ctypes.byref(rr))
     _check(lib, status)
     return it.value, rr.value
+
+
+class Batch:
+    """Independent simulations advanced together, one CUDA graph per step
+    (sim_batch_* of the C ABI).  The Simulation objects stay owned by the
+    caller and must outlive the batch."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        self.lib = load()
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
+        st = stream if stream is not None else self.sims[0].stream
+        self.stream = st
+        h = ctypes.c_void_p()
+        _check(self.lib, self.lib.sim_batch_create(arr, len(self.sims), ctypes.c_void_p(st.cuda_stream),
+                                                   ctypes.byref(h)))
+        self.h = h
+        self.torch = torch
+
+    def _check(self, st):
+        if st != SIM_OK:
+            raise SimError(st, self.lib.sim_batch_last_error(self.h).decode())
+
+    def step(self, nsteps=1):
+        self._check(self.lib.sim_batch_step(self.h, int(nsteps)))
+
+    def sync(self):
+        self._check(self.lib.sim_batch_sync(self.h))
+
+    def cells(self):
+        return sum(int(s.query(SIM_Q_NCELLS)) for s in self.sims)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sim_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,106 @@
+"""Batched flames (sim_batch_*): independent simulations of uneven sizes
+advanced by one CUDA graph per step.  A batch must give bit-for-bit the
+result of stepping each simulation on its own, and its members keep their
+parity with the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import step as S
+from oracle.operators import V
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2603_01727_gb300 import build
+    build.build()
+
+
+def _flames(precision):
+    out = []
+    for (nx, ny), Re, zst, ratio in (((32, 64), 120.0, 0.05, 6.0), ((48, 96), 300.0, 0.07, 4.5),
+                                     ((64, 128), 200.0, 0.055, 7.5)):
+        prm, geo, f = W.slot_burner(nx, ny, Re=Re, Z_st=zst, density_ratio=ratio, Da_ib=max(1e-4, (2.0 / nx) ** 2))
+        prm["precision"] = precision
+        prm["poisson_rtol"] = 1e-12
+        out.append((prm, geo, f))
+    return out
+
+
+def _sims(flames, stream):
+    from paper_2603_01727_gb300.lowmach import Simulation
+    sims = []
+    for prm, geo, f in flames:
+        s = Simulation(prm, geo, stream=stream)
+        s.set_fields(f)
+        sims.append(s)
+    return sims
+
+
+@pytest.mark.parametrize("precision", [W.FP64, W.MIXED])
+def test_batch_is_bitwise_equal_to_separate_steps(precision):
+    import torch
+    from paper_2603_01727_gb300.lowmach import Batch
+    flames = _flames(precision)
+    stream = torch.cuda.Stream()
+    alone = _sims(flames, stream)
+    for s in alone:
+        s.step(9)                        # eager steps, then every rotation phase of the graphs
+        s.sync()
+    members = _sims(flames, stream)
+    batch = Batch(members, stream=stream)
+    batch.step(4)
+    batch.step(5)
+    batch.sync()
+    for a, b in zip(alone, members):
+        names = ["U", "V", "Z", "H", "T", "RHO", "P", "FX", "FY"]
+        for k in names:
+            assert np.array_equal(a.get(k), b.get(k)), k
+
+
+def test_batch_member_matches_oracle():
+    import torch
+    from paper_2603_01727_gb300.lowmach import Batch
+    flames = _flames(W.FP64)
+    stream = torch.cuda.Stream()
+    members = _sims(flames, stream)
+    batch = Batch(members, stream=stream)
+    batch.step(6)
+    batch.sync()
+    prm, geo, f = flames[1]
+    pb = S.Problem(prm, geo)
+    st = S.initial_state(pb, f["v"], f["Z"], f["H"])
+    for _ in range(6):
+        st = S.advance(pb, st)
+    g = pb.g
+    ref = {"U": V(st.v[0], g), "V": V(st.v[1], g), "Z": V(st.Z, g), "T": V(st.T, g), "P": V(st.P, g)}
+    for k, r in ref.items():
+        err = float(np.max(np.abs(members[1].get(k) - r)) / np.max(np.abs(r)))
+        assert err <= 1e-9, (k, err)
+
+
+def test_batch_requires_lockstep():
+    import torch
+    from paper_2603_01727_gb300.lowmach import Batch, SimError, SIM_ESTATE
+    flames = _flames(W.MIXED)[:2]
+    stream = torch.cuda.Stream()
+    members = _sims(flames, stream)
+    members[0].step(3)
+    members[1].step(4)
+    members[0].sync()
+    members[1].sync()
+    batch = Batch(members, stream=stream)
+    with pytest.raises(SimError) as e:
+        batch.step(1)
+    assert e.value.status == SIM_ESTATE
+
+
+def test_autotuner_picks_a_measured_candidate():
+    from paper_2603_01727_gb300 import autotune
+    prm, geo, f = _flames(W.MIXED)[0]
+    best, table = autotune.tune(prm, geo, f, candidates=((2, 0), (1, 0)), copies=2)
+    assert best in table and all(t > 0 for t in table.values())
+    assert table[best] == min(table.values())

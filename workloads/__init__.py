@@ -37,7 +37,7 @@ def _base_params():
         Re=100.0, Pr=0.7, inv_Fr2=0.0, Le_F=1.0, Le_O=1.0, gamma=1.4, sigma=0.7,
         Z_st=0.055, density_ratio=7.0, eps_reg=0.5, tol_reg=1e-3,
         closed_system=0, incompressible=0, dt=0.0,
-        precision=FP64, poisson_rtol=1e-10, poisson_max_iter=200)
+        precision=FP64, poisson_rtol=1e-10, poisson_max_iter=200, mg_sweeps=0, mg_tail_cells=0)
 
 
 def paper_scalars(Z_st, ratio):
@@ -142,7 +142,8 @@ def periodic_blobs(n=64, seed=SEED, cfl=0.4, nblobs=8):
     return prm, None, fields
 
 
-def slot_burner(nx=256, ny=512, cfl=0.4, Re=200.0, profile=None, U_coflow=0.2):
+def slot_burner(nx=256, ny=512, cfl=0.4, Re=200.0, profile=None, U_coflow=0.2, Z_st=0.055, density_ratio=7.0,
+                Da_ib=1e-4):
     """2D planar slot burner: [0,1] x [0,2], periodic in x; bottom inflow of air
     (v = (0, U_coflow), Z = 0, H = H_inf) outside the burner foot; top outflow.
     Immersed rectangular burner 0.1 x 0.3 standing on the bottom boundary at
@@ -154,10 +155,10 @@ def slot_burner(nx=256, ny=512, cfl=0.4, Re=200.0, profile=None, U_coflow=0.2):
     prm = _base_params()
     prm.update(dim=2, n=[nx, ny, 1], L=[1.0, 2.0, 1.0], Re=Re, Pr=0.7,
                bc=[[PERIODIC, PERIODIC], [INFLOW, OUTFLOW], [PERIODIC, PERIODIC]],
-               inflow_v=[0.0, U_coflow, 0.0])
+               inflow_v=[0.0, U_coflow, 0.0], Z_st=Z_st, density_ratio=density_ratio)
     S, Q, H_inf, Z_fuel = paper_scalars(prm["Z_st"], prm["density_ratio"])
     prm.update(inflow_Z=0.0, inflow_H=H_inf)
-    Da = 1e-4
+    Da = Da_ib
     geo = dict(kind=IBM_SLOT, center=[0.5, 0.15, 0.0], half=[0.05, 0.15, 0.0], radius=0.0,
                Da_ib=Da, rho_b=1.0, U_b=1.0, Z_ib=Z_fuel, H_ib=H_inf,
                profile=None if profile is None else list(profile))
@@ -176,6 +177,29 @@ def slot_burner(nx=256, ny=512, cfl=0.4, Re=200.0, profile=None, U_coflow=0.2):
     prm["dt"] = stable_dt((nx, ny), (1.0, 2.0), Re, prm["Pr"], prm["density_ratio"],
                           prm["sigma"], 1.0, cfl, Da_ib=Da)
     return prm, geo, dict(v=[u, v], Z=Z, H=H)
+
+
+BATCH_GRIDS = ((64, 128), (96, 192), (128, 256))
+
+
+def batched_flames(count=256, seed=SEED, precision=MIXED):
+    """Independent 2D slot-burner flames of uneven sizes: grid drawn uniformly
+    from 64x128, 96x192, 128x256; inlet Re ~ U[50, 400]; Z_st ~ U[0.04, 0.08];
+    density ratio ~ U[4, 8].  Da_ib = max(1e-4, (2 dx)^2), so the Brinkman
+    layer sqrt(Da_ib) spans at least two cells on the coarsest grids.
+    Returns a list of (prm, geo, fields)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        nx, ny = BATCH_GRIDS[int(rng.integers(0, len(BATCH_GRIDS)))]
+        Re = float(rng.uniform(50.0, 400.0))
+        Z_st = float(rng.uniform(0.04, 0.08))
+        ratio = float(rng.uniform(4.0, 8.0))
+        Da = max(1e-4, (2.0 / nx) ** 2)
+        prm, geo, f = slot_burner(nx, ny, Re=Re, Z_st=Z_st, density_ratio=ratio, Da_ib=Da)
+        prm["precision"] = precision
+        out.append((prm, geo, f))
+    return out
 
 
 def sphere_burner(n=192, cfl=0.4, Re=150.0, seed=SEED, rms=0.01):
