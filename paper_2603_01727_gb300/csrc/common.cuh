@@ -61,6 +61,33 @@ struct Phys {
 };
 
 // ---------------------------------------------------------------------------
+// Forward-mode dual number (value, derivative): instantiating a cell function
+// with Dual evaluates its exact derivative along one seeded input, which the
+// adjoint kernels assemble into transposed Jacobian-vector products.
+// ---------------------------------------------------------------------------
+struct Dual {
+    double v, d;
+    __host__ __device__ Dual() : v(0.0), d(0.0) {}
+    __host__ __device__ Dual(double x) : v(x), d(0.0) {}
+    __host__ __device__ Dual(double x, double dx) : v(x), d(dx) {}
+};
+__host__ __device__ inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+__host__ __device__ inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+__host__ __device__ inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+__host__ __device__ inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+__host__ __device__ inline Dual operator/(Dual a, Dual b) {
+    const double q = a.v / b.v;
+    return Dual(q, (a.d - q * b.d) / b.v);
+}
+__host__ __device__ inline Dual& operator+=(Dual& a, Dual b) { return a = a + b; }
+__host__ __device__ inline Dual& operator-=(Dual& a, Dual b) { return a = a - b; }
+__device__ inline double tanh_c(double x) { return tanh(x); }
+__device__ inline Dual tanh_c(Dual x) {
+    const double t = tanh(x.v);
+    return Dual(t, (1.0 - t * t) * x.d);
+}
+
+// ---------------------------------------------------------------------------
 // Deterministic block reduction (fixed tree for a fixed block size).
 // ---------------------------------------------------------------------------
 template <int NT>

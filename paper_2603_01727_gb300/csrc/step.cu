@@ -195,39 +195,59 @@ __global__ void k_density(Geom g, const double* __restrict__ T, double* __restri
 // C is the arithmetic type of the residual terms and of the stored residual
 // history (double in both precision modes, see launch_residual); the state
 // updates X = X_b + dt * combination are FP64.
-template <int DIM, class C>
-__global__ void __launch_bounds__(NT) k_residual(Geom g, Phys ph, ResidArgs a) {
-    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
-    if (t >= g.ncell) return;
-    const long long c = pad_index(g, t);
-    const C* Rrd[5];
-    C* Rst[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        Rrd[k] = reinterpret_cast<const C*>(a.Rrd[k]);
-        Rst[k] = reinterpret_cast<C*>(a.Rst[k]);
-    }
+// Fields read by the stage stencil, by loader id.
+enum : int {
+    RF_V0 = 0, RF_V1 = 1, RF_V2 = 2, RF_Z = 3, RF_H = 4, RF_RHO = 5, RF_KAP = 6,
+    RF_F0 = 7, RF_F1 = 8, RF_F2 = 9, RF_T = 10, RF_VIB0 = 11, RF_VIB1 = 12, RF_VIB2 = 13, RF_N = 14
+};
 
-    // dp0/dt for the H source (Eqs 3.5, 3.14)
-    const double p0dot = (a.wden != 0.0) ? (a.w0 * a.sc[a.p0a] + a.w1 * a.sc[a.p0b] + a.w2 * a.sc[a.p0c]) * a.iwden
-                                         : 0.0;
+// Plain FP64 loads of the stencil's inputs.
+struct PlainLoad {
+    const ResidArgs* a;
+    __device__ __forceinline__ double operator()(int f, long long i) const {
+        switch (f) {
+            case RF_V0: return a->v[0][i];
+            case RF_V1: return a->v[1][i];
+            case RF_V2: return a->v[2][i];
+            case RF_Z: return a->Z[i];
+            case RF_H: return a->H[i];
+            case RF_RHO: return a->rho[i];
+            case RF_KAP: return a->kap[i];
+            case RF_F0: return a->F[0][i];
+            case RF_F1: return a->F[1][i];
+            case RF_F2: return a->F[2][i];
+            case RF_T: return a->T[i];
+            case RF_VIB0: return a->vib[0][i];
+            case RF_VIB1: return a->vib[1][i];
+            default: return a->vib[2][i];
+        }
+    }
+};
+
+// Stage residuals at padded cell c (Eqs 3.1-3.4, 3.7-3.8, 3.26, 3.30-3.32):
+// R[i] = Res_v,i + f_v,i + F_v,i (i < DIM), R[3] = Res_Z, R[4] = Res_H.  C is
+// the arithmetic type (double, or a dual number for the adjoint); ld(f, i)
+// returns input field f at padded index i as a C.
+template <int DIM, class C, class LD>
+__device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, const ResidArgs& a, long long c,
+                                              double p0dot, const LD& ld, C R[5]) {
     const C half = (C)0.5;
-    const C rho_c = (C)a.rho[c];
-    const C kap_c = (C)a.kap[c];
-    const C Zc = (C)a.Z[c], Hc = (C)a.H[c];
+    const C rho_c = ld(RF_RHO, c);
+    const C kap_c = ld(RF_KAP, c);
+    const C Zc = ld(RF_Z, c), Hc = ld(RF_H, c);
 
     // scalar convection (Eq 3.26b) and diffusion div(kappa grad .)
-    C convZ = 0, convH = 0, difZ = 0, difH = 0;
+    C convZ = 0.0, convH = 0.0, difZ = 0.0, difH = 0.0;
     C kf_lo[DIM], kf_hi[DIM];
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
         const long long s = g.s[j];
         const C ih = (C)g.ih[j];
-        const C Flo = (C)a.F[j][c], Fhi = (C)a.F[j][c + s];
-        kf_lo[j] = half * ((C)a.kap[c - s] + kap_c);
-        kf_hi[j] = half * (kap_c + (C)a.kap[c + s]);
-        const C dZlo = (Zc - (C)a.Z[c - s]) * ih, dZhi = ((C)a.Z[c + s] - Zc) * ih;
-        const C dHlo = (Hc - (C)a.H[c - s]) * ih, dHhi = ((C)a.H[c + s] - Hc) * ih;
+        const C Flo = ld(RF_F0 + j, c), Fhi = ld(RF_F0 + j, c + s);
+        kf_lo[j] = half * (ld(RF_KAP, c - s) + kap_c);
+        kf_hi[j] = half * (kap_c + ld(RF_KAP, c + s));
+        const C dZlo = (Zc - ld(RF_Z, c - s)) * ih, dZhi = (ld(RF_Z, c + s) - Zc) * ih;
+        const C dHlo = (Hc - ld(RF_H, c - s)) * ih, dHhi = (ld(RF_H, c + s) - Hc) * ih;
         convZ += half * (Flo * dZlo + Fhi * dZhi);
         convH += half * (Flo * dHlo + Fhi * dHhi);
         difZ += (kf_hi[j] * dZhi - kf_lo[j] * dZlo) * ih;
@@ -236,17 +256,15 @@ __global__ void __launch_bounds__(NT) k_residual(Geom g, Phys ph, ResidArgs a) {
 
     // momentum: convection Eq 3.26a, viscous stress Eq 2.46 on the interfaces
     const C two3 = (C)(2.0 / 3.0);
-    C Rv[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-        const double* vi = a.v[i];
-        C conv = 0, visc = 0;
+        C conv = 0.0, visc = 0.0;
 #pragma unroll
         for (int j = 0; j < DIM; ++j) {
             const long long s = g.s[j];
             const C ih = (C)g.ih[j];
-            const C Flo = (C)a.F[j][c], Fhi = (C)a.F[j][c + s];
-            const C vl = (C)vi[c - s], vc = (C)vi[c], vh = (C)vi[c + s];
+            const C Flo = ld(RF_F0 + j, c), Fhi = ld(RF_F0 + j, c + s);
+            const C vl = ld(RF_V0 + i, c - s), vc = ld(RF_V0 + i, c), vh = ld(RF_V0 + i, c + s);
             conv += (Fhi * (half * (vc + vh)) - Flo * (half * (vl + vc))) * ih;
             C tau_f[2];
 #pragma unroll
@@ -260,10 +278,9 @@ __global__ void __launch_bounds__(NT) k_residual(Geom g, Phys ph, ResidArgs a) {
                     dvj = dvi;
                 } else {
                     const long long si = g.s[i];
-                    const double* vj = a.v[j];
                     const C hi2 = (C)(0.5 * g.ih[i]);
-                    const C da = ((C)vj[ca + si] - (C)vj[ca - si]) * hi2;
-                    const C db = ((C)vj[cb + si] - (C)vj[cb - si]) * hi2;
+                    const C da = (ld(RF_V0 + j, ca + si) - ld(RF_V0 + j, ca - si)) * hi2;
+                    const C db = (ld(RF_V0 + j, cb + si) - ld(RF_V0 + j, cb - si)) * hi2;
                     dvj = half * (da + db);
                 }
                 C tau = kf * (dvi + dvj);
@@ -273,10 +290,9 @@ __global__ void __launch_bounds__(NT) k_residual(Geom g, Phys ph, ResidArgs a) {
                     for (int k = 0; k < DIM; ++k) {
                         if (k == j) continue;
                         const long long sk = g.s[k];
-                        const double* vk = a.v[k];
                         const C hk2 = (C)(0.5 * g.ih[k]);
-                        const C da = ((C)vk[ca + sk] - (C)vk[ca - sk]) * hk2;
-                        const C db = ((C)vk[cb + sk] - (C)vk[cb - sk]) * hk2;
+                        const C da = (ld(RF_V0 + k, ca + sk) - ld(RF_V0 + k, ca - sk)) * hk2;
+                        const C db = (ld(RF_V0 + k, cb + sk) - ld(RF_V0 + k, cb - sk)) * hk2;
                         div = div + half * (da + db);
                     }
                     tau = tau - two3 * kf * div;
@@ -285,20 +301,20 @@ __global__ void __launch_bounds__(NT) k_residual(Geom g, Phys ph, ResidArgs a) {
             }
             visc += (tau_f[1] - tau_f[0]) * ih;
         }
-        C R = -conv + (C)ph.PrPe * visc;
-        if (i == 1 && ph.inv_Fr2 != 0.0) R = R + (C)ph.inv_Fr2 * ((C)1 - rho_c);              // Eq 3.8b
+        C Rm = -conv + (C)ph.PrPe * visc;
+        if (i == 1 && ph.inv_Fr2 != 0.0) Rm = Rm + (C)ph.inv_Fr2 * ((C)1.0 - rho_c);                  // Eq 3.8b
         if (a.ibm && a.chi[c])
-            R = R - (C)(ph.PrPe * a.inv_Da) * kap_c * ((C)vi[c] - (C)a.vib[i][c]);           // Eq 3.30
-        Rv[i] = R;
+            Rm = Rm - (C)(ph.PrPe * a.inv_Da) * kap_c * (ld(RF_V0 + i, c) - ld(RF_VIB0 + i, c));    // Eq 3.30
+        R[i] = Rm;
     }
 
     // Lewis and N coefficients (Eq 3.35)
     C iLePe = (C)ph.iLePe, Nn = (C)ph.N_O;
     if (ph.Le_F != ph.Le_O) {
-        const C th = half * ((C)1 + (C)tanh(ph.k * ((double)Zc - 1.0)));
+        const C th = half * ((C)1.0 + tanh_c(ph.k * (Zc - (C)1.0)));
         const C Le = (C)(ph.Le_F - ph.Le_O) * th + (C)ph.Le_O;
         Nn = (C)(ph.N_F - ph.N_O) * th + (C)ph.N_O;
-        iLePe = (C)1 / (Le * (C)ph.Pe);
+        iLePe = (C)1.0 / (Le * (C)ph.Pe);
     }
     const C iPe = (C)ph.iPe;
     C bZ = -convZ + difZ * iLePe;
@@ -309,9 +325,33 @@ __global__ void __launch_bounds__(NT) k_residual(Geom g, Phys ph, ResidArgs a) {
         bH = bH - kap_c * (Hc - (C)a.H_ib) * iPe * iDa;                                     // Eq 3.32
     }
     // 1/rho = T / p0 (Eq 2.49)
-    const C irho = (C)(a.T[c] * a.sc[a.p0r + SC_INV_OFF]);
-    const C RZ = bZ * irho;
-    const C RH = bH * irho;
+    const C irho = ld(RF_T, c) * (C)a.sc[a.p0r + SC_INV_OFF];
+    R[3] = bZ * irho;
+    R[4] = bH * irho;
+}
+
+template <int DIM, class C>
+__global__ void __launch_bounds__(NT) k_residual(Geom g, Phys ph, ResidArgs a) {
+    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+    if (t >= g.ncell) return;
+    const long long c = pad_index(g, t);
+    const C* Rrd[5];
+    C* Rst[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        Rrd[k] = reinterpret_cast<const C*>(a.Rrd[k]);
+        Rst[k] = reinterpret_cast<C*>(a.Rst[k]);
+    }
+    // dp0/dt for the H source (Eqs 3.5, 3.14)
+    const double p0dot = (a.wden != 0.0) ? (a.w0 * a.sc[a.p0a] + a.w1 * a.sc[a.p0b] + a.w2 * a.sc[a.p0c]) * a.iwden
+                                         : 0.0;
+    C Rall[5];
+    residual_cell<DIM, C>(g, ph, a, c, p0dot, PlainLoad{&a}, Rall);
+    C Rv[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) Rv[i] = Rall[i];
+    const C RZ = Rall[3], RH = Rall[4];
+    const C half = (C)0.5;
 
     // combination (FP64 state update)
     const double dt = a.dt;
@@ -638,6 +678,448 @@ __global__ void k_u8_to_double(Geom g, const uint8_t* __restrict__ src, double* 
     dst[t] = (double)src[pad_index(g, t)];
 }
 
+// ============================================================================
+// Discrete adjoint (reverse mode) of the step's kernels.  Every adjoint kernel
+// takes lambda (the adjoint of the forward kernel's outputs) and ADDS the
+// adjoint of its inputs, so contributions from several uses accumulate.
+// ============================================================================
+
+// Loader that seeds one input value (field sf at padded index si): the stencil
+// evaluated with it returns, in .d, the derivative along that input.
+struct DualLoad {
+    PlainLoad p;
+    int sf;
+    long long si;
+    __device__ __forceinline__ Dual operator()(int f, long long i) const {
+        return Dual(p(f, i), (f == sf && i == si) ? 1.0 : 0.0);
+    }
+};
+
+__device__ __forceinline__ bool padded_interior(const Geom& g, const int q[3]) {
+    for (int d = 0; d < g.dim; ++d)
+        if (q[d] < 1 || q[d] > g.n[d]) return false;
+    return true;
+}
+
+// Stencil transpose by gather: for padded cell j and each input field f,
+//   lam_f[j] += sum_{interior c within one cell of j} sum_o dR_o(c)/df(j) lamR_o(c),
+// each derivative taken exactly by evaluating residual_cell at c in dual
+// numbers with f(j) seeded.  lamR: adjoint of the residuals (v0..v2, Z, H).
+template <int DIM>
+__global__ void __launch_bounds__(NT)
+    k_residual_adj(Geom g, Phys ph, ResidArgs a, double p0dot, AdjR lr, AdjIn li) {
+    const long long j = (long long)blockIdx.x * NT + threadIdx.x;
+    if (j >= g.npad) return;
+    int q[3];
+    padded_coords(g, j, q);
+    const int fields[] = {RF_V0, RF_V1, RF_V2, RF_Z, RF_H, RF_KAP, RF_F0, RF_F1, RF_F2, RF_T, RF_VIB0, RF_VIB1,
+                          RF_VIB2, RF_RHO};
+    for (int fi = 0; fi < 14; ++fi) {
+        const int f = fields[fi];
+        if (!li.out[f]) continue;
+        if ((f == RF_V2 || f == RF_F2 || f == RF_VIB2) && DIM < 3) continue;
+        double acc = 0.0;
+        const int oz = (DIM == 3) ? 1 : 0;
+        for (int dz = -oz; dz <= oz; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int qc[3] = {q[0] + dx, q[1] + dy, q[2] + dz};
+                    if (!padded_interior(g, qc)) continue;
+                    const long long c = j + dx + (long long)dy * g.s[1] + (long long)dz * g.s[2];
+                    Dual R[5];
+                    residual_cell<DIM, Dual>(g, ph, a, c, p0dot, DualLoad{PlainLoad{&a}, f, j}, R);
+                    for (int o = 0; o < DIM; ++o) acc += R[o].d * lr.R[o][c];
+                    acc += R[3].d * lr.R[3][c] + R[4].d * lr.R[4][c];
+                }
+        li.out[f][j] += acc;
+    }
+}
+
+// Ghost fill of direction d transposed: ghost = s * adjacent (+ constant) or a
+// periodic copy, so lam_adjacent += s * lam_ghost and the ghost's lambda is
+// consumed (zeroed).  Directions are transposed in reverse order.
+__global__ void k_ghost_adj(Geom g, const uint8_t* __restrict__ klo, const uint8_t* __restrict__ khi, int d,
+                            int periodic, GhostJob job) {
+    const int a = (d == 0) ? 1 : 0;
+    const int b = (d == 2) ? 1 : 2;
+    const long long nslab = (long long)g.p[a] * g.p[b];
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nslab) return;
+    const int ca = (int)(q % g.p[a]);
+    const int cb = (int)(q / g.p[a]);
+    const long long base = (long long)ca * g.s[a] + (long long)cb * g.s[b];
+    const int n = g.n[d];
+    const long long sd = g.s[d];
+    const long long i_g0 = base, i_1 = base + sd, i_n = base + (long long)n * sd, i_gh = base + (long long)(n + 1) * sd;
+    for (int f = 0; f < job.nf; ++f) {
+        double* x = job.f[f];
+        const int what = job.what[f];
+        if (periodic) {
+            x[i_n] += x[i_g0];
+            x[i_1] += x[i_gh];
+            x[i_g0] = 0.0;
+            x[i_gh] = 0.0;
+            continue;
+        }
+        const bool vel = what >= GW_V0;
+        const bool normal = vel && (what - GW_V0 == d);
+        for (int side = 0; side < 2; ++side) {
+            const long long ig = side ? i_gh : i_g0;
+            const long long ia = side ? i_n : i_1;
+            const int kind = side ? khi[q] : klo[q];
+            double sg;
+            if (kind == BC_INFLOW) sg = -1.0;
+            else if (kind == BC_OUTFLOW) sg = 1.0;
+            else if (kind == BC_WALL) sg = vel ? -1.0 : 1.0;
+            else sg = normal ? -1.0 : 1.0;
+            x[ia] += sg * x[ig];
+            x[ig] = 0.0;
+        }
+    }
+}
+
+// State relation transposed (FP64 path, open system: rho = 1/T, kappa = T^sigma,
+// T = cT (cA (|x| + log1p(e^-2|x|)) + cB (Z - 1) + H), x = k (Z - 1)):
+// dT/dZ = cT (cA k tanh(x) + cB), dT/dH = cT, drho/dT = -1/T^2,
+// dkappa/dT = sigma kappa / T.
+__global__ void k_state_adj(Geom g, Phys ph, const double* __restrict__ Z, const double* __restrict__ T,
+                            const double* __restrict__ kap, double* lT, double* lrho, double* lkap, double* lZ,
+                            double* lH) {
+    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+    if (t >= g.ncell) return;
+    const long long c = pad_index(g, t);
+    const double Tv = T[c];
+    const double lt = lT[c] - lrho[c] / (Tv * Tv) + lkap[c] * ph.sigma * kap[c] / Tv;
+    const double x = ph.k * (Z[c] - 1.0);
+    lZ[c] += lt * ph.cT * (ph.cA * ph.k * tanh(x) + ph.cB);
+    lH[c] += lt * ph.cT;
+    lT[c] = 0.0;      // T, rho, kappa are outputs of the state relation
+    lrho[c] = 0.0;
+    lkap[c] = 0.0;
+}
+
+// Face fluxes and Poisson right-hand side transposed, part A.  lFt = total
+// adjoint of every interface flux after the outflow shift: the adjoint of the
+// final flux (which the projection passes through unchanged) plus its uses in
+// b = d_t rho - S_m + sum_j (F_j(hi) - F_j(lo)) / h_j.  Block partials of the
+// adjoint of the uniform outflow shift, sum(lFt over high outflow faces) -
+// sum(lFt over low outflow faces).
+template <int DIM>
+__global__ void k_flux_adj_a(Geom g, Bnd bnd, FluxAdj a) {
+    __shared__ double sm[NT / 32];
+    double acc = 0.0;
+    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
+        const long long c = pad_index(g, t);
+        int ct[3], q[3];
+        interior_coords(g, t, ct);
+        padded_coords(g, c, q);
+        const double lb = a.lb[t];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+            const long long s = g.s[j];
+            const long long st = compact_stride(g, j);
+            const double ih = g.ih[j];
+            const int n = g.n[j];
+            const double lo = a.lF[j][c] - lb * ih + (ct[j] > 0 ? a.lb[t - st] * ih : 0.0);
+            a.lFt[j][c] = lo;
+            if (ct[j] == 0 && !g.periodic[j] && bnd.kind[j][0][slab_index(g, j, q)] == BC_OUTFLOW) acc -= lo;
+            if (ct[j] == n - 1) {
+                const double hi = a.lF[j][c + s] + lb * ih;
+                a.lFt[j][c + s] = hi;
+                if (!g.periodic[j] && bnd.kind[j][1][slab_index(g, j, q)] == BC_OUTFLOW) acc += hi;
+            }
+        }
+    }
+    acc = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = acc;
+}
+
+// Part B: adjoint of the mass-balance total (shift = -total / area), of the
+// density rate (BDF weights onto the three density levels), of S_m, and of
+// the provisional momentum through the face interpolation and the extrapolated
+// outflow faces.  Consumes lF (zeroed: the fluxes are outputs of this stage).
+template <int DIM>
+__global__ void k_flux_adj_b(Geom g, Bnd bnd, FluxAdj a, int np) {
+    __shared__ double sm[NT / 32];
+    const double lshift = sum_partials<NT>(a.part, np, sm);
+    const double area = a.sc[SC_OUT_AREA];
+    const double ltot = (area > 0.0) ? -lshift / area : 0.0;
+    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
+        const long long c = pad_index(g, t);
+        int ct[3], q[3];
+        interior_coords(g, t, ct);
+        padded_coords(g, c, q);
+        const double ldrho = a.lb[t] + ltot * g.dV;
+        const double iden = 1.0 / a.bdf_den;
+        a.lrho_new[c] += a.bdf_c0 * iden * ldrho;
+        a.lrho_n[c] += a.bdf_c1 * iden * ldrho;
+        if (a.bdf_c2 != 0.0) a.lrho_prev[c] += a.bdf_c2 * iden * ldrho;
+        if (a.lSm) a.lSm[c] -= ldrho;
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+            const long long s = g.s[j];
+            const int n = g.n[j];
+            const double dA = g.dV * g.ih[j];
+            const bool per = g.periodic[j];
+            double lm = 0.0;
+            if (ct[j] > 0 || per) lm += 0.5 * a.lFt[j][c];
+            else if (bnd.kind[j][0][slab_index(g, j, q)] == BC_OUTFLOW) lm += a.lFt[j][c] - ltot * dA;
+            if (ct[j] < n - 1 || per) lm += 0.5 * a.lFt[j][c + s];
+            else if (bnd.kind[j][1][slab_index(g, j, q)] == BC_OUTFLOW) lm += a.lFt[j][c + s] + ltot * dA;
+            if (per && ct[j] == 0) lm += 0.5 * a.lFt[j][c + (long long)n * s];          // last cell's wrap face
+            if (per && ct[j] == n - 1) lm += 0.5 * a.lFt[j][c - (long long)(n - 1) * s];  // first cell's low face
+            a.lmom[j][c] += lm;
+            a.lF[j][c] = 0.0;
+            if (ct[j] == n - 1) a.lF[j][c + s] = 0.0;
+        }
+    }
+}
+
+// Coefficients of P at position k (one direction) in P_c, P_minus and P_plus of
+// the projection at position i (Eqs 3.27-3.28 extrapolation at walls/outflow).
+struct PCoef {
+    double c, m, p;
+};
+__device__ __forceinline__ PCoef proj_coef(int i, int k, int n, int per, double eA, double eB, double eC) {
+    PCoef r;
+    r.c = (i == k) ? 1.0 : 0.0;
+    if (i > 0) r.m = (k == i - 1) ? 1.0 : 0.0;
+    else if (per) r.m = (k == n - 1) ? 1.0 : 0.0;
+    else r.m = (k == i ? eA : 0.0) + (k == i + 1 ? eB : 0.0) + (k == i + 2 ? eC : 0.0);
+    if (i < n - 1) r.p = (k == i + 1) ? 1.0 : 0.0;
+    else if (per) r.p = (k == 0) ? 1.0 : 0.0;
+    else r.p = (k == i ? eA : 0.0) + (k == i - 1 ? eB : 0.0) + (k == i - 2 ? eC : 0.0);
+    return r;
+}
+
+// Projection transposed (Eqs 3.23, 3.25, 3.27-3.28): from the adjoints of the
+// projected velocity lv (interior) and of the final fluxes lF (unchanged: the
+// provisional fluxes carry them on), adds lmom += lv / rho,
+// lT += lv (mom - delta_2 P / 2h) / p0, and sets lP (compact) by gathering, for
+// every pressure value, the projection positions that read it.
+template <int DIM>
+__global__ void k_project_adj(Geom g, ProjAdj a) {
+    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+    if (t >= g.ncell) return;
+    const long long c = pad_index(g, t);
+    int ct[3];
+    interior_coords(g, t, ct);
+    const double ip0 = a.sc[a.p0_slot + SC_INV_OFF];
+    const double irho = a.T[c] * ip0;
+    const double Pc = a.P[t];
+    double lT = 0.0, lP = 0.0;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        const long long s = g.s[j];
+        const long long st = compact_stride(g, j);
+        const int n = g.n[j];
+        const int per = g.periodic[j];
+        const double ih = g.ih[j];
+        double Pm, Pp;
+        if (ct[j] > 0) Pm = a.P[t - st];
+        else if (per) Pm = a.P[t + (long long)(n - 1) * st];
+        else Pm = a.eA * Pc + a.eB * a.P[t + st] + a.eC * a.P[t + 2 * st];
+        if (ct[j] < n - 1) Pp = a.P[t + st];
+        else if (per) Pp = a.P[t - (long long)(n - 1) * st];
+        else Pp = a.eA * Pc + a.eB * a.P[t - st] + a.eC * a.P[t - 2 * st];
+        const double lv = a.lv[j][c];
+        a.lmom[j][c] += lv * irho;
+        lT += lv * (a.mom[j][c] - (Pp - Pm) * (0.5 * ih)) * ip0;
+
+        // gather over the positions i whose projection reads P at k = ct[j]
+        const int k = ct[j];
+        int cand[7];
+        int nc = 0;
+        for (int i = (k - 2 > 0 ? k - 2 : 0); i <= (k + 2 < n - 1 ? k + 2 : n - 1); ++i) cand[nc++] = i;
+        if (per && k == n - 1 && 0 < k - 2) cand[nc++] = 0;
+        if (per && k == 0 && n - 1 > 2) cand[nc++] = n - 1;
+        for (int m = 0; m < nc; ++m) {
+            const int i = cand[m];
+            const PCoef co = proj_coef(i, k, n, per, a.eA, a.eB, a.eC);
+            const long long ci = c + (long long)(i - k) * s;
+            const double irho_i = a.T[ci] * ip0;
+            lP += a.lv[j][ci] * (-0.5 * ih * irho_i) * (co.p - co.m);
+            if (i > 0 || per) lP += a.lF[j][ci] * (-ih) * (co.c - co.m);
+            if (i == n - 1 && per) lP += a.lF[j][ci + s] * (-ih) * (co.p - co.c);
+        }
+    }
+    a.lT[c] += lT;
+    a.lP[t] = lP;
+}
+
+// AB2 / Euler (predictor) or AM2 (corrector) combination transposed
+// (Eqs 3.1-3.4, 3.12-3.13, 3.16): X = X_b + dt * (weights of R_now, R_hist).
+//   corrector: lR = dt/2 (lmom, lZ, lH); lRh += dt/2 (...); lv = rho^n lmom;
+//              lrho_n += v^n . lmom; lZ, lH carry on to level n unchanged.
+//   predictor: lR = lRh + w dt (lmom, lZs, lHs) (w = 3/2 AB2, 1 Euler);
+//              lRh = -dt/2 (...) (AB2) or 0; lv += rho^n lmom; lrho_n += v^n . lmom;
+//              lZ += lZs, lH += lHs.
+template <int DIM>
+__global__ void k_comb_adj(Geom g, CombAdj a) {
+    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+    if (t >= g.ncell) return;
+    const long long c = pad_index(g, t);
+    const double dt = a.dt;
+    const double rn = a.rho_n[c];
+    double lr = 0.0;
+    double lin[5];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) lin[i] = a.lmom[i][c];
+    lin[3] = a.lZin[c];
+    lin[4] = a.lHin[c];
+    if (a.mode == MODE_CORR) {
+        const double h = 0.5 * dt;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            a.lR[i][c] = h * lin[i];
+            a.lRh[i][c] += h * lin[i];
+            a.lv[i][c] = rn * lin[i];
+            lr += a.v_n[i][c] * lin[i];
+        }
+        for (int k = 3; k < 5; ++k) {
+            a.lR[k][c] = h * lin[k];
+            a.lRh[k][c] += h * lin[k];
+        }
+    } else {
+        const bool ab2 = a.mode == MODE_PRED_AB2;
+        const double w = ab2 ? 1.5 * dt : dt;
+        const double wh = ab2 ? -0.5 * dt : 0.0;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            a.lR[i][c] = a.lRh[i][c] + w * lin[i];
+            a.lRh[i][c] = wh * lin[i];
+            a.lv[i][c] += rn * lin[i];
+            lr += a.v_n[i][c] * lin[i];
+        }
+        for (int k = 3; k < 5; ++k) {
+            a.lR[k][c] = a.lRh[k][c] + w * lin[k];
+            a.lRh[k][c] = wh * lin[k];
+        }
+        a.lZ[c] += lin[3];
+        a.lH[c] += lin[4];
+    }
+    a.lrho_n[c] += lr;
+}
+
+// Heat-release rate of the flame sheet with unit Lewis number:
+// omega = -Q/(S+1) F_eps''(Z) kappa |grad Z|^2 / Pe
+//       = (Q/S)(k/2) sech^2(k (Z - 1)) kappa |delta_2 Z|^2 / Pe   (Eqs 2.30, 3.41).
+struct ObjLoad {
+    const double* Z;
+    const double* kap;
+    int sf;
+    long long si;
+    __device__ __forceinline__ Dual operator()(int f, long long i) const {
+        const double v = (f == RF_Z) ? Z[i] : kap[i];
+        return Dual(v, (f == sf && i == si) ? 1.0 : 0.0);
+    }
+};
+struct ObjPlain {
+    const double* Z;
+    const double* kap;
+    __device__ __forceinline__ double operator()(int f, long long i) const { return (f == RF_Z) ? Z[i] : kap[i]; }
+};
+
+template <int DIM, class C, class LD>
+__device__ __forceinline__ C omega_cell(const Geom& g, const Phys& ph, long long c, const LD& ld) {
+    const C th = tanh_c((C)ph.k * (ld(RF_Z, c) - (C)1.0));
+    C g2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        const C dz = (ld(RF_Z, c + g.s[j]) - ld(RF_Z, c - g.s[j])) * (C)(0.5 * g.ih[j]);
+        g2 = g2 + dz * dz;
+    }
+    const double coef = ph.Q / ph.S * 0.5 * ph.k / ph.Pe;
+    return (C)coef * ((C)1.0 - th * th) * ld(RF_KAP, c) * g2;
+}
+
+template <int DIM>
+__global__ void k_objective(Geom g, Phys ph, const double* __restrict__ Z, const double* __restrict__ kap,
+                            double* part) {
+    __shared__ double sm[NT / 32];
+    double acc = 0.0;
+    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT)
+        acc += omega_cell<DIM, double>(g, ph, pad_index(g, t), ObjPlain{Z, kap});
+    acc = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// lZ[j] += w d(sum_c omega_c dV)/dZ_j over the cells c within one step of j;
+// lkap[j] += w dV d omega_j / d kappa_j (j interior).
+template <int DIM>
+__global__ void k_objective_adj(Geom g, Phys ph, const double* __restrict__ Z, const double* __restrict__ kap,
+                                double w, double* lZ, double* lkap) {
+    const long long j = (long long)blockIdx.x * NT + threadIdx.x;
+    if (j >= g.npad) return;
+    int q[3];
+    padded_coords(g, j, q);
+    const double wv = w * g.dV;
+    double az = 0.0;
+    if (padded_interior(g, q)) {
+        az += omega_cell<DIM, Dual>(g, ph, j, ObjLoad{Z, kap, RF_Z, j}).d;
+        lkap[j] += wv * omega_cell<DIM, Dual>(g, ph, j, ObjLoad{Z, kap, RF_KAP, j}).d;
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            int qc[3] = {q[0], q[1], q[2]};
+            qc[d] += sgn;
+            if (!padded_interior(g, qc)) continue;
+            az += omega_cell<DIM, Dual>(g, ph, j + sgn * g.s[d], ObjLoad{Z, kap, RF_Z, j}).d;
+        }
+    lZ[j] += wv * az;
+}
+
+// Gradient of the adjoint-weighted IBM forcing with respect to the slot's
+// flux-profile samples.  v_ib,2 = m U (x_2 - y_lo) / (y_hi - y_lo) and
+// S_m = chi rho_b U / (n_col h_2) are linear in U = U_b base(x) mod(x), mod the
+// piecewise-linear interpolant of the samples (the forward set-up kernel), so
+// per column: col = U_b base(x) sum_rows (lvib2 m (x_2 - y_lo)/(y_hi - y_lo)
+// + lSm chi rho_b / (n_col h_2)), then spread on the two samples around x.
+__global__ void k_profile_col(Geom g, IbmDev b, const uint8_t* __restrict__ chi, const double* __restrict__ lvib1,
+                              const double* __restrict__ lSm, double* col) {
+    const int i = blockIdx.x * NT + threadIdx.x;
+    if (i >= g.n[0]) return;
+    const double x = ((double)(i + 1) - 0.5) * g.h[0];
+    const double r = (x - b.c[0]) / (b.half[0] + b.s);
+    double base = 1.0 - r * r;
+    base = base > 0.0 ? base : 0.0;
+    const double ylo = b.c[1] - b.half[1] - b.s, yhi = b.c[1] + b.half[1] + b.s;
+    int cnt = 0;
+    for (int j = 1; j <= g.n[1]; ++j) cnt += chi[(i + 1) + (long long)j * g.s[1]];
+    const double nc = cnt > 0 ? (double)cnt : 1.0;
+    double acc = 0.0;
+    for (int j = 1; j <= g.n[1]; ++j) {
+        const long long c = (i + 1) + (long long)j * g.s[1];
+        if (!chi[c]) continue;
+        const double y = ((double)j - 0.5) * g.h[1];
+        acc += lvib1[c] * (y - ylo) / (yhi - ylo) + lSm[c] * b.rho_b / (nc * g.h[1]);
+    }
+    col[i] = b.U_b * base * acc;
+}
+
+__global__ void k_profile_spread(Geom g, IbmDev b, const double* __restrict__ col, double* grad) {
+    const int k = blockIdx.x * NT + threadIdx.x;
+    if (k >= b.n_profile) return;
+    const double lo = b.c[0] - b.half[0] - b.s, hi = b.c[0] + b.half[0] + b.s;
+    double acc = 0.0;
+    for (int i = 0; i < g.n[0]; ++i) {
+        const double x = ((double)(i + 1) - 0.5) * g.h[0];
+        double wk;
+        if (x <= lo) wk = (k == 0) ? 1.0 : 0.0;
+        else if (x >= hi) wk = (k == b.n_profile - 1) ? 1.0 : 0.0;
+        else {
+            const double pos = (x - lo) / (hi - lo) * (double)(b.n_profile - 1);
+            int i0 = (int)floor(pos);
+            if (i0 > b.n_profile - 2) i0 = b.n_profile - 2;
+            const double fr = pos - (double)i0;
+            wk = (k == i0) ? 1.0 - fr : (k == i0 + 1) ? fr : 0.0;
+        }
+        acc += wk * col[i];
+    }
+    grad[k] = acc;
+}
+
 }  // namespace
 
 int reduce_grid(const Geom& g) { return reduce_blocks(g.ncell); }
@@ -769,6 +1251,68 @@ void launch_unpack(const Geom& g, const double* compact, double* padded, cudaStr
 
 void launch_u8_to_double(const Geom& g, const uint8_t* padded, double* compact, cudaStream_t s) {
     k_u8_to_double<<<blocks_for(g.ncell), NT, 0, s>>>(g, padded, compact);
+}
+
+// ------------------------------- adjoint launchers -------------------------------
+void launch_residual_adj(const Geom& g, const Phys& ph, const ResidArgs& a, double p0dot, const AdjR& lr,
+                         const AdjIn& li, cudaStream_t s) {
+    if (g.dim == 3) k_residual_adj<3><<<blocks_for(g.npad), NT, 0, s>>>(g, ph, a, p0dot, lr, li);
+    else k_residual_adj<2><<<blocks_for(g.npad), NT, 0, s>>>(g, ph, a, p0dot, lr, li);
+}
+
+void launch_ghost_adj(const Geom& g, const Bnd& bnd, const GhostJob& job, cudaStream_t s) {
+    for (int d = g.dim - 1; d >= 0; --d) {   // the forward fill runs d = 0, 1, 2
+        const int a = (d == 0) ? 1 : 0;
+        const int b = (d == 2) ? 1 : 2;
+        const long long nslab = (long long)g.p[a] * g.p[b];
+        k_ghost_adj<<<blocks_for(nslab), NT, 0, s>>>(g, bnd.kind[d][0], bnd.kind[d][1], d, g.periodic[d], job);
+    }
+}
+
+void launch_state_adj(const Geom& g, const Phys& ph, const double* Z, const double* T, const double* kap,
+                      double* lT, double* lrho, double* lkap, double* lZ, double* lH, cudaStream_t s) {
+    k_state_adj<<<blocks_for(g.ncell), NT, 0, s>>>(g, ph, Z, T, kap, lT, lrho, lkap, lZ, lH);
+}
+
+void launch_flux_adj(const Geom& g, const Bnd& bnd, const FluxAdj& a, cudaStream_t s) {
+    const int rb = reduce_grid(g);
+    if (g.dim == 3) {
+        k_flux_adj_a<3><<<rb, NT, 0, s>>>(g, bnd, a);
+        k_flux_adj_b<3><<<rb, NT, 0, s>>>(g, bnd, a, rb);
+    } else {
+        k_flux_adj_a<2><<<rb, NT, 0, s>>>(g, bnd, a);
+        k_flux_adj_b<2><<<rb, NT, 0, s>>>(g, bnd, a, rb);
+    }
+}
+
+void launch_project_adj(const Geom& g, const ProjAdj& a, cudaStream_t s) {
+    if (g.dim == 3) k_project_adj<3><<<blocks_for(g.ncell), NT, 0, s>>>(g, a);
+    else k_project_adj<2><<<blocks_for(g.ncell), NT, 0, s>>>(g, a);
+}
+
+void launch_comb_adj(const Geom& g, const CombAdj& a, cudaStream_t s) {
+    if (g.dim == 3) k_comb_adj<3><<<blocks_for(g.ncell), NT, 0, s>>>(g, a);
+    else k_comb_adj<2><<<blocks_for(g.ncell), NT, 0, s>>>(g, a);
+}
+
+void launch_objective(const Geom& g, const Phys& ph, const double* Z, const double* kap, double* part,
+                      double* out, cudaStream_t s) {
+    const int rb = reduce_grid(g);
+    if (g.dim == 3) k_objective<3><<<rb, NT, 0, s>>>(g, ph, Z, kap, part);
+    else k_objective<2><<<rb, NT, 0, s>>>(g, ph, Z, kap, part);
+    k_store_sum<<<1, NT, 0, s>>>(part, rb, g.dV, out);
+}
+
+void launch_objective_adj(const Geom& g, const Phys& ph, const double* Z, const double* kap, double w, double* lZ,
+                          double* lkap, cudaStream_t s) {
+    if (g.dim == 3) k_objective_adj<3><<<blocks_for(g.npad), NT, 0, s>>>(g, ph, Z, kap, w, lZ, lkap);
+    else k_objective_adj<2><<<blocks_for(g.npad), NT, 0, s>>>(g, ph, Z, kap, w, lZ, lkap);
+}
+
+void launch_profile_grad(const Geom& g, const IbmDev& b, const uint8_t* chi, const double* lvib1,
+                         const double* lSm, double* col, double* grad, cudaStream_t s) {
+    k_profile_col<<<blocks_for(g.n[0]), NT, 0, s>>>(g, b, chi, lvib1, lSm, col);
+    k_profile_spread<<<blocks_for(b.n_profile), NT, 0, s>>>(g, b, col, grad);
 }
 
 }  // namespace lm

@@ -95,6 +95,57 @@ struct ProjArgs {
     double eA, eB, eC;       // quadratic extrapolation coefficients (Eq 3.28)
 };
 
+// Adjoint (reverse-mode) arguments: lambda of the stage residuals (padded,
+// interior cells) and the lambda arrays of the stencil's inputs (padded; null
+// entries are not needed), indexed by the stencil's field ids (v0..v2, Z, H,
+// rho, kappa, F0..F2, T, v_ib0..v_ib2).
+struct AdjR {
+    const double* R[5];
+};
+struct AdjIn {
+    double* out[14];
+};
+struct FluxAdj {
+    double* lF[3];            // in: adjoint of the final fluxes (consumed, zeroed)
+    double* lFt[3];           // scratch: total adjoint of each shifted flux
+    const double* lb;         // in: adjoint of b (compact)
+    double* lmom[3];          // out (+=): provisional momentum
+    double* lrho_new;         // out (+=): density of the stage
+    double* lrho_n;           // out (+=): density at level n
+    double* lrho_prev;        // out (+=): density at level n-1 (BDF2 only)
+    double* lSm;              // out (+=): mass source (may be null)
+    double bdf_c0, bdf_c1, bdf_c2, bdf_den;
+    const double* sc;
+    double* part;
+};
+struct ProjAdj {
+    const double* lv[3];      // in: adjoint of the projected velocity (interior)
+    const double* lF[3];      // in: adjoint of the final fluxes
+    const double* P;          // forward pressure (compact)
+    const double* mom[3];     // forward provisional momentum
+    const double* T;          // forward temperature of the stage
+    const double* sc;
+    int p0_slot;
+    double* lmom[3];          // out (+=)
+    double* lT;               // out (+=)
+    double* lP;               // out (=, compact)
+    double eA, eB, eC;
+};
+struct CombAdj {
+    const double* lmom[3];    // in: adjoint of the stage's momentum output
+    const double* lZin;       // in: adjoint of the stage's Z output
+    const double* lHin;
+    double* lR[5];            // out (=): adjoint of the stage's residual
+    double* lRh[5];           // in/out: adjoint of the stored level-n residual
+    double* lv[3];            // out: adjoint of v^n (= in the corrector, += in the predictor)
+    double* lZ;               // out (+=, predictor only): adjoint of Z^n
+    double* lH;
+    double* lrho_n;           // out (+=)
+    const double* rho_n;      // forward rho^n
+    const double* v_n[3];     // forward v^n
+    double dt;
+    int mode;
+};
 void launch_ghost(const Geom& g, const Bnd& bnd, const Phys& ph, const GhostJob& job, cudaStream_t s,
                   int* launches);
 void launch_state(const Geom& g, const Phys& ph, const double* Z, const double* H, double* T,
@@ -128,6 +179,23 @@ void launch_bkinds(const Geom& g, const int bc[3][2], const uint8_t* chi, uint8_
 void launch_pack(const Geom& g, const double* padded, double* compact, int face_dir, cudaStream_t s);
 void launch_unpack(const Geom& g, const double* compact, double* padded, cudaStream_t s);
 void launch_u8_to_double(const Geom& g, const uint8_t* padded, double* compact, cudaStream_t s);
+
+// Adjoint (reverse-mode) launchers; every one adds the adjoint of its forward
+// kernel's inputs given the adjoint of its outputs.
+void launch_residual_adj(const Geom& g, const Phys& ph, const ResidArgs& a, double p0dot, const AdjR& lr,
+                         const AdjIn& li, cudaStream_t s);
+void launch_ghost_adj(const Geom& g, const Bnd& bnd, const GhostJob& job, cudaStream_t s);
+void launch_state_adj(const Geom& g, const Phys& ph, const double* Z, const double* T, const double* kap,
+                      double* lT, double* lrho, double* lkap, double* lZ, double* lH, cudaStream_t s);
+void launch_flux_adj(const Geom& g, const Bnd& bnd, const FluxAdj& a, cudaStream_t s);
+void launch_project_adj(const Geom& g, const ProjAdj& a, cudaStream_t s);
+void launch_comb_adj(const Geom& g, const CombAdj& a, cudaStream_t s);
+void launch_objective(const Geom& g, const Phys& ph, const double* Z, const double* kap, double* part,
+                      double* out, cudaStream_t s);
+void launch_objective_adj(const Geom& g, const Phys& ph, const double* Z, const double* kap, double w, double* lZ,
+                          double* lkap, cudaStream_t s);
+void launch_profile_grad(const Geom& g, const IbmDev& b, const uint8_t* chi, const double* lvib1,
+                         const double* lSm, double* col, double* grad, cudaStream_t s);
 
 int reduce_grid(const Geom& g);
 
