@@ -210,6 +210,42 @@ const char *sim_last_error(const sim_t *sim);
 void sim_destroy(sim_t *sim);
 
 /* ---------------------------------------------------------------------------
+ * Heat-release objective and the discrete adjoint of the time step.
+ * The paper has no adjoint; this is the exact transpose (reverse mode) of the
+ * step as discretised here (Eqs 3.1-3.19, 3.20-3.28, 3.30-3.33, 3.41-3.42).
+ *   objective: *out = sum over interior cells of omega dV at the current level,
+ *            omega = (Q/S)(k/2) sech^2(k (Z - 1)) kappa |delta_2 Z|^2 / Pe, the
+ *            heat-release rate of the flame sheet for Le = 1 (-Q/(S+1) F_eps''(Z)
+ *            kappa |grad Z|^2 / Pe from Eqs 2.30 and 3.41).  Host out; synchronous.
+ *   adjoint_workspace_size / begin: device memory (caller-owned, 256-byte
+ *            aligned, live until end) for the adjoint state lambda and the
+ *            recomputed step's values.  begin zeroes lambda and the accumulated
+ *            forcing adjoints.  Supported: dim 2, SIM_FP64, open system, no
+ *            incompressible switch, Le_F == Le_O, inv_Fr2 == 0 (SIM_EINVAL else).
+ *   adjoint_step: the simulation must hold the state of some level n (e.g. from
+ *            sim_state_load).  Recomputes step n (the simulation ends at level
+ *            n+1), adds objective_weight * d(objective at n+1)/d(state n+1) to
+ *            lambda, and transposes step n: lambda becomes the adjoint of the
+ *            level-n state, and the adjoints of v_ib and S_m are accumulated.
+ *            Call it for n = N-1, ..., 0 with the matching states to get the
+ *            gradient of sum_n w_n objective(n) + <seed, state N>.  dJ_dprofile
+ *            (host, n_profile doubles, or NULL) receives the gradient with
+ *            respect to the slot's profile samples accumulated so far (slot body
+ *            with a profile only).  Synchronous; SIM_ENOCONV if a transposed
+ *            pressure solve did not converge.
+ *   adjoint_field: dir = SIM_GET copies the adjoint of a state field at the
+ *            current level to host buf (interior cells, or faces for FX / FY;
+ *            SIM_FIELD_SM: the accumulated adjoint of S_m); SIM_SET adds host
+ *            buf to it (cell fields U, V, Z, H, T, RHO, KAPPA: a seed).
+ * ------------------------------------------------------------------------- */
+sim_status sim_objective(sim_t *sim, double *out);
+sim_status sim_adjoint_workspace_size(const sim_t *sim, size_t *bytes);
+sim_status sim_adjoint_begin(sim_t *sim, void *d_workspace, size_t workspace_bytes);
+sim_status sim_adjoint_step(sim_t *sim, double objective_weight, double *dJ_dprofile);
+sim_status sim_adjoint_field(sim_t *sim, int field_id, double *buf, int dir);
+sim_status sim_adjoint_end(sim_t *sim);
+
+/* ---------------------------------------------------------------------------
  * Batches of independent simulations (many flames, e.g. of uneven grid sizes).
  * One CUDA graph per step holds every simulation's whole step as an
  * independent branch (forked streams at capture), so their latency-bound

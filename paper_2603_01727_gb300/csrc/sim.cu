@@ -24,6 +24,33 @@ size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
+// Discrete adjoint state: lambda arrays (padded layout unless noted) and the
+// forward values of the recomputed step that its transposes read.
+struct AdjWs {
+    double* Lv[3];          // lambda of v at the level being stepped back to
+    double* Lvs[3];         // lambda of v*
+    double *LZ, *LH, *LZs, *LHs, *LT, *Lkap;
+    double* LF[3];          // lambda of the interface fluxes
+    double* LFt[3];         // scratch of the flux transpose
+    double* LRh[5];         // lambda of the stored residual history
+    double* LR[5];          // lambda of the stage residual being transposed
+    double* Lm[3];          // lambda of the provisional momentum
+    double* Lr[3];          // rotating lambda of the density levels
+    int i_rho, i_prev;      // Lr roles: rho at the level, rho one level below
+    double* Lvib[3];        // accumulated lambda of v_ib over all steps
+    double* LSm;            // accumulated lambda of S_m over all steps
+    double *LP, *Lb;        // compact: lambda of P and of the Poisson rhs
+    double* v0[3];          // level-n forward values
+    double *Z0, *H0, *T0, *kap0, *rho0;
+    double* F0[3];
+    double* m0[3];          // predictor values: provisional momentum, T*, kappa*, P*, F*
+    double *Ts, *kaps, *Ps;
+    double* Fs[3];
+    double *col, *grad, *obj, *rep, *part;
+    char* lam_base;         // lambda region (zeroed by begin)
+    size_t lam_bytes;
+};
+
 struct sim {
     sim_params_t prm;
     Geom g;
@@ -70,6 +97,11 @@ struct sim {
     cudaGraphExec_t gexec[6];
     bool gvalid[6];
     int use_graph;
+
+    IbmDev ibm;            // body description of the last set-up (device profile copy)
+    AdjWs adj;
+    bool adj_active;
+    bool adj_save;         // the eager step copies its predictor values into adj
 
     char err[512];
 };
@@ -527,6 +559,19 @@ cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int
     pa.eC = s->eC;
     launch_project(g, pa, st, L);
     ghost_v(s, s->vs, st, L);
+    if (s->adj_save) {
+        // predictor values read by the reverse pass (overwritten by the corrector)
+        const size_t fp = sizeof(double) * (size_t)g.npad;
+        for (int d = 0; d < D && e == cudaSuccess; ++d) {
+            e = cudaMemcpyAsync(s->adj.m0[d], s->mom[d], fp, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(s->adj.Fs[d], s->F[d], fp, cudaMemcpyDeviceToDevice, st);
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s->adj.Ts, s->T, fp, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s->adj.kaps, s->kap, fp, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->adj.Ps, s->P, sizeof(double) * (size_t)g.ncell, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
 
     // ---------------- corrector ----------------
     ResidArgs c = resid_common(s);
@@ -746,6 +791,7 @@ sim_status sim_set_ibm_geometry(sim_t* s, const sim_ibm_t* geo) {
         b.profile = s->profile;
     }
     launch_ibm(s->g, b, s->chi, s->vib, s->U, s->Sm, s->stream);
+    s->ibm = b;
     launch_bkinds(s->g, bc, s->chi, s->kind, s->part, s->sc, s->stream);
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
@@ -1141,6 +1187,373 @@ sim_status sim_poisson_solve(int dim, const int n[3], const double h[3], const i
     if (iters) *iters = (int)sc[PS_ITERS];
     if (rel_resid) *rel_resid = sc[PS_RELRES];
     return ic[PI_NOCONV] ? SIM_ENOCONV : SIM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------ discrete adjoint -----------------------------
+namespace {
+
+// Adjoint workspace layout: the lambda region first (zeroed by begin), then the
+// saved forward values.  Returns the bytes used (a null base only measures).
+size_t adj_layout(const sim_t* s, AdjWs* A, char* base) {
+    const Geom& g = s->g;
+    const int D = g.dim;
+    const size_t fpad = sizeof(double) * (size_t)g.npad;
+    const size_t fcmp = sizeof(double) * (size_t)g.ncell;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> double* {
+        double* p = base ? (double*)(base + off) : nullptr;
+        off += a256(bytes);
+        return p;
+    };
+    AdjWs tmp;
+    AdjWs& a = A ? *A : tmp;
+    std::memset(&a, 0, sizeof(a));
+    for (int d = 0; d < D; ++d) a.Lv[d] = take(fpad);
+    for (int d = 0; d < D; ++d) a.Lvs[d] = take(fpad);
+    a.LZ = take(fpad); a.LH = take(fpad); a.LZs = take(fpad); a.LHs = take(fpad);
+    a.LT = take(fpad); a.Lkap = take(fpad);
+    for (int d = 0; d < D; ++d) a.LF[d] = take(fpad);
+    for (int d = 0; d < D; ++d) a.LFt[d] = take(fpad);
+    for (int k = 0; k < 5; ++k)
+        if (k < D || k >= 3) {
+            a.LRh[k] = take(fpad);
+            a.LR[k] = take(fpad);
+        }
+    for (int d = 0; d < D; ++d) a.Lm[d] = take(fpad);
+    for (int r = 0; r < 3; ++r) a.Lr[r] = take(fpad);
+    for (int d = 0; d < D; ++d) a.Lvib[d] = take(fpad);
+    a.LSm = take(fpad);
+    a.LP = take(fcmp);
+    a.Lb = take(fcmp);
+    a.lam_base = base;
+    a.lam_bytes = off;
+    for (int d = 0; d < D; ++d) a.v0[d] = take(fpad);
+    a.Z0 = take(fpad); a.H0 = take(fpad); a.T0 = take(fpad); a.kap0 = take(fpad); a.rho0 = take(fpad);
+    for (int d = 0; d < D; ++d) a.F0[d] = take(fpad);
+    for (int d = 0; d < D; ++d) a.m0[d] = take(fpad);
+    a.Ts = take(fpad); a.kaps = take(fpad);
+    a.Ps = take(fcmp);
+    for (int d = 0; d < D; ++d) a.Fs[d] = take(fpad);
+    a.col = take(sizeof(double) * (size_t)g.n[0]);
+    a.grad = take(sizeof(double) * kMaxProfile);
+    a.obj = take(sizeof(double) * 4);
+    a.rep = take(sizeof(double) * 4);
+    a.part = take(sizeof(double) * kMaxPartials);
+    return off;
+}
+
+// The adjoint covers the FP64 2D open-system step with unit Lewis numbers and
+// no gravity; null when supported, else the reason.
+const char* adj_unsupported(const sim_t* s) {
+    if (s->g.dim != 2) return "the adjoint step is 2D only";
+    if (s->prm.precision != SIM_FP64) return "the adjoint step needs precision SIM_FP64";
+    if (s->ph.closed) return "the adjoint step needs an open system (p0 = 1)";
+    if (s->ph.incompressible) return "the adjoint step needs the variable-density model";
+    if (s->ph.Le_F != s->ph.Le_O) return "the adjoint step needs Le_F == Le_O";
+    if (s->ph.inv_Fr2 != 0.0) return "the adjoint step needs inv_Fr2 == 0";
+    return nullptr;
+}
+
+void adj_ghost(sim_t* s, std::initializer_list<std::pair<double*, int>> fields, cudaStream_t st) {
+    GhostJob job;
+    std::memset(&job, 0, sizeof(job));
+    for (auto& f : fields) {
+        job.f[job.nf] = f.first;
+        job.what[job.nf] = f.second;
+        ++job.nf;
+    }
+    launch_ghost_adj(s->g, s->bnd, job, st);
+}
+
+void adj_ghost_v(sim_t* s, double* const* lv, cudaStream_t st) {
+    GhostJob job;
+    std::memset(&job, 0, sizeof(job));
+    for (int d = 0; d < s->g.dim; ++d) {
+        job.f[d] = lv[d];
+        job.what[d] = GW_V0 + d;
+    }
+    job.nf = s->g.dim;
+    launch_ghost_adj(s->g, s->bnd, job, st);
+}
+
+// The pressure solve maps b to the zero-mean P = M A^+ M b (M removes the
+// mean, A the symmetric compact Laplacian), a symmetric operator: its
+// transpose is the same solve applied to lambda_P.
+cudaError_t adj_poisson(sim_t* s, const double* lP, double* lb, cudaStream_t st) {
+    PoissonPlan* pl = &s->pp;
+    cudaError_t e = poisson_enqueue_prologue(pl, lP, lb, st, 0ULL);
+    if (e != cudaSuccess) return e;
+    int done = 0;
+    for (int guard = 0; guard <= pl->max_iter + 1; ++guard) {
+        e = cudaMemcpyAsync(&done, pl->ictl + PI_DONE, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        if (done) break;
+        e = poisson_enqueue_body(pl, lb, st, 0ULL);
+        if (e != cudaSuccess) return e;
+    }
+    return poisson_enqueue_epilogue(pl, lb, st, s->adj.rep, s->status, ST_NOCONV);
+}
+
+ResidArgs adj_resid_args(sim_t* s, double* const* v, const double* Z, const double* H, const double* kap,
+                         double* const* F, const double* T) {
+    ResidArgs a = resid_common(s);
+    for (int d = 0; d < s->g.dim; ++d) {
+        a.v[d] = v[d];
+        a.F[d] = F[d];
+    }
+    a.Z = Z;
+    a.H = H;
+    a.kap = kap;
+    a.T = T;
+    a.rho = s->adj.rho0;     // read by the buoyancy term only, which the adjoint excludes
+    a.p0r = SC_P0_N;         // open system: p0 = 1 in every slot
+    return a;
+}
+
+AdjIn adj_in(sim_t* s, double* const* lv, double* lZ, double* lH) {
+    AdjWs& A = s->adj;
+    AdjIn li;
+    std::memset(&li, 0, sizeof(li));
+    for (int d = 0; d < s->g.dim; ++d) {
+        li.out[RF_V0 + d] = lv[d];
+        li.out[RF_F0 + d] = A.LF[d];
+        if (s->ibm_active) li.out[RF_VIB0 + d] = A.Lvib[d];
+    }
+    li.out[RF_Z] = lZ;
+    li.out[RF_H] = lH;
+    li.out[RF_KAP] = A.Lkap;
+    li.out[RF_T] = A.LT;
+    return li;
+}
+
+}  // namespace
+
+extern "C" {
+
+sim_status sim_objective(sim_t* s, double* out) {
+    if (!s || !out) return SIM_EINVAL;
+    if (s->need_init) return fail(s, SIM_ESTATE, "no state yet: step once after setting the fields");
+    launch_objective(s->g, s->ph, s->Z, s->kap, s->part, s->io, s->stream);
+    CK(cudaMemcpyAsync(out, s->io, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    return SIM_OK;
+}
+
+sim_status sim_adjoint_workspace_size(const sim_t* s, size_t* bytes) {
+    if (!s || !bytes) return SIM_EINVAL;
+    *bytes = adj_layout(s, nullptr, nullptr);
+    return SIM_OK;
+}
+
+sim_status sim_adjoint_begin(sim_t* s, void* d_workspace, size_t workspace_bytes) {
+    if (!s) return SIM_EINVAL;
+    const char* why = adj_unsupported(s);
+    if (why) return fail(s, SIM_EINVAL, "%s", why);
+    const size_t need = adj_layout(s, nullptr, nullptr);
+    if (!d_workspace || workspace_bytes < need) return fail(s, SIM_ENOMEM, "adjoint workspace needs %zu bytes", need);
+    if (((uintptr_t)d_workspace & 255) != 0) return fail(s, SIM_EINVAL, "adjoint workspace must be 256-byte aligned");
+    adj_layout(s, &s->adj, (char*)d_workspace);
+    s->adj.i_rho = 0;
+    s->adj.i_prev = 1;
+    CK(cudaMemsetAsync(s->adj.lam_base, 0, s->adj.lam_bytes, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->adj_active = true;
+    return SIM_OK;
+}
+
+sim_status sim_adjoint_end(sim_t* s) {
+    if (!s) return SIM_EINVAL;
+    s->adj_active = false;
+    std::memset(&s->adj, 0, sizeof(s->adj));
+    return SIM_OK;
+}
+
+sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofile) {
+    if (!s) return SIM_EINVAL;
+    if (!s->adj_active) return fail(s, SIM_ESTATE, "sim_adjoint_begin first");
+    if (s->need_init) return fail(s, SIM_ESTATE, "no state yet: load a saved state or step once");
+    AdjWs& A = s->adj;
+    const Geom& g = s->g;
+    const Phys& ph = s->ph;
+    const int D = g.dim;
+    const double dt = s->prm.dt;
+    const long long n = s->nstep;
+    cudaStream_t st = s->stream;
+    const size_t fpad = sizeof(double) * (size_t)g.npad;
+    const Roles r = roles(s, n);
+
+    // level-n values, then the step recomputed with its predictor values saved
+    for (int d = 0; d < D; ++d) {
+        CK(cudaMemcpyAsync(A.v0[d], s->v[d], fpad, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(A.F0[d], s->F[d], fpad, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaMemcpyAsync(A.Z0, s->Z, fpad, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(A.H0, s->H, fpad, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(A.T0, s->T, fpad, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(A.kap0, s->kap, fpad, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(A.rho0, r.rho_n, fpad, cudaMemcpyDeviceToDevice, st));
+    {
+        int L = 0, body = 0;
+        s->adj_save = true;
+        cudaError_t e = enqueue_step(s, n, st, false, &L, &body);
+        s->adj_save = false;
+        CK(e);
+        s->launches_last = L;
+        after_step(s);
+    }
+    // s->vs = v*, s->Zs / Hs = Z* / H*, s->mom = corrector momentum, s->Z / H / T /
+    // kap / P = level n+1; A.m0 / Ts / kaps / Ps / Fs = predictor values.
+    double* Lrho = A.Lr[A.i_rho];                 // lambda rho^{n+1}, then rho*
+    double* Lrn = A.Lr[A.i_prev];                 // lambda rho^n
+    const int i_free = 3 - A.i_rho - A.i_prev;
+    double* Lrp = A.Lr[i_free];                   // lambda rho^{n-1} (zero on entry)
+    const double bc0 = 1.0, bc1 = n == 0 ? -1.0 : -4.0;
+    const double bdf[4] = {n == 0 ? bc0 : 3.0, bc1, n == 0 ? 0.0 : 1.0, n == 0 ? dt : 2.0 * dt};
+
+    // objective term of level n+1
+    if (objective_weight != 0.0) launch_objective_adj(g, ph, s->Z, s->kap, objective_weight, A.LZ, A.Lkap, st);
+
+    for (int stage = 1; stage >= 0; --stage) {   // corrector, then predictor
+        const bool corr = stage == 1;
+        double* const* lv = corr ? A.Lv : A.Lvs;
+        // projection^T (ghost fill of the projected velocity first)
+        adj_ghost_v(s, lv, st);
+        for (int d = 0; d < D; ++d) CK(cudaMemsetAsync(A.Lm[d], 0, fpad, st));
+        ProjAdj pj;
+        std::memset(&pj, 0, sizeof(pj));
+        for (int d = 0; d < D; ++d) {
+            pj.lv[d] = lv[d];
+            pj.lF[d] = A.LF[d];
+            pj.mom[d] = corr ? s->mom[d] : A.m0[d];
+            pj.lmom[d] = A.Lm[d];
+        }
+        pj.P = corr ? s->P : A.Ps;
+        pj.T = corr ? s->T : A.Ts;
+        pj.sc = s->sc;
+        pj.p0_slot = SC_P0_N;
+        pj.lT = A.LT;
+        pj.lP = A.LP;
+        pj.eA = s->eA;
+        pj.eB = s->eB;
+        pj.eC = s->eC;
+        launch_project_adj(g, pj, st);
+        // pressure solve^T
+        CK(adj_poisson(s, A.LP, A.Lb, st));
+        // face fluxes and right-hand side^T
+        FluxAdj fa;
+        std::memset(&fa, 0, sizeof(fa));
+        for (int d = 0; d < D; ++d) {
+            fa.lF[d] = A.LF[d];
+            fa.lFt[d] = A.LFt[d];
+            fa.lmom[d] = A.Lm[d];
+        }
+        fa.lb = A.Lb;
+        fa.lrho_new = Lrho;
+        fa.lrho_n = Lrn;
+        fa.lrho_prev = Lrp;
+        fa.lSm = s->ibm_active ? A.LSm : nullptr;
+        fa.bdf_c0 = bdf[0];
+        fa.bdf_c1 = bdf[1];
+        fa.bdf_c2 = bdf[2];
+        fa.bdf_den = bdf[3];
+        fa.sc = s->sc;
+        fa.part = A.part;
+        launch_flux_adj(g, s->bnd, fa, st);
+        // state relation^T (kappa ghosts first), then the Z, H ghost fill^T
+        double* lZo = corr ? A.LZ : A.LZs;
+        double* lHo = corr ? A.LH : A.LHs;
+        adj_ghost(s, {{A.Lkap, GW_KAPPA}}, st);
+        launch_state_adj(g, ph, corr ? s->Z : s->Zs, corr ? s->T : A.Ts, corr ? s->kap : A.kaps, A.LT, Lrho,
+                         A.Lkap, lZo, lHo, st);
+        adj_ghost(s, {{lZo, GW_Z}, {lHo, GW_H}}, st);
+        // combination^T
+        CombAdj cb;
+        std::memset(&cb, 0, sizeof(cb));
+        for (int d = 0; d < D; ++d) {
+            cb.lmom[d] = A.Lm[d];
+            cb.lv[d] = A.Lv[d];
+            cb.v_n[d] = A.v0[d];
+        }
+        cb.lZin = lZo;
+        cb.lHin = lHo;
+        for (int k = 0; k < 5; ++k) {
+            cb.lR[k] = A.LR[k];
+            cb.lRh[k] = A.LRh[k];
+        }
+        cb.lZ = A.LZ;
+        cb.lH = A.LH;
+        cb.lrho_n = Lrn;
+        cb.rho_n = A.rho0;
+        cb.dt = dt;
+        cb.mode = corr ? MODE_CORR : (n == 0 ? MODE_PRED_EULER : MODE_PRED_AB2);
+        launch_comb_adj(g, cb, st);
+        // stencil^T at the stage's input level
+        AdjR lr;
+        for (int k = 0; k < 5; ++k) lr.R[k] = A.LR[k];
+        if (corr) {
+            for (int d = 0; d < D; ++d) CK(cudaMemsetAsync(A.Lvs[d], 0, fpad, st));
+            CK(cudaMemsetAsync(A.LZs, 0, fpad, st));
+            CK(cudaMemsetAsync(A.LHs, 0, fpad, st));
+            const ResidArgs a = adj_resid_args(s, s->vs, s->Zs, s->Hs, A.kaps, A.Fs, A.Ts);
+            launch_residual_adj(g, ph, a, 0.0, lr, adj_in(s, A.Lvs, A.LZs, A.LHs), st);
+        } else {
+            const ResidArgs a = adj_resid_args(s, A.v0, A.Z0, A.H0, A.kap0, A.F0, A.T0);
+            launch_residual_adj(g, ph, a, 0.0, lr, adj_in(s, A.Lv, A.LZ, A.LH), st);
+        }
+    }
+    // density roles one level down; the consumed rho buffer is zero again
+    A.i_rho = A.i_prev;
+    A.i_prev = i_free;
+    CK(cudaGetLastError());
+    if (dJ_dprofile) {
+        if (!s->ibm_active || s->ibm.kind != SIM_IBM_SLOT || s->ibm.n_profile < 2)
+            return fail(s, SIM_EINVAL, "dJ_dprofile needs a slot body with a flux profile");
+        launch_profile_grad(g, s->ibm, s->chi, A.Lvib[1], A.LSm, A.col, A.grad, st);
+        CK(cudaMemcpyAsync(dJ_dprofile, A.grad, sizeof(double) * s->ibm.n_profile, cudaMemcpyDeviceToHost, st));
+    }
+    return check_device_status(s);
+}
+
+// Adjoint of a state field at the current level, interior cells (or faces)
+// as for sim_fields: get copies it out, set adds buf to it.
+sim_status sim_adjoint_field(sim_t* s, int id, double* buf, int dir) {
+    if (!s || !buf || (dir != SIM_GET && dir != SIM_SET)) return SIM_EINVAL;
+    if (!s->adj_active) return fail(s, SIM_ESTATE, "sim_adjoint_begin first");
+    AdjWs& A = s->adj;
+    const Geom& g = s->g;
+    double* f = nullptr;
+    int face = -1;
+    switch (id) {
+        case SIM_FIELD_U: f = A.Lv[0]; break;
+        case SIM_FIELD_V: f = A.Lv[1]; break;
+        case SIM_FIELD_Z: f = A.LZ; break;
+        case SIM_FIELD_H: f = A.LH; break;
+        case SIM_FIELD_T: f = A.LT; break;
+        case SIM_FIELD_RHO: f = A.Lr[A.i_rho]; break;
+        case SIM_FIELD_KAPPA: f = A.Lkap; break;
+        case SIM_FIELD_SM: f = A.LSm; break;
+        case SIM_FIELD_FX: f = A.LF[0]; face = 0; break;
+        case SIM_FIELD_FY: f = A.LF[1]; face = 1; break;
+        default: return fail(s, SIM_EINVAL, "no adjoint for field %d", id);
+    }
+    long long m = 1;
+    for (int d = 0; d < g.dim; ++d) m *= g.n[d] + (d == face ? 1 : 0);
+    const size_t bytes = sizeof(double) * (size_t)m;
+    if (dir == SIM_GET) {
+        launch_pack(g, f, s->io, face, s->stream);
+        CK(cudaMemcpyAsync(buf, s->io, bytes, cudaMemcpyDeviceToHost, s->stream));
+    } else {
+        if (face >= 0) return fail(s, SIM_EINVAL, "adjoint seeds are cell fields");
+        CK(cudaMemcpyAsync(s->io, buf, bytes, cudaMemcpyHostToDevice, s->stream));
+        launch_add_unpack(g, s->io, f, s->stream);
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    return SIM_OK;
 }
 
 // ------------------------------ batches --------------------------------------

@@ -195,11 +195,6 @@ __global__ void k_density(Geom g, const double* __restrict__ T, double* __restri
 // C is the arithmetic type of the residual terms and of the stored residual
 // history (double in both precision modes, see launch_residual); the state
 // updates X = X_b + dt * combination are FP64.
-// Fields read by the stage stencil, by loader id.
-enum : int {
-    RF_V0 = 0, RF_V1 = 1, RF_V2 = 2, RF_Z = 3, RF_H = 4, RF_RHO = 5, RF_KAP = 6,
-    RF_F0 = 7, RF_F1 = 8, RF_F2 = 9, RF_T = 10, RF_VIB0 = 11, RF_VIB1 = 12, RF_VIB2 = 13, RF_N = 14
-};
 
 // Plain FP64 loads of the stencil's inputs.
 struct PlainLoad {
@@ -670,6 +665,11 @@ __global__ void k_unpack(Geom g, const double* __restrict__ src, double* __restr
     const long long t = (long long)blockIdx.x * NT + threadIdx.x;
     if (t >= g.ncell) return;
     dst[pad_index(g, t)] = src[t];
+}
+
+__global__ void k_add_unpack(Geom g, const double* __restrict__ src, double* __restrict__ dst) {
+    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+    if (t < g.ncell) dst[pad_index(g, t)] += src[t];
 }
 
 __global__ void k_u8_to_double(Geom g, const uint8_t* __restrict__ src, double* __restrict__ dst) {
@@ -1247,6 +1247,10 @@ void launch_pack(const Geom& g, const double* padded, double* compact, int face_
 
 void launch_unpack(const Geom& g, const double* compact, double* padded, cudaStream_t s) {
     k_unpack<<<blocks_for(g.ncell), NT, 0, s>>>(g, compact, padded);
+}
+
+void launch_add_unpack(const Geom& g, const double* compact, double* padded, cudaStream_t s) {
+    k_add_unpack<<<blocks_for(g.ncell), NT, 0, s>>>(g, compact, padded);
 }
 
 void launch_u8_to_double(const Geom& g, const uint8_t* padded, double* compact, cudaStream_t s) {

@@ -95,6 +95,12 @@ struct ProjArgs {
     double eA, eB, eC;       // quadratic extrapolation coefficients (Eq 3.28)
 };
 
+// Fields read by the stage stencil, by loader id.
+enum : int {
+    RF_V0 = 0, RF_V1 = 1, RF_V2 = 2, RF_Z = 3, RF_H = 4, RF_RHO = 5, RF_KAP = 6,
+    RF_F0 = 7, RF_F1 = 8, RF_F2 = 9, RF_T = 10, RF_VIB0 = 11, RF_VIB1 = 12, RF_VIB2 = 13, RF_N = 14
+};
+
 // Adjoint (reverse-mode) arguments: lambda of the stage residuals (padded,
 // interior cells) and the lambda arrays of the stencil's inputs (padded; null
 // entries are not needed), indexed by the stencil's field ids (v0..v2, Z, H,
@@ -103,7 +109,7 @@ struct AdjR {
     const double* R[5];
 };
 struct AdjIn {
-    double* out[14];
+    double* out[RF_N];
 };
 struct FluxAdj {
     double* lF[3];            // in: adjoint of the final fluxes (consumed, zeroed)
@@ -179,6 +185,7 @@ void launch_bkinds(const Geom& g, const int bc[3][2], const uint8_t* chi, uint8_
 void launch_pack(const Geom& g, const double* padded, double* compact, int face_dir, cudaStream_t s);
 void launch_unpack(const Geom& g, const double* compact, double* padded, cudaStream_t s);
 void launch_u8_to_double(const Geom& g, const uint8_t* padded, double* compact, cudaStream_t s);
+void launch_add_unpack(const Geom& g, const double* compact, double* padded, cudaStream_t s);
 
 // Adjoint (reverse-mode) launchers; every one adds the adjoint of its forward
 // kernel's inputs given the adjoint of its outputs.

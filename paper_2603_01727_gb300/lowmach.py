@@ -87,6 +87,12 @@ def load():
         "sim_poisson_workspace_size": ([I, P(I), P(I), P(SZ)], I),
         "sim_poisson_solve": ([I, P(I), P(D), P(I), VP, VP, D, I, VP, SZ, VP, P(I), P(D)], I),
         "sim_poisson_solve_noalloc": ([I, P(I), P(D), P(I), VP, VP, D, I, VP, P(I), P(D)], I),
+        "sim_objective": ([VP, P(D)], I),
+        "sim_adjoint_workspace_size": ([VP, P(SZ)], I),
+        "sim_adjoint_begin": ([VP, VP, SZ], I),
+        "sim_adjoint_step": ([VP, D, P(D)], I),
+        "sim_adjoint_field": ([VP, I, VP, I], I),
+        "sim_adjoint_end": ([VP], I),
         "sim_batch_create": ([P(VP), I, VP, P(VP)], I),
         "sim_batch_step": ([VP, I], I),
         "sim_batch_sync": ([VP], I),
@@ -106,7 +112,9 @@ def exported_symbols():
             "sim_sync", "sim_query", "sim_last_error", "sim_destroy", "sim_time_kernel", "sim_state_size",
             "sim_state_save",
             "sim_state_load", "sim_poisson_workspace_size",
-            "sim_poisson_solve", "sim_poisson_solve_noalloc", "sim_batch_create", "sim_batch_step",
+            "sim_poisson_solve", "sim_poisson_solve_noalloc", "sim_objective", "sim_adjoint_workspace_size",
+            "sim_adjoint_begin", "sim_adjoint_step", "sim_adjoint_field", "sim_adjoint_end",
+            "sim_batch_create", "sim_batch_step",
             "sim_batch_sync", "sim_batch_last_error", "sim_batch_destroy"]
 
 
@@ -259,6 +267,53 @@ class Simulation:
     def state_load(self, buf):
         ptr, dev = self._buf(buf)
         _check(self.lib, self.lib.sim_state_load(self.h, ptr, dev), self.h)
+
+    # --------------------------- objective and adjoint ---------------------------
+    def objective(self):
+        """Heat-release integral sum(omega dV) at the current level (synchronous)."""
+        v = ctypes.c_double()
+        _check(self.lib, self.lib.sim_objective(self.h, ctypes.byref(v)), self.h)
+        return v.value
+
+    def adjoint_begin(self):
+        """Allocate the adjoint workspace and zero the adjoint state."""
+        sz = ctypes.c_size_t()
+        _check(self.lib, self.lib.sim_adjoint_workspace_size(self.h, ctypes.byref(sz)), self.h)
+        self._adj_ws = self.torch.empty(sz.value + 256, dtype=self.torch.uint8, device=self.workspace.device)
+        ptr = (self._adj_ws.data_ptr() + 255) // 256 * 256
+        _check(self.lib, self.lib.sim_adjoint_begin(self.h, ctypes.c_void_p(ptr), ctypes.c_size_t(sz.value)),
+               self.h)
+
+    def adjoint_step(self, objective_weight=0.0, n_profile=0):
+        """Recompute the step from the loaded level n and transpose it; with
+        n_profile > 0, also return the gradient with respect to the profile
+        samples accumulated so far (numpy)."""
+        if n_profile > 0:
+            g = np.zeros(int(n_profile), dtype=np.float64)
+            ptr = g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        else:
+            g, ptr = None, None
+        _check(self.lib, self.lib.sim_adjoint_step(self.h, float(objective_weight), ptr), self.h)
+        return g
+
+    def adjoint_get(self, name):
+        fid = FIELD_IDS[name]
+        face = {"FX": 0, "FY": 1, "FZ": 2}.get(name)
+        a = np.empty(self.shape(face), dtype=np.float64)
+        _check(self.lib, self.lib.sim_adjoint_field(self.h, fid, a.ctypes.data_as(ctypes.c_void_p), SIM_GET),
+               self.h)
+        return a
+
+    def adjoint_seed(self, name, arr):
+        """Add arr (interior cells) to the adjoint of a state field."""
+        a = np.ascontiguousarray(arr, dtype=np.float64)
+        assert a.shape == self.shape()
+        _check(self.lib, self.lib.sim_adjoint_field(self.h, FIELD_IDS[name], a.ctypes.data_as(ctypes.c_void_p),
+                                                    SIM_SET), self.h)
+
+    def adjoint_end(self):
+        _check(self.lib, self.lib.sim_adjoint_end(self.h), self.h)
+        self._adj_ws = None
 
     def _buf(self, buf):
         if isinstance(buf, np.ndarray):

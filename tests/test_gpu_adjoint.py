@@ -1,0 +1,157 @@
+"""Discrete adjoint of the step (sim_adjoint_*): gradients of the heat-release
+objective and of a seeded state functional with respect to the slot burner's
+profile coefficients, against central differences of the forward map (the
+CUDA step itself, and the FP64 oracle).
+
+FD step: the derivative along a unit direction of the coefficients (order
+one) is only ~1e-4 J, so a step of 1e-6 leaves the quotient with ~1e-5
+relative rounding noise (J itself carries ~1e-16 relative rounding); at
+h = 1e-3 the truncation error is ~1e-8 relative (J is smooth in c) and the
+noise ~1e-8.  The tolerance is 1e-6 relative; Poisson solves run to rtol 1e-13."""
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FD_H = 1e-3
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2603_01727_gb300 import build
+    build.build()
+
+
+def _case(nx=32, ny=64, n_bumps=8, n_profile=64):
+    prm, geo, f, A, c = W.slot_bumps(nx, ny, n_bumps=n_bumps, n_profile=n_profile, Da_ib=(2.0 / nx) ** 2)
+    prm["poisson_rtol"] = 1e-13
+    prm["poisson_max_iter"] = 400
+    return prm, geo, f, A, c
+
+
+def _direction(m, seed=7):
+    e = np.random.Generator(np.random.PCG64(seed)).standard_normal(m)
+    return e / np.linalg.norm(e)
+
+
+def test_heat_release_gradient_matches_central_differences():
+    from paper_2603_01727_gb300.adjoint import HeatReleaseProblem
+    prm, geo, f, A, c = _case()
+    pb = HeatReleaseProblem(prm, geo, f, A, nsteps=12, every=5)
+    J0 = pb.value(c)
+    gc, gp = pb.gradient()
+    assert J0 > 0.0 and np.all(np.isfinite(gc))
+    e = _direction(len(c))
+    fd = (pb.value(c + FD_H * e, False) - pb.value(c - FD_H * e, False)) / (2.0 * FD_H)
+    ad = float(gc @ e)
+    assert abs(fd - ad) <= TOL * abs(ad), (fd, ad)
+    # single coefficients, and the profile-sample gradient through the basis
+    for m in (0, len(c) // 2):
+        em = np.zeros(len(c))
+        em[m] = 1.0
+        fdm = (pb.value(c + FD_H * em, False) - pb.value(c - FD_H * em, False)) / (2.0 * FD_H)
+        assert abs(fdm - gc[m]) <= TOL * np.max(np.abs(gc)), (m, fdm, gc[m])
+    assert np.allclose(A.T @ gp, gc, rtol=0, atol=1e-14 * np.max(np.abs(gc)))
+    pb.close()
+
+
+def test_checkpoint_spacing_does_not_change_the_gradient():
+    from paper_2603_01727_gb300.adjoint import HeatReleaseProblem
+    prm, geo, f, A, c = _case(24, 48, 6, 32)
+    grads = []
+    for every in (1, 4, 50):
+        pb = HeatReleaseProblem(prm, geo, f, A, nsteps=9, every=every)
+        pb.value(c)
+        grads.append(pb.gradient()[0])
+        pb.close()
+    for g in grads[1:]:
+        assert np.array_equal(g, grads[0])
+
+
+def test_seeded_state_functional_gradient():
+    """Objective weight 0 and a seed on Z at the final level: the gradient of
+    <w, Z^N> (and the adjoint field accessors)."""
+    from paper_2603_01727_gb300.lowmach import Simulation
+    prm, geo, f, A, c = _case(24, 48, 6, 32)
+    N = 6
+    w = np.random.Generator(np.random.PCG64(3)).standard_normal((48, 24))
+
+    def run(cc, states=None):
+        g = dict(geo, profile=list(A @ cc))
+        sim = Simulation(prm, g)
+        sim.set_fields(f)
+        sim.step(0)
+        for _ in range(N):
+            if states is not None:
+                buf = np.empty(sim.state_size(), dtype=np.uint8)
+                sim.state_save(buf)
+                states.append(buf)
+            sim.step(1)
+        sim.sync()
+        return sim, float(np.sum(w * sim.get("Z")))
+
+    states = []
+    sim, _ = run(c, states)
+    sim.adjoint_begin()
+    sim.adjoint_seed("Z", w)
+    assert np.array_equal(sim.adjoint_get("Z"), w)
+    gp = None
+    for n in range(N - 1, -1, -1):
+        sim.state_load(states[n])
+        gp = sim.adjoint_step(0.0, n_profile=A.shape[0])
+    gc = A.T @ gp
+    lz = sim.adjoint_get("Z")
+    assert np.all(np.isfinite(lz)) and np.any(lz != 0.0)
+    sim.adjoint_end()
+    sim.close()
+    e = _direction(len(c), seed=11)
+    fp = run(c + FD_H * e)
+    fm = run(c - FD_H * e)
+    fd = (fp[1] - fm[1]) / (2.0 * FD_H)
+    fp[0].close()
+    fm[0].close()
+    ad = float(gc @ e)
+    assert abs(fd - ad) <= TOL * abs(ad), (fd, ad)
+
+
+def test_adjoint_gradient_matches_oracle_differences():
+    """The GPU adjoint's directional derivative against central differences of
+    the FP64 oracle's objective (its own step and exact transform Poisson)."""
+    from oracle import objective as O
+    from oracle import step as S
+    from paper_2603_01727_gb300.adjoint import HeatReleaseProblem
+    prm, geo, f, A, c = _case(24, 48, 6, 32)
+    N = 6
+    pb = HeatReleaseProblem(prm, geo, f, A, nsteps=N, every=3)
+    Jg = pb.value(c)
+    gc, _ = pb.gradient()
+    pb.close()
+    e = _direction(len(c), seed=5)
+
+    def J_oracle(cc):
+        p = S.Problem(prm, dict(geo, profile=list(A @ cc)))
+        st = S.initial_state(p, f["v"], f["Z"], f["H"])
+        return O.objective(p, st, N, S.advance)
+
+    J0 = J_oracle(c)
+    assert abs(J0 - Jg) <= 1e-9 * abs(J0)
+    fd = (J_oracle(c + FD_H * e) - J_oracle(c - FD_H * e)) / (2.0 * FD_H)
+    ad = float(gc @ e)
+    assert abs(fd - ad) <= TOL * abs(ad), (fd, ad)
+
+
+def test_adjoint_rejects_unsupported_configurations():
+    from paper_2603_01727_gb300.lowmach import Simulation, SimError, SIM_EINVAL
+    prm, geo, f, A, c = _case(24, 48, 6, 32)
+    prm = dict(prm, precision=W.MIXED)
+    sim = Simulation(prm, geo)
+    sim.set_fields(f)
+    sim.step(1)
+    with pytest.raises(SimError) as e:
+        sim.adjoint_begin()
+    assert e.value.status == SIM_EINVAL
+    sim.close()

@@ -348,3 +348,51 @@ def test_penalisation_relaxation_rates():
     for a, b in zip(e1, e2):
         assert a < 2e-3
         assert observed_order(a, b, 2.0) == pytest.approx(2.0, abs=0.15)
+
+
+# ---------------------------------------------------------------------------
+# Heat-release objective (oracle/objective.py)
+# ---------------------------------------------------------------------------
+def test_heat_release_curvature_matches_second_differences_of_eq_3_41():
+    from oracle import objective as O
+    fp = flame.derived_parameters(0.055, 7.0, 0.5, 1e-3)
+    Z = np.linspace(0.0, 3.0, 301)
+    h = 1e-4
+    num = (flame.F_eps(Z + h, fp["S"], fp["k"]) - 2.0 * flame.F_eps(Z, fp["S"], fp["k"])
+           + flame.F_eps(Z - h, fp["S"], fp["k"])) / h ** 2
+    ana = O.F_eps_second_derivative(Z, fp["S"], fp["k"])
+    assert np.max(np.abs(num - ana)) <= 1e-5 * np.max(np.abs(ana))
+    assert np.all(ana < 0.0)                     # concave: omega >= 0
+
+
+def test_heat_release_rate_is_the_temperature_curvature_times_dissipation():
+    """omega = -d^2T/dZ^2 kappa |grad Z|^2 / Pe at fixed H (T from Eq 3.42),
+    on a linear Z(x) whose delta_2 gradient is exact."""
+    from oracle import objective as O
+    prm, geo, f = W.slot_burner(16, 32)
+    pb = S.Problem(prm, None)
+    g = pb.g
+    x = (np.arange(g.shape[-1]) - 0.5) * g.h[0]          # padded cell centres along x
+    slope = 7.3
+    Z = np.broadcast_to(0.2 + slope * x, g.shape).copy()
+    kap = np.full(g.shape, 1.7)
+    om = O.heat_release_rate(pb, Z, kap)
+    Zi = V(Z, g)
+    H = 1.3
+    hz = 1e-4
+    d2T = (flame.temperature(Zi + hz, H, pb.fp) - 2.0 * flame.temperature(Zi, H, pb.fp)
+           + flame.temperature(Zi - hz, H, pb.fp)) / hz ** 2
+    ref = -d2T * 1.7 * slope ** 2 / pb.Pe
+    assert np.max(np.abs(om - ref)) <= 1e-5 * np.max(np.abs(ref))
+    assert np.all(om >= 0.0)
+
+
+def test_heat_release_vanishes_for_uniform_mixture():
+    """Z uniform and equal to the inflow value: every delta_2 Z is zero (the
+    Dirichlet and zero-gradient ghosts agree with the interior)."""
+    from oracle import objective as O
+    prm, geo, f = W.slot_burner(16, 32)
+    pb = S.Problem(prm, None)
+    st = S.initial_state(pb, [np.zeros_like(f["Z"]), np.full_like(f["Z"], 0.2)],
+                         np.full_like(f["Z"], prm["inflow_Z"]), f["H"])
+    assert O.heat_release(pb, st) == 0.0

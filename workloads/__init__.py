@@ -179,6 +179,35 @@ def slot_burner(nx=256, ny=512, cfl=0.4, Re=200.0, profile=None, U_coflow=0.2, Z
     return prm, geo, dict(v=[u, v], Z=Z, H=H)
 
 
+def bump_basis(geo, Da_ib, n_bumps=64, n_profile=256):
+    """Gaussian bumps evenly spaced across the shifted slot face [lo, hi]
+    (centres at the midpoints of n_bumps equal parts, standard deviation one
+    part), sampled at n_profile uniform points of [lo, hi]: the profile samples
+    are A @ c with A[k, m] = phi_m(x_k) / sum_m' phi_m'(x_k), so the ejected
+    flux is U_base(x) sum_m c_m phi_m / sum_m phi_m (c = 1: the plain parabola)."""
+    s = np.sqrt(Da_ib)
+    lo = geo["center"][0] - geo["half"][0] - s
+    hi = geo["center"][0] + geo["half"][0] + s
+    xk = np.linspace(lo, hi, n_profile)
+    part = (hi - lo) / n_bumps
+    xm = lo + (np.arange(n_bumps) + 0.5) * part
+    phi = np.exp(-0.5 * ((xk[:, None] - xm[None, :]) / part) ** 2)
+    return phi / phi.sum(axis=1, keepdims=True)
+
+
+def slot_bumps(nx=128, ny=256, n_bumps=64, n_profile=256, seed=SEED, Da_ib=1e-4):
+    """Slot burner (the 2D slot geometry, FP64) whose ejected mass-flux profile
+    is parametrised by n_bumps Gaussian bumps (bump_basis); coefficients
+    c_m ~ U[0.8, 1.2] (seeded).  Returns (prm, geo, fields, basis, c)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = rng.uniform(0.8, 1.2, n_bumps)
+    prm, geo, f = slot_burner(nx, ny, Da_ib=Da_ib)
+    prm["precision"] = FP64
+    A = bump_basis(geo, Da_ib, n_bumps, n_profile)
+    geo["profile"] = list(A @ c)
+    return prm, geo, f, A, c
+
+
 BATCH_GRIDS = ((64, 128), (96, 192), (128, 256))
 
 
