@@ -47,6 +47,8 @@ struct AdjWs {
     double *Ts, *kaps, *Ps;
     double* Fs[3];
     double *col, *grad, *obj, *rep, *part;
+    double* cont;           // scratch of the reverse stencil sweep (slots x padded cells)
+    int use_dual;           // 1: exact dual-number stencil transpose (LOWMACH_ADJ_DUAL=1)
     char* lam_base;         // lambda region (zeroed by begin)
     size_t lam_bytes;
 };
@@ -1241,6 +1243,7 @@ size_t adj_layout(const sim_t* s, AdjWs* A, char* base) {
     a.obj = take(sizeof(double) * 4);
     a.rep = take(sizeof(double) * 4);
     a.part = take(sizeof(double) * kMaxPartials);
+    a.cont = take(fpad * (size_t)residual_rev_slots());
     return off;
 }
 
@@ -1359,6 +1362,10 @@ sim_status sim_adjoint_begin(sim_t* s, void* d_workspace, size_t workspace_bytes
     adj_layout(s, &s->adj, (char*)d_workspace);
     s->adj.i_rho = 0;
     s->adj.i_prev = 1;
+    {
+        const char* dual = std::getenv("LOWMACH_ADJ_DUAL");
+        s->adj.use_dual = (dual && dual[0] == '1') ? 1 : 0;
+    }
     CK(cudaMemsetAsync(s->adj.lam_base, 0, s->adj.lam_bytes, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->adj_active = true;
@@ -1499,10 +1506,11 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
             CK(cudaMemsetAsync(A.LZs, 0, fpad, st));
             CK(cudaMemsetAsync(A.LHs, 0, fpad, st));
             const ResidArgs a = adj_resid_args(s, s->vs, s->Zs, s->Hs, A.kaps, A.Fs, A.Ts);
-            launch_residual_adj(g, ph, a, 0.0, lr, adj_in(s, A.Lvs, A.LZs, A.LHs), st);
+            launch_residual_adj(g, ph, a, 0.0, lr, adj_in(s, A.Lvs, A.LZs, A.LHs), A.use_dual ? nullptr : A.cont,
+                                st);
         } else {
             const ResidArgs a = adj_resid_args(s, A.v0, A.Z0, A.H0, A.kap0, A.F0, A.T0);
-            launch_residual_adj(g, ph, a, 0.0, lr, adj_in(s, A.Lv, A.LZ, A.LH), st);
+            launch_residual_adj(g, ph, a, 0.0, lr, adj_in(s, A.Lv, A.LZ, A.LH), A.use_dual ? nullptr : A.cont, st);
         }
     }
     // density roles one level down; the consumed rho buffer is zero again

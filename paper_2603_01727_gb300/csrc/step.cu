@@ -735,6 +735,250 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Stencil transpose by a hand-written reverse sweep (2D), two phases.
+// Phase 1, per interior cell c: the partial derivatives of
+// sum_o lamR_o(c) R_o(c) with respect to the 40 input values of c's stencil
+// (slots below), stored per slot.  Phase 2, per padded cell j: lambda_f[j] +=
+// the slots of the cells whose stencil reaches j, summed in a fixed order.
+// Same result as the dual-number gather up to rounding order.
+// ---------------------------------------------------------------------------
+// 5-point fields (Z, H, kappa): centre, then -x, +x, -y, +y.
+constexpr int SL_Z = 0, SL_H = 5, SL_K = 10;
+constexpr int SL_F0 = 15;   // F_0 at c and c + s_0
+constexpr int SL_F1 = 17;   // F_1 at c and c + s_1
+constexpr int SL_T = 19;
+constexpr int SL_V0 = 20, SL_V1 = 29;   // v_i on the 3x3 block, (dy+1)*3 + (dx+1)
+constexpr int SL_VIB0 = 38, SL_VIB1 = 39;
+constexpr int SL_N = 40;
+
+__host__ __device__ constexpr int sl5(int j, int sgn) { return sgn == 0 ? 0 : 1 + 2 * j + (sgn > 0 ? 1 : 0); }
+__host__ __device__ constexpr int sl9(int dx, int dy) { return (dy + 1) * 3 + (dx + 1); }
+
+// (field id, dx, dy) of every slot
+struct SlotTab {
+    int f[SL_N], dx[SL_N], dy[SL_N];
+};
+__host__ __device__ constexpr SlotTab make_slots() {
+    SlotTab t{};
+    const int fld5[3] = {RF_Z, RF_H, RF_KAP};
+    for (int q = 0; q < 3; ++q) {
+        const int b = 5 * q;
+        t.f[b] = fld5[q]; t.dx[b] = 0; t.dy[b] = 0;
+        t.f[b + 1] = fld5[q]; t.dx[b + 1] = -1; t.dy[b + 1] = 0;
+        t.f[b + 2] = fld5[q]; t.dx[b + 2] = 1; t.dy[b + 2] = 0;
+        t.f[b + 3] = fld5[q]; t.dx[b + 3] = 0; t.dy[b + 3] = -1;
+        t.f[b + 4] = fld5[q]; t.dx[b + 4] = 0; t.dy[b + 4] = 1;
+    }
+    t.f[SL_F0] = RF_F0; t.dx[SL_F0] = 0; t.dy[SL_F0] = 0;
+    t.f[SL_F0 + 1] = RF_F0; t.dx[SL_F0 + 1] = 1; t.dy[SL_F0 + 1] = 0;
+    t.f[SL_F1] = RF_F1; t.dx[SL_F1] = 0; t.dy[SL_F1] = 0;
+    t.f[SL_F1 + 1] = RF_F1; t.dx[SL_F1 + 1] = 0; t.dy[SL_F1 + 1] = 1;
+    t.f[SL_T] = RF_T; t.dx[SL_T] = 0; t.dy[SL_T] = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            t.f[SL_V0 + sl9(dx, dy)] = RF_V0; t.dx[SL_V0 + sl9(dx, dy)] = dx; t.dy[SL_V0 + sl9(dx, dy)] = dy;
+            t.f[SL_V1 + sl9(dx, dy)] = RF_V1; t.dx[SL_V1 + sl9(dx, dy)] = dx; t.dy[SL_V1 + sl9(dx, dy)] = dy;
+        }
+    t.f[SL_VIB0] = RF_VIB0; t.dx[SL_VIB0] = 0; t.dy[SL_VIB0] = 0;
+    t.f[SL_VIB1] = RF_VIB1; t.dx[SL_VIB1] = 0; t.dy[SL_VIB1] = 0;
+    return t;
+}
+__constant__ SlotTab c_slots = make_slots();
+
+// unit offsets of direction d (2D)
+__device__ __forceinline__ int ex(int d) { return d == 0 ? 1 : 0; }
+__device__ __forceinline__ int ey(int d) { return d == 1 ? 1 : 0; }
+
+__global__ void __launch_bounds__(NT) k_residual_rev(Geom g, Phys ph, ResidArgs a, double p0dot, AdjR lr,
+                                                     double* __restrict__ cont) {
+    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+    if (t >= g.ncell) return;
+    const long long c = pad_index(g, t);
+    double gs[SL_N];
+#pragma unroll
+    for (int k = 0; k < SL_N; ++k) gs[k] = 0.0;
+    const long long S[2] = {g.s[0], g.s[1]};
+
+    // ---- forward values of the scalar part
+    const double kc = a.kap[c], Zc = a.Z[c], Hc = a.H[c];
+    double kflo[2], kfhi[2], dZlo[2], dZhi[2], dHlo[2], dHhi[2], Flo[2], Fhi[2];
+    double convZ = 0.0, convH = 0.0, difZ = 0.0, difH = 0.0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const double ih = g.ih[j];
+        Flo[j] = a.F[j][c];
+        Fhi[j] = a.F[j][c + S[j]];
+        kflo[j] = 0.5 * (a.kap[c - S[j]] + kc);
+        kfhi[j] = 0.5 * (kc + a.kap[c + S[j]]);
+        dZlo[j] = (Zc - a.Z[c - S[j]]) * ih;
+        dZhi[j] = (a.Z[c + S[j]] - Zc) * ih;
+        dHlo[j] = (Hc - a.H[c - S[j]]) * ih;
+        dHhi[j] = (a.H[c + S[j]] - Hc) * ih;
+        convZ += 0.5 * (Flo[j] * dZlo[j] + Fhi[j] * dZhi[j]);
+        convH += 0.5 * (Flo[j] * dHlo[j] + Fhi[j] * dHhi[j]);
+        difZ += (kfhi[j] * dZhi[j] - kflo[j] * dZlo[j]) * ih;
+        difH += (kfhi[j] * dHhi[j] - kflo[j] * dHlo[j]) * ih;
+    }
+    const double iLePe = ph.iLePe, iPe = ph.iPe, Nn = ph.N_O;
+    const bool pen = a.ibm && a.chi[c];
+    double bZ = -convZ + difZ * iLePe;
+    double bH = -convH + difH * iPe + ph.zeta * p0dot + Nn * difZ * iPe;
+    if (pen) {
+        bZ -= kc * (Zc - a.Z_ib) * iLePe * a.inv_Da;
+        bH -= kc * (Hc - a.H_ib) * iPe * a.inv_Da;
+    }
+    const double ip0 = a.sc[a.p0r + SC_INV_OFF];
+    const double irho = a.T[c] * ip0;
+
+    // ---- reverse: scalars
+    const double lR3 = lr.R[3][c], lR4 = lr.R[4][c];
+    gs[SL_T] += (lR3 * bZ + lR4 * bH) * ip0;
+    const double lbZ = lR3 * irho, lbH = lR4 * irho;
+    if (pen) {
+        gs[SL_K] -= (lbZ * (Zc - a.Z_ib) * iLePe + lbH * (Hc - a.H_ib) * iPe) * a.inv_Da;
+        gs[SL_Z] -= lbZ * kc * iLePe * a.inv_Da;
+        gs[SL_H] -= lbH * kc * iPe * a.inv_Da;
+    }
+    const double lconvZ = -lbZ, lconvH = -lbH;
+    const double ldifZ = lbZ * iLePe + lbH * Nn * iPe, ldifH = lbH * iPe;
+    double lkflo[2], lkfhi[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const double ih = g.ih[j];
+        gs[(j == 0 ? SL_F0 : SL_F1)] += 0.5 * (lconvZ * dZlo[j] + lconvH * dHlo[j]);
+        gs[(j == 0 ? SL_F0 : SL_F1) + 1] += 0.5 * (lconvZ * dZhi[j] + lconvH * dHhi[j]);
+        const double ldZlo = 0.5 * lconvZ * Flo[j] - ldifZ * kflo[j] * ih;
+        const double ldZhi = 0.5 * lconvZ * Fhi[j] + ldifZ * kfhi[j] * ih;
+        const double ldHlo = 0.5 * lconvH * Flo[j] - ldifH * kflo[j] * ih;
+        const double ldHhi = 0.5 * lconvH * Fhi[j] + ldifH * kfhi[j] * ih;
+        lkfhi[j] = (ldifZ * dZhi[j] + ldifH * dHhi[j]) * ih;
+        lkflo[j] = -(ldifZ * dZlo[j] + ldifH * dHlo[j]) * ih;
+        gs[SL_Z + sl5(j, 0)] += (ldZlo - ldZhi) * ih;
+        gs[SL_Z + sl5(j, -1)] -= ldZlo * ih;
+        gs[SL_Z + sl5(j, 1)] += ldZhi * ih;
+        gs[SL_H + sl5(j, 0)] += (ldHlo - ldHhi) * ih;
+        gs[SL_H + sl5(j, -1)] -= ldHlo * ih;
+        gs[SL_H + sl5(j, 1)] += ldHhi * ih;
+    }
+
+    // ---- momentum
+    const double two3 = 2.0 / 3.0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const double* vi = a.v[i];
+        const int SVi = (i == 0) ? SL_V0 : SL_V1;
+        const double lRi = lr.R[i][c];
+        const double lconv = -lRi, lvisc = ph.PrPe * lRi;
+        if (pen) {
+            const double q = lRi * ph.PrPe * a.inv_Da;
+            gs[SL_K] -= q * (vi[c] - a.vib[i][c]);
+            gs[SVi + sl9(0, 0)] -= q * kc;
+            gs[(i == 0) ? SL_VIB0 : SL_VIB1] += q * kc;
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const long long s = S[j];
+            const double ih = g.ih[j];
+            const int SFj = (j == 0) ? SL_F0 : SL_F1;
+            const double vl = vi[c - s], vc = vi[c], vh = vi[c + s];
+            gs[SFj + 1] += lconv * ih * 0.5 * (vc + vh);
+            gs[SFj] -= lconv * ih * 0.5 * (vl + vc);
+            gs[SVi + sl9(0, 0)] += lconv * ih * 0.5 * (Fhi[j] - Flo[j]);
+            gs[SVi + sl9(ex(j), ey(j))] += lconv * ih * 0.5 * Fhi[j];
+            gs[SVi + sl9(-ex(j), -ey(j))] -= lconv * ih * 0.5 * Flo[j];
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const double lt = (side ? 1.0 : -1.0) * lvisc * ih;
+                const int oax = side ? 0 : -ex(j), oay = side ? 0 : -ey(j);   // ca offset
+                const int obx = oax + ex(j), oby = oay + ey(j);                // cb offset
+                const double kf = side ? kfhi[j] : kflo[j];
+                const double dvi = (side ? (vh - vc) : (vc - vl)) * ih;
+                double ldvi, lkf;
+                if (i != j) {
+                    const int k2 = i;   // the other direction
+                    const double* vj = a.v[j];
+                    const long long sk = S[k2];
+                    const double hk2 = 0.5 * g.ih[k2];
+                    const long long ca = c + oax + (long long)oay * g.s[1];
+                    const long long cb = c + obx + (long long)oby * g.s[1];
+                    const double da = (vj[ca + sk] - vj[ca - sk]) * hk2;
+                    const double db = (vj[cb + sk] - vj[cb - sk]) * hk2;
+                    const double dvj = 0.5 * (da + db);
+                    lkf = lt * (dvi + dvj);
+                    ldvi = lt * kf;
+                    const double q = 0.5 * lt * kf * hk2;
+                    const int SVj = (j == 0) ? SL_V0 : SL_V1;
+                    gs[SVj + sl9(oax + ex(k2), oay + ey(k2))] += q;
+                    gs[SVj + sl9(oax - ex(k2), oay - ey(k2))] -= q;
+                    gs[SVj + sl9(obx + ex(k2), oby + ey(k2))] += q;
+                    gs[SVj + sl9(obx - ex(k2), oby - ey(k2))] -= q;
+                } else {
+                    const int k2 = 1 - j;
+                    const double* vk = a.v[k2];
+                    const long long sk = S[k2];
+                    const double hk2 = 0.5 * g.ih[k2];
+                    const long long ca = c + oax + (long long)oay * g.s[1];
+                    const long long cb = c + obx + (long long)oby * g.s[1];
+                    const double da = (vk[ca + sk] - vk[ca - sk]) * hk2;
+                    const double db = (vk[cb + sk] - vk[cb - sk]) * hk2;
+                    const double div = dvi + 0.5 * (da + db);
+                    lkf = lt * (2.0 * dvi - two3 * div);
+                    ldvi = lt * kf * (2.0 - two3);
+                    const double q = -two3 * lt * kf * 0.5 * hk2;
+                    const int SVk = (k2 == 0) ? SL_V0 : SL_V1;
+                    gs[SVk + sl9(oax + ex(k2), oay + ey(k2))] += q;
+                    gs[SVk + sl9(oax - ex(k2), oay - ey(k2))] -= q;
+                    gs[SVk + sl9(obx + ex(k2), oby + ey(k2))] += q;
+                    gs[SVk + sl9(obx - ex(k2), oby - ey(k2))] -= q;
+                }
+                if (side) {
+                    gs[SVi + sl9(ex(j), ey(j))] += ldvi * ih;
+                    gs[SVi + sl9(0, 0)] -= ldvi * ih;
+                    lkfhi[j] += lkf;
+                } else {
+                    gs[SVi + sl9(0, 0)] += ldvi * ih;
+                    gs[SVi + sl9(-ex(j), -ey(j))] -= ldvi * ih;
+                    lkflo[j] += lkf;
+                }
+            }
+        }
+    }
+    // face kappa = arithmetic mean of the two cells
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        gs[SL_K + sl5(j, -1)] += 0.5 * lkflo[j];
+        gs[SL_K + sl5(j, 0)] += 0.5 * (lkflo[j] + lkfhi[j]);
+        gs[SL_K + sl5(j, 1)] += 0.5 * lkfhi[j];
+    }
+    const long long np = g.npad;
+#pragma unroll
+    for (int k = 0; k < SL_N; ++k) cont[(long long)k * np + c] = gs[k];
+}
+
+__global__ void __launch_bounds__(NT) k_residual_rev_gather(Geom g, const double* __restrict__ cont, AdjIn li) {
+    const long long j = (long long)blockIdx.x * NT + threadIdx.x;
+    if (j >= g.npad) return;
+    int q[3];
+    padded_coords(g, j, q);
+    const long long np = g.npad;
+    double acc = 0.0;
+    int cur = c_slots.f[0];
+    for (int k = 0; k < SL_N; ++k) {
+        const int f = c_slots.f[k];
+        if (f != cur) {
+            if (li.out[cur]) li.out[cur][j] += acc;
+            acc = 0.0;
+            cur = f;
+        }
+        // the cell whose stencil offset (dx, dy) lands on j
+        const int qc[3] = {q[0] - c_slots.dx[k], q[1] - c_slots.dy[k], q[2]};
+        if (!padded_interior(g, qc)) continue;
+        acc += cont[(long long)k * np + j - c_slots.dx[k] - (long long)c_slots.dy[k] * g.s[1]];
+    }
+    if (li.out[cur]) li.out[cur][j] += acc;
+}
+
 // Ghost fill of direction d transposed: ghost = s * adjacent (+ constant) or a
 // periodic copy, so lam_adjacent += s * lam_ghost and the ghost's lambda is
 // consumed (zeroed).  Directions are transposed in reverse order.
@@ -1259,10 +1503,17 @@ void launch_u8_to_double(const Geom& g, const uint8_t* padded, double* compact, 
 
 // ------------------------------- adjoint launchers -------------------------------
 void launch_residual_adj(const Geom& g, const Phys& ph, const ResidArgs& a, double p0dot, const AdjR& lr,
-                         const AdjIn& li, cudaStream_t s) {
+                         const AdjIn& li, double* cont, cudaStream_t s) {
+    if (cont && g.dim == 2) {
+        k_residual_rev<<<blocks_for(g.ncell), NT, 0, s>>>(g, ph, a, p0dot, lr, cont);
+        k_residual_rev_gather<<<blocks_for(g.npad), NT, 0, s>>>(g, cont, li);
+        return;
+    }
     if (g.dim == 3) k_residual_adj<3><<<blocks_for(g.npad), NT, 0, s>>>(g, ph, a, p0dot, lr, li);
     else k_residual_adj<2><<<blocks_for(g.npad), NT, 0, s>>>(g, ph, a, p0dot, lr, li);
 }
+
+int residual_rev_slots() { return SL_N; }
 
 void launch_ghost_adj(const Geom& g, const Bnd& bnd, const GhostJob& job, cudaStream_t s) {
     for (int d = g.dim - 1; d >= 0; --d) {   // the forward fill runs d = 0, 1, 2

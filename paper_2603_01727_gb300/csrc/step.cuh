@@ -189,8 +189,12 @@ void launch_add_unpack(const Geom& g, const double* compact, double* padded, cud
 
 // Adjoint (reverse-mode) launchers; every one adds the adjoint of its forward
 // kernel's inputs given the adjoint of its outputs.
+// Stencil transpose: with cont (residual_rev_slots() padded arrays of
+// scratch, 2D), the hand-written reverse sweep and its gather; with cont null,
+// the exact dual-number gather (any dimension; the checker of the former).
 void launch_residual_adj(const Geom& g, const Phys& ph, const ResidArgs& a, double p0dot, const AdjR& lr,
-                         const AdjIn& li, cudaStream_t s);
+                         const AdjIn& li, double* cont, cudaStream_t s);
+int residual_rev_slots();
 void launch_ghost_adj(const Geom& g, const Bnd& bnd, const GhostJob& job, cudaStream_t s);
 void launch_state_adj(const Geom& g, const Phys& ph, const double* Z, const double* T, const double* kap,
                       double* lT, double* lrho, double* lkap, double* lZ, double* lH, cudaStream_t s);
