@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="slot", choices=["slot", "sphere", "blobs", "batch"])
+    ap.add_argument("--config", default="slot", choices=["slot", "sphere", "blobs", "batch", "adjoint"])
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -75,6 +75,13 @@ def workload(name):
         cfg = {"workload": "3D 192^3 spherical porous burner (IBM sphere r=0.1L, radial fuel mass flux "
                            "Re=150, quiescent air, density ratio 7, 1% perturbations, outflow all sides)",
                "grid": [192, 192, 192]}
+    elif name == "adjoint":
+        prm, geo, f, _, _ = W.slot_bumps()
+        cfg = {"workload": "discrete adjoint of the step on the 2D 128x256 slot burner whose fuel flux profile "
+                           "is 64 Gaussian bumps (coefficients ~U[0.8,1.2]); one adjoint step = recompute of "
+                           "the step from its level + transpose of corrector and predictor (two transposed "
+                           "Poisson solves); gradient of the heat release over 200 steps, checkpoints every 20",
+               "grid": [128, 256], "bumps": 64, "profile_samples": 256}
     elif name == "batch":
         # the oracle's sample of the batched workload: its first flame
         prm, geo, f = W.batched_flames(1)[0]
@@ -379,6 +386,96 @@ def run_gpu_batch(args, precision, world, rank, local, pg):
     return out
 
 
+def run_gpu_adjoint(args, precision, world, rank, local, pg):
+    """Adjoint config: K reverse steps over the states of a K-step forward run
+    (device copies), each a recompute of the step plus its transpose; and the
+    wall time of the whole checkpointed gradient of J over 200 steps."""
+    import torch
+    from paper_2603_01727_gb300 import lowmach as LM
+    from paper_2603_01727_gb300.adjoint import HeatReleaseProblem
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    prm, geo, f, cfg = workload("adjoint")
+    _, _, _, basis, coef = W.slot_bumps()
+    stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(stream)
+    sim = LM.Simulation(prm, geo, device=device, stream=stream)
+    sim.set_fields(f)
+    ncell = int(sim.query(LM.SIM_Q_NCELLS))
+    K = max(1, min(args.steps, 200))
+    sim.step(max(args.warmup, 3))
+    states = []
+    for _ in range(K):
+        b = torch.empty(sim.state_size(), dtype=torch.uint8, device=device)
+        sim.state_save(b)
+        states.append(b)
+        sim.step(1)
+    sim.sync()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    sim.adjoint_begin()
+    for n in range(min(3, K) - 1, -1, -1):             # warm-up reverse steps
+        sim.state_load(states[n])
+        sim.adjoint_step(prm["dt"])
+    sim.adjoint_end()
+    sim.adjoint_begin()
+    clocks = Clocks(device.index)
+    barrier(pg, device)
+    torch.cuda.synchronize(device)
+    flush.zero_()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for n in range(K - 1, -1, -1):
+        sim.state_load(states[n])
+        sim.adjoint_step(prm["dt"])
+        launches += int(sim.query(LM.SIM_Q_KERNEL_LAUNCHES))
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    barrier(pg, device)
+    ms = e0.elapsed_time(e1)
+    ms_max = reduce_max(pg, ms, device)
+    value = reduce_sum(pg, float(ncell) * K, device) / (ms_max * 1e-3)
+    # the reverse stencil sweep timed alone (graph of 100 launches on the stream)
+    reps = 100
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        sim.time_kernel(LM.SIM_K_RESIDUAL_REV, reps)
+    graph.replay()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    graph.replay()
+    graph.replay()
+    b.record(stream)
+    torch.cuda.synchronize(device)
+    t_rev = a.elapsed_time(b) * 1e-3 / (2 * reps)
+    del graph
+    sim.adjoint_end()
+    # whole checkpointed gradient, wall clock
+    hp = HeatReleaseProblem(prm, geo, f, basis, nsteps=200, every=20, device=device, stream=stream)
+    t0 = time.perf_counter()
+    J = hp.value(coef)
+    t1 = time.perf_counter()
+    gc, _ = hp.gradient()
+    t2 = time.perf_counter()
+    hp.close()
+    flops = 400.0 * ncell                  # operations of the reverse sweep per cell (model)
+    tfl = flops / t_rev / 1e12
+    share = 2 * t_rev / (ms / K * 1e-3)
+    rl = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (fp64)",
+          "frac": tfl / FP64_PEAK_TFLOPS, "kernel": "reverse stencil sweep + gather (k_residual_rev, "
+          "k_residual_rev_gather)", "launch_us": t_rev * 1e6, "share_of_step": share, "traffic": None,
+          "peak_source": "nominal GB300 FP64 rate (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)",
+          "flops_per_cell": 400.0}
+    cfg.update(gradient={"J": J, "forward_s": t1 - t0, "gradient_s": t2 - t1, "steps": 200, "checkpoint_every": 20,
+                         "grad_norm": float(np.linalg.norm(gc))})
+    return dict(value=value, ms_per_step=ms_max / K, launches=launches, iters_per_step=float("nan"), relres=None,
+                clocks=clk, ktimes={}, models={}, ncell=ncell, cfg=cfg, sim=None, roofline=rl)
+
+
 def e2e_gpu(args, precision, res, device):
     """Same metric through the C ABI with host buffers: every step loads the
     restart state from pinned host memory, steps once and saves the state back
@@ -526,11 +623,13 @@ def main():
     import torch
     device = torch.device("cuda", local)
     precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    if args.config == "adjoint":
+        precs = ["fp64"]                   # the adjoint covers the FP64 step
     from paper_2603_01727_gb300 import lowmach as LM
     results = {}
     for p in precs:
         try:
-            runner = run_gpu_batch if args.config == "batch" else run_gpu
+            runner = {"batch": run_gpu_batch, "adjoint": run_gpu_adjoint}.get(args.config, run_gpu)
             results[p] = runner(args, p, world, rank, local, pg)
         except LM.SimError as e:
             if p == "mixed" and e.status == LM.SIM_EINVAL and args.precision == "both":
@@ -547,6 +646,9 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{done} FP64 oracle steps of the same workload from its initial state "
                          f"({secs:.1f} s, numpy/scipy single-threaded)"}
+        if args.config == "adjoint":
+            cpu["sample"] += ("; forward steps: the oracle has no adjoint, its gradient by central differences "
+                              "costs 2 forward runs per coefficient (128 for 64 bumps)")
     if rank != 0:
         return
     cfg = dict(res["cfg"])

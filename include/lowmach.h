@@ -200,7 +200,9 @@ enum {
     SIM_K_MG_UP = 3,      /* fine level: prolongation-add, black, red (one kernel)        */
     SIM_K_STATE = 4,      /* flame-sheet state relation                                  */
     SIM_K_PROJECT = 5,    /* interface fluxes + cell velocities (projection)             */
-    SIM_K_MG_TAIL = 6     /* coarse multigrid levels in one thread block                 */
+    SIM_K_MG_TAIL = 6,    /* coarse multigrid levels in one thread block                 */
+    SIM_K_RESIDUAL_REV = 7 /* adjoint: reverse stencil sweep + gather (after
+                              sim_adjoint_begin; adds into the adjoint state)            */
 };
 sim_status sim_time_kernel(sim_t *sim, int kernel, int reps);
 

@@ -659,6 +659,13 @@ sim_status check_device_status(sim_t* s) {
 
 }  // namespace
 
+// adjoint helpers (defined with the adjoint entry points below)
+namespace {
+ResidArgs adj_resid_args(sim_t* s, double* const* v, const double* Z, const double* H, const double* kap,
+                         double* const* F, const double* T);
+AdjIn adj_in(sim_t* s, double* const* lv, double* lZ, double* lH);
+}  // namespace
+
 // ============================== C ABI ========================================
 extern "C" {
 
@@ -1030,6 +1037,18 @@ sim_status sim_time_kernel(sim_t* s, int kernel, int reps) {
                 launch_project(g, pa, s->stream, &L);
                 break;
             }
+            case SIM_K_RESIDUAL_REV: {
+                // reverse stencil sweep and gather of the predictor stage (adds into lambda)
+                if (!s->adj_active) return fail(s, SIM_ESTATE, "time the reverse stencil after sim_adjoint_begin");
+                AdjWs& A = s->adj;
+                AdjR lr;
+                for (int k = 0; k < 5; ++k) lr.R[k] = A.LR[k];
+                const ResidArgs a = adj_resid_args(s, s->v, s->Z, s->H, s->kap, s->F, s->T);
+                launch_residual_adj(g, s->ph, a, 0.0, lr, adj_in(s, A.Lv, A.LZ, A.LH), A.use_dual ? nullptr : A.cont,
+                                    s->stream);
+                L += 2;
+                break;
+            }
             default: return fail(s, SIM_EINVAL, "unknown kernel id %d", kernel);
         }
     }
@@ -1392,6 +1411,7 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
     cudaStream_t st = s->stream;
     const size_t fpad = sizeof(double) * (size_t)g.npad;
     const Roles r = roles(s, n);
+    int La = 0;   // kernels enqueued by this call
 
     // level-n values, then the step recomputed with its predictor values saved
     for (int d = 0; d < D; ++d) {
@@ -1409,7 +1429,7 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
         cudaError_t e = enqueue_step(s, n, st, false, &L, &body);
         s->adj_save = false;
         CK(e);
-        s->launches_last = L;
+        La += L;
         after_step(s);
     }
     // s->vs = v*, s->Zs / Hs = Z* / H*, s->mom = corrector momentum, s->Z / H / T /
@@ -1422,7 +1442,10 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
     const double bdf[4] = {n == 0 ? bc0 : 3.0, bc1, n == 0 ? 0.0 : 1.0, n == 0 ? dt : 2.0 * dt};
 
     // objective term of level n+1
-    if (objective_weight != 0.0) launch_objective_adj(g, ph, s->Z, s->kap, objective_weight, A.LZ, A.Lkap, st);
+    if (objective_weight != 0.0) {
+        launch_objective_adj(g, ph, s->Z, s->kap, objective_weight, A.LZ, A.Lkap, st);
+        La += 1;
+    }
 
     for (int stage = 1; stage >= 0; --stage) {   // corrector, then predictor
         const bool corr = stage == 1;
@@ -1449,7 +1472,9 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
         pj.eC = s->eC;
         launch_project_adj(g, pj, st);
         // pressure solve^T
+        s->pp.launches = 0;
         CK(adj_poisson(s, A.LP, A.Lb, st));
+        La += D + 1 + s->pp.launches;
         // face fluxes and right-hand side^T
         FluxAdj fa;
         std::memset(&fa, 0, sizeof(fa));
@@ -1470,6 +1495,7 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
         fa.sc = s->sc;
         fa.part = A.part;
         launch_flux_adj(g, s->bnd, fa, st);
+        La += 2 + 2 * D + 2;       // flux (2), kappa and Z/H ghost fills (2 x D), state, combination
         // state relation^T (kappa ghosts first), then the Z, H ghost fill^T
         double* lZo = corr ? A.LZ : A.LZs;
         double* lHo = corr ? A.LH : A.LHs;
@@ -1512,15 +1538,18 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
             const ResidArgs a = adj_resid_args(s, A.v0, A.Z0, A.H0, A.kap0, A.F0, A.T0);
             launch_residual_adj(g, ph, a, 0.0, lr, adj_in(s, A.Lv, A.LZ, A.LH), A.use_dual ? nullptr : A.cont, st);
         }
+        La += A.use_dual ? 1 : 2;
     }
     // density roles one level down; the consumed rho buffer is zero again
     A.i_rho = A.i_prev;
     A.i_prev = i_free;
+    s->launches_last = La;
     CK(cudaGetLastError());
     if (dJ_dprofile) {
         if (!s->ibm_active || s->ibm.kind != SIM_IBM_SLOT || s->ibm.n_profile < 2)
             return fail(s, SIM_EINVAL, "dJ_dprofile needs a slot body with a flux profile");
         launch_profile_grad(g, s->ibm, s->chi, A.Lvib[1], A.LSm, A.col, A.grad, st);
+        s->launches_last += 2;
         CK(cudaMemcpyAsync(dJ_dprofile, A.grad, sizeof(double) * s->ibm.n_profile, cudaMemcpyDeviceToHost, st));
     }
     return check_device_status(s);

@@ -26,7 +26,7 @@ SIM_IBM_NONE, SIM_IBM_SLOT, SIM_IBM_SPHERE = 0, 1, 2
  SIM_FIELD_KAPPA) = range(14)
 SIM_GET, SIM_SET = 0, 1
 (SIM_K_RESIDUAL, SIM_K_MG_DOWN, SIM_K_CG_MATVEC, SIM_K_MG_UP, SIM_K_STATE, SIM_K_PROJECT,
- SIM_K_MG_TAIL) = range(7)
+ SIM_K_MG_TAIL, SIM_K_RESIDUAL_REV) = range(8)
 (SIM_Q_TIME, SIM_Q_DT, SIM_Q_P0, SIM_Q_STEPS, SIM_Q_ITERS_PRED, SIM_Q_ITERS_CORR, SIM_Q_RESID_PRED,
  SIM_Q_RESID_CORR, SIM_Q_MASS, SIM_Q_NCELLS, SIM_Q_MG_LEVELS, SIM_Q_KERNEL_LAUNCHES, SIM_Q_TAIL_NX,
  SIM_Q_TAIL_NY, SIM_Q_TAIL_FDM) = range(15)
