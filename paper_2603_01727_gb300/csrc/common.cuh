@@ -88,6 +88,73 @@ __device__ inline Dual tanh_c(Dual x) {
 }
 
 // ---------------------------------------------------------------------------
+// Float-float number: an unevaluated sum hi + lo of two FP32 values with
+// |lo| <= ulp(hi)/2, about 48 significant bits, computed on the FP32 pipes
+// (GB300 runs FP64 at 1/64 of the FP32 rate).  Error-free transformations:
+// Knuth's two-sum, the fast two-sum of Dekker (|a| >= |b|), and the exact
+// product error by one fused multiply-add.  Addition is the one-pass
+// ("sloppy") form: relative error ~2^-44, or an absolute ~2^-48 max(|a|,|b|)
+// under cancellation; multiplication ~2^-46.  Conversions from double keep 48
+// bits of the input.
+// ---------------------------------------------------------------------------
+struct FF {
+    float hi, lo;
+    __device__ __forceinline__ FF() : hi(0.f), lo(0.f) {}
+    __device__ __forceinline__ FF(float h, float l) : hi(h), lo(l) {}
+    // Split of a double by integer operations on its bits (no FP64 or
+    // conversion instructions): hi = x truncated to 24 significant bits, lo =
+    // the remaining 29 bits truncated to 24; |x| < 2^-74 (far below every
+    // field's scale) keeps hi only, zero and non-normal floats map to zero.
+    __device__ __forceinline__ FF(double x) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+        const unsigned int h32 = (unsigned int)(b >> 32), l32 = (unsigned int)b;
+        const unsigned int sgn = h32 & 0x80000000u;
+        const int e = (int)((h32 >> 20) & 0x7ffu);
+        if (e < 897 || e > 1150) {
+            hi = 0.f;
+            lo = 0.f;
+            return;
+        }
+        hi = __uint_as_float(sgn | ((unsigned int)(e - 896) << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29));
+        const unsigned int r = l32 & 0x1fffffffu;
+        const int lz = __clz(r);
+        const int ef = e - 917 - lz;   // float exponent field of r * 2^(e - 1075)
+        lo = (r == 0u || ef < 1) ? 0.f
+                                 : __uint_as_float(sgn | ((unsigned int)ef << 23) | ((r << (lz + 1)) >> 9));
+    }
+    __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return FF(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ FF operator+(FF a, FF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return ff_fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ FF operator-(FF a) { return FF(-a.hi, -a.lo); }
+__device__ __forceinline__ FF operator-(FF a, FF b) { return a + (-b); }
+__device__ __forceinline__ FF operator*(FF a, FF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ FF operator/(FF a, FF b) {
+    // q1 = a/b in FP32, then one correction from the float-float remainder
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const FF r = a - b * FF(q1, 0.f);
+    const float q2 = __fdiv_rn(r.hi, b.hi);
+    return ff_fast_two_sum(q1, q2);
+}
+__device__ __forceinline__ FF& operator+=(FF& a, FF b) { return a = a + b; }
+__device__ __forceinline__ FF& operator-=(FF& a, FF b) { return a = a - b; }
+__device__ inline FF tanh_c(FF x) { return FF(tanh((double)x)); }
+
+// ---------------------------------------------------------------------------
 // Deterministic block reduction (fixed tree for a fixed block size).
 // ---------------------------------------------------------------------------
 template <int NT>

@@ -325,28 +325,29 @@ __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, con
     R[4] = bH * irho;
 }
 
+// C: arithmetic of the stencil terms (double, or float-float in the mixed
+// path); the residuals are stored and combined in FP64.
 template <int DIM, class C>
 __global__ void __launch_bounds__(NT) k_residual(Geom g, Phys ph, ResidArgs a) {
     const long long t = (long long)blockIdx.x * NT + threadIdx.x;
     if (t >= g.ncell) return;
     const long long c = pad_index(g, t);
-    const C* Rrd[5];
-    C* Rst[5];
+    const double* Rrd[5];
+    double* Rst[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        Rrd[k] = reinterpret_cast<const C*>(a.Rrd[k]);
-        Rst[k] = reinterpret_cast<C*>(a.Rst[k]);
+        Rrd[k] = reinterpret_cast<const double*>(a.Rrd[k]);
+        Rst[k] = reinterpret_cast<double*>(a.Rst[k]);
     }
     // dp0/dt for the H source (Eqs 3.5, 3.14)
     const double p0dot = (a.wden != 0.0) ? (a.w0 * a.sc[a.p0a] + a.w1 * a.sc[a.p0b] + a.w2 * a.sc[a.p0c]) * a.iwden
                                          : 0.0;
     C Rall[5];
     residual_cell<DIM, C>(g, ph, a, c, p0dot, PlainLoad{&a}, Rall);
-    C Rv[DIM];
+    double Rv[DIM];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) Rv[i] = Rall[i];
-    const C RZ = Rall[3], RH = Rall[4];
-    const C half = (C)0.5;
+    for (int i = 0; i < DIM; ++i) Rv[i] = (double)Rall[i];
+    const double RZ = (double)Rall[3], RH = (double)Rall[4];
 
     // combination (FP64 state update)
     const double dt = a.dt;
@@ -354,24 +355,23 @@ __global__ void __launch_bounds__(NT) k_residual(Geom g, Phys ph, ResidArgs a) {
     if (a.mode == MODE_CORR) {
         const double hdt = 0.5 * dt;
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) a.mo[i][c] = fma(hdt, (double)(Rv[i] + Rrd[i][c]), rb * a.vb[i][c]);
-        a.Zo[c] = fma(hdt, (double)(RZ + Rrd[3][c]), a.Zb[c]);
-        a.Ho[c] = fma(hdt, (double)(RH + Rrd[4][c]), a.Hb[c]);
+        for (int i = 0; i < DIM; ++i) a.mo[i][c] = fma(hdt, Rv[i] + Rrd[i][c], rb * a.vb[i][c]);
+        a.Zo[c] = fma(hdt, RZ + Rrd[3][c], a.Zb[c]);
+        a.Ho[c] = fma(hdt, RH + Rrd[4][c], a.Hb[c]);
     } else {
         const bool ab2 = (a.mode == MODE_PRED_AB2);
-        const C c15 = (C)1.5;
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
-            const C cv = ab2 ? (c15 * Rv[i] - half * Rrd[i][c]) : Rv[i];
+            const double cv = ab2 ? (1.5 * Rv[i] - 0.5 * Rrd[i][c]) : Rv[i];
             Rst[i][c] = Rv[i];
-            a.mo[i][c] = fma(dt, (double)cv, rb * a.vb[i][c]);
+            a.mo[i][c] = fma(dt, cv, rb * a.vb[i][c]);
         }
-        const C cZ = ab2 ? (c15 * RZ - half * Rrd[3][c]) : RZ;
-        const C cH = ab2 ? (c15 * RH - half * Rrd[4][c]) : RH;
+        const double cZ = ab2 ? (1.5 * RZ - 0.5 * Rrd[3][c]) : RZ;
+        const double cH = ab2 ? (1.5 * RH - 0.5 * Rrd[4][c]) : RH;
         Rst[3][c] = RZ;
         Rst[4][c] = RH;
-        a.Zo[c] = fma(dt, (double)cZ, a.Zb[c]);
-        a.Ho[c] = fma(dt, (double)cH, a.Hb[c]);
+        a.Zo[c] = fma(dt, cZ, a.Zb[c]);
+        a.Ho[c] = fma(dt, cH, a.Hb[c]);
     }
 }
 
@@ -1396,10 +1396,17 @@ void launch_state(const Geom& g, const Phys& ph, const double* Z, const double* 
 
 void launch_residual(const Geom& g, const Phys& ph, const ResidArgs& a, cudaStream_t s, int* launches) {
     const int nb = blocks_for(g.ncell);
-    // FP64 in both precision modes: the pressure is the dt-scaled divergence of
-    // the momentum increment and inherits its relative rounding directly
-    if (g.dim == 3) k_residual<3, double><<<nb, NT, 0, s>>>(g, ph, a);
-    else k_residual<2, double><<<nb, NT, 0, s>>>(g, ph, a);
+    // FP64, or float-float (~48 bits on the FP32 pipes) in the mixed path: the
+    // pressure is the dt-scaled divergence of the momentum increment and
+    // inherits the stencil's relative rounding directly, which plain FP32
+    // (24 bits) leaves above 1e-6
+    if (ph.mixed) {
+        if (g.dim == 3) k_residual<3, FF><<<nb, NT, 0, s>>>(g, ph, a);
+        else k_residual<2, FF><<<nb, NT, 0, s>>>(g, ph, a);
+    } else {
+        if (g.dim == 3) k_residual<3, double><<<nb, NT, 0, s>>>(g, ph, a);
+        else k_residual<2, double><<<nb, NT, 0, s>>>(g, ph, a);
+    }
     ++*launches;
 }
 
