@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="slot", choices=["slot", "sphere", "blobs", "batch", "adjoint"])
     ap.add_argument("--batch-size", type=int, default=256)
+    ap.add_argument("--n", type=int, default=0,
+                    help="grid override for small profiling captures: slot n x 2n, sphere n^3 (0: the workload's)")
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -63,18 +65,20 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name):
-    """(prm, geo, fields, config description)."""
+def workload(name, n=0):
+    """(prm, geo, fields, config description); n > 0 shrinks the grid (profiling)."""
     if name == "slot":
-        prm, geo, f = W.slot_burner(256, 512)
-        cfg = {"workload": "2D 256x512 planar slot-burner diffusion flame (immersed 0.1x0.3 burner, "
+        nx = n if n > 0 else 256
+        prm, geo, f = W.slot_burner(nx, 2 * nx)
+        cfg = {"workload": f"2D {nx}x{2 * nx} planar slot-burner diffusion flame (immersed 0.1x0.3 burner, "
                            "parabolic fuel mass flux peak Re=200, coflow 0.2, density ratio 7, Z_st=0.055, "
-                           "outflow top)", "grid": [256, 512]}
+                           "outflow top)", "grid": [nx, 2 * nx]}
     elif name == "sphere":
-        prm, geo, f = W.sphere_burner(192)
-        cfg = {"workload": "3D 192^3 spherical porous burner (IBM sphere r=0.1L, radial fuel mass flux "
+        m = n if n > 0 else 192
+        prm, geo, f = W.sphere_burner(m)
+        cfg = {"workload": f"3D {m}^3 spherical porous burner (IBM sphere r=0.1L, radial fuel mass flux "
                            "Re=150, quiescent air, density ratio 7, 1% perturbations, outflow all sides)",
-               "grid": [192, 192, 192]}
+               "grid": [m, m, m]}
     elif name == "adjoint":
         prm, geo, f, _, _ = W.slot_bumps()
         cfg = {"workload": "discrete adjoint of the step on the 2D 128x256 slot burner whose fuel flux profile "
@@ -237,7 +241,7 @@ def run_gpu(args, precision, world, rank, local, pg):
     from paper_2603_01727_gb300 import lowmach as LM
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
-    prm, geo, f, cfg = workload(args.config)
+    prm, geo, f, cfg = workload(args.config, args.n)
     prm["precision"] = LM.SIM_MIXED if precision == "mixed" else LM.SIM_FP64
     stream = torch.cuda.Stream(device)     # side stream: kernel timing captures graphs on it
     torch.cuda.set_stream(stream)
@@ -538,6 +542,21 @@ def roofline(res, peaks, precision):
     gbs = m["bytes"] / t / 1e9
     fp64_tflops = FP64_PEAK_TFLOPS
     tfl = m["flops"] / t / 1e12
+    if top == "residual" and precision == "mixed":
+        # float-float stencil on the FP32 pipes: bound by instruction issue
+        # (4 warp instructions / clk / SM); warp instructions per cell measured
+        # by ncu (smsp__inst_executed.sum / cells on 128x256 and 64^3)
+        dim = res["prm"]["dim"]
+        wi = RESIDUAL_FF_WARP_INSTR_PER_CELL[dim] * res["ncell"]
+        pk = ISSUE_PEAK_WARP_INSTR / 1e12
+        ach = wi / t / 1e12
+        rl = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "T warp-instructions/s (issue)",
+              "frac": ach / pk}
+        rl.update(kernel=top, launch_us=t * 1e6, share_of_step=share[top], traffic=None,
+                  peak_source="152 SMs x 4 warp instructions/clk x 2.07 GHz; instructions per cell "
+                              f"{RESIDUAL_FF_WARP_INSTR_PER_CELL[dim]} measured by ncu",
+                  shares={k: round(v, 4) for k, v in share.items()}, nlev=nlev)
+        return rl
     fp64_kernel = (precision == "fp64") or top in ("residual", "state", "project")
     if m.get("one_sm"):
         # one thread block by design: the ceiling is one SM's ALU rate
@@ -563,6 +582,9 @@ def roofline(res, peaks, precision):
 
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12    # 1.26 TFLOP/s
+ISSUE_PEAK_WARP_INSTR = 152 * 4 * 2.07e9           # warp instructions / s
+# float-float stage stencil: smsp__inst_executed.sum / cells (ncu, 2D 128x256, 3D 64^3)
+RESIDUAL_FF_WARP_INSTR_PER_CELL = {2: 121.7, 3: 270.1}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 80.5 TFLOP/s
 
 
