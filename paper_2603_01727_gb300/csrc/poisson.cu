@@ -29,6 +29,7 @@
 // reproducible run to run.  The last block also writes the CG scalars and sets
 // the while-node conditional.
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -78,6 +79,7 @@ constexpr int kTailThreads = 512;
 constexpr long long kTailCellsF32 = 4096;   // largest level handled by the tail (FP32)
 constexpr long long kTailCellsF64 = 128;    // (FP64: one SM's FP64 rate is 1/64 of FP32)
 constexpr size_t kTailSmemMax = 200 * 1024;
+constexpr long long kMg3MinCells = 1LL << 20;   // smallest 3D level on the z-marching kernels
 
 template <int DIM>
 struct Tile;
@@ -1408,6 +1410,344 @@ __global__ void __launch_bounds__(FT) fdm(int nx, int ny, const float* __restric
 
 }  // namespace k2
 
+// ---------------------------------------------------------------------------
+// 3D kernels, z-marching ("2.5D"): a block owns a 32-column x 32-row box in
+// x-y (lane = column, each warp two rows) and marches through a chunk of
+// z-planes, keeping rings of 4 planes in shared memory.  The x-y halo is
+// recomputed by neighbouring blocks; the z-halo only at the ends of a chunk.
+// Per-cell arithmetic as in the tile kernels above (same smoother, residual,
+// restriction and prolongation formulas).
+// ---------------------------------------------------------------------------
+namespace k3 {
+
+using k2::Ax;
+using k2::axis;
+constexpr int NW = 16;            // warps per block
+constexpr int NT = 32 * NW;
+constexpr int SB = 32;            // box rows and columns
+constexpr int FD = 26, CD = 13;   // down: fine tile (halo 3), coarse tile
+constexpr int FU = 28;            // up: fine tile (halo 2)
+constexpr int FP = 30;            // pq: tile (halo 1)
+constexpr int KC = 8;             // down: coarse planes per block
+constexpr int ZU = 16;            // up, pq: fine planes per block
+constexpr int RING = 4;
+
+template <class T>
+using Pl = T[SB][SB];
+
+template <class T>
+__device__ __forceinline__ T off3(const LvT<T>& L, const Pl<T>* su, int sm, int s0, int sp, int r, int c) {
+    T off = L.w[0] * (su[s0][r][c - 1] + su[s0][r][c + 1]) + L.w[1] * (su[s0][r - 1][c] + su[s0][r + 1][c]);
+    off += L.w[2] * (su[sm][r][c] + su[sp][r][c]);
+    return off;
+}
+
+// One colour on plane z (ring slot z & 3) over rows [r0, r1] x columns [c0, c1].
+template <class T>
+__device__ __forceinline__ void color_plane(const LvT<T>& L, Pl<T>* su, const Pl<T>* sf, int ox, int oy, int z,
+                                            int zcls, int color, int r0, int r1, int c0, int c1) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int par = (ox + oy + z) & 1;
+    const int s0 = z & 3, sm = (z - 1) & 3, sp = (z + 1) & 3;
+    const int npairs = (r1 - r0 + 2) / 2;
+    for (int rp = warp; rp < npairs; rp += NW) {
+        const int r = r0 + 2 * rp + (lane >> 4);
+        const int c = 2 * (lane & 15) + ((color - par - r) & 1);
+        if (r > r1 || c < c0 || c > c1) continue;
+        const Ax ax = axis(ox + c, L.n[0], L.per[0]);
+        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        if (!(ax.valid && ay.valid)) continue;
+        su[s0][r][c] = (sf[s0][r][c] + off3<T>(L, su, sm, s0, sp, r, c)) * L.invd[ax.cls + 3 * ay.cls + 9 * zcls];
+    }
+}
+
+// down: red from zero, black, residual, restriction.  Block (bx, by, bz): the
+// coarse tile CD x CD of columns / rows and coarse planes [K0, K1).
+template <class T, class TF>
+__global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restrict__ f, T* __restrict__ upre,
+                                           T* __restrict__ fc) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int H = 3;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Pl<T>* sF = reinterpret_cast<Pl<T>*>(smraw);
+    Pl<T>* sU = sF + RING;
+    Pl<T>* sR = sU + RING;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ox = blockIdx.x * FD - H, oy = blockIdx.y * FD - H;
+    const int K0 = blockIdx.z * KC;
+    const int K1 = min(K0 + KC, C.n[2]);
+    const int zs = 2 * K0 - 3, ze = 2 * K1 + 2;
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const long long nxy = (long long)nx * ny;
+    const Ax ax = axis(ox + lane, nx, L.per[0]);
+    Ax ay[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) ay[k] = axis(oy + warp + NW * k, ny, L.per[1]);
+    const bool colo = ax.in && lane >= H && lane < H + FD;
+
+    for (int q = zs; q <= ze; ++q) {
+        // (a) f and the red cells of u (from a zero guess) on plane q
+        {
+            const Ax az = axis(q, nz, L.per[2]);
+            const int sl = q & 3;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int r = warp + NW * k;
+                T fv = (T)0, uv = (T)0;
+                if (ax.valid && ay[k].valid && az.valid) {
+                    fv = (T)f[ax.gw + (long long)nx * ay[k].gw + nxy * az.gw];
+                    if (((ox + lane + oy + r + q) & 1) == 0) uv = fv * L.invd[ax.cls + 3 * ay[k].cls + 9 * az.cls];
+                }
+                sF[sl][r][lane] = fv;
+                sU[sl][r][lane] = uv;
+            }
+        }
+        __syncthreads();
+        // (b) black on plane q-1, box minus one layer
+        {
+            const int z = q - 1;
+            if (z >= zs + 1 && z <= ze - 1) {
+                const Ax az = axis(z, nz, L.per[2]);
+                if (az.valid) color_plane<T>(L, sU, sF, ox, oy, z, az.cls, 1, 1, SB - 2, 1, SB - 2);
+            }
+        }
+        __syncthreads();
+        // (c) residual on plane q-2, box minus two layers; u of the owned cells
+        const int pr = q - 2;
+        if (pr >= zs + 2 && pr <= ze - 2) {
+            const Ax az = axis(pr, nz, L.per[2]);
+            const int s0 = pr & 3, sm = (pr - 1) & 3, sp = (pr + 1) & 3;
+            const bool zown = az.in && pr >= 2 * K0 && pr < 2 * K1;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int r = warp + NW * k;
+                T rv = (T)0;
+                if (r >= 2 && r <= SB - 3 && lane >= 2 && lane <= SB - 3 && ax.valid && ay[k].valid && az.valid) {
+                    const T u = sU[s0][r][lane];
+                    rv = sF[s0][r][lane] -
+                         (L.diag[ax.cls + 3 * ay[k].cls + 9 * az.cls] * u - off3<T>(L, sU, sm, s0, sp, r, lane));
+                    if (zown && colo && ay[k].in && r >= H && r < H + FD)
+                        upre[ax.gw + (long long)nx * ay[k].gw + nxy * az.gw] = u;
+                }
+                sR[s0][r][lane] = rv;
+            }
+        }
+        __syncthreads();
+        // (d) restriction of coarse plane K = (pr - 2) / 2 once its fine planes
+        // 2K-1 .. 2K+2 are in the residual ring
+        if (pr >= 2 * K0 + 2 && pr <= 2 * K1 && ((pr & 1) == 0)) {
+            const int K = (pr - 2) / 2;
+            for (int c = threadIdx.x; c < CD * CD; c += NT) {
+                const int cx = c % CD, cy = c / CD;
+                const int I = blockIdx.x * CD + cx, J = blockIdx.y * CD + cy;
+                if (I >= C.n[0] || J >= C.n[1]) continue;
+                T acc = (T)0;
+                for (int az = 0; az < 4; ++az) {
+                    const T wz = (T)rweight(az, K, C.n[2], C.per[2]);
+                    if (wz == (T)0) continue;
+                    const int sl = (2 * K - 1 + az) & 3;
+                    for (int ayy = 0; ayy < 4; ++ayy) {
+                        const T wy = (T)rweight(ayy, J, C.n[1], C.per[1]);
+                        if (wy == (T)0) continue;
+                        const int r = 2 * cy + H - 1 + ayy;
+                        T row = (T)0;
+#pragma unroll
+                        for (int axx = 0; axx < 4; ++axx)
+                            row += (T)rweight(axx, I, C.n[0], C.per[0]) * sR[sl][r][2 * cx + H - 1 + axx];
+                        acc += wz * wy * row;
+                    }
+                }
+                fc[I + C.n[0] * (J + (long long)C.n[1] * K)] = acc * (T)0.125;
+            }
+        }
+    }
+}
+
+// up: prolongation-add, black, red; on the fine level also the partial sums
+// of r.z and sum z (finished by the last block).  Block (bx, by, bz): the fine
+// tile FU x FU and fine planes [z0, z1).
+template <class T, class TF, bool FINE>
+__global__ void __launch_bounds__(NT)
+    up(LvT<T> L, LvT<T> C, const T* __restrict__ upre, const TF* __restrict__ f, const T* __restrict__ uc,
+       T* __restrict__ upost, double* part_rz, double* part_sz, double* scal, const int* ictl, unsigned int* cnt) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int H = 2;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Pl<T>* sF = reinterpret_cast<Pl<T>*>(smraw);
+    Pl<T>* sU = sF + RING;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ox = blockIdx.x * FU - H, oy = blockIdx.y * FU - H;
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int z0 = blockIdx.z * ZU, z1 = min(z0 + ZU, nz);
+    const long long nxy = (long long)nx * ny;
+    const Ax ax = axis(ox + lane, nx, L.per[0]);
+    Ax ay[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) ay[k] = axis(oy + warp + NW * k, ny, L.per[1]);
+    const bool colo = ax.in && lane >= H && lane < H + FU;
+    TF rz = (TF)0, sz = (TF)0;
+
+    for (int q = z0 - 2; q <= z1 + 1; ++q) {
+        // (a) f and u = u_pre + P u_coarse on plane q
+        {
+            const Ax az = axis(q, nz, L.per[2]);
+            const int sl = q & 3;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int r = warp + NW * k;
+                T fv = (T)0, uv = (T)0;
+                if (ax.valid && ay[k].valid && az.valid) {
+                    const long long g = ax.gw + (long long)nx * ay[k].gw + nxy * az.gw;
+                    fv = (T)f[g];
+                    const int gw[3] = {ax.gw, ay[k].gw, az.gw};
+                    uv = upre[g] + prolong_at<T, 3>(C, uc, gw);
+                }
+                sF[sl][r][lane] = fv;
+                sU[sl][r][lane] = uv;
+            }
+        }
+        __syncthreads();
+        // (b) black on plane q-1, box minus one layer
+        {
+            const int z = q - 1;
+            if (z >= z0 - 1 && z <= z1) {
+                const Ax az = axis(z, nz, L.per[2]);
+                if (az.valid) color_plane<T>(L, sU, sF, ox, oy, z, az.cls, 1, 1, SB - 2, 1, SB - 2);
+            }
+        }
+        __syncthreads();
+        // (c) red on plane q-2 over the tile
+        {
+            const int z = q - 2;
+            if (z >= z0 && z < z1) {
+                const Ax az = axis(z, nz, L.per[2]);
+                if (az.valid) color_plane<T>(L, sU, sF, ox, oy, z, az.cls, 0, H, SB - 1 - H, H, SB - 1 - H);
+            }
+        }
+        __syncthreads();
+        // (d) store the owned cells of plane q-2
+        {
+            const int z = q - 2;
+            if (z >= z0 && z < z1) {
+                const int sl = z & 3;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int r = warp + NW * k;
+                    if (!colo || !ay[k].in || r < H || r >= H + FU) continue;
+                    const long long g = ax.gw + (long long)nx * ay[k].gw + nxy * z;
+                    const T u = sU[sl][r][lane];
+                    upost[g] = u;
+                    if (FINE) {
+                        rz = fma(f[g], (TF)u, rz);
+                        sz += (TF)u;
+                    }
+                }
+            }
+        }
+    }
+    if (FINE) {
+        __shared__ double red[NT / 32];
+        __shared__ float redf[NT / 32];
+        const double brz = block_sum_any<NT>(rz, red, redf);
+        const double bsz = block_sum_any<NT>(sz, red, redf);
+        const int nb = gridDim.x * gridDim.y * gridDim.z;
+        if (threadIdx.x == 0) {
+            part_rz[block_linear()] = brz;
+            part_sz[block_linear()] = bsz;
+        }
+        if (arrive_last(cnt)) {
+            const double RZ = sum_parts_cg<NT>(part_rz, nb, red);
+            const double SZ = sum_parts_cg<NT>(part_sz, nb, red);
+            if (threadIdx.x == 0) {
+                const int it = ictl[PI_IT];
+                scal[PS_BETA] = (it == 0) ? 0.0 : RZ / scal[PS_RZ];
+                scal[PS_RZ] = RZ;
+                scal[PS_MEANZ] = SZ / (double)L.N;
+                *cnt = 0u;
+            }
+        }
+    }
+}
+
+// CG: p = (z - mean z) + beta p_old (p_new buffer by parity), q = A p, p.q;
+// the last block forms alpha = r.z / p.q.  Tile FP x FP, fine planes [z0, z1).
+// One barrier per plane: the plane written at step qq + 1 (slot qq - 3) is not
+// read at step qq.
+template <class T, class V>
+__global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p0, V* p1, V* __restrict__ q,
+                                         double* part, double* scal, const int* ictl, unsigned int* cnt) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int H = 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Pl<V>* sP = reinterpret_cast<Pl<V>*>(smraw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int it = ictl[PI_IT];
+    const V* pold = (it & 1) ? p0 : p1;
+    V* pnew = (it & 1) ? p1 : p0;
+    const V beta = (V)scal[PS_BETA], mz = (V)scal[PS_MEANZ];
+    const int ox = blockIdx.x * FP - H, oy = blockIdx.y * FP - H;
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int z0 = blockIdx.z * ZU, z1 = min(z0 + ZU, nz);
+    const long long nxy = (long long)nx * ny;
+    const Ax ax = axis(ox + lane, nx, L.per[0]);
+    Ax ay[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) ay[k] = axis(oy + warp + NW * k, ny, L.per[1]);
+    const bool colo = ax.in && lane >= H && lane < H + FP;
+    V acc = (V)0;
+    for (int qq = z0 - 1; qq <= z1; ++qq) {
+        {
+            const Ax az = axis(qq, nz, L.per[2]);
+            const int sl = qq & 3;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int r = warp + NW * k;
+                V pv = (V)0;
+                if (ax.valid && ay[k].valid && az.valid) {
+                    const long long g = ax.gw + (long long)nx * ay[k].gw + nxy * az.gw;
+                    pv = (V)z[g] - mz;
+                    if (it > 0) pv = fma(beta, pold[g], pv);
+                }
+                sP[sl][r][lane] = pv;
+            }
+        }
+        __syncthreads();
+        const int zc = qq - 1;
+        if (zc >= z0 && zc < z1) {
+            const Ax az = axis(zc, nz, L.per[2]);
+            const int s0 = zc & 3, sm = (zc - 1) & 3, sp = (zc + 1) & 3;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int r = warp + NW * k;
+                if (!colo || !ay[k].in || r < H || r >= H + FP) continue;
+                const long long g = ax.gw + (long long)nx * ay[k].gw + nxy * zc;
+                const V pv = sP[s0][r][lane];
+                const V qv = L.diag[ax.cls + 3 * ay[k].cls + 9 * az.cls] * pv - off3<V>(L, sP, sm, s0, sp, r, lane);
+                pnew[g] = pv;
+                q[g] = qv;
+                acc = fma(pv, qv, acc);
+            }
+        }
+    }
+    __shared__ double red[NT / 32];
+    __shared__ float redf[NT / 32];
+    const double bacc = block_sum_any<NT>(acc, red, redf);
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (threadIdx.x == 0) part[block_linear()] = bacc;
+    if (arrive_last(cnt)) {
+        const double PQ = sum_parts_cg<NT>(part, nb, red);
+        if (threadIdx.x == 0) {
+            scal[PS_ALPHA] = scal[PS_RZ] / PQ;
+            *cnt = 0u;
+        }
+    }
+}
+
+}  // namespace k3
+
 // ------------------------------ host helpers --------------------------------
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -1486,6 +1826,20 @@ long long tile_blocks(const int n_fine[3]) {
     constexpr int FX = 2 * Tile<DIM>::CX, FY = 2 * Tile<DIM>::CY, FZ = (DIM == 3) ? 2 * Tile<DIM>::CZ : 1;
     return (long long)((n_fine[0] + FX - 1) / FX) * ((n_fine[1] + FY - 1) / FY) *
            ((DIM == 3) ? (n_fine[2] + FZ - 1) / FZ : 1);
+}
+
+// z-marching 3D grids (k3): down over coarse tiles and chunks of coarse
+// planes, up and pq over fine tiles and chunks of fine planes
+dim3 k3_down_grid(const int nc[3]) {
+    return dim3((nc[0] + k3::CD - 1) / k3::CD, (nc[1] + k3::CD - 1) / k3::CD, (nc[2] + k3::KC - 1) / k3::KC);
+}
+dim3 k3_tile_grid(const int n[3], int tile) {
+    return dim3((n[0] + tile - 1) / tile, (n[1] + tile - 1) / tile, (n[2] + k3::ZU - 1) / k3::ZU);
+}
+long long k3_blocks(const int n[3]) {
+    const dim3 a = k3_tile_grid(n, k3::FU), b = k3_tile_grid(n, k3::FP);
+    const long long na = (long long)a.x * a.y * a.z, nb = (long long)b.x * b.y * b.z;
+    return na > nb ? na : nb;
 }
 
 template <int DIM>
@@ -1649,6 +2003,15 @@ void set_smem_attrs() {
     cudaFuncSetAttribute(k_cg_pq<T, 3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          Box<3, 1>::SN * (int)sizeof(double));
     cudaFuncSetAttribute(k2::tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+    const int pl3 = k3::SB * k3::SB * k3::RING;
+    cudaFuncSetAttribute(k3::down<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * pl3 * (int)sizeof(T));
+    cudaFuncSetAttribute(k3::down<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * pl3 * (int)sizeof(T));
+    cudaFuncSetAttribute(k3::up<T, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * pl3 * (int)sizeof(T));
+    cudaFuncSetAttribute(k3::up<T, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * pl3 * (int)sizeof(T));
+    cudaFuncSetAttribute(k3::up<T, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pl3 * (int)sizeof(T));
+    cudaFuncSetAttribute(k3::pq<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl3 * (int)sizeof(double));
     cudaFuncSetAttribute(k2::fdm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
 }
 
@@ -1664,7 +2027,7 @@ size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg
     const int top = pick_top(s, mg_fp32, tail_cells, &tail_smem);
     const size_t w = mg_fp32 ? 4 : 8;
     const long long N = s.N[0];
-    const long long nblk = (dim == 3) ? tile_blocks<3>(s.n[0]) : k2_blocks(s.n[0]);
+    const long long nblk = (dim == 3) ? std::max(tile_blocks<3>(s.n[0]), k3_blocks(s.n[0])) : k2_blocks(s.n[0]);
     const long long npart = nblk > kMaxPartials ? nblk : kMaxPartials;
     size_t b = 0;
     b += 4 * align256(sizeof(double) * N);                  // r p0 p1 q
@@ -1733,8 +2096,16 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
         const int v = std::atoi(e);
         if (v == 1 || v == 2) pl->sweeps = v;
     }
-    const long long nblk = (dim == 3) ? tile_blocks<3>(s.n[0]) : k2_blocks(s.n[0]);
+    const long long nblk = (dim == 3) ? std::max(tile_blocks<3>(s.n[0]), k3_blocks(s.n[0])) : k2_blocks(s.n[0]);
     pl->npart = (int)(nblk > kMaxPartials ? nblk : kMaxPartials);
+    {
+        // LOWMACH_MG3_TILES=1: the cube-tile 3D kernels instead of the z-marching ones
+        const char* e = std::getenv("LOWMACH_MG3_TILES");
+        pl->mg3_tiles = (e && e[0] == '1') ? 1 : 0;
+        // levels below this many cells keep the cube tiles (too few z-marching blocks)
+        const char* m = std::getenv("LOWMACH_MG3_MIN_CELLS");
+        pl->mg3_min_cells = (m && std::atoll(m) >= 0) ? std::atoll(m) : kMg3MinCells;
+    }
     pl->r = (double*)take(sizeof(double) * pl->N);
     pl->p[0] = (double*)take(sizeof(double) * pl->N);
     pl->p[1] = (double*)take(sizeof(double) * pl->N);
@@ -1937,6 +2308,15 @@ void enqueue_down(PoissonPlan* pl, int l, cudaStream_t s) {
             }
         }
         enqueue_down2<T, 1>(pl, l, L, C, fc, s);
+    } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells) {
+        const dim3 grid = k3_down_grid(pl->lev[l + 1].n);
+        const size_t smem = 3 * k3::RING * k3::SB * k3::SB * sizeof(T);
+        if (l == 0 && ir)
+            launch(k3::down<T, float>, grid, k3::NT, smem, s, L, C, pl->r32, (T*)pl->u0pre, fc);
+        else if (l == 0)
+            launch(k3::down<T, double>, grid, k3::NT, smem, s, L, C, pl->r, (T*)pl->u0pre, fc);
+        else
+            launch(k3::down<T, T>, grid, k3::NT, smem, s, L, C, (const T*)pl->lev[l].f, (T*)pl->lev[l].upre, fc);
     } else {
         const dim3 grid = tile_grid<DIM>(pl->lev[l].n);
         const size_t smem = 2 * Box<DIM, 3>::SN * sizeof(T);
@@ -1965,6 +2345,19 @@ void enqueue_up(PoissonPlan* pl, int l, cudaStream_t s) {
             }
         }
         enqueue_up2<T, 1>(pl, l, L, C, uc, s);
+    } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells) {
+        const dim3 grid = k3_tile_grid(pl->lev[l].n, k3::FU);
+        const size_t smem = 2 * k3::RING * k3::SB * k3::SB * sizeof(T);
+        if (l == 0 && ir)
+            launch(k3::up<T, float, true>, grid, k3::NT, smem, s, L, C, (const T*)pl->u0pre, pl->r32, uc, (T*)pl->z,
+                   pl->part0, pl->part1, pl->scal, pl->ictl, pl->cnt + CNT_UP0);
+        else if (l == 0)
+            launch(k3::up<T, double, true>, grid, k3::NT, smem, s, L, C, (const T*)pl->u0pre, pl->r, uc, (T*)pl->z,
+                   pl->part0, pl->part1, pl->scal, pl->ictl, pl->cnt + CNT_UP0);
+        else
+            launch(k3::up<T, T, false>, grid, k3::NT, smem, s, L, C, (const T*)pl->lev[l].upre,
+                   (const T*)pl->lev[l].f, uc, (T*)pl->lev[l].upost, (double*)nullptr, (double*)nullptr,
+                   (double*)nullptr, (const int*)nullptr, (unsigned int*)nullptr);
     } else {
         const dim3 grid = tile_grid<DIM>(pl->lev[l].n);
         const size_t smem = 2 * Box<DIM, 2>::SN * sizeof(T);
@@ -2025,6 +2418,16 @@ void enqueue_pq(PoissonPlan* pl, cudaStream_t s) {
             launch(k2::pq<T, double>, grid, k2::NT, 0, s, make_lv<double>(pl->lev[0], DIM), (const T*)pl->z, pl->p[0],
                                                       pl->p[1], pl->q, pl->part2, pl->scal, pl->ictl,
                                                       pl->cnt + CNT_PQ);
+    } else if (!pl->mg3_tiles && pl->lev[0].N >= pl->mg3_min_cells) {
+        const dim3 grid = k3_tile_grid(pl->lev[0].n, k3::FP);
+        const size_t pl3 = (size_t)k3::RING * k3::SB * k3::SB;
+        if (ir)
+            launch(k3::pq<T, float>, grid, k3::NT, pl3 * sizeof(float), s, make_lv<float>(pl->lev[0], DIM),
+                   (const T*)pl->z, pl->p32[0], pl->p32[1], pl->q32, pl->part2, pl->scal, pl->ictl,
+                   pl->cnt + CNT_PQ);
+        else
+            launch(k3::pq<T, double>, grid, k3::NT, pl3 * sizeof(double), s, make_lv<double>(pl->lev[0], DIM),
+                   (const T*)pl->z, pl->p[0], pl->p[1], pl->q, pl->part2, pl->scal, pl->ictl, pl->cnt + CNT_PQ);
     } else {
         const dim3 grid = tile_grid<DIM>(pl->lev[0].n);
         if (ir)

@@ -70,6 +70,8 @@ struct PoissonPlan {
     int top;              // first level of the single-block tail (levels top .. nlev-1)
     int mg_fp32;          // 1: multigrid in FP32, else FP64
     int sweeps;           // red-black sweeps per pre / post smoothing (2D kernels)
+    int mg3_tiles;        // 1: cube-tile 3D level kernels instead of the z-marching ones
+    long long mg3_min_cells;  // 3D levels with fewer cells use the cube tiles
     MgLevel lev[kMaxLevels];
     long long N;          // fine cells
     double* r;            // FP64 Krylov vectors on the fine level

@@ -260,3 +260,27 @@ def test_step_before_fields_is_a_state_error():
     with pytest.raises(SimError) as e:
         sim.step(1)
     assert e.value.status == SIM_ESTATE
+
+
+@pytest.mark.parametrize("n,periodic_x,precision", [(48, False, W.MIXED), (48, False, W.FP64), (32, True, W.FP64),
+                                                    (32, True, W.MIXED)])
+def test_z_marching_3d_multigrid_matches_cube_tiles(n, periodic_x, precision, monkeypatch):
+    """The z-marching 3D level kernels apply the same smoother, residual,
+    restriction and prolongation as the cube-tile kernels (LOWMACH_MG3_TILES=1):
+    same iteration counts and the same fields to solver tolerance."""
+    from paper_2603_01727_gb300.lowmach import SIM_Q_ITERS_PRED, SIM_Q_ITERS_CORR
+    prm, geo, f = W.sphere_burner(n)
+    prm["precision"] = precision
+    prm["poisson_rtol"] = 1e-12
+    if periodic_x:
+        prm["bc"] = [[W.PERIODIC, W.PERIODIC]] + prm["bc"][1:]
+    out = {}
+    monkeypatch.setenv("LOWMACH_MG3_MIN_CELLS", "0")     # every level on the z-marching kernels
+    for tiles in ("0", "1"):
+        monkeypatch.setenv("LOWMACH_MG3_TILES", tiles)
+        sim = gpu_run(prm, geo, f, 4)
+        out[tiles] = ({k: sim.get(k) for k in ("U", "W", "Z", "P")},
+                      (sim.query(SIM_Q_ITERS_PRED), sim.query(SIM_Q_ITERS_CORR)))
+    assert out["0"][1] == out["1"][1], (out["0"][1], out["1"][1])
+    for k in out["0"][0]:
+        assert rel(out["0"][0][k], out["1"][0][k]) <= 1e-9, k
