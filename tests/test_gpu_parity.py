@@ -147,6 +147,46 @@ def test_slot_burner_matches_oracle(nx, ny, steps):
     assert rel(sim.get("SM"), pb.ibm["Sm"]) < 1e-14
 
 
+# Method variants: differential diffusion with the paper's Lewis numbers
+# (Le_F = 0.97, Le_O = 1.11; regularised Le_eps and N_eps of Eq 3.35) and the
+# buoyancy term of Eq 3.8b, on the slot burner and the enclosed box.
+@pytest.mark.parametrize("case", ["lewis_slot", "lewis_box", "buoyant_slot", "buoyant_lewis_box"])
+def test_method_variants_match_oracle(case):
+    if case.endswith("slot"):
+        prm, geo, f = W.slot_burner(32, 64)
+        steps = 20
+    else:
+        prm, geo, f = W.periodic_blobs(48)
+        steps = 30
+    if "lewis" in case:
+        prm.update(Le_F=0.97, Le_O=1.11)
+    if "buoyant" in case:
+        prm["inv_Fr2"] = 1.0
+    prm["poisson_rtol"] = 1e-13
+    pb, st = oracle_run(prm, geo, f, steps)
+    sim = gpu_run(prm, geo, f, steps)
+    worst = compare(sim, oracle_fields(pb, st), 1e-9)
+    print(case, {k: f"{v:.1e}" for k, v in worst.items()})
+
+
+@pytest.mark.parametrize("case", ["lewis_slot", "buoyant_lewis_box"])
+def test_method_variants_mixed_precision_error(case):
+    if case.endswith("slot"):
+        prm, geo, f = W.slot_burner(32, 64)
+        steps = 20
+        prm.update(Le_F=0.97, Le_O=1.11)
+    else:
+        prm, geo, f = W.periodic_blobs(48)
+        steps = 30
+        prm.update(Le_F=0.97, Le_O=1.11, inv_Fr2=1.0)
+    prm["poisson_rtol"] = 1e-12
+    prm["precision"] = W.MIXED
+    pb, st = oracle_run(prm, geo, f, steps)
+    sim = gpu_run(prm, geo, f, steps)
+    worst = compare(sim, oracle_fields(pb, st), MIXED_TOL)
+    print(case, {k: f"{v:.1e}" for k, v in worst.items()})
+
+
 def test_sphere_burner_3d_matches_oracle():
     prm, geo, f = W.sphere_burner(24)
     prm["poisson_rtol"] = 1e-13
