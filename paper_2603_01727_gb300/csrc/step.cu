@@ -327,8 +327,19 @@ __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, con
 
 // C: arithmetic of the stencil terms (double, or float-float in the mixed
 // path); the residuals are stored and combined in FP64.
+// Float-float stencil: three blocks per SM (80 registers); latency-bound at
+// the two blocks its uncapped register count allows.
+template <class C>
+struct ResidMinBlocks {
+    static constexpr int v = 1;
+};
+template <>
+struct ResidMinBlocks<FF> {
+    static constexpr int v = 3;
+};
+
 template <int DIM, class C>
-__global__ void __launch_bounds__(NT) k_residual(Geom g, Phys ph, ResidArgs a) {
+__global__ void __launch_bounds__(NT, ResidMinBlocks<C>::v) k_residual(Geom g, Phys ph, ResidArgs a) {
     const long long t = (long long)blockIdx.x * NT + threadIdx.x;
     if (t >= g.ncell) return;
     const long long c = pad_index(g, t);
