@@ -150,6 +150,18 @@ __device__ __forceinline__ FF operator/(FF a, FF b) {
     const float q2 = __fdiv_rn(r.hi, b.hi);
     return ff_fast_two_sum(q1, q2);
 }
+// Exact float -> double by integer operations on the bits (normal floats;
+// zero and subnormal floats give zero, infinities and NaN give NaN), so that
+// no conversion instruction is issued.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    if (e == 0xffu) return __longlong_as_double(0x7ff8000000000000LL);
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
 __device__ __forceinline__ FF& operator+=(FF& a, FF b) { return a = a + b; }
 __device__ __forceinline__ FF& operator-=(FF& a, FF b) { return a = a - b; }
 __device__ inline FF tanh_c(FF x) { return FF(tanh((double)x)); }

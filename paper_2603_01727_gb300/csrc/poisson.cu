@@ -592,9 +592,13 @@ __global__ void __launch_bounds__(NTV)
     }
 }
 
-// Reliable update (FP64), only when flagged: x += e, r64 -= A e (e exact in
-// FP64), r32 = r64, ||r64||^2; the last block applies the FP64 stopping test.
-// The FP32 search direction and r.z are kept (no restart).
+// Reliable update, only when flagged: x += e, r64 -= A e, r32 = r64,
+// ||r64||^2; the last block applies the FP64 stopping test.  A e and the
+// residual difference are formed in float-float arithmetic from the FP32
+// correction e (about 2^-46 relative, far below what the stopping test needs)
+// with float <-> double conversions by bit operations, so that only three
+// FP64 operations per cell (two additions, the squared norm) use the
+// 1/64-rate FP64 pipe.  The FP32 search direction and r.z are kept.
 template <int DIM>
 __global__ void __launch_bounds__(NTV)
     k_ir_refine(LvT<double> L, double* __restrict__ x, double* __restrict__ r64, const float* __restrict__ e,
@@ -603,29 +607,36 @@ __global__ void __launch_bounds__(NTV)
     pdl_wait();
     pdl_trigger();
     if (!ictl[PI_REFINE]) return;
+    FF wd[3];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) wd[d] = FF(L.w[d]);
     double rr = 0.0;
     for (int t = blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
         int c[3];
         coords(L.n, t, c);
-        double off = 0.0;
+        FF off;
         int stride = 1, p3 = 1, cl = 0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             const int n = L.n[d];
-            if (c[d] > 0) off += L.w[d] * (double)e[t - stride];
-            else if (L.per[d]) off += L.w[d] * (double)e[t + (n - 1) * stride];
-            if (c[d] < n - 1) off += L.w[d] * (double)e[t + stride];
-            else if (L.per[d]) off += L.w[d] * (double)e[t - (n - 1) * stride];
+            float a = 0.0f, b = 0.0f;
+            if (c[d] > 0) a = e[t - stride];
+            else if (L.per[d]) a = e[t + (n - 1) * stride];
+            if (c[d] < n - 1) b = e[t + stride];
+            else if (L.per[d]) b = e[t - (n - 1) * stride];
+            off += wd[d] * (FF(a, 0.0f) + FF(b, 0.0f));
             cl += (L.per[d] ? 2 : (int)(c[d] > 0) + (int)(c[d] < n - 1)) * p3;
             stride *= n;
             p3 *= 3;
         }
-        const double ev = (double)e[t];
-        x[t] += ev;
-        const double rv = r64[t] - (L.diag[cl] * ev - off);
-        r64[t] = rv;
-        r32[t] = (float)rv;
-        rr = fma(rv, rv, rr);
+        const float ev = e[t];
+        const FF Ae = FF(L.diag[cl]) * FF(ev, 0.0f) - off;
+        const FF rv = FF(r64[t]) - Ae;
+        x[t] = x[t] + f2d_bits(ev);
+        const double rvd = f2d_bits(rv.hi) + f2d_bits(rv.lo);
+        r64[t] = rvd;
+        r32[t] = rv.hi;
+        rr = fma(rvd, rvd, rr);
     }
     __shared__ double red[NTV / 32];
     rr = block_sum<NTV>(rr, red);
