@@ -290,6 +290,25 @@ sim_status sim_poisson_solve(int dim, const int n[3], const double h[3], const i
                              void *d_workspace, size_t workspace_bytes, void *cuda_stream,
                              int *iters, double *rel_resid);
 
+/* Batched stand-alone pressure solve: nb independent systems on the same 2D
+ * grid (periodic / Neumann sides as above), advanced together: one launch per
+ * multigrid level and CG update serves every system, with per-system
+ * scalars, convergence test and iteration count; a system that has converged
+ * stops updating while the others continue.  d_b and d_P hold nb consecutive
+ * n0*n1 arrays (system k at offset k*n0*n1).  precision: SIM_FP64 (FP64
+ * multigrid) or SIM_MIXED (FP32 multigrid and inner CG with FP64 reliable
+ * updates, as in sim_params_t).  Each system gets the same iterates it would
+ * get solved alone.  iters (nb ints) and rel_resid (nb doubles), host
+ * pointers that may be NULL, receive the per-system results; the call
+ * synchronises the stream.  Returns SIM_EINVAL for nb < 1, a 3D grid or a grid
+ * that does not coarsen, SIM_ENOCONV if some system reached max_iter first. */
+sim_status sim_poisson_batch_workspace_size(const int n[2], const int periodic[2], int nb, int precision,
+                                            size_t *bytes);
+sim_status sim_poisson_solve_batch(const int n[2], const double h[2], const int periodic[2], int nb,
+                                   int precision, const double *d_b, double *d_P, double rtol, int max_iter,
+                                   void *d_workspace, size_t workspace_bytes, void *cuda_stream, int *iters,
+                                   double *rel_resid);
+
 /* ---------------------------------------------------------------------------
  * Pressure solve without any allocation (no counterpart in the paper; an
  * interface convenience).  Same operator, arguments, results and status codes

@@ -197,17 +197,29 @@ __device__ __forceinline__ T prolong_at(const LvT<T>& C, const T* __restrict__ u
 // Last block of a grid to arrive.  The block's partial sums are written by
 // thread 0 before the call, so only thread 0 fences them (release) before
 // counting in; the last block fences again (acquire) before reading the others'.
-__device__ __forceinline__ bool arrive_last(unsigned int* cnt) {
+// arrive_last_n: the same among nblocks blocks (the blocks of one system of a
+// batch, which counts on that system's counter).
+__device__ __forceinline__ bool arrive_last_n(unsigned int* cnt, unsigned int nblocks) {
     __shared__ int am_last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
-        am_last = (atomicAdd(cnt, 1u) == nb - 1u);
+        am_last = (atomicAdd(cnt, 1u) == nblocks - 1u);
         if (am_last) __threadfence();
     }
     __syncthreads();
     return am_last != 0;
+}
+__device__ __forceinline__ bool arrive_last(unsigned int* cnt) {
+    return arrive_last_n(cnt, gridDim.x * gridDim.y * gridDim.z);
+}
+
+// Batches: the system of a block (grid dimension y of the vector kernels, z
+// of the 2D level kernels) and the offsets of its control words.
+__device__ __forceinline__ void batch_ctl(int fb, double** scal, int** ictl, unsigned int** cnt) {
+    *scal += (long long)fb * PS_NSCAL;
+    *ictl += (long long)fb * PI_NINT;
+    *cnt += (long long)fb * kNumCounters;
 }
 
 template <int NT>
@@ -511,6 +523,15 @@ __global__ void __launch_bounds__(NTV)
                 unsigned int* cnt, double rtol, int max_iter, cudaGraphConditionalHandle h, int use_graph) {
     pdl_wait();
     pdl_trigger();
+    const int fb = blockIdx.y;
+    batch_ctl(fb, &scal, &ictl, &cnt);
+    if (gridDim.y > 1 && ictl[PI_DONE]) return;   // this system of the batch has converged
+    x += fb * N;
+    r += fb * N;
+    p0 += fb * N;
+    p1 += fb * N;
+    q += fb * N;
+    part += (long long)fb * gridDim.x;
     const int it = ictl[PI_IT];
     const double* __restrict__ p = (it & 1) ? p1 : p0;
     const double alpha = scal[PS_ALPHA];
@@ -524,7 +545,7 @@ __global__ void __launch_bounds__(NTV)
     __shared__ double red[NTV / 32];
     rr = block_sum<NTV>(rr, red);
     if (threadIdx.x == 0) part[blockIdx.x] = rr;
-    if (arrive_last(cnt)) {
+    if (arrive_last_n(cnt, gridDim.x)) {
         const double RR = sum_parts_cg<NTV>(part, gridDim.x, red);
         if (threadIdx.x == 0) {
             const int itn = it + 1;
@@ -557,6 +578,15 @@ __global__ void __launch_bounds__(NTV)
                 double inner_tol, int inner_max, int max_iter, cudaGraphConditionalHandle h, int use_graph) {
     pdl_wait();
     pdl_trigger();
+    const int fb = blockIdx.y;
+    batch_ctl(fb, &scal, &ictl, &cnt);
+    if (gridDim.y > 1 && ictl[PI_DONE]) return;   // this system of the batch has converged
+    e += fb * N;
+    r += fb * N;
+    p0 += fb * N;
+    p1 += fb * N;
+    q += fb * N;
+    part += (long long)fb * gridDim.x;
     const int it = ictl[PI_IT];
     const int ereset = ictl[PI_ERESET];
     const float* __restrict__ p = (it & 1) ? p1 : p0;
@@ -573,7 +603,7 @@ __global__ void __launch_bounds__(NTV)
     __shared__ double red[NTV / 32];
     const float brr = block_sum_f<NTV>(rr, redf);
     if (threadIdx.x == 0) part[blockIdx.x] = (double)brr;
-    if (arrive_last(cnt)) {
+    if (arrive_last_n(cnt, gridDim.x)) {
         const double RR = sum_parts_cg<NTV>(part, gridDim.x, red);
         if (threadIdx.x == 0) {
             const int itn = it + 1, tot = ictl[PI_TOTAL] + 1, since = ictl[PI_SINCE] + 1;
@@ -606,7 +636,15 @@ __global__ void __launch_bounds__(NTV)
                 int max_iter, cudaGraphConditionalHandle h, int use_graph) {
     pdl_wait();
     pdl_trigger();
+    const int fb = blockIdx.y;
+    batch_ctl(fb, &scal, &ictl, &cnt);
     if (!ictl[PI_REFINE]) return;
+    if (gridDim.y > 1 && ictl[PI_DONE]) return;   // this system of the batch has converged
+    x += (long long)fb * L.N;
+    r64 += (long long)fb * L.N;
+    e += (long long)fb * L.N;
+    r32 += (long long)fb * L.N;
+    part += (long long)fb * gridDim.x;
     FF wd[3];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) wd[d] = FF(L.w[d]);
@@ -641,7 +679,7 @@ __global__ void __launch_bounds__(NTV)
     __shared__ double red[NTV / 32];
     rr = block_sum<NTV>(rr, red);
     if (threadIdx.x == 0) part[blockIdx.x] = rr;
-    if (arrive_last(cnt)) {
+    if (arrive_last_n(cnt, gridDim.x)) {
         const double RR = sum_parts_cg<NTV>(part, gridDim.x, red);
         if (threadIdx.x == 0) {
             const double ff = scal[PS_FF];
@@ -690,12 +728,17 @@ __global__ void __launch_bounds__(NTV) k_mean(const double* __restrict__ b, long
                                               double* scal, int slot, unsigned int* cnt) {
     pdl_wait();
     pdl_trigger();
+    const int fb = blockIdx.y;
+    scal += (long long)fb * PS_NSCAL;
+    cnt += (long long)fb * kNumCounters;
+    b += fb * N;
+    part += (long long)fb * gridDim.x;
     double v = 0.0;
     for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV) v += b[t];
     __shared__ double red[NTV / 32];
     v = block_sum<NTV>(v, red);
     if (threadIdx.x == 0) part[blockIdx.x] = v;
-    if (arrive_last(cnt)) {
+    if (arrive_last_n(cnt, gridDim.x)) {
         const double s = sum_parts_cg<NTV>(part, gridDim.x, red);
         if (threadIdx.x == 0) {
             scal[slot] = s / (double)N;
@@ -713,6 +756,14 @@ __global__ void __launch_bounds__(NTV)
                double rtol, cudaGraphConditionalHandle h, int use_graph) {
     pdl_wait();
     pdl_trigger();
+    const int fb = blockIdx.y;
+    batch_ctl(fb, &scal, &ictl, &cnt);
+    b += (long long)fb * L.N;
+    x += (long long)fb * L.N;
+    r += (long long)fb * L.N;
+    if (r32) r32 += (long long)fb * L.N;
+    pff += (long long)fb * gridDim.x;
+    prr += (long long)fb * gridDim.x;
     const double mean_b = scal[PS_MEANB];
     double ff = 0.0, rr = 0.0;
     for (int t = blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
@@ -734,7 +785,7 @@ __global__ void __launch_bounds__(NTV)
         pff[blockIdx.x] = ff;
         prr[blockIdx.x] = rr;
     }
-    if (arrive_last(cnt)) {
+    if (arrive_last_n(cnt, gridDim.x)) {
         const double FF = sum_parts_cg<NTV>(pff, gridDim.x, red);
         const double RR = sum_parts_cg<NTV>(prr, gridDim.x, red);
         if (threadIdx.x == 0) {
@@ -765,11 +816,45 @@ __global__ void __launch_bounds__(NTV)
     }
 }
 
+// Batches: the solve continues while any system is active (sets the
+// while-node condition, and bdone for a host-driven loop).
+__global__ void __launch_bounds__(NTV) k_batch_cond(const int* ictl, int nb, int* bdone,
+                                                    cudaGraphConditionalHandle h, int use_graph) {
+    pdl_wait();
+    pdl_trigger();
+    int active = 0;
+    for (int k = threadIdx.x; k < nb; k += NTV) active |= !ictl[(long long)k * PI_NINT + PI_DONE];
+    active = __syncthreads_or(active);
+    if (threadIdx.x == 0) {
+        *bdone = !active;
+        if (use_graph) cudaGraphSetConditional(h, active ? 1u : 0u);
+    }
+}
+
+// Batches: each system's iteration count and relative residual to rep[k],
+// non-convergence into *status[k].
+__global__ void __launch_bounds__(NTV) k_batch_report(const double* scal, const int* ictl, int nb,
+                                                      double* const* rep, int* const* status, int bit) {
+    pdl_wait();
+    pdl_trigger();
+    for (int k = threadIdx.x; k < nb; k += NTV) {
+        if (rep && rep[k]) {
+            rep[k][0] = scal[(long long)k * PS_NSCAL + PS_ITERS];
+            rep[k][1] = scal[(long long)k * PS_NSCAL + PS_RELRES];
+        }
+        if (status && status[k] && ictl[(long long)k * PI_NINT + PI_NOCONV]) atomicOr(status[k], bit);
+    }
+}
+
 // Zero-mean x; report iterations / residual / status.
 __global__ void __launch_bounds__(NTV) k_sub_mean(double* __restrict__ x, long long N, const double* scal,
                                                   const int* ictl, double* rep, int* status, int bit) {
     pdl_wait();
     pdl_trigger();
+    const int fb = blockIdx.y;
+    scal += (long long)fb * PS_NSCAL;
+    ictl += (long long)fb * PI_NINT;
+    x += fb * N;
     const double mean = scal[PS_MEANX];
     const int zero = ictl[PI_ZERO];
     for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV)
@@ -1000,6 +1085,12 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
                                            T* __restrict__ fc) {
     pdl_wait();
     pdl_trigger();
+    {   // system of a batch
+        const long long fb = blockIdx.z;
+        f += fb * L.N;
+        upre += fb * L.N;
+        fc += fb * C.N;
+    }
     constexpr int H = 2 * NS + 1, FD = fd_of(NS), CD = cd_of(NS);
     __shared__ T sf[SY][32];
     __shared__ T su[SY][32];
@@ -1069,6 +1160,20 @@ __global__ void __launch_bounds__(NT)
        T* __restrict__ upost, double* part_rz, double* part_sz, double* scal, const int* ictl, unsigned int* cnt) {
     pdl_wait();
     pdl_trigger();
+    {   // system of a batch
+        const long long fb = blockIdx.z;
+        upre += fb * L.N;
+        f += fb * L.N;
+        uc += fb * C.N;
+        upost += fb * L.N;
+        if (FINE) {
+            part_rz += fb * gridDim.x * gridDim.y;
+            part_sz += fb * gridDim.x * gridDim.y;
+            scal += fb * PS_NSCAL;
+            ictl += fb * PI_NINT;
+            cnt += fb * kNumCounters;
+        }
+    }
     constexpr int H = 2 * NS, FU = fu_of(NS);
     __shared__ T sf[SY][32];
     __shared__ T su[SY][32];
@@ -1133,7 +1238,7 @@ __global__ void __launch_bounds__(NT)
             part_rz[bid] = brz;
             part_sz[bid] = bsz;
         }
-        if (arrive_last(cnt)) {
+        if (arrive_last_n(cnt, gridDim.x * gridDim.y)) {
             const double RZ = sum_parts_cg<NT>(part_rz, nb, red);
             const double SZ = sum_parts_cg<NT>(part_sz, nb, red);
             if (threadIdx.x == 0) {
@@ -1152,6 +1257,17 @@ __global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p
                                          double* part, double* scal, const int* ictl, unsigned int* cnt) {
     pdl_wait();
     pdl_trigger();
+    {   // system of a batch
+        const long long fb = blockIdx.z;
+        z += fb * L.N;
+        p0 += fb * L.N;
+        p1 += fb * L.N;
+        q += fb * L.N;
+        part += fb * gridDim.x * gridDim.y;
+        scal += fb * PS_NSCAL;
+        ictl += fb * PI_NINT;
+        cnt += fb * kNumCounters;
+    }
     constexpr int H = 1;
     __shared__ V sp[SY][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1196,7 +1312,7 @@ __global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p
     const double bacc = block_sum_any<NT>(acc, red, redf);
     const int nb = gridDim.x * gridDim.y;
     if (threadIdx.x == 0) part[blockIdx.x + gridDim.x * blockIdx.y] = bacc;
-    if (arrive_last(cnt)) {
+    if (arrive_last_n(cnt, gridDim.x * gridDim.y)) {
         const double PQ = sum_parts_cg<NT>(part, nb, red);
         if (threadIdx.x == 0) {
             scal[PS_ALPHA] = scal[PS_RZ] / PQ;
@@ -1243,6 +1359,11 @@ __global__ void __launch_bounds__(TT) tail(const LvT<T>* __restrict__ levs, Tail
                                            T* __restrict__ u_top, const T* __restrict__ Minv) {
     pdl_wait();
     pdl_trigger();
+    {   // system of a batch (one block each)
+        const long long fb = blockIdx.x;
+        f_top += fb * levs[a.top].N;
+        u_top += fb * levs[a.top].N;
+    }
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ LvT<T> lv[kMaxLevels];
     T* sm = reinterpret_cast<T*>(smraw);
@@ -1395,6 +1516,8 @@ __global__ void __launch_bounds__(FT) fdm(int nx, int ny, const float* __restric
                                           float* __restrict__ u) {
     pdl_wait();
     pdl_trigger();
+    f += (long long)blockIdx.x * nx * ny;   // system of a batch (one block each)
+    u += (long long)blockIdx.x * nx * ny;
     extern __shared__ __align__(16) unsigned char smraw[];
     float* Sx = reinterpret_cast<float*>(smraw);
     float* SxT = Sx + nx * nx;
@@ -2031,9 +2154,19 @@ void set_smem_attrs() {
 // ------------------------------ plan ----------------------------------------
 size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg_fp32, int tail_cells,
                           int* nlev_out, long long* Nc_out, const char** err) {
+    return poisson_plan_bytes_batch(dim, n, periodic, mg_fp32, tail_cells, 1, nlev_out, Nc_out, err);
+}
+
+size_t poisson_plan_bytes_batch(int dim, const int n[3], const int periodic[3], int mg_fp32, int tail_cells, int nb,
+                                int* nlev_out, long long* Nc_out, const char** err) {
     (void)periodic;
     Shapes s;
     if (!make_shapes(dim, n, &s, err)) return 0;
+    if (nb < 1 || (nb > 1 && (dim != 2 || s.nlev == 1))) {
+        *err = "batched solves need a 2D grid with at least two multigrid levels";
+        return 0;
+    }
+    const size_t B = (size_t)nb;
     size_t tail_smem = 0;
     const int top = pick_top(s, mg_fp32, tail_cells, &tail_smem);
     const size_t w = mg_fp32 ? 4 : 8;
@@ -2041,15 +2174,15 @@ size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg
     const long long nblk = (dim == 3) ? std::max(tile_blocks<3>(s.n[0]), k3_blocks(s.n[0])) : k2_blocks(s.n[0]);
     const long long npart = nblk > kMaxPartials ? nblk : kMaxPartials;
     size_t b = 0;
-    b += 4 * align256(sizeof(double) * N);                  // r p0 p1 q
-    b += align256(sizeof(double) * N) + align256(w * N);    // z (double-sized: one-level grids), u0pre
-    if (mg_fp32 && s.nlev > 1) b += 5 * align256(sizeof(float) * N);   // r32 e32 p32[2] q32
-    b += 3 * align256(sizeof(double) * npart);              // partials
-    b += align256(sizeof(double) * PS_NSCAL) + align256(sizeof(int) * PI_NINT) +
-         align256(sizeof(unsigned int) * kNumCounters);
+    b += 4 * align256(B * sizeof(double) * N);                      // r p0 p1 q
+    b += align256(B * sizeof(double) * N) + align256(B * w * N);    // z (double-sized: one-level grids), u0pre
+    if (mg_fp32 && s.nlev > 1) b += 5 * align256(B * sizeof(float) * N);   // r32 e32 p32[2] q32
+    b += 3 * align256(B * sizeof(double) * npart);                  // partials
+    b += align256(B * sizeof(double) * PS_NSCAL) + align256(B * sizeof(int) * PI_NINT) +
+         align256(B * sizeof(unsigned int) * kNumCounters) + align256(sizeof(int));
     for (int l = 1; l < s.nlev; ++l) {
-        if (l < top) b += 3 * align256(w * s.N[l]);          // upre upost f
-        else if (l == top) b += 2 * align256(w * s.N[l]);    // f (in), upost (out)
+        if (l < top) b += 3 * align256(B * w * s.N[l]);          // upre upost f
+        else if (l == top) b += 2 * align256(B * w * s.N[l]);    // f (in), upost (out)
     }
     b += align256((mg_fp32 ? sizeof(LvT<float>) : sizeof(LvT<double>)) * s.nlev);
     const long long Nc = s.N[s.nlev - 1];
@@ -2066,9 +2199,17 @@ size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg
 bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[3], const int periodic[3],
                        int mg_fp32, int sweeps, int tail_cells, double rtol, int max_iter, void* ws,
                        size_t ws_bytes, std::vector<double>* minv_host, const char** err) {
+    return poisson_plan_init_batch(pl, dim, n, h, periodic, mg_fp32, sweeps, tail_cells, rtol, max_iter, 1, ws,
+                                   ws_bytes, minv_host, err);
+}
+
+bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const double h[3], const int periodic[3],
+                             int mg_fp32, int sweeps, int tail_cells, double rtol, int max_iter, int nb, void* ws,
+                             size_t ws_bytes, std::vector<double>* minv_host, const char** err) {
     Shapes s;
     if (!make_shapes(dim, n, &s, err)) return false;
-    const size_t need = poisson_plan_bytes(dim, n, periodic, mg_fp32, tail_cells, nullptr, nullptr, err);
+    const size_t need = poisson_plan_bytes_batch(dim, n, periodic, mg_fp32, tail_cells, nb, nullptr, nullptr, err);
+    const size_t B = (size_t)nb;
     if (need == 0) return false;
     if (ws_bytes < need) {
         *err = "poisson workspace too small";
@@ -2117,22 +2258,23 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
         const char* m = std::getenv("LOWMACH_MG3_MIN_CELLS");
         pl->mg3_min_cells = (m && std::atoll(m) >= 0) ? std::atoll(m) : kMg3MinCells;
     }
-    pl->r = (double*)take(sizeof(double) * pl->N);
-    pl->p[0] = (double*)take(sizeof(double) * pl->N);
-    pl->p[1] = (double*)take(sizeof(double) * pl->N);
-    pl->q = (double*)take(sizeof(double) * pl->N);
-    pl->z = take(sizeof(double) * pl->N);
-    pl->u0pre = take(w * pl->N);
+    pl->nb = nb;
+    pl->r = (double*)take(B * sizeof(double) * pl->N);
+    pl->p[0] = (double*)take(B * sizeof(double) * pl->N);
+    pl->p[1] = (double*)take(B * sizeof(double) * pl->N);
+    pl->q = (double*)take(B * sizeof(double) * pl->N);
+    pl->z = take(B * sizeof(double) * pl->N);
+    pl->u0pre = take(B * w * pl->N);
     // Refinement mode (FP32 CG with reliable updates) is the mixed default; the
     // tuning override LOWMACH_REFINE=0 keeps the FP64 CG around the FP32 multigrid.
     const char* rf = std::getenv("LOWMACH_REFINE");
     const bool refine_mode = mg_fp32 && s.nlev > 1 && !(rf && rf[0] == '0');
     if (refine_mode) {   // refinement mode (a one-level grid is solved exactly in FP64)
-        pl->r32 = (float*)take(sizeof(float) * pl->N);
-        pl->e32 = (float*)take(sizeof(float) * pl->N);
-        pl->p32[0] = (float*)take(sizeof(float) * pl->N);
-        pl->p32[1] = (float*)take(sizeof(float) * pl->N);
-        pl->q32 = (float*)take(sizeof(float) * pl->N);
+        pl->r32 = (float*)take(B * sizeof(float) * pl->N);
+        pl->e32 = (float*)take(B * sizeof(float) * pl->N);
+        pl->p32[0] = (float*)take(B * sizeof(float) * pl->N);
+        pl->p32[1] = (float*)take(B * sizeof(float) * pl->N);
+        pl->q32 = (float*)take(B * sizeof(float) * pl->N);
         pl->inner_tol = 0.1;     // reliable update whenever ||r|| fell 10x since the last one
         pl->inner_max = 50;
         // tuning override: LOWMACH_INNER_TOL = residual drop between reliable updates
@@ -2141,12 +2283,13 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
             if (v > 0.0 && v < 1.0) pl->inner_tol = v;
         }
     }
-    pl->part0 = (double*)take(sizeof(double) * pl->npart);
-    pl->part1 = (double*)take(sizeof(double) * pl->npart);
-    pl->part2 = (double*)take(sizeof(double) * pl->npart);
-    pl->scal = (double*)take(sizeof(double) * PS_NSCAL);
-    pl->ictl = (int*)take(sizeof(int) * PI_NINT);
-    pl->cnt = (unsigned int*)take(sizeof(unsigned int) * kNumCounters);
+    pl->part0 = (double*)take(B * sizeof(double) * pl->npart);
+    pl->part1 = (double*)take(B * sizeof(double) * pl->npart);
+    pl->part2 = (double*)take(B * sizeof(double) * pl->npart);
+    pl->scal = (double*)take(B * sizeof(double) * PS_NSCAL);
+    pl->ictl = (int*)take(B * sizeof(int) * PI_NINT);
+    pl->cnt = (unsigned int*)take(B * sizeof(unsigned int) * kNumCounters);
+    pl->bdone = (int*)take(sizeof(int));
     for (int l = 0; l < s.nlev; ++l) {
         MgLevel& L = pl->lev[l];
         for (int d = 0; d < 3; ++d) {
@@ -2158,12 +2301,12 @@ bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[
         }
         L.N = s.N[l];
         if (l >= 1 && l < pl->top) {
-            L.upre = take(w * L.N);
-            L.upost = take(w * L.N);
-            L.f = take(w * L.N);
+            L.upre = take(B * w * L.N);
+            L.upost = take(B * w * L.N);
+            L.f = take(B * w * L.N);
         } else if (l >= 1 && l == pl->top) {
-            L.f = take(w * L.N);
-            L.upost = take(w * L.N);
+            L.f = take(B * w * L.N);
+            L.upost = take(B * w * L.N);
         }
     }
     const size_t lvsz = mg_fp32 ? sizeof(LvT<float>) : sizeof(LvT<double>);
@@ -2250,8 +2393,10 @@ bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& M, cudaSt
         e = cudaMemcpyAsync(pl->fdm_tab, hp, sizeof(float) * (2 * nx * nx + 2 * ny * ny + nx * ny),
                             cudaMemcpyHostToDevice, s);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(pl->cnt, 0, sizeof(unsigned int) * kNumCounters, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(pl->ictl, 0, sizeof(int) * PI_NINT, s);
+    const size_t nb = (size_t)(pl->nb > 0 ? pl->nb : 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->cnt, 0, nb * sizeof(unsigned int) * kNumCounters, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->ictl, 0, nb * sizeof(int) * PI_NINT, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->bdone, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         *err = cudaGetErrorString(e);
@@ -2281,7 +2426,7 @@ LvT<T> lv_host(PoissonPlan* pl, int l) {
 template <class T, int NS>
 void enqueue_down2(PoissonPlan* pl, int l, const LvT<T>& L, const LvT<T>& C, T* fc, cudaStream_t s) {
     constexpr int CD = k2::cd_of(NS);
-    const dim3 grid((C.n[0] + CD - 1) / CD, (C.n[1] + CD - 1) / CD);
+    const dim3 grid((C.n[0] + CD - 1) / CD, (C.n[1] + CD - 1) / CD, pl->nb);
     if (l == 0 && pl->r32) launch(k2::down<T, float, NS>, grid, k2::NT, 0, s, L, C, pl->r32, (T*)pl->u0pre, fc);
     else if (l == 0) launch(k2::down<T, double, NS>, grid, k2::NT, 0, s, L, C, pl->r, (T*)pl->u0pre, fc);
     else launch(k2::down<T, T, NS>, grid, k2::NT, 0, s, L, C, (const T*)pl->lev[l].f, (T*)pl->lev[l].upre, fc);
@@ -2290,7 +2435,7 @@ void enqueue_down2(PoissonPlan* pl, int l, const LvT<T>& L, const LvT<T>& C, T* 
 template <class T, int NS>
 void enqueue_up2(PoissonPlan* pl, int l, const LvT<T>& L, const LvT<T>& C, const T* uc, cudaStream_t s) {
     constexpr int FU = k2::fu_of(NS);
-    const dim3 grid((L.n[0] + FU - 1) / FU, (L.n[1] + FU - 1) / FU);
+    const dim3 grid((L.n[0] + FU - 1) / FU, (L.n[1] + FU - 1) / FU, pl->nb);
     if (l == 0 && pl->r32)
         launch(k2::up<T, float, true, NS>, grid, k2::NT, 0, s, L, C, (const T*)pl->u0pre, pl->r32, uc, (T*)pl->z,
                pl->part0, pl->part1, pl->scal, pl->ictl, pl->cnt + CNT_UP0);
@@ -2403,10 +2548,10 @@ void enqueue_tail(PoissonPlan* pl, cudaStream_t s) {
     const T* Minv = (sizeof(T) == 4) ? (const T*)pl->Minv_f : (const T*)pl->Minv;
     if (DIM == 2 && pl->fdm) {
         const int nx = pl->lev[pl->top].n[0], ny = pl->lev[pl->top].n[1];
-        launch(k2::fdm, 1, k2::FT, pl->fdm_smem, s, nx, ny, pl->fdm_tab, (const float*)pl->lev[pl->top].f,
+        launch(k2::fdm, pl->nb, k2::FT, pl->fdm_smem, s, nx, ny, pl->fdm_tab, (const float*)pl->lev[pl->top].f,
                                                 (float*)pl->lev[pl->top].upost);
     } else if (DIM == 2)
-        launch(k2::tail<T>, 1, k2::TT, pl->tail_smem, s, lv_dev<T>(pl), a, (const T*)pl->lev[pl->top].f,
+        launch(k2::tail<T>, pl->nb, k2::TT, pl->tail_smem, s, lv_dev<T>(pl), a, (const T*)pl->lev[pl->top].f,
                                                      (T*)pl->lev[pl->top].upost, Minv);
     else
         launch(k_mg_tail<T, DIM>, 1, kTailThreads, pl->tail_smem, s, lv_dev<T>(pl), a, (const T*)pl->lev[pl->top].f,
@@ -2420,7 +2565,7 @@ template <class T, int DIM>
 void enqueue_pq(PoissonPlan* pl, cudaStream_t s) {
     const bool ir = pl->r32 != nullptr;
     if (DIM == 2) {
-        const dim3 grid((pl->lev[0].n[0] + k2::FP - 1) / k2::FP, (pl->lev[0].n[1] + k2::FP - 1) / k2::FP);
+        const dim3 grid((pl->lev[0].n[0] + k2::FP - 1) / k2::FP, (pl->lev[0].n[1] + k2::FP - 1) / k2::FP, pl->nb);
         if (ir)
             launch(k2::pq<T, float>, grid, k2::NT, 0, s, make_lv<float>(pl->lev[0], DIM), (const T*)pl->z, pl->p32[0],
                                                      pl->p32[1], pl->q32, pl->part2, pl->scal, pl->ictl,
@@ -2468,18 +2613,22 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
         for (int l = pl->top - 1; l >= 0; --l) enqueue_up<T, DIM>(pl, l, s);
         enqueue_pq<T, DIM>(pl, s);
     }
-    const int rb = reduce_blocks(pl->N);
+    const dim3 rb(reduce_blocks(pl->N), pl->nb);
+    // a batch sets the while-node condition once, from every system's state
+    const int ug = (pl->nb > 1) ? 0 : use_graph;
     if (ir) {
         launch(k_ir_update, rb, NTV, 0, s, pl->e32, pl->r32, pl->p32[0], pl->p32[1], pl->q32, pl->N, pl->part0, pl->scal,
-                                       pl->ictl, pl->cnt + CNT_UPD, pl->inner_tol, pl->inner_max, pl->max_iter, h,
-                                       use_graph);
+                                       pl->ictl, pl->cnt + CNT_UPD, pl->inner_tol, pl->inner_max, pl->max_iter, h, ug);
         launch(k_ir_refine<DIM>, rb, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r, pl->e32, pl->r32, pl->part1,
-                                            pl->scal, pl->ictl, pl->cnt + CNT_REF, pl->rtol, pl->max_iter, h,
-                                            use_graph);
+                                            pl->scal, pl->ictl, pl->cnt + CNT_REF, pl->rtol, pl->max_iter, h, ug);
         pl->launches += 2;
     } else {
         launch(k_cg_update, rb, NTV, 0, s, x, pl->r, pl->p[0], pl->p[1], pl->q, pl->N, pl->part0, pl->scal, pl->ictl,
-                                       pl->cnt + CNT_UPD, pl->rtol, pl->max_iter, h, use_graph);
+                                       pl->cnt + CNT_UPD, pl->rtol, pl->max_iter, h, ug);
+        pl->launches += 1;
+    }
+    if (pl->nb > 1) {
+        launch(k_batch_cond, 1, NTV, 0, s, (const int*)pl->ictl, pl->nb, pl->bdone, h, use_graph);
         pl->launches += 1;
     }
 }
@@ -2487,12 +2636,16 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
 template <int DIM>
 void prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s, cudaGraphConditionalHandle h,
               int use_graph) {
-    const int rb = reduce_blocks(pl->N);
+    const dim3 rb(reduce_blocks(pl->N), pl->nb);
     launch(k_mean, rb, NTV, 0, s, b, pl->N, pl->part0, pl->scal, PS_MEANB, pl->cnt + CNT_MEANB);
     const LvT<double> L = make_lv<double>(pl->lev[0], DIM);
     launch(k_pcg_init<DIM>, rb, NTV, 0, s, L, b, x, pl->r, pl->r32, pl->part1, pl->part2, pl->scal, pl->ictl,
-                                       pl->cnt + CNT_INIT, pl->rtol, h, use_graph);
+                                       pl->cnt + CNT_INIT, pl->rtol, h, (pl->nb > 1) ? 0 : use_graph);
     pl->launches += 2;
+    if (pl->nb > 1) {
+        launch(k_batch_cond, 1, NTV, 0, s, (const int*)pl->ictl, pl->nb, pl->bdone, h, use_graph);
+        pl->launches += 1;
+    }
 }
 
 }  // namespace
@@ -2522,9 +2675,10 @@ cudaError_t poisson_enqueue_body(PoissonPlan* pl, double* x, cudaStream_t s, uns
 
 cudaError_t poisson_enqueue_epilogue(PoissonPlan* pl, double* x, cudaStream_t s, double* rep, int* status,
                                      int status_bit) {
-    const int rb = reduce_blocks(pl->N);
-    launch(k_mean, rb, NTV, 0, s, x, pl->N, pl->part0, pl->scal, PS_MEANX, pl->cnt + CNT_MEANX);
-    launch(k_sub_mean, rb, NTV, 0, s, x, pl->N, pl->scal, pl->ictl, rep, status, status_bit);
+    const dim3 rb(reduce_blocks(pl->N), pl->nb);
+    launch(k_mean, rb, NTV, 0, s, (const double*)x, pl->N, pl->part0, pl->scal, PS_MEANX, pl->cnt + CNT_MEANX);
+    launch(k_sub_mean, rb, NTV, 0, s, x, pl->N, (const double*)pl->scal, (const int*)pl->ictl,
+           pl->nb > 1 ? nullptr : rep, pl->nb > 1 ? nullptr : status, status_bit);
     pl->launches += 2;
     return cudaGetLastError();
 }
@@ -2554,17 +2708,27 @@ cudaError_t poisson_launch_single(PoissonPlan* pl, int which, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+const int* poisson_done_flag(const PoissonPlan* pl) { return pl->nb > 1 ? pl->bdone : pl->ictl + PI_DONE; }
+
+cudaError_t poisson_enqueue_batch_report(PoissonPlan* pl, double* const* rep, int* const* status, int status_bit,
+                                         cudaStream_t s) {
+    launch(k_batch_report, 1, NTV, 0, s, (const double*)pl->scal, (const int*)pl->ictl, pl->nb, rep, status,
+           status_bit);
+    pl->launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t poisson_solve_host_loop(PoissonPlan* pl, const double* b, double* x, cudaStream_t s) {
     cudaError_t e = poisson_enqueue_prologue(pl, b, x, s, 0ULL);
     if (e != cudaSuccess) return e;
     int done = 0;
-    e = cudaMemcpyAsync(&done, pl->ictl + PI_DONE, sizeof(int), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(&done, poisson_done_flag(pl), sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
     for (int guard = 0; !done && guard <= pl->max_iter; ++guard) {
         e = poisson_enqueue_body(pl, x, s, 0ULL);
         if (e != cudaSuccess) return e;
-        e = cudaMemcpyAsync(&done, pl->ictl + PI_DONE, sizeof(int), cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(&done, poisson_done_flag(pl), sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
     }

@@ -113,6 +113,13 @@ struct PoissonPlan {
     float* fdm_tab;       // S_x, S_x^T (nx x nx, eigenvectors as columns), S_y, S_y^T (ny x ny),
                           // inverse eigenvalue sums (ny x nx, 0 for the null mode)
     size_t fdm_smem;
+    // Batch of nb independent systems on the same grid (nb = 1: one system).
+    // Every per-solve array above holds nb consecutive copies (vectors and
+    // level arrays by their length, scal by PS_NSCAL, ictl by PI_NINT, cnt by
+    // kNumCounters, partial sums by npart); the kernels take the system index
+    // from one grid dimension.  bdone: 1 once every system has converged.
+    int nb;
+    int* bdone;
 };
 
 // Workspace bytes for a grid (no allocation).
@@ -127,6 +134,23 @@ size_t poisson_plan_bytes(int dim, const int n[3], const int periodic[3], int mg
 bool poisson_plan_init(PoissonPlan* pl, int dim, const int n[3], const double h[3], const int periodic[3],
                        int mg_fp32, int sweeps, int tail_cells, double rtol, int max_iter, void* ws,
                        size_t ws_bytes, std::vector<double>* minv_host, const char** err);
+
+// The same for a batch of nb independent systems on one 2D grid (nb >= 1).
+size_t poisson_plan_bytes_batch(int dim, const int n[3], const int periodic[3], int mg_fp32, int tail_cells, int nb,
+                                int* nlev_out, long long* Nc_out, const char** err);
+bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const double h[3], const int periodic[3],
+                             int mg_fp32, int sweeps, int tail_cells, double rtol, int max_iter, int nb, void* ws,
+                             size_t ws_bytes, std::vector<double>* minv_host, const char** err);
+
+// Device flag a host-driven loop polls: 1 once the solve (every system of a
+// batch) has finished.
+const int* poisson_done_flag(const PoissonPlan* pl);
+
+// Batches: copy each system's iteration count and final relative residual to
+// rep[k][0..1] and OR status_bit into *status[k] when system k did not
+// converge (rep, status: device arrays of nb device pointers).
+cudaError_t poisson_enqueue_batch_report(PoissonPlan* pl, double* const* rep, int* const* status, int status_bit,
+                                         cudaStream_t s);
 
 // Copy the host-prepared tables into the plan's device buffers (synchronises s).
 bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& minv_host, cudaStream_t s,

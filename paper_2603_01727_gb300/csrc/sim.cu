@@ -1593,6 +1593,59 @@ sim_status sim_adjoint_field(sim_t* s, int id, double* buf, int dir) {
     return SIM_OK;
 }
 
+sim_status sim_poisson_batch_workspace_size(const int n[2], const int periodic[2], int nb, int precision,
+                                            size_t* bytes) {
+    if (!n || !periodic || !bytes || nb < 1 || (precision != SIM_FP64 && precision != SIM_MIXED)) return SIM_EINVAL;
+    const int nn[3] = {n[0], n[1], 1};
+    const int per[3] = {periodic[0] != 0, periodic[1] != 0, 0};
+    const char* err = nullptr;
+    const size_t b = poisson_plan_bytes_batch(2, nn, per, precision == SIM_MIXED, 0, nb, nullptr, nullptr, &err);
+    if (b == 0) return SIM_EINVAL;
+    *bytes = b;
+    return SIM_OK;
+}
+
+sim_status sim_poisson_solve_batch(const int n[2], const double h[2], const int periodic[2], int nb, int precision,
+                                   const double* d_b, double* d_P, double rtol, int max_iter, void* d_workspace,
+                                   size_t workspace_bytes, void* cuda_stream, int* iters, double* rel_resid) {
+    if (!n || !h || !periodic || !d_b || !d_P || !d_workspace || nb < 1) return SIM_EINVAL;
+    if (precision != SIM_FP64 && precision != SIM_MIXED) return SIM_EINVAL;
+    if (!(rtol > 0.0 && rtol < 1.0) || max_iter < 1) return SIM_EINVAL;
+    const int nn[3] = {n[0], n[1], 1};
+    const double hh[3] = {h[0], h[1], 1.0};
+    const int per[3] = {periodic[0] != 0, periodic[1] != 0, 0};
+    for (int d = 0; d < 2; ++d)
+        if (nn[d] < 2 || !(hh[d] > 0.0)) return SIM_EINVAL;
+    const int mixed = precision == SIM_MIXED;
+    const char* err = nullptr;
+    const size_t need = poisson_plan_bytes_batch(2, nn, per, mixed, 0, nb, nullptr, nullptr, &err);
+    if (need == 0) return SIM_EINVAL;
+    if (workspace_bytes < need) return SIM_ENOMEM;
+    PoissonPlan pl;
+    std::vector<double> minv;
+    if (!poisson_plan_init_batch(&pl, 2, nn, hh, per, mixed, 0, 0, rtol, max_iter, nb, d_workspace, workspace_bytes,
+                                 &minv, &err))
+        return SIM_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!poisson_upload_coarse(&pl, minv, st, &err)) return SIM_ECUDA;
+    cudaError_t e = poisson_solve_host_loop(&pl, d_b, d_P, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return SIM_ECUDA;
+    std::vector<double> sc((size_t)nb * PS_NSCAL);
+    std::vector<int> ic((size_t)nb * PI_NINT);
+    if (cudaMemcpy(sc.data(), pl.scal, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SIM_ECUDA;
+    if (cudaMemcpy(ic.data(), pl.ictl, sizeof(int) * ic.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SIM_ECUDA;
+    int noconv = 0;
+    for (int k = 0; k < nb; ++k) {
+        if (iters) iters[k] = (int)sc[(size_t)k * PS_NSCAL + PS_ITERS];
+        if (rel_resid) rel_resid[k] = sc[(size_t)k * PS_NSCAL + PS_RELRES];
+        noconv |= ic[(size_t)k * PI_NINT + PI_NOCONV];
+    }
+    return noconv ? SIM_ENOCONV : SIM_OK;
+}
+
 // ------------------------------ batches --------------------------------------
 // Many independent simulations advanced by one CUDA graph per step: each
 // simulation's whole step (its kernels and its two pressure-solve while nodes)

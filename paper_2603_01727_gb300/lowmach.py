@@ -87,6 +87,8 @@ def load():
         "sim_poisson_workspace_size": ([I, P(I), P(I), P(SZ)], I),
         "sim_poisson_solve": ([I, P(I), P(D), P(I), VP, VP, D, I, VP, SZ, VP, P(I), P(D)], I),
         "sim_poisson_solve_noalloc": ([I, P(I), P(D), P(I), VP, VP, D, I, VP, P(I), P(D)], I),
+        "sim_poisson_batch_workspace_size": ([P(I), P(I), I, I, P(SZ)], I),
+        "sim_poisson_solve_batch": ([P(I), P(D), P(I), I, I, VP, VP, D, I, VP, SZ, VP, P(I), P(D)], I),
         "sim_objective": ([VP, P(D)], I),
         "sim_adjoint_workspace_size": ([VP, P(SZ)], I),
         "sim_adjoint_begin": ([VP, VP, SZ], I),
@@ -112,7 +114,8 @@ def exported_symbols():
             "sim_sync", "sim_query", "sim_last_error", "sim_destroy", "sim_time_kernel", "sim_state_size",
             "sim_state_save",
             "sim_state_load", "sim_poisson_workspace_size",
-            "sim_poisson_solve", "sim_poisson_solve_noalloc", "sim_objective", "sim_adjoint_workspace_size",
+            "sim_poisson_solve", "sim_poisson_solve_noalloc", "sim_poisson_batch_workspace_size",
+            "sim_poisson_solve_batch", "sim_objective", "sim_adjoint_workspace_size",
             "sim_adjoint_begin", "sim_adjoint_step", "sim_adjoint_field", "sim_adjoint_end",
             "sim_batch_create", "sim_batch_step",
             "sim_batch_sync", "sim_batch_last_error", "sim_batch_destroy"]
@@ -354,6 +357,32 @@ def poisson_solve(b, P, h, periodic, rtol=1e-12, max_iter=200, stream=None):
                                    ctypes.c_void_p(st.cuda_stream), ctypes.byref(it), ctypes.byref(rr))
     _check(lib, status)
     return it.value, rr.value
+
+
+def poisson_solve_batch(b, P, h, periodic, precision=SIM_FP64, rtol=1e-12, max_iter=200, stream=None):
+    """Batched stand-alone pressure solve: b, P CUDA float64 tensors of shape
+    (nb, n1, n0), nb independent 2D systems on one grid, advanced together.
+    Returns (iterations per system, final relative residual per system)."""
+    import torch
+    lib = load()
+    assert b.dim() == 3 and b.shape == P.shape
+    nb = int(b.shape[0])
+    n = (ctypes.c_int * 2)(int(b.shape[2]), int(b.shape[1]))
+    per = (ctypes.c_int * 2)(*[int(bool(x)) for x in periodic])
+    hh = (ctypes.c_double * 2)(*[float(x) for x in h])
+    sz = ctypes.c_size_t()
+    _check(lib, lib.sim_poisson_batch_workspace_size(n, per, nb, int(precision), ctypes.byref(sz)))
+    ws = torch.empty(sz.value + 256, dtype=torch.uint8, device=b.device)
+    ptr = (ws.data_ptr() + 255) // 256 * 256
+    st = stream if stream is not None else torch.cuda.current_stream(b.device)
+    it = (ctypes.c_int * nb)()
+    rr = (ctypes.c_double * nb)()
+    status = lib.sim_poisson_solve_batch(n, hh, per, nb, int(precision), ctypes.c_void_p(b.data_ptr()),
+                                         ctypes.c_void_p(P.data_ptr()), float(rtol), int(max_iter),
+                                         ctypes.c_void_p(ptr), ctypes.c_size_t(sz.value),
+                                         ctypes.c_void_p(st.cuda_stream), it, rr)
+    _check(lib, status)
+    return list(it), list(rr)
 
 
 def poisson_solve_noalloc(b, P, h, periodic, rtol=1e-12, max_iter=200, stream=None):
