@@ -362,7 +362,7 @@ def run_gpu_batch(args, precision, world, rank, local, pg):
         batch.step(1)
         ends[k].record(stream)
         batch.sync()
-        launches += sum(int(s.query(LM.SIM_Q_KERNEL_LAUNCHES)) for s in sims)
+        launches += int(batch.launches())
         iters.append(float(np.mean([s.query(LM.SIM_Q_ITERS_PRED) + s.query(LM.SIM_Q_ITERS_CORR) for s in sims])))
     torch.cuda.synchronize(device)
     clk = clocks.stop()

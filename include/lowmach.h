@@ -264,7 +264,18 @@ sim_status sim_adjoint_end(sim_t *sim);
  *   sync:    waits and returns the first failing member's device status.
  * ------------------------------------------------------------------------- */
 typedef struct sim_batch sim_batch_t;
-sim_status sim_batch_create(sim_t *const *sims, int n, void *cuda_stream, sim_batch_t **out);
+/* Batched pressure solves.  Members with the same 2D grid, spacing, sides
+ * and solver settings form a group whose two solves per step run as one
+ * batched solve (sim_poisson_solve_batch's kernels: one launch per multigrid
+ * level and CG update for the whole group), with bitwise the results of
+ * their own solves.  That needs a device workspace of
+ * sim_batch_workspace_size bytes (caller-owned, 256-byte aligned, live until
+ * destroy); with d_workspace NULL every member keeps its own solves.
+ * query_launches (after sync): kernels the last batch step launched. */
+sim_status sim_batch_workspace_size(sim_t *const *sims, int n, size_t *bytes);
+sim_status sim_batch_create(sim_t *const *sims, int n, void *d_workspace, size_t workspace_bytes,
+                            void *cuda_stream, sim_batch_t **out);
+sim_status sim_batch_query_launches(sim_batch_t *batch, double *out);
 sim_status sim_batch_step(sim_batch_t *batch, int nsteps);
 sim_status sim_batch_sync(sim_batch_t *batch);
 const char *sim_batch_last_error(const sim_batch_t *batch);

@@ -376,6 +376,46 @@ cudaError_t enqueue_init(sim_t* s, cudaStream_t st) {
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// Capture a solve's prologue and its CG loop as a conditional while node on
+// st (being captured); the loop body is captured on side into the node's body
+// graph.  body_launch: kernels per iteration.
+cudaError_t capture_while_solve(PoissonPlan* pl, const double* b, double* x, cudaStream_t st, cudaStream_t side,
+                                int* body_launch) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph_h;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph_h, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, graph_h, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    e = poisson_enqueue_prologue(pl, b, x, st, (unsigned long long)h);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph_h, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph_h, dv.data(), nullptr, dv.size(), &np);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(side, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    const int before = pl->launches;
+    e = poisson_enqueue_body(pl, x, side, (unsigned long long)h);
+    cudaGraph_t body_out = bodyg;
+    cudaError_t e2 = cudaStreamEndCapture(side, &body_out);
+    if (e != cudaSuccess) return e;
+    if (e2 != cudaSuccess) return e2;
+    *body_launch = pl->launches - before;
+    return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
 // Pressure solve of one stage; graph mode adds a conditional while node whose
 // condition the prologue and every iteration set on the device.
 cudaError_t enqueue_poisson(sim_t* s, cudaStream_t st, bool graph, int iter_slot, int* L, int* body_launch) {
@@ -397,39 +437,7 @@ cudaError_t enqueue_poisson(sim_t* s, cudaStream_t st, bool graph, int iter_slot
             *body_launch = pl->launches - before;
         }
     } else {
-        cudaStreamCaptureStatus cs;
-        cudaGraph_t graph_h;
-        const cudaGraphNode_t* deps = nullptr;
-        size_t ndeps = 0;
-        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph_h, &deps, nullptr, &ndeps);
-        if (e != cudaSuccess) return e;
-        cudaGraphConditionalHandle h;
-        e = cudaGraphConditionalHandleCreate(&h, graph_h, 1, cudaGraphCondAssignDefault);
-        if (e != cudaSuccess) return e;
-        e = poisson_enqueue_prologue(pl, s->b, s->P, st, (unsigned long long)h);
-        if (e != cudaSuccess) return e;
-        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph_h, &deps, nullptr, &ndeps);
-        if (e != cudaSuccess) return e;
-        std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
-        cudaGraphNodeParams np = {};
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = h;
-        np.conditional.type = cudaGraphCondTypeWhile;
-        np.conditional.size = 1;
-        cudaGraphNode_t node;
-        e = cudaGraphAddNode(&node, graph_h, dv.data(), nullptr, dv.size(), &np);
-        if (e != cudaSuccess) return e;
-        cudaGraph_t body = np.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(s->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-        if (e != cudaSuccess) return e;
-        const int before = pl->launches;
-        e = poisson_enqueue_body(pl, s->P, s->side, (unsigned long long)h);
-        cudaGraph_t body_out = body;
-        cudaError_t e2 = cudaStreamEndCapture(s->side, &body_out);
-        if (e != cudaSuccess) return e;
-        if (e2 != cudaSuccess) return e2;
-        *body_launch = pl->launches - before;
-        e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        e = capture_while_solve(pl, s->b, s->P, st, s->side, body_launch);
         if (e != cudaSuccess) return e;
     }
     // zero mean; iterations / residual into the step's scalar slots and
@@ -474,8 +482,16 @@ ResidArgs resid_common(sim_t* s) {
     return a;
 }
 
-// Enqueue step number n (predictor + corrector).  graph: being captured on st.
-cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int* L, int* body) {
+// Sections of a step, in order: SEC_PRED (predictor up to the right-hand
+// side), SEC_POIS_PRED (its pressure solve), SEC_MID (predictor projection to
+// the corrector's right-hand side), SEC_POIS_CORR, SEC_END (corrector
+// projection, ghosts, p0 rotation).  A batch runs the solves of same-grid
+// members as one batched solve between the other sections.
+enum StepSec : int { SEC_PRED = 0, SEC_POIS_PRED = 1, SEC_MID = 2, SEC_POIS_CORR = 3, SEC_END = 4 };
+
+cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool graph, int* L, int* body, int first,
+                                  int last) {
+    auto on = [&](int k) { return k >= first && k <= last; };
     const Geom& g = s->g;
     const int D = g.dim;
     const double dt = s->prm.dt;
@@ -516,10 +532,12 @@ cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int
         a.w0 = 3.0; a.w1 = -4.0; a.w2 = 1.0; a.wden = 2.0 * dt;
     }
     a.iwden = (a.wden != 0.0) ? 1.0 / a.wden : 0.0;
-    launch_residual(g, s->ph, a, st, L);
-    ghost(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}}, st, L);
-    launch_state(g, s->ph, s->Zs, s->Hs, s->T, r.rho_new, s->kap, s->sc, SC_P0_STAR, s->part, s->status, st, L);
-    ghost(s, {{s->kap, GW_KAPPA}}, st, L);
+    if (on(SEC_PRED)) {
+        launch_residual(g, s->ph, a, st, L);
+        ghost(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}}, st, L);
+        launch_state(g, s->ph, s->Zs, s->Hs, s->T, r.rho_new, s->kap, s->sc, SC_P0_STAR, s->part, s->status, st, L);
+        ghost(s, {{s->kap, GW_KAPPA}}, st, L);
+    }
 
     FluxArgs fa;
     std::memset(&fa, 0, sizeof(fa));
@@ -541,8 +559,9 @@ cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int
     fa.part = s->part;
     fa.b = s->b;
     fa.correct = 1;
-    launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
-    cudaError_t e = enqueue_poisson(s, st, graph, SC_ITERS_PRED, L, body);
+    if (on(SEC_PRED)) launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
+    cudaError_t e = cudaSuccess;
+    if (on(SEC_POIS_PRED)) e = enqueue_poisson(s, st, graph, SC_ITERS_PRED, L, body);
     if (e != cudaSuccess) return e;
     ProjArgs pa;
     std::memset(&pa, 0, sizeof(pa));
@@ -559,9 +578,11 @@ cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int
     pa.eA = s->eA;
     pa.eB = s->eB;
     pa.eC = s->eC;
-    launch_project(g, pa, st, L);
-    ghost_v(s, s->vs, st, L);
-    if (s->adj_save) {
+    if (on(SEC_MID)) {
+        launch_project(g, pa, st, L);
+        ghost_v(s, s->vs, st, L);
+    }
+    if (on(SEC_MID) && s->adj_save) {
         // predictor values read by the reverse pass (overwritten by the corrector)
         const size_t fp = sizeof(double) * (size_t)g.npad;
         for (int d = 0; d < D && e == cudaSuccess; ++d) {
@@ -605,20 +626,29 @@ cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int
         c.w0 = 3.0; c.w1 = -4.0; c.w2 = 1.0; c.wden = 2.0 * dt;
     }
     c.iwden = 1.0 / c.wden;
-    launch_residual(g, s->ph, c, st, L);
-    ghost(s, {{s->Z, GW_Z}, {s->H, GW_H}}, st, L);
-    launch_state(g, s->ph, s->Z, s->H, s->T, r.rho_new, s->kap, s->sc, SC_P0_NEW, s->part, s->status, st, L);
-    ghost(s, {{s->kap, GW_KAPPA}}, st, L);
     fa.p0_slot = SC_P0_NEW;
-    launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
-    e = enqueue_poisson(s, st, graph, SC_ITERS_CORR, L, body);
+    if (on(SEC_MID)) {
+        launch_residual(g, s->ph, c, st, L);
+        ghost(s, {{s->Z, GW_Z}, {s->H, GW_H}}, st, L);
+        launch_state(g, s->ph, s->Z, s->H, s->T, r.rho_new, s->kap, s->sc, SC_P0_NEW, s->part, s->status, st, L);
+        ghost(s, {{s->kap, GW_KAPPA}}, st, L);
+        launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
+    }
+    if (on(SEC_POIS_CORR)) e = enqueue_poisson(s, st, graph, SC_ITERS_CORR, L, body);
     if (e != cudaSuccess) return e;
     for (int d = 0; d < D; ++d) pa.v[d] = s->v[d];
     pa.p0_slot = SC_P0_NEW;  // T^{n+1}, p0^{n+1}
-    launch_project(g, pa, st, L);
-    ghost_v(s, s->v, st, L);
-    launch_rotate_p0(s->sc, st, L);
+    if (on(SEC_END)) {
+        launch_project(g, pa, st, L);
+        ghost_v(s, s->v, st, L);
+        launch_rotate_p0(s->sc, st, L);
+    }
     return cudaGetLastError();
+}
+
+// Enqueue step number n (predictor + corrector).  graph: being captured on st.
+cudaError_t enqueue_step(sim_t* s, long long n, cudaStream_t st, bool graph, int* L, int* body) {
+    return enqueue_step_sections(s, n, st, graph, L, body, SEC_PRED, SEC_END);
 }
 
 void after_step(sim_t* s) {
@@ -1654,6 +1684,25 @@ sim_status sim_poisson_solve_batch(const int n[2], const double h[2], const int 
 // concurrently.  Simulations must step in lockstep (same step count).
 }  // extern "C"
 
+// Members of a batch with the same grid and pressure-solver settings share
+// one batched solve per stage (one launch per multigrid level and CG update
+// for all of them) when the batch has a workspace.
+struct BatchGroup {
+    std::vector<int> members;
+    PoissonPlan pl;
+    std::vector<double> minv;
+    double* bb;                  // contiguous right-hand sides [nb][N]
+    double* xb;                  // contiguous solutions (warm start in, answer out)
+    const double** bptr;         // device table: each member's b
+    double** xptr;               // device table: each member's P
+    double** rep[2];             // device tables: each member's predictor / corrector report slots
+    int** status;                // device table: each member's status word
+    cudaStream_t st, side;
+    cudaEvent_t ev;
+    int fixed_launches;          // kernels of one solve outside its loop
+    int body_launches;           // kernels per iteration
+};
+
 struct sim_batch {
     std::vector<sim_t*> sims;
     cudaStream_t stream;         // caller's stream (the batch graph runs here)
@@ -1662,10 +1711,50 @@ struct sim_batch {
     std::vector<cudaEvent_t> join;
     cudaGraphExec_t gexec[6];
     bool gvalid[6];
+    std::vector<BatchGroup> groups;
+    std::vector<int> group_of;   // member -> group, or -1 (own solves)
     char err[512];
 };
 
 namespace {
+
+// Members whose pressure solves can be batched together: same 2D grid,
+// spacing, sides and solver settings (precision, sweeps, coarse level,
+// tolerance, iteration cap).
+std::vector<std::vector<int>> batch_groups(sim_t* const* sims, int n) {
+    std::vector<std::vector<int>> out;
+    auto same = [](const sim_t* a, const sim_t* b) {
+        const PoissonPlan &p = a->pp, &q = b->pp;
+        return a->g.dim == 2 && b->g.dim == 2 && a->g.n[0] == b->g.n[0] && a->g.n[1] == b->g.n[1] &&
+               a->g.h[0] == b->g.h[0] && a->g.h[1] == b->g.h[1] && a->g.periodic[0] == b->g.periodic[0] &&
+               a->g.periodic[1] == b->g.periodic[1] && p.mg_fp32 == q.mg_fp32 && p.sweeps == q.sweeps &&
+               p.top == q.top && p.rtol == q.rtol && p.max_iter == q.max_iter &&
+               (p.r32 != nullptr) == (q.r32 != nullptr) && p.nlev > 1;
+    };
+    std::vector<int> used((size_t)n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (used[(size_t)i] || sims[i]->g.dim != 2 || sims[i]->pp.nlev < 2) continue;
+        std::vector<int> g{i};
+        used[(size_t)i] = 1;
+        for (int j = i + 1; j < n; ++j)
+            if (!used[(size_t)j] && same(sims[i], sims[j])) {
+                g.push_back(j);
+                used[(size_t)j] = 1;
+            }
+        if (g.size() >= 2) out.push_back(g);
+    }
+    return out;
+}
+
+// Workspace bytes of one group (plan, contiguous b and x, pointer tables).
+size_t group_bytes(const sim_t* s0, int nb, const char** err) {
+    const PoissonPlan& p = s0->pp;
+    const int per[3] = {s0->g.periodic[0], s0->g.periodic[1], 0};
+    const size_t pb = poisson_plan_bytes_batch(2, s0->g.n, per, p.mg_fp32, s0->prm.mg_tail_cells, nb, nullptr,
+                                               nullptr, err);
+    if (pb == 0) return 0;
+    return a256(pb) + 2 * a256(sizeof(double) * (size_t)nb * (size_t)s0->g.ncell) + 5 * a256(sizeof(void*) * nb);
+}
 
 sim_status bfail(sim_batch_t* b, sim_status st, const char* fmt, ...) {
     if (b) {
@@ -1691,18 +1780,59 @@ void batch_drop_graphs(sim_batch_t* b) {
         }
 }
 
+// One stage's batched solve of a group, captured on G.st: gather b and the
+// warm start, prologue + while node, epilogue, scatter, per-member reports.
+cudaError_t batch_group_solve(BatchGroup& G, int which) {
+    const int nb = (int)G.members.size();
+    const long long N = G.pl.N;
+    G.pl.launches = 0;
+    launch_gather(G.bptr, G.bb, N, nb, G.st);
+    launch_gather((const double* const*)G.xptr, G.xb, N, nb, G.st);
+    int body = 0;
+    cudaError_t e = capture_while_solve(&G.pl, G.bb, G.xb, G.st, G.side, &body);
+    if (e != cudaSuccess) return e;
+    e = poisson_enqueue_epilogue(&G.pl, G.xb, G.st, nullptr, nullptr, 0);
+    if (e != cudaSuccess) return e;
+    launch_scatter(G.xb, G.xptr, N, nb, G.st);
+    e = poisson_enqueue_batch_report(&G.pl, G.rep[which], G.status, ST_NOCONV, G.st);
+    G.body_launches = body;
+    G.fixed_launches = G.pl.launches - body + 3;   // + gathers and scatter
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// The batch step as one graph: per-member sections on forked streams, joined
+// before and after each stage's batched solves (one forked stream per group).
 sim_status batch_capture(sim_batch_t* b, int phase) {
     BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
-    cudaError_t e = cudaEventRecord(b->fork, b->cap);
-    for (size_t i = 0; i < b->sims.size() && e == cudaSuccess; ++i) {
-        sim_t* s = b->sims[i];
-        e = cudaStreamWaitEvent(s->cap, b->fork, 0);
-        int L = 0, body = 0;
-        if (e == cudaSuccess) e = enqueue_step(s, s->nstep, s->cap, true, &L, &body);
-        s->launches_fixed_graph[phase] = L;
-        s->body_launches = body;
-        if (e == cudaSuccess) e = cudaEventRecord(b->join[i], s->cap);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[i], 0);
+    cudaError_t e = cudaSuccess;
+    const int secs[3][2] = {{SEC_PRED, SEC_POIS_PRED}, {SEC_MID, SEC_POIS_CORR}, {SEC_END, SEC_END}};
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+        b->sims[i]->launches_fixed_graph[phase] = 0;
+        b->sims[i]->body_launches = 0;
+    }
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b->fork, b->cap);
+        for (size_t i = 0; i < b->sims.size() && e == cudaSuccess; ++i) {
+            sim_t* s = b->sims[i];
+            const bool batched = b->group_of[i] >= 0;
+            // a batched member leaves its solve to the group
+            const int last = (batched && k < 2) ? secs[k][0] : secs[k][1];
+            e = cudaStreamWaitEvent(s->cap, b->fork, 0);
+            int L = 0, body = 0;
+            if (e == cudaSuccess) e = enqueue_step_sections(s, s->nstep, s->cap, true, &L, &body, secs[k][0], last);
+            s->launches_fixed_graph[phase] += L;
+            if (!batched && body > 0) s->body_launches = body;
+            if (e == cudaSuccess) e = cudaEventRecord(b->join[i], s->cap);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[i], 0);
+        }
+        if (k == 2 || b->groups.empty()) continue;
+        if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->cap);
+        for (BatchGroup& G : b->groups) {
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(G.st, b->fork, 0);
+            if (e == cudaSuccess) e = batch_group_solve(G, k);
+            if (e == cudaSuccess) e = cudaEventRecord(G.ev, G.st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, G.ev, 0);
+        }
     }
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
@@ -1721,16 +1851,41 @@ sim_status batch_capture(sim_batch_t* b, int phase) {
 
 extern "C" {
 
-sim_status sim_batch_create(sim_t* const* sims, int n, void* cuda_stream, sim_batch_t** out) {
+sim_status sim_batch_workspace_size(sim_t* const* sims, int n, size_t* bytes) {
+    if (!sims || n < 1 || !bytes) return SIM_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!sims[i]) return SIM_EINVAL;
+    size_t total = 0;
+    const char* err = nullptr;
+    for (const auto& g : batch_groups(sims, n)) {
+        const size_t gb = group_bytes(sims[g[0]], (int)g.size(), &err);
+        if (gb == 0) return SIM_EINVAL;
+        total += gb;
+    }
+    *bytes = total;
+    return SIM_OK;
+}
+
+sim_status sim_batch_create(sim_t* const* sims, int n, void* d_workspace, size_t workspace_bytes, void* cuda_stream,
+                            sim_batch_t** out) {
     if (!out || !sims || n < 1) return SIM_EINVAL;
     *out = nullptr;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < i; ++j)
             if (!sims[i] || sims[i] == sims[j]) return SIM_EINVAL;
+    if (!sims[0]) return SIM_EINVAL;
+    if (d_workspace && ((uintptr_t)d_workspace & 255) != 0) return SIM_EINVAL;
+    size_t need = 0;
+    if (d_workspace) {
+        const sim_status st = sim_batch_workspace_size(sims, n, &need);
+        if (st != SIM_OK) return st;
+        if (workspace_bytes < need) return SIM_ENOMEM;
+    }
     sim_batch_t* b = new sim_batch();
     b->sims.assign(sims, sims + n);
     b->stream = (cudaStream_t)cuda_stream;
     b->join.assign((size_t)n, nullptr);
+    b->group_of.assign((size_t)n, -1);
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
@@ -1738,7 +1893,91 @@ sim_status sim_batch_create(sim_t* const* sims, int n, void* cuda_stream, sim_ba
         sim_batch_destroy(b);
         return SIM_ECUDA;
     }
+    if (d_workspace) {
+        // batched solves of same-grid members: plans, contiguous vectors and
+        // device pointer tables carved from the workspace
+        char* cur = (char*)d_workspace;
+        const char* err = nullptr;
+        for (const auto& gm : batch_groups(sims, n)) {
+            b->groups.emplace_back();
+            BatchGroup& G = b->groups.back();
+            std::memset(&G.pl, 0, sizeof(G.pl));
+            G.members = gm;
+            const int nb = (int)gm.size();
+            const sim_t* s0 = sims[gm[0]];
+            const size_t gb = group_bytes(s0, nb, &err);
+            const int per[3] = {s0->g.periodic[0], s0->g.periodic[1], 0};
+            const size_t pb = a256(poisson_plan_bytes_batch(2, s0->g.n, per, s0->pp.mg_fp32, s0->prm.mg_tail_cells,
+                                                            nb, nullptr, nullptr, &err));
+            bool ok = poisson_plan_init_batch(&G.pl, 2, s0->g.n, s0->g.h, per, s0->pp.mg_fp32, s0->pp.sweeps,
+                                              s0->prm.mg_tail_cells, s0->pp.rtol, s0->pp.max_iter, nb, cur, pb,
+                                              &G.minv, &err);
+            if (ok) ok = poisson_upload_coarse(&G.pl, G.minv, b->stream, &err);
+            if (!ok) {
+                sim_batch_destroy(b);
+                return SIM_EINVAL;
+            }
+            char* q = cur + pb;
+            const size_t vb = a256(sizeof(double) * (size_t)nb * (size_t)s0->g.ncell), tb = a256(sizeof(void*) * nb);
+            G.bb = (double*)q;
+            G.xb = (double*)(q + vb);
+            G.bptr = (const double**)(q + 2 * vb);
+            G.xptr = (double**)(q + 2 * vb + tb);
+            G.rep[0] = (double**)(q + 2 * vb + 2 * tb);
+            G.rep[1] = (double**)(q + 2 * vb + 3 * tb);
+            G.status = (int**)(q + 2 * vb + 4 * tb);
+            cur += gb;
+            std::vector<const void*> tab[5];
+            for (int k : gm) {
+                sim_t* m = sims[k];
+                b->group_of[(size_t)k] = (int)b->groups.size() - 1;
+                tab[0].push_back(m->b);
+                tab[1].push_back(m->P);
+                tab[2].push_back(m->sc + SC_ITERS_PRED);
+                tab[3].push_back(m->sc + SC_ITERS_CORR);
+                tab[4].push_back(m->status);
+            }
+            void* dst[5] = {(void*)G.bptr, (void*)G.xptr, (void*)G.rep[0], (void*)G.rep[1], (void*)G.status};
+            for (int t = 0; t < 5 && e == cudaSuccess; ++t)
+                e = cudaMemcpyAsync(dst[t], tab[t].data(), sizeof(void*) * nb, cudaMemcpyHostToDevice, b->stream);
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G.side, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+            if (e != cudaSuccess) {
+                sim_batch_destroy(b);
+                return SIM_ECUDA;
+            }
+        }
+    }
     *out = b;
+    return SIM_OK;
+}
+
+// Kernels the last batch step launched, after sim_batch_sync: the members'
+// own kernels plus, per group, its solves' kernels (the loop runs as long as
+// its slowest member).
+sim_status sim_batch_query_launches(sim_batch_t* b, double* out) {
+    if (!b || !out) return SIM_EINVAL;
+    double total = 0.0;
+    for (sim_t* s : b->sims) {
+        double v = 0.0;
+        const sim_status st = sim_query(s, SIM_Q_KERNEL_LAUNCHES, &v);
+        if (st != SIM_OK) return bfail(b, st, "%s", s->err);
+        total += v;
+    }
+    for (const BatchGroup& G : b->groups) {
+        double itp = 0.0, itc = 0.0;
+        for (int k : G.members) {
+            double a = 0.0, c = 0.0;
+            sim_query(b->sims[(size_t)k], SIM_Q_ITERS_PRED, &a);
+            sim_query(b->sims[(size_t)k], SIM_Q_ITERS_CORR, &c);
+            itp = a > itp ? a : itp;
+            itc = c > itc ? c : itc;
+        }
+        total += 2.0 * G.fixed_launches + G.body_launches * (itp + itc);
+    }
+    *out = total;
     return SIM_OK;
 }
 
@@ -1801,6 +2040,11 @@ const char* sim_batch_last_error(const sim_batch_t* b) { return b ? b->err : "nu
 void sim_batch_destroy(sim_batch_t* b) {
     if (!b) return;
     batch_drop_graphs(b);
+    for (BatchGroup& G : b->groups) {
+        if (G.st) cudaStreamDestroy(G.st);
+        if (G.side) cudaStreamDestroy(G.side);
+        if (G.ev) cudaEventDestroy(G.ev);
+    }
     for (cudaEvent_t e : b->join)
         if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);

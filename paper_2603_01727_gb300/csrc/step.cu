@@ -683,6 +683,19 @@ __global__ void k_add_unpack(Geom g, const double* __restrict__ src, double* __r
     if (t < g.ncell) dst[pad_index(g, t)] += src[t];
 }
 
+// Batched solves: copy the systems' separate arrays into / out of one
+// contiguous [nb][N] array (grid dimension y = system).
+__global__ void k_gather(const double* const* __restrict__ src, double* __restrict__ dst, long long N) {
+    const double* s = src[blockIdx.y];
+    double* d = dst + (long long)blockIdx.y * N;
+    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < N; t += (long long)gridDim.x * NT) d[t] = s[t];
+}
+__global__ void k_scatter(const double* __restrict__ src, double* const* __restrict__ dst, long long N) {
+    const double* s = src + (long long)blockIdx.y * N;
+    double* d = dst[blockIdx.y];
+    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < N; t += (long long)gridDim.x * NT) d[t] = s[t];
+}
+
 __global__ void k_u8_to_double(Geom g, const uint8_t* __restrict__ src, double* __restrict__ dst) {
     const long long t = (long long)blockIdx.x * NT + threadIdx.x;
     if (t >= g.ncell) return;
@@ -1513,6 +1526,13 @@ void launch_unpack(const Geom& g, const double* compact, double* padded, cudaStr
 
 void launch_add_unpack(const Geom& g, const double* compact, double* padded, cudaStream_t s) {
     k_add_unpack<<<blocks_for(g.ncell), NT, 0, s>>>(g, compact, padded);
+}
+
+void launch_gather(const double* const* src, double* dst, long long N, int nb, cudaStream_t s) {
+    k_gather<<<dim3(reduce_blocks(N), nb), NT, 0, s>>>(src, dst, N);
+}
+void launch_scatter(const double* src, double* const* dst, long long N, int nb, cudaStream_t s) {
+    k_scatter<<<dim3(reduce_blocks(N), nb), NT, 0, s>>>(src, dst, N);
 }
 
 void launch_u8_to_double(const Geom& g, const uint8_t* padded, double* compact, cudaStream_t s) {

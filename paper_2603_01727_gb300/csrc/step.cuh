@@ -185,6 +185,10 @@ void launch_bkinds(const Geom& g, const int bc[3][2], const uint8_t* chi, uint8_
 void launch_pack(const Geom& g, const double* padded, double* compact, int face_dir, cudaStream_t s);
 void launch_unpack(const Geom& g, const double* compact, double* padded, cudaStream_t s);
 void launch_u8_to_double(const Geom& g, const uint8_t* padded, double* compact, cudaStream_t s);
+// Batched solves: nb device arrays of N doubles (src[k] / dst[k], device
+// pointer tables) to and from one contiguous [nb][N] array.
+void launch_gather(const double* const* src, double* dst, long long N, int nb, cudaStream_t s);
+void launch_scatter(const double* src, double* const* dst, long long N, int nb, cudaStream_t s);
 void launch_add_unpack(const Geom& g, const double* compact, double* padded, cudaStream_t s);
 
 // Adjoint (reverse-mode) launchers; every one adds the adjoint of its forward

@@ -95,7 +95,9 @@ def load():
         "sim_adjoint_step": ([VP, D, P(D)], I),
         "sim_adjoint_field": ([VP, I, VP, I], I),
         "sim_adjoint_end": ([VP], I),
-        "sim_batch_create": ([P(VP), I, VP, P(VP)], I),
+        "sim_batch_workspace_size": ([P(VP), I, P(SZ)], I),
+        "sim_batch_create": ([P(VP), I, VP, SZ, VP, P(VP)], I),
+        "sim_batch_query_launches": ([VP, P(D)], I),
         "sim_batch_step": ([VP, I], I),
         "sim_batch_sync": ([VP], I),
         "sim_batch_last_error": ([VP], ctypes.c_char_p),
@@ -117,7 +119,7 @@ def exported_symbols():
             "sim_poisson_solve", "sim_poisson_solve_noalloc", "sim_poisson_batch_workspace_size",
             "sim_poisson_solve_batch", "sim_objective", "sim_adjoint_workspace_size",
             "sim_adjoint_begin", "sim_adjoint_step", "sim_adjoint_field", "sim_adjoint_end",
-            "sim_batch_create", "sim_batch_step",
+            "sim_batch_workspace_size", "sim_batch_create", "sim_batch_query_launches", "sim_batch_step",
             "sim_batch_sync", "sim_batch_last_error", "sim_batch_destroy"]
 
 
@@ -410,18 +412,36 @@ class Batch:
     (sim_batch_* of the C ABI).  The Simulation objects stay owned by the
     caller and must outlive the batch."""
 
-    def __init__(self, sims, stream=None):
+    def __init__(self, sims, stream=None, batched_solves=True):
+        """batched_solves: same-grid members share one batched pressure solve
+        per stage (a torch workspace is allocated for it); False keeps every
+        member's own solves."""
         import torch
         self.lib = load()
         self.sims = list(sims)
         arr = (ctypes.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
         st = stream if stream is not None else self.sims[0].stream
         self.stream = st
+        self.workspace = None
+        ptr, nbytes = None, 0
+        if batched_solves:
+            sz = ctypes.c_size_t()
+            _check(self.lib, self.lib.sim_batch_workspace_size(arr, len(self.sims), ctypes.byref(sz)))
+            if sz.value > 0:
+                self.workspace = torch.empty(sz.value + 256, dtype=torch.uint8, device=self.sims[0].workspace.device)
+                ptr = (self.workspace.data_ptr() + 255) // 256 * 256
+                nbytes = sz.value
         h = ctypes.c_void_p()
-        _check(self.lib, self.lib.sim_batch_create(arr, len(self.sims), ctypes.c_void_p(st.cuda_stream),
-                                                   ctypes.byref(h)))
+        _check(self.lib, self.lib.sim_batch_create(arr, len(self.sims), ctypes.c_void_p(ptr), ctypes.c_size_t(nbytes),
+                                                   ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)))
         self.h = h
         self.torch = torch
+
+    def launches(self):
+        """Kernels launched by the last batch step (synchronises)."""
+        v = ctypes.c_double()
+        self._check(self.lib.sim_batch_query_launches(self.h, ctypes.byref(v)))
+        return v.value
 
     def _check(self, st):
         if st != SIM_OK:

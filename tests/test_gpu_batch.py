@@ -61,6 +61,63 @@ def test_batch_is_bitwise_equal_to_separate_steps(precision):
             assert np.array_equal(a.get(k), b.get(k)), k
 
 
+def _same_grid_flames(precision):
+    """Four flames on one 64x128 grid (one batched-solve group) with different
+    Re, Z_st and density ratio, and one 32x64 flame solved on its own."""
+    out = []
+    for (nx, ny), Re, zst, ratio in (((64, 128), 150.0, 0.05, 6.0), ((64, 128), 300.0, 0.07, 4.5),
+                                     ((64, 128), 220.0, 0.06, 7.5), ((32, 64), 120.0, 0.055, 7.0),
+                                     ((64, 128), 80.0, 0.045, 5.0)):
+        prm, geo, f = W.slot_burner(nx, ny, Re=Re, Z_st=zst, density_ratio=ratio, Da_ib=max(1e-4, (2.0 / nx) ** 2))
+        prm["precision"] = precision
+        prm["poisson_rtol"] = 1e-12
+        out.append((prm, geo, f))
+    return out
+
+
+@pytest.mark.parametrize("precision", [W.FP64, W.MIXED])
+def test_batched_solves_are_bitwise_equal_to_separate_steps(precision):
+    """Same-grid members share one batched pressure solve per stage; every
+    member must still get bitwise its own result."""
+    import torch
+    from paper_2603_01727_gb300.lowmach import Batch, SIM_Q_ITERS_PRED, SIM_Q_ITERS_CORR
+    flames = _same_grid_flames(precision)
+    stream = torch.cuda.Stream()
+    alone = _sims(flames, stream)
+    for s in alone:
+        s.step(9)
+        s.sync()
+    members = _sims(flames, stream)
+    batch = Batch(members, stream=stream)
+    assert batch.workspace is not None             # a batched-solve group exists
+    batch.step(4)
+    batch.step(5)
+    batch.sync()
+    assert batch.launches() > 0
+    for a, b in zip(alone, members):
+        for k in ["U", "V", "Z", "H", "T", "RHO", "P", "FX", "FY"]:
+            assert np.array_equal(a.get(k), b.get(k)), k
+        for q in (SIM_Q_ITERS_PRED, SIM_Q_ITERS_CORR):
+            assert a.query(q) == b.query(q)
+
+
+def test_batch_without_batched_solves_matches_batched():
+    import torch
+    from paper_2603_01727_gb300.lowmach import Batch
+    flames = _same_grid_flames(W.MIXED)
+    stream = torch.cuda.Stream()
+    out = []
+    for batched in (True, False):
+        members = _sims(flames, stream)
+        batch = Batch(members, stream=stream, batched_solves=batched)
+        batch.step(7)
+        batch.sync()
+        out.append([m.get("P") for m in members])
+        batch.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
 def test_batch_member_matches_oracle():
     import torch
     from paper_2603_01727_gb300.lowmach import Batch
