@@ -330,6 +330,29 @@ void ghost(sim_t* s, std::initializer_list<std::pair<double*, int>> fields, cuda
     launch_ghost(s->g, s->bnd, s->ph, job, st, L);
 }
 
+GhostJob job_of(sim_t* s, std::initializer_list<std::pair<double*, int>> fields) {
+    (void)s;
+    GhostJob job;
+    std::memset(&job, 0, sizeof(job));
+    for (auto& f : fields) {
+        job.f[job.nf] = f.first;
+        job.what[job.nf] = f.second;
+        ++job.nf;
+    }
+    return job;
+}
+
+GhostJob job_v(sim_t* s, double* const* v) {
+    GhostJob job;
+    std::memset(&job, 0, sizeof(job));
+    for (int d = 0; d < s->g.dim; ++d) {
+        job.f[d] = v[d];
+        job.what[d] = GW_V0 + d;
+    }
+    job.nf = s->g.dim;
+    return job;
+}
+
 void ghost_v(sim_t* s, double* const* v, cudaStream_t st, int* L) {
     GhostJob job;
     std::memset(&job, 0, sizeof(job));
@@ -532,11 +555,16 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
         a.w0 = 3.0; a.w1 = -4.0; a.w2 = 1.0; a.wden = 2.0 * dt;
     }
     a.iwden = (a.wden != 0.0) ? 1.0 / a.wden : 0.0;
+    // ghost cells of Z*, H*, kappa, v are filled by the kernels that write them
+    a.bnd = s->bnd;
+    a.gj = job_of(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}});
+    if (D == 3) a.gj.nf = 0;   // 3D: separate ghost fills (the 3D kernels run faster without)
     if (on(SEC_PRED)) {
         launch_residual(g, s->ph, a, st, L);
-        ghost(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}}, st, L);
-        launch_state(g, s->ph, s->Zs, s->Hs, s->T, r.rho_new, s->kap, s->sc, SC_P0_STAR, s->part, s->status, st, L);
-        ghost(s, {{s->kap, GW_KAPPA}}, st, L);
+        if (D == 3) ghost(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}}, st, L);
+        launch_state(g, s->ph, s->Zs, s->Hs, s->T, r.rho_new, s->kap, s->sc, SC_P0_STAR, s->part, s->status, st, L,
+                     &s->bnd, D == 2);
+        if (D == 3) ghost(s, {{s->kap, GW_KAPPA}}, st, L);
     }
 
     FluxArgs fa;
@@ -578,9 +606,12 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     pa.eA = s->eA;
     pa.eB = s->eB;
     pa.eC = s->eC;
+    pa.bnd = s->bnd;
+    pa.gj = job_v(s, s->vs);
+    if (D == 3) pa.gj.nf = 0;   // 3D: separate ghost fills (measured faster there)
     if (on(SEC_MID)) {
-        launch_project(g, pa, st, L);
-        ghost_v(s, s->vs, st, L);
+        launch_project(g, s->ph, pa, st, L);
+        if (D == 3) ghost_v(s, s->vs, st, L);
     }
     if (on(SEC_MID) && s->adj_save) {
         // predictor values read by the reverse pass (overwritten by the corrector)
@@ -626,21 +657,27 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
         c.w0 = 3.0; c.w1 = -4.0; c.w2 = 1.0; c.wden = 2.0 * dt;
     }
     c.iwden = 1.0 / c.wden;
+    c.bnd = s->bnd;
+    c.gj = job_of(s, {{s->Z, GW_Z}, {s->H, GW_H}});
+    if (D == 3) c.gj.nf = 0;
     fa.p0_slot = SC_P0_NEW;
     if (on(SEC_MID)) {
         launch_residual(g, s->ph, c, st, L);
-        ghost(s, {{s->Z, GW_Z}, {s->H, GW_H}}, st, L);
-        launch_state(g, s->ph, s->Z, s->H, s->T, r.rho_new, s->kap, s->sc, SC_P0_NEW, s->part, s->status, st, L);
-        ghost(s, {{s->kap, GW_KAPPA}}, st, L);
+        if (D == 3) ghost(s, {{s->Z, GW_Z}, {s->H, GW_H}}, st, L);
+        launch_state(g, s->ph, s->Z, s->H, s->T, r.rho_new, s->kap, s->sc, SC_P0_NEW, s->part, s->status, st, L,
+                     &s->bnd, D == 2);
+        if (D == 3) ghost(s, {{s->kap, GW_KAPPA}}, st, L);
         launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
     }
     if (on(SEC_POIS_CORR)) e = enqueue_poisson(s, st, graph, SC_ITERS_CORR, L, body);
     if (e != cudaSuccess) return e;
     for (int d = 0; d < D; ++d) pa.v[d] = s->v[d];
     pa.p0_slot = SC_P0_NEW;  // T^{n+1}, p0^{n+1}
+    pa.gj = job_v(s, s->v);
+    if (D == 3) pa.gj.nf = 0;
     if (on(SEC_END)) {
-        launch_project(g, pa, st, L);
-        ghost_v(s, s->v, st, L);
+        launch_project(g, s->ph, pa, st, L);
+        if (D == 3) ghost_v(s, s->v, st, L);
         launch_rotate_p0(s->sc, st, L);
     }
     return cudaGetLastError();
@@ -1064,7 +1101,7 @@ sim_status sim_time_kernel(sim_t* s, int kernel, int reps) {
                 pa.eA = s->eA;
                 pa.eB = s->eB;
                 pa.eC = s->eC;
-                launch_project(g, pa, s->stream, &L);
+                launch_project(g, s->ph, pa, s->stream, &L);
                 break;
             }
             case SIM_K_RESIDUAL_REV: {

@@ -10,6 +10,7 @@
 // Poisson right-hand side b are compact interior arrays.
 
 #include <cmath>
+#include <cstring>
 
 #include "step.cuh"
 
@@ -84,6 +85,61 @@ __global__ void k_ghost(Geom g, Phys ph, const uint8_t* __restrict__ klo, const 
 }
 
 // ----------------------------------------------------------------------------
+// Ghost fill fused into the kernel that produces a field: the thread that
+// writes interior cell c (padded coordinates q) also writes every ghost cell
+// whose value k_ghost's direction-by-direction fill (d = 0, 1, 2) would take
+// from c, composing the per-direction maps in the same order (a corner is the
+// d = 1 map of the d = 0 ghost).  Same formulas, so the same values.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double ghost_value(const Phys& ph, int what, int d, int kind, double adj) {
+    double dv;
+    if (what == GW_Z) dv = ph.inflow_Z;
+    else if (what == GW_H) dv = ph.inflow_H;
+    else if (what == GW_KAPPA) dv = ph.kappa_in;
+    else dv = ph.inflow_v[what - GW_V0];
+    const bool vel = what >= GW_V0;
+    const bool normal = vel && (what - GW_V0 == d);
+    if (kind == BC_INFLOW) return 2.0 * dv - adj;
+    if (kind == BC_OUTFLOW) return adj;
+    if (kind == BC_WALL) return vel ? -adj : adj;
+    return normal ? -adj : adj;   // BC_SLIP
+}
+
+// vals[f]: the value just written to job.f[f] at interior cell q.
+__device__ __forceinline__ void fill_ghosts_of(const Geom& g, const Phys& ph, const Bnd& bnd, const GhostJob& job,
+                                               const int q[3], const double* vals) {
+    int opt[3][3], nopt[3] = {1, 1, 1};
+    bool any = false;
+    for (int d = 0; d < 3; ++d) {
+        opt[d][0] = 0;
+        if (d >= g.dim) continue;
+        const int n = g.n[d];
+        const bool per = g.periodic[d];
+        if (per ? (q[d] == n) : (q[d] == 1)) opt[d][nopt[d]++] = 1;   // source of the low ghost
+        if (per ? (q[d] == 1) : (q[d] == n)) opt[d][nopt[d]++] = 2;   // source of the high ghost
+        any = any || nopt[d] > 1;
+    }
+    if (!any) return;
+    for (int i2 = 0; i2 < nopt[2]; ++i2)
+        for (int i1 = 0; i1 < nopt[1]; ++i1)
+            for (int i0 = 0; i0 < nopt[0]; ++i0) {
+                const int o[3] = {opt[0][i0], opt[1][i1], opt[2][i2]};
+                if (o[0] == 0 && o[1] == 0 && o[2] == 0) continue;
+                for (int f = 0; f < job.nf; ++f) {
+                    double v = vals[f];
+                    int qq[3] = {q[0], q[1], q[2]};
+                    for (int d = 0; d < g.dim; ++d) {
+                        if (o[d] == 0) continue;
+                        const int side = o[d] - 1;
+                        if (!g.periodic[d]) v = ghost_value(ph, job.what[f], d, bnd.kind[d][side][slab_index(g, d, qq)], v);
+                        qq[d] = side ? g.n[d] + 1 : 0;
+                    }
+                    job.f[f][(long long)qq[0] + (long long)qq[1] * g.s[1] + (long long)qq[2] * g.s[2]] = v;
+                }
+            }
+}
+
+// ----------------------------------------------------------------------------
 // Flame-sheet state relation (Eqs 3.41-3.42 with the level translation, 2.49,
 // 2.50) at the interior cells; block partials of sum(1/T) for Eq 2.40.
 // ----------------------------------------------------------------------------
@@ -137,7 +193,11 @@ __device__ __forceinline__ double kappa_mixed(const Phys& ph, double T) {
 template <bool MIXED>
 __global__ void k_state(Geom g, Phys ph, const double* __restrict__ Z, const double* __restrict__ H,
                         double* __restrict__ T, double* __restrict__ rho, double* __restrict__ kap,
-                        double* __restrict__ part, int* status, double* sc, int p0_slot) {
+                        double* __restrict__ part, int* status, double* sc, int p0_slot, Bnd bnd, int kap_ghosts) {
+    GhostJob kj;
+    kj.f[0] = kap;
+    kj.what[0] = GW_KAPPA;
+    kj.nf = 1;
     __shared__ double sm[NT / 32];
     double acc = 0.0;
     int bad = 0;
@@ -159,6 +219,11 @@ __global__ void k_state(Geom g, Phys ph, const double* __restrict__ Z, const dou
         }
         T[c] = Tv;
         kap[c] = kv;
+        if (kap_ghosts) {
+            int q[3];
+            padded_coords(g, c, q);
+            fill_ghosts_of(g, ph, bnd, kj, q, &kv);
+        }
         if (!ph.closed) rho[c] = iT;        // p0 = 1 (Eq 2.41), rho = p0 / T (Eq 2.49)
         acc += iT;
         if (!(Tv > 0.0) || !(Tv < 1e300)) bad = 1;
@@ -331,7 +396,7 @@ __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, con
 // the two blocks its uncapped register count allows.
 template <class C>
 struct ResidMinBlocks {
-    static constexpr int v = 1;
+    static constexpr int v = 2;
 };
 template <>
 struct ResidMinBlocks<FF> {
@@ -363,12 +428,13 @@ __global__ void __launch_bounds__(NT, ResidMinBlocks<C>::v) k_residual(Geom g, P
     // combination (FP64 state update)
     const double dt = a.dt;
     const double rb = a.rhob[c];
+    double zo, ho;
     if (a.mode == MODE_CORR) {
         const double hdt = 0.5 * dt;
 #pragma unroll
         for (int i = 0; i < DIM; ++i) a.mo[i][c] = fma(hdt, Rv[i] + Rrd[i][c], rb * a.vb[i][c]);
-        a.Zo[c] = fma(hdt, RZ + Rrd[3][c], a.Zb[c]);
-        a.Ho[c] = fma(hdt, RH + Rrd[4][c], a.Hb[c]);
+        zo = fma(hdt, RZ + Rrd[3][c], a.Zb[c]);
+        ho = fma(hdt, RH + Rrd[4][c], a.Hb[c]);
     } else {
         const bool ab2 = (a.mode == MODE_PRED_AB2);
 #pragma unroll
@@ -381,8 +447,16 @@ __global__ void __launch_bounds__(NT, ResidMinBlocks<C>::v) k_residual(Geom g, P
         const double cH = ab2 ? (1.5 * RH - 0.5 * Rrd[4][c]) : RH;
         Rst[3][c] = RZ;
         Rst[4][c] = RH;
-        a.Zo[c] = fma(dt, cZ, a.Zb[c]);
-        a.Ho[c] = fma(dt, cH, a.Hb[c]);
+        zo = fma(dt, cZ, a.Zb[c]);
+        ho = fma(dt, cH, a.Hb[c]);
+    }
+    a.Zo[c] = zo;
+    a.Ho[c] = ho;
+    if (DIM == 2 && a.gj.nf) {   // fused ghost fill of Z, H (2D: the 3D stencil runs out of registers)
+        int q[3];
+        padded_coords(g, c, q);
+        const double vals[2] = {zo, ho};
+        fill_ghosts_of(g, ph, a.bnd, a.gj, q, vals);
     }
 }
 
@@ -475,7 +549,8 @@ __global__ void k_rhs(Geom g, Bnd bnd, FluxArgs a, int np) {
 // (Eq 3.25) with P ghosts by quadratic extrapolation (Eqs 3.27-3.28).
 // ----------------------------------------------------------------------------
 template <int DIM>
-__global__ void k_project(Geom g, ProjArgs a) {
+__global__ void k_project(Geom g, Phys ph, ProjArgs a) {
+    double vout[3];
     const long long t = (long long)blockIdx.x * NT + threadIdx.x;
     if (t >= g.ncell) return;
     const long long c = pad_index(g, t);
@@ -498,7 +573,13 @@ __global__ void k_project(Geom g, ProjArgs a) {
         else Pp = a.eA * Pc + a.eB * a.P[t - st] + a.eC * a.P[t - 2 * st];
         if (ct[j] > 0 || g.periodic[j]) a.F[j][c] = a.F[j][c] - (Pc - Pm) * ih;
         if (ct[j] == n - 1 && g.periodic[j]) a.F[j][c + s] = a.F[j][c + s] - (Pp - Pc) * ih;
-        a.v[j][c] = (a.mom[j][c] - (Pp - Pm) * (0.5 * ih)) * irho;
+        vout[j] = (a.mom[j][c] - (Pp - Pm) * (0.5 * ih)) * irho;
+        a.v[j][c] = vout[j];
+    }
+    if (a.gj.nf) {   // fused ghost fill of v
+        int q[3];
+        padded_coords(g, c, q);
+        fill_ghosts_of(g, ph, a.bnd, a.gj, q, vout);
     }
 }
 
@@ -1405,12 +1486,16 @@ void launch_ghost(const Geom& g, const Bnd& bnd, const Phys& ph, const GhostJob&
 
 void launch_state(const Geom& g, const Phys& ph, const double* Z, const double* H, double* T, double* rho,
                   double* kap, double* sc, int p0_slot, double* part, int* status, cudaStream_t s,
-                  int* launches) {
+                  int* launches, const Bnd* bnd, bool kap_ghosts) {
     const int rb = reduce_grid(g);
+    Bnd b;
+    std::memset(&b, 0, sizeof(b));
+    if (bnd) b = *bnd;
+    const int kg = (bnd && kap_ghosts) ? 1 : 0;
     if (ph.mixed)
-        k_state<true><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, part, status, sc, p0_slot);
+        k_state<true><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, part, status, sc, p0_slot, b, kg);
     else
-        k_state<false><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, part, status, sc, p0_slot);
+        k_state<false><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, part, status, sc, p0_slot, b, kg);
     ++*launches;
     if (ph.closed) {
         k_density<<<rb, NT, 0, s>>>(g, T, rho, part, rb, sc, p0_slot, ph.mixed);
@@ -1450,11 +1535,11 @@ void launch_flux_rhs(const Geom& g, const Phys& ph, const Bnd& bnd, const FluxAr
     ++*launches;
 }
 
-void launch_project(const Geom& g, const ProjArgs& a, cudaStream_t s, int* launches) {
+void launch_project(const Geom& g, const Phys& ph, const ProjArgs& a, cudaStream_t s, int* launches) {
     if (g.dim == 3)
-        k_project<3><<<blocks_for(g.ncell), NT, 0, s>>>(g, a);
+        k_project<3><<<blocks_for(g.ncell), NT, 0, s>>>(g, ph, a);
     else
-        k_project<2><<<blocks_for(g.ncell), NT, 0, s>>>(g, a);
+        k_project<2><<<blocks_for(g.ncell), NT, 0, s>>>(g, ph, a);
     ++*launches;
 }
 

@@ -58,6 +58,8 @@ struct ResidArgs {
     double* mo[3];
     const uint8_t* chi;
     const double* vib[3];
+    Bnd bnd;                 // boundary kinds for the fused ghost fill of Zo, Ho
+    GhostJob gj;             // {Zo, Ho} to ghost-fill in the kernel (nf = 0: none)
     double Z_ib, H_ib, inv_Da;
     int ibm;
     const double* sc;
@@ -93,6 +95,8 @@ struct ProjArgs {
     int p0_slot;
     double* v[3];
     double eA, eB, eC;       // quadratic extrapolation coefficients (Eq 3.28)
+    Bnd bnd;                 // boundary kinds for the fused ghost fill of v
+    GhostJob gj;             // v components to ghost-fill in the kernel (nf = 0: none)
 };
 
 // Fields read by the stage stencil, by loader id.
@@ -154,13 +158,14 @@ struct CombAdj {
 };
 void launch_ghost(const Geom& g, const Bnd& bnd, const Phys& ph, const GhostJob& job, cudaStream_t s,
                   int* launches);
+// bnd / kap_ghosts (optional): ghost-fill kappa in the same kernel.
 void launch_state(const Geom& g, const Phys& ph, const double* Z, const double* H, double* T,
                   double* rho, double* kap, double* sc, int p0_slot, double* part, int* status,
-                  cudaStream_t s, int* launches);
+                  cudaStream_t s, int* launches, const Bnd* bnd = nullptr, bool kap_ghosts = false);
 void launch_residual(const Geom& g, const Phys& ph, const ResidArgs& a, cudaStream_t s, int* launches);
 void launch_flux_rhs(const Geom& g, const Phys& ph, const Bnd& bnd, const FluxArgs& a, cudaStream_t s,
                      int* launches);
-void launch_project(const Geom& g, const ProjArgs& a, cudaStream_t s, int* launches);
+void launch_project(const Geom& g, const Phys& ph, const ProjArgs& a, cudaStream_t s, int* launches);
 void launch_momentum(const Geom& g, const double* rho, double* const v[3], double* mom[3], cudaStream_t s,
                      int* launches);
 void launch_sum(const Geom& g, const double* x, double* part, cudaStream_t s, int* launches);
