@@ -104,6 +104,13 @@ struct sim {
     AdjWs adj;
     bool adj_active;
     bool adj_save;         // the eager step copies its predictor values into adj
+    // Adjoint steps run their pressure solves (recompute: predictor,
+    // corrector; transpose: lambda_P -> lambda_b) as captured one-solve
+    // graphs instead of the host-driven loop.
+    bool solve_graphs;
+    cudaGraphExec_t solve_exec[3];
+    bool solve_valid[3];
+    int solve_fixed[3], solve_body[3];   // kernels of a solve graph outside / per loop iteration
 
     char err[512];
 };
@@ -439,12 +446,55 @@ cudaError_t capture_while_solve(PoissonPlan* pl, const double* b, double* x, cud
     return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
 }
 
+// One solve as its own graph (prologue, while node, epilogue), captured once
+// on the simulation's capture stream: 0 and 1 the step's predictor and
+// corrector solves (b -> P), 2 the adjoint's transposed solve.
+sim_status launch_solve_graph(sim_t* s, int which, cudaStream_t st) {
+    if (!s->solve_valid[which]) {
+        PoissonPlan* pl = &s->pp;
+        const double* b = which == 2 ? s->adj.LP : s->b;
+        double* x = which == 2 ? s->adj.Lb : s->P;
+        double* rep = which == 2 ? s->adj.rep : s->sc + (which == 0 ? SC_ITERS_PRED : SC_ITERS_CORR);
+        CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeRelaxed));
+        int body = 0;
+        pl->launches = 0;
+        cudaError_t e = capture_while_solve(pl, b, x, s->cap, s->side, &body);
+        if (e == cudaSuccess) e = poisson_enqueue_epilogue(pl, x, s->cap, rep, s->status, ST_NOCONV);
+        s->solve_body[which] = body;
+        s->solve_fixed[which] = pl->launches - body;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s->cap, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(s, SIM_ECUDA, "solve graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&s->solve_exec[which], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(s, SIM_ECUDA, "solve graph instantiate: %s", cudaGetErrorString(e));
+        s->solve_valid[which] = true;
+    }
+    CK(cudaGraphLaunch(s->solve_exec[which], st));
+    return SIM_OK;
+}
+
+void drop_solve_graphs(sim_t* s) {
+    for (int k = 0; k < 3; ++k)
+        if (s->solve_valid[k]) {
+            cudaGraphExecDestroy(s->solve_exec[k]);
+            s->solve_valid[k] = false;
+        }
+}
+
 // Pressure solve of one stage; graph mode adds a conditional while node whose
 // condition the prologue and every iteration set on the device.
 cudaError_t enqueue_poisson(sim_t* s, cudaStream_t st, bool graph, int iter_slot, int* L, int* body_launch) {
     PoissonPlan* pl = &s->pp;
     pl->launches = 0;
     cudaError_t e;
+    if (!graph && s->solve_graphs) {
+        const sim_status ss = launch_solve_graph(s, iter_slot == SC_ITERS_PRED ? 0 : 1, st);
+        return ss == SIM_OK ? cudaGetLastError() : cudaErrorUnknown;
+    }
     if (!graph) {
         e = poisson_enqueue_prologue(pl, s->b, s->P, st, 0ULL);
         if (e != cudaSuccess) return e;
@@ -1225,6 +1275,7 @@ const char* sim_last_error(const sim_t* s) { return s ? s->err : "null handle"; 
 
 void sim_destroy(sim_t* s) {
     if (!s) return;
+    drop_solve_graphs(s);
     for (int k = 0; k < 6; ++k)
         if (s->gvalid[k]) cudaGraphExecDestroy(s->gexec[k]);
     if (s->cap) cudaStreamDestroy(s->cap);
@@ -1371,6 +1422,8 @@ void adj_ghost_v(sim_t* s, double* const* lv, cudaStream_t st) {
 // mean, A the symmetric compact Laplacian), a symmetric operator: its
 // transpose is the same solve applied to lambda_P.
 cudaError_t adj_poisson(sim_t* s, const double* lP, double* lb, cudaStream_t st) {
+    if (s->solve_graphs && lP == s->adj.LP && lb == s->adj.Lb)
+        return launch_solve_graph(s, 2, st) == SIM_OK ? cudaGetLastError() : cudaErrorUnknown;
     PoissonPlan* pl = &s->pp;
     cudaError_t e = poisson_enqueue_prologue(pl, lP, lb, st, 0ULL);
     if (e != cudaSuccess) return e;
@@ -1455,12 +1508,16 @@ sim_status sim_adjoint_begin(sim_t* s, void* d_workspace, size_t workspace_bytes
     CK(cudaMemsetAsync(s->adj.lam_base, 0, s->adj.lam_bytes, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->adj_active = true;
+    drop_solve_graphs(s);        // captured against the previous adjoint workspace
+    s->solve_graphs = true;
     return SIM_OK;
 }
 
 sim_status sim_adjoint_end(sim_t* s) {
     if (!s) return SIM_EINVAL;
     s->adj_active = false;
+    s->solve_graphs = false;
+    drop_solve_graphs(s);
     std::memset(&s->adj, 0, sizeof(s->adj));
     return SIM_OK;
 }
@@ -1541,7 +1598,7 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
         // pressure solve^T
         s->pp.launches = 0;
         CK(adj_poisson(s, A.LP, A.Lb, st));
-        La += D + 1 + s->pp.launches;
+        La += D + 1 + (s->solve_graphs ? 0 : s->pp.launches);
         // face fluxes and right-hand side^T
         FluxAdj fa;
         std::memset(&fa, 0, sizeof(fa));
@@ -1619,7 +1676,19 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
         s->launches_last += 2;
         CK(cudaMemcpyAsync(dJ_dprofile, A.grad, sizeof(double) * s->ibm.n_profile, cudaMemcpyDeviceToHost, st));
     }
-    return check_device_status(s);
+    const sim_status st_dev = check_device_status(s);
+    if (st_dev != SIM_OK) return st_dev;
+    if (s->solve_graphs) {
+        // kernels of the graph-launched solves: their loops ran as many times as
+        // the reported iterations (the last transposed solve's count for both)
+        double it[4] = {0.0, 0.0, 0.0, 0.0};
+        CK(cudaMemcpy(&it[0], s->sc + SC_ITERS_PRED, sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&it[1], s->sc + SC_ITERS_CORR, sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&it[2], A.rep, sizeof(double), cudaMemcpyDeviceToHost));
+        s->launches_last += s->solve_fixed[0] + (int)(s->solve_body[0] * it[0]) + s->solve_fixed[1] +
+                            (int)(s->solve_body[1] * it[1]) + 2 * (s->solve_fixed[2] + (int)(s->solve_body[2] * it[2]));
+    }
+    return SIM_OK;
 }
 
 // Adjoint of a state field at the current level, interior cells (or faces)
