@@ -1576,22 +1576,43 @@ __device__ __forceinline__ T off3(const LvT<T>& L, const Pl<T>* su, int sm, int 
     return off;
 }
 
+// Per-block axis data of the box: the two columns a lane can take in a colour
+// sweep (2 (lane & 15) and that + 1), and every row (shared), each as
+// class | valid << 2 (valid: inside the domain or periodic).
+struct BoxAxes {
+    int col[2];
+};
+__device__ __forceinline__ int axis_code(int g, int n, int per) {
+    const Ax a = axis(g, n, per);
+    return a.cls | ((int)a.valid << 2);
+}
+template <class T>
+__device__ __forceinline__ BoxAxes box_axes(const LvT<T>& L, int ox, int oy, int* srow) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < SB) srow[threadIdx.x] = axis_code(oy + (int)threadIdx.x, L.n[1], L.per[1]);
+    BoxAxes b;
+    b.col[0] = axis_code(ox + 2 * (lane & 15), L.n[0], L.per[0]);
+    b.col[1] = axis_code(ox + 2 * (lane & 15) + 1, L.n[0], L.per[0]);
+    return b;   // srow is read after the caller's next barrier
+}
+
 // One colour on plane z (ring slot z & 3) over rows [r0, r1] x columns [c0, c1].
 template <class T>
 __device__ __forceinline__ void color_plane(const LvT<T>& L, Pl<T>* su, const Pl<T>* sf, int ox, int oy, int z,
-                                            int zcls, int color, int r0, int r1, int c0, int c1) {
+                                            int zcls, int color, int r0, int r1, int c0, int c1, const BoxAxes& ba,
+                                            const int* srow) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int par = (ox + oy + z) & 1;
     const int s0 = z & 3, sm = (z - 1) & 3, sp = (z + 1) & 3;
     const int npairs = (r1 - r0 + 2) / 2;
     for (int rp = warp; rp < npairs; rp += NW) {
         const int r = r0 + 2 * rp + (lane >> 4);
-        const int c = 2 * (lane & 15) + ((color - par - r) & 1);
+        const int odd = (color - par - r) & 1;
+        const int c = 2 * (lane & 15) + odd;
         if (r > r1 || c < c0 || c > c1) continue;
-        const Ax ax = axis(ox + c, L.n[0], L.per[0]);
-        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
-        if (!(ax.valid && ay.valid)) continue;
-        su[s0][r][c] = (sf[s0][r][c] + off3<T>(L, su, sm, s0, sp, r, c)) * L.invd[ax.cls + 3 * ay.cls + 9 * zcls];
+        const int cx = ba.col[odd], cy = srow[r];
+        if (!((cx & cy) & 4)) continue;
+        su[s0][r][c] = (sf[s0][r][c] + off3<T>(L, su, sm, s0, sp, r, c)) * L.invd[(cx & 3) + 3 * (cy & 3) + 9 * zcls];
     }
 }
 
@@ -1619,6 +1640,28 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
 #pragma unroll
     for (int k = 0; k < 2; ++k) ay[k] = axis(oy + warp + NW * k, ny, L.per[1]);
     const bool colo = ax.in && lane >= H && lane < H + FD;
+    __shared__ int srow[SB];
+    const BoxAxes ba = box_axes<T>(L, ox, oy, srow);
+    // restriction weights of this thread's coarse cell (fixed across planes)
+    const int rcx = threadIdx.x % CD, rcy = threadIdx.x / CD;
+    const int rI = blockIdx.x * CD + rcx, rJ = blockIdx.y * CD + rcy;
+    const bool rown = threadIdx.x < CD * CD && rI < C.n[0] && rJ < C.n[1];
+    T wxr[4], wyr[4];
+#pragma unroll
+    for (int a4 = 0; a4 < 4; ++a4) {
+        wxr[a4] = (T)rweight(a4, rI, C.n[0], C.per[0]);
+        wyr[a4] = (T)rweight(a4, rJ, C.n[1], C.per[1]);
+    }
+    // the next plane's f is loaded one step ahead (its DRAM latency overlaps
+    // the current plane's sweeps)
+    TF fpre[2];
+    auto load_f = [&](int qz) {
+        const Ax az = axis(qz, nz, L.per[2]);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            fpre[k] = (ax.valid && ay[k].valid && az.valid) ? f[ax.gw + (long long)nx * ay[k].gw + nxy * az.gw] : (TF)0;
+    };
+    load_f(zs);
 
     for (int q = zs; q <= ze; ++q) {
         // (a) f and the red cells of u (from a zero guess) on plane q
@@ -1630,20 +1673,21 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
                 const int r = warp + NW * k;
                 T fv = (T)0, uv = (T)0;
                 if (ax.valid && ay[k].valid && az.valid) {
-                    fv = (T)f[ax.gw + (long long)nx * ay[k].gw + nxy * az.gw];
+                    fv = (T)fpre[k];
                     if (((ox + lane + oy + r + q) & 1) == 0) uv = fv * L.invd[ax.cls + 3 * ay[k].cls + 9 * az.cls];
                 }
                 sF[sl][r][lane] = fv;
                 sU[sl][r][lane] = uv;
             }
         }
+        if (q < ze) load_f(q + 1);
         __syncthreads();
         // (b) black on plane q-1, box minus one layer
         {
             const int z = q - 1;
             if (z >= zs + 1 && z <= ze - 1) {
                 const Ax az = axis(z, nz, L.per[2]);
-                if (az.valid) color_plane<T>(L, sU, sF, ox, oy, z, az.cls, 1, 1, SB - 2, 1, SB - 2);
+                if (az.valid) color_plane<T>(L, sU, sF, ox, oy, z, az.cls, 1, 1, SB - 2, 1, SB - 2, ba, srow);
             }
         }
         __syncthreads();
@@ -1670,30 +1714,23 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
         __syncthreads();
         // (d) restriction of coarse plane K = (pr - 2) / 2 once its fine planes
         // 2K-1 .. 2K+2 are in the residual ring
-        if (pr >= 2 * K0 + 2 && pr <= 2 * K1 && ((pr & 1) == 0)) {
+        if (pr >= 2 * K0 + 2 && pr <= 2 * K1 && ((pr & 1) == 0) && rown) {
             const int K = (pr - 2) / 2;
-            for (int c = threadIdx.x; c < CD * CD; c += NT) {
-                const int cx = c % CD, cy = c / CD;
-                const int I = blockIdx.x * CD + cx, J = blockIdx.y * CD + cy;
-                if (I >= C.n[0] || J >= C.n[1]) continue;
-                T acc = (T)0;
-                for (int az = 0; az < 4; ++az) {
-                    const T wz = (T)rweight(az, K, C.n[2], C.per[2]);
-                    if (wz == (T)0) continue;
-                    const int sl = (2 * K - 1 + az) & 3;
-                    for (int ayy = 0; ayy < 4; ++ayy) {
-                        const T wy = (T)rweight(ayy, J, C.n[1], C.per[1]);
-                        if (wy == (T)0) continue;
-                        const int r = 2 * cy + H - 1 + ayy;
-                        T row = (T)0;
+            T acc = (T)0;
 #pragma unroll
-                        for (int axx = 0; axx < 4; ++axx)
-                            row += (T)rweight(axx, I, C.n[0], C.per[0]) * sR[sl][r][2 * cx + H - 1 + axx];
-                        acc += wz * wy * row;
-                    }
+            for (int az = 0; az < 4; ++az) {
+                const T wz = (T)rweight(az, K, C.n[2], C.per[2]);
+                const int sl = (2 * K - 1 + az) & 3;
+#pragma unroll
+                for (int ayy = 0; ayy < 4; ++ayy) {
+                    const int r = 2 * rcy + H - 1 + ayy;
+                    T row = (T)0;
+#pragma unroll
+                    for (int axx = 0; axx < 4; ++axx) row += wxr[axx] * sR[sl][r][2 * rcx + H - 1 + axx];
+                    acc += wz * wyr[ayy] * row;
                 }
-                fc[I + C.n[0] * (J + (long long)C.n[1] * K)] = acc * (T)0.125;
             }
+            fc[rI + C.n[0] * (rJ + (long long)C.n[1] * K)] = acc * (T)0.125;
         }
     }
 }
@@ -1721,7 +1758,23 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
     for (int k = 0; k < 2; ++k) ay[k] = axis(oy + warp + NW * k, ny, L.per[1]);
     const bool colo = ax.in && lane >= H && lane < H + FU;
+    __shared__ int srow[SB];
+    const BoxAxes ba = box_axes<T>(L, ox, oy, srow);
     TF rz = (TF)0, sz = (TF)0;
+    // the next plane's f and u_pre are loaded one step ahead
+    TF fpre[2];
+    T upre_n[2];
+    auto load_fu = [&](int qz) {
+        const Ax az = axis(qz, nz, L.per[2]);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const bool v = ax.valid && ay[k].valid && az.valid;
+            const long long g = ax.gw + (long long)nx * ay[k].gw + nxy * az.gw;
+            fpre[k] = v ? f[g] : (TF)0;
+            upre_n[k] = v ? upre[g] : (T)0;
+        }
+    };
+    load_fu(z0 - 2);
 
     for (int q = z0 - 2; q <= z1 + 1; ++q) {
         // (a) f and u = u_pre + P u_coarse on plane q
@@ -1733,22 +1786,22 @@ __global__ void __launch_bounds__(NT)
                 const int r = warp + NW * k;
                 T fv = (T)0, uv = (T)0;
                 if (ax.valid && ay[k].valid && az.valid) {
-                    const long long g = ax.gw + (long long)nx * ay[k].gw + nxy * az.gw;
-                    fv = (T)f[g];
+                    fv = (T)fpre[k];
                     const int gw[3] = {ax.gw, ay[k].gw, az.gw};
-                    uv = upre[g] + prolong_at<T, 3>(C, uc, gw);
+                    uv = upre_n[k] + prolong_at<T, 3>(C, uc, gw);
                 }
                 sF[sl][r][lane] = fv;
                 sU[sl][r][lane] = uv;
             }
         }
+        if (q < z1 + 1) load_fu(q + 1);
         __syncthreads();
         // (b) black on plane q-1, box minus one layer
         {
             const int z = q - 1;
             if (z >= z0 - 1 && z <= z1) {
                 const Ax az = axis(z, nz, L.per[2]);
-                if (az.valid) color_plane<T>(L, sU, sF, ox, oy, z, az.cls, 1, 1, SB - 2, 1, SB - 2);
+                if (az.valid) color_plane<T>(L, sU, sF, ox, oy, z, az.cls, 1, 1, SB - 2, 1, SB - 2, ba, srow);
             }
         }
         __syncthreads();
@@ -1757,7 +1810,7 @@ __global__ void __launch_bounds__(NT)
             const int z = q - 2;
             if (z >= z0 && z < z1) {
                 const Ax az = axis(z, nz, L.per[2]);
-                if (az.valid) color_plane<T>(L, sU, sF, ox, oy, z, az.cls, 0, H, SB - 1 - H, H, SB - 1 - H);
+                if (az.valid) color_plane<T>(L, sU, sF, ox, oy, z, az.cls, 0, H, SB - 1 - H, H, SB - 1 - H, ba, srow);
             }
         }
         __syncthreads();
@@ -1832,6 +1885,20 @@ __global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p
     for (int k = 0; k < 2; ++k) ay[k] = axis(oy + warp + NW * k, ny, L.per[1]);
     const bool colo = ax.in && lane >= H && lane < H + FP;
     V acc = (V)0;
+    // the next plane's z and p_old are loaded one step ahead
+    T zpre[2];
+    V ppre[2];
+    auto load_zp = [&](int qz) {
+        const Ax az = axis(qz, nz, L.per[2]);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const bool v = ax.valid && ay[k].valid && az.valid;
+            const long long g = ax.gw + (long long)nx * ay[k].gw + nxy * az.gw;
+            zpre[k] = v ? z[g] : (T)0;
+            ppre[k] = (v && it > 0) ? pold[g] : (V)0;
+        }
+    };
+    load_zp(z0 - 1);
     for (int qq = z0 - 1; qq <= z1; ++qq) {
         {
             const Ax az = axis(qq, nz, L.per[2]);
@@ -1841,13 +1908,13 @@ __global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p
                 const int r = warp + NW * k;
                 V pv = (V)0;
                 if (ax.valid && ay[k].valid && az.valid) {
-                    const long long g = ax.gw + (long long)nx * ay[k].gw + nxy * az.gw;
-                    pv = (V)z[g] - mz;
-                    if (it > 0) pv = fma(beta, pold[g], pv);
+                    pv = (V)zpre[k] - mz;
+                    if (it > 0) pv = fma(beta, ppre[k], pv);
                 }
                 sP[sl][r][lane] = pv;
             }
         }
+        if (qq < z1) load_zp(qq + 1);
         __syncthreads();
         const int zc = qq - 1;
         if (zc >= z0 && zc < z1) {
