@@ -468,6 +468,7 @@ template <int DIM>
 __global__ void k_face_flux(Geom g, Phys ph, Bnd bnd, FluxArgs a) {
     __shared__ double sm[NT / 32];
     const double rho_in = ph.incompressible ? 1.0 : a.sc[a.p0_slot] / ph.rho_in_T;
+    const double iden = 1.0 / a.bdf_den;     // once per thread: FP64 division is a long sequence
     double acc = 0.0;
     for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
         const long long c = pad_index(g, t);
@@ -476,7 +477,7 @@ __global__ void k_face_flux(Geom g, Phys ph, Bnd bnd, FluxArgs a) {
         padded_coords(g, c, q);
         if (a.correct) {
             const double drho = (a.bdf_c0 * a.rho_new[c] + a.bdf_c1 * a.rho_n[c] +
-                                 (a.bdf_c2 != 0.0 ? a.bdf_c2 * a.rho_prev[c] : 0.0)) / a.bdf_den;
+                                 (a.bdf_c2 != 0.0 ? a.bdf_c2 * a.rho_prev[c] : 0.0)) * iden;
             const double Sm = a.Sm ? a.Sm[c] : 0.0;
             acc += (drho - Sm) * g.dV;
         }
@@ -520,13 +521,14 @@ __global__ void k_rhs(Geom g, Bnd bnd, FluxArgs a, int np) {
     const double total = sum_partials<NT>(a.part, np, sm);
     const double area = a.sc[SC_OUT_AREA];
     const double shift = (area > 0.0) ? -total / area : 0.0;
+    const double iden = 1.0 / a.bdf_den;
     for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
         const long long c = pad_index(g, t);
         int ct[3], q[3];
         interior_coords(g, t, ct);
         padded_coords(g, c, q);
         const double drho = (a.bdf_c0 * a.rho_new[c] + a.bdf_c1 * a.rho_n[c] +
-                             (a.bdf_c2 != 0.0 ? a.bdf_c2 * a.rho_prev[c] : 0.0)) / a.bdf_den;
+                             (a.bdf_c2 != 0.0 ? a.bdf_c2 * a.rho_prev[c] : 0.0)) * iden;
         const double Sm = a.Sm ? a.Sm[c] : 0.0;
         double b = drho - Sm;
 #pragma unroll
