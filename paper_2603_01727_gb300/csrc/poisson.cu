@@ -1063,20 +1063,39 @@ __device__ __forceinline__ T off2(const LvT<T>& L, T (*su)[32], int r, int c) {
     return L.w[0] * (su[r][c - 1] + su[r][c + 1]) + L.w[1] * (su[r - 1][c] + su[r + 1][c]);
 }
 
+// Per-block axis codes (class | valid << 2) of the two columns a lane can take
+// in a colour sweep (2 (lane & 15) and that + 1) and of every row (shared).
+__device__ __forceinline__ int axis_code2(int g, int n, int per) {
+    const Ax a = axis(g, n, per);
+    return a.cls | ((int)a.valid << 2);
+}
+struct ColCodes {
+    int c[2];
+};
+template <class T>
+__device__ __forceinline__ ColCodes box_codes(const LvT<T>& L, int ox, int oy, int* srow) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < SY) srow[threadIdx.x] = axis_code2(oy + (int)threadIdx.x, L.n[1], L.per[1]);
+    ColCodes cc;
+    cc.c[0] = axis_code2(ox + 2 * (lane & 15), L.n[0], L.per[0]);
+    cc.c[1] = axis_code2(ox + 2 * (lane & 15) + 1, L.n[0], L.per[0]);
+    return cc;   // srow is read after the caller's next barrier
+}
+
 // One colour on rows [r0, r1] x columns [c0, c1] of the box.
 template <class T>
-__device__ __forceinline__ void color_sweep(const LvT<T>& L, T (*su)[32], T (*sf)[32], int ox, int oy, int par0,
-                                            int color, int r0, int r1, int c0, int c1) {
+__device__ __forceinline__ void color_sweep(const LvT<T>& L, T (*su)[32], T (*sf)[32], int par0, int color, int r0,
+                                            int r1, int c0, int c1, const ColCodes& cc, const int* srow) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int npairs = (r1 - r0 + 2) / 2;
     for (int rp = warp; rp < npairs; rp += NW) {
         const int r = r0 + 2 * rp + (lane >> 4);
-        const int c = 2 * (lane & 15) + ((color - par0 - r) & 1);
+        const int odd = (color - par0 - r) & 1;
+        const int c = 2 * (lane & 15) + odd;
         if (r > r1 || c < c0 || c > c1) continue;
-        const Ax ax = axis(ox + c, L.n[0], L.per[0]);
-        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
-        if (!(ax.valid && ay.valid)) continue;
-        su[r][c] = (sf[r][c] + off2<T>(L, su, r, c)) * L.invd[ax.cls + 3 * ay.cls];
+        const int cx = cc.c[odd], cy = srow[r];
+        if (!((cx & cy) & 4)) continue;
+        su[r][c] = (sf[r][c] + off2<T>(L, su, r, c)) * L.invd[(cx & 3) + 3 * (cy & 3)];
     }
 }
 
@@ -1099,6 +1118,8 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
     const int nx = L.n[0];
     const int par0 = (ox + oy) & 1;
     const Ax ax = axis(ox + lane, nx, L.per[0]);
+    __shared__ int srow[SY];
+    const ColCodes cc = box_codes<T>(L, ox, oy, srow);
 #pragma unroll
     for (int k = 0; k < SY / NW; ++k) {
         const int r = warp + NW * k;
@@ -1116,7 +1137,7 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
     // the box minus k layers
 #pragma unroll
     for (int k = 1; k < 2 * NS; ++k) {
-        color_sweep<T>(L, su, sf, ox, oy, par0, k & 1, k, SY - 1 - k, k, 31 - k);
+        color_sweep<T>(L, su, sf, par0, k & 1, k, SY - 1 - k, k, 31 - k, cc, srow);
         __syncthreads();
     }
     // residual on the box minus 2 NS layers (overwrites f); store the tile's u
@@ -1182,6 +1203,8 @@ __global__ void __launch_bounds__(NT)
     const int nx = L.n[0];
     const int par0 = (ox + oy) & 1;
     const Ax ax = axis(ox + lane, nx, L.per[0]);
+    __shared__ int srow[SY];
+    const ColCodes cc = box_codes<T>(L, ox, oy, srow);
     // coarse columns of this lane's fine column (bilinear prolongation)
     int I0 = 0, I1 = 0;
     if (ax.valid) pro_pair(ax.gw, C.n[0], C.per[0], &I0, &I1);
@@ -1208,7 +1231,7 @@ __global__ void __launch_bounds__(NT)
     // last (red) sweep covers exactly the tile
 #pragma unroll
     for (int k = 1; k <= 2 * NS; ++k) {
-        color_sweep<T>(L, su, sf, ox, oy, par0, k & 1, k, SY - 1 - k, k, 31 - k);
+        color_sweep<T>(L, su, sf, par0, k & 1, k, SY - 1 - k, k, 31 - k, cc, srow);
         __syncthreads();
     }
     TF rz = (TF)0, sz = (TF)0;    // FP64 path: double; refinement mode: FP32
