@@ -1497,29 +1497,29 @@ __global__ void __launch_bounds__(TT) tail(const LvT<T>* __restrict__ levs, Tail
 // four small dense products in shared memory.  F, u: ny rows of nx values.
 constexpr int FT = 256;            // threads of the fast-diagonalisation block
 
-// C[M x N] = L[M x K] R[K x N] (row-major, leading dimensions K and N), each
-// thread a 2 x 4 tile: per k two scalar loads of L (shared by the threads of a
-// tile row) and one float4 load of R; optionally C .*= S.  N % 4 == 0, M even.
-__device__ __forceinline__ void mm24(float* __restrict__ C, const float* __restrict__ L, const float* __restrict__ R,
-                                     int M, int N, int K, const float* __restrict__ S) {
+// C[M x N] = LT^T R with LT[K x M] (leading dimension ldl) and R[K x N]
+// (leading dimension N), row-major; each thread a 2 x 4 tile: per k one float2
+// load of LT and one float4 load of R (no bank conflicts: a warp's float2 loads
+// fall on at most four consecutive pairs); optionally C .*= S.  The sum over k
+// runs in ascending order with one fmaf per term.  N % 4 == 0, M even.
+__device__ __forceinline__ void mmT(float* __restrict__ C, const float* __restrict__ LT, int ldl,
+                                    const float* __restrict__ R, int M, int N, int K, const float* __restrict__ S) {
     const int tn = N / 4;
     for (int tile = threadIdx.x; tile < (M / 2) * tn; tile += FT) {
         const int m0 = 2 * (tile / tn), n0 = 4 * (tile % tn);
-        const float* l0 = L + m0 * K;
-        const float* l1 = l0 + K;
         float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
-#pragma unroll 4
+#pragma unroll 8
         for (int k = 0; k < K; ++k) {
+            const float2 a = *reinterpret_cast<const float2*>(LT + k * ldl + m0);
             const float4 r = *reinterpret_cast<const float4*>(R + k * N + n0);
-            const float a0 = l0[k], a1 = l1[k];
-            c0.x = fmaf(a0, r.x, c0.x);
-            c0.y = fmaf(a0, r.y, c0.y);
-            c0.z = fmaf(a0, r.z, c0.z);
-            c0.w = fmaf(a0, r.w, c0.w);
-            c1.x = fmaf(a1, r.x, c1.x);
-            c1.y = fmaf(a1, r.y, c1.y);
-            c1.z = fmaf(a1, r.z, c1.z);
-            c1.w = fmaf(a1, r.w, c1.w);
+            c0.x = fmaf(a.x, r.x, c0.x);
+            c0.y = fmaf(a.x, r.y, c0.y);
+            c0.z = fmaf(a.x, r.z, c0.z);
+            c0.w = fmaf(a.x, r.w, c0.w);
+            c1.x = fmaf(a.y, r.x, c1.x);
+            c1.y = fmaf(a.y, r.y, c1.y);
+            c1.z = fmaf(a.y, r.z, c1.z);
+            c1.w = fmaf(a.y, r.w, c1.w);
         }
         if (S) {
             const float4 s0 = *reinterpret_cast<const float4*>(S + m0 * N + n0);
@@ -1532,37 +1532,62 @@ __device__ __forceinline__ void mm24(float* __restrict__ C, const float* __restr
     }
 }
 
+// Asynchronous global -> shared copies (no registers held while in flight).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__host__ __device__ constexpr int fdm_ldf(int ny) { return ny + 2; }   // row stride of F^T in shared (2-way store conflicts)
+__host__ __device__ constexpr long long fdm_smem_floats(long long nx, long long ny) {
+    return 2 * nx * nx + 2 * ny * ny + nx * ny + nx * fdm_ldf((int)ny) + nx * ny;
+}
+
 // Shared-memory layout (floats): Sx, SxT (nx*nx each), Sy, SyT (ny*ny each),
-// IL, A, B (nx*ny each); the global table holds Sx, SxT, Sy, SyT, IL in that
-// order and is copied linearly.
+// IL (ny*nx) -- the global table, copied linearly -- then X (nx rows of
+// ny + 2) and Y (nx*ny).  With C = LT^T R the four products are
+//   Y = F Sx                   (LT = F^T in X, R = Sx)
+//   X = (Sy^T Y) .* IL         (LT = Sy,       R = Y)
+//   Y = (Sy X)^T = X^T Sy^T    (LT = X,        R = SyT)
+//   u = Y^T Sx^T               (LT = Y,        R = SxT), written straight to global;
+// fdm_smem_floats is the total.
+// The table does not depend on the previous kernel, so its copy is issued
+// before the programmatic-dependency wait.
 __global__ void __launch_bounds__(FT) fdm(int nx, int ny, const float* __restrict__ tab, const float* __restrict__ f,
                                           float* __restrict__ u) {
-    pdl_wait();
-    pdl_trigger();
-    f += (long long)blockIdx.x * nx * ny;   // system of a batch (one block each)
-    u += (long long)blockIdx.x * nx * ny;
     extern __shared__ __align__(16) unsigned char smraw[];
     float* Sx = reinterpret_cast<float*>(smraw);
     float* SxT = Sx + nx * nx;
     float* Sy = SxT + nx * nx;
     float* SyT = Sy + ny * ny;
     float* IL = SyT + ny * ny;
-    float* A = IL + nx * ny;
-    float* B = A + nx * ny;
-    const int ntab = 2 * nx * nx + 2 * ny * ny + nx * ny;     // a multiple of 4 (nx % 4 == 0, ny even)
-    for (int i = threadIdx.x; i < ntab / 4; i += FT)
-        reinterpret_cast<float4*>(Sx)[i] = reinterpret_cast<const float4*>(tab)[i];
-    for (int i = threadIdx.x; i < nx * ny; i += FT) A[i] = f[i];
+    float* X = IL + nx * ny;
+    float* Y = X + nx * fdm_ldf(ny);
+    const int ntab = 2 * nx * nx + 2 * ny * ny + nx * ny;     // a multiple of 4 (nx % 4 == 0, ny % 4 == 0)
+    for (int i = threadIdx.x; i < ntab / 4; i += FT) cp_async16(Sx + 4 * i, tab + 4 * i);
+    pdl_wait();
+    pdl_trigger();
+    f += (long long)blockIdx.x * nx * ny;   // system of a batch (one block each)
+    u += (long long)blockIdx.x * nx * ny;
+    const int ldf = fdm_ldf(ny);
+    for (int i = threadIdx.x; i < nx * ny; i += FT) {
+        const int y = i / nx, x = i - y * nx;
+        cp_async4(X + x * ldf + y, f + i);
+    }
+    cp_async_wait_all();
     __syncthreads();
-    mm24(B, A, Sx, ny, nx, nx, nullptr);    // B = F Sx
+    mmT(Y, X, ldf, Sx, ny, nx, nx, nullptr);
     __syncthreads();
-    mm24(A, SyT, B, ny, nx, ny, IL);        // A = (Sy^T B) .* IL
+    mmT(X, Sy, ny, Y, ny, nx, ny, IL);
     __syncthreads();
-    mm24(B, Sy, A, ny, nx, ny, nullptr);    // B = Sy A
+    mmT(Y, X, nx, SyT, nx, ny, ny, nullptr);
     __syncthreads();
-    mm24(A, B, SxT, ny, nx, nx, nullptr);   // A = B Sx^T
-    __syncthreads();
-    for (int i = threadIdx.x; i < nx * ny; i += FT) u[i] = A[i];
+    mmT(u, Y, ny, SxT, ny, nx, nx, nullptr);
 }
 
 }  // namespace k2
@@ -2187,8 +2212,8 @@ void eig1d(int n, int periodic, double h, std::vector<double>& S, std::vector<do
 bool fdm_fits(const Shapes& s, int top, int dim, int mg_fp32) {
     if (dim != 2 || !mg_fp32 || s.nlev < 2) return false;
     const long long nx = s.n[top][0], ny = s.n[top][1];
-    const size_t smem = sizeof(float) * (size_t)(2 * nx * nx + 2 * ny * ny + 3 * nx * ny);
-    return nx % 4 == 0 && ny % 2 == 0 && nx <= 128 && ny <= 128 && smem <= kTailSmemMax;
+    const size_t smem = sizeof(float) * (size_t)k2::fdm_smem_floats(nx, ny);
+    return nx % 4 == 0 && ny % 4 == 0 && nx <= 128 && ny <= 128 && smem <= kTailSmemMax;
 }
 
 template <class T>
@@ -2409,7 +2434,7 @@ bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const dou
         // the top level is solved exactly by fast diagonalisation (replaces the tail V-cycle)
         const int nx = s.n[pl->top][0], ny = s.n[pl->top][1];
         pl->fdm_tab = (float*)take(sizeof(float) * (2 * nx * nx + 2 * ny * ny + nx * ny));
-        pl->fdm_smem = sizeof(float) * (size_t)(2 * nx * nx + 2 * ny * ny + 3 * nx * ny);
+        pl->fdm_smem = sizeof(float) * (size_t)k2::fdm_smem_floats(nx, ny);
     }
     // tail shared-memory offsets (elements of T)
     {
