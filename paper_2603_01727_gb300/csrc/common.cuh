@@ -213,6 +213,54 @@ __device__ inline float block_sum_f(float v, float* smem /* NT/32 floats */) {
     return r;
 }
 
+// Two sums at once, each with the tree of block_sum / block_sum_f (bitwise the
+// same values as two separate calls, with half the barriers).
+template <int NT, class V>
+__device__ inline void block_sum2_t(V& a, V& b, V* smem /* 2 NT/32 */) {
+    static_assert(NT % 32 == 0 && NT <= 1024, "block size");
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) {
+        smem[w] = a;
+        smem[NT / 32 + w] = b;
+    }
+    __syncthreads();
+    if (w == 0) {
+        V ra = (l < NT / 32) ? smem[l] : (V)0;
+        V rb = (l < NT / 32) ? smem[NT / 32 + l] : (V)0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ra += __shfl_xor_sync(0xffffffffu, ra, o);
+            rb += __shfl_xor_sync(0xffffffffu, rb, o);
+        }
+        if (l == 0) {
+            smem[0] = ra;
+            smem[1] = rb;
+        }
+    }
+    __syncthreads();
+    a = smem[0];
+    b = smem[1];
+    __syncthreads();
+}
+template <int NT>
+__device__ inline void block_sum2_any(double a, double b, double* smem, float*, double* A, double* B) {
+    block_sum2_t<NT, double>(a, b, smem);
+    *A = a;
+    *B = b;
+}
+template <int NT>
+__device__ inline void block_sum2_any(float a, float b, double*, float* smemf, double* A, double* B) {
+    block_sum2_t<NT, float>(a, b, smemf);
+    *A = (double)a;
+    *B = (double)b;
+}
+
 // Block sum in the accumulator's own type, returned as double.
 template <int NT>
 __device__ inline double block_sum_any(double v, double* smem, float*) { return block_sum<NT>(v, smem); }

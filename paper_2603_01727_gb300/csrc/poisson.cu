@@ -195,18 +195,21 @@ __device__ __forceinline__ T prolong_at(const LvT<T>& C, const T* __restrict__ u
 }
 
 // Last block of a grid to arrive.  The block's partial sums are written by
-// thread 0 before the call, so only thread 0 fences them (release) before
-// counting in; the last block fences again (acquire) before reading the others'.
+// thread 0 before the call; thread 0 counts in with one acquire-release atomic
+// at GPU scope, which publishes its partials (release) and, in the last block,
+// makes every other block's published partials visible (acquire) before the
+// block barrier hands them to the block's other threads.
 // arrive_last_n: the same among nblocks blocks (the blocks of one system of a
 // batch, which counts on that system's counter).
+__device__ __forceinline__ unsigned int atomic_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 __device__ __forceinline__ bool arrive_last_n(unsigned int* cnt, unsigned int nblocks) {
     __shared__ int am_last;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        am_last = (atomicAdd(cnt, 1u) == nblocks - 1u);
-        if (am_last) __threadfence();
-    }
+    if (threadIdx.x == 0) am_last = (atomic_add_acq_rel_gpu(cnt, 1u) == nblocks - 1u);
     __syncthreads();
     return am_last != 0;
 }
@@ -227,6 +230,20 @@ __device__ __forceinline__ double sum_parts_cg(const double* part, int np, doubl
     double v = 0.0;
     for (int i = threadIdx.x; i < np; i += NT) v += __ldcg(part + i);
     return block_sum<NT>(v, smem);
+}
+
+// The same for two partial arrays of np entries in one pass.
+template <int NT>
+__device__ __forceinline__ void sum_parts2_cg(const double* pa, const double* pb, int np, double* smem2, double* A,
+                                              double* B) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < np; i += NT) {
+        a += __ldcg(pa + i);
+        b += __ldcg(pb + i);
+    }
+    block_sum2_t<NT, double>(a, b, smem2);
+    *A = a;
+    *B = b;
 }
 
 __device__ __forceinline__ int block_linear() {
@@ -428,18 +445,18 @@ __global__ void __launch_bounds__(Tile<DIM>::NT)
         }
     }
     if (FINE) {
-        __shared__ double red[NT / 32];
-        __shared__ float redf[NT / 32];
-        const double brz = block_sum_any<NT>(rz, red, redf);
-        const double bsz = block_sum_any<NT>(sz, red, redf);
+        __shared__ double red[2 * (NT / 32)];
+        __shared__ float redf[2 * (NT / 32)];
+        double brz, bsz;
+        block_sum2_any<NT>(rz, sz, red, redf, &brz, &bsz);
         const int nb = gridDim.x * gridDim.y * gridDim.z;
         if (threadIdx.x == 0) {
             part_rz[block_linear()] = brz;
             part_sz[block_linear()] = bsz;
         }
         if (arrive_last(cnt)) {
-            const double RZ = sum_parts_cg<NT>(part_rz, nb, red);
-            const double SZ = sum_parts_cg<NT>(part_sz, nb, red);
+            double RZ, SZ;
+            sum_parts2_cg<NT>(part_rz, part_sz, nb, red, &RZ, &SZ);
             if (threadIdx.x == 0) {
                 const int it = ictl[PI_IT];
                 scal[PS_BETA] = (it == 0) ? 0.0 : RZ / scal[PS_RZ];
@@ -778,16 +795,15 @@ __global__ void __launch_bounds__(NTV)
         ff = fma(f, f, ff);
         rr = fma(rv, rv, rr);
     }
-    __shared__ double red[NTV / 32];
-    ff = block_sum<NTV>(ff, red);
-    rr = block_sum<NTV>(rr, red);
+    __shared__ double red[2 * (NTV / 32)];
+    block_sum2_t<NTV, double>(ff, rr, red);
     if (threadIdx.x == 0) {
         pff[blockIdx.x] = ff;
         prr[blockIdx.x] = rr;
     }
     if (arrive_last_n(cnt, gridDim.x)) {
-        const double FF = sum_parts_cg<NTV>(pff, gridDim.x, red);
-        const double RR = sum_parts_cg<NTV>(prr, gridDim.x, red);
+        double FF, RR;
+        sum_parts2_cg<NTV>(pff, prr, gridDim.x, red, &FF, &RR);
         if (threadIdx.x == 0) {
             scal[PS_FF] = FF;
             scal[PS_RR] = RR;
@@ -1251,10 +1267,10 @@ __global__ void __launch_bounds__(NT)
         }
     }
     if (FINE) {
-        __shared__ double red[NT / 32];
-        __shared__ float redf[NT / 32];
-        const double brz = block_sum_any<NT>(rz, red, redf);
-        const double bsz = block_sum_any<NT>(sz, red, redf);
+        __shared__ double red[2 * (NT / 32)];
+        __shared__ float redf[2 * (NT / 32)];
+        double brz, bsz;
+        block_sum2_any<NT>(rz, sz, red, redf, &brz, &bsz);
         const int nb = gridDim.x * gridDim.y;
         const int bid = blockIdx.x + gridDim.x * blockIdx.y;
         if (threadIdx.x == 0) {
@@ -1262,8 +1278,8 @@ __global__ void __launch_bounds__(NT)
             part_sz[bid] = bsz;
         }
         if (arrive_last_n(cnt, gridDim.x * gridDim.y)) {
-            const double RZ = sum_parts_cg<NT>(part_rz, nb, red);
-            const double SZ = sum_parts_cg<NT>(part_sz, nb, red);
+            double RZ, SZ;
+            sum_parts2_cg<NT>(part_rz, part_sz, nb, red, &RZ, &SZ);
             if (threadIdx.x == 0) {
                 const int it = ictl[PI_IT];
                 scal[PS_BETA] = (it == 0) ? 0.0 : RZ / scal[PS_RZ];
@@ -1883,18 +1899,18 @@ __global__ void __launch_bounds__(NT)
         }
     }
     if (FINE) {
-        __shared__ double red[NT / 32];
-        __shared__ float redf[NT / 32];
-        const double brz = block_sum_any<NT>(rz, red, redf);
-        const double bsz = block_sum_any<NT>(sz, red, redf);
+        __shared__ double red[2 * (NT / 32)];
+        __shared__ float redf[2 * (NT / 32)];
+        double brz, bsz;
+        block_sum2_any<NT>(rz, sz, red, redf, &brz, &bsz);
         const int nb = gridDim.x * gridDim.y * gridDim.z;
         if (threadIdx.x == 0) {
             part_rz[block_linear()] = brz;
             part_sz[block_linear()] = bsz;
         }
         if (arrive_last(cnt)) {
-            const double RZ = sum_parts_cg<NT>(part_rz, nb, red);
-            const double SZ = sum_parts_cg<NT>(part_sz, nb, red);
+            double RZ, SZ;
+            sum_parts2_cg<NT>(part_rz, part_sz, nb, red, &RZ, &SZ);
             if (threadIdx.x == 0) {
                 const int it = ictl[PI_IT];
                 scal[PS_BETA] = (it == 0) ? 0.0 : RZ / scal[PS_RZ];
