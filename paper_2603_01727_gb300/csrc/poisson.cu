@@ -1262,7 +1262,9 @@ __global__ void __launch_bounds__(NT)
         const T u = su[r][lane];
         upost[g] = u;
         if (FINE) {
-            rz = fma(f[g], (TF)u, rz);
+            // f is still in shared memory, exactly, when T and TF agree
+            const TF fv = (sizeof(T) == sizeof(TF)) ? (TF)sf[r][lane] : f[g];
+            rz = fma(fv, (TF)u, rz);
             sz += (TF)u;
         }
     }
@@ -1891,7 +1893,9 @@ __global__ void __launch_bounds__(NT)
                     const T u = sU[sl][r][lane];
                     upost[g] = u;
                     if (FINE) {
-                        rz = fma(f[g], (TF)u, rz);
+                        // plane z's f is still in the ring, exactly, when T and TF agree
+                        const TF fv = (sizeof(T) == sizeof(TF)) ? (TF)sF[sl][r][lane] : f[g];
+                        rz = fma(fv, (TF)u, rz);
                         sz += (TF)u;
                     }
                 }
