@@ -537,7 +537,8 @@ __global__ void __launch_bounds__(Tile<DIM>::NT)
 __global__ void __launch_bounds__(NTV)
     k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* p0, const double* p1,
                 const double* __restrict__ q, long long N, double* part, double* scal, int* ictl,
-                unsigned int* cnt, double rtol, int max_iter, cudaGraphConditionalHandle h, int use_graph) {
+                unsigned int* cnt, double rtol, int max_iter, cudaGraphConditionalHandle h, int use_graph,
+                int vec2) {
     pdl_wait();
     pdl_trigger();
     const int fb = blockIdx.y;
@@ -553,11 +554,31 @@ __global__ void __launch_bounds__(NTV)
     const double* __restrict__ p = (it & 1) ? p1 : p0;
     const double alpha = scal[PS_ALPHA];
     double rr = 0.0;
-    for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV) {
-        x[t] = fma(alpha, p[t], x[t]);
-        const double rv = fma(-alpha, q[t], r[t]);
-        r[t] = rv;
-        rr = fma(rv, rv, rr);
+    if (vec2) {
+        // two cells per thread step (16-byte accesses; N even and x 16-byte aligned,
+        // the launch is sized by N / 2)
+        const long long N2 = N >> 1;
+        for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N2; t += (long long)gridDim.x * NTV) {
+            const double2 pv = reinterpret_cast<const double2*>(p)[t];
+            const double2 qv = reinterpret_cast<const double2*>(q)[t];
+            double2 xv = reinterpret_cast<const double2*>(x)[t];
+            double2 rv = reinterpret_cast<const double2*>(r)[t];
+            xv.x = fma(alpha, pv.x, xv.x);
+            xv.y = fma(alpha, pv.y, xv.y);
+            rv.x = fma(-alpha, qv.x, rv.x);
+            rv.y = fma(-alpha, qv.y, rv.y);
+            reinterpret_cast<double2*>(x)[t] = xv;
+            reinterpret_cast<double2*>(r)[t] = rv;
+            rr = fma(rv.x, rv.x, rr);
+            rr = fma(rv.y, rv.y, rr);
+        }
+    } else {
+        for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV) {
+            x[t] = fma(alpha, p[t], x[t]);
+            const double rv = fma(-alpha, q[t], r[t]);
+            r[t] = rv;
+            rr = fma(rv, rv, rr);
+        }
     }
     __shared__ double red[NTV / 32];
     rr = block_sum<NTV>(rr, red);
@@ -608,13 +629,39 @@ __global__ void __launch_bounds__(NTV)
     const int ereset = ictl[PI_ERESET];
     const float* __restrict__ p = (it & 1) ? p1 : p0;
     const float alpha = (float)scal[PS_ALPHA];
+    const bool fresh = (it == 0 || ereset);
     float rr = 0.0f;
-    for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV) {
-        const float ev = (it == 0 || ereset) ? 0.0f : e[t];
-        e[t] = fmaf(alpha, p[t], ev);
-        const float rv = fmaf(-alpha, q[t], r[t]);
-        r[t] = rv;
-        rr = fmaf(rv, rv, rr);
+    if ((N & 3) == 0) {
+        // four cells per thread step (16-byte accesses; the launch is sized by N / 4)
+        const long long N4 = N >> 2;
+        for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N4; t += (long long)gridDim.x * NTV) {
+            const float4 pv = reinterpret_cast<const float4*>(p)[t];
+            const float4 qv = reinterpret_cast<const float4*>(q)[t];
+            float4 rv = reinterpret_cast<const float4*>(r)[t];
+            float4 ev = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(e)[t];
+            ev.x = fmaf(alpha, pv.x, ev.x);
+            ev.y = fmaf(alpha, pv.y, ev.y);
+            ev.z = fmaf(alpha, pv.z, ev.z);
+            ev.w = fmaf(alpha, pv.w, ev.w);
+            rv.x = fmaf(-alpha, qv.x, rv.x);
+            rv.y = fmaf(-alpha, qv.y, rv.y);
+            rv.z = fmaf(-alpha, qv.z, rv.z);
+            rv.w = fmaf(-alpha, qv.w, rv.w);
+            reinterpret_cast<float4*>(e)[t] = ev;
+            reinterpret_cast<float4*>(r)[t] = rv;
+            rr = fmaf(rv.x, rv.x, rr);
+            rr = fmaf(rv.y, rv.y, rr);
+            rr = fmaf(rv.z, rv.z, rr);
+            rr = fmaf(rv.w, rv.w, rr);
+        }
+    } else {
+        for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV) {
+            const float ev = fresh ? 0.0f : e[t];
+            e[t] = fmaf(alpha, p[t], ev);
+            const float rv = fmaf(-alpha, q[t], r[t]);
+            r[t] = rv;
+            rr = fmaf(rv, rv, rr);
+        }
     }
     __shared__ float redf[NTV / 32];
     __shared__ double red[NTV / 32];
@@ -2752,14 +2799,20 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
     // a batch sets the while-node condition once, from every system's state
     const int ug = (pl->nb > 1) ? 0 : use_graph;
     if (ir) {
-        launch(k_ir_update, rb, NTV, 0, s, pl->e32, pl->r32, pl->p32[0], pl->p32[1], pl->q32, pl->N, pl->part0, pl->scal,
+        // the update runs four cells per thread step when N % 4 == 0
+        const dim3 rbu((pl->N % 4 == 0) ? reduce_blocks(pl->N / 4) : reduce_blocks(pl->N), pl->nb);
+        launch(k_ir_update, rbu, NTV, 0, s, pl->e32, pl->r32, pl->p32[0], pl->p32[1], pl->q32, pl->N, pl->part0, pl->scal,
                                        pl->ictl, pl->cnt + CNT_UPD, pl->inner_tol, pl->inner_max, pl->max_iter, h, ug);
         launch(k_ir_refine<DIM>, rb, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r, pl->e32, pl->r32, pl->part1,
                                             pl->scal, pl->ictl, pl->cnt + CNT_REF, pl->rtol, pl->max_iter, h, ug);
         pl->launches += 2;
     } else {
-        launch(k_cg_update, rb, NTV, 0, s, x, pl->r, pl->p[0], pl->p[1], pl->q, pl->N, pl->part0, pl->scal, pl->ictl,
-                                       pl->cnt + CNT_UPD, pl->rtol, pl->max_iter, h, ug);
+        // the update runs two cells per thread step when N is even and x (the
+        // caller's array) is 16-byte aligned
+        const int vec2 = (pl->N % 2 == 0) && (((uintptr_t)x & 15) == 0);
+        const dim3 rbu(vec2 ? reduce_blocks(pl->N / 2) : reduce_blocks(pl->N), pl->nb);
+        launch(k_cg_update, rbu, NTV, 0, s, x, pl->r, pl->p[0], pl->p[1], pl->q, pl->N, pl->part0, pl->scal, pl->ictl,
+                                       pl->cnt + CNT_UPD, pl->rtol, pl->max_iter, h, ug, vec2);
         pl->launches += 1;
     }
     if (pl->nb > 1) {
