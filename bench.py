@@ -205,20 +205,22 @@ def kernel_models(prm, mixed):
     """Algorithmic traffic (bytes) and arithmetic (flops) per launch of the
     kernels timed by sim_time_kernel, from the arrays each one must read and
     write once (ghost layers and shared-memory halos ignored).  w = bytes of a
-    multigrid word (4 in the mixed path, 8 in FP64); Krylov vectors are FP64."""
+    multigrid word, v = bytes of a Krylov vector of the CG loop: 4 and 4 in the
+    mixed path (FP32 inner loop), 8 and 8 in FP64."""
     dim = prm["dim"]
     N = float(np.prod(prm["n"][:dim]))
     w = 4.0 if mixed else 8.0
+    v = 4.0 if mixed else 8.0
     nb = 2 * dim                        # neighbours of the compact operator
     m = {}
     # fine level down: read r, write u_pre and the coarse right-hand side;
     # red (1 flop), black (2nb+1), residual (2nb+2), restriction (2 x 4^d / 2^d)
-    m["mg_down"] = dict(id=1, bytes=8 * N + w * N + w * N / 2 ** dim,
+    m["mg_down"] = dict(id=1, bytes=v * N + w * N + w * N / 2 ** dim,
                         flops=N * (0.5 + 0.5 * (2 * nb + 1) + (2 * nb + 2) + 2.0 * 2 ** dim))
     # CG: p = z - mean + beta p_old, q = A p, p.q: read z, p_old; write p, q
-    m["cg_matvec"] = dict(id=2, bytes=w * N + 3 * 8 * N, flops=N * (2 + 2 * nb + 2 + 2))
+    m["cg_matvec"] = dict(id=2, bytes=w * N + 3 * v * N, flops=N * (2 + 2 * nb + 2 + 2))
     # fine level up: read u_pre, r, coarse u; write z; r.z and sum z
-    m["mg_up"] = dict(id=3, bytes=w * N + 8 * N + w * N / 2 ** dim + w * N,
+    m["mg_up"] = dict(id=3, bytes=w * N + v * N + w * N / 2 ** dim + w * N,
                       flops=N * (2 * 2 ** dim + (2 * nb + 1) + 4))
     # predictor stencil pass: reads v, Z, H, rho, kappa, F (dim faces), chi-data, R^(n-1);
     # writes R^n, Z*, H*, rho v~ (the data model of the stage kernel)
@@ -574,7 +576,8 @@ def roofline(res, peaks, precision):
               "frac": tfl / fp64_tflops}
     else:
         rl = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
-    rl.update(kernel=top, launch_us=t * 1e6, share_of_step=share[top], traffic=None,
+    rl.update(kernel=top, launch_us=t * 1e6, share_of_step=share[top],
+              traffic=NCU_TRAFFIC.get((tuple(res["cfg"].get("grid", ())), precision, top)),
               peak_source="MEASURED_PEAKS.json hbm_gbs (burst copy)" if rl["bound"] == "hbm"
               else "nominal GB300 FP64 rate (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)",
               shares={k: round(v, 4) for k, v in share.items()}, nlev=nlev)
@@ -584,8 +587,12 @@ def roofline(res, peaks, precision):
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12    # 1.26 TFLOP/s
 ISSUE_PEAK_WARP_INSTR = 152 * 4 * 2.07e9           # warp instructions / s
 # float-float stage stencil: smsp__inst_executed.sum / cells (ncu, 2D 128x256, 3D 64^3)
-RESIDUAL_FF_WARP_INSTR_PER_CELL = {2: 121.7, 3: 270.1}
+RESIDUAL_FF_WARP_INSTR_PER_CELL = {2: 129.8, 3: 273.4}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 80.5 TFLOP/s
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel, by
+# (grid, precision, kernel); entries are removed when the kernel changes.
+# 256x512 slot, fine-level up (k2::up<float, float, 1, 2>): 1.214 MB read, 0 written
+NCU_TRAFFIC = {((256, 512), "mixed", "mg_up"): 1.214e6}
 
 
 def load_peaks():
