@@ -1183,10 +1183,12 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
     const Ax ax = axis(ox + lane, nx, L.per[0]);
     __shared__ int srow[SY];
     const ColCodes cc = box_codes<T>(L, ox, oy, srow);
+    Ax ayk[SY / NW];   // this thread's rows (kept for the residual pass)
 #pragma unroll
     for (int k = 0; k < SY / NW; ++k) {
         const int r = warp + NW * k;
         const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        ayk[k] = ay;
         T fv = (T)0, uv = (T)0;
         if (ax.valid && ay.valid) {
             fv = (T)f[ax.gw + nx * ay.gw];
@@ -1210,7 +1212,7 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
     for (int k = 0; k < SY / NW; ++k) {
         const int r = warp + NW * k;
         if (r < R0 || r > R1 || !colr) continue;
-        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        const Ax ay = ayk[k];
         if (!(ax.valid && ay.valid)) continue;
         const T u = su[r][lane];
         sf[r][lane] = sf[r][lane] - (L.diag[ax.cls + 3 * ay.cls] * u - off2<T>(L, su, r, lane));
@@ -1223,6 +1225,9 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
         const int cx = c % CD, cy = c / CD;
         const int I = blockIdx.x * CD + cx, J = blockIdx.y * CD + cy;
         if (I >= C.n[0] || J >= C.n[1]) continue;
+        T wx[4];
+#pragma unroll
+        for (int axx = 0; axx < 4; ++axx) wx[axx] = (T)rweight(axx, I, C.n[0], C.per[0]);
         T acc = (T)0;
 #pragma unroll
         for (int ay = 0; ay < 4; ++ay) {
@@ -1230,8 +1235,7 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
             const int r = 2 * cy + H - 1 + ay;
             T row = (T)0;
 #pragma unroll
-            for (int axx = 0; axx < 4; ++axx)
-                row += (T)rweight(axx, I, C.n[0], C.per[0]) * sf[r][2 * cx + H - 1 + axx];
+            for (int axx = 0; axx < 4; ++axx) row += wx[axx] * sf[r][2 * cx + H - 1 + axx];
             acc += wy * row;
         }
         fc[I + C.n[0] * J] = acc * (T)0.25;
@@ -1272,10 +1276,12 @@ __global__ void __launch_bounds__(NT)
     int I0 = 0, I1 = 0;
     if (ax.valid) pro_pair(ax.gw, C.n[0], C.per[0], &I0, &I1);
     const T a = (T)0.75, b = (T)0.25;
+    Ax ayk[SY / NW];   // this thread's rows (kept for the output pass)
 #pragma unroll
     for (int k = 0; k < SY / NW; ++k) {
         const int r = warp + NW * k;
         const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        ayk[k] = ay;
         T fv = (T)0, uv = (T)0;
         if (ax.valid && ay.valid) {
             const int g = ax.gw + nx * ay.gw;
@@ -1303,7 +1309,7 @@ __global__ void __launch_bounds__(NT)
     for (int k = 0; k < SY / NW; ++k) {
         const int r = warp + NW * k;
         if (!colo || r < H || r >= H + FU) continue;
-        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        const Ax ay = ayk[k];
         if (!ay.in) continue;
         const int g = ax.gw + nx * ay.gw;
         const T u = su[r][lane];
@@ -1366,10 +1372,13 @@ __global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p
     const int ox = blockIdx.x * FP - H, oy = blockIdx.y * FP - H;
     const int nx = L.n[0];
     const Ax ax = axis(ox + lane, nx, L.per[0]);
+    Ax ayk[SY / NW];   // this thread's rows and p values (kept for the second pass)
+    V pvk[SY / NW];
 #pragma unroll
     for (int k = 0; k < SY / NW; ++k) {
         const int r = warp + NW * k;
         const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        ayk[k] = ay;
         V pv = (V)0;
         if (ax.valid && ay.valid) {
             const int g = ax.gw + nx * ay.gw;
@@ -1377,6 +1386,7 @@ __global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p
             if (it > 0) pv = fma(beta, pold[g], pv);
         }
         sp[r][lane] = pv;
+        pvk[k] = pv;
     }
     __syncthreads();
     V acc = (V)0;
@@ -1385,10 +1395,10 @@ __global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p
     for (int k = 0; k < SY / NW; ++k) {
         const int r = warp + NW * k;
         if (!colo || r < H || r >= H + FP) continue;
-        const Ax ay = axis(oy + r, L.n[1], L.per[1]);
+        const Ax ay = ayk[k];
         if (!ay.in) continue;
         const int g = ax.gw + nx * ay.gw;
-        const V pv = sp[r][lane];
+        const V pv = pvk[k];
         const V off = L.w[0] * (sp[r][lane - 1] + sp[r][lane + 1]) + L.w[1] * (sp[r - 1][lane] + sp[r + 1][lane]);
         const V qv = L.diag[ax.cls + 3 * ay.cls] * pv - off;
         pnew[g] = pv;
