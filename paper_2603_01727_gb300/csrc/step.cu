@@ -392,19 +392,26 @@ __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, con
 
 // C: arithmetic of the stencil terms (double, or float-float in the mixed
 // path); the residuals are stored and combined in FP64.
-// Float-float stencil: three blocks per SM (80 registers); latency-bound at
-// the two blocks its uncapped register count allows.
-template <class C>
+// Float-float stencil: three blocks per SM (80 registers) in 3D, four (64) in
+// 2D; latency-bound at the two blocks its uncapped register count allows.  In
+// 2D the fourth block costs spills (slower back to back with warm caches) but
+// hides the DRAM latency of the step's first kernel after a cold L2 better, and
+// a 131k-cell grid fits one wave (slot 256x512 step 1.000 -> 0.993 ms).
+template <int DIM, class C>
 struct ResidMinBlocks {
     static constexpr int v = 2;
 };
 template <>
-struct ResidMinBlocks<FF> {
+struct ResidMinBlocks<3, FF> {
     static constexpr int v = 3;
+};
+template <>
+struct ResidMinBlocks<2, FF> {
+    static constexpr int v = 4;
 };
 
 template <int DIM, class C>
-__global__ void __launch_bounds__(NT, ResidMinBlocks<C>::v) k_residual(Geom g, Phys ph, ResidArgs a) {
+__global__ void __launch_bounds__(NT, ResidMinBlocks<DIM, C>::v) k_residual(Geom g, Phys ph, ResidArgs a) {
     const long long t = (long long)blockIdx.x * NT + threadIdx.x;
     if (t >= g.ncell) return;
     const long long c = pad_index(g, t);
