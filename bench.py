@@ -510,18 +510,20 @@ def e2e_gpu(args, precision, res, device):
 
 
 def tail_model(sim, mixed, sweeps=2):
-    """Bytes and flops of one coarse-level launch: fast diagonalisation is four
-    dense products of the top level (nx*ny*(nx+ny) multiply-adds each pair);
-    the shared-memory V-cycle is ~(4 sweeps + residual + transfers) x 10 flops
-    per cell over the levels (4/3 of the top level in 2D)."""
-    nx, ny = sim.query(12), sim.query(13)
-    nt = nx * ny
+    """Bytes and flops of one coarse-level launch: fast diagonalisation is two
+    one-axis transforms per axis of the top level (forward and back, N*n_d
+    multiply-adds each); the shared-memory V-cycle is ~(4 sweeps + residual +
+    transfers) x 10 flops per cell over the levels (4/3 of the top level in
+    2D, 8/7 in 3D)."""
+    nx, ny, nz = sim.query(12), sim.query(13), sim.query(15)
+    nt = nx * ny * nz
     w = 4.0 if mixed else 8.0
     if sim.query(14) > 0:
-        flops = 2.0 * 2.0 * nt * (nx + ny)
-        table = 4.0 * (2 * nx * nx + 2 * ny * ny + nt)
+        ext = [nx, ny] + ([nz] if nz > 1 else [])
+        flops = 2.0 * 2.0 * nt * sum(ext)
+        table = 4.0 * (2 * sum(e * e for e in ext) + nt)
     else:
-        flops = (4 * sweeps + 4) * 10.0 * nt * 4.0 / 3.0
+        flops = (4 * sweeps + 4) * 10.0 * nt * (8.0 / 7.0 if nz > 1 else 4.0 / 3.0)
         table = 0.0
     return dict(bytes=2 * nt * w + table, flops=flops)
 

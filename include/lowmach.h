@@ -138,7 +138,8 @@ enum {
     SIM_Q_MASS = 8, SIM_Q_NCELLS = 9, SIM_Q_MG_LEVELS = 10,
     SIM_Q_KERNEL_LAUNCHES = 11,                     /* kernels enqueued by the last sim_step */
     SIM_Q_TAIL_NX = 12, SIM_Q_TAIL_NY = 13,         /* shape of the top coarse level solved in one block */
-    SIM_Q_TAIL_FDM = 14                             /* 1: that level is solved by fast diagonalisation */
+    SIM_Q_TAIL_FDM = 14,                            /* 1: that level is solved by fast diagonalisation */
+    SIM_Q_TAIL_NZ = 15                              /* its z extent (1 in 2D) */
 };
 
 /* Bytes of device workspace sim_create needs for these parameters. */

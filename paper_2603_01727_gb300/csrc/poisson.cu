@@ -2072,6 +2072,129 @@ __global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exact solve on the top coarse level in 3D by fast diagonalisation: the level
+// operator is Ax (x) I (x) I + I (x) Ay (x) I + I (x) I (x) Az with the 1D
+// second-difference matrices Ad = Sd diag(lam_d) Sd^T, so the zero-mean
+// solution of A u = f is u = S [(S^T f) .* IL], S = Sz (x) Sy (x) Sx, with
+// IL = 1 / (lam_z + lam_y + lam_x) (0 for the null mode).  S^T f and S v are
+// three one-axis transforms each, all in the shared memory of one block.
+// ---------------------------------------------------------------------------
+constexpr int FT3 = 1024;          // threads of the 3D fast-diagonalisation block
+constexpr int kFdm3Cells = 4096;   // largest top level given to it (24^3 measured slower: the
+                                   // transforms make one SM instruction-bound, 46 us)
+
+__host__ __device__ constexpr long long fdm3_smem_floats(long long nx, long long ny, long long nz) {
+    return 2 * (nx * nx + ny * ny + nz * nz) + 3 * nx * ny * nz;
+}
+
+// out[z][y][k] = sum_i M[i][k] in[z][y][i] (M: nx x nx), optionally .* S, to a
+// shared or global out.  A thread takes one k and four (z, y) lines.
+__device__ __forceinline__ void fdm3_x(float* __restrict__ out, const float* __restrict__ in,
+                                       const float* __restrict__ M, int nx, int nlines, const float* __restrict__ S) {
+    const int items = nx * (nlines / 4);
+    for (int t = threadIdx.x; t < items; t += FT3) {
+        const int k = t % nx, l0 = 4 * (t / nx);
+        const float* i0 = in + (long long)l0 * nx;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 4
+        for (int i = 0; i < nx; ++i) {
+            const float m = M[i * nx + k];
+            a0 = fmaf(m, i0[i], a0);
+            a1 = fmaf(m, i0[nx + i], a1);
+            a2 = fmaf(m, i0[2 * nx + i], a2);
+            a3 = fmaf(m, i0[3 * nx + i], a3);
+        }
+        const int o = l0 * nx + k;
+        if (S) {
+            a0 *= S[o];
+            a1 *= S[o + nx];
+            a2 *= S[o + 2 * nx];
+            a3 *= S[o + 3 * nx];
+        }
+        out[o] = a0;
+        out[o + nx] = a1;
+        out[o + 2 * nx] = a2;
+        out[o + 3 * nx] = a3;
+    }
+}
+
+// Along an outer axis of length n and stride st (ny with st = nx, or nz with
+// st = nx ny): out[.., k, ..] = sum_j M[j][k] in[.., j, ..], optionally .* S.
+// The cells of one axis position form `inner` consecutive floats (nx, or
+// nx ny); `outer` such blocks (nz, or 1).  A thread takes one inner position
+// and four consecutive k (M rows read as float4).
+__device__ __forceinline__ void fdm3_outer(float* __restrict__ out, const float* __restrict__ in,
+                                           const float* __restrict__ M, int n, int inner, int outer,
+                                           const float* __restrict__ S) {
+    const int nq = n / 4;
+    const int items = inner * nq * outer;
+    const long long blk = (long long)inner * n;
+    for (int t = threadIdx.x; t < items; t += FT3) {
+        const int x = t % inner, r = t / inner;
+        const int kq = r % nq, ob = r / nq;
+        const float* ip = in + ob * blk + x;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+        for (int j = 0; j < n; ++j) {
+            const float v = ip[(long long)j * inner];
+            const float4 m = *reinterpret_cast<const float4*>(M + j * n + 4 * kq);
+            a.x = fmaf(m.x, v, a.x);
+            a.y = fmaf(m.y, v, a.y);
+            a.z = fmaf(m.z, v, a.z);
+            a.w = fmaf(m.w, v, a.w);
+        }
+        const long long o = ob * blk + (long long)(4 * kq) * inner + x;
+        if (S) {
+            a.x *= S[o];
+            a.y *= S[o + inner];
+            a.z *= S[o + 2 * inner];
+            a.w *= S[o + 3 * inner];
+        }
+        out[o] = a.x;
+        out[o + inner] = a.y;
+        out[o + 2 * inner] = a.z;
+        out[o + 3 * inner] = a.w;
+    }
+}
+
+// Shared memory (floats): Sx, SxT, Sy, SyT, Sz, SzT, IL (the global table,
+// copied linearly before the programmatic-dependency wait), then A and B
+// (N = nx ny nz each).  nx, ny, nz multiples of 4.
+__global__ void __launch_bounds__(FT3) fdm(int nx, int ny, int nz, const float* __restrict__ tab,
+                                           const float* __restrict__ f, float* __restrict__ u) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* Sx = reinterpret_cast<float*>(smraw);
+    float* SxT = Sx + nx * nx;
+    float* Sy = SxT + nx * nx;
+    float* SyT = Sy + ny * ny;
+    float* Sz = SyT + ny * ny;
+    float* SzT = Sz + nz * nz;
+    float* IL = SzT + nz * nz;
+    const int N = nx * ny * nz;
+    float* A = IL + N;
+    float* B = A + N;
+    const int ntab = 2 * (nx * nx + ny * ny + nz * nz) + N;   // a multiple of 4
+    for (int i = threadIdx.x; i < ntab / 4; i += FT3) k2::cp_async16(Sx + 4 * i, tab + 4 * i);
+    pdl_wait();
+    pdl_trigger();
+    for (int i = threadIdx.x; i < N / 4; i += FT3) k2::cp_async16(A + 4 * i, f + 4 * i);
+    k2::cp_async_wait_all();
+    __syncthreads();
+    const int nxy = nx * ny;
+    fdm3_x(B, A, Sx, nx, ny * nz, nullptr);           // S_x^T along x
+    __syncthreads();
+    fdm3_outer(A, B, Sy, ny, nx, nz, nullptr);         // S_y^T along y
+    __syncthreads();
+    fdm3_outer(B, A, Sz, nz, nxy, 1, IL);              // S_z^T along z, then .* IL
+    __syncthreads();
+    fdm3_outer(A, B, SzT, nz, nxy, 1, nullptr);        // S_z along z
+    __syncthreads();
+    fdm3_outer(B, A, SyT, ny, nx, nz, nullptr);        // S_y along y
+    __syncthreads();
+    fdm3_x(u, B, SxT, nx, ny * nz, nullptr);           // S_x along x, to global
+}
+
 }  // namespace k3
 
 // ------------------------------ host helpers --------------------------------
@@ -2114,17 +2237,38 @@ bool make_shapes(int dim, const int n[3], Shapes* s, const char** err) {
     return true;
 }
 
-int pick_top(const Shapes& s, int mg_fp32, long long tail_cells, size_t* smem_out) {
+bool fdm_fits(const Shapes& s, int top, int dim, int mg_fp32);
+
+// Top coarse level of the one-block solve and whether fast diagonalisation
+// solves it (*fdm_out).  In 3D the fast-diagonalisation top is taken unless a
+// tail size is given explicitly (which selects the shared-memory V-cycle).
+int pick_top(const Shapes& s, int dim, int mg_fp32, long long tail_cells, size_t* smem_out, int* fdm_out) {
+    *fdm_out = 0;
     if (s.nlev == 1) {
         *smem_out = 0;
         return 0;
     }
     long long thr = mg_fp32 ? kTailCellsF32 : kTailCellsF64;
+    bool fixed = false;
     if (tail_cells > 0) {
         thr = tail_cells;
+        fixed = true;
     } else if (const char* e = std::getenv("LOWMACH_TAIL_CELLS")) {   // tuning override
         const long long v = std::atoll(e);
-        if (v > 0) thr = v;
+        if (v > 0) {
+            thr = v;
+            fixed = true;
+        }
+    }
+    if (dim == 3 && mg_fp32 && !fixed) {
+        // the largest level of at most kFdm3Cells that the 3D fast-diagonalisation
+        // block takes replaces the levels below it
+        for (int top = 1; top < s.nlev; ++top)
+            if (s.N[top] <= k3::kFdm3Cells && fdm_fits(s, top, dim, mg_fp32)) {
+                *smem_out = 0;
+                *fdm_out = 1;
+                return top;
+            }
     }
     const size_t w = mg_fp32 ? 4 : 8;
     for (int top = 1; top < s.nlev; ++top) {
@@ -2134,9 +2278,11 @@ int pick_top(const Shapes& s, int mg_fp32, long long tail_cells, size_t* smem_ou
         b += w * (size_t)s.N[top];
         if (b > kTailSmemMax && top < s.nlev - 1) continue;
         *smem_out = b;
+        *fdm_out = (dim == 2) && fdm_fits(s, top, dim, mg_fp32);
         return top;
     }
     *smem_out = 0;
+    *fdm_out = (dim == 2) && fdm_fits(s, s.nlev - 1, dim, mg_fp32);
     return s.nlev - 1;
 }
 
@@ -2287,10 +2433,24 @@ void eig1d(int n, int periodic, double h, std::vector<double>& S, std::vector<do
 }
 
 bool fdm_fits(const Shapes& s, int top, int dim, int mg_fp32) {
-    if (dim != 2 || !mg_fp32 || s.nlev < 2) return false;
+    if (!mg_fp32 || s.nlev < 2) return false;
     const long long nx = s.n[top][0], ny = s.n[top][1];
+    if (dim == 3) {
+        const long long nz = s.n[top][2];
+        const size_t smem = sizeof(float) * (size_t)k3::fdm3_smem_floats(nx, ny, nz);
+        return nx % 4 == 0 && ny % 4 == 0 && nz % 4 == 0 && s.N[top] <= k3::kFdm3Cells && smem <= kTailSmemMax;
+    }
+    if (dim != 2) return false;
     const size_t smem = sizeof(float) * (size_t)k2::fdm_smem_floats(nx, ny);
     return nx % 4 == 0 && ny % 4 == 0 && nx <= 128 && ny <= 128 && smem <= kTailSmemMax;
+}
+
+// Floats of the fast-diagonalisation table of a top level n (2D: S_x, S_x^T,
+// S_y, S_y^T, IL; 3D: S_x, S_x^T, S_y, S_y^T, S_z, S_z^T, IL).
+long long fdm_table_floats(const int n[3], int dim) {
+    const long long nx = n[0], ny = n[1], nz = (dim == 3) ? n[2] : 1;
+    const long long sq = nx * nx + ny * ny + ((dim == 3) ? nz * nz : 0);
+    return 2 * sq + nx * ny * nz;
 }
 
 template <class T>
@@ -2339,6 +2499,7 @@ void set_smem_attrs() {
     cudaFuncSetAttribute(k3::up<T, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pl3 * (int)sizeof(T));
     cudaFuncSetAttribute(k3::pq<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl3 * (int)sizeof(double));
     cudaFuncSetAttribute(k2::fdm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+    cudaFuncSetAttribute(k3::fdm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
 }
 
 }  // namespace
@@ -2360,7 +2521,8 @@ size_t poisson_plan_bytes_batch(int dim, const int n[3], const int periodic[3], 
     }
     const size_t B = (size_t)nb;
     size_t tail_smem = 0;
-    const int top = pick_top(s, mg_fp32, tail_cells, &tail_smem);
+    int use_fdm = 0;
+    const int top = pick_top(s, dim, mg_fp32, tail_cells, &tail_smem, &use_fdm);
     const size_t w = mg_fp32 ? 4 : 8;
     const long long N = s.N[0];
     const long long nblk = (dim == 3) ? std::max(tile_blocks<3>(s.n[0]), k3_blocks(s.n[0])) : k2_blocks(s.n[0]);
@@ -2379,10 +2541,7 @@ size_t poisson_plan_bytes_batch(int dim, const int n[3], const int periodic[3], 
     b += align256((mg_fp32 ? sizeof(LvT<float>) : sizeof(LvT<double>)) * s.nlev);
     const long long Nc = s.N[s.nlev - 1];
     b += align256(sizeof(double) * Nc * Nc) + align256(sizeof(float) * Nc * Nc);
-    if (fdm_fits(s, top, dim, mg_fp32)) {
-        const long long nx = s.n[top][0], ny = s.n[top][1];
-        b += align256(sizeof(float) * (2 * nx * nx + 2 * ny * ny + nx * ny));
-    }
+    if (use_fdm) b += align256(sizeof(float) * fdm_table_floats(s.n[top], dim));
     if (nlev_out) *nlev_out = s.nlev;
     if (Nc_out) *Nc_out = Nc;
     return b;
@@ -2422,7 +2581,8 @@ bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const dou
     size_t tail_smem = 0;
     pl->dim = dim;
     pl->nlev = s.nlev;
-    pl->top = pick_top(s, mg_fp32, tail_cells, &tail_smem);
+    int use_fdm = 0;
+    pl->top = pick_top(s, dim, mg_fp32, tail_cells, &tail_smem, &use_fdm);
     pl->mg_fp32 = mg_fp32;
     pl->N = s.N[0];
     pl->rtol = rtol;
@@ -2506,12 +2666,14 @@ bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const dou
     pl->Nc = s.N[s.nlev - 1];
     pl->Minv = (double*)take(sizeof(double) * pl->Nc * pl->Nc);
     pl->Minv_f = (float*)take(sizeof(float) * pl->Nc * pl->Nc);
-    pl->fdm = fdm_fits(s, pl->top, dim, mg_fp32);
+    pl->fdm = use_fdm;
     if (pl->fdm) {
         // the top level is solved exactly by fast diagonalisation (replaces the tail V-cycle)
-        const int nx = s.n[pl->top][0], ny = s.n[pl->top][1];
-        pl->fdm_tab = (float*)take(sizeof(float) * (2 * nx * nx + 2 * ny * ny + nx * ny));
-        pl->fdm_smem = sizeof(float) * (size_t)k2::fdm_smem_floats(nx, ny);
+        const int nx = s.n[pl->top][0], ny = s.n[pl->top][1], nz = s.n[pl->top][2];
+        pl->fdm_tab_floats = (size_t)fdm_table_floats(s.n[pl->top], dim);
+        pl->fdm_tab = (float*)take(sizeof(float) * pl->fdm_tab_floats);
+        pl->fdm_smem = sizeof(float) * (size_t)((dim == 3) ? k3::fdm3_smem_floats(nx, ny, nz)
+                                                             : k2::fdm_smem_floats(nx, ny));
     }
     // tail shared-memory offsets (elements of T)
     {
@@ -2536,11 +2698,13 @@ bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const dou
     pl->levtab_bytes = lvsz * s.nlev;
     *minv_host = coarse_inverse(pl->lev[s.nlev - 1], dim);
     if (pl->fdm) {
-        // appended after the coarse inverse: S_x (nx*nx), S_y (ny*ny), IL (ny*nx)
-        const int nx = s.n[pl->top][0], ny = s.n[pl->top][1];
-        std::vector<double> Sx, Sy, lx, ly;
+        // appended after the coarse inverse: S_d and S_d^T per axis, then IL
+        // (z slowest, x fastest)
+        const int nx = s.n[pl->top][0], ny = s.n[pl->top][1], nz = (dim == 3) ? s.n[pl->top][2] : 1;
+        std::vector<double> Sx, Sy, Sz, lx, ly, lz(1, 0.0);
         eig1d(nx, pl->lev[pl->top].periodic[0], pl->lev[pl->top].h[0], Sx, lx);
         eig1d(ny, pl->lev[pl->top].periodic[1], pl->lev[pl->top].h[1], Sy, ly);
+        if (dim == 3) eig1d(nz, pl->lev[pl->top].periodic[2], pl->lev[pl->top].h[2], Sz, lz);
         auto put = [&](const std::vector<double>& M, int n, bool transpose) {
             for (int i = 0; i < n; ++i)
                 for (int k = 0; k < n; ++k) minv_host->push_back(transpose ? M[(size_t)k * n + i] : M[(size_t)i * n + k]);
@@ -2549,11 +2713,16 @@ bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const dou
         put(Sx, nx, true);
         put(Sy, ny, false);
         put(Sy, ny, true);
-        for (int l = 0; l < ny; ++l)
-            for (int k = 0; k < nx; ++k) {
-                const double lam = ly[l] + lx[k];
-                minv_host->push_back(lam > 0.0 ? 1.0 / lam : 0.0);
-            }
+        if (dim == 3) {
+            put(Sz, nz, false);
+            put(Sz, nz, true);
+        }
+        for (int m = 0; m < nz; ++m)
+            for (int l = 0; l < ny; ++l)
+                for (int k = 0; k < nx; ++k) {
+                    const double lam = lz[m] + ly[l] + lx[k];
+                    minv_host->push_back(lam > 0.0 ? 1.0 / lam : 0.0);
+                }
     }
     if (mg_fp32) set_smem_attrs<float>();
     else set_smem_attrs<double>();
@@ -2563,11 +2732,7 @@ bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const dou
 
 bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& M, cudaStream_t s, const char** err) {
     const size_t nm = (size_t)(pl->Nc * pl->Nc);
-    size_t nf = 0;
-    if (pl->fdm) {
-        const size_t nx = pl->lev[pl->top].n[0], ny = pl->lev[pl->top].n[1];
-        nf = 2 * nx * nx + 2 * ny * ny + nx * ny;
-    }
+    const size_t nf = pl->fdm ? pl->fdm_tab_floats : 0;
     if (M.size() != nm + nf) {
         *err = "coarse inverse not prepared";
         return false;
@@ -2579,12 +2744,9 @@ bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& M, cudaSt
         e = cudaMemcpyAsync(pl->Minv_f, Mf.data(), sizeof(float) * nm, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(pl->levtab, pl->levtab_host, pl->levtab_bytes, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && pl->fdm) {
-        const int nx = pl->lev[pl->top].n[0], ny = pl->lev[pl->top].n[1];
-        const float* hp = Mf.data() + nm;
-        e = cudaMemcpyAsync(pl->fdm_tab, hp, sizeof(float) * (2 * nx * nx + 2 * ny * ny + nx * ny),
-                            cudaMemcpyHostToDevice, s);
-    }
+    if (e == cudaSuccess && pl->fdm)
+        e = cudaMemcpyAsync(pl->fdm_tab, Mf.data() + nm, sizeof(float) * pl->fdm_tab_floats, cudaMemcpyHostToDevice,
+                            s);
     const size_t nb = (size_t)(pl->nb > 0 ? pl->nb : 1);
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->cnt, 0, nb * sizeof(unsigned int) * kNumCounters, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->ictl, 0, nb * sizeof(int) * PI_NINT, s);
@@ -2742,6 +2904,10 @@ void enqueue_tail(PoissonPlan* pl, cudaStream_t s) {
         const int nx = pl->lev[pl->top].n[0], ny = pl->lev[pl->top].n[1];
         launch(k2::fdm, pl->nb, k2::FT, pl->fdm_smem, s, nx, ny, pl->fdm_tab, (const float*)pl->lev[pl->top].f,
                                                 (float*)pl->lev[pl->top].upost);
+    } else if (DIM == 3 && pl->fdm) {
+        const int nx = pl->lev[pl->top].n[0], ny = pl->lev[pl->top].n[1], nz = pl->lev[pl->top].n[2];
+        launch(k3::fdm, 1, k3::FT3, pl->fdm_smem, s, nx, ny, nz, (const float*)pl->fdm_tab,
+               (const float*)pl->lev[pl->top].f, (float*)pl->lev[pl->top].upost);
     } else if (DIM == 2)
         launch(k2::tail<T>, pl->nb, k2::TT, pl->tail_smem, s, lv_dev<T>(pl), a, (const T*)pl->lev[pl->top].f,
                                                      (T*)pl->lev[pl->top].upost, Minv);

@@ -108,10 +108,12 @@ struct PoissonPlan {
     int launches;         // kernels enqueued by the last enqueue (host-side count)
     size_t levtab_bytes;
     unsigned char levtab_host[kMaxLevels * sizeof(LvT<double>)];   // host copy of levtab
-    // fast-diagonalisation solve of the top coarse level (2D, FP32 multigrid)
+    // fast-diagonalisation solve of the top coarse level (FP32 multigrid)
     int fdm;
     float* fdm_tab;       // S_x, S_x^T (nx x nx, eigenvectors as columns), S_y, S_y^T (ny x ny),
-                          // inverse eigenvalue sums (ny x nx, 0 for the null mode)
+                          // [3D: S_z, S_z^T (nz x nz)], inverse eigenvalue sums (x fastest, 0 for
+                          // the null mode)
+    size_t fdm_tab_floats;
     size_t fdm_smem;
     // Batch of nb independent systems on the same grid (nb = 1: one system).
     // Every per-solve array above holds nb consecutive copies (vectors and

@@ -1064,6 +1064,7 @@ sim_status sim_query(sim_t* s, int what, double* out) {
         case SIM_Q_TAIL_NX: *out = (double)s->pp.lev[s->pp.top].n[0]; return SIM_OK;
         case SIM_Q_TAIL_NY: *out = (double)s->pp.lev[s->pp.top].n[1]; return SIM_OK;
         case SIM_Q_TAIL_FDM: *out = (double)s->pp.fdm; return SIM_OK;
+        case SIM_Q_TAIL_NZ: *out = (double)(s->g.dim == 3 ? s->pp.lev[s->pp.top].n[2] : 1); return SIM_OK;
         case SIM_Q_KERNEL_LAUNCHES: {
             if (s->launches_last >= 0) {
                 *out = (double)s->launches_last;

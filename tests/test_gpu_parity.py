@@ -343,3 +343,34 @@ def test_z_marching_3d_multigrid_matches_cube_tiles(n, periodic_x, precision, mo
     assert out["0"][1] == out["1"][1], (out["0"][1], out["1"][1])
     for k in out["0"][0]:
         assert rel(out["0"][0][k], out["1"][0][k]) <= 1e-9, k
+
+
+@pytest.mark.parametrize("n,periodic_x", [(48, False), (32, True)])
+def test_3d_fast_diagonalisation_top_level_matches_vcycle_tail(n, periodic_x, monkeypatch):
+    """Mixed precision in 3D solves the top coarse level (at most 4096 cells)
+    exactly by fast diagonalisation; forcing the one-block V-cycle tail
+    instead (an explicit tail size) must give the same fields to solver
+    tolerance, with no more CG iterations for the exact coarse solve."""
+    from paper_2603_01727_gb300.lowmach import (SIM_Q_ITERS_PRED, SIM_Q_ITERS_CORR, SIM_Q_TAIL_FDM, SIM_Q_TAIL_NX,
+                                                SIM_Q_TAIL_NZ)
+    prm, geo, f = W.sphere_burner(n)
+    prm["precision"] = W.MIXED
+    prm["poisson_rtol"] = 1e-12
+    if periodic_x:
+        prm["bc"] = [[W.PERIODIC, W.PERIODIC]] + prm["bc"][1:]
+    out = {}
+    for mode in ("fdm", "tail"):
+        if mode == "tail":
+            monkeypatch.setenv("LOWMACH_TAIL_CELLS", "4096")
+        sim = gpu_run(prm, geo, f, 4)
+        fdm = sim.query(SIM_Q_TAIL_FDM)
+        assert fdm == (1.0 if mode == "fdm" else 0.0), (mode, fdm)
+        if mode == "fdm":
+            top = sim.query(SIM_Q_TAIL_NX)
+            assert sim.query(SIM_Q_TAIL_NZ) == top and top ** 3 <= 4096, top
+        out[mode] = ({k: sim.get(k) for k in ("U", "W", "Z", "P")},
+                     sim.query(SIM_Q_ITERS_PRED) + sim.query(SIM_Q_ITERS_CORR))
+        sim.close()
+    assert out["fdm"][1] <= out["tail"][1], (out["fdm"][1], out["tail"][1])
+    for k in out["fdm"][0]:
+        assert rel(out["fdm"][0][k], out["tail"][0][k]) <= 1e-9, k
