@@ -14,6 +14,34 @@ enum BcKind : int { BC_PERIODIC = 0, BC_INFLOW = 1, BC_OUTFLOW = 2, BC_WALL = 3,
 // Grid geometry.  Cell fields live in a padded array with one ghost layer on
 // each side of every active direction (ghost index 0 and n+1, interior 1..n),
 // x fastest.  In 2D the z extent is 1 and has no ghosts.
+// Unsigned 32-bit division by an invariant divisor as a multiply-high and two
+// shifts (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, Fig. 4.1): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0)
+// where t = mulhi(m, n), exact for every 32-bit n.  Cell indices stay below
+// 2^32, so the index maps below need no 64-bit division.
+struct DivU32 {
+    unsigned m;
+    int s1, s2;
+};
+inline DivU32 make_divu32(unsigned d) {
+    int l = 0;
+    while ((1ULL << l) < d) ++l;
+    DivU32 f;
+    f.m = (unsigned)(((1ULL << 32) * ((1ULL << l) - d)) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+__host__ __device__ __forceinline__ unsigned divu32(unsigned n, const DivU32& f) {
+#ifdef __CUDA_ARCH__
+    const unsigned t = __umulhi(f.m, n);
+#else
+    const unsigned t = (unsigned)(((unsigned long long)f.m * n) >> 32);
+#endif
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 struct Geom {
     int dim;
     int n[3];        // interior cells (n[2] = 1 in 2D)
@@ -26,23 +54,25 @@ struct Geom {
     double ih2[3];   // 1 / h^2
     double dV;       // cell volume
     int periodic[3];
+    DivU32 dn0, dn1; // division by n[0], n[1] (interior index maps)
+    DivU32 dp0, dp1; // division by p[0], p[1] (padded index maps)
 };
 
 // Interior linear index t (x fastest over the interior) -> padded index.
-__host__ __device__ inline long long pad_index(const Geom& g, long long t) {
-    int i = (int)(t % g.n[0]);
-    long long r = t / g.n[0];
-    int j = (int)(r % g.n[1]);
-    int k = (int)(r / g.n[1]);
-    long long kz = (g.dim == 3) ? (k + 1) : 0;
-    return (long long)(i + 1) + (long long)(j + 1) * g.s[1] + kz * g.s[2];
+__host__ __device__ inline void interior_coords(const Geom& g, long long t, int c[3]) {
+    const unsigned tt = (unsigned)t;
+    const unsigned r = divu32(tt, g.dn0);
+    const unsigned k = divu32(r, g.dn1);
+    c[0] = (int)(tt - r * (unsigned)g.n[0]);
+    c[1] = (int)(r - k * (unsigned)g.n[1]);
+    c[2] = (int)k;
 }
 
-__host__ __device__ inline void interior_coords(const Geom& g, long long t, int c[3]) {
-    c[0] = (int)(t % g.n[0]);
-    long long r = t / g.n[0];
-    c[1] = (int)(r % g.n[1]);
-    c[2] = (int)(r / g.n[1]);
+__host__ __device__ inline long long pad_index(const Geom& g, long long t) {
+    int c[3];
+    interior_coords(g, t, c);
+    const long long kz = (g.dim == 3) ? (c[2] + 1) : 0;
+    return (long long)(c[0] + 1) + (long long)(c[1] + 1) * g.s[1] + kz * g.s[2];
 }
 
 // Physical constants of a run (paper notation), derived once on the host.

@@ -153,6 +153,10 @@ Geom make_geom(const sim_params_t* p) {
     g.ncell = (long long)g.n[0] * g.n[1] * g.n[2];
     g.dV = 1.0;
     for (int d = 0; d < p->dim; ++d) g.dV *= g.h[d];
+    g.dn0 = make_divu32((unsigned)g.n[0]);
+    g.dn1 = make_divu32((unsigned)g.n[1]);
+    g.dp0 = make_divu32((unsigned)g.p[0]);
+    g.dp1 = make_divu32((unsigned)g.p[1]);
     return g;
 }
 

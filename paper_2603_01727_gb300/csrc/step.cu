@@ -21,10 +21,12 @@ namespace {
 constexpr int NT = kThreads;
 
 __device__ __forceinline__ void padded_coords(const Geom& g, long long c, int q[3]) {
-    q[0] = (int)(c % g.p[0]);
-    long long r = c / g.p[0];
-    q[1] = (int)(r % g.p[1]);
-    q[2] = (int)(r / g.p[1]);
+    const unsigned cc = (unsigned)c;
+    const unsigned r = divu32(cc, g.dp0);
+    const unsigned k = divu32(r, g.dp1);
+    q[0] = (int)(cc - r * (unsigned)g.p[0]);
+    q[1] = (int)(r - k * (unsigned)g.p[1]);
+    q[2] = (int)k;
 }
 
 // Slab position (the two other padded coordinates) of padded cell c for direction d.
@@ -397,6 +399,19 @@ __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, con
 // 2D the fourth block costs spills (slower back to back with warm caches) but
 // hides the DRAM latency of the step's first kernel after a cold L2 better, and
 // a 131k-cell grid fits one wave (slot 256x512 step 1.000 -> 0.993 ms).
+// The interior -> padded index map with 64-bit division, kept for the 3D
+// stage stencil only: at its 80-register cap the compiler spills 96 bytes with
+// this form and 524 with the 32-bit invariant-divisor map (measured 2.32 vs
+// 2.55 ms per 192^3 launch); every other kernel uses pad_index.
+__device__ __forceinline__ long long pad_index_div64(const Geom& g, long long t) {
+    const int i = (int)(t % g.n[0]);
+    const long long r = t / g.n[0];
+    const int j = (int)(r % g.n[1]);
+    const int k = (int)(r / g.n[1]);
+    const long long kz = (g.dim == 3) ? (k + 1) : 0;
+    return (long long)(i + 1) + (long long)(j + 1) * g.s[1] + kz * g.s[2];
+}
+
 template <int DIM, class C>
 struct ResidMinBlocks {
     static constexpr int v = 2;
@@ -414,7 +429,7 @@ template <int DIM, class C>
 __global__ void __launch_bounds__(NT, ResidMinBlocks<DIM, C>::v) k_residual(Geom g, Phys ph, ResidArgs a) {
     const long long t = (long long)blockIdx.x * NT + threadIdx.x;
     if (t >= g.ncell) return;
-    const long long c = pad_index(g, t);
+    const long long c = (DIM == 3) ? pad_index_div64(g, t) : pad_index(g, t);
     const double* Rrd[5];
     double* Rst[5];
 #pragma unroll
