@@ -161,35 +161,59 @@ __device__ __forceinline__ double temperature(const Phys& ph, double z, double h
 // is ~18x smaller than F in air) needs FP64, is FP64 everywhere.
 constexpr double kStoichBand = 6.5;
 
+// The band test and the FP32 argument use the leading 24 bits of |x| taken
+// from its bit pattern (FF split), and the FP32 value returns through bit
+// operations: the FP64 pipe (1/64 of the FP32 rate) sees only the affine part.
 __device__ __forceinline__ double temperature_mixed(const Phys& ph, double z, double h) {
-    const double ax = fabs(ph.k * (z - 1.0));
+    const double zm1 = z - 1.0;
+    const double ax = fabs(ph.k * zm1);
+    const float axf = FF(ax).hi;
     double L;
-    if (ax < kStoichBand) L = log1p(exp(-2.0 * ax));
-    else L = (double)log1pf(expf(-2.0f * (float)ax));
-    return ph.cT * (ph.cA * (ax + L) + ph.cB * (z - 1.0) + h);
+    if (axf < (float)kStoichBand) L = log1p(exp(-2.0 * ax));
+    else L = f2d_bits(log1pf(expf(-2.0f * axf)));
+    return ph.cT * (ph.cA * (ax + L) + ph.cB * zm1 + h);
 }
 
-// 1/T to FP64 accuracy from an FP32 reciprocal and one Newton step
-// (y <- y + y (1 - T y) doubles the ~24 correct bits).
+// 1/T to FP64 accuracy: an FP32 reciprocal of the split's leading part, one
+// FP32 Newton step against both parts (y to ~2^-24 relative), then one FP64
+// Newton step (y <- y + y (1 - T y) squares the error: ~4e-15).  The FP32
+// operand and result cross by bit operations.
 __device__ __forceinline__ double recip_newton(double T) {
-    const double y = (double)(1.0f / (float)T);
-    return fma(y, fma(-T, y, 1.0), y);
+    const FF t(T);
+    float y = __frcp_rn(t.hi);
+    y = fmaf(y, fmaf(-t.lo, y, fmaf(-t.hi, y, 1.0f)), y);
+    const double yd = f2d_bits(y);
+    return fma(yd, fma(-T, yd, 1.0), yd);
 }
 
 // kappa = T^sigma (Eq 2.50) in the mixed path.  For the paper's sigma = 7/10:
 // y0 = powf(T, 0.7) (FP32), then with delta = T^7 / y0^10 - 1 (~1e-7) the exact
-// y = y0 (1 + delta)^(1/10) = y0 (1 + delta/10 - 0.045 delta^2 + O(delta^3)),
-// evaluated in FP64 (T^7 and y0^10 by repeated squaring, the quotient through
-// a Newton-refined reciprocal): FP64-accurate kappa without an FP64 pow, so
-// kappa carries no FP32 rounding noise into the diffusion-flux differences.
-// Other exponents use the FP64 pow.
+// y = y0 (1 + delta)^(1/10) = y0 (1 + delta/10 - 0.045 delta^2 + O(delta^3)).
+// T^7 and y0^10 (repeated squaring) and their quotient are float-float (about
+// 2^-46 relative per operation, eight of them: delta to ~1e-13 and kappa to
+// ~1e-14 relative, measured 2e-14 against the FP64 pow); the
+// correction y0 (delta/10 - 0.045 delta^2), ~1e-8 of y0, is FP32, and y0 plus
+// it is exact as a float pair.  Only the final pair-to-double sum uses the
+// FP64 pipe, so kappa carries no FP32 rounding noise into the diffusion-flux
+// differences at a fraction of an FP64 pow's cost.  Other exponents use the
+// FP64 pow.
 __device__ __forceinline__ double kappa_mixed(const Phys& ph, double T) {
     if (!ph.sigma_is_07) return pow(T, ph.sigma);
-    const double y0 = (double)powf((float)T, 0.7f);
-    const double T2 = T * T, T4 = T2 * T2, T7 = T4 * T2 * T;
-    const double y2 = y0 * y0, y4 = y2 * y2, y8 = y4 * y4, y10 = y8 * y2;
-    const double delta = fma(T7, recip_newton(y10), -1.0);
-    return fma(y0, delta * fma(-0.045, delta, 0.1), y0);
+    const FF t(T);
+    const float y0 = powf(t.hi, 0.7f);
+    const FF t2 = t * t, t4 = t2 * t2, t7 = t4 * t2 * t;
+    const FF y(y0, 0.f);
+    const FF y2 = y * y, y4 = y2 * y2, y8 = y4 * y4, y10 = y8 * y2;
+    const float delta = (t7 / y10 - FF(1.f, 0.f)).hi;
+    const FF k = ff_fast_two_sum(y0, y0 * (delta * fmaf(-0.045f, delta, 0.1f)));
+    return f2d_bits(k.hi) + f2d_bits(k.lo);
+}
+
+// T > 0 and T < 1e300 (not NaN) from the bit pattern: positive doubles order
+// as their bits, so no FP64 comparison is issued.
+__device__ __forceinline__ bool temperature_ok(double T) {
+    const long long b = __double_as_longlong(T);
+    return b > 0 && b < 0x7e37e43c8800759cLL;   // the bits of 1e300
 }
 
 template <bool MIXED>
@@ -228,7 +252,7 @@ __global__ void k_state(Geom g, Phys ph, const double* __restrict__ Z, const dou
         }
         if (!ph.closed) rho[c] = iT;        // p0 = 1 (Eq 2.41), rho = p0 / T (Eq 2.49)
         acc += iT;
-        if (!(Tv > 0.0) || !(Tv < 1e300)) bad = 1;
+        if (MIXED ? !temperature_ok(Tv) : (!(Tv > 0.0) || !(Tv < 1e300))) bad = 1;
     }
     if (bad) atomicOr(status, ST_NAN);
     acc = block_sum<NT>(acc, sm);

@@ -374,3 +374,32 @@ def test_3d_fast_diagonalisation_top_level_matches_vcycle_tail(n, periodic_x, mo
     assert out["fdm"][1] <= out["tail"][1], (out["fdm"][1], out["tail"][1])
     for k in out["fdm"][0]:
         assert rel(out["fdm"][0][k], out["tail"][0][k]) <= 1e-9, k
+
+
+@pytest.mark.parametrize("case", ["slot", "sphere"])
+def test_mixed_state_relation_is_fp64_accurate(case):
+    """The mixed path's state relation evaluates kappa = T^0.7 with a
+    float-float correction of an FP32 seed and rho = p0 / T with FP32
+    reciprocal steps and one FP64 Newton step; both must match the FP64
+    formulas of the stored T far below the FP32 rounding (~6e-8) they replace.
+    Bounds: kappa's correction delta = T^7 / y0^10 - 1 comes from eight
+    float-float products and a quotient, each ~2^-46 relative, so delta is
+    good to ~1e-13 and kappa = y0 (1 + delta/10 + ...) to ~1e-14; one FP64
+    Newton step from a seed within ~2^-24 leaves ~2^-48 (plus rounding)."""
+    from paper_2603_01727_gb300.lowmach import SIM_Q_P0
+    if case == "slot":
+        prm, geo, f = W.slot_burner(64, 128)
+    else:
+        prm, geo, f = W.sphere_burner(24)
+    prm["precision"] = W.MIXED
+    sim = gpu_run(prm, geo, f, 3)
+    T = sim.get("T")
+    kap = sim.get("KAPPA")
+    rho = sim.get("RHO")
+    p0 = sim.query(SIM_Q_P0)
+    assert np.all(T > 0.0)
+    ek = np.max(np.abs(kap / T ** 0.7 - 1.0))
+    er = np.max(np.abs(rho * T / p0 - 1.0))
+    assert ek < 1e-13, ek          # measured 2e-14; an FP32 kappa would be ~6e-8
+    assert er < 1e-14, er          # measured 3.6e-15
+    sim.close()
