@@ -510,6 +510,15 @@ __global__ void __launch_bounds__(NT, ResidMinBlocks<DIM, C>::v) k_residual(Geom
 // Interface mass fluxes of the provisional momentum (first term of Eq 3.23) and
 // block partials of the global mass balance (Eq 3.24 + S_m, Eq 3.33).
 // ----------------------------------------------------------------------------
+// s / 2 without the FP64 pipe: a normal double halves exactly by decrementing
+// its exponent field; zero, subnormal, infinite and NaN values take the FP64
+// multiply (bitwise the same result either way).
+__device__ __forceinline__ double half_exact(double s) {
+    const long long b = __double_as_longlong(s);
+    const int e = (int)((b >> 52) & 0x7ff);
+    return (e > 1 && e < 0x7ff) ? __longlong_as_double(b - (1LL << 52)) : s * 0.5;
+}
+
 template <int DIM>
 __global__ void k_face_flux(Geom g, Phys ph, Bnd bnd, FluxArgs a) {
     __shared__ double sm[NT / 32];
@@ -525,6 +534,7 @@ __global__ void k_face_flux(Geom g, Phys ph, Bnd bnd, FluxArgs a) {
             const double drho = (a.bdf_c0 * a.rho_new[c] + a.bdf_c1 * a.rho_n[c] +
                                  (a.bdf_c2 != 0.0 ? a.bdf_c2 * a.rho_prev[c] : 0.0)) * iden;
             const double Sm = a.Sm ? a.Sm[c] : 0.0;
+            a.b[t] = drho - Sm;   // completed by k_rhs with the flux divergence
             acc += (drho - Sm) * g.dV;
         }
 #pragma unroll
@@ -535,7 +545,7 @@ __global__ void k_face_flux(Geom g, Phys ph, Bnd bnd, FluxArgs a) {
             const double dA = g.dV * g.ih[j];
             if (ct[j] > 0 || g.periodic[j]) {
                 const long long cl = (ct[j] > 0) ? c - s : c + (long long)(n - 1) * s;
-                a.F[j][c] = 0.5 * (m[cl] + m[c]);
+                a.F[j][c] = half_exact(m[cl] + m[c]);
             } else {
                 const int kind = bnd.kind[j][0][slab_index(g, j, q)];
                 const double val = (kind == BC_INFLOW) ? rho_in * ph.inflow_v[j] : (kind == BC_OUTFLOW) ? m[c] : 0.0;
@@ -544,7 +554,7 @@ __global__ void k_face_flux(Geom g, Phys ph, Bnd bnd, FluxArgs a) {
             }
             if (ct[j] == n - 1) {
                 if (g.periodic[j]) {
-                    a.F[j][c + s] = 0.5 * (m[c] + m[c - (long long)(n - 1) * s]);
+                    a.F[j][c + s] = half_exact(m[c] + m[c - (long long)(n - 1) * s]);
                 } else {
                     const int kind = bnd.kind[j][1][slab_index(g, j, q)];
                     const double val =
@@ -567,16 +577,12 @@ __global__ void k_rhs(Geom g, Bnd bnd, FluxArgs a, int np) {
     const double total = sum_partials<NT>(a.part, np, sm);
     const double area = a.sc[SC_OUT_AREA];
     const double shift = (area > 0.0) ? -total / area : 0.0;
-    const double iden = 1.0 / a.bdf_den;
     for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
         const long long c = pad_index(g, t);
         int ct[3], q[3];
         interior_coords(g, t, ct);
         padded_coords(g, c, q);
-        const double drho = (a.bdf_c0 * a.rho_new[c] + a.bdf_c1 * a.rho_n[c] +
-                             (a.bdf_c2 != 0.0 ? a.bdf_c2 * a.rho_prev[c] : 0.0)) * iden;
-        const double Sm = a.Sm ? a.Sm[c] : 0.0;
-        double b = drho - Sm;
+        double b = a.b[t];   // d_t rho - S_m, stored by k_face_flux
 #pragma unroll
         for (int j = 0; j < DIM; ++j) {
             const long long s = g.s[j];
