@@ -3038,12 +3038,29 @@ cudaError_t poisson_enqueue_body(PoissonPlan* pl, double* x, cudaStream_t s, uns
 }
 
 cudaError_t poisson_enqueue_epilogue(PoissonPlan* pl, double* x, cudaStream_t s, double* rep, int* status,
-                                     int status_bit) {
+                                     int status_bit, int remove_mean) {
+    if (!remove_mean) {
+        // the report alone (one block, no pass over x); a batch reports separately
+        if (pl->nb == 1) {
+            launch(k_sub_mean, dim3(1, 1), NTV, 0, s, x, 0LL, (const double*)pl->scal, (const int*)pl->ictl, rep,
+                   status, status_bit);
+            pl->launches += 1;
+        }
+        return cudaGetLastError();
+    }
     const dim3 rb(reduce_blocks(pl->N), pl->nb);
     launch(k_mean, rb, NTV, 0, s, (const double*)x, pl->N, pl->part0, pl->scal, PS_MEANX, pl->cnt + CNT_MEANX);
     launch(k_sub_mean, rb, NTV, 0, s, x, pl->N, (const double*)pl->scal, (const int*)pl->ictl,
            pl->nb > 1 ? nullptr : rep, pl->nb > 1 ? nullptr : status, status_bit);
     pl->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t poisson_enqueue_remove_mean(PoissonPlan* pl, double* x, cudaStream_t s) {
+    const dim3 rb(reduce_blocks(pl->N), 1);
+    launch(k_mean, rb, NTV, 0, s, (const double*)x, pl->N, pl->part0, pl->scal, PS_MEANX, pl->cnt + CNT_MEANX);
+    launch(k_sub_mean, rb, NTV, 0, s, x, pl->N, (const double*)pl->scal, (const int*)pl->ictl, (double*)nullptr,
+           (int*)nullptr, 0);
     return cudaGetLastError();
 }
 
@@ -3096,7 +3113,7 @@ cudaError_t poisson_solve_host_loop(PoissonPlan* pl, const double* b, double* x,
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
     }
-    return poisson_enqueue_epilogue(pl, x, s, nullptr, nullptr, 0);
+    return poisson_enqueue_epilogue(pl, x, s, nullptr, nullptr, 0, 1);
 }
 
 }  // namespace lm

@@ -166,10 +166,14 @@ bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& minv_host
 cudaError_t poisson_enqueue_prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s,
                                      unsigned long long graph_handle);
 cudaError_t poisson_enqueue_body(PoissonPlan* pl, double* x, cudaStream_t s, unsigned long long graph_handle);
-// Zero-mean x; optionally report iterations / relative residual into
-// rep[0], rep[1] and OR status_bit into *status on non-convergence.
+// Zero-mean x (remove_mean; the solve itself keeps x's mean, since every
+// correction is zero-mean, up to rounding); optionally report iterations /
+// relative residual into rep[0], rep[1] and OR status_bit into *status on
+// non-convergence.
 cudaError_t poisson_enqueue_epilogue(PoissonPlan* pl, double* x, cudaStream_t s, double* rep, int* status,
-                                     int status_bit);
+                                     int status_bit, int remove_mean);
+// x -= mean(x) on one system of the plan's grid (its scratch words).
+cudaError_t poisson_enqueue_remove_mean(PoissonPlan* pl, double* x, cudaStream_t s);
 // Single kernels for timing (scratch only): 0 = fine-level down sweep,
 // 1 = CG direction update + operator application, 2 = fine-level up sweep,
 // 3 = coarse-level tail.

@@ -463,7 +463,9 @@ sim_status launch_solve_graph(sim_t* s, int which, cudaStream_t st) {
         int body = 0;
         pl->launches = 0;
         cudaError_t e = capture_while_solve(pl, b, x, s->cap, s->side, &body);
-        if (e == cudaSuccess) e = poisson_enqueue_epilogue(pl, x, s->cap, rep, s->status, ST_NOCONV);
+        // P keeps the rounding-level mean the solve leaves (only its differences
+        // act; sim_get removes it); the adjoint's transposed solve is zero-mean
+        if (e == cudaSuccess) e = poisson_enqueue_epilogue(pl, x, s->cap, rep, s->status, ST_NOCONV, which == 2);
         s->solve_body[which] = body;
         s->solve_fixed[which] = pl->launches - body;
         cudaGraph_t graph = nullptr;
@@ -517,9 +519,11 @@ cudaError_t enqueue_poisson(sim_t* s, cudaStream_t st, bool graph, int iter_slot
         e = capture_while_solve(pl, s->b, s->P, st, s->side, body_launch);
         if (e != cudaSuccess) return e;
     }
-    // zero mean; iterations / residual into the step's scalar slots and
-    // non-convergence into the status word
-    e = poisson_enqueue_epilogue(pl, s->P, st, s->sc + iter_slot, s->status, ST_NOCONV);
+    // iterations / residual into the step's scalar slots and non-convergence
+    // into the status word; P keeps the rounding-level mean the solve leaves
+    // (every correction is zero-mean; only P's differences act), sim_get
+    // removes it
+    e = poisson_enqueue_epilogue(pl, s->P, st, s->sc + iter_slot, s->status, ST_NOCONV, 0);
     if (e != cudaSuccess) return e;
     // in graph mode the body is counted per executed iteration at query time
     *L += graph ? pl->launches - *body_launch : pl->launches;
@@ -980,7 +984,10 @@ sim_status sim_fields(sim_t* s, int id, void* buf, int dir, int on_device) {
     } else if (id == SIM_FIELD_KAPPA) {
         launch_pack(g, s->kap, s->io, -1, st);
     } else if (id == SIM_FIELD_P) {
+        // the zero-mean P of Eqs 3.17 / 3.24 (the stored P carries the
+        // rounding-level mean the solves leave)
         CK(cudaMemcpyAsync(s->io, s->P, cells, cudaMemcpyDeviceToDevice, st));
+        CK(poisson_enqueue_remove_mean(&s->pp, (double*)s->io, st));
     } else if (id >= SIM_FIELD_FX && id <= SIM_FIELD_FZ) {
         const int d = id - SIM_FIELD_FX;
         if (d >= D) return fail(s, SIM_EINVAL, "no z faces in 2D");
@@ -1441,7 +1448,7 @@ cudaError_t adj_poisson(sim_t* s, const double* lP, double* lb, cudaStream_t st)
         e = poisson_enqueue_body(pl, lb, st, 0ULL);
         if (e != cudaSuccess) return e;
     }
-    return poisson_enqueue_epilogue(pl, lb, st, s->adj.rep, s->status, ST_NOCONV);
+    return poisson_enqueue_epilogue(pl, lb, st, s->adj.rep, s->status, ST_NOCONV, 1);
 }
 
 ResidArgs adj_resid_args(sim_t* s, double* const* v, const double* Z, const double* H, const double* kap,
@@ -1902,7 +1909,7 @@ cudaError_t batch_group_solve(BatchGroup& G, int which) {
     int body = 0;
     cudaError_t e = capture_while_solve(&G.pl, G.bb, G.xb, G.st, G.side, &body);
     if (e != cudaSuccess) return e;
-    e = poisson_enqueue_epilogue(&G.pl, G.xb, G.st, nullptr, nullptr, 0);
+    e = poisson_enqueue_epilogue(&G.pl, G.xb, G.st, nullptr, nullptr, 0, 0);
     if (e != cudaSuccess) return e;
     launch_scatter(G.xb, G.xptr, N, nb, G.st);
     e = poisson_enqueue_batch_report(&G.pl, G.rep[which], G.status, ST_NOCONV, G.st);
