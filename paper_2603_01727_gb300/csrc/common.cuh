@@ -306,6 +306,25 @@ __device__ inline double sum_partials(const double* part, int npart, double* sme
     return block_sum<NT>(v, smem);
 }
 
+// Last block of a grid to arrive (nblocks blocks counting on *cnt).  The
+// block's partial sums are written by thread 0 before the call; thread 0
+// counts in with one acquire-release atomic at GPU scope, which publishes its
+// partials (release) and, in the last block, makes every other block's
+// published partials visible (acquire) before the block barrier hands them to
+// the block's other threads.  The last block resets *cnt.
+__device__ __forceinline__ unsigned int atomic_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ bool arrive_last_n(unsigned int* cnt, unsigned int nblocks) {
+    __shared__ int am_last;
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomic_add_acq_rel_gpu(cnt, 1u) == nblocks - 1u);
+    __syncthreads();
+    return am_last != 0;
+}
+
 constexpr int kThreads = 256;     // block size of the stencil / vector kernels
 constexpr int kMaxPartials = 2048; // capacity of a partial-sum buffer
 

@@ -194,25 +194,8 @@ __device__ __forceinline__ T prolong_at(const LvT<T>& C, const T* __restrict__ u
     return plane(0);
 }
 
-// Last block of a grid to arrive.  The block's partial sums are written by
-// thread 0 before the call; thread 0 counts in with one acquire-release atomic
-// at GPU scope, which publishes its partials (release) and, in the last block,
-// makes every other block's published partials visible (acquire) before the
-// block barrier hands them to the block's other threads.
-// arrive_last_n: the same among nblocks blocks (the blocks of one system of a
-// batch, which counts on that system's counter).
-__device__ __forceinline__ unsigned int atomic_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
-    unsigned int old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-__device__ __forceinline__ bool arrive_last_n(unsigned int* cnt, unsigned int nblocks) {
-    __shared__ int am_last;
-    __syncthreads();
-    if (threadIdx.x == 0) am_last = (atomic_add_acq_rel_gpu(cnt, 1u) == nblocks - 1u);
-    __syncthreads();
-    return am_last != 0;
-}
+// Last block of the whole grid to arrive (arrive_last_n, common.cuh, counts the
+// blocks of one system of a batch on that system's counter).
 __device__ __forceinline__ bool arrive_last(unsigned int* cnt) {
     return arrive_last_n(cnt, gridDim.x * gridDim.y * gridDim.z);
 }
@@ -2999,13 +2982,16 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
 
 template <int DIM>
 void prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s, cudaGraphConditionalHandle h,
-              int use_graph) {
+              int use_graph, int mean_ready) {
     const dim3 rb(reduce_blocks(pl->N), pl->nb);
-    launch(k_mean, rb, NTV, 0, s, b, pl->N, pl->part0, pl->scal, PS_MEANB, pl->cnt + CNT_MEANB);
+    if (!mean_ready) {
+        launch(k_mean, rb, NTV, 0, s, b, pl->N, pl->part0, pl->scal, PS_MEANB, pl->cnt + CNT_MEANB);
+        pl->launches += 1;
+    }
     const LvT<double> L = make_lv<double>(pl->lev[0], DIM);
     launch(k_pcg_init<DIM>, rb, NTV, 0, s, L, b, x, pl->r, pl->r32, pl->part1, pl->part2, pl->scal, pl->ictl,
                                        pl->cnt + CNT_INIT, pl->rtol, h, (pl->nb > 1) ? 0 : use_graph);
-    pl->launches += 2;
+    pl->launches += 1;
     if (pl->nb > 1) {
         launch(k_batch_cond, 1, NTV, 0, s, (const int*)pl->ictl, pl->nb, pl->bdone, h, use_graph);
         pl->launches += 1;
@@ -3015,13 +3001,19 @@ void prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s, cudaG
 }  // namespace
 
 cudaError_t poisson_enqueue_prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s,
-                                     unsigned long long graph_handle) {
+                                     unsigned long long graph_handle, int mean_ready) {
     const int use_graph = graph_handle != 0ULL;
     if (pl->dim == 3)
-        prologue<3>(pl, b, x, s, (cudaGraphConditionalHandle)graph_handle, use_graph);
+        prologue<3>(pl, b, x, s, (cudaGraphConditionalHandle)graph_handle, use_graph, mean_ready);
     else
-        prologue<2>(pl, b, x, s, (cudaGraphConditionalHandle)graph_handle, use_graph);
+        prologue<2>(pl, b, x, s, (cudaGraphConditionalHandle)graph_handle, use_graph, mean_ready);
     return cudaGetLastError();
+}
+
+void poisson_meanb_target(PoissonPlan* pl, double** part, unsigned int** cnt, double** out) {
+    *part = pl->part0;
+    *cnt = pl->cnt + CNT_MEANB;
+    *out = pl->scal + PS_MEANB;
 }
 
 cudaError_t poisson_enqueue_body(PoissonPlan* pl, double* x, cudaStream_t s, unsigned long long graph_handle) {
@@ -3100,7 +3092,7 @@ cudaError_t poisson_enqueue_batch_report(PoissonPlan* pl, double* const* rep, in
 }
 
 cudaError_t poisson_solve_host_loop(PoissonPlan* pl, const double* b, double* x, cudaStream_t s) {
-    cudaError_t e = poisson_enqueue_prologue(pl, b, x, s, 0ULL);
+    cudaError_t e = poisson_enqueue_prologue(pl, b, x, s, 0ULL, 0);
     if (e != cudaSuccess) return e;
     int done = 0;
     e = cudaMemcpyAsync(&done, poisson_done_flag(pl), sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -163,8 +163,13 @@ bool poisson_upload_coarse(PoissonPlan* pl, const std::vector<double>& minv_host
 // of each iteration sets the conditional of a while node when graph_handle != 0
 // (the body is then being captured into that node's body graph); with
 // graph_handle == 0 the loop is host-driven.
+// mean_ready: mean(b) is already in the plan's scratch word (written by the
+// kernel that formed b, through poisson_meanb_target), so no mean pass runs.
 cudaError_t poisson_enqueue_prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s,
-                                     unsigned long long graph_handle);
+                                     unsigned long long graph_handle, int mean_ready);
+// Where a kernel producing b can leave mean(b) for a single-system plan: its
+// block partials, its last-block counter and the scratch word.
+void poisson_meanb_target(PoissonPlan* pl, double** part, unsigned int** cnt, double** out);
 cudaError_t poisson_enqueue_body(PoissonPlan* pl, double* x, cudaStream_t s, unsigned long long graph_handle);
 // Zero-mean x (remove_mean; the solve itself keeps x's mean, since every
 // correction is zero-mean, up to rounding); optionally report iterations /

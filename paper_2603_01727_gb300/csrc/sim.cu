@@ -414,7 +414,7 @@ cudaError_t enqueue_init(sim_t* s, cudaStream_t st) {
 // st (being captured); the loop body is captured on side into the node's body
 // graph.  body_launch: kernels per iteration.
 cudaError_t capture_while_solve(PoissonPlan* pl, const double* b, double* x, cudaStream_t st, cudaStream_t side,
-                                int* body_launch) {
+                                int* body_launch, int mean_ready) {
     cudaStreamCaptureStatus cs;
     cudaGraph_t graph_h;
     const cudaGraphNode_t* deps = nullptr;
@@ -424,7 +424,7 @@ cudaError_t capture_while_solve(PoissonPlan* pl, const double* b, double* x, cud
     cudaGraphConditionalHandle h;
     e = cudaGraphConditionalHandleCreate(&h, graph_h, 1, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) return e;
-    e = poisson_enqueue_prologue(pl, b, x, st, (unsigned long long)h);
+    e = poisson_enqueue_prologue(pl, b, x, st, (unsigned long long)h, mean_ready);
     if (e != cudaSuccess) return e;
     e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph_h, &deps, nullptr, &ndeps);
     if (e != cudaSuccess) return e;
@@ -462,7 +462,7 @@ sim_status launch_solve_graph(sim_t* s, int which, cudaStream_t st) {
         CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeRelaxed));
         int body = 0;
         pl->launches = 0;
-        cudaError_t e = capture_while_solve(pl, b, x, s->cap, s->side, &body);
+        cudaError_t e = capture_while_solve(pl, b, x, s->cap, s->side, &body, which != 2);
         // P keeps the rounding-level mean the solve leaves (only its differences
         // act; sim_get removes it); the adjoint's transposed solve is zero-mean
         if (e == cudaSuccess) e = poisson_enqueue_epilogue(pl, x, s->cap, rep, s->status, ST_NOCONV, which == 2);
@@ -502,7 +502,7 @@ cudaError_t enqueue_poisson(sim_t* s, cudaStream_t st, bool graph, int iter_slot
         return ss == SIM_OK ? cudaGetLastError() : cudaErrorUnknown;
     }
     if (!graph) {
-        e = poisson_enqueue_prologue(pl, s->b, s->P, st, 0ULL);
+        e = poisson_enqueue_prologue(pl, s->b, s->P, st, 0ULL, 1);
         if (e != cudaSuccess) return e;
         int done = 0;
         for (int guard = 0; guard <= pl->max_iter + 1; ++guard) {
@@ -516,7 +516,7 @@ cudaError_t enqueue_poisson(sim_t* s, cudaStream_t st, bool graph, int iter_slot
             *body_launch = pl->launches - before;
         }
     } else {
-        e = capture_while_solve(pl, s->b, s->P, st, s->side, body_launch);
+        e = capture_while_solve(pl, s->b, s->P, st, s->side, body_launch, 1);
         if (e != cudaSuccess) return e;
     }
     // iterations / residual into the step's scalar slots and non-convergence
@@ -645,6 +645,9 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     fa.part = s->part;
     fa.b = s->b;
     fa.correct = 1;
+    // k_rhs leaves mean(b) in the plan's scratch word (the solve's prologue
+    // then runs no mean pass)
+    poisson_meanb_target(&s->pp, &fa.mb_part, &fa.mb_cnt, &fa.mb_out);
     if (on(SEC_PRED)) launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
     cudaError_t e = cudaSuccess;
     if (on(SEC_POIS_PRED)) e = enqueue_poisson(s, st, graph, SC_ITERS_PRED, L, body);
@@ -1437,7 +1440,7 @@ cudaError_t adj_poisson(sim_t* s, const double* lP, double* lb, cudaStream_t st)
     if (s->solve_graphs && lP == s->adj.LP && lb == s->adj.Lb)
         return launch_solve_graph(s, 2, st) == SIM_OK ? cudaGetLastError() : cudaErrorUnknown;
     PoissonPlan* pl = &s->pp;
-    cudaError_t e = poisson_enqueue_prologue(pl, lP, lb, st, 0ULL);
+    cudaError_t e = poisson_enqueue_prologue(pl, lP, lb, st, 0ULL, 0);
     if (e != cudaSuccess) return e;
     int done = 0;
     for (int guard = 0; guard <= pl->max_iter + 1; ++guard) {
@@ -1907,7 +1910,7 @@ cudaError_t batch_group_solve(BatchGroup& G, int which) {
     launch_gather(G.bptr, G.bb, N, nb, G.st);
     launch_gather((const double* const*)G.xptr, G.xb, N, nb, G.st);
     int body = 0;
-    cudaError_t e = capture_while_solve(&G.pl, G.bb, G.xb, G.st, G.side, &body);
+    cudaError_t e = capture_while_solve(&G.pl, G.bb, G.xb, G.st, G.side, &body, 0);
     if (e != cudaSuccess) return e;
     e = poisson_enqueue_epilogue(&G.pl, G.xb, G.st, nullptr, nullptr, 0, 0);
     if (e != cudaSuccess) return e;

@@ -577,6 +577,7 @@ __global__ void k_rhs(Geom g, Bnd bnd, FluxArgs a, int np) {
     const double total = sum_partials<NT>(a.part, np, sm);
     const double area = a.sc[SC_OUT_AREA];
     const double shift = (area > 0.0) ? -total / area : 0.0;
+    double bsum = 0.0;
     for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
         const long long c = pad_index(g, t);
         int ct[3], q[3];
@@ -594,6 +595,22 @@ __global__ void k_rhs(Geom g, Bnd bnd, FluxArgs a, int np) {
             b = b + (a.F[j][c + s] - a.F[j][c]) * g.ih[j];
         }
         a.b[t] = b;
+        bsum += b;
+    }
+    if (a.mb_out) {
+        // mean(b) for the pressure solve, with the block decomposition and the
+        // fixed-order sums of the solver's own mean pass (bitwise the same)
+        bsum = block_sum<NT>(bsum, sm);
+        if (threadIdx.x == 0) a.mb_part[blockIdx.x] = bsum;
+        if (arrive_last_n(a.mb_cnt, gridDim.x)) {
+            double v = 0.0;
+            for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) v += __ldcg(a.mb_part + i);
+            v = block_sum<NT>(v, sm);
+            if (threadIdx.x == 0) {
+                *a.mb_out = v / (double)g.ncell;
+                *a.mb_cnt = 0u;
+            }
+        }
     }
 }
 

@@ -83,6 +83,11 @@ struct FluxArgs {
     double* part;            // partial sums of the global mass balance
     double* b;               // right-hand side (compact)
     int correct;             // 1: shift outflow fluxes, build b; 0: fluxes only (t = 0)
+    // k_rhs: mean(b) into *mb_out (block partials mb_part, last-block counter
+    // mb_cnt), when mb_out is not null
+    double* mb_part;
+    unsigned int* mb_cnt;
+    double* mb_out;
 };
 
 struct ProjArgs {
