@@ -593,8 +593,8 @@ RESIDUAL_FF_WARP_INSTR_PER_CELL = {2: 129.8, 3: 273.4}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 80.5 TFLOP/s
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel, by
 # (grid, precision, kernel); entries are removed when the kernel changes.
-# 256x512 slot, fine-level up (k2::up<float, float, 1, 2>): 1.214 MB read, 0 written
-NCU_TRAFFIC = {((256, 512), "mixed", "mg_up"): 1.214e6}
+# 256x512 slot, fine-level up (k2::up<float, float, 1, 2>): 1.2137 MB read, 0 written
+NCU_TRAFFIC = {((256, 512), "mixed", "mg_up"): 1.2137e6}
 
 
 def load_peaks():
