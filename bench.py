@@ -556,7 +556,8 @@ def roofline(res, peaks, precision):
         ach = wi / t / 1e12
         rl = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "T warp-instructions/s (issue)",
               "frac": ach / pk}
-        rl.update(kernel=top, launch_us=t * 1e6, share_of_step=share[top], traffic=None,
+        rl.update(kernel=top, launch_us=t * 1e6, share_of_step=share[top],
+                  traffic=NCU_TRAFFIC.get((tuple(res["cfg"].get("grid", ())), precision, top)),
                   peak_source="152 SMs x 4 warp instructions/clk x 2.07 GHz; instructions per cell "
                               f"{RESIDUAL_FF_WARP_INSTR_PER_CELL[dim]} measured by ncu",
                   shares={k: round(v, 4) for k, v in share.items()}, nlev=nlev)
@@ -593,8 +594,12 @@ RESIDUAL_FF_WARP_INSTR_PER_CELL = {2: 129.8, 3: 273.4}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 80.5 TFLOP/s
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel, by
 # (grid, precision, kernel); entries are removed when the kernel changes.
-# 256x512 slot, fine-level up (k2::up<float, float, 1, 2>): 1.2137 MB read, 0 written
-NCU_TRAFFIC = {((256, 512), "mixed", "mg_up"): 1.2137e6}
+# 256x512 slot, fine-level up (k2::up<float, float, 1, 2>): 1.2137 MB read, 0 written.
+# 192^3 sphere, float-float stage stencil (predictor launch): the 128^3 capture
+# (285.78 MB read + 146.88 MB written = 206.3 B per cell; its working set, like
+# 192^3's, exceeds L2, while 64^3 fits and is not proportional) scaled by cells.
+NCU_TRAFFIC = {((256, 512), "mixed", "mg_up"): 1.2137e6,
+               ((192, 192, 192), "mixed", "residual"): 432665856.0 / 128 ** 3 * 192 ** 3}
 
 
 def load_peaks():
