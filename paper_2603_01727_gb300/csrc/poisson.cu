@@ -101,11 +101,15 @@ struct Box {
     static constexpr int S1 = SX, S2 = SX * SY;   // shared-memory strides of y and z
 };
 
-__device__ __forceinline__ void coords(const int n[3], int t, int c[3]) {
-    c[0] = t % n[0];
-    const int r = t / n[0];
-    c[1] = r % n[1];
-    c[2] = r / n[1];
+// Compact index -> coordinates of a level by its invariant-divisor
+// multiplications (no integer division instruction sequence).
+template <class LV>
+__device__ __forceinline__ void coords(const LV& L, int t, int c[3]) {
+    const unsigned r = divu32((unsigned)t, L.dn0);
+    const unsigned k = divu32(r, L.dn1);
+    c[0] = (int)((unsigned)t - r * (unsigned)L.n[0]);
+    c[1] = (int)(r - k * (unsigned)L.n[1]);
+    c[2] = (int)k;
 }
 
 __device__ __forceinline__ int wrapi(int g, int n) {
@@ -698,7 +702,7 @@ __global__ void __launch_bounds__(NTV)
     double rr = 0.0;
     for (int t = blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
         int c[3];
-        coords(L.n, t, c);
+        coords(L, t, c);
         FF off;
         int stride = 1, p3 = 1, cl = 0;
 #pragma unroll
@@ -815,7 +819,7 @@ __global__ void __launch_bounds__(NTV)
     double ff = 0.0, rr = 0.0;
     for (int t = blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
         int c[3];
-        coords(L.n, t, c);
+        coords(L, t, c);
         int cl;
         const double off = off_compact<double, DIM>(L, x, t, c, &cl);
         const double f = -(b[t] - mean_b);
@@ -926,7 +930,7 @@ template <class T, int DIM>
 __device__ void tail_smooth_color(const LvT<T>& L, T* u, const T* f, int color) {
     for (int t = threadIdx.x; t < L.N; t += kTailThreads) {
         int c[3];
-        coords(L.n, t, c);
+        coords(L, t, c);
         if (((c[0] + c[1] + c[2]) & 1) != color) continue;
         int cl;
         const T off = off_compact<T, DIM>(L, u, t, c, &cl);
@@ -958,7 +962,7 @@ __global__ void __launch_bounds__(kTailThreads)
         T* fc = sm + a.off_f[l + 1];
         for (int t = threadIdx.x; t < L.N; t += kTailThreads) {
             int c[3];
-            coords(L.n, t, c);
+            coords(L, t, c);
             int cl = 0, p3 = 1;
             for (int d = 0; d < DIM; ++d) {
                 cl += (L.per[d] ? 2 : (int)(c[d] > 0) + (int)(c[d] < L.n[d] - 1)) * p3;
@@ -971,7 +975,7 @@ __global__ void __launch_bounds__(kTailThreads)
         __syncthreads();
         for (int t = threadIdx.x; t < L.N; t += kTailThreads) {
             int c[3];
-            coords(L.n, t, c);
+            coords(L, t, c);
             int cl;
             const T off = off_compact<T, DIM>(L, u, t, c, &cl);
             r[t] = f[t] - (L.diag[cl] * u[t] - off);
@@ -979,7 +983,7 @@ __global__ void __launch_bounds__(kTailThreads)
         __syncthreads();
         for (int T_ = threadIdx.x; T_ < C.N; T_ += kTailThreads) {
             int I[3];
-            coords(C.n, T_, I);
+            coords(C, T_, I);
             T acc = (T)0;
             const int az_n = (DIM == 3) ? 4 : 1;
             for (int az = 0; az < az_n; ++az) {
@@ -1027,7 +1031,7 @@ __global__ void __launch_bounds__(kTailThreads)
         const T* uc = sm + a.off_u[l + 1];
         for (int t = threadIdx.x; t < L.N; t += kTailThreads) {
             int c[3];
-            coords(L.n, t, c);
+            coords(L, t, c);
             u[t] += prolong_at<T, DIM>(C, uc, c);
         }
         __syncthreads();
@@ -2460,6 +2464,8 @@ LvT<T> make_lv(const MgLevel& L, int dim) {
         v.w[d] = (T)((d < dim) ? L.ih2[d] : 0.0);
     }
     v.N = (int)L.N;
+    v.dn0 = make_divu32((unsigned)L.n[0]);
+    v.dn1 = make_divu32((unsigned)L.n[1]);
     for (int c = 0; c < 27; ++c) {
         const int cnt[3] = {c % 3, (c / 3) % 3, c / 9};
         double diag = 0.0;

@@ -28,6 +28,7 @@ struct LvT {
     T w[3];
     T diag[27];
     T invd[27];
+    DivU32 dn0, dn1;   // division by n[0], n[1] (compact index -> coordinates)
 };
 
 // Host view of a level: shape plus its device arrays.
