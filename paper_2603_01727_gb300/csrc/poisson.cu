@@ -684,7 +684,7 @@ template <int DIM>
 __global__ void __launch_bounds__(NTV)
     k_ir_refine(LvT<double> L, double* __restrict__ x, double* __restrict__ r64, const float* __restrict__ e,
                 float* __restrict__ r32, double* part, double* scal, int* ictl, unsigned int* cnt, double rtol,
-                int max_iter, cudaGraphConditionalHandle h, int use_graph) {
+                int max_iter, cudaGraphConditionalHandle h, int use_graph, int vec4) {
     pdl_wait();
     pdl_trigger();
     const int fb = blockIdx.y;
@@ -700,7 +700,77 @@ __global__ void __launch_bounds__(NTV)
 #pragma unroll
     for (int d = 0; d < DIM; ++d) wd[d] = FF(L.w[d]);
     double rr = 0.0;
-    for (int t = blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
+    if (vec4) {
+        // four x-consecutive cells per thread step (nx % 4 == 0, x 16-byte
+        // aligned; the launch is sized by N / 4): one coordinate map, 16-byte
+        // loads of e's rows and of x, r64; each cell's arithmetic is the
+        // scalar path's, in its order
+        const int nx = L.n[0], ny = L.n[1];
+        const int N4 = L.N >> 2;
+        for (int q = blockIdx.x * NTV + threadIdx.x; q < N4; q += gridDim.x * NTV) {
+            const int t0 = 4 * q;
+            int c[3];
+            coords(L, t0, c);
+            const float4 ec = *reinterpret_cast<const float4*>(e + t0);
+            float el = 0.0f, er = 0.0f;
+            if (c[0] > 0) el = e[t0 - 1];
+            else if (L.per[0]) el = e[t0 + nx - 1];
+            if (c[0] + 4 < nx) er = e[t0 + 4];
+            else if (L.per[0]) er = e[t0 + 4 - nx];
+            float4 nb[2][2];   // [y, z][low, high] neighbour rows
+            int clo = 0, p3 = 3;
+#pragma unroll
+            for (int d = 1; d < DIM; ++d) {
+                const int n = L.n[d];
+                const int stride = (d == 1) ? nx : nx * ny;
+                nb[d - 1][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                nb[d - 1][1] = nb[d - 1][0];
+                if (c[d] > 0) nb[d - 1][0] = *reinterpret_cast<const float4*>(e + t0 - stride);
+                else if (L.per[d]) nb[d - 1][0] = *reinterpret_cast<const float4*>(e + t0 + (n - 1) * stride);
+                if (c[d] < n - 1) nb[d - 1][1] = *reinterpret_cast<const float4*>(e + t0 + stride);
+                else if (L.per[d]) nb[d - 1][1] = *reinterpret_cast<const float4*>(e + t0 - (n - 1) * stride);
+                clo += (L.per[d] ? 2 : (int)(c[d] > 0) + (int)(c[d] < n - 1)) * p3;
+                p3 *= 3;
+            }
+            const double2 ra = *reinterpret_cast<const double2*>(r64 + t0);
+            const double2 rb = *reinterpret_cast<const double2*>(r64 + t0 + 2);
+            const double2 xa = *reinterpret_cast<const double2*>(x + t0);
+            const double2 xb = *reinterpret_cast<const double2*>(x + t0 + 2);
+            const float ev[4] = {ec.x, ec.y, ec.z, ec.w};
+            const double rin[4] = {ra.x, ra.y, rb.x, rb.y};
+            const double xin[4] = {xa.x, xa.y, xb.x, xb.y};
+            double rout[4], xout[4];
+            float r32o[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float a0 = (i == 0) ? el : ev[i - 1];
+                const float b0 = (i == 3) ? er : ev[i + 1];
+                FF off;
+                off += wd[0] * (FF(a0, 0.0f) + FF(b0, 0.0f));
+#pragma unroll
+                for (int d = 1; d < DIM; ++d) {
+                    const float4 lo = nb[d - 1][0], hi = nb[d - 1][1];
+                    const float a = (i == 0) ? lo.x : (i == 1) ? lo.y : (i == 2) ? lo.z : lo.w;
+                    const float b = (i == 0) ? hi.x : (i == 1) ? hi.y : (i == 2) ? hi.z : hi.w;
+                    off += wd[d] * (FF(a, 0.0f) + FF(b, 0.0f));
+                }
+                const int xg = c[0] + i;
+                const int cl = (L.per[0] ? 2 : (int)(xg > 0) + (int)(xg < nx - 1)) + clo;
+                const FF Ae = FF(L.diag[cl]) * FF(ev[i], 0.0f) - off;
+                const FF rv = FF(rin[i]) - Ae;
+                xout[i] = xin[i] + f2d_bits(ev[i]);
+                rout[i] = f2d_bits(rv.hi) + f2d_bits(rv.lo);
+                r32o[i] = rv.hi;
+                rr = fma(rout[i], rout[i], rr);
+            }
+            *reinterpret_cast<double2*>(x + t0) = make_double2(xout[0], xout[1]);
+            *reinterpret_cast<double2*>(x + t0 + 2) = make_double2(xout[2], xout[3]);
+            *reinterpret_cast<double2*>(r64 + t0) = make_double2(rout[0], rout[1]);
+            *reinterpret_cast<double2*>(r64 + t0 + 2) = make_double2(rout[2], rout[3]);
+            *reinterpret_cast<float4*>(r32 + t0) = make_float4(r32o[0], r32o[1], r32o[2], r32o[3]);
+        }
+    }
+    for (int t = vec4 ? L.N : blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
         int c[3];
         coords(L, t, c);
         FF off;
@@ -2982,8 +3052,12 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
         const dim3 rbu((pl->N % 4 == 0) ? reduce_blocks(pl->N / 4) : reduce_blocks(pl->N), pl->nb);
         launch(k_ir_update, rbu, NTV, 0, s, pl->e32, pl->r32, pl->p32[0], pl->p32[1], pl->q32, pl->N, pl->part0, pl->scal,
                                        pl->ictl, pl->cnt + CNT_UPD, pl->inner_tol, pl->inner_max, pl->max_iter, h, ug);
-        launch(k_ir_refine<DIM>, rb, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r, pl->e32, pl->r32, pl->part1,
-                                            pl->scal, pl->ictl, pl->cnt + CNT_REF, pl->rtol, pl->max_iter, h, ug);
+        // the reliable update runs four x-consecutive cells per thread step when
+        // nx % 4 == 0 and x (the caller's array) is 16-byte aligned
+        const int vec4 = (pl->lev[0].n[0] % 4 == 0) && (((uintptr_t)x & 15) == 0);
+        const dim3 rbr(vec4 ? reduce_blocks(pl->N / 4) : reduce_blocks(pl->N), pl->nb);
+        launch(k_ir_refine<DIM>, rbr, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r, pl->e32, pl->r32,
+               pl->part1, pl->scal, pl->ictl, pl->cnt + CNT_REF, pl->rtol, pl->max_iter, h, ug, vec4);
         pl->launches += 2;
     } else {
         // the update runs two cells per thread step when N is even and x (the
