@@ -737,9 +737,9 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     pa.gj = job_v(s, s->v);
     if (D == 3) pa.gj.nf = 0;
     if (on(SEC_END)) {
+        pa.rot = s->sc;   // the projection's block 0 rotates the p0 history at its end
         launch_project(g, s->ph, pa, st, L);
         if (D == 3) ghost_v(s, s->v, st, L);
-        launch_rotate_p0(s->sc, st, L);
     }
     return cudaGetLastError();
 }

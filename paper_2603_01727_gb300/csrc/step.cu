@@ -619,6 +619,16 @@ __global__ void k_rhs(Geom g, Bnd bnd, FluxArgs a, int np) {
 // a pressure term (Eq 3.23), v_i = (rho v~_i - delta_2 P / delta_2 x_i) / rho
 // (Eq 3.25) with P ghosts by quadratic extrapolation (Eqs 3.27-3.28).
 // ----------------------------------------------------------------------------
+// p0 history n-2 <- n-1 <- n <- n+1 (and the inverses) at the end of a step.
+__device__ __forceinline__ void rotate_p0(double* sc) {
+    sc[SC_P0_NM2] = sc[SC_P0_NM1];
+    sc[SC_P0_NM1] = sc[SC_P0_N];
+    sc[SC_P0_N] = sc[SC_P0_NEW];
+    sc[SC_P0_NM2 + SC_INV_OFF] = sc[SC_P0_NM1 + SC_INV_OFF];
+    sc[SC_P0_NM1 + SC_INV_OFF] = sc[SC_P0_N + SC_INV_OFF];
+    sc[SC_P0_N + SC_INV_OFF] = sc[SC_P0_NEW + SC_INV_OFF];
+}
+
 template <int DIM>
 __global__ void k_project(Geom g, Phys ph, ProjArgs a) {
     double vout[3];
@@ -652,6 +662,9 @@ __global__ void k_project(Geom g, Phys ph, ProjArgs a) {
         padded_coords(g, c, q);
         fill_ghosts_of(g, ph, a.bnd, a.gj, q, vout);
     }
+    // the step's last projection rotates the p0 history (it reads only the new
+    // p0, which the rotation leaves as it is)
+    if (a.rot && t == 0) rotate_p0(a.rot);
 }
 
 __global__ void k_momentum(Geom g, const double* __restrict__ rho, const double* v0, const double* v1,
@@ -680,14 +693,6 @@ __global__ void k_store_sum(const double* part, int np, double scale, double* ds
     if (threadIdx.x == 0) *dst = s * scale;
 }
 
-__global__ void k_rotate_p0(double* sc) {
-    sc[SC_P0_NM2] = sc[SC_P0_NM1];
-    sc[SC_P0_NM1] = sc[SC_P0_N];
-    sc[SC_P0_N] = sc[SC_P0_NEW];
-    sc[SC_P0_NM2 + SC_INV_OFF] = sc[SC_P0_NM1 + SC_INV_OFF];
-    sc[SC_P0_NM1 + SC_INV_OFF] = sc[SC_P0_N + SC_INV_OFF];
-    sc[SC_P0_N + SC_INV_OFF] = sc[SC_P0_NEW + SC_INV_OFF];
-}
 
 __global__ void k_copy_scalar(const double* src, double* dst, int n) {
     if (threadIdx.x < n) dst[threadIdx.x] = src[threadIdx.x];
@@ -1630,10 +1635,6 @@ void launch_store_sum(const double* part, int np, double scale, double* dst, cud
     ++*launches;
 }
 
-void launch_rotate_p0(double* sc, cudaStream_t s, int* launches) {
-    k_rotate_p0<<<1, 1, 0, s>>>(sc);
-    ++*launches;
-}
 
 void launch_copy_scalar(const double* src, double* dst, int n, cudaStream_t s, int* launches) {
     k_copy_scalar<<<1, 32, 0, s>>>(src, dst, n);

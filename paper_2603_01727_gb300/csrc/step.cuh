@@ -102,6 +102,7 @@ struct ProjArgs {
     double eA, eB, eC;       // quadratic extrapolation coefficients (Eq 3.28)
     Bnd bnd;                 // boundary kinds for the fused ghost fill of v
     GhostJob gj;             // v components to ghost-fill in the kernel (nf = 0: none)
+    double* rot;             // not null: rotate the p0 history in these scalars (the step's end)
 };
 
 // Fields read by the stage stencil, by loader id.
@@ -175,7 +176,6 @@ void launch_momentum(const Geom& g, const double* rho, double* const v[3], doubl
                      int* launches);
 void launch_sum(const Geom& g, const double* x, double* part, cudaStream_t s, int* launches);
 void launch_store_sum(const double* part, int np, double scale, double* dst, cudaStream_t s, int* launches);
-void launch_rotate_p0(double* sc, cudaStream_t s, int* launches);
 void launch_copy_scalar(const double* src, double* dst, int n, cudaStream_t s, int* launches);
 void launch_or_status(const int* src_flag, int bit, int* status, cudaStream_t s, int* launches);
 
