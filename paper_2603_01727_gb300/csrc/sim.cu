@@ -617,14 +617,6 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     a.bnd = s->bnd;
     a.gj = job_of(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}});
     if (D == 3) a.gj.nf = 0;   // 3D: separate ghost fills (the 3D kernels run faster without)
-    if (on(SEC_PRED)) {
-        launch_residual(g, s->ph, a, st, L);
-        if (D == 3) ghost(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}}, st, L);
-        launch_state(g, s->ph, s->Zs, s->Hs, s->T, r.rho_new, s->kap, s->sc, SC_P0_STAR, s->part, s->status, st, L,
-                     &s->bnd, D == 2);
-        if (D == 3) ghost(s, {{s->kap, GW_KAPPA}}, st, L);
-    }
-
     FluxArgs fa;
     std::memset(&fa, 0, sizeof(fa));
     for (int d = 0; d < D; ++d) {
@@ -648,7 +640,22 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     // k_rhs leaves mean(b) in the plan's scratch word (the solve's prologue
     // then runs no mean pass)
     poisson_meanb_target(&s->pp, &fa.mb_part, &fa.mb_cnt, &fa.mb_out);
-    if (on(SEC_PRED)) launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
+    // an open system (p0 = 1) forms its state and face fluxes in one kernel
+    const bool fuse = !s->ph.closed;
+    if (on(SEC_PRED)) {
+        launch_residual(g, s->ph, a, st, L);
+        if (D == 3) ghost(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}}, st, L);
+        if (fuse) {
+            launch_state_flux_rhs(g, s->ph, s->Zs, s->Hs, s->T, r.rho_new, s->kap, s->sc, s->status, s->bnd, D == 2,
+                                  fa, st, L);
+            if (D == 3) ghost(s, {{s->kap, GW_KAPPA}}, st, L);
+        } else {
+            launch_state(g, s->ph, s->Zs, s->Hs, s->T, r.rho_new, s->kap, s->sc, SC_P0_STAR, s->part, s->status, st,
+                         L, &s->bnd, D == 2);
+            if (D == 3) ghost(s, {{s->kap, GW_KAPPA}}, st, L);
+            launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
+        }
+    }
     cudaError_t e = cudaSuccess;
     if (on(SEC_POIS_PRED)) e = enqueue_poisson(s, st, graph, SC_ITERS_PRED, L, body);
     if (e != cudaSuccess) return e;
@@ -725,10 +732,16 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     if (on(SEC_MID)) {
         launch_residual(g, s->ph, c, st, L);
         if (D == 3) ghost(s, {{s->Z, GW_Z}, {s->H, GW_H}}, st, L);
-        launch_state(g, s->ph, s->Z, s->H, s->T, r.rho_new, s->kap, s->sc, SC_P0_NEW, s->part, s->status, st, L,
-                     &s->bnd, D == 2);
-        if (D == 3) ghost(s, {{s->kap, GW_KAPPA}}, st, L);
-        launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
+        if (fuse) {
+            launch_state_flux_rhs(g, s->ph, s->Z, s->H, s->T, r.rho_new, s->kap, s->sc, s->status, s->bnd, D == 2, fa,
+                                  st, L);
+            if (D == 3) ghost(s, {{s->kap, GW_KAPPA}}, st, L);
+        } else {
+            launch_state(g, s->ph, s->Z, s->H, s->T, r.rho_new, s->kap, s->sc, SC_P0_NEW, s->part, s->status, st, L,
+                         &s->bnd, D == 2);
+            if (D == 3) ghost(s, {{s->kap, GW_KAPPA}}, st, L);
+            launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
+        }
     }
     if (on(SEC_POIS_CORR)) e = enqueue_poisson(s, st, graph, SC_ITERS_CORR, L, body);
     if (e != cudaSuccess) return e;

@@ -216,43 +216,59 @@ __device__ __forceinline__ bool temperature_ok(double T) {
     return b > 0 && b < 0x7e37e43c8800759cLL;   // the bits of 1e300
 }
 
+// State relation at one cell (Eqs 2.49-2.51): T and kappa from Z, H (kappa's
+// ghost copies too when kj names them), rho = 1/T for an open system (p0 = 1,
+// Eq 2.41); returns 1/T and sets bad on an out-of-range temperature.
 template <bool MIXED>
-__global__ void k_state(Geom g, Phys ph, const double* __restrict__ Z, const double* __restrict__ H,
-                        double* __restrict__ T, double* __restrict__ rho, double* __restrict__ kap,
-                        double* __restrict__ part, int* status, double* sc, int p0_slot, Bnd bnd, int kap_ghosts) {
+__device__ __forceinline__ double state_cell(const Geom& g, const Phys& ph, const double* __restrict__ Z,
+                                             const double* __restrict__ H, double* __restrict__ T,
+                                             double* __restrict__ rho, double* __restrict__ kap, const Bnd& bnd,
+                                             const GhostJob& kj, int kap_ghosts, long long c, int& bad) {
+    double Tv, kv, iT;
+    if (ph.incompressible) {
+        Tv = 1.0;
+        kv = 1.0;
+        iT = 1.0;
+    } else if (MIXED) {
+        Tv = temperature_mixed(ph, Z[c], H[c]);
+        kv = kappa_mixed(ph, Tv);
+        iT = recip_newton(Tv);
+    } else {
+        Tv = temperature(ph, Z[c], H[c]);
+        kv = pow(Tv, ph.sigma);
+        iT = 1.0 / Tv;
+    }
+    T[c] = Tv;
+    kap[c] = kv;
+    if (kap_ghosts) {
+        int q[3];
+        padded_coords(g, c, q);
+        fill_ghosts_of(g, ph, bnd, kj, q, &kv);
+    }
+    if (!ph.closed) rho[c] = iT;        // p0 = 1 (Eq 2.41), rho = p0 / T (Eq 2.49)
+    if (MIXED ? !temperature_ok(Tv) : (!(Tv > 0.0) || !(Tv < 1e300))) bad = 1;
+    return iT;
+}
+
+__device__ __forceinline__ GhostJob kappa_job(double* kap) {
     GhostJob kj;
     kj.f[0] = kap;
     kj.what[0] = GW_KAPPA;
     kj.nf = 1;
+    return kj;
+}
+
+template <bool MIXED>
+__global__ void k_state(Geom g, Phys ph, const double* __restrict__ Z, const double* __restrict__ H,
+                        double* __restrict__ T, double* __restrict__ rho, double* __restrict__ kap,
+                        double* __restrict__ part, int* status, double* sc, int p0_slot, Bnd bnd, int kap_ghosts) {
+    const GhostJob kj = kappa_job(kap);
     __shared__ double sm[NT / 32];
     double acc = 0.0;
     int bad = 0;
     for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
         const long long c = pad_index(g, t);
-        double Tv, kv, iT;
-        if (ph.incompressible) {
-            Tv = 1.0;
-            kv = 1.0;
-            iT = 1.0;
-        } else if (MIXED) {
-            Tv = temperature_mixed(ph, Z[c], H[c]);
-            kv = kappa_mixed(ph, Tv);
-            iT = recip_newton(Tv);
-        } else {
-            Tv = temperature(ph, Z[c], H[c]);
-            kv = pow(Tv, ph.sigma);
-            iT = 1.0 / Tv;
-        }
-        T[c] = Tv;
-        kap[c] = kv;
-        if (kap_ghosts) {
-            int q[3];
-            padded_coords(g, c, q);
-            fill_ghosts_of(g, ph, bnd, kj, q, &kv);
-        }
-        if (!ph.closed) rho[c] = iT;        // p0 = 1 (Eq 2.41), rho = p0 / T (Eq 2.49)
-        acc += iT;
-        if (MIXED ? !temperature_ok(Tv) : (!(Tv > 0.0) || !(Tv < 1e300))) bad = 1;
+        acc += state_cell<MIXED>(g, ph, Z, H, T, rho, kap, bnd, kj, kap_ghosts, c, bad);
     }
     if (bad) atomicOr(status, ST_NAN);
     acc = block_sum<NT>(acc, sm);
@@ -519,6 +535,54 @@ __device__ __forceinline__ double half_exact(double s) {
     return (e > 1 && e < 0x7ff) ? __longlong_as_double(b - (1LL << 52)) : s * 0.5;
 }
 
+// Face fluxes of one cell (its low faces, and its high faces on the last layer)
+// and its term of the mass balance; rho_new_c = rho^{new} at the cell (read
+// only when a.correct), rho_in = inflow density, iden = 1 / bdf_den.
+template <int DIM>
+__device__ __forceinline__ double flux_cell(const Geom& g, const Phys& ph, const Bnd& bnd, const FluxArgs& a,
+                                            long long t, long long c, double rho_new_c, double rho_in,
+                                            double iden) {
+    double acc = 0.0;
+    int ct[3], q[3];
+    interior_coords(g, t, ct);
+    padded_coords(g, c, q);
+    if (a.correct) {
+        const double drho = (a.bdf_c0 * rho_new_c + a.bdf_c1 * a.rho_n[c] +
+                             (a.bdf_c2 != 0.0 ? a.bdf_c2 * a.rho_prev[c] : 0.0)) * iden;
+        const double Sm = a.Sm ? a.Sm[c] : 0.0;
+        a.b[t] = drho - Sm;   // completed by k_rhs with the flux divergence
+        acc += (drho - Sm) * g.dV;
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        const long long s = g.s[j];
+        const int n = g.n[j];
+        const double* m = a.mom[j];
+        const double dA = g.dV * g.ih[j];
+        if (ct[j] > 0 || g.periodic[j]) {
+            const long long cl = (ct[j] > 0) ? c - s : c + (long long)(n - 1) * s;
+            a.F[j][c] = half_exact(m[cl] + m[c]);
+        } else {
+            const int kind = bnd.kind[j][0][slab_index(g, j, q)];
+            const double val = (kind == BC_INFLOW) ? rho_in * ph.inflow_v[j] : (kind == BC_OUTFLOW) ? m[c] : 0.0;
+            a.F[j][c] = val;
+            acc += -val * dA;
+        }
+        if (ct[j] == n - 1) {
+            if (g.periodic[j]) {
+                a.F[j][c + s] = half_exact(m[c] + m[c - (long long)(n - 1) * s]);
+            } else {
+                const int kind = bnd.kind[j][1][slab_index(g, j, q)];
+                const double val =
+                    (kind == BC_INFLOW) ? rho_in * ph.inflow_v[j] : (kind == BC_OUTFLOW) ? m[c] : 0.0;
+                a.F[j][c + s] = val;
+                acc += val * dA;
+            }
+        }
+    }
+    return acc;
+}
+
 template <int DIM>
 __global__ void k_face_flux(Geom g, Phys ph, Bnd bnd, FluxArgs a) {
     __shared__ double sm[NT / 32];
@@ -527,46 +591,39 @@ __global__ void k_face_flux(Geom g, Phys ph, Bnd bnd, FluxArgs a) {
     double acc = 0.0;
     for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
         const long long c = pad_index(g, t);
-        int ct[3], q[3];
-        interior_coords(g, t, ct);
-        padded_coords(g, c, q);
-        if (a.correct) {
-            const double drho = (a.bdf_c0 * a.rho_new[c] + a.bdf_c1 * a.rho_n[c] +
-                                 (a.bdf_c2 != 0.0 ? a.bdf_c2 * a.rho_prev[c] : 0.0)) * iden;
-            const double Sm = a.Sm ? a.Sm[c] : 0.0;
-            a.b[t] = drho - Sm;   // completed by k_rhs with the flux divergence
-            acc += (drho - Sm) * g.dV;
-        }
-#pragma unroll
-        for (int j = 0; j < DIM; ++j) {
-            const long long s = g.s[j];
-            const int n = g.n[j];
-            const double* m = a.mom[j];
-            const double dA = g.dV * g.ih[j];
-            if (ct[j] > 0 || g.periodic[j]) {
-                const long long cl = (ct[j] > 0) ? c - s : c + (long long)(n - 1) * s;
-                a.F[j][c] = half_exact(m[cl] + m[c]);
-            } else {
-                const int kind = bnd.kind[j][0][slab_index(g, j, q)];
-                const double val = (kind == BC_INFLOW) ? rho_in * ph.inflow_v[j] : (kind == BC_OUTFLOW) ? m[c] : 0.0;
-                a.F[j][c] = val;
-                acc += -val * dA;
-            }
-            if (ct[j] == n - 1) {
-                if (g.periodic[j]) {
-                    a.F[j][c + s] = half_exact(m[c] + m[c - (long long)(n - 1) * s]);
-                } else {
-                    const int kind = bnd.kind[j][1][slab_index(g, j, q)];
-                    const double val =
-                        (kind == BC_INFLOW) ? rho_in * ph.inflow_v[j] : (kind == BC_OUTFLOW) ? m[c] : 0.0;
-                    a.F[j][c + s] = val;
-                    acc += val * dA;
-                }
-            }
-        }
+        acc += flux_cell<DIM>(g, ph, bnd, a, t, c, a.correct ? a.rho_new[c] : 0.0, rho_in, iden);
     }
     acc = block_sum<NT>(acc, sm);
     if (threadIdx.x == 0) a.part[blockIdx.x] = acc;
+}
+
+// Open system (p0 = 1): the state relation and the face fluxes of a stage in
+// one pass.  The flux needs rho^{new} only at its own cell, just computed, and
+// p0 = 1 for the inflow density (so the same bits as k_state then
+// k_face_flux); the state's sum of 1/T serves only the enclosed system's p0, so
+// the block partials are the mass balance's.
+template <int DIM, bool MIXED>
+__global__ void k_state_flux(Geom g, Phys ph, const double* __restrict__ Z, const double* __restrict__ H,
+                             double* __restrict__ T, double* __restrict__ rho, double* __restrict__ kap,
+                             int* status, double* sc, Bnd bnd, int kap_ghosts, FluxArgs a) {
+    const GhostJob kj = kappa_job(kap);
+    __shared__ double sm[NT / 32];
+    const double rho_in = ph.incompressible ? 1.0 : 1.0 / ph.rho_in_T;
+    const double iden = 1.0 / a.bdf_den;
+    double acc = 0.0;
+    int bad = 0;
+    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
+        const long long c = pad_index(g, t);
+        const double iT = state_cell<MIXED>(g, ph, Z, H, T, rho, kap, bnd, kj, kap_ghosts, c, bad);
+        acc += flux_cell<DIM>(g, ph, bnd, a, t, c, iT, rho_in, iden);
+    }
+    if (bad) atomicOr(status, ST_NAN);
+    acc = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = acc;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc[a.p0_slot] = 1.0;
+        sc[a.p0_slot + SC_INV_OFF] = 1.0;
+    }
 }
 
 // Uniform shift of the outflow fluxes closing the mass balance, then
@@ -1609,6 +1666,23 @@ void launch_flux_rhs(const Geom& g, const Phys& ph, const Bnd& bnd, const FluxAr
     else
         k_rhs<2><<<rb, NT, 0, s>>>(g, bnd, a, rb);
     ++*launches;
+}
+
+void launch_state_flux_rhs(const Geom& g, const Phys& ph, const double* Z, const double* H, double* T, double* rho,
+                           double* kap, double* sc, int* status, const Bnd& bnd, bool kap_ghosts, const FluxArgs& a,
+                           cudaStream_t s, int* launches) {
+    const int rb = reduce_grid(g);
+    const int kg = kap_ghosts ? 1 : 0;
+    if (g.dim == 3) {
+        if (ph.mixed) k_state_flux<3, true><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, status, sc, bnd, kg, a);
+        else k_state_flux<3, false><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, status, sc, bnd, kg, a);
+        k_rhs<3><<<rb, NT, 0, s>>>(g, bnd, a, rb);
+    } else {
+        if (ph.mixed) k_state_flux<2, true><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, status, sc, bnd, kg, a);
+        else k_state_flux<2, false><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, status, sc, bnd, kg, a);
+        k_rhs<2><<<rb, NT, 0, s>>>(g, bnd, a, rb);
+    }
+    *launches += 2;
 }
 
 void launch_project(const Geom& g, const Phys& ph, const ProjArgs& a, cudaStream_t s, int* launches) {

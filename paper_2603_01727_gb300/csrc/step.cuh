@@ -171,6 +171,11 @@ void launch_state(const Geom& g, const Phys& ph, const double* Z, const double* 
 void launch_residual(const Geom& g, const Phys& ph, const ResidArgs& a, cudaStream_t s, int* launches);
 void launch_flux_rhs(const Geom& g, const Phys& ph, const Bnd& bnd, const FluxArgs& a, cudaStream_t s,
                      int* launches);
+// Open systems (p0 = 1, a.correct): state relation + face fluxes in one kernel,
+// then the right-hand side; the same results as launch_state + launch_flux_rhs.
+void launch_state_flux_rhs(const Geom& g, const Phys& ph, const double* Z, const double* H, double* T, double* rho,
+                           double* kap, double* sc, int* status, const Bnd& bnd, bool kap_ghosts,
+                           const FluxArgs& a, cudaStream_t s, int* launches);
 void launch_project(const Geom& g, const Phys& ph, const ProjArgs& a, cudaStream_t s, int* launches);
 void launch_momentum(const Geom& g, const double* rho, double* const v[3], double* mom[3], cudaStream_t s,
                      int* launches);
