@@ -123,6 +123,7 @@ struct PoissonPlan {
     // from one grid dimension.  bdone: 1 once every system has converged.
     int nb;
     int* bdone;
+    int prefix;           // CG iterations a graph solve captures ahead of its while node
 };
 
 // Workspace bytes for a grid (no allocation).
@@ -144,6 +145,12 @@ size_t poisson_plan_bytes_batch(int dim, const int n[3], const int periodic[3], 
 bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const double h[3], const int periodic[3],
                              int mg_fp32, int sweeps, int tail_cells, double rtol, int max_iter, int nb, void* ws,
                              size_t ws_bytes, std::vector<double>* minv_host, const char** err);
+
+// Iterations a graph-captured solve runs ahead of its while node (0 for a
+// batch or a one-level grid), and the while node's iterations for a solve of
+// iters iterations.
+int poisson_prefix_iters(const PoissonPlan* pl);
+double poisson_loop_iters(const PoissonPlan* pl, double iters);
 
 // Device flag a host-driven loop polls: 1 once the solve (every system of a
 // batch) has finished.

@@ -426,6 +426,12 @@ cudaError_t capture_while_solve(PoissonPlan* pl, const double* b, double* x, cud
     if (e != cudaSuccess) return e;
     e = poisson_enqueue_prologue(pl, b, x, st, (unsigned long long)h, mean_ready);
     if (e != cudaSuccess) return e;
+    // the first iterations ahead of the loop (no per-iteration loop cost); an
+    // iteration after convergence changes nothing (its update kernels test the
+    // done flag) and the loop then does not run
+    const int prefix = poisson_prefix_iters(pl);
+    for (int u = 0; u < prefix && e == cudaSuccess; ++u) e = poisson_enqueue_body(pl, x, st, (unsigned long long)h);
+    if (e != cudaSuccess) return e;
     e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph_h, &deps, nullptr, &ndeps);
     if (e != cudaSuccess) return e;
     std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
@@ -1102,7 +1108,10 @@ sim_status sim_query(sim_t* s, int what, double* out) {
             if (st != SIM_OK) return st;
             st = dev(SC_ITERS_CORR, &ic);
             if (st != SIM_OK) return st;
-            *out = (double)(-s->launches_last - 1) + (ip + ic) * s->body_launches;
+            // the step graph's fixed part holds the iterations captured ahead of
+            // each solve's loop; the loops ran the rest
+            *out = (double)(-s->launches_last - 1) +
+                   (poisson_loop_iters(&s->pp, ip) + poisson_loop_iters(&s->pp, ic)) * s->body_launches;
             return SIM_OK;
         }
         default: return fail(s, SIM_EINVAL, "unknown query %d", what);
@@ -1707,12 +1716,14 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
     const sim_status st_dev = check_device_status(s);
     if (st_dev != SIM_OK) return st_dev;
     if (s->solve_graphs) {
-        // kernels of the graph-launched solves: their loops ran as many times as
-        // the reported iterations (the last transposed solve's count for both)
+        // kernels of the graph-launched solves: their loops ran the reported
+        // iterations (the last transposed solve's count for both) less those
+        // captured ahead of the loop, which solve_fixed holds
         double it[4] = {0.0, 0.0, 0.0, 0.0};
         CK(cudaMemcpy(&it[0], s->sc + SC_ITERS_PRED, sizeof(double), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(&it[1], s->sc + SC_ITERS_CORR, sizeof(double), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(&it[2], A.rep, sizeof(double), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < 3; ++k) it[k] = poisson_loop_iters(&s->pp, it[k]);
         s->launches_last += s->solve_fixed[0] + (int)(s->solve_body[0] * it[0]) + s->solve_fixed[1] +
                             (int)(s->solve_body[1] * it[1]) + 2 * (s->solve_fixed[2] + (int)(s->solve_body[2] * it[2]));
     }
@@ -2109,7 +2120,8 @@ sim_status sim_batch_query_launches(sim_batch_t* b, double* out) {
             itp = a > itp ? a : itp;
             itc = c > itc ? c : itc;
         }
-        total += 2.0 * G.fixed_launches + G.body_launches * (itp + itc);
+        total += 2.0 * G.fixed_launches +
+                 G.body_launches * (poisson_loop_iters(&G.pl, itp) + poisson_loop_iters(&G.pl, itc));
     }
     *out = total;
     return SIM_OK;

@@ -376,6 +376,37 @@ def test_3d_fast_diagonalisation_top_level_matches_vcycle_tail(n, periodic_x, mo
         assert rel(out["fdm"][0][k], out["tail"][0][k]) <= 1e-9, k
 
 
+@pytest.mark.parametrize("case,precision", [("slot", W.MIXED), ("slot", W.FP64), ("sphere", W.MIXED)])
+def test_cg_iterations_captured_ahead_of_the_loop_change_nothing(case, precision, monkeypatch):
+    """A graph-launched solve captures its first CG iterations ahead of its
+    while node; once a solve has converged, the remaining captured iterations
+    must leave x and the reported scalars untouched (the update kernels test
+    the done flag).  A prefix longer than any solve (40 iterations) and none
+    must give bitwise the same fields and iteration counts, through the eager
+    first steps and the step graphs."""
+    from paper_2603_01727_gb300.lowmach import SIM_Q_ITERS_PRED, SIM_Q_ITERS_CORR, SIM_Q_KERNEL_LAUNCHES, Simulation
+    prm, geo, f = W.slot_burner(64, 128) if case == "slot" else W.sphere_burner(24)
+    prm["precision"] = precision
+    out = {}
+    for u in ("40", "0"):
+        monkeypatch.setenv("LOWMACH_CG_PREFIX", u)
+        sim = Simulation(prm, geo)
+        sim.set_fields(f)
+        its = []
+        for _ in range(5):
+            sim.step(1)
+            its.append((sim.query(SIM_Q_ITERS_PRED), sim.query(SIM_Q_ITERS_CORR)))
+        launches = sim.query(SIM_Q_KERNEL_LAUNCHES)
+        out[u] = ({k: sim.get(k) for k in ("U", "V", "Z", "H", "P")}, its, launches)
+        sim.close()
+    assert out["40"][1] == out["0"][1], (out["40"][1], out["0"][1])
+    assert all(a < 40 and b < 40 for a, b in out["0"][1])
+    for k in out["0"][0]:
+        assert np.array_equal(out["40"][0][k], out["0"][0][k]), k
+    # the captured iterations are launched whether or not they were needed
+    assert out["40"][2] > out["0"][2], (out["40"][2], out["0"][2])
+
+
 @pytest.mark.parametrize("case", ["slot", "sphere"])
 def test_mixed_state_relation_is_fp64_accurate(case):
     """The mixed path's state relation evaluates kappa = T^0.7 with a
