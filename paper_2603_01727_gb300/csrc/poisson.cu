@@ -51,13 +51,17 @@ namespace {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
-bool pdl_enabled() {
-    static const bool on = [] {
-        const char* e = std::getenv("LOWMACH_NO_PDL");   // tuning override: disable PDL
-        return !(e && e[0] == '1');
-    }();
-    return on;
-}
+// PDL for the launches of the plan being enqueued (set by each entry point
+// from the plan, on the enqueuing host thread).
+thread_local bool g_pdl = true;
+
+struct PdlScope {
+    bool saved;
+    explicit PdlScope(const PoissonPlan* pl) : saved(g_pdl) { g_pdl = pl->pdl != 0; }
+    ~PdlScope() { g_pdl = saved; }
+};
+
+bool pdl_enabled() { return g_pdl; }
 
 template <typename... KArgs, typename... Args>
 void launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
@@ -593,112 +597,47 @@ __global__ void __launch_bounds__(NTV)
 }
 
 // ---------------------------------------------------------------------------
-// Refinement mode: FP32 inner update, then (when due) the FP64 outer step.
+// Refinement mode: the CG update of an iteration with a reliable update.
 // ---------------------------------------------------------------------------
-// e = (folded into x since the last update ? 0 : e) + alpha p, r32 -= alpha q,
-// ||r32||^2; the last block counts the iteration and flags a reliable update
-// when the residual dropped by inner_tol since the last one, after inner_max
-// iterations, or at the solve's iteration cap.
-__global__ void __launch_bounds__(NTV)
-    k_ir_update(float* __restrict__ e, float* __restrict__ r, const float* p0, const float* p1,
-                const float* __restrict__ q, long long N, double* part, double* scal, int* ictl, unsigned int* cnt,
-                double inner_tol, int inner_max, int max_iter, cudaGraphConditionalHandle h, int use_graph) {
-    pdl_wait();
-    pdl_trigger();
-    const int fb = blockIdx.y;
-    batch_ctl(fb, &scal, &ictl, &cnt);
-    // the system has converged (a batch member, or an iteration captured ahead
-    // of the loop): e, r32 and the control words stay as they are
-    const int it = ictl[PI_IT], ereset = ictl[PI_ERESET], done = ictl[PI_DONE];
-    const float alpha = (float)scal[PS_ALPHA];
-    if (done) return;
-    e += fb * N;
-    r += fb * N;
-    p0 += fb * N;
-    p1 += fb * N;
-    q += fb * N;
-    part += (long long)fb * gridDim.x;
-    const float* __restrict__ p = (it & 1) ? p1 : p0;
-    const bool fresh = (it == 0 || ereset);
-    float rr = 0.0f;
-    if ((N & 3) == 0) {
-        // four cells per thread step (16-byte accesses; the launch is sized by N / 4)
-        const long long N4 = N >> 2;
-        for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N4; t += (long long)gridDim.x * NTV) {
-            const float4 pv = reinterpret_cast<const float4*>(p)[t];
-            const float4 qv = reinterpret_cast<const float4*>(q)[t];
-            float4 rv = reinterpret_cast<const float4*>(r)[t];
-            float4 ev = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(e)[t];
-            ev.x = fmaf(alpha, pv.x, ev.x);
-            ev.y = fmaf(alpha, pv.y, ev.y);
-            ev.z = fmaf(alpha, pv.z, ev.z);
-            ev.w = fmaf(alpha, pv.w, ev.w);
-            rv.x = fmaf(-alpha, qv.x, rv.x);
-            rv.y = fmaf(-alpha, qv.y, rv.y);
-            rv.z = fmaf(-alpha, qv.z, rv.z);
-            rv.w = fmaf(-alpha, qv.w, rv.w);
-            reinterpret_cast<float4*>(e)[t] = ev;
-            reinterpret_cast<float4*>(r)[t] = rv;
-            rr = fmaf(rv.x, rv.x, rr);
-            rr = fmaf(rv.y, rv.y, rr);
-            rr = fmaf(rv.z, rv.z, rr);
-            rr = fmaf(rv.w, rv.w, rr);
-        }
-    } else {
-        for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV) {
-            const float ev = fresh ? 0.0f : e[t];
-            e[t] = fmaf(alpha, p[t], ev);
-            const float rv = fmaf(-alpha, q[t], r[t]);
-            r[t] = rv;
-            rr = fmaf(rv, rv, rr);
-        }
-    }
-    __shared__ float redf[NTV / 32];
-    __shared__ double red[NTV / 32];
-    const float brr = block_sum_f<NTV>(rr, redf);
-    if (threadIdx.x == 0) part[blockIdx.x] = (double)brr;
-    if (arrive_last_n(cnt, gridDim.x)) {
-        const double RR = sum_parts_cg<NTV>(part, gridDim.x, red);
-        if (threadIdx.x == 0) {
-            const int itn = it + 1, tot = ictl[PI_TOTAL] + 1, since = ictl[PI_SINCE] + 1;
-            ictl[PI_IT] = itn;
-            ictl[PI_TOTAL] = tot;
-            ictl[PI_ERESET] = 0;
-            ictl[PI_SINCE] = since;           // iterations since the last reliable update
-            scal[PS_ITERS] = (double)tot;
-            const int bad = !(RR == RR) || !(RR < 1e300);
-            const int refine = (RR <= inner_tol * inner_tol * scal[PS_RR0]) || (since >= inner_max) ||
-                               (tot >= max_iter) || bad;
-            ictl[PI_REFINE] = refine;
-            if (!refine && use_graph) cudaGraphSetConditional(h, 1u);
-            *cnt = 0u;
-        }
-    }
-}
-
-// Reliable update, only when flagged: x += e, r64 -= A e, r32 = r64,
-// ||r64||^2; the last block applies the FP64 stopping test.  A e and the
-// residual difference are formed in float-float arithmetic from the FP32
-// correction e (about 2^-46 relative, far below what the stopping test needs)
-// with float <-> double conversions by bit operations, so that only three
-// FP64 operations per cell (two additions, the squared norm) use the
-// 1/64-rate FP64 pipe.  The FP32 search direction and r.z are kept.
+// The CG update of an iteration in refinement mode, with a reliable update
+// every time: the FP32 correction e = alpha p (p the FP32 search direction)
+// is folded into the FP64 x, the FP64 residual is updated, r64 -= A e, and
+// replaces the FP32 one, r32 = r64; the last block counts the iteration and
+// applies the FP64 stopping test to ||r64||^2.  e is formed from p on the fly,
+// for each cell and its neighbours, so neither e nor a recursively updated
+// FP32 residual is stored.  A e and the residual difference are formed in
+// float-float arithmetic from the FP32 e (about 2^-46 relative, far below
+// what the stopping test needs) with float <-> double conversions by bit
+// operations, so that only three FP64 operations per cell (two additions, the
+// squared norm) use the 1/64-rate FP64 pipe.  The FP32 search direction and
+// r.z are kept.
 template <int DIM>
 __global__ void __launch_bounds__(NTV)
-    k_ir_refine(LvT<double> L, double* __restrict__ x, double* __restrict__ r64, const float* __restrict__ e,
-                float* __restrict__ r32, double* part, double* scal, int* ictl, unsigned int* cnt, double rtol,
-                int max_iter, cudaGraphConditionalHandle h, int use_graph, int vec4) {
+    k_ir_step(LvT<double> L, double* __restrict__ x, double* __restrict__ r64, const float* p0, const float* p1,
+              float* __restrict__ r32, double* part, double* scal, int* ictl, unsigned int* cnt, double rtol,
+              int max_iter, cudaGraphConditionalHandle h, int use_graph, int vec4) {
     pdl_wait();
     pdl_trigger();
     const int fb = blockIdx.y;
     batch_ctl(fb, &scal, &ictl, &cnt);
-    // not flagged, or the system has converged (a batch member, or an
-    // iteration captured ahead of the loop)
-    const int refine = ictl[PI_REFINE], done = ictl[PI_DONE];
-    if (!refine || done) return;
+    // the system has converged (a batch member, or an iteration captured
+    // ahead of the loop): x, r and the reported scalars stay as they are
+    const int done = ictl[PI_DONE], it = ictl[PI_IT];
+    const float alpha = (float)scal[PS_ALPHA];
+    if (done) return;
+    // the correction e = alpha p at compact index i (the product rounded once)
+    const float* __restrict__ p = ((it & 1) ? p1 : p0) + (long long)fb * L.N;
+    auto ld1 = [&](int i) -> float { return fmaf(alpha, p[i], 0.0f); };
+    auto ld4 = [&](int i) -> float4 {
+        float4 v = *reinterpret_cast<const float4*>(p + i);
+        v.x = fmaf(alpha, v.x, 0.0f);
+        v.y = fmaf(alpha, v.y, 0.0f);
+        v.z = fmaf(alpha, v.z, 0.0f);
+        v.w = fmaf(alpha, v.w, 0.0f);
+        return v;
+    };
     x += (long long)fb * L.N;
     r64 += (long long)fb * L.N;
-    e += (long long)fb * L.N;
     r32 += (long long)fb * L.N;
     part += (long long)fb * gridDim.x;
     FF wd[3];
@@ -716,12 +655,12 @@ __global__ void __launch_bounds__(NTV)
             const int t0 = 4 * q;
             int c[3];
             coords(L, t0, c);
-            const float4 ec = *reinterpret_cast<const float4*>(e + t0);
+            const float4 ec = ld4(t0);
             float el = 0.0f, er = 0.0f;
-            if (c[0] > 0) el = e[t0 - 1];
-            else if (L.per[0]) el = e[t0 + nx - 1];
-            if (c[0] + 4 < nx) er = e[t0 + 4];
-            else if (L.per[0]) er = e[t0 + 4 - nx];
+            if (c[0] > 0) el = ld1(t0 - 1);
+            else if (L.per[0]) el = ld1(t0 + nx - 1);
+            if (c[0] + 4 < nx) er = ld1(t0 + 4);
+            else if (L.per[0]) er = ld1(t0 + 4 - nx);
             float4 nb[2][2];   // [y, z][low, high] neighbour rows
             int clo = 0, p3 = 3;
 #pragma unroll
@@ -730,10 +669,10 @@ __global__ void __launch_bounds__(NTV)
                 const int stride = (d == 1) ? nx : nx * ny;
                 nb[d - 1][0] = make_float4(0.f, 0.f, 0.f, 0.f);
                 nb[d - 1][1] = nb[d - 1][0];
-                if (c[d] > 0) nb[d - 1][0] = *reinterpret_cast<const float4*>(e + t0 - stride);
-                else if (L.per[d]) nb[d - 1][0] = *reinterpret_cast<const float4*>(e + t0 + (n - 1) * stride);
-                if (c[d] < n - 1) nb[d - 1][1] = *reinterpret_cast<const float4*>(e + t0 + stride);
-                else if (L.per[d]) nb[d - 1][1] = *reinterpret_cast<const float4*>(e + t0 - (n - 1) * stride);
+                if (c[d] > 0) nb[d - 1][0] = ld4(t0 - stride);
+                else if (L.per[d]) nb[d - 1][0] = ld4(t0 + (n - 1) * stride);
+                if (c[d] < n - 1) nb[d - 1][1] = ld4(t0 + stride);
+                else if (L.per[d]) nb[d - 1][1] = ld4(t0 - (n - 1) * stride);
                 clo += (L.per[d] ? 2 : (int)(c[d] > 0) + (int)(c[d] < n - 1)) * p3;
                 p3 *= 3;
             }
@@ -784,16 +723,16 @@ __global__ void __launch_bounds__(NTV)
         for (int d = 0; d < DIM; ++d) {
             const int n = L.n[d];
             float a = 0.0f, b = 0.0f;
-            if (c[d] > 0) a = e[t - stride];
-            else if (L.per[d]) a = e[t + (n - 1) * stride];
-            if (c[d] < n - 1) b = e[t + stride];
-            else if (L.per[d]) b = e[t - (n - 1) * stride];
+            if (c[d] > 0) a = ld1(t - stride);
+            else if (L.per[d]) a = ld1(t + (n - 1) * stride);
+            if (c[d] < n - 1) b = ld1(t + stride);
+            else if (L.per[d]) b = ld1(t - (n - 1) * stride);
             off += wd[d] * (FF(a, 0.0f) + FF(b, 0.0f));
             cl += (L.per[d] ? 2 : (int)(c[d] > 0) + (int)(c[d] < n - 1)) * p3;
             stride *= n;
             p3 *= 3;
         }
-        const float ev = e[t];
+        const float ev = ld1(t);
         const FF Ae = FF(L.diag[cl]) * FF(ev, 0.0f) - off;
         const FF rv = FF(r64[t]) - Ae;
         x[t] = x[t] + f2d_bits(ev);
@@ -808,16 +747,16 @@ __global__ void __launch_bounds__(NTV)
     if (arrive_last_n(cnt, gridDim.x)) {
         const double RR = sum_parts_cg<NTV>(part, gridDim.x, red);
         if (threadIdx.x == 0) {
+            const int tot = ictl[PI_TOTAL] + 1;
+            ictl[PI_IT] = it + 1;
+            ictl[PI_TOTAL] = tot;
+            scal[PS_ITERS] = (double)tot;
             const double ff = scal[PS_FF];
             const int conv = (RR <= rtol * rtol * ff);
             const int bad = !(RR == RR) || !(RR < 1e300);
-            const int done = conv || bad || (ictl[PI_TOTAL] >= max_iter);
+            const int done = conv || bad || (tot >= max_iter);
             scal[PS_RR] = RR;
-            scal[PS_RR0] = RR;
             scal[PS_RELRES] = sqrt(RR / ff);
-            ictl[PI_REFINE] = 0;
-            ictl[PI_ERESET] = 1;                   // e now lives in x
-            ictl[PI_SINCE] = 0;
             ictl[PI_DONE] = done;
             if (done && !conv) ictl[PI_NOCONV] = 1;
             if (use_graph) cudaGraphSetConditional(h, done ? 0u : 1u);
@@ -919,12 +858,8 @@ __global__ void __launch_bounds__(NTV)
             scal[PS_RZ] = 0.0;
             scal[PS_BETA] = 0.0;
             scal[PS_ITERS] = 0.0;
-            scal[PS_RR0] = RR;
             ictl[PI_IT] = 0;
             ictl[PI_TOTAL] = 0;
-            ictl[PI_REFINE] = 0;
-            ictl[PI_ERESET] = 1;
-            ictl[PI_SINCE] = 0;
             ictl[PI_NOCONV] = 0;
             const int zero = !(FF > 0.0);
             ictl[PI_ZERO] = zero;
@@ -2608,7 +2543,7 @@ size_t poisson_plan_bytes_batch(int dim, const int n[3], const int periodic[3], 
     size_t b = 0;
     b += 4 * align256(B * sizeof(double) * N);                      // r p0 p1 q
     b += align256(B * sizeof(double) * N) + align256(B * w * N);    // z (double-sized: one-level grids), u0pre
-    if (mg_fp32 && s.nlev > 1) b += 5 * align256(B * sizeof(float) * N);   // r32 e32 p32[2] q32
+    if (mg_fp32 && s.nlev > 1) b += 4 * align256(B * sizeof(float) * N);   // r32 p32[2] q32
     b += 3 * align256(B * sizeof(double) * npart);                  // partials
     b += align256(B * sizeof(double) * PS_NSCAL) + align256(B * sizeof(int) * PI_NINT) +
          align256(B * sizeof(unsigned int) * kNumCounters) + align256(sizeof(int));
@@ -2680,6 +2615,16 @@ bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const dou
         u = u < 0 ? 0 : (u > max_iter ? max_iter : u);
         pl->prefix = (nb == 1) ? u : 0;
     }
+    // Programmatic dependent launch for the FP32 multigrid: its kernels are
+    // short, and the next one's launch overlaps this one's drain.  The FP64
+    // multigrid's kernels run several waves, and successors scheduled early
+    // hold SM slots while they wait: its 256 x 512 step measured 2.454 ms with
+    // PDL against 2.365 ms without.  LOWMACH_NO_PDL=1 / LOWMACH_PDL=1 override.
+    pl->pdl = mg_fp32 ? 1 : 0;
+    if (const char* e = std::getenv("LOWMACH_NO_PDL"))
+        if (e[0] == '1') pl->pdl = 0;
+    if (const char* e = std::getenv("LOWMACH_PDL"))
+        if (e[0] == '1') pl->pdl = 1;
     pl->tail_smem = tail_smem;
     // red-black sweeps per smoothing (2D kernels): two, V(2,2).  The fused
     // kernels are latency-bound, so the extra shared-memory sweeps cost less
@@ -2716,17 +2661,9 @@ bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const dou
     const bool refine_mode = mg_fp32 && s.nlev > 1 && !(rf && rf[0] == '0');
     if (refine_mode) {   // refinement mode (a one-level grid is solved exactly in FP64)
         pl->r32 = (float*)take(B * sizeof(float) * pl->N);
-        pl->e32 = (float*)take(B * sizeof(float) * pl->N);
         pl->p32[0] = (float*)take(B * sizeof(float) * pl->N);
         pl->p32[1] = (float*)take(B * sizeof(float) * pl->N);
         pl->q32 = (float*)take(B * sizeof(float) * pl->N);
-        pl->inner_tol = 0.1;     // reliable update whenever ||r|| fell 10x since the last one
-        pl->inner_max = 50;
-        // tuning override: LOWMACH_INNER_TOL = residual drop between reliable updates
-        if (const char* e = std::getenv("LOWMACH_INNER_TOL")) {
-            const double v = std::atof(e);
-            if (v > 0.0 && v < 1.0) pl->inner_tol = v;
-        }
     }
     pl->part0 = (double*)take(B * sizeof(double) * pl->npart);
     pl->part1 = (double*)take(B * sizeof(double) * pl->npart);
@@ -3068,17 +3005,14 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
     // a batch sets the while-node condition once, from every system's state
     const int ug = (pl->nb > 1) ? 0 : use_graph;
     if (ir) {
-        // the update runs four cells per thread step when N % 4 == 0
-        const dim3 rbu((pl->N % 4 == 0) ? reduce_blocks(pl->N / 4) : reduce_blocks(pl->N), pl->nb);
-        launch(k_ir_update, rbu, NTV, 0, s, pl->e32, pl->r32, pl->p32[0], pl->p32[1], pl->q32, pl->N, pl->part0, pl->scal,
-                                       pl->ictl, pl->cnt + CNT_UPD, pl->inner_tol, pl->inner_max, pl->max_iter, h, ug);
-        // the reliable update runs four x-consecutive cells per thread step when
-        // nx % 4 == 0 and x (the caller's array) is 16-byte aligned
+        // four x-consecutive cells per thread step when nx % 4 == 0 and x (the
+        // caller's array) is 16-byte aligned
         const int vec4 = (pl->lev[0].n[0] % 4 == 0) && (((uintptr_t)x & 15) == 0);
         const dim3 rbr(vec4 ? reduce_blocks(pl->N / 4) : reduce_blocks(pl->N), pl->nb);
-        launch(k_ir_refine<DIM>, rbr, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r, pl->e32, pl->r32,
-               pl->part1, pl->scal, pl->ictl, pl->cnt + CNT_REF, pl->rtol, pl->max_iter, h, ug, vec4);
-        pl->launches += 2;
+        launch(k_ir_step<DIM>, rbr, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r, (const float*)pl->p32[0],
+               (const float*)pl->p32[1], pl->r32, pl->part1, pl->scal, pl->ictl, pl->cnt + CNT_REF, pl->rtol,
+               pl->max_iter, h, ug, vec4);
+        pl->launches += 1;
     } else {
         // the update runs two cells per thread step when N is even and x (the
         // caller's array) is 16-byte aligned
@@ -3116,6 +3050,7 @@ void prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s, cudaG
 
 cudaError_t poisson_enqueue_prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s,
                                      unsigned long long graph_handle, int mean_ready) {
+    const PdlScope pdl(pl);
     const int use_graph = graph_handle != 0ULL;
     if (pl->dim == 3)
         prologue<3>(pl, b, x, s, (cudaGraphConditionalHandle)graph_handle, use_graph, mean_ready);
@@ -3131,6 +3066,7 @@ void poisson_meanb_target(PoissonPlan* pl, double** part, unsigned int** cnt, do
 }
 
 cudaError_t poisson_enqueue_body(PoissonPlan* pl, double* x, cudaStream_t s, unsigned long long graph_handle) {
+    const PdlScope pdl(pl);
     const int use_graph = graph_handle != 0ULL;
     const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)graph_handle;
     if (pl->mg_fp32) {
@@ -3145,6 +3081,7 @@ cudaError_t poisson_enqueue_body(PoissonPlan* pl, double* x, cudaStream_t s, uns
 
 cudaError_t poisson_enqueue_epilogue(PoissonPlan* pl, double* x, cudaStream_t s, double* rep, int* status,
                                      int status_bit, int remove_mean) {
+    const PdlScope pdl(pl);
     if (!remove_mean) {
         // the report alone (one block, no pass over x); a batch reports separately
         if (pl->nb == 1) {
@@ -3163,6 +3100,7 @@ cudaError_t poisson_enqueue_epilogue(PoissonPlan* pl, double* x, cudaStream_t s,
 }
 
 cudaError_t poisson_enqueue_remove_mean(PoissonPlan* pl, double* x, cudaStream_t s) {
+    const PdlScope pdl(pl);
     const dim3 rb(reduce_blocks(pl->N), 1);
     launch(k_mean, rb, NTV, 0, s, (const double*)x, pl->N, pl->part0, pl->scal, PS_MEANX, pl->cnt + CNT_MEANX);
     launch(k_sub_mean, rb, NTV, 0, s, x, pl->N, (const double*)pl->scal, (const int*)pl->ictl, (double*)nullptr,
@@ -3171,6 +3109,7 @@ cudaError_t poisson_enqueue_remove_mean(PoissonPlan* pl, double* x, cudaStream_t
 }
 
 cudaError_t poisson_launch_single(PoissonPlan* pl, int which, cudaStream_t s) {
+    const PdlScope pdl(pl);
     if (pl->nlev == 1) return cudaSuccess;
     const int f32 = pl->mg_fp32, d3 = pl->dim == 3;
     switch (which) {
@@ -3206,6 +3145,7 @@ const int* poisson_done_flag(const PoissonPlan* pl) { return pl->nb > 1 ? pl->bd
 
 cudaError_t poisson_enqueue_batch_report(PoissonPlan* pl, double* const* rep, int* const* status, int status_bit,
                                          cudaStream_t s) {
+    const PdlScope pdl(pl);
     launch(k_batch_report, 1, NTV, 0, s, (const double*)pl->scal, (const int*)pl->ictl, pl->nb, rep, status,
            status_bit);
     pl->launches += 1;
@@ -3213,6 +3153,7 @@ cudaError_t poisson_enqueue_batch_report(PoissonPlan* pl, double* const* rep, in
 }
 
 cudaError_t poisson_solve_host_loop(PoissonPlan* pl, const double* b, double* x, cudaStream_t s) {
+    const PdlScope pdl(pl);
     cudaError_t e = poisson_enqueue_prologue(pl, b, x, s, 0ULL, 0);
     if (e != cudaSuccess) return e;
     int done = 0;

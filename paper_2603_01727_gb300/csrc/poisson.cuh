@@ -54,15 +54,11 @@ enum : int {
     PS_RELRES = 7,    // sqrt(rr/ff) at exit
     PS_ALPHA = 8,
     PS_MEANX = 9,
-    PS_RR0 = 10,      // ||r||^2 at the start of the current inner solve (refinement mode)
     PS_NSCAL = 16
 };
-// PI_IT: CG iterations of the solve (FP32 CG iterations in refinement mode);
-// PI_TOTAL: the same count for the iteration cap; PI_REFINE: a reliable
-// update is due; PI_ERESET: the FP32 correction was folded into x; PI_SINCE:
-// iterations since the last reliable update (refinement mode).
-enum : int { PI_IT = 0, PI_DONE = 1, PI_NOCONV = 2, PI_ZERO = 3, PI_REFINE = 4, PI_TOTAL = 5, PI_ERESET = 6,
-             PI_SINCE = 7, PI_NINT = 8 };
+// PI_IT: CG iterations of the solve (its parity selects the search-direction
+// buffer); PI_TOTAL: the same count for the iteration cap.
+enum : int { PI_IT = 0, PI_DONE = 1, PI_NOCONV = 2, PI_ZERO = 3, PI_TOTAL = 5, PI_NINT = 8 };
 constexpr int kNumCounters = 8;          // last-block counters (one per reducing kernel kind)
 
 struct PoissonPlan {
@@ -80,17 +76,14 @@ struct PoissonPlan {
     double* q;
     void* z;              // preconditioned residual (T)
     void* u0pre;          // pre-smoothed fine-level correction (T)
-    // Refinement mode (mg_fp32): the CG runs in FP32 on the correction e with
-    // reliable updates: whenever its residual has dropped by inner_tol since
-    // the last update, e is folded into the FP64 x, the FP64 residual is
-    // updated (r -= A e) and replaces the FP32 one, and the FP64 stopping test
-    // runs; the search direction is kept across updates.
-    float* r32;           // inner residual
-    float* e32;           // inner solution (correction)
-    float* p32[2];        // inner search direction, double-buffered
+    // Refinement mode (mg_fp32): the CG's search direction, operator
+    // application and preconditioner run in FP32; every iteration folds its
+    // correction e = alpha p into the FP64 x, updates the FP64 residual
+    // (r -= A e, float-float), replaces the FP32 residual with it and applies
+    // the FP64 stopping test (a reliable update every iteration).
+    float* r32;           // FP32 copy of the FP64 residual
+    float* p32[2];        // search direction, double-buffered
     float* q32;
-    double inner_tol;
-    int inner_max;
     double* part0;        // partial sums (npart entries each)
     double* part1;
     double* part2;
@@ -124,6 +117,7 @@ struct PoissonPlan {
     int nb;
     int* bdone;
     int prefix;           // CG iterations a graph solve captures ahead of its while node
+    int pdl;              // 1: the solver's kernels launch with programmatic dependent launch
 };
 
 // Workspace bytes for a grid (no allocation).
