@@ -647,8 +647,8 @@ __global__ void __launch_bounds__(NTV)
     if (vec4) {
         // four x-consecutive cells per thread step (nx % 4 == 0, x 16-byte
         // aligned; the launch is sized by N / 4): one coordinate map, 16-byte
-        // loads of e's rows and of x, r64; each cell's arithmetic is the
-        // scalar path's, in its order
+        // loads of p's rows (e = alpha p) and of x, r64; each cell's
+        // arithmetic is the scalar path's, in its order
         const int nx = L.n[0], ny = L.n[1];
         const int N4 = L.N >> 2;
         for (int q = blockIdx.x * NTV + threadIdx.x; q < N4; q += gridDim.x * NTV) {
