@@ -256,6 +256,33 @@ def test_mixed_precision_error_against_oracle(case):
     print(case, {k: f"{v:.2e}" for k, v in worst.items()})
 
 
+def test_slot_burner_full_size_mixed_matches_oracle():
+    """The bench's headline configuration: 256x512, mixed precision,
+    poisson_rtol = 1e-10, graphs on, 4 steps (two of them through the step
+    graph).  Scalars to 1e-9; P, v and F to the mixed-precision bound."""
+    prm, geo, f = W.slot_burner()
+    prm["precision"] = W.MIXED
+    pb, st = oracle_run(prm, geo, f, 4)
+    sim = gpu_run(prm, geo, f, 4)
+    ref = oracle_fields(pb, st)
+    compare(sim, ref, 1e-9, names=["Z", "H", "T", "RHO", "KAPPA"])
+    compare(sim, ref, MIXED_TOL, names=["U", "V", "P", "FX", "FY"])
+    assert sim.query(7) <= 1e-10 and sim.query(6) <= 1e-10
+
+
+def test_sphere_burner_full_size_mixed_matches_oracle():
+    """The 3D configuration the bench times with --config sphere: 192^3,
+    mixed precision, poisson_rtol = 1e-10, one step (the oracle takes about
+    20 s and 4 GB for it).  Every field to the mixed-precision bound."""
+    prm, geo, f = W.sphere_burner(192)
+    prm["precision"] = W.MIXED
+    pb, st = oracle_run(prm, geo, f, 1)
+    sim = gpu_run(prm, geo, f, 1)
+    compare(sim, oracle_fields(pb, st), MIXED_TOL)
+    assert np.array_equal(sim.get("CHI"), V(pb.ibm["chi"], pb.g))
+    assert sim.query(7) <= 1e-10 and sim.query(6) <= 1e-10
+
+
 # ---------------------------------------------------------------------------
 # Execution paths and error handling
 # ---------------------------------------------------------------------------
