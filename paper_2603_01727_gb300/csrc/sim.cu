@@ -1243,6 +1243,35 @@ std::vector<std::pair<void*, size_t>> state_segments(sim_t* s) {
     return seg;
 }
 
+// The device address of a pinned (mapped) host buffer, or null: a restart
+// blob there moves in one pack / unpack kernel instead of one copy per array.
+char* mapped_host(const void* buf, const std::vector<std::pair<void*, size_t>>& seg) {
+    if (seg.size() > (size_t)kMaxStateSeg) return nullptr;
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, buf) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (pa.type != cudaMemoryTypeHost || !pa.devicePointer || ((uintptr_t)pa.devicePointer & 15) != 0) return nullptr;
+    for (auto& q : seg)
+        if (((uintptr_t)q.first & 15) != 0) return nullptr;
+    return (char*)pa.devicePointer;
+}
+
+StateCopy state_copy_table(const std::vector<std::pair<void*, size_t>>& seg) {
+    StateCopy c;
+    std::memset(&c, 0, sizeof(c));
+    size_t off = a256(sizeof(StateHeader));
+    for (auto& q : seg) {
+        c.dev[c.n] = (char*)q.first;
+        c.bytes[c.n] = q.second;
+        c.off[c.n] = off;
+        ++c.n;
+        off += a256(q.second);
+    }
+    return c;
+}
+
 size_t state_bytes(sim_t* s) {
     size_t b = a256(sizeof(StateHeader));
     for (auto& q : state_segments(s)) b += a256(q.second);
@@ -1273,10 +1302,17 @@ sim_status sim_state_save(sim_t* s, void* buf, int on_device) {
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     char* out = (char*)buf;
     CK(cudaMemcpyAsync(out, &h, sizeof(h), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s->stream));
-    size_t off = a256(sizeof(StateHeader));
-    for (auto& q : state_segments(s)) {
-        CK(cudaMemcpyAsync(out + off, q.first, q.second, k, s->stream));
-        off += a256(q.second);
+    const auto seg = state_segments(s);
+    char* mapped = on_device ? nullptr : mapped_host(buf, seg);
+    if (mapped) {
+        launch_state_copy(state_copy_table(seg), mapped, 0, s->stream);
+        CK(cudaGetLastError());
+    } else {
+        size_t off = a256(sizeof(StateHeader));
+        for (auto& q : seg) {
+            CK(cudaMemcpyAsync(out + off, q.first, q.second, k, s->stream));
+            off += a256(q.second);
+        }
     }
     CK(cudaStreamSynchronize(s->stream));
     return SIM_OK;
@@ -1294,10 +1330,17 @@ sim_status sim_state_load(sim_t* s, const void* buf, int on_device) {
         return fail(s, SIM_EINVAL, "restart blob does not match this simulation");
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const char* in = (const char*)buf;
-    size_t off = a256(sizeof(StateHeader));
-    for (auto& q : state_segments(s)) {
-        CK(cudaMemcpyAsync(q.first, in + off, q.second, k, s->stream));
-        off += a256(q.second);
+    const auto seg = state_segments(s);
+    char* mapped = on_device ? nullptr : mapped_host(buf, seg);
+    if (mapped) {
+        launch_state_copy(state_copy_table(seg), mapped, 1, s->stream);
+        CK(cudaGetLastError());
+    } else {
+        size_t off = a256(sizeof(StateHeader));
+        for (auto& q : seg) {
+            CK(cudaMemcpyAsync(q.first, in + off, q.second, k, s->stream));
+            off += a256(q.second);
+        }
     }
     if (!on_device) CK(cudaStreamSynchronize(s->stream));
     s->rho_base = h.rho_base;
