@@ -1301,7 +1301,7 @@ sim_status sim_state_save(sim_t* s, void* buf, int on_device) {
     h.ibm_active = s->ibm_active;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     char* out = (char*)buf;
-    CK(cudaMemcpyAsync(out, &h, sizeof(h), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s->stream));
+    if (on_device) CK(cudaMemcpyAsync(out, &h, sizeof(h), cudaMemcpyHostToDevice, s->stream));
     const auto seg = state_segments(s);
     char* mapped = on_device ? nullptr : mapped_host(buf, seg);
     if (mapped) {
@@ -1315,6 +1315,7 @@ sim_status sim_state_save(sim_t* s, void* buf, int on_device) {
         }
     }
     CK(cudaStreamSynchronize(s->stream));
+    if (!on_device) std::memcpy(out, &h, sizeof(h));   // a host blob's header, written by the host
     return SIM_OK;
 }
 
