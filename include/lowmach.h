@@ -184,10 +184,10 @@ sim_status sim_query(sim_t *sim, int what, double *out);
  * header that identifies the grid.  save copies the blob out (synchronises);
  * load copies it in and the next sim_step continues from it exactly as if the
  * run had never stopped (SIM_EINVAL if the header does not match this grid).
- * buf is a device pointer when on_device = 1, else a host pointer.  A pinned
- * (page-locked, device-mapped) host buffer moves in one pack / unpack kernel
- * that addresses it directly; pageable host memory moves by one copy per
- * array.  Both return once the host buffer may be reused. */
+ * buf is a device pointer when on_device = 1, else a host pointer.  The
+ * blob's body is one contiguous image of the workspace's state arrays, so it
+ * moves in one copy (fastest from pinned host memory); both calls return once
+ * a host buffer may be reused. */
 sim_status sim_state_size(const sim_t *sim, size_t *bytes);
 sim_status sim_state_save(sim_t *sim, void *buf, int on_device);
 sim_status sim_state_load(sim_t *sim, const void *buf, int on_device);

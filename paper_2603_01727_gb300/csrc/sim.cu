@@ -272,24 +272,34 @@ size_t layout(const sim_params_t* p, sim_t* s, char* base) {
     sim_t tmp;
     sim_t* t = s ? s : &tmp;
     auto F = [&](double** dst) { *dst = (double*)take(fpad); };
+    // the restart state first, in the order and with the padding of the
+    // restart blob (state_segments), so that the blob's body is one
+    // contiguous image of the workspace
     for (int d = 0; d < D; ++d) F(&t->v[d]);
-    for (int d = 0; d < D; ++d) F(&t->vs[d]);
-    F(&t->Z); F(&t->H); F(&t->Zs); F(&t->Hs); F(&t->T); F(&t->kap);
+    F(&t->Z); F(&t->H); F(&t->T); F(&t->kap);
     for (int r = 0; r < 3; ++r) F(&t->rho[r]);
-    for (int d = 0; d < D; ++d) F(&t->mom[d]);
     for (int d = 0; d < D; ++d) F(&t->F[d]);
     for (int k = 0; k < 2; ++k) {
         for (int d = 0; d < D; ++d) F(&t->R[k][d]);
         F(&t->R[k][3]);
         F(&t->R[k][4]);
     }
+    {
+        double* q = (double*)take(fcmp);
+        if (s) s->P = q;
+        q = (double*)take(sizeof(double) * SC_NSCAL);
+        if (s) s->sc = q;
+        int* st = (int*)take(sizeof(int) * 8);
+        if (s) s->status = st;
+    }
+    for (int d = 0; d < D; ++d) F(&t->vs[d]);
+    F(&t->Zs); F(&t->Hs);
+    for (int d = 0; d < D; ++d) F(&t->mom[d]);
     for (int d = 0; d < D; ++d) F(&t->vib[d]);
     F(&t->Sm);
     F(&t->U);
     {
         double* q = (double*)take(fcmp);
-        if (s) s->P = q;
-        q = (double*)take(fcmp);
         if (s) s->b = q;
         q = (double*)take(sizeof(double) * (size_t)(maxface > g.ncell ? maxface : g.ncell));
         if (s) s->io = q;
@@ -297,12 +307,8 @@ size_t layout(const sim_params_t* p, sim_t* s, char* base) {
         if (s) s->part = q;
         q = (double*)take(sizeof(double) * kMaxPartials);
         if (s) s->part2 = q;
-        q = (double*)take(sizeof(double) * SC_NSCAL);
-        if (s) s->sc = q;
         q = (double*)take(sizeof(double) * kMaxProfile);
         if (s) s->profile = q;
-        int* st = (int*)take(sizeof(int) * 8);
-        if (s) s->status = st;
         uint8_t* c = (uint8_t*)take((size_t)g.npad);
         if (s) s->chi = c;
         for (int d = 0; d < 3; ++d)
@@ -825,6 +831,11 @@ sim_status sim_workspace_size(const sim_params_t* prm, size_t* bytes) {
     return SIM_OK;
 }
 
+namespace {
+std::vector<std::pair<void*, size_t>> state_segments(sim_t* s);
+char* state_image(const std::vector<std::pair<void*, size_t>>& seg, size_t* bytes);
+}  // namespace
+
 sim_status sim_create(const sim_params_t* prm, void* d_workspace, size_t workspace_bytes, void* cuda_stream,
                       sim_t** out) {
     if (!out) return SIM_EINVAL;
@@ -885,7 +896,14 @@ sim_status sim_create(const sim_params_t* prm, void* d_workspace, size_t workspa
     int bc[3][2];
     for (int d = 0; d < 3; ++d)
         for (int q = 0; q < 2; ++q) bc[d][q] = s->bnd.bc[d][q];
-    e = cudaMemsetAsync(s->sc, 0, sizeof(double) * SC_NSCAL, s->stream);
+    {
+        // the restart-state arrays and the padding between them (a blob's
+        // body is their contiguous image, padding included)
+        size_t nimg = 0;
+        char* img = state_image(state_segments(s), &nimg);
+        e = img ? cudaMemsetAsync(img, 0, nimg, s->stream) : cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->sc, 0, sizeof(double) * SC_NSCAL, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->status, 0, sizeof(int) * 8, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->chi, 0, (size_t)s->g.npad, s->stream);
     if (e == cudaSuccess) {
@@ -1243,33 +1261,18 @@ std::vector<std::pair<void*, size_t>> state_segments(sim_t* s) {
     return seg;
 }
 
-// The device address of a pinned (mapped) host buffer, or null: a restart
-// blob there moves in one pack / unpack kernel instead of one copy per array.
-char* mapped_host(const void* buf, const std::vector<std::pair<void*, size_t>>& seg) {
-    if (seg.size() > (size_t)kMaxStateSeg) return nullptr;
-    cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, buf) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (pa.type != cudaMemoryTypeHost || !pa.devicePointer || ((uintptr_t)pa.devicePointer & 15) != 0) return nullptr;
-    for (auto& q : seg)
-        if (((uintptr_t)q.first & 15) != 0) return nullptr;
-    return (char*)pa.devicePointer;
-}
-
-StateCopy state_copy_table(const std::vector<std::pair<void*, size_t>>& seg) {
-    StateCopy c;
-    std::memset(&c, 0, sizeof(c));
-    size_t off = a256(sizeof(StateHeader));
+// The blob's body as one contiguous image of the workspace's state arrays
+// (layout carves them first, in blob order, with the blob's padding): its
+// start and length, or null.
+char* state_image(const std::vector<std::pair<void*, size_t>>& seg, size_t* bytes) {
+    char* base = (char*)seg[0].first;
+    size_t off = 0;
     for (auto& q : seg) {
-        c.dev[c.n] = (char*)q.first;
-        c.bytes[c.n] = q.second;
-        c.off[c.n] = off;
-        ++c.n;
+        if ((char*)q.first != base + off) return nullptr;
         off += a256(q.second);
     }
-    return c;
+    *bytes = off;
+    return base;
 }
 
 size_t state_bytes(sim_t* s) {
@@ -1303,10 +1306,11 @@ sim_status sim_state_save(sim_t* s, void* buf, int on_device) {
     char* out = (char*)buf;
     if (on_device) CK(cudaMemcpyAsync(out, &h, sizeof(h), cudaMemcpyHostToDevice, s->stream));
     const auto seg = state_segments(s);
-    char* mapped = on_device ? nullptr : mapped_host(buf, seg);
-    if (mapped) {
-        launch_state_copy(state_copy_table(seg), mapped, 0, s->stream);
-        CK(cudaGetLastError());
+    size_t nimg = 0;
+    char* img = state_image(seg, &nimg);
+    if (img) {
+        // one copy of the contiguous state image
+        CK(cudaMemcpyAsync(out + a256(sizeof(StateHeader)), img, nimg, k, s->stream));
     } else {
         size_t off = a256(sizeof(StateHeader));
         for (auto& q : seg) {
@@ -1332,10 +1336,10 @@ sim_status sim_state_load(sim_t* s, const void* buf, int on_device) {
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const char* in = (const char*)buf;
     const auto seg = state_segments(s);
-    char* mapped = on_device ? nullptr : mapped_host(buf, seg);
-    if (mapped) {
-        launch_state_copy(state_copy_table(seg), mapped, 1, s->stream);
-        CK(cudaGetLastError());
+    size_t nimg = 0;
+    char* img = state_image(seg, &nimg);
+    if (img) {
+        CK(cudaMemcpyAsync(img, in + a256(sizeof(StateHeader)), nimg, k, s->stream));
     } else {
         size_t off = a256(sizeof(StateHeader));
         for (auto& q : seg) {

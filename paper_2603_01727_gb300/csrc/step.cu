@@ -1685,31 +1685,6 @@ void launch_state_flux_rhs(const Geom& g, const Phys& ph, const double* Z, const
     *launches += 2;
 }
 
-// One block row per segment (blockIdx.y); 16-byte accesses, the ragged tail
-// bytewise.  load: host -> state arrays, else state arrays -> host.
-__global__ void k_state_copy(StateCopy c, char* host, int load) {
-    const int k = blockIdx.y;
-    char* dev = c.dev[k];
-    char* hst = host + c.off[k];
-    const size_t nb = c.bytes[k], n16 = nb >> 4;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x) {
-        if (load) reinterpret_cast<int4*>(dev)[i] = reinterpret_cast<const int4*>(hst)[i];
-        else reinterpret_cast<int4*>(hst)[i] = reinterpret_cast<const int4*>(dev)[i];
-    }
-    if (blockIdx.x == 0)
-        for (size_t b = (n16 << 4) + threadIdx.x; b < nb; b += blockDim.x) {
-            if (load) dev[b] = hst[b];
-            else hst[b] = dev[b];
-        }
-}
-
-void launch_state_copy(const StateCopy& c, char* host, int load, cudaStream_t s) {
-    if (c.n <= 0) return;
-    // about eight blocks per SM over all segments
-    const int bx = (152 * 8 + c.n - 1) / c.n;
-    k_state_copy<<<dim3(bx, c.n), NT, 0, s>>>(c, host, load);
-}
-
 void launch_project(const Geom& g, const Phys& ph, const ProjArgs& a, cudaStream_t s, int* launches) {
     if (g.dim == 3)
         k_project<3><<<blocks_for(g.ncell), NT, 0, s>>>(g, ph, a);

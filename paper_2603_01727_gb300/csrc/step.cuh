@@ -177,18 +177,6 @@ void launch_state_flux_rhs(const Geom& g, const Phys& ph, const double* Z, const
                            double* kap, double* sc, int* status, const Bnd& bnd, bool kap_ghosts,
                            const FluxArgs& a, cudaStream_t s, int* launches);
 void launch_project(const Geom& g, const Phys& ph, const ProjArgs& a, cudaStream_t s, int* launches);
-
-// Restart blob <-> state arrays in one launch, through a host buffer the
-// device can address (pinned, mapped): segment k is bytes[k] bytes at dev[k]
-// (16-byte aligned) and at host + off[k] (off[k] a multiple of 16).
-constexpr int kMaxStateSeg = 32;
-struct StateCopy {
-    int n;
-    char* dev[kMaxStateSeg];
-    size_t bytes[kMaxStateSeg];
-    size_t off[kMaxStateSeg];
-};
-void launch_state_copy(const StateCopy& c, char* host, int load, cudaStream_t s);
 void launch_momentum(const Geom& g, const double* rho, double* const v[3], double* mom[3], cudaStream_t s,
                      int* launches);
 void launch_sum(const Geom& g, const double* x, double* part, cudaStream_t s, int* launches);

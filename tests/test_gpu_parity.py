@@ -297,11 +297,11 @@ def test_graph_and_eager_paths_agree_bitwise(monkeypatch):
 
 @pytest.mark.parametrize("case", ["slot", "sphere"])
 def test_restart_blob_same_through_pinned_pageable_and_device_buffers(case):
-    """sim_state_save / sim_state_load move the restart state through a
-    pinned host buffer with one pack / unpack kernel (the device addresses the
-    buffer), and through pageable host or device memory with one copy per
-    array.  The three blobs must agree byte for byte, and a state loaded
-    through either host path must step to the same bits."""
+    """sim_state_save / sim_state_load move the restart state as one
+    contiguous image of the workspace's state arrays (padding zeroed at
+    creation), into pinned or pageable host memory or device memory.  The three
+    blobs must agree byte for byte, and a state loaded through either host
+    buffer must step to the same bits."""
     import torch
     prm, geo, f = W.slot_burner(64, 128) if case == "slot" else W.sphere_burner(24)
     prm["precision"] = W.MIXED
