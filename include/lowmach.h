@@ -191,6 +191,13 @@ sim_status sim_query(sim_t *sim, int what, double *out);
 sim_status sim_state_size(const sim_t *sim, size_t *bytes);
 sim_status sim_state_save(sim_t *sim, void *buf, int on_device);
 sim_status sim_state_load(sim_t *sim, const void *buf, int on_device);
+/* One step (sim_step(sim, 1)) whose restart blob -- the state after the step,
+ * as sim_state_save writes it -- goes to buf while the step runs: the arrays
+ * that are final once the corrector's state relation has run (Z, H, T,
+ * kappa, rho, the stored residuals) are copied on a private stream during the
+ * corrector's pressure solve, the rest after the step.  buf as for
+ * sim_state_save (sim_state_size() bytes); synchronises. */
+sim_status sim_step_save(sim_t *sim, void *buf, int on_device);
 
 /* Kernel timing support: enqueue `reps` back-to-back launches of one kernel of
  * the next step with that step's arguments (no synchronisation), so a caller

@@ -111,6 +111,8 @@ struct sim {
     cudaGraphExec_t solve_exec[3];
     bool solve_valid[3];
     int solve_fixed[3], solve_body[3];   // kernels of a solve graph outside / per loop iteration
+    cudaStream_t save_stream = nullptr;   // private stream: the restart blob's early part (sim_step_save)
+    cudaEvent_t ev_early = nullptr;   // recorded in a step once the early state arrays are final
 
     char err[512];
 };
@@ -274,16 +276,17 @@ size_t layout(const sim_params_t* p, sim_t* s, char* base) {
     auto F = [&](double** dst) { *dst = (double*)take(fpad); };
     // the restart state first, in the order and with the padding of the
     // restart blob (state_segments), so that the blob's body is one
-    // contiguous image of the workspace
-    for (int d = 0; d < D; ++d) F(&t->v[d]);
+    // contiguous image of the workspace: the arrays final once the
+    // corrector's state relation has run, then those the step's end writes
     F(&t->Z); F(&t->H); F(&t->T); F(&t->kap);
     for (int r = 0; r < 3; ++r) F(&t->rho[r]);
-    for (int d = 0; d < D; ++d) F(&t->F[d]);
     for (int k = 0; k < 2; ++k) {
         for (int d = 0; d < D; ++d) F(&t->R[k][d]);
         F(&t->R[k][3]);
         F(&t->R[k][4]);
     }
+    for (int d = 0; d < D; ++d) F(&t->v[d]);
+    for (int d = 0; d < D; ++d) F(&t->F[d]);
     {
         double* q = (double*)take(fcmp);
         if (s) s->P = q;
@@ -754,6 +757,14 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
             if (D == 3) ghost(s, {{s->kap, GW_KAPPA}}, st, L);
             launch_flux_rhs(g, s->ph, s->bnd, fa, st, L);
         }
+        // Z, H, T, kappa, rho and the stored residuals -- the early part of the
+        // restart blob -- are final from here on (sim_step_save copies them
+        // while the corrector's solve runs)
+        if (first == SEC_PRED && last == SEC_END && s->ev_early) {
+            const cudaError_t er = cudaEventRecordWithFlags(s->ev_early, st,
+                                                            graph ? cudaEventRecordExternal : cudaEventRecordDefault);
+            if (er != cudaSuccess) return er;
+        }
     }
     if (on(SEC_POIS_CORR)) e = enqueue_poisson(s, st, graph, SC_ITERS_CORR, L, body);
     if (e != cudaSuccess) return e;
@@ -884,6 +895,8 @@ sim_status sim_create(const sim_params_t* prm, void* d_workspace, size_t workspa
     sim_status st = SIM_OK;
     cudaError_t e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->save_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_early, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         delete s;
         return SIM_ECUDA;
@@ -1243,18 +1256,20 @@ std::vector<std::pair<void*, size_t>> state_segments(sim_t* s) {
     const Geom& g = s->g;
     const size_t fpad = sizeof(double) * (size_t)g.npad;
     std::vector<std::pair<void*, size_t>> seg;
-    for (int d = 0; d < g.dim; ++d) seg.push_back({s->v[d], fpad});
+    // final once the corrector's state relation has run (kEarlySegments(dim))
     seg.push_back({s->Z, fpad});
     seg.push_back({s->H, fpad});
     seg.push_back({s->T, fpad});
     seg.push_back({s->kap, fpad});
     for (int r = 0; r < 3; ++r) seg.push_back({s->rho[r], fpad});
-    for (int d = 0; d < g.dim; ++d) seg.push_back({s->F[d], fpad});
     for (int k = 0; k < 2; ++k) {
         for (int d = 0; d < g.dim; ++d) seg.push_back({s->R[k][d], fpad});
         seg.push_back({s->R[k][3], fpad});
         seg.push_back({s->R[k][4], fpad});
     }
+    // written at the step's end
+    for (int d = 0; d < g.dim; ++d) seg.push_back({s->v[d], fpad});
+    for (int d = 0; d < g.dim; ++d) seg.push_back({s->F[d], fpad});
     seg.push_back({s->P, sizeof(double) * (size_t)g.ncell});
     seg.push_back({s->sc, sizeof(double) * SC_NSCAL});
     seg.push_back({s->status, sizeof(int) * 8});
@@ -1275,6 +1290,19 @@ char* state_image(const std::vector<std::pair<void*, size_t>>& seg, size_t* byte
     return base;
 }
 
+void fill_header(const sim_t* s, StateHeader* h) {
+    std::memset(h, 0, sizeof(*h));
+    std::memcpy(h->magic, "LMSTATE", 8);
+    h->version = 2;
+    h->dim = s->g.dim;
+    for (int d = 0; d < 3; ++d) h->n[d] = s->g.n[d];
+    h->rho_base = s->rho_base;
+    h->nstep = s->nstep;
+    h->t = s->t;
+    h->dt = s->prm.dt;
+    h->ibm_active = s->ibm_active;
+}
+
 size_t state_bytes(sim_t* s) {
     size_t b = a256(sizeof(StateHeader));
     for (auto& q : state_segments(s)) b += a256(q.second);
@@ -1292,16 +1320,7 @@ sim_status sim_state_save(sim_t* s, void* buf, int on_device) {
     if (!s || !buf) return SIM_EINVAL;
     if (s->need_init) return fail(s, SIM_ESTATE, "no state yet: step once after setting the fields");
     StateHeader h;
-    std::memset(&h, 0, sizeof(h));
-    std::memcpy(h.magic, "LMSTATE", 8);
-    h.version = 1;
-    h.dim = s->g.dim;
-    for (int d = 0; d < 3; ++d) h.n[d] = s->g.n[d];
-    h.rho_base = s->rho_base;
-    h.nstep = s->nstep;
-    h.t = s->t;
-    h.dt = s->prm.dt;
-    h.ibm_active = s->ibm_active;
+    fill_header(s, &h);
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     char* out = (char*)buf;
     if (on_device) CK(cudaMemcpyAsync(out, &h, sizeof(h), cudaMemcpyHostToDevice, s->stream));
@@ -1323,6 +1342,32 @@ sim_status sim_state_save(sim_t* s, void* buf, int on_device) {
     return SIM_OK;
 }
 
+sim_status sim_step_save(sim_t* s, void* buf, int on_device) {
+    if (!s || !buf) return SIM_EINVAL;
+    const sim_status st = sim_step(s, 1);
+    if (st != SIM_OK) return st;
+    const auto seg = state_segments(s);
+    size_t nimg = 0;
+    char* img = state_image(seg, &nimg);
+    if (!img) return sim_state_save(s, buf, on_device);
+    // the arrays final after the corrector's state relation lead the image
+    const int ne = 7 + 2 * (s->g.dim + 2);
+    size_t nearly = 0;
+    for (int i = 0; i < ne; ++i) nearly += a256(seg[(size_t)i].second);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    char* out = (char*)buf + a256(sizeof(StateHeader));
+    CK(cudaStreamWaitEvent(s->save_stream, s->ev_early, 0));
+    CK(cudaMemcpyAsync(out, img, nearly, k, s->save_stream));
+    CK(cudaMemcpyAsync(out + nearly, img + nearly, nimg - nearly, k, s->stream));
+    StateHeader h;
+    fill_header(s, &h);
+    if (on_device) CK(cudaMemcpyAsync(buf, &h, sizeof(h), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->save_stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (!on_device) std::memcpy(buf, &h, sizeof(h));
+    return SIM_OK;
+}
+
 sim_status sim_state_load(sim_t* s, const void* buf, int on_device) {
     if (!s || !buf) return SIM_EINVAL;
     StateHeader h;
@@ -1330,7 +1375,7 @@ sim_status sim_state_load(sim_t* s, const void* buf, int on_device) {
         CK(cudaMemcpy(&h, buf, sizeof(h), cudaMemcpyDeviceToHost));
     else
         std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "LMSTATE", 8) != 0 || h.version != 1 || h.dim != s->g.dim || h.dt != s->prm.dt ||
+    if (std::memcmp(h.magic, "LMSTATE", 8) != 0 || h.version != 2 || h.dim != s->g.dim || h.dt != s->prm.dt ||
         h.n[0] != s->g.n[0] || h.n[1] != s->g.n[1] || h.n[2] != s->g.n[2] || h.ibm_active != s->ibm_active)
         return fail(s, SIM_EINVAL, "restart blob does not match this simulation");
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -1365,6 +1410,8 @@ void sim_destroy(sim_t* s) {
         if (s->gvalid[k]) cudaGraphExecDestroy(s->gexec[k]);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->side) cudaStreamDestroy(s->side);
+    if (s->save_stream) cudaStreamDestroy(s->save_stream);
+    if (s->ev_early) cudaEventDestroy(s->ev_early);
     delete s;
 }
 

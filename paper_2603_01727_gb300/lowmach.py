@@ -84,6 +84,7 @@ def load():
         "sim_state_size": ([VP, P(SZ)], I),
         "sim_state_save": ([VP, VP, I], I),
         "sim_state_load": ([VP, VP, I], I),
+        "sim_step_save": ([VP, VP, I], I),
         "sim_poisson_workspace_size": ([I, P(I), P(I), P(SZ)], I),
         "sim_poisson_solve": ([I, P(I), P(D), P(I), VP, VP, D, I, VP, SZ, VP, P(I), P(D)], I),
         "sim_poisson_solve_noalloc": ([I, P(I), P(D), P(I), VP, VP, D, I, VP, P(I), P(D)], I),
@@ -115,7 +116,7 @@ def exported_symbols():
     return ["sim_workspace_size", "sim_create", "sim_set_ibm_geometry", "sim_fields", "sim_step",
             "sim_sync", "sim_query", "sim_last_error", "sim_destroy", "sim_time_kernel", "sim_state_size",
             "sim_state_save",
-            "sim_state_load", "sim_poisson_workspace_size",
+            "sim_state_load", "sim_step_save", "sim_poisson_workspace_size",
             "sim_poisson_solve", "sim_poisson_solve_noalloc", "sim_poisson_batch_workspace_size",
             "sim_poisson_solve_batch", "sim_objective", "sim_adjoint_workspace_size",
             "sim_adjoint_begin", "sim_adjoint_step", "sim_adjoint_field", "sim_adjoint_end",
@@ -272,6 +273,11 @@ class Simulation:
     def state_load(self, buf):
         ptr, dev = self._buf(buf)
         _check(self.lib, self.lib.sim_state_load(self.h, ptr, dev), self.h)
+
+    def step_save(self, buf):
+        """One step, its restart blob copied into buf while the step runs."""
+        ptr, dev = self._buf(buf)
+        _check(self.lib, self.lib.sim_step_save(self.h, ptr, dev), self.h)
 
     # --------------------------- objective and adjoint ---------------------------
     def objective(self):

@@ -328,6 +328,31 @@ def test_restart_blob_same_through_pinned_pageable_and_device_buffers(case):
     sim.close()
 
 
+@pytest.mark.parametrize("case", ["slot", "sphere"])
+def test_step_save_equals_step_then_state_save(case):
+    """sim_step_save copies the arrays that are final after the corrector's
+    state relation while the corrector's solve runs, the rest after the step:
+    its blob must equal sim_step followed by sim_state_save byte for byte,
+    through the eager first steps and the step graphs."""
+    import torch
+    from paper_2603_01727_gb300.lowmach import Simulation
+    prm, geo, f = W.slot_burner(64, 128) if case == "slot" else W.sphere_burner(24)
+    prm["precision"] = W.MIXED
+    a, b = Simulation(prm, geo), Simulation(prm, geo)
+    a.set_fields(f)
+    b.set_fields(f)
+    n = a.state_size()
+    ref = np.zeros(n, dtype=np.uint8)
+    out = torch.zeros(n, dtype=torch.uint8, pin_memory=True)
+    for _ in range(5):
+        a.step(1)
+        a.state_save(ref)
+        b.step_save(out)
+        assert np.array_equal(ref, out.numpy())
+    a.close()
+    b.close()
+
+
 def test_repeat_runs_are_bitwise_deterministic():
     prm, geo, f = W.periodic_blobs(48)
     a = gpu_run(prm, geo, f, 12)
