@@ -898,6 +898,11 @@ sim_status sim_create(const sim_params_t* prm, void* d_workspace, size_t workspa
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->save_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_early, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        // release whatever was created before the failure
+        if (s->cap) cudaStreamDestroy(s->cap);
+        if (s->side) cudaStreamDestroy(s->side);
+        if (s->save_stream) cudaStreamDestroy(s->save_stream);
+        if (s->ev_early) cudaEventDestroy(s->ev_early);
         delete s;
         return SIM_ECUDA;
     }
