@@ -318,6 +318,267 @@ def test_variable_density_richardson_order():
 
 
 # ---------------------------------------------------------------------------
+# Manufactured solution (verification of Sec. 4.1, Eq 4.1): the discrete
+# right-hand sides of the oracle against the continuous operators of
+# Eqs 2.43-2.46 applied to smooth, non-solenoidal, variable-density fields.
+# ---------------------------------------------------------------------------
+def _mms_exact(dim, Pr, Pe, fp, p0dot, inv_Fr2):
+    """Continuous right-hand sides, symbolically differentiated (sympy):
+
+    Rv_i = -div(rho v v_i) + (Pr/Pe) div(tau_i) + (1/Fr^2)(1 - rho) e_2   (Eqs 2.43, 2.46)
+    RZ   = [-rho v.grad Z + div(kappa grad Z)/(Le Pe)] / rho              (Eq 2.44)
+    RH   = [-rho v.grad H + zeta dp0/dt
+            + (div(kappa grad H) + N div(kappa grad Z))/Pe] / rho         (Eq 2.45)
+    with Le(Z), N(Z) regularised by Eq 3.35."""
+    sp = pytest.importorskip("sympy")
+    X = sp.symbols("x y z")[:dim]
+    tp = 2 * sp.pi
+    if dim == 2:
+        x, y = X
+        vel = [0.3 * sp.sin(tp * x) * sp.cos(2 * tp * y) + 0.2 * sp.cos(tp * (x + 2 * y)),
+               0.25 * sp.cos(tp * x + 1) * sp.sin(tp * y) + 0.1 * sp.sin(2 * tp * x)]
+        T = 2 + 0.8 * sp.sin(tp * x) * sp.sin(tp * y + 0.3)
+        Z = 1.1 + 0.6 * sp.cos(tp * x) * sp.sin(tp * y + 0.7)
+        H = 1.4 + 0.3 * sp.sin(tp * (x - y))
+    else:
+        x, y, z = X
+        vel = [0.3 * sp.sin(tp * x) * sp.cos(tp * y) * sp.cos(tp * z + 0.4),
+               0.25 * sp.cos(tp * x + 1) * sp.sin(tp * y) + 0.1 * sp.sin(tp * z),
+               0.2 * sp.sin(tp * (x + y)) * sp.cos(tp * z) + 0.15 * sp.cos(tp * z)]
+        T = 2 + 0.8 * sp.sin(tp * x) * sp.sin(tp * y + 0.3) * sp.cos(tp * z)
+        Z = 1.1 + 0.6 * sp.cos(tp * x) * sp.sin(tp * y + 0.7) * sp.sin(tp * z + 0.2)
+        H = 1.4 + 0.3 * sp.sin(tp * (x - y + z))
+    rho = 1 / T
+    kap = T ** sp.Rational(7, 10)
+    div = sum(sp.diff(vel[k], X[k]) for k in range(dim))
+    Rv = []
+    for i in range(dim):
+        conv = sum(sp.diff(rho * vel[j] * vel[i], X[j]) for j in range(dim))
+        visc = 0
+        for j in range(dim):
+            tau = kap * (sp.diff(vel[i], X[j]) + sp.diff(vel[j], X[i]))
+            if i == j:
+                tau -= sp.Rational(2, 3) * kap * div
+            visc += sp.diff(tau, X[j])
+        R = -conv + Pr / Pe * visc
+        if i == 1:
+            R += inv_Fr2 * (1 - rho)
+        Rv.append(R)
+    theta = (1 + sp.tanh(fp["k"] * (Z - 1))) / 2
+    Le = (fp["Le_F"] - fp["Le_O"]) * theta + fp["Le_O"]
+    N = (fp["N_F"] - fp["N_O"]) * theta + fp["N_O"]
+    lap = lambda phi: sum(sp.diff(kap * sp.diff(phi, X[j]), X[j]) for j in range(dim))
+    adv = lambda phi: sum(rho * vel[j] * sp.diff(phi, X[j]) for j in range(dim))
+    RZ = (-adv(Z) + lap(Z) / (Le * Pe)) / rho
+    RH = (-adv(H) + fp["zeta"] * p0dot + (lap(H) + N * lap(Z)) / Pe) / rho
+    f = lambda e: sp.lambdify(X, e, "numpy")
+    return dict(v=[f(e) for e in vel], T=f(T), rho=f(rho), kap=f(kap), Z=f(Z), H=f(H),
+                mflux=[f(rho * vel[j]) for j in range(dim)],
+                Rv=[f(e) for e in Rv], RZ=f(RZ), RH=f(RH))
+
+
+def _mms_errors(dim, n, ex, prm_over):
+    prm = W.taylor_green(n)[0]
+    prm.update(incompressible=0, dim=dim, n=[n] * dim + [1] * (3 - dim), L=[1.0, 1.0, 1.0])
+    prm.update(prm_over)
+    pb = S.Problem(prm, None)
+    g = pb.g
+    cen = [g.centres(d) for d in range(dim)]
+    ev = lambda fn, pts: np.broadcast_to(fn(*pts), g.shape).copy()
+    v = [ev(ex["v"][i], cen) for i in range(dim)]
+    Z, H, rho, kap = (ev(ex[k], cen) for k in ("Z", "H", "rho", "kap"))
+    F = []
+    for j in range(dim):
+        pts = list(cen)
+        pts[j] = cen[j] - 0.5 * g.h[j]          # padded face f of direction j at (f-1) h_j
+        F.append(ev(ex["mflux"][j], pts))
+    R = S.residuals(pb, v, Z, H, rho, kap, F, prm_over["p0dot"])
+    inner = [V(c, g) for c in cen]
+    err = {}
+    for i in range(dim):
+        want = ex["Rv"][i](*inner)
+        err[f"v{i}"] = float(np.max(np.abs(R["v"][i] - want)))
+    err["Z"] = float(np.max(np.abs(R["Z"] - ex["RZ"](*inner))))
+    err["H"] = float(np.max(np.abs(R["H"] - ex["RH"](*inner))))
+    return err
+
+
+@pytest.mark.parametrize("dim,ns", [(2, (32, 64, 128)), (3, (16, 32, 64))])
+def test_manufactured_residuals_second_order(dim, ns):
+    """Every component of the oracle's right-hand sides (momentum with the
+    transpose and -2/3 dilatation terms of Eq 2.46 and interface-interpolated
+    kappa of Eq 3.20, Z and H with variable kappa, the 1/rho bracket, the
+    regularised Le and N of Eq 3.35, zeta dp0/dt and buoyancy) converges to the
+    continuous operator at the observed order 2 of Eq 4.1."""
+    over = dict(Re=40.0, Pr=0.7, Le_F=0.8, Le_O=1.3, eps_reg=2.0, tol_reg=1e-3,
+                inv_Fr2=0.6, p0dot=0.37)
+    fp = flame.derived_parameters(0.055, 7.0, over["eps_reg"], over["tol_reg"],
+                                  over["Le_F"], over["Le_O"], 1.4)
+    ex = _mms_exact(dim, over["Pr"], over["Re"] * over["Pr"], fp, over["p0dot"], over["inv_Fr2"])
+    errs = [_mms_errors(dim, n, ex, over) for n in ns]
+    for key in errs[0]:
+        b1 = observed_order(errs[0][key], errs[1][key], 2.0)
+        b2 = observed_order(errs[1][key], errs[2][key], 2.0)
+        assert b2 == pytest.approx(2.0, abs=0.05), (key, [e[key] for e in errs], b1, b2)
+        assert b1 == pytest.approx(2.0, abs=0.15), (key, [e[key] for e in errs], b1, b2)
+
+
+# ---------------------------------------------------------------------------
+# Differential diffusion (Eqs 2.34-2.37, 3.35): away from the flame the Z and H
+# right-hand sides are the combinations of the species and temperature
+# equations (Eqs 2.28-2.30) that define Z = S Y_F - Y_O + 1 and
+# H = (S+1) T/Q + Y_F + Y_O, with no reaction on either side of the sheet.
+# ---------------------------------------------------------------------------
+def _smooth_periodic_state(n, zlo, zhi):
+    x, y = W.cell_centres((n, n), (1.0, 1.0))
+    tp = 2 * np.pi
+    mid, amp = 0.5 * (zlo + zhi), 0.5 * (zhi - zlo)
+    Z = mid + amp * np.sin(tp * x + 0.3) * np.cos(tp * y)
+    H = 1.2 + 0.2 * np.cos(tp * (x + y))
+    u = 0.2 * np.sin(tp * x) * np.cos(tp * y) + 0.05 * np.cos(tp * y)
+    v = -0.1 * np.cos(tp * x) * np.sin(2 * tp * y)
+    rho = 1.0 / (1.5 + 0.4 * np.sin(tp * y + 0.1) * np.cos(tp * x))
+    kap = (1.0 / rho) ** 0.7
+    return [u, v], Z, H, rho, kap
+
+
+def _rhs(prm, over, v, Z, H, rho, kap, p0dot):
+    """Oracle right-hand sides for interior fields on a periodic box (ghosts periodic)."""
+    p = dict(prm)
+    p.update(over)
+    pb = S.Problem(p, None)
+    g = pb.g
+    padded = []
+    for a in list(v) + [Z, H, rho, kap]:
+        A = g.zeros()
+        V(A, g)[...] = a
+        for j in range(g.dim):
+            S.bnd_fill_periodic(A, g, j)
+        padded.append(A)
+    vp, Zp, Hp, rp, kp = padded[:2], padded[2], padded[3], padded[4], padded[5]
+    mom = [V(rp, g) * V(vp[j], g) for j in range(g.dim)]
+    F = []
+    for j in range(g.dim):
+        m = g.zeros()
+        V(m, g)[...] = mom[j]
+        S.bnd_fill_periodic(m, g, j)
+        for k in range(g.dim):
+            if k != j:
+                S.bnd_fill_periodic(m, g, k)
+        Fj = g.zeros()
+        V(Fj, g, face=j)[...] = 0.5 * (V(m, g, off=g.unit(j, -1), face=j) + V(m, g, face=j))
+        F.append(Fj)
+    return S.residuals(pb, vp, Zp, Hp, rp, kp, F, p0dot), pb.fp
+
+
+@pytest.mark.parametrize("side", ["fuel", "oxidiser"])
+def test_lewis_number_terms_follow_the_species_equations(side):
+    """Fuel side (Z > 1): Y_O = 0, Y_F = (Z-1)/S, so Z obeys the fuel equation
+    (Le_F) and H = (S+1)T/Q + Y_F combines the temperature and fuel equations.
+    Oxidiser side (Z < 1): Y_F = 0, Y_O = 1 - Z, Le_O.  The reference right-hand
+    sides are built from constant-Lewis-number scalar transport (the operator
+    pinned by the manufactured solution) applied to Y_F, Y_O and T, so a swapped
+    Le_F / Le_O or N_F / N_O, a wrong sign of N or a wrong zeta fails here."""
+    n = 24
+    prm = W.periodic_blobs(n)[0]
+    prm.update(closed_system=0)
+    LeF, LeO, gam = 0.85, 1.25, 1.4
+    sharp = dict(eps_reg=0.5, tol_reg=1e-15)         # theta_eps = 0 or 1 to rounding away from Z = 1
+    zlo, zhi = (1.6, 4.0) if side == "fuel" else (-1.5, 0.4)
+    v, Z, H, rho, kap = _smooth_periodic_state(n, zlo, zhi)
+    p0dot = 0.31
+    got, fp = _rhs(prm, dict(sharp, Le_F=LeF, Le_O=LeO, gamma=gam), v, Z, H, rho, kap, p0dot)
+    S_, Q = fp["S"], fp["Q"]
+    # constant-Lewis-number transport of a passive scalar phi: (1/rho)[-F.grad phi + div(kappa grad phi)/(Le Pe)]
+    scal = lambda phi, Le: _rhs(prm, dict(sharp, Le_F=Le, Le_O=Le, gamma=gam), v, phi, H, rho, kap, 0.0)[0]["Z"]
+    if side == "fuel":
+        Y = (Z - 1.0) / S_
+        Le_side, dZ_dY = LeF, S_
+    else:
+        Y = 1.0 - Z
+        Le_side, dZ_dY = LeO, -1.0
+    T = Q / (S_ + 1.0) * (H - Y)
+    R_Y = scal(Y, Le_side)                                        # Eqs 2.28 / 2.29, no reaction
+    R_T = scal(T, 1.0) + (gam - 1.0) / gam * p0dot / rho          # Eq 2.30
+    want_Z = dZ_dY * R_Y
+    want_H = (S_ + 1.0) / Q * R_T + R_Y
+    scale_Z = np.max(np.abs(want_Z))
+    scale_H = np.max(np.abs(want_H))
+    assert np.max(np.abs(got["Z"] - want_Z)) < 1e-11 * scale_Z
+    assert np.max(np.abs(got["H"] - want_H)) < 1e-11 * scale_H
+    # the Lewis-number terms are not negligible here: Le = 1 would fail the check
+    unit, _ = _rhs(prm, dict(sharp, Le_F=1.0, Le_O=1.0, gamma=gam), v, Z, H, rho, kap, p0dot)
+    assert np.max(np.abs(unit["H"] - want_H)) > 1e-3 * scale_H
+    assert np.max(np.abs(unit["Z"] - want_Z)) > 1e-3 * scale_Z
+
+
+def test_regularised_lewis_number_midpoint_and_limits():
+    """At the flame (Z = 1) the regularised Heaviside of Eq 3.34 is 1/2, so
+    Le_eps and N_eps of Eq 3.35 are the means of their two sides; far from it
+    they tend to the side values at the rate exp(-2k|Z-1|)."""
+    fp = flame.derived_parameters(0.055, 7.0, 0.5, 1e-3, Le_F=0.97, Le_O=1.11)
+    S_, k = fp["S"], fp["k"]
+    NF = (1.0 - 0.97) / (S_ * 0.97)
+    NO = (1.11 - 1.0) / 1.11
+    assert flame.lewis_eps(np.array(1.0), fp) == pytest.approx(0.5 * (0.97 + 1.11), rel=1e-15)
+    assert flame.N_eps(np.array(1.0), fp) == pytest.approx(0.5 * (NF + NO), rel=1e-14)
+    for dz in (1.0, 2.0, 3.0):
+        w = np.exp(-2.0 * k * dz)
+        assert abs(flame.lewis_eps(np.array(1.0 + dz), fp) - 0.97) <= 1.01 * w * abs(0.97 - 1.11) + 1e-16
+        assert abs(flame.lewis_eps(np.array(1.0 - dz), fp) - 1.11) <= 1.01 * w * abs(0.97 - 1.11) + 1e-16
+        assert abs(flame.N_eps(np.array(1.0 + dz), fp) - NF) <= 1.01 * w * abs(NF - NO) + 1e-16
+        assert abs(flame.N_eps(np.array(1.0 - dz), fp) - NO) <= 1.01 * w * abs(NF - NO) + 1e-16
+
+
+def _vd_taylor_green(n, nsteps, dt):
+    """Taylor-Green velocity in the enclosed periodic box with a non-uniform
+    mixture fraction on the oxidiser side of the sheet (Z in [0.05, 0.45], so
+    T = 1 + Q Z/(S+1) in [1.3, 3.7] and no heat release) and slow scalar
+    diffusion (Pr = 50): a variable-density vortex that is nearly solenoidal.
+    Returns the kinetic energy int rho |v|^2 / 2 dV after every step and the
+    density range."""
+    prm, geo, f = W.periodic_blobs(n)
+    prm.update(dt=dt, Pr=50.0)
+    pb = S.Problem(prm, geo)
+    g = pb.g
+    x, y = W.cell_centres((n, n), (1.0, 1.0))
+    Z0 = 0.25 + 0.2 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+    u0 = 0.1 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    v0 = -0.1 * np.cos(2 * np.pi * x) * np.sin(2 * np.pi * y)
+    st = S.initial_state(pb, [u0, v0], Z0, f["H"])
+    ke = lambda s: 0.5 * float(np.sum(V(s.rho, g) * (V(s.v[0], g) ** 2 + V(s.v[1], g) ** 2)) * g.dV)
+    out = [ke(st)]
+    lo, hi = float(V(st.rho, g).min()), float(V(st.rho, g).max())
+    for _ in range(nsteps):
+        st = S.advance(pb, st)
+        out.append(ke(st))
+        lo, hi = min(lo, float(V(st.rho, g).min())), max(hi, float(V(st.rho, g).max()))
+    return np.array(out), lo, hi, prm
+
+
+def test_variable_density_taylor_green_decay():
+    """Kinetic energy of the variable-density vortex decays monotonically (the
+    viscous term of Eqs 2.43/2.46 dissipates, kappa [2 S:S - 2/3 (div v)^2] >= 0 in
+    2D), no faster than the hottest, lightest fluid and no slower than the
+    coldest, densest fluid would let the single Taylor-Green mode decay, and the
+    final energy converges at second order across three grids (Eq 4.2)."""
+    finals = []
+    for n in (16, 32, 64):
+        ke, rho_lo, rho_hi, prm = _vd_taylor_green(n, 100, 2e-4)
+        assert np.all(np.diff(ke) < 0.0), n
+        assert rho_hi / rho_lo > 2.5                       # a genuinely variable density
+        finals.append(ke[-1])
+    t = 100 * 2e-4
+    Re = prm["Re"]
+    T_lo, T_hi = 1.0 / rho_hi, 1.0 / rho_lo                # p0 stays close to 1: rho ~ 1/T
+    # single-mode decay rate 16 pi^2 nu of the energy, nu = kappa/rho in [T_lo^1.7, T_hi^1.7]/Re
+    slow = np.exp(-16 * np.pi ** 2 * (0.5 * T_lo ** 1.7) / Re * t)
+    fast = np.exp(-16 * np.pi ** 2 * (2.0 * T_hi ** 1.7) / Re * t)
+    assert fast < finals[-1] / ke[0] < slow
+    assert richardson_order(*finals, 2.0) == pytest.approx(2.0, abs=0.1)
+
+
+# ---------------------------------------------------------------------------
 # Penalisation (Eqs 3.30-3.32): a body filling a periodic box relaxes v, Z, H
 # exponentially towards the targets; the discrete decay converges at second order
 # ---------------------------------------------------------------------------
