@@ -187,7 +187,12 @@ sim_status sim_query(sim_t *sim, int what, double *out);
  * buf is a device pointer when on_device = 1, else a host pointer.  The
  * blob's body is one contiguous image of the workspace's state arrays, so it
  * moves in one copy (fastest from pinned host memory); both calls return once
- * a host buffer may be reused. */
+ * a host buffer may be reused.  Blob format version 2: a 256-byte-aligned
+ * header, then the segments in this order, each padded to 256 bytes: Z, H, T,
+ * kappa, rho (three levels), the stored residuals of the last two steps (the
+ * arrays final after the corrector's state relation, first), then v, F, P,
+ * the scalars and the status words.  Blobs of version 1 (v and F first) are
+ * refused with SIM_EINVAL. */
 sim_status sim_state_size(const sim_t *sim, size_t *bytes);
 sim_status sim_state_save(sim_t *sim, void *buf, int on_device);
 sim_status sim_state_load(sim_t *sim, const void *buf, int on_device);
@@ -196,7 +201,9 @@ sim_status sim_state_load(sim_t *sim, const void *buf, int on_device);
  * that are final once the corrector's state relation has run (Z, H, T,
  * kappa, rho, the stored residuals) are copied on a private stream during the
  * corrector's pressure solve, the rest after the step.  buf as for
- * sim_state_save (sim_state_size() bytes); synchronises. */
+ * sim_state_save (sim_state_size() bytes); synchronises.  On every return,
+ * an error included, both copies have finished, so the caller may free or
+ * reuse buf at once. */
 sim_status sim_step_save(sim_t *sim, void *buf, int on_device);
 
 /* Kernel timing support: enqueue `reps` back-to-back launches of one kernel of
@@ -346,7 +353,9 @@ sim_status sim_poisson_solve_batch(const int n[2], const double h[2], const int 
  *
  * - The first call on a device looks up the array's device address with that
  *   device current (one-time set-up); make that first call before any stream
- *   capture on the device.
+ *   capture on the device.  The address is kept for the life of the process,
+ *   so cudaDeviceReset between calls is not supported: a reset reloads the
+ *   module and the kept address would no longer name the array.
  * - Returns SIM_ENOMEM, before touching the GPU, when the grid needs more than
  *   SIM_NOALLOC_SCRATCH_BYTES of scratch (sim_poisson_workspace_size gives the
  *   need; about 40 bytes per cell, e.g. 2D grids up to roughly 400 000 cells).

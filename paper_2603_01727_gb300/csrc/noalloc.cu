@@ -13,7 +13,9 @@
 // in every GPU that loads this library until the process exits.  Host code
 // cannot use the array's name as a device address (on the host it names a
 // shadow object), so the first call on each device looks the device address up
-// with cudaGetSymbolAddress while that device is current and caches it.
+// with cudaGetSymbolAddress while that device is current and caches it.  The
+// cache is never invalidated: a cudaDeviceReset between calls (which reloads
+// the module) is not supported, as the header states.
 
 #include <cstring>
 #include <mutex>

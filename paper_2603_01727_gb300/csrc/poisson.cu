@@ -246,9 +246,12 @@ __device__ __forceinline__ int block_linear() {
 // ---------------------------------------------------------------------------
 template <class T, class TF, int DIM>
 __global__ void __launch_bounds__(Tile<DIM>::NT) k_mg_down(LvT<T> L, LvT<T> C, const TF* __restrict__ f,
-                                                           T* __restrict__ upre, T* __restrict__ fc) {
+                                                           T* __restrict__ upre, T* __restrict__ fc,
+                                                           const double* __restrict__ scal_r) {
     pdl_wait();
     pdl_trigger();
+    // fine level: the CG residual enters the preconditioner with its mean removed
+    const TF mr = scal_r ? (TF)scal_r[PS_MEANR] : (TF)0;
     constexpr int H = 3;
     using B = Box<DIM, H>;
     constexpr int NT = Tile<DIM>::NT;
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(Tile<DIM>::NT) k_mg_down(LvT<T> L, LvT<T> C, c
         bool own;
         T fv = (T)0, uv = (T)0;
         if (cell_info<T, DIM>(L, o, s, H, F, &gi, &cl, &own)) {
-            fv = (T)f[gi];
+            fv = (T)(f[gi] - mr);
             if (((par0 + s[0] + s[1] + s[2]) & 1) == 0) uv = fv * L.invd[cl];
         }
         sf[i] = fv;
@@ -354,6 +357,7 @@ __global__ void __launch_bounds__(Tile<DIM>::NT)
             unsigned int* cnt) {
     pdl_wait();
     pdl_trigger();
+    const TF mr = FINE ? (TF)scal[PS_MEANR] : (TF)0;   // fine level: residual mean removed
     constexpr int H = 2;
     using B = Box<DIM, H>;
     constexpr int NT = Tile<DIM>::NT;
@@ -371,7 +375,7 @@ __global__ void __launch_bounds__(Tile<DIM>::NT)
         bool own;
         T fv = (T)0, uv = (T)0;
         if (cell_info<T, DIM>(L, o, s, H, F, &gi, &cl, &own)) {
-            fv = (T)f[gi];
+            fv = (T)(f[gi] - mr);
             int gw[3] = {0, 0, 0};
             int rem = gi;
             gw[0] = rem % L.n[0];
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(Tile<DIM>::NT)
             const T u = su[s[0] + B::S1 * s[1] + B::S2 * s[2]];
             upost[gi] = u;
             if (FINE) {
-                rz = fma(f[gi], (TF)u, rz);
+                rz = fma(f[gi] - mr, (TF)u, rz);
                 sz += (TF)u;
             }
         }
@@ -527,7 +531,7 @@ __global__ void __launch_bounds__(Tile<DIM>::NT)
 // x += alpha p, r -= alpha q, ||r||^2; the last block tests convergence.
 __global__ void __launch_bounds__(NTV)
     k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* p0, const double* p1,
-                const double* __restrict__ q, long long N, double* part, double* scal, int* ictl,
+                const double* __restrict__ q, long long N, double* part, double* part_s, double* scal, int* ictl,
                 unsigned int* cnt, double rtol, int max_iter, cudaGraphConditionalHandle h, int use_graph,
                 int vec2) {
     pdl_wait();
@@ -545,8 +549,9 @@ __global__ void __launch_bounds__(NTV)
     p1 += fb * N;
     q += fb * N;
     part += (long long)fb * gridDim.x;
+    part_s += (long long)fb * gridDim.x;
     const double* __restrict__ p = (it & 1) ? p1 : p0;
-    double rr = 0.0;
+    double rr = 0.0, sr = 0.0;
     if (vec2) {
         // two cells per thread step (16-byte accesses; N even and x 16-byte aligned,
         // the launch is sized by N / 2)
@@ -564,6 +569,7 @@ __global__ void __launch_bounds__(NTV)
             reinterpret_cast<double2*>(r)[t] = rv;
             rr = fma(rv.x, rv.x, rr);
             rr = fma(rv.y, rv.y, rr);
+            sr += rv.x + rv.y;
         }
     } else {
         for (long long t = (long long)blockIdx.x * NTV + threadIdx.x; t < N; t += (long long)gridDim.x * NTV) {
@@ -571,17 +577,23 @@ __global__ void __launch_bounds__(NTV)
             const double rv = fma(-alpha, q[t], r[t]);
             r[t] = rv;
             rr = fma(rv, rv, rr);
+            sr += rv;
         }
     }
-    __shared__ double red[NTV / 32];
-    rr = block_sum<NTV>(rr, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = rr;
+    __shared__ double red[2 * (NTV / 32)];
+    block_sum2_t<NTV, double>(rr, sr, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = rr;
+        part_s[blockIdx.x] = sr;
+    }
     if (arrive_last_n(cnt, gridDim.x)) {
-        const double RR = sum_parts_cg<NTV>(part, gridDim.x, red);
+        double RR, SR;
+        sum_parts2_cg<NTV>(part, part_s, gridDim.x, red, &RR, &SR);
         if (threadIdx.x == 0) {
             const int itn = it + 1;
             ictl[PI_IT] = itn;
             scal[PS_RR] = RR;
+            scal[PS_MEANR] = SR / (double)N;
             const double ff = scal[PS_FF];
             const int conv = (RR <= rtol * rtol * ff);
             const int bad = !(RR == RR) || !(RR < 1e300);
@@ -614,8 +626,8 @@ __global__ void __launch_bounds__(NTV)
 template <int DIM>
 __global__ void __launch_bounds__(NTV)
     k_ir_step(LvT<double> L, double* __restrict__ x, double* __restrict__ r64, const float* p0, const float* p1,
-              float* __restrict__ r32, double* part, double* scal, int* ictl, unsigned int* cnt, double rtol,
-              int max_iter, cudaGraphConditionalHandle h, int use_graph, int vec4) {
+              float* __restrict__ r32, double* part, double* part_s, double* scal, int* ictl, unsigned int* cnt,
+              double rtol, int max_iter, cudaGraphConditionalHandle h, int use_graph, int vec4) {
     pdl_wait();
     pdl_trigger();
     const int fb = blockIdx.y;
@@ -640,10 +652,11 @@ __global__ void __launch_bounds__(NTV)
     r64 += (long long)fb * L.N;
     r32 += (long long)fb * L.N;
     part += (long long)fb * gridDim.x;
+    part_s += (long long)fb * gridDim.x;
     FF wd[3];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) wd[d] = FF(L.w[d]);
-    double rr = 0.0;
+    double rr = 0.0, sr = 0.0;
     if (vec4) {
         // four x-consecutive cells per thread step (nx % 4 == 0, x 16-byte
         // aligned; the launch is sized by N / 4): one coordinate map, 16-byte
@@ -706,6 +719,7 @@ __global__ void __launch_bounds__(NTV)
                 rout[i] = f2d_bits(rv.hi) + f2d_bits(rv.lo);
                 r32o[i] = rv.hi;
                 rr = fma(rout[i], rout[i], rr);
+                sr += rout[i];
             }
             *reinterpret_cast<double2*>(x + t0) = make_double2(xout[0], xout[1]);
             *reinterpret_cast<double2*>(x + t0 + 2) = make_double2(xout[2], xout[3]);
@@ -740,13 +754,19 @@ __global__ void __launch_bounds__(NTV)
         r64[t] = rvd;
         r32[t] = rv.hi;
         rr = fma(rvd, rvd, rr);
+        sr += rvd;
     }
-    __shared__ double red[NTV / 32];
-    rr = block_sum<NTV>(rr, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = rr;
+    __shared__ double red[2 * (NTV / 32)];
+    block_sum2_t<NTV, double>(rr, sr, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = rr;
+        part_s[blockIdx.x] = sr;
+    }
     if (arrive_last_n(cnt, gridDim.x)) {
-        const double RR = sum_parts_cg<NTV>(part, gridDim.x, red);
+        double RR, SR;
+        sum_parts2_cg<NTV>(part, part_s, gridDim.x, red, &RR, &SR);
         if (threadIdx.x == 0) {
+            scal[PS_MEANR] = SR / (double)L.N;
             const int tot = ictl[PI_TOTAL] + 1;
             ictl[PI_IT] = it + 1;
             ictl[PI_TOTAL] = tot;
@@ -817,8 +837,8 @@ __global__ void __launch_bounds__(NTV) k_mean(const double* __restrict__ b, long
 template <int DIM>
 __global__ void __launch_bounds__(NTV)
     k_pcg_init(LvT<double> L, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
-               float* __restrict__ r32, double* pff, double* prr, double* scal, int* ictl, unsigned int* cnt,
-               double rtol, cudaGraphConditionalHandle h, int use_graph) {
+               float* __restrict__ r32, double* pff, double* prr, double* psr, double* scal, int* ictl,
+               unsigned int* cnt, double rtol, cudaGraphConditionalHandle h, int use_graph) {
     pdl_wait();
     pdl_trigger();
     const int fb = blockIdx.y;
@@ -829,8 +849,9 @@ __global__ void __launch_bounds__(NTV)
     if (r32) r32 += (long long)fb * L.N;
     pff += (long long)fb * gridDim.x;
     prr += (long long)fb * gridDim.x;
+    psr += (long long)fb * gridDim.x;
     const double mean_b = scal[PS_MEANB];
-    double ff = 0.0, rr = 0.0;
+    double ff = 0.0, rr = 0.0, sr = 0.0;
     for (int t = blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
         int c[3];
         coords(L, t, c);
@@ -842,19 +863,24 @@ __global__ void __launch_bounds__(NTV)
         if (r32) r32[t] = (float)rv;
         ff = fma(f, f, ff);
         rr = fma(rv, rv, rr);
+        sr += rv;
     }
     __shared__ double red[2 * (NTV / 32)];
     block_sum2_t<NTV, double>(ff, rr, red);
+    sr = block_sum<NTV>(sr, red);
     if (threadIdx.x == 0) {
         pff[blockIdx.x] = ff;
         prr[blockIdx.x] = rr;
+        psr[blockIdx.x] = sr;
     }
     if (arrive_last_n(cnt, gridDim.x)) {
         double FF, RR;
         sum_parts2_cg<NTV>(pff, prr, gridDim.x, red, &FF, &RR);
+        const double SR = sum_parts_cg<NTV>(psr, gridDim.x, red);
         if (threadIdx.x == 0) {
             scal[PS_FF] = FF;
             scal[PS_RR] = RR;
+            scal[PS_MEANR] = SR / (double)L.N;
             scal[PS_RZ] = 0.0;
             scal[PS_BETA] = 0.0;
             scal[PS_ITERS] = 0.0;
@@ -1165,7 +1191,7 @@ __device__ __forceinline__ void color_sweep(const LvT<T>& L, T (*su)[32], T (*sf
 
 template <class T, class TF, int NS>
 __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restrict__ f, T* __restrict__ upre,
-                                           T* __restrict__ fc) {
+                                           T* __restrict__ fc, const double* __restrict__ scal_r) {
     pdl_wait();
     pdl_trigger();
     {   // system of a batch
@@ -1173,7 +1199,10 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
         f += fb * L.N;
         upre += fb * L.N;
         fc += fb * C.N;
+        if (scal_r) scal_r += fb * PS_NSCAL;
     }
+    // fine level: the CG residual enters the preconditioner with its mean removed
+    const TF mr = scal_r ? (TF)scal_r[PS_MEANR] : (TF)0;
     constexpr int H = 2 * NS + 1, FD = fd_of(NS), CD = cd_of(NS);
     __shared__ T sf[SY][32];
     __shared__ T su[SY][32];
@@ -1192,7 +1221,7 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
         ayk[k] = ay;
         T fv = (T)0, uv = (T)0;
         if (ax.valid && ay.valid) {
-            fv = (T)f[ax.gw + nx * ay.gw];
+            fv = (T)(f[ax.gw + nx * ay.gw] - mr);
             if (((par0 + lane + r) & 1) == 0) uv = fv * L.invd[ax.cls + 3 * ay.cls];
         }
         sf[r][lane] = fv;
@@ -1263,6 +1292,7 @@ __global__ void __launch_bounds__(NT)
             cnt += fb * kNumCounters;
         }
     }
+    const TF mr = FINE ? (TF)scal[PS_MEANR] : (TF)0;   // fine level: residual mean removed
     constexpr int H = 2 * NS, FU = fu_of(NS);
     __shared__ T sf[SY][32];
     __shared__ T su[SY][32];
@@ -1286,7 +1316,7 @@ __global__ void __launch_bounds__(NT)
         T fv = (T)0, uv = (T)0;
         if (ax.valid && ay.valid) {
             const int g = ax.gw + nx * ay.gw;
-            fv = (T)f[g];
+            fv = (T)(f[g] - mr);
             int J0, J1;
             pro_pair(ay.gw, C.n[1], C.per[1], &J0, &J1);
             const T* c0 = uc + C.n[0] * J0;
@@ -1317,7 +1347,7 @@ __global__ void __launch_bounds__(NT)
         upost[g] = u;
         if (FINE) {
             // f is still in shared memory, exactly, when T and TF agree
-            const TF fv = (sizeof(T) == sizeof(TF)) ? (TF)sf[r][lane] : f[g];
+            const TF fv = (sizeof(T) == sizeof(TF)) ? (TF)sf[r][lane] : (TF)(f[g] - mr);
             rz = fma(fv, (TF)u, rz);
             sz += (TF)u;
         }
@@ -1754,9 +1784,11 @@ __device__ __forceinline__ void color_plane(const LvT<T>& L, Pl<T>* su, const Pl
 // coarse tile CD x CD of columns / rows and coarse planes [K0, K1).
 template <class T, class TF>
 __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restrict__ f, T* __restrict__ upre,
-                                           T* __restrict__ fc) {
+                                           T* __restrict__ fc, const double* __restrict__ scal_r) {
     pdl_wait();
     pdl_trigger();
+    // fine level: the CG residual enters the preconditioner with its mean removed
+    const TF mr = scal_r ? (TF)scal_r[PS_MEANR] : (TF)0;
     constexpr int H = 3;
     extern __shared__ __align__(16) unsigned char smraw[];
     Pl<T>* sF = reinterpret_cast<Pl<T>*>(smraw);
@@ -1793,7 +1825,8 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
         const Ax az = axis(qz, nz, L.per[2]);
 #pragma unroll
         for (int k = 0; k < 2; ++k)
-            fpre[k] = (ax.valid && ay[k].valid && az.valid) ? f[ax.gw + (long long)nx * ay[k].gw + nxy * az.gw] : (TF)0;
+            fpre[k] = (ax.valid && ay[k].valid && az.valid) ? (TF)(f[ax.gw + (long long)nx * ay[k].gw + nxy * az.gw] - mr)
+                                                            : (TF)0;
     };
     load_f(zs);
 
@@ -1878,6 +1911,7 @@ __global__ void __launch_bounds__(NT)
        T* __restrict__ upost, double* part_rz, double* part_sz, double* scal, const int* ictl, unsigned int* cnt) {
     pdl_wait();
     pdl_trigger();
+    const TF mr = FINE ? (TF)scal[PS_MEANR] : (TF)0;   // fine level: residual mean removed
     constexpr int H = 2;
     extern __shared__ __align__(16) unsigned char smraw[];
     Pl<T>* sF = reinterpret_cast<Pl<T>*>(smraw);
@@ -1904,7 +1938,7 @@ __global__ void __launch_bounds__(NT)
         for (int k = 0; k < 2; ++k) {
             const bool v = ax.valid && ay[k].valid && az.valid;
             const long long g = ax.gw + (long long)nx * ay[k].gw + nxy * az.gw;
-            fpre[k] = v ? f[g] : (TF)0;
+            fpre[k] = v ? (TF)(f[g] - mr) : (TF)0;
             upre_n[k] = v ? upre[g] : (T)0;
         }
     };
@@ -1962,7 +1996,7 @@ __global__ void __launch_bounds__(NT)
                     upost[g] = u;
                     if (FINE) {
                         // plane z's f is still in the ring, exactly, when T and TF agree
-                        const TF fv = (sizeof(T) == sizeof(TF)) ? (TF)sF[sl][r][lane] : f[g];
+                        const TF fv = (sizeof(T) == sizeof(TF)) ? (TF)sF[sl][r][lane] : (TF)(f[g] - mr);
                         rz = fma(fv, (TF)u, rz);
                         sz += (TF)u;
                     }
@@ -2811,9 +2845,11 @@ template <class T, int NS>
 void enqueue_down2(PoissonPlan* pl, int l, const LvT<T>& L, const LvT<T>& C, T* fc, cudaStream_t s) {
     constexpr int CD = k2::cd_of(NS);
     const dim3 grid((C.n[0] + CD - 1) / CD, (C.n[1] + CD - 1) / CD, pl->nb);
-    if (l == 0 && pl->r32) launch(k2::down<T, float, NS>, grid, k2::NT, 0, s, L, C, pl->r32, (T*)pl->u0pre, fc);
-    else if (l == 0) launch(k2::down<T, double, NS>, grid, k2::NT, 0, s, L, C, pl->r, (T*)pl->u0pre, fc);
-    else launch(k2::down<T, T, NS>, grid, k2::NT, 0, s, L, C, (const T*)pl->lev[l].f, (T*)pl->lev[l].upre, fc);
+    const double* sr = pl->scal;   // the fine level removes the CG residual's mean
+    if (l == 0 && pl->r32) launch(k2::down<T, float, NS>, grid, k2::NT, 0, s, L, C, pl->r32, (T*)pl->u0pre, fc, sr);
+    else if (l == 0) launch(k2::down<T, double, NS>, grid, k2::NT, 0, s, L, C, pl->r, (T*)pl->u0pre, fc, sr);
+    else launch(k2::down<T, T, NS>, grid, k2::NT, 0, s, L, C, (const T*)pl->lev[l].f, (T*)pl->lev[l].upre, fc,
+                (const double*)nullptr);
 }
 
 template <class T, int NS>
@@ -2851,22 +2887,25 @@ void enqueue_down(PoissonPlan* pl, int l, cudaStream_t s) {
     } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells) {
         const dim3 grid = k3_down_grid(pl->lev[l + 1].n);
         const size_t smem = 3 * k3::RING * k3::SB * k3::SB * sizeof(T);
+        const double* sr = pl->scal;   // the fine level removes the CG residual's mean
         if (l == 0 && ir)
-            launch(k3::down<T, float>, grid, k3::NT, smem, s, L, C, pl->r32, (T*)pl->u0pre, fc);
+            launch(k3::down<T, float>, grid, k3::NT, smem, s, L, C, pl->r32, (T*)pl->u0pre, fc, sr);
         else if (l == 0)
-            launch(k3::down<T, double>, grid, k3::NT, smem, s, L, C, pl->r, (T*)pl->u0pre, fc);
+            launch(k3::down<T, double>, grid, k3::NT, smem, s, L, C, pl->r, (T*)pl->u0pre, fc, sr);
         else
-            launch(k3::down<T, T>, grid, k3::NT, smem, s, L, C, (const T*)pl->lev[l].f, (T*)pl->lev[l].upre, fc);
+            launch(k3::down<T, T>, grid, k3::NT, smem, s, L, C, (const T*)pl->lev[l].f, (T*)pl->lev[l].upre, fc,
+                   (const double*)nullptr);
     } else {
         const dim3 grid = tile_grid<DIM>(pl->lev[l].n);
         const size_t smem = 2 * Box<DIM, 3>::SN * sizeof(T);
+        const double* sr = pl->scal;   // the fine level removes the CG residual's mean
         if (l == 0 && ir)
-            launch(k_mg_down<T, float, DIM>, grid, Tile<DIM>::NT, smem, s, L, C, pl->r32, (T*)pl->u0pre, fc);
+            launch(k_mg_down<T, float, DIM>, grid, Tile<DIM>::NT, smem, s, L, C, pl->r32, (T*)pl->u0pre, fc, sr);
         else if (l == 0)
-            launch(k_mg_down<T, double, DIM>, grid, Tile<DIM>::NT, smem, s, L, C, pl->r, (T*)pl->u0pre, fc);
+            launch(k_mg_down<T, double, DIM>, grid, Tile<DIM>::NT, smem, s, L, C, pl->r, (T*)pl->u0pre, fc, sr);
         else
             launch(k_mg_down<T, T, DIM>, grid, Tile<DIM>::NT, smem, s, L, C, (const T*)pl->lev[l].f,
-                                                                   (T*)pl->lev[l].upre, fc);
+                                                                   (T*)pl->lev[l].upre, fc, (const double*)nullptr);
     }
     pl->launches += 1;
 }
@@ -3010,7 +3049,8 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
         const int vec4 = (pl->lev[0].n[0] % 4 == 0) && (((uintptr_t)x & 15) == 0);
         const dim3 rbr(vec4 ? reduce_blocks(pl->N / 4) : reduce_blocks(pl->N), pl->nb);
         launch(k_ir_step<DIM>, rbr, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r, (const float*)pl->p32[0],
-               (const float*)pl->p32[1], pl->r32, pl->part1, pl->scal, pl->ictl, pl->cnt + CNT_REF, pl->rtol,
+               (const float*)pl->p32[1], pl->r32, pl->part1, pl->part2, pl->scal, pl->ictl, pl->cnt + CNT_REF,
+               pl->rtol,
                pl->max_iter, h, ug, vec4);
         pl->launches += 1;
     } else {
@@ -3018,7 +3058,8 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
         // caller's array) is 16-byte aligned
         const int vec2 = (pl->N % 2 == 0) && (((uintptr_t)x & 15) == 0);
         const dim3 rbu(vec2 ? reduce_blocks(pl->N / 2) : reduce_blocks(pl->N), pl->nb);
-        launch(k_cg_update, rbu, NTV, 0, s, x, pl->r, pl->p[0], pl->p[1], pl->q, pl->N, pl->part0, pl->scal, pl->ictl,
+        launch(k_cg_update, rbu, NTV, 0, s, x, pl->r, pl->p[0], pl->p[1], pl->q, pl->N, pl->part0, pl->part2,
+               pl->scal, pl->ictl,
                                        pl->cnt + CNT_UPD, pl->rtol, pl->max_iter, h, ug, vec2);
         pl->launches += 1;
     }
@@ -3037,7 +3078,8 @@ void prologue(PoissonPlan* pl, const double* b, double* x, cudaStream_t s, cudaG
         pl->launches += 1;
     }
     const LvT<double> L = make_lv<double>(pl->lev[0], DIM);
-    launch(k_pcg_init<DIM>, rb, NTV, 0, s, L, b, x, pl->r, pl->r32, pl->part1, pl->part2, pl->scal, pl->ictl,
+    launch(k_pcg_init<DIM>, rb, NTV, 0, s, L, b, x, pl->r, pl->r32, pl->part1, pl->part2, pl->part0, pl->scal,
+           pl->ictl,
                                        pl->cnt + CNT_INIT, pl->rtol, h, (pl->nb > 1) ? 0 : use_graph);
     pl->launches += 1;
     if (pl->nb > 1) {

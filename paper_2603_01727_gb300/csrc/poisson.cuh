@@ -54,6 +54,7 @@ enum : int {
     PS_RELRES = 7,    // sqrt(rr/ff) at exit
     PS_ALPHA = 8,
     PS_MEANX = 9,
+    PS_MEANR = 10,    // mean of the current CG residual (removed before the preconditioner)
     PS_NSCAL = 16
 };
 // PI_IT: CG iterations of the solve (its parity selects the search-direction

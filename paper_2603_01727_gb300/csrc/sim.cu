@@ -1363,12 +1363,28 @@ sim_status sim_step_save(sim_t* s, void* buf, int on_device) {
     char* out = (char*)buf + a256(sizeof(StateHeader));
     CK(cudaStreamWaitEvent(s->save_stream, s->ev_early, 0));
     CK(cudaMemcpyAsync(out, img, nearly, k, s->save_stream));
-    CK(cudaMemcpyAsync(out + nearly, img + nearly, nimg - nearly, k, s->stream));
+    // From here the early copy may be writing into the caller's buffer: every
+    // return, failed or not, first waits for it, so the buffer is free again
+    // when the call returns.
+    const char* what = nullptr;
+    cudaError_t e = cudaMemcpyAsync(out + nearly, img + nearly, nimg - nearly, k, s->stream);
+    if (e != cudaSuccess) what = "cudaMemcpyAsync (late part)";
     StateHeader h;
     fill_header(s, &h);
-    if (on_device) CK(cudaMemcpyAsync(buf, &h, sizeof(h), cudaMemcpyHostToDevice, s->stream));
-    CK(cudaStreamSynchronize(s->save_stream));
-    CK(cudaStreamSynchronize(s->stream));
+    if (!what && on_device) {
+        e = cudaMemcpyAsync(buf, &h, sizeof(h), cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) what = "cudaMemcpyAsync (header)";
+    }
+    const cudaError_t e_save = cudaStreamSynchronize(s->save_stream);
+    if (!what) {
+        e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) what = "cudaStreamSynchronize (step stream)";
+    }
+    if (!what && e_save != cudaSuccess) {
+        e = e_save;
+        what = "cudaStreamSynchronize (save stream)";
+    }
+    if (what) return fail(s, SIM_ECUDA, "sim_step_save: %s: %s", what, cudaGetErrorString(e));
     if (!on_device) std::memcpy(buf, &h, sizeof(h));
     return SIM_OK;
 }

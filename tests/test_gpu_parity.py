@@ -284,6 +284,55 @@ def test_sphere_burner_full_size_mixed_matches_oracle():
 
 
 # ---------------------------------------------------------------------------
+# The parity bar at full size: the bench's 256x512 slot burner over 100 steps
+# (FP64 within 1e-9 on every field; mixed precision within its stated bound)
+# and the 192^3 sphere burner in FP64.  The oracle's 100 slot steps are shared.
+# ---------------------------------------------------------------------------
+_FULL = {}
+
+
+def _slot_full_oracle():
+    if "slot" not in _FULL:
+        prm, geo, f = W.slot_burner()
+        prm["poisson_rtol"] = 1e-13
+        _FULL["slot"] = oracle_run(prm, geo, f, 100)
+    return _FULL["slot"]
+
+
+def test_slot_burner_full_size_100_steps_fp64_within_1e9():
+    prm, geo, f = W.slot_burner()
+    prm["poisson_rtol"] = 1e-13
+    pb, st = _slot_full_oracle()
+    sim = gpu_run(prm, geo, f, 100)
+    worst = compare(sim, oracle_fields(pb, st), 1e-9)
+    print("slot 256x512 fp64 100 steps", {k: f"{v:.1e}" for k, v in worst.items()})
+    sim.close()
+
+
+def test_slot_burner_full_size_100_steps_mixed_within_bound():
+    prm, geo, f = W.slot_burner()
+    prm["poisson_rtol"] = 1e-12
+    prm["precision"] = W.MIXED
+    pb, st = _slot_full_oracle()
+    sim = gpu_run(prm, geo, f, 100)
+    worst = compare(sim, oracle_fields(pb, st), MIXED_TOL)
+    print("slot 256x512 mixed 100 steps", {k: f"{v:.1e}" for k, v in worst.items()})
+    sim.close()
+
+
+def test_sphere_burner_full_size_fp64_within_1e9():
+    """192^3 in FP64, 3 steps (one eager start-up step and two through the step
+    graph); the oracle takes about 10 s and 4 GB per step."""
+    prm, geo, f = W.sphere_burner(192)
+    prm["poisson_rtol"] = 1e-13
+    pb, st = oracle_run(prm, geo, f, 3)
+    sim = gpu_run(prm, geo, f, 3)
+    worst = compare(sim, oracle_fields(pb, st), 1e-9)
+    print("sphere 192^3 fp64 3 steps", {k: f"{v:.1e}" for k, v in worst.items()})
+    sim.close()
+
+
+# ---------------------------------------------------------------------------
 # Execution paths and error handling
 # ---------------------------------------------------------------------------
 def test_graph_and_eager_paths_agree_bitwise(monkeypatch):
@@ -328,12 +377,14 @@ def test_restart_blob_same_through_pinned_pageable_and_device_buffers(case):
     sim.close()
 
 
-@pytest.mark.parametrize("case", ["slot", "sphere"])
-def test_step_save_equals_step_then_state_save(case):
+@pytest.mark.parametrize("case,buf", [("slot", "pinned"), ("slot", "pageable"), ("slot", "device"),
+                                      ("sphere", "pinned"), ("sphere", "pageable"), ("sphere", "device")])
+def test_step_save_equals_step_then_state_save(case, buf):
     """sim_step_save copies the arrays that are final after the corrector's
     state relation while the corrector's solve runs, the rest after the step:
     its blob must equal sim_step followed by sim_state_save byte for byte,
-    through the eager first steps and the step graphs."""
+    through the eager first steps and the step graphs, into pinned or pageable
+    host memory or device memory."""
     import torch
     from paper_2603_01727_gb300.lowmach import Simulation
     prm, geo, f = W.slot_burner(64, 128) if case == "slot" else W.sphere_burner(24)
@@ -343,12 +394,18 @@ def test_step_save_equals_step_then_state_save(case):
     b.set_fields(f)
     n = a.state_size()
     ref = np.zeros(n, dtype=np.uint8)
-    out = torch.zeros(n, dtype=torch.uint8, pin_memory=True)
+    if buf == "pinned":
+        out = torch.zeros(n, dtype=torch.uint8, pin_memory=True)
+    elif buf == "pageable":
+        out = np.zeros(n, dtype=np.uint8)
+    else:
+        out = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    host = lambda o: o.cpu().numpy() if isinstance(o, torch.Tensor) else o
     for _ in range(5):
         a.step(1)
         a.state_save(ref)
         b.step_save(out)
-        assert np.array_equal(ref, out.numpy())
+        assert np.array_equal(ref, host(out))
     a.close()
     b.close()
 
