@@ -84,9 +84,14 @@ typedef struct {
     int closed_system;       /* 1: p0 from the mass constraint (Eq 2.40); 0: p0 = 1 (Eq 2.41) */
     int incompressible;      /* 1: T = rho = kappa = p0 = 1 (constant-density runs)     */
     double dt;               /* fixed time step (> 0)                                   */
-    int precision;           /* SIM_FP64: every kernel in FP64.  SIM_MIXED: multigrid
-                                preconditioner in FP32 inside the FP64 CG (the CG
-                                residual and the stopping test stay FP64)              */
+    int precision;           /* SIM_FP64: every kernel in FP64.  SIM_MIXED: the stage
+                                stencil in float-float arithmetic (pairs of FP32,
+                                about 48 bits) with FP64 residual storage and state
+                                updates; the multigrid preconditioner and the CG
+                                iteration in FP32 with a reliable update of the FP64
+                                solution and residual every iteration (the stopping
+                                test stays FP64); the state relation FP64-accurate,
+                                FP64 near stoichiometry                                */
     double poisson_rtol;     /* stop when ||r||_2 / ||f||_2 <= rtol (0 < rtol < 1)      */
     int poisson_max_iter;    /* PCG iteration cap (>= 1)                                */
     /* Multigrid tuning (0 = library default): red-black sweeps per pre / post
@@ -139,7 +144,24 @@ enum {
     SIM_Q_KERNEL_LAUNCHES = 11,                     /* kernels enqueued by the last sim_step */
     SIM_Q_TAIL_NX = 12, SIM_Q_TAIL_NY = 13,         /* shape of the top coarse level solved in one block */
     SIM_Q_TAIL_FDM = 14,                            /* 1: that level is solved by fast diagonalisation */
-    SIM_Q_TAIL_NZ = 15                              /* its z extent (1 in 2D) */
+    SIM_Q_TAIL_NZ = 15,                             /* its z extent (1 in 2D) */
+    /* Per-step checks of the last completed step, computed on demand from the
+     * state (one pass over the grid; SIM_ESTATE before the first step):     */
+    SIM_Q_DIV_RESID = 16,     /* max |d_t rho + sum_j delta_1 F_j / delta_1 x_j - S_m|
+                                 over the cells: the discrete continuity of Eq 3.24
+                                 with the mass source of Eq 3.33, d_t rho by the
+                                 step's own rule (Eq 3.19; first order on step 1);
+                                 bounded by the pressure solve's residual        */
+    SIM_Q_DIV_SCALE = 17,     /* max |d_t rho| + max |S_m|: a scale for the above */
+    SIM_Q_MASS_BALANCE = 18,  /* sum (d_t rho - S_m) dV + net outward flux of F
+                                 through the domain boundary: the global mass
+                                 balance closed by the outflow correction (text
+                                 after Eq 4.22); zero up to rounding            */
+    SIM_Q_PC_DIFF_U = 19,     /* L2 norms, sqrt(sum e^2 dV), of the difference  */
+    SIM_Q_PC_DIFF_V = 20,     /* between the predicted and corrected velocity   */
+    SIM_Q_PC_DIFF_W = 21,     /* components and P (P after removing the mean of  */
+    SIM_Q_PC_DIFF_P = 22      /* the difference): the local truncation error
+                                 measure of Sec. 4.2.2 (Table 2)                */
 };
 
 /* Bytes of device workspace sim_create needs for these parameters. */

@@ -221,6 +221,29 @@ __device__ inline double block_sum(double v, double* smem /* NT/32 doubles */) {
     return r;
 }
 
+// Block maximum of non-negative values (same tree as block_sum).
+template <int NT>
+__device__ inline double block_max(double v, double* smem /* NT/32 doubles */) {
+    static_assert(NT % 32 == 0 && NT <= 1024, "block size");
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) smem[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (l < NT / 32) ? smem[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if (l == 0) smem[0] = r;
+    }
+    __syncthreads();
+    r = smem[0];
+    __syncthreads();
+    return r;
+}
+
 // FP32 variant (for the FP32 inner Krylov loop); same fixed tree.
 template <int NT>
 __device__ inline float block_sum_f(float v, float* smem /* NT/32 floats */) {

@@ -71,6 +71,8 @@ struct sim {
     double* vib[3];
     double *Sm, *U;
     double *P, *b, *io;
+    double* Pstar;         // the predictor's P of the last step (per-step checks)
+    double* diag;          // per-step check partials and results
     double* part;
     double* part2;
     double* sc;
@@ -303,6 +305,10 @@ size_t layout(const sim_params_t* p, sim_t* s, char* base) {
     F(&t->U);
     {
         double* q = (double*)take(fcmp);
+        if (s) s->Pstar = q;
+        q = (double*)take(sizeof(double) * (size_t)(DG_N * kDiagBlocks + DG_N));
+        if (s) s->diag = q;
+        q = (double*)take(fcmp);
         if (s) s->b = q;
         q = (double*)take(sizeof(double) * (size_t)(maxface > g.ncell ? maxface : g.ncell));
         if (s) s->io = q;
@@ -695,6 +701,9 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     if (on(SEC_MID)) {
         launch_project(g, s->ph, pa, st, L);
         if (D == 3) ghost_v(s, s->vs, st, L);
+        // P* kept for the predictor-corrector difference (per-step checks)
+        e = cudaMemcpyAsync(s->Pstar, s->P, sizeof(double) * (size_t)g.ncell, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
     }
     if (on(SEC_MID) && s->adj_save) {
         // predictor values read by the reverse pass (overwritten by the corrector)
@@ -1072,11 +1081,13 @@ sim_status sim_step(sim_t* s, int nsteps) {
     const int need = (s->g.dim == 3) ? 0x1f : 0x1b;
     if ((s->fields_set & need) != need) return fail(s, SIM_ESTATE, "set U, V, (W,) Z, H before stepping");
     if (s->need_init) {
-        CK(enqueue_init(s, s->stream));
-        s->need_init = false;
+        // level 0 starts the rotation afresh: the set-up writes rho^0 into the
+        // buffer the first step reads as rho^n, whatever a previous run left
         s->nstep = 0;
         s->rho_base = 0;
         s->t = 0.0;
+        CK(enqueue_init(s, s->stream));
+        s->need_init = false;
         for (int k = 0; k < 6; ++k)
             if (s->gvalid[k]) {
                 cudaGraphExecDestroy(s->gexec[k]);
@@ -1110,6 +1121,41 @@ sim_status sim_sync(sim_t* s) {
     CK(cudaGetLastError());
     return check_device_status(s);
 }
+
+namespace {
+// Per-step checks of the last completed step, from the state: rho^{n+1},
+// rho^n, rho^{n-1} are the three rotating levels; the step's own rate rule
+// (first order on the first step, Eq 3.11 / 3.19 after).
+sim_status run_diagnostics(sim_t* s, double* res) {
+    const Geom& g = s->g;
+    DiagArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const int b = s->rho_base;
+    a.rho_new = s->rho[b];
+    a.rho_n = s->rho[(b + 2) % 3];
+    a.rho_prev = s->rho[(b + 1) % 3];
+    const double dt = s->prm.dt;
+    if (s->nstep == 1) {
+        a.c0 = 1.0; a.c1 = -1.0; a.c2 = 0.0; a.iden = 1.0 / dt;
+    } else {
+        a.c0 = 3.0; a.c1 = -4.0; a.c2 = 1.0; a.iden = 1.0 / (2.0 * dt);
+    }
+    for (int d = 0; d < g.dim; ++d) {
+        a.F[d] = s->F[d];
+        a.v[d] = s->v[d];
+        a.vs[d] = s->vs[d];
+    }
+    a.Sm = s->ibm_active ? s->Sm : nullptr;
+    a.P = s->P;
+    a.Ps = s->Pstar;
+    a.part = s->diag;
+    a.out = s->diag + DG_N * kDiagBlocks;
+    CK(launch_diagnostics(g, a, s->stream));
+    CK(cudaMemcpyAsync(res, a.out, sizeof(double) * DG_N, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+}  // namespace
 
 sim_status sim_query(sim_t* s, int what, double* out) {
     if (!s || !out) return SIM_EINVAL;
@@ -1148,6 +1194,33 @@ sim_status sim_query(sim_t* s, int what, double* out) {
             // each solve's loop; the loops ran the rest
             *out = (double)(-s->launches_last - 1) +
                    (poisson_loop_iters(&s->pp, ip) + poisson_loop_iters(&s->pp, ic)) * s->body_launches;
+            return SIM_OK;
+        }
+        case SIM_Q_DIV_RESID:
+        case SIM_Q_DIV_SCALE:
+        case SIM_Q_MASS_BALANCE:
+        case SIM_Q_PC_DIFF_U:
+        case SIM_Q_PC_DIFF_V:
+        case SIM_Q_PC_DIFF_W:
+        case SIM_Q_PC_DIFF_P: {
+            if (s->nstep < 1 || s->need_init) return fail(s, SIM_ESTATE, "per-step checks need a completed step");
+            double r[DG_N];
+            const sim_status st = run_diagnostics(s, r);
+            if (st != SIM_OK) return st;
+            const double N = (double)s->g.ncell;
+            switch (what) {
+                case SIM_Q_DIV_RESID: *out = r[DG_MAXRES]; break;
+                case SIM_Q_DIV_SCALE: *out = r[DG_MAXDRHO] + r[DG_MAXSM]; break;
+                case SIM_Q_MASS_BALANCE: *out = r[DG_BAL]; break;
+                case SIM_Q_PC_DIFF_U: *out = std::sqrt(r[DG_DU]); break;
+                case SIM_Q_PC_DIFF_V: *out = std::sqrt(r[DG_DU + 1]); break;
+                case SIM_Q_PC_DIFF_W: *out = s->g.dim == 3 ? std::sqrt(r[DG_DU + 2]) : 0.0; break;
+                default: {
+                    // P is unique up to a constant: the difference's mean is removed
+                    const double sd = r[DG_DP] / s->g.dV, m = sd / N;
+                    *out = std::sqrt(std::fmax(r[DG_DP2] - m * sd * s->g.dV, 0.0));
+                }
+            }
             return SIM_OK;
         }
         default: return fail(s, SIM_EINVAL, "unknown query %d", what);

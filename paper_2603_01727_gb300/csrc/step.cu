@@ -279,6 +279,67 @@ __global__ void k_state(Geom g, Phys ph, const double* __restrict__ Z, const dou
     }
 }
 
+// Per-step checks after the corrector's projection: the discrete continuity
+// residual of Eq 3.24 (with the mass source of Eq 3.33) cell by cell, the
+// global mass balance over the boundary faces (text after Eq 4.22), and the
+// differences between the predictor's and the corrector's v and P (the local
+// truncation error measure of Sec. 4.2.2).  Block partials in DG_* order;
+// k_diag_final reduces them in index order (deterministic).
+template <int DIM>
+__global__ void __launch_bounds__(NT) k_diag(Geom g, DiagArgs a) {
+    double mres = 0.0, mdr = 0.0, msm = 0.0, bal = 0.0, du[3] = {0.0, 0.0, 0.0}, dp = 0.0, dp2 = 0.0;
+    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
+        int cc[3];
+        interior_coords(g, t, cc);
+        const long long c = pad_index(g, t);
+        const double drho = (a.c0 * a.rho_new[c] + a.c1 * a.rho_n[c] + a.c2 * a.rho_prev[c]) * a.iden;
+        const double sm = a.Sm ? a.Sm[c] : 0.0;
+        double div = 0.0;
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+            const double lo = a.F[j][c], hi = a.F[j][c + g.s[j]];
+            div += (hi - lo) * g.ih[j];
+            if (!g.periodic[j]) {
+                const double dA = g.dV * g.ih[j];
+                if (cc[j] == 0) bal -= lo * dA;
+                if (cc[j] == g.n[j] - 1) bal += hi * dA;
+            }
+        }
+        bal += (drho - sm) * g.dV;
+        mres = fmax(mres, fabs(drho + div - sm));
+        mdr = fmax(mdr, fabs(drho));
+        msm = fmax(msm, fabs(sm));
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            const double d = a.vs[i][c] - a.v[i][c];
+            du[i] = fma(d, d, du[i]);
+        }
+        const double d = a.Ps[t] - a.P[t];
+        dp += d;
+        dp2 = fma(d, d, dp2);
+    }
+    __shared__ double red[NT / 32];
+    double vals[DG_N] = {mres, mdr, msm, bal, du[0], du[1], du[2], dp, dp2};
+#pragma unroll
+    for (int k = 0; k < DG_N; ++k) {
+        const double v = (k < DG_BAL) ? block_max<NT>(vals[k], red) : block_sum<NT>(vals[k], red);
+        if (threadIdx.x == 0) a.part[k * kDiagBlocks + blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_diag_final(Geom g, DiagArgs a, int nb) {
+    __shared__ double red[NT / 32];
+    for (int k = 0; k < DG_N; ++k) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < nb; i += NT) {
+            const double x = a.part[k * kDiagBlocks + i];
+            v = (k < DG_BAL) ? fmax(v, x) : v + x;
+        }
+        v = (k < DG_BAL) ? block_max<NT>(v, red) : block_sum<NT>(v, red);
+        if (threadIdx.x == 0) a.out[k] = (k >= DG_DU) ? v * g.dV : v;
+    }
+}
+
 // Enclosed system: p0 = m / (sum(1/T) dV) (Eq 2.40), rho = p0 / T (Eq 2.49).
 __global__ void k_density(Geom g, const double* __restrict__ T, double* __restrict__ rho,
                           const double* __restrict__ part, int np, double* sc, int p0_slot, int mixed) {
@@ -1603,6 +1664,16 @@ __global__ void k_profile_spread(Geom g, IbmDev b, const double* __restrict__ co
 }
 
 }  // namespace
+
+cudaError_t launch_diagnostics(const Geom& g, const DiagArgs& a, cudaStream_t st) {
+    long long nb = (g.ncell + NT - 1) / NT;
+    if (nb > kDiagBlocks) nb = kDiagBlocks;
+    if (g.dim == 3) k_diag<3><<<(int)nb, NT, 0, st>>>(g, a);
+    else k_diag<2><<<(int)nb, NT, 0, st>>>(g, a);
+    k_diag_final<<<1, NT, 0, st>>>(g, a, (int)nb);
+    return cudaGetLastError();
+}
+
 
 int reduce_grid(const Geom& g) { return reduce_blocks(g.ncell); }
 

@@ -38,6 +38,36 @@ struct GhostJob {
     int nf;
 };
 
+// Per-step checks (paper Eq 3.24, the global mass balance stated after
+// Eq 4.22, and the predictor-corrector differences of Sec. 4.2.2), computed on
+// demand from the state after a step.
+enum : int {
+    DG_MAXRES = 0,   // max |d_t rho + sum_j delta_1 F_j / delta_1 x_j - S_m|
+    DG_MAXDRHO = 1,  // max |d_t rho|
+    DG_MAXSM = 2,    // max |S_m|
+    DG_BAL = 3,      // sum (d_t rho - S_m) dV + net outward boundary flux
+    DG_DU = 4,       // sum (v*_i - v_i)^2 dV, i = 0, 1, 2
+    DG_DP = 7,       // sum (P* - P)
+    DG_DP2 = 8,      // sum (P* - P)^2
+    DG_N = 9
+};
+constexpr int kDiagBlocks = 608;
+struct DiagArgs {
+    const double* rho_new;
+    const double* rho_n;
+    const double* rho_prev;
+    double c0, c1, c2, iden;   // d_t rho = (c0 rho_new + c1 rho_n + c2 rho_prev) * iden
+    const double* F[3];
+    const double* Sm;          // may be null
+    const double* v[3];        // corrector velocity (padded)
+    const double* vs[3];       // predictor velocity (padded)
+    const double* P;           // compact P^{n+1}
+    const double* Ps;          // compact P* of the same step
+    double* part;              // DG_N x kDiagBlocks partials
+    double* out;               // DG_N results (sums already times dV)
+};
+cudaError_t launch_diagnostics(const Geom& g, const DiagArgs& a, cudaStream_t st);
+
 struct ResidArgs {
     const double* v[3];
     const double* Z;

@@ -29,7 +29,8 @@ SIM_GET, SIM_SET = 0, 1
  SIM_K_MG_TAIL, SIM_K_RESIDUAL_REV) = range(8)
 (SIM_Q_TIME, SIM_Q_DT, SIM_Q_P0, SIM_Q_STEPS, SIM_Q_ITERS_PRED, SIM_Q_ITERS_CORR, SIM_Q_RESID_PRED,
  SIM_Q_RESID_CORR, SIM_Q_MASS, SIM_Q_NCELLS, SIM_Q_MG_LEVELS, SIM_Q_KERNEL_LAUNCHES, SIM_Q_TAIL_NX,
- SIM_Q_TAIL_NY, SIM_Q_TAIL_FDM, SIM_Q_TAIL_NZ) = range(16)
+ SIM_Q_TAIL_NY, SIM_Q_TAIL_FDM, SIM_Q_TAIL_NZ, SIM_Q_DIV_RESID, SIM_Q_DIV_SCALE, SIM_Q_MASS_BALANCE,
+ SIM_Q_PC_DIFF_U, SIM_Q_PC_DIFF_V, SIM_Q_PC_DIFF_W, SIM_Q_PC_DIFF_P) = range(23)
 
 FIELD_IDS = dict(U=SIM_FIELD_U, V=SIM_FIELD_V, W=SIM_FIELD_W, Z=SIM_FIELD_Z, H=SIM_FIELD_H,
                  T=SIM_FIELD_T, RHO=SIM_FIELD_RHO, P=SIM_FIELD_P, FX=SIM_FIELD_FX, FY=SIM_FIELD_FY,

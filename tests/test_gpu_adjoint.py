@@ -195,3 +195,71 @@ def test_reverse_stencil_matches_dual_number_gather(lewis, monkeypatch):
         scale = np.max(np.abs(b))
         assert scale > 0.0, k
         assert np.max(np.abs(a - b)) <= 1e-12 * scale, (k, np.max(np.abs(a - b)) / scale)
+
+
+def test_autograd_function_matches_problem_gradient():
+    """The torch.autograd.Function wrapper: J from forward() and dJ/dc from
+    torch.autograd are bit for bit those of HeatReleaseProblem.value /
+    .gradient, and the chain rule through the Function holds."""
+    import torch
+    from paper_2603_01727_gb300.adjoint import HeatReleaseProblem, heat_release_function
+    prm, geo, f, A, c = _case(24, 48, 6, 32)
+    pb = HeatReleaseProblem(prm, geo, f, A, nsteps=8, every=3)
+    HR = heat_release_function()
+    ct = torch.tensor(c, dtype=torch.float64, requires_grad=True)
+    J = HR.apply(ct, pb)
+    (gt,) = torch.autograd.grad(J, ct)
+    J_ref = pb.value(c)
+    g_ref, _ = pb.gradient()
+    assert float(J.detach()) == J_ref
+    assert np.array_equal(gt.numpy(), g_ref)
+    ct2 = torch.tensor(c, dtype=torch.float64, requires_grad=True)
+    loss = 3.0 * HR.apply(ct2, pb) ** 2
+    loss.backward()
+    assert np.allclose(ct2.grad.numpy(), 6.0 * J_ref * g_ref, rtol=1e-15, atol=0.0)
+    pb.close()
+
+
+def test_c4_configuration_gradient():
+    """The adjoint configuration itself: the 128x256 slot burner whose flux
+    profile is 64 Gaussian bumps, J over 200 steps, checkpoints every 20.  The
+    adjoint gradient against central differences of the CUDA forward map along
+    a random direction and for three single coefficients; J against the FP64
+    oracle's J at the same coefficients."""
+    from oracle import objective as O
+    from oracle import step as S
+    from paper_2603_01727_gb300.adjoint import HeatReleaseProblem
+    prm, geo, f, A, c = W.slot_bumps()
+    prm["poisson_rtol"] = 1e-13
+    prm["poisson_max_iter"] = 400
+    N = 200
+    pb = HeatReleaseProblem(prm, geo, f, A, nsteps=N, every=20)
+    J = pb.value(c)
+    gc, _ = pb.gradient()
+    assert J > 0.0 and np.all(np.isfinite(gc))
+
+    def fd(e, h=1e-2):
+        # Over 200 steps a unit direction moves J by only ~5e-6 of itself, so
+        # at h = 1e-3 the quotient's rounding noise is ~1e-6 relative.  Central
+        # differences at h and 2h, Richardson-combined (error O(h^4)), keep
+        # both the noise and the truncation error near 1e-8.
+        d = lambda hh: (pb.value(c + hh * e, False) - pb.value(c - hh * e, False)) / (2.0 * hh)
+        return (4.0 * d(h) - d(2.0 * h)) / 3.0
+
+    e = _direction(len(c), seed=13)
+    fdv = fd(e)
+    ad = float(gc @ e)
+    print("c4 direction: adjoint", ad, "fd", fdv, "rel", abs(fdv - ad) / abs(ad))
+    assert abs(fdv - ad) <= TOL * abs(ad), (fdv, ad)
+    for m in (0, 31, 63):
+        em = np.zeros(len(c))
+        em[m] = 1.0
+        fdm = fd(em)
+        print("c4 coefficient", m, "adjoint", gc[m], "fd", fdm, "rel", abs(fdm - gc[m]) / np.max(np.abs(gc)))
+        assert abs(fdm - gc[m]) <= TOL * np.max(np.abs(gc)), (m, fdm, gc[m])
+    pb.close()
+    p = S.Problem(prm, dict(geo, profile=list(A @ c)))
+    st = S.initial_state(p, f["v"], f["Z"], f["H"])
+    J_oracle = O.objective(p, st, N, S.advance)
+    print("c4 J", J, "oracle", J_oracle)
+    assert abs(J_oracle - J) <= 1e-9 * abs(J_oracle)

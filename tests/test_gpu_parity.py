@@ -333,6 +333,59 @@ def test_sphere_burner_full_size_fp64_within_1e9():
 
 
 # ---------------------------------------------------------------------------
+# Per-step checks (sim_query): discrete continuity (Eq 3.24 with S_m), the
+# global mass balance (text after Eq 4.22) and the predictor-corrector
+# differences of Sec. 4.2.2
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case,precision", [("slot", W.FP64), ("slot", W.MIXED), ("blobs", W.FP64),
+                                            ("sphere", W.MIXED)])
+def test_per_step_continuity_and_mass_balance(case, precision):
+    from paper_2603_01727_gb300 import lowmach as LM
+    if case == "slot":
+        prm, geo, f = W.slot_burner(64, 128)
+    elif case == "blobs":
+        prm, geo, f = W.periodic_blobs(48)
+    else:
+        prm, geo, f = W.sphere_burner(32)
+    prm["poisson_rtol"] = 1e-12
+    prm["precision"] = precision
+    sim = LM.Simulation(prm, geo)
+    sim.set_fields(f)
+    with pytest.raises(LM.SimError):
+        sim.query(LM.SIM_Q_DIV_RESID)           # no step yet
+    vol = float(np.prod(prm["L"][:prm["dim"]]))
+    for k in range(6):
+        sim.step(1)
+        res = sim.query(LM.SIM_Q_DIV_RESID)
+        scale = sim.query(LM.SIM_Q_DIV_SCALE)
+        bal = sim.query(LM.SIM_Q_MASS_BALANCE)
+        # the continuity residual is the pressure solve's residual: rtol-small
+        assert res <= 1e-8 * max(scale, 1.0), (k, res, scale)
+        # the outflow shift closes the global balance exactly (rounding only)
+        assert abs(bal) <= 1e-12 * max(scale, 1.0) * vol, (k, bal, scale)
+        assert sim.query(LM.SIM_Q_PC_DIFF_U) > 0.0 and sim.query(LM.SIM_Q_PC_DIFF_P) > 0.0
+    sim.close()
+
+
+def test_predictor_corrector_difference_matches_table2():
+    """Taylor-Green vortex, 50x50, to t = 1.3: the L2 differences between
+    predicted and corrected v1, v2 and P reproduce Table 2 (dt = 4e-3 and 2e-3)
+    to 0.2 %, as the oracle does."""
+    from conftest import golden
+    from paper_2603_01727_gb300 import lowmach as LM
+    rows = golden("taylor_green_table2.txt")
+    want = {(float(r[1]), r[2]): float(r[3]) for r in rows}
+    for dt in (4e-3, 2e-3):
+        prm, geo, f = W.taylor_green(50, dt)
+        sim = gpu_run(prm, geo, f, int(round(1.3 / dt)))
+        got = {"P": sim.query(LM.SIM_Q_PC_DIFF_P), "v1": sim.query(LM.SIM_Q_PC_DIFF_U),
+               "v2": sim.query(LM.SIM_Q_PC_DIFF_V)}
+        for var, v in got.items():
+            assert v == pytest.approx(want[(dt, var)], rel=2e-3), (dt, var, v, want[(dt, var)])
+        sim.close()
+
+
+# ---------------------------------------------------------------------------
 # Execution paths and error handling
 # ---------------------------------------------------------------------------
 def test_graph_and_eager_paths_agree_bitwise(monkeypatch):
@@ -408,6 +461,25 @@ def test_step_save_equals_step_then_state_save(case, buf):
         assert np.array_equal(ref, host(out))
     a.close()
     b.close()
+
+
+def test_second_run_after_set_fields_repeats_the_first():
+    """Setting the fields again restarts from level 0 whatever the previous
+    run left in the rotating density buffers: after 5 steps (a count that is
+    not a multiple of the three-level rotation) a second run on the same
+    simulation reproduces the first bit for bit."""
+    from paper_2603_01727_gb300.lowmach import Simulation
+    prm, geo, f = W.slot_burner(32, 64)
+    sim = Simulation(prm, geo)
+    out = []
+    for _ in range(2):
+        sim.set_fields(f)
+        sim.step(5)
+        sim.sync()
+        out.append({k: sim.get(k) for k in ("U", "V", "Z", "RHO", "P")})
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+    sim.close()
 
 
 def test_repeat_runs_are_bitwise_deterministic():
