@@ -62,7 +62,7 @@ enum {
 };
 
 enum { SIM_FP64 = 0, SIM_MIXED = 1 };
-enum { SIM_IBM_NONE = 0, SIM_IBM_SLOT = 1, SIM_IBM_SPHERE = 2 };
+enum { SIM_IBM_NONE = 0, SIM_IBM_SLOT = 1, SIM_IBM_SPHERE = 2, SIM_IBM_MARKERS = 3 };
 
 /* Run parameters (paper notation, Eqs 2.42-2.50). */
 typedef struct {
@@ -109,7 +109,18 @@ typedef struct {
  * the piecewise-linear interpolant of profile[0..n_profile-1] sampled uniformly
  * over the shifted width (profile may be NULL); v_ib = (0, U (x_2-y_lo)/(y_hi-y_lo)),
  * S_m = rho_b U / (n_col h_2) on the n_col masked cells of each column.
- * SPHERE (circle in 2D): v_ib = U_b (x-c)/r, S_m = (dim-1) rho_b U_b / r. */
+ * SPHERE (circle in 2D): v_ib = U_b (x-c)/r, S_m = (dim-1) rho_b U_b / r.
+ * MARKERS: a body given by n_markers surface markers, row m of `markers`
+ * being (x[dim], n[dim], U, A): position, unit outward normal, normal ejection
+ * speed and surface element (arc length in 2D, area in 3D).  Every cell centre
+ * p is matched with its nearest marker (least |p - x_m|^2, lowest index on a
+ * tie); p is in the shifted body iff (p - x_m).n_m <= sqrt(Da_ib), and there
+ * v_ib = U_m n_m.  Cells outside the markers' bounding box widened by
+ * 2 sqrt(Da_ib) are outside.  Marker m's flow rho_b U_m A_m is spread
+ * uniformly over the N_m masked interior cells matched with it,
+ * S_m = rho_b U_m A_m / (N_m dV); SIM_EINVAL if some N_m = 0 (markers denser
+ * than the cells) or if 2 dim + 2 times n_markers exceeds the padded cell
+ * count.  center, half, radius, U_b and the profile are unused. */
 typedef struct {
     int kind;                /* SIM_IBM_*                                              */
     double center[3];
@@ -120,6 +131,9 @@ typedef struct {
     double Z_ib, H_ib;       /* body targets in the paper's variables (Eq 4.21)        */
     int n_profile;           /* number of profile samples (0: none)                    */
     const double *profile;   /* host pointer, copied during the call                   */
+    int n_markers;           /* MARKERS: number of markers                             */
+    const double *markers;   /* MARKERS: host pointer to n_markers rows of 2 dim + 2
+                                doubles, copied during the call                        */
 } sim_ibm_t;
 
 /* Field identifiers for sim_fields. */

@@ -14,13 +14,40 @@ H_ib, and mass source S_m.
   bottom and top of the body; S_m = rho_b U(x_1)/(n_col dx_2) on the n_col masked
   cells of each column, so that the discrete integral of S_m (Eq 3.22) equals the
   prescribed ejected mass flow sum_i rho_b U(x_1,i) dx_1 exactly.
+* Body given by surface markers (the marker form of the immersed boundary,
+  Sec. 3.4): marker m carries its position x_m, unit outward normal n_m, normal
+  ejection speed U_m and surface element A_m (length in 2D, area in 3D).  A
+  cell centre p is matched with its nearest marker (least |p - x_m|^2, the
+  lowest index on a tie); its signed distance to the body is the normal
+  offset (p - x_m).n_m, so chi = 1 iff that offset is <= s; v_ib = U_m n_m
+  there (outward normal ejection, the radial form of Eq 4.20 when the markers
+  lie on a sphere).  Cells outside the markers' bounding box widened by 2s
+  are outside the shifted body.  The ejected flow rho_b U_m A_m of each marker
+  is spread uniformly over the N_m masked interior cells matched with it,
+  S_m = rho_b U_m A_m / (N_m dV), so the discrete integral of S_m equals the
+  total sum_m rho_b U_m A_m exactly; every marker needs N_m >= 1 (markers no
+  denser than the cells).
 """
 
 import numpy as np
 
 from .operators import V
 
-NONE, SLOT, SPHERE = 0, 1, 2
+NONE, SLOT, SPHERE, MARKERS = 0, 1, 2, 3
+
+
+def nearest_markers(pts, X):
+    """Index of the nearest marker of every point (first minimum of the squared
+    distance, summed over the directions in order), by brute force in chunks."""
+    out = np.empty(len(pts), dtype=np.int64)
+    for a in range(0, len(pts), 4096):
+        P = pts[a:a + 4096]
+        d2 = None
+        for d in range(X.shape[1]):
+            t = P[:, d:d + 1] - X[None, :, d]
+            d2 = t * t if d2 is None else d2 + t * t
+        out[a:a + 4096] = np.argmin(d2, axis=1)
+    return out
 
 
 def build(g, geo):
@@ -73,6 +100,36 @@ def build(g, geo):
         n_col = np.sum(chi_int, axis=g.ax(1), keepdims=True)
         n_col_safe = np.where(n_col > 0, n_col, 1.0)
         Sm_int = chi_int * rho_b * V(U, g) / (n_col_safe * g.h[1])
+        Sm_full = g.zeros()
+        V(Sm_full, g)[...] = Sm_int
+    elif geo["kind"] == MARKERS:
+        M = np.asarray(geo["markers"], dtype=float).reshape(-1, 2 * dim + 2)
+        X, Nrm, Um, Am = M[:, :dim], M[:, dim:2 * dim], M[:, 2 * dim], M[:, 2 * dim + 1]
+        lo = X.min(axis=0) - 2.0 * s
+        hi = X.max(axis=0) + 2.0 * s
+        pts = np.stack([x[d].ravel() for d in range(dim)], axis=1)
+        inbox = np.all((pts >= lo) & (pts <= hi), axis=1)
+        near = np.full(len(pts), -1, dtype=np.int64)
+        near[inbox] = nearest_markers(pts[inbox], X)
+        m = near[inbox]
+        off = None
+        for d in range(dim):
+            t = (pts[inbox, d] - X[m, d]) * Nrm[m, d]
+            off = t if off is None else off + t
+        chi_flat = np.zeros(len(pts))
+        chi_flat[inbox] = (off <= s).astype(float)
+        chi = chi_flat.reshape(g.shape)
+        near = near.reshape(g.shape)
+        safe = np.where(near >= 0, near, 0)
+        for d in range(dim):
+            vib[d] = chi * Um[safe] * Nrm[safe, d]
+        chi_int = V(chi, g)
+        near_int = V(near, g)
+        counts = np.bincount(near_int[chi_int > 0].ravel(), minlength=len(M))
+        if np.any(counts == 0):
+            raise ValueError("a marker has no masked cell matched with it (markers denser than the cells)")
+        mi = np.where(near_int >= 0, near_int, 0)
+        Sm_int = chi_int * (rho_b * Um[mi] * Am[mi] / (counts[mi] * g.dV))
         Sm_full = g.zeros()
         V(Sm_full, g)[...] = Sm_int
     else:

@@ -965,8 +965,12 @@ sim_status sim_set_ibm_geometry(sim_t* s, const sim_ibm_t* geo) {
         CK(cudaGetLastError());
         return SIM_OK;
     }
-    if (geo->kind != SIM_IBM_SLOT && geo->kind != SIM_IBM_SPHERE)
+    if (geo->kind != SIM_IBM_SLOT && geo->kind != SIM_IBM_SPHERE && geo->kind != SIM_IBM_MARKERS)
         return fail(s, SIM_EINVAL, "unknown body kind %d", geo->kind);
+    const int mk_stride = 2 * s->g.dim + 2;
+    if (geo->kind == SIM_IBM_MARKERS &&
+        (geo->n_markers < 1 || !geo->markers || (long long)geo->n_markers * mk_stride > s->g.npad))
+        return fail(s, SIM_EINVAL, "markers: need 1 to %lld rows of %d doubles", s->g.npad / mk_stride, mk_stride);
     if (!(geo->Da_ib > 0.0)) return fail(s, SIM_EINVAL, "Da_ib must be > 0");
     if (geo->n_profile < 0 || geo->n_profile > kMaxProfile || (geo->n_profile > 0 && !geo->profile) ||
         geo->n_profile == 1)
@@ -991,7 +995,51 @@ sim_status sim_set_ibm_geometry(sim_t* s, const sim_ibm_t* geo) {
                            s->stream));
         b.profile = s->profile;
     }
-    launch_ibm(s->g, b, s->chi, s->vib, s->U, s->Sm, s->stream);
+    if (geo->kind == SIM_IBM_MARKERS) {
+        // set-up scratch: the marker rows in the first momentum array, the
+        // nearest-marker index per padded cell and the per-marker counts in
+        // the predictor velocity arrays (all rewritten by every step)
+        const int D = s->g.dim;
+        b.n_mk = geo->n_markers;
+        for (int d = 0; d < 3; ++d) {
+            b.bb_lo[d] = 0.0;
+            b.bb_hi[d] = 0.0;
+        }
+        for (int d = 0; d < D; ++d) {
+            double lo = geo->markers[d], hi = geo->markers[d];
+            for (int m = 1; m < geo->n_markers; ++m) {
+                const double v = geo->markers[(size_t)m * mk_stride + d];
+                lo = v < lo ? v : lo;
+                hi = v > hi ? v : hi;
+            }
+            b.bb_lo[d] = lo - 2.0 * b.s;
+            b.bb_hi[d] = hi + 2.0 * b.s;
+        }
+        CK(cudaMemcpyAsync(s->mom[0], geo->markers, sizeof(double) * (size_t)geo->n_markers * mk_stride,
+                           cudaMemcpyHostToDevice, s->stream));
+        b.mk = s->mom[0];
+        int* near = reinterpret_cast<int*>(s->vs[0]);
+        int* counts = reinterpret_cast<int*>(s->vs[1]);
+        CK(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)geo->n_markers, s->stream));
+        launch_marker_cells(s->g, b, s->chi, s->vib, s->U, s->Sm, near, counts, s->stream);
+        CK(cudaGetLastError());
+        std::vector<int> hc((size_t)geo->n_markers);
+        CK(cudaMemcpyAsync(hc.data(), counts, sizeof(int) * hc.size(), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        for (int m = 0; m < geo->n_markers; ++m)
+            if (hc[(size_t)m] == 0) {
+                s->ibm_active = 0;
+                CK(cudaMemsetAsync(s->chi, 0, (size_t)s->g.npad, s->stream));
+                launch_bkinds(s->g, bc, nullptr, s->kind, s->part, s->sc, s->stream);
+                CK(cudaStreamSynchronize(s->stream));
+                return fail(s, SIM_EINVAL, "marker %d has no masked cell matched with it (markers denser than "
+                            "the cells)", m);
+            }
+        launch_marker_source(s->g, b, s->chi, near, counts, s->Sm, s->stream);
+        b.mk = nullptr;   // the scratch is reused by the steps
+    } else {
+        launch_ibm(s->g, b, s->chi, s->vib, s->U, s->Sm, s->stream);
+    }
     s->ibm = b;
     launch_bkinds(s->g, bc, s->chi, s->kind, s->part, s->sc, s->stream);
     CK(cudaStreamSynchronize(s->stream));

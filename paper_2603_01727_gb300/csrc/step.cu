@@ -888,6 +888,94 @@ __global__ void k_ibm_cells(Geom g, IbmDev b, uint8_t* chi, double* vib0, double
     }
 }
 
+// Marker body (Sec. 3.4 with the body given by surface markers): every padded
+// cell centre p is matched with its nearest marker (least |p - x_m|^2 summed
+// over the directions in order, the lowest index on a tie); the normal offset
+// (p - x_m).n_m <= s marks it (shifted mask), and v_ib = U_m n_m there.  Cells
+// outside the markers' box widened by 2 s are outside the body.  The distance
+// and offset are formed with explicitly rounded products and sums, so the
+// integer decisions do not depend on FMA contraction.  Markers are scanned in
+// chunks staged in shared memory.
+constexpr int kMkChunk = 256;
+__global__ void __launch_bounds__(NT) k_marker_cells(Geom g, IbmDev b, uint8_t* chi, double* vib0, double* vib1,
+                                                     double* vib2, double* U, double* Sm, int* near, int* counts) {
+    __shared__ double sx[3][kMkChunk];
+    const int D = g.dim, stride = 2 * g.dim + 2;
+    const long long c = (long long)blockIdx.x * NT + threadIdx.x;
+    const bool live = c < g.npad;
+    int q[3] = {0, 0, 0};
+    double x[3] = {0.0, 0.0, 0.0};
+    bool inbox = false;
+    if (live) {
+        padded_coords(g, c, q);
+        inbox = true;
+        for (int d = 0; d < D; ++d) {
+            x[d] = ((double)q[d] - 0.5) * g.h[d];
+            if (x[d] < b.bb_lo[d] || x[d] > b.bb_hi[d]) inbox = false;
+        }
+    }
+    double best = 0.0;
+    int bm = -1;
+    if (__syncthreads_or(inbox)) {
+        for (int m0 = 0; m0 < b.n_mk; m0 += kMkChunk) {
+            const int cnt = min(kMkChunk, b.n_mk - m0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < cnt; i += NT)
+                for (int d = 0; d < D; ++d) sx[d][i] = b.mk[(long long)(m0 + i) * stride + d];
+            __syncthreads();
+            if (!inbox) continue;
+            for (int i = 0; i < cnt; ++i) {
+                double d2 = 0.0;
+                for (int d = 0; d < D; ++d) {
+                    const double t = __dsub_rn(x[d], sx[d][i]);
+                    d2 = (d == 0) ? __dmul_rn(t, t) : __dadd_rn(d2, __dmul_rn(t, t));
+                }
+                if (bm < 0 || d2 < best) {
+                    best = d2;
+                    bm = m0 + i;
+                }
+            }
+        }
+    }
+    if (!live) return;
+    double* vib[3] = {vib0, vib1, vib2};
+    double m = 0.0, Um = 0.0, nrm[3] = {0.0, 0.0, 0.0};
+    if (bm >= 0) {
+        const double* M = b.mk + (long long)bm * stride;
+        double off = 0.0;
+        for (int d = 0; d < D; ++d) {
+            nrm[d] = M[D + d];
+            const double t = __dmul_rn(__dsub_rn(x[d], M[d]), nrm[d]);
+            off = (d == 0) ? t : __dadd_rn(off, t);
+        }
+        m = (off <= b.s) ? 1.0 : 0.0;
+        Um = M[2 * D];
+    }
+    near[c] = bm;
+    chi[c] = (uint8_t)(m != 0.0);
+    for (int d = 0; d < D; ++d) vib[d][c] = __dmul_rn(__dmul_rn(m, Um), nrm[d]);
+    U[c] = 0.0;
+    Sm[c] = 0.0;
+    bool interior = true;
+    for (int d = 0; d < D; ++d)
+        if (q[d] < 1 || q[d] > g.n[d]) interior = false;
+    if (interior && m != 0.0) atomicAdd(counts + bm, 1);
+}
+
+// S_m = rho_b U_m A_m / (N_m dV) on the N_m masked interior cells matched with
+// marker m: the discrete integral of S_m is the markers' total ejected flow.
+__global__ void k_marker_source(Geom g, IbmDev b, const uint8_t* chi, const int* near, const int* counts,
+                                double* Sm) {
+    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+    if (t >= g.ncell) return;
+    const long long c = pad_index(g, t);
+    if (!chi[c]) return;
+    const int stride = 2 * g.dim + 2;
+    const double* M = b.mk + (long long)near[c] * stride;
+    Sm[c] = __dmul_rn(__dmul_rn(b.rho_b, M[2 * g.dim]), M[2 * g.dim + 1]) /
+            __dmul_rn((double)counts[near[c]], g.dV);
+}
+
 // Slot source per x_2-column: S_m = rho_b U / (n_col h_2) on the masked cells.
 __global__ void k_slot_source(Geom g, IbmDev b, const uint8_t* chi, const double* U, double* Sm) {
     const long long col = (long long)blockIdx.x * NT + threadIdx.x;
@@ -1798,6 +1886,16 @@ void launch_ibm(const Geom& g, const IbmDev& b, uint8_t* chi, double* vib[3], do
         const long long ncol = (long long)g.n[0] * (g.dim == 3 ? g.n[2] : 1);
         k_slot_source<<<blocks_for(ncol), NT, 0, s>>>(g, b, chi, U, Sm);
     }
+}
+
+void launch_marker_cells(const Geom& g, const IbmDev& b, uint8_t* chi, double* vib[3], double* U, double* Sm,
+                         int* near, int* counts, cudaStream_t s) {
+    k_marker_cells<<<blocks_for(g.npad), NT, 0, s>>>(g, b, chi, vib[0], vib[1], vib[2], U, Sm, near, counts);
+}
+
+void launch_marker_source(const Geom& g, const IbmDev& b, const uint8_t* chi, const int* near, const int* counts,
+                          double* Sm, cudaStream_t s) {
+    k_marker_source<<<blocks_for(g.ncell), NT, 0, s>>>(g, b, chi, near, counts, Sm);
 }
 
 void launch_bkinds(const Geom& g, const int bc[3][2], const uint8_t* chi, uint8_t* kind[3][2], double* part,

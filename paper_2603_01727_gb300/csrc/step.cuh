@@ -220,9 +220,22 @@ struct IbmDev {
     double c[3], half[3], radius, s, rho_b, U_b;
     const double* profile;  // device copy (may be null)
     int n_profile;
+    // marker body (kind 3): rows (x[dim], n[dim], U, A), device copy valid
+    // during set-up only; bounding box of the positions widened by 2 s
+    const double* mk;
+    int n_mk;
+    double bb_lo[3], bb_hi[3];
 };
 void launch_ibm(const Geom& g, const IbmDev& b, uint8_t* chi, double* vib[3], double* U, double* Sm,
                 cudaStream_t s);
+// Marker body, in two parts around the host's check that every marker has a
+// masked cell: nearest marker, mask and v_ib of every padded cell plus the
+// per-marker counts of masked interior cells (counts zeroed by the caller);
+// then S_m from the counts.
+void launch_marker_cells(const Geom& g, const IbmDev& b, uint8_t* chi, double* vib[3], double* U, double* Sm,
+                         int* near, int* counts, cudaStream_t s);
+void launch_marker_source(const Geom& g, const IbmDev& b, const uint8_t* chi, const int* near, const int* counts,
+                          double* Sm, cudaStream_t s);
 void launch_bkinds(const Geom& g, const int bc[3][2], const uint8_t* chi, uint8_t* kind[3][2],
                    double* part, double* sc, cudaStream_t s);
 

@@ -56,7 +56,8 @@ class SimIbm(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("center", ctypes.c_double * 3), ("half", ctypes.c_double * 3),
                 ("radius", ctypes.c_double), ("Da_ib", ctypes.c_double), ("rho_b", ctypes.c_double),
                 ("U_b", ctypes.c_double), ("Z_ib", ctypes.c_double), ("H_ib", ctypes.c_double),
-                ("n_profile", ctypes.c_int), ("profile", ctypes.POINTER(ctypes.c_double))]
+                ("n_profile", ctypes.c_int), ("profile", ctypes.POINTER(ctypes.c_double)),
+                ("n_markers", ctypes.c_int), ("markers", ctypes.POINTER(ctypes.c_double))]
 
 
 _lib = None
@@ -164,11 +165,18 @@ def ibm_struct(geo):
     for k in ("Da_ib", "rho_b", "U_b", "Z_ib", "H_ib"):
         setattr(b, k, float(geo[k]))
     prof = geo.get("profile")
-    keep = None
+    keep = []
     if prof is not None and len(prof) > 0:
-        keep = np.ascontiguousarray(np.asarray(prof, dtype=np.float64))
-        b.n_profile = len(keep)
-        b.profile = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        arr = np.ascontiguousarray(np.asarray(prof, dtype=np.float64))
+        keep.append(arr)
+        b.n_profile = len(arr)
+        b.profile = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    mk = geo.get("markers")
+    if mk is not None and len(mk) > 0:
+        arr = np.ascontiguousarray(np.asarray(mk, dtype=np.float64))
+        keep.append(arr)
+        b.n_markers = arr.shape[0]
+        b.markers = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     return b, keep
 
 

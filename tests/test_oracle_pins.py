@@ -657,3 +657,63 @@ def test_heat_release_vanishes_for_uniform_mixture():
     st = S.initial_state(pb, [np.zeros_like(f["Z"]), np.full_like(f["Z"], 0.2)],
                          np.full_like(f["Z"], prm["inflow_Z"]), f["H"])
     assert O.heat_release(pb, st) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Body given by surface markers (Sec. 3.4, marker form): nearest-marker search,
+# shifted mask against the analytic circle, exact integral of S_m
+# ---------------------------------------------------------------------------
+def test_nearest_marker_search_matches_a_kd_tree():
+    from scipy.spatial import cKDTree
+    from oracle.ibm import nearest_markers
+    rng = np.random.Generator(np.random.PCG64(17))
+    for dim in (2, 3):
+        X = rng.uniform(0.0, 1.0, size=(300, dim))
+        P = rng.uniform(0.0, 1.0, size=(5000, dim))
+        assert np.array_equal(nearest_markers(P, X), cKDTree(X).query(P)[1])
+
+
+@pytest.mark.parametrize("dim,n,spacing", [(2, 128, 1.0), (3, 48, 1.5)])
+def test_marker_body_mask_velocity_and_source(dim, n, spacing):
+    """Markers on a circle / sphere with radial normals describe the analytic
+    body: every cell whose marker mask differs from the analytic shifted mask
+    (r - R <= s) lies within the band that the marker spacing allows, the masked
+    v_ib is U_b along a direction within the marker spacing of radial, and the
+    discrete integral of S_m is the markers' total flow exactly, marker by
+    marker."""
+    from oracle.ibm import build, nearest_markers
+    prm, geo, _ = W.marker_burner(n, dim, spacing=spacing)
+    g = Grid(prm["n"][:dim], prm["L"][:dim])
+    ib = build(g, geo)
+    ana = build(g, dict(geo, kind=W.IBM_SPHERE))
+    M = geo["markers"]
+    R, s = geo["radius"], np.sqrt(geo["Da_ib"])
+    x = [V(g.centres(d), g) for d in range(dim)]
+    r = np.sqrt(sum((x[d] - 0.5) ** 2 for d in range(dim)))
+    chi, chia = V(ib["chi"], g), V(ana["chi"], g)
+    # angular gap to the nearest marker: half the arc spacing on the circle,
+    # the largest marker-to-cell-direction angle on the sphere
+    X = M[:, :dim] - 0.5
+    if dim == 2:
+        phi = np.pi / len(M)
+    else:
+        dirs = np.stack([(x[d] - 0.5).ravel() for d in range(dim)], axis=1)
+        dirs = dirs[np.abs(r.ravel() - R - s) < 3.0 / n]
+        dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+        near = nearest_markers(dirs * R, X)
+        phi = float(np.max(np.arccos(np.clip(np.sum(dirs * X[near] / R, axis=1), -1, 1))))
+    band = r * (1.0 - np.cos(phi)) + 1e-12
+    diff = chi != chia
+    assert np.all(np.abs(r[diff] - R - s) <= band[diff])
+    assert np.sum(diff) <= 0.02 * np.sum(chia)
+    vm = [V(ib["vib"][d], g)[chi > 0] for d in range(dim)]
+    speed = np.sqrt(sum(v * v for v in vm))
+    assert np.allclose(speed, 1.0, rtol=1e-14)
+    radial = sum(vm[d] * (x[d][chi > 0] - 0.5) for d in range(dim)) / np.maximum(r[chi > 0], 1e-300)
+    assert np.all(radial >= np.cos(phi) - 1e-12)
+    flow = geo["rho_b"] * M[:, 2 * dim] * M[:, 2 * dim + 1]
+    assert np.sum(ib["Sm"]) * g.dV == pytest.approx(np.sum(flow), rel=1e-13)
+    pts = np.stack([x[d][chi > 0] for d in range(dim)], axis=1)
+    owner = nearest_markers(pts, M[:, :dim])
+    per = np.bincount(owner, weights=ib["Sm"][chi > 0] * g.dV, minlength=len(M))
+    assert np.allclose(per, flow, rtol=1e-13, atol=0.0)

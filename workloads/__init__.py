@@ -18,12 +18,14 @@ Workloads
                         blobs, solenoidal random velocity (rms 0.1), 64x64.
   slot_burner(...)      2D planar slot burner, 256x512 on [0,1]x[0,2].
   sphere_burner(...)    3D spherical porous burner, 192^3 on [0,1]^3.
+  marker_burner(...)    the porous burner (circle in 2D, sphere in 3D) given by
+                        surface markers instead of its analytic shape.
 """
 
 import numpy as np
 
 PERIODIC, INFLOW, OUTFLOW, WALL, SLIP = 0, 1, 2, 3, 4
-IBM_NONE, IBM_SLOT, IBM_SPHERE = 0, 1, 2
+IBM_NONE, IBM_SLOT, IBM_SPHERE, IBM_MARKERS = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 
 SEED = 20260101
@@ -272,3 +274,61 @@ def sphere_burner(n=192, cfl=0.4, Re=150.0, seed=SEED, rms=0.01):
     prm["dt"] = stable_dt((n, n, n), (1.0, 1.0, 1.0), Re, prm["Pr"], prm["density_ratio"],
                           prm["sigma"], 1.0, cfl, Da_ib=Da, dim=3)
     return prm, geo, dict(v=[u * s, v * s, w * s], Z=Z, H=H)
+
+
+def circle_markers(center, R, count, U_b=1.0):
+    """Markers on a circle: count equal arcs, each marker at its arc's midpoint
+    with the outward radial normal, ejection speed U_b and arc length 2 pi R /
+    count.  Rows (x, y, n_x, n_y, U, A)."""
+    th = 2.0 * np.pi * (np.arange(count) + 0.5) / count
+    nx, ny = np.cos(th), np.sin(th)
+    A = np.full(count, 2.0 * np.pi * R / count)
+    return np.stack([center[0] + R * nx, center[1] + R * ny, nx, ny, np.full(count, U_b), A], axis=1)
+
+
+def sphere_markers(center, R, count, U_b=1.0):
+    """Markers on a sphere: the Fibonacci lattice (equal-area points), outward
+    radial normals, ejection speed U_b and area 4 pi R^2 / count each.  Rows
+    (x, y, z, n_x, n_y, n_z, U, A)."""
+    k = np.arange(count)
+    nz = 1.0 - (2.0 * k + 1.0) / count
+    rr = np.sqrt(1.0 - nz * nz)
+    ph = k * np.pi * (3.0 - np.sqrt(5.0))
+    nx, ny = rr * np.cos(ph), rr * np.sin(ph)
+    A = np.full(count, 4.0 * np.pi * R * R / count)
+    return np.stack([center[0] + R * nx, center[1] + R * ny, center[2] + R * nz, nx, ny, nz,
+                     np.full(count, U_b), A], axis=1)
+
+
+def marker_burner(n=64, dim=2, spacing=1.5, cfl=0.4, Re=150.0, seed=SEED, rms=0.01):
+    """The porous burner given by surface markers: a circle (2D, n x n) or a
+    sphere (3D, n^3) of radius 0.1 at the centre of the unit box, outflow on all
+    sides, markers about ``spacing`` cells apart ejecting fuel with U_b = 1.
+    3D: the sphere_burner recipe with its body replaced by markers.  2D: quiescent
+    air plus a solenoidal perturbation of rms 0.01, fuel inside the circle
+    falling off outside it as a Gaussian of the distance."""
+    R, h = 0.1, 1.0 / n
+    if dim == 3:
+        prm, geo, f = sphere_burner(n, cfl=cfl, Re=Re, seed=seed, rms=rms)
+        count = int(round(4.0 * np.pi * R * R / (spacing * h) ** 2))
+        M = sphere_markers([0.5, 0.5, 0.5], R, count)
+    else:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        prm = _base_params()
+        prm.update(dim=2, n=[n, n, 1], L=[1.0, 1.0, 1.0], Re=Re, Pr=0.7, bc=[[OUTFLOW, OUTFLOW]] * 2 +
+                   [[PERIODIC, PERIODIC]])
+        S, Q, H_inf, Z_fuel = paper_scalars(prm["Z_st"], prm["density_ratio"])
+        prm.update(inflow_Z=0.0, inflow_H=H_inf)
+        geo = dict(kind=IBM_SPHERE, center=[0.5, 0.5, 0.0], half=[0.0, 0.0, 0.0], radius=R, Da_ib=1e-4,
+                   rho_b=1.0, U_b=1.0, Z_ib=Z_fuel, H_ib=H_inf, profile=None)
+        u, v = _solenoidal_2d(rng, (n, n), (1.0, 1.0), 3, rms)
+        x, y = cell_centres((n, n), (1.0, 1.0))
+        dist = np.maximum(np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2) - R, 0.0)
+        width = max(0.04, 10.0 / n)
+        f = dict(v=[u, v], Z=Z_fuel * np.exp(-dist * dist / (2.0 * width * width)), H=np.full(x.shape, H_inf))
+        prm["dt"] = stable_dt((n, n), (1.0, 1.0), Re, prm["Pr"], prm["density_ratio"], prm["sigma"], 1.0, cfl,
+                              Da_ib=1e-4, dim=2)
+        count = int(round(2.0 * np.pi * R / (spacing * h)))
+        M = circle_markers([0.5, 0.5], R, count)
+    geo = dict(geo, kind=IBM_MARKERS, markers=M)
+    return prm, geo, f
