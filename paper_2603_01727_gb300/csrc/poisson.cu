@@ -30,6 +30,7 @@
 // the while-node conditional.
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -623,22 +624,14 @@ __global__ void __launch_bounds__(NTV)
 // operations, so that only three FP64 operations per cell (two additions, the
 // squared norm) use the 1/64-rate FP64 pipe.  The FP32 search direction and
 // r.z are kept.
+// The cells of the reliable-update CG step handled by one thread: compact
+// indices (quads of four x-consecutive cells when vec4) from i0 by stride,
+// below iend; adds ||r||^2 and sum r of the new residual to rr, sr.
 template <int DIM>
-__global__ void __launch_bounds__(NTV)
-    k_ir_step(LvT<double> L, double* __restrict__ x, double* __restrict__ r64, const float* p0, const float* p1,
-              float* __restrict__ r32, double* part, double* part_s, double* scal, int* ictl, unsigned int* cnt,
-              double rtol, int max_iter, cudaGraphConditionalHandle h, int use_graph, int vec4) {
-    pdl_wait();
-    pdl_trigger();
-    const int fb = blockIdx.y;
-    batch_ctl(fb, &scal, &ictl, &cnt);
-    // the system has converged (a batch member, or an iteration captured
-    // ahead of the loop): x, r and the reported scalars stay as they are
-    const int done = ictl[PI_DONE], it = ictl[PI_IT];
-    const float alpha = (float)scal[PS_ALPHA];
-    if (done) return;
+__device__ __forceinline__ void ir_cells(const LvT<double>& L, double* __restrict__ x, double* __restrict__ r64,
+                                         const float* __restrict__ p, float* __restrict__ r32, float alpha,
+                                         int vec4, int i0, int stride, int iend, double& rr, double& sr) {
     // the correction e = alpha p at compact index i (the product rounded once)
-    const float* __restrict__ p = ((it & 1) ? p1 : p0) + (long long)fb * L.N;
     auto ld1 = [&](int i) -> float { return fmaf(alpha, p[i], 0.0f); };
     auto ld4 = [&](int i) -> float4 {
         float4 v = *reinterpret_cast<const float4*>(p + i);
@@ -648,15 +641,9 @@ __global__ void __launch_bounds__(NTV)
         v.w = fmaf(alpha, v.w, 0.0f);
         return v;
     };
-    x += (long long)fb * L.N;
-    r64 += (long long)fb * L.N;
-    r32 += (long long)fb * L.N;
-    part += (long long)fb * gridDim.x;
-    part_s += (long long)fb * gridDim.x;
     FF wd[3];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) wd[d] = FF(L.w[d]);
-    double rr = 0.0, sr = 0.0;
     if (vec4) {
         // four x-consecutive cells per thread step (nx % 4 == 0, x 16-byte
         // aligned; the launch is sized by N / 4): one coordinate map, 16-byte
@@ -664,7 +651,7 @@ __global__ void __launch_bounds__(NTV)
         // arithmetic is the scalar path's, in its order
         const int nx = L.n[0], ny = L.n[1];
         const int N4 = L.N >> 2;
-        for (int q = blockIdx.x * NTV + threadIdx.x; q < N4; q += gridDim.x * NTV) {
+        for (int q = i0; q < min(N4, iend); q += stride) {
             const int t0 = 4 * q;
             int c[3];
             coords(L, t0, c);
@@ -728,7 +715,7 @@ __global__ void __launch_bounds__(NTV)
             *reinterpret_cast<float4*>(r32 + t0) = make_float4(r32o[0], r32o[1], r32o[2], r32o[3]);
         }
     }
-    for (int t = vec4 ? L.N : blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
+    for (int t = vec4 ? L.N : i0; t < min(L.N, iend); t += stride) {
         int c[3];
         coords(L, t, c);
         FF off;
@@ -756,6 +743,31 @@ __global__ void __launch_bounds__(NTV)
         rr = fma(rvd, rvd, rr);
         sr += rvd;
     }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(NTV)
+    k_ir_step(LvT<double> L, double* __restrict__ x, double* __restrict__ r64, const float* p0, const float* p1,
+              float* __restrict__ r32, double* part, double* part_s, double* scal, int* ictl, unsigned int* cnt,
+              double rtol, int max_iter, cudaGraphConditionalHandle h, int use_graph, int vec4) {
+    pdl_wait();
+    pdl_trigger();
+    const int fb = blockIdx.y;
+    batch_ctl(fb, &scal, &ictl, &cnt);
+    // the system has converged (a batch member, or an iteration captured
+    // ahead of the loop): x, r and the reported scalars stay as they are
+    const int done = ictl[PI_DONE], it = ictl[PI_IT];
+    const float alpha = (float)scal[PS_ALPHA];
+    if (done) return;
+    const float* __restrict__ p = ((it & 1) ? p1 : p0) + (long long)fb * L.N;
+    x += (long long)fb * L.N;
+    r64 += (long long)fb * L.N;
+    r32 += (long long)fb * L.N;
+    part += (long long)fb * gridDim.x;
+    part_s += (long long)fb * gridDim.x;
+    double rr = 0.0, sr = 0.0;
+    ir_cells<DIM>(L, x, r64, p, r32, alpha, vec4, blockIdx.x * NTV + threadIdx.x, gridDim.x * NTV, INT_MAX, rr,
+                  sr);
     __shared__ double red[2 * (NTV / 32)];
     block_sum2_t<NTV, double>(rr, sr, red);
     if (threadIdx.x == 0) {
@@ -832,6 +844,28 @@ __global__ void __launch_bounds__(NTV) k_mean(const double* __restrict__ b, long
     }
 }
 
+// r = -(b - mean b) - A x at the compact cells from i0 by stride; adds
+// ||f||^2, ||r||^2 and sum r to ff, rr, sr.
+template <int DIM>
+__device__ __forceinline__ void init_cells(const LvT<double>& L, const double* __restrict__ b,
+                                           const double* __restrict__ x, double* __restrict__ r,
+                                           float* __restrict__ r32, double mean_b, int i0, int stride, double& ff,
+                                           double& rr, double& sr) {
+    for (int t = i0; t < L.N; t += stride) {
+        int c[3];
+        coords(L, t, c);
+        int cl;
+        const double off = off_compact<double, DIM>(L, x, t, c, &cl);
+        const double f = -(b[t] - mean_b);
+        const double rv = f - (L.diag[cl] * x[t] - off);
+        r[t] = rv;
+        if (r32) r32[t] = (float)rv;
+        ff = fma(f, f, ff);
+        rr = fma(rv, rv, rr);
+        sr += rv;
+    }
+}
+
 // r = -(b - mean b) - A x; ||f||^2, ||r||^2; the last block initialises the
 // control words and the while-node conditional.
 template <int DIM>
@@ -852,19 +886,7 @@ __global__ void __launch_bounds__(NTV)
     psr += (long long)fb * gridDim.x;
     const double mean_b = scal[PS_MEANB];
     double ff = 0.0, rr = 0.0, sr = 0.0;
-    for (int t = blockIdx.x * NTV + threadIdx.x; t < L.N; t += gridDim.x * NTV) {
-        int c[3];
-        coords(L, t, c);
-        int cl;
-        const double off = off_compact<double, DIM>(L, x, t, c, &cl);
-        const double f = -(b[t] - mean_b);
-        const double rv = f - (L.diag[cl] * x[t] - off);
-        r[t] = rv;
-        if (r32) r32[t] = (float)rv;
-        ff = fma(f, f, ff);
-        rr = fma(rv, rv, rr);
-        sr += rv;
-    }
+    init_cells<DIM>(L, b, x, r, r32, mean_b, blockIdx.x * NTV + threadIdx.x, gridDim.x * NTV, ff, rr, sr);
     __shared__ double red[2 * (NTV / 32)];
     block_sum2_t<NTV, double>(ff, rr, red);
     sr = block_sum<NTV>(sr, red);
@@ -1189,29 +1211,21 @@ __device__ __forceinline__ void color_sweep(const LvT<T>& L, T (*su)[32], T (*sf
     }
 }
 
+// down on the tile (bx, by) of a level: load f (minus mr on the fine level)
+// and red from zero, then black, red, black, the residual and the
+// restriction.  sf, su (SY x 32) and srow (SY) are the caller's shared
+// arrays; the leading barrier lets a block run tiles back to back.
 template <class T, class TF, int NS>
-__global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restrict__ f, T* __restrict__ upre,
-                                           T* __restrict__ fc, const double* __restrict__ scal_r) {
-    pdl_wait();
-    pdl_trigger();
-    {   // system of a batch
-        const long long fb = blockIdx.z;
-        f += fb * L.N;
-        upre += fb * L.N;
-        fc += fb * C.N;
-        if (scal_r) scal_r += fb * PS_NSCAL;
-    }
-    // fine level: the CG residual enters the preconditioner with its mean removed
-    const TF mr = scal_r ? (TF)scal_r[PS_MEANR] : (TF)0;
+__device__ __forceinline__ void down_tile(const LvT<T>& L, const LvT<T>& C, const TF* __restrict__ f,
+                                          T* __restrict__ upre, T* __restrict__ fc, TF mr, int bx, int by,
+                                          T (*sf)[32], T (*su)[32], int* srow) {
+    __syncthreads();
     constexpr int H = 2 * NS + 1, FD = fd_of(NS), CD = cd_of(NS);
-    __shared__ T sf[SY][32];
-    __shared__ T su[SY][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ox = blockIdx.x * FD - H, oy = blockIdx.y * FD - H;
+    const int ox = bx * FD - H, oy = by * FD - H;
     const int nx = L.n[0];
     const int par0 = (ox + oy) & 1;
     const Ax ax = axis(ox + lane, nx, L.per[0]);
-    __shared__ int srow[SY];
     const ColCodes cc = box_codes<T>(L, ox, oy, srow);
     Ax ayk[SY / NW];   // this thread's rows (kept for the residual pass)
 #pragma unroll
@@ -1253,7 +1267,7 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
     // box offset 2 c + H - 1 + a
     for (int c = threadIdx.x; c < CD * CD; c += NT) {
         const int cx = c % CD, cy = c / CD;
-        const int I = blockIdx.x * CD + cx, J = blockIdx.y * CD + cy;
+        const int I = bx * CD + cx, J = by * CD + cy;
         if (I >= C.n[0] || J >= C.n[1]) continue;
         T wx[4];
 #pragma unroll
@@ -1272,36 +1286,41 @@ __global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restr
     }
 }
 
-template <class T, class TF, bool FINE, int NS>
-__global__ void __launch_bounds__(NT)
-    up(LvT<T> L, LvT<T> C, const T* __restrict__ upre, const TF* __restrict__ f, const T* __restrict__ uc,
-       T* __restrict__ upost, double* part_rz, double* part_sz, double* scal, const int* ictl, unsigned int* cnt) {
+template <class T, class TF, int NS>
+__global__ void __launch_bounds__(NT) down(LvT<T> L, LvT<T> C, const TF* __restrict__ f, T* __restrict__ upre,
+                                           T* __restrict__ fc, const double* __restrict__ scal_r) {
     pdl_wait();
     pdl_trigger();
     {   // system of a batch
         const long long fb = blockIdx.z;
-        upre += fb * L.N;
         f += fb * L.N;
-        uc += fb * C.N;
-        upost += fb * L.N;
-        if (FINE) {
-            part_rz += fb * gridDim.x * gridDim.y;
-            part_sz += fb * gridDim.x * gridDim.y;
-            scal += fb * PS_NSCAL;
-            ictl += fb * PI_NINT;
-            cnt += fb * kNumCounters;
-        }
+        upre += fb * L.N;
+        fc += fb * C.N;
+        if (scal_r) scal_r += fb * PS_NSCAL;
     }
-    const TF mr = FINE ? (TF)scal[PS_MEANR] : (TF)0;   // fine level: residual mean removed
-    constexpr int H = 2 * NS, FU = fu_of(NS);
+    // fine level: the CG residual enters the preconditioner with its mean removed
+    const TF mr = scal_r ? (TF)scal_r[PS_MEANR] : (TF)0;
     __shared__ T sf[SY][32];
     __shared__ T su[SY][32];
+    __shared__ int srow[SY];
+    down_tile<T, TF, NS>(L, C, f, upre, fc, mr, blockIdx.x, blockIdx.y, sf, su, srow);
+}
+
+// up on the tile (bx, by) of a level: prolongation-add, then black, red,
+// black, red; on the fine level the partial sums of r.z and sum z over the
+// tile's cells are added to rz, sz.  Shared arrays as for down_tile.
+template <class T, class TF, bool FINE, int NS>
+__device__ __forceinline__ void up_tile(const LvT<T>& L, const LvT<T>& C, const T* __restrict__ upre,
+                                        const TF* __restrict__ f, const T* __restrict__ uc, T* __restrict__ upost,
+                                        TF mr, int bx, int by, T (*sf)[32], T (*su)[32], int* srow, TF& rz,
+                                        TF& sz) {
+    __syncthreads();
+    constexpr int H = 2 * NS, FU = fu_of(NS);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ox = blockIdx.x * FU - H, oy = blockIdx.y * FU - H;
+    const int ox = bx * FU - H, oy = by * FU - H;
     const int nx = L.n[0];
     const int par0 = (ox + oy) & 1;
     const Ax ax = axis(ox + lane, nx, L.per[0]);
-    __shared__ int srow[SY];
     const ColCodes cc = box_codes<T>(L, ox, oy, srow);
     // coarse columns of this lane's fine column (bilinear prolongation)
     int I0 = 0, I1 = 0;
@@ -1334,7 +1353,6 @@ __global__ void __launch_bounds__(NT)
         color_sweep<T>(L, su, sf, par0, k & 1, k, SY - 1 - k, k, 31 - k, cc, srow);
         __syncthreads();
     }
-    TF rz = (TF)0, sz = (TF)0;    // FP64 path: double; refinement mode: FP32
     const bool colo = ax.in && lane >= H && lane < H + FU;
 #pragma unroll
     for (int k = 0; k < SY / NW; ++k) {
@@ -1352,6 +1370,34 @@ __global__ void __launch_bounds__(NT)
             sz += (TF)u;
         }
     }
+}
+
+template <class T, class TF, bool FINE, int NS>
+__global__ void __launch_bounds__(NT)
+    up(LvT<T> L, LvT<T> C, const T* __restrict__ upre, const TF* __restrict__ f, const T* __restrict__ uc,
+       T* __restrict__ upost, double* part_rz, double* part_sz, double* scal, const int* ictl, unsigned int* cnt) {
+    pdl_wait();
+    pdl_trigger();
+    {   // system of a batch
+        const long long fb = blockIdx.z;
+        upre += fb * L.N;
+        f += fb * L.N;
+        uc += fb * C.N;
+        upost += fb * L.N;
+        if (FINE) {
+            part_rz += fb * gridDim.x * gridDim.y;
+            part_sz += fb * gridDim.x * gridDim.y;
+            scal += fb * PS_NSCAL;
+            ictl += fb * PI_NINT;
+            cnt += fb * kNumCounters;
+        }
+    }
+    const TF mr = FINE ? (TF)scal[PS_MEANR] : (TF)0;   // fine level: residual mean removed
+    __shared__ T sf[SY][32];
+    __shared__ T su[SY][32];
+    __shared__ int srow[SY];
+    TF rz = (TF)0, sz = (TF)0;    // FP64 path: double; refinement mode: FP32
+    up_tile<T, TF, FINE, NS>(L, C, upre, f, uc, upost, mr, blockIdx.x, blockIdx.y, sf, su, srow, rz, sz);
     if (FINE) {
         __shared__ double red[2 * (NT / 32)];
         __shared__ float redf[2 * (NT / 32)];
@@ -1377,30 +1423,18 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
+// CG direction and operator on the tile (bx, by): p = (z - mz) + beta p_old
+// (double-buffered by the iteration parity it), q = A p; p.q over the tile's
+// cells is added to acc.  sp (SY x 32) is the caller's shared array.
 template <class T, class V>
-__global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p0, V* p1, V* __restrict__ q,
-                                         double* part, double* scal, const int* ictl, unsigned int* cnt) {
-    pdl_wait();
-    pdl_trigger();
-    {   // system of a batch
-        const long long fb = blockIdx.z;
-        z += fb * L.N;
-        p0 += fb * L.N;
-        p1 += fb * L.N;
-        q += fb * L.N;
-        part += fb * gridDim.x * gridDim.y;
-        scal += fb * PS_NSCAL;
-        ictl += fb * PI_NINT;
-        cnt += fb * kNumCounters;
-    }
+__device__ __forceinline__ void pq_tile(const LvT<V>& L, const T* __restrict__ z, V* p0, V* p1, V* __restrict__ q,
+                                        int it, V beta, V mz, int bx, int by, V (*sp)[32], V& acc) {
+    __syncthreads();
     constexpr int H = 1;
-    __shared__ V sp[SY][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int it = ictl[PI_IT];
     const V* pold = (it & 1) ? p0 : p1;
     V* pnew = (it & 1) ? p1 : p0;
-    const V beta = (V)scal[PS_BETA], mz = (V)scal[PS_MEANZ];
-    const int ox = blockIdx.x * FP - H, oy = blockIdx.y * FP - H;
+    const int ox = bx * FP - H, oy = by * FP - H;
     const int nx = L.n[0];
     const Ax ax = axis(ox + lane, nx, L.per[0]);
     Ax ayk[SY / NW];   // this thread's rows and p values (kept for the second pass)
@@ -1420,7 +1454,6 @@ __global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p
         pvk[k] = pv;
     }
     __syncthreads();
-    V acc = (V)0;
     const bool colo = ax.in && lane >= H && lane < H + FP;
 #pragma unroll
     for (int k = 0; k < SY / NW; ++k) {
@@ -1436,6 +1469,28 @@ __global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p
         q[g] = qv;
         acc = fma(pv, qv, acc);
     }
+}
+
+template <class T, class V>
+__global__ void __launch_bounds__(NT) pq(LvT<V> L, const T* __restrict__ z, V* p0, V* p1, V* __restrict__ q,
+                                         double* part, double* scal, const int* ictl, unsigned int* cnt) {
+    pdl_wait();
+    pdl_trigger();
+    {   // system of a batch
+        const long long fb = blockIdx.z;
+        z += fb * L.N;
+        p0 += fb * L.N;
+        p1 += fb * L.N;
+        q += fb * L.N;
+        part += fb * gridDim.x * gridDim.y;
+        scal += fb * PS_NSCAL;
+        ictl += fb * PI_NINT;
+        cnt += fb * kNumCounters;
+    }
+    __shared__ V sp[SY][32];
+    V acc = (V)0;
+    pq_tile<T, V>(L, z, p0, p1, q, ictl[PI_IT], (V)scal[PS_BETA], (V)scal[PS_MEANZ], blockIdx.x, blockIdx.y, sp,
+                  acc);
     __shared__ double red[NT / 32];
     __shared__ float redf[NT / 32];
     const double bacc = block_sum_any<NT>(acc, red, redf);
@@ -1609,9 +1664,10 @@ constexpr int FT = 256;            // threads of the fast-diagonalisation block
 // fall on at most four consecutive pairs); optionally C .*= S.  The sum over k
 // runs in ascending order with one fmaf per term.  N % 4 == 0, M even.
 __device__ __forceinline__ void mmT(float* __restrict__ C, const float* __restrict__ LT, int ldl,
-                                    const float* __restrict__ R, int M, int N, int K, const float* __restrict__ S) {
+                                    const float* __restrict__ R, int M, int N, int K, const float* __restrict__ S,
+                                    int nthreads = FT) {
     const int tn = N / 4;
-    for (int tile = threadIdx.x; tile < (M / 2) * tn; tile += FT) {
+    for (int tile = threadIdx.x; tile < (M / 2) * tn; tile += nthreads) {
         const int m0 = 2 * (tile / tn), n0 = 4 * (tile % tn);
         float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
 #pragma unroll 8
@@ -1697,6 +1753,346 @@ __global__ void __launch_bounds__(FT) fdm(int nx, int ny, const float* __restric
 }
 
 }  // namespace k2
+
+// ---------------------------------------------------------------------------
+// Persistent 2D solve.  A small 2D system (the 256 x 512 flame: about 15 CG
+// iterations per step, each a chain of nine short kernels) is bound by launch
+// and drain latency, not by its bytes.  Here the whole solve -- the mean of
+// b, r = f - A x, then every CG iteration (the V(2,2) cycle's down sweeps,
+// the fast-diagonalisation top level, the up sweeps with r.z, the direction
+// and operator p, q, and the reliable update of x and r) -- runs in one
+// cooperative launch whose blocks are all resident.  Each phase spreads the
+// level's tiles (or cells) over the blocks and ends at a grid barrier; a
+// phase that ends in a reduction finishes it in the last block to arrive,
+// which sums the blocks' partials in index order (deterministic) and writes
+// the scalars before releasing the others.  Every wait is bounded: a block
+// that waits longer than kSpin polls raises the abort word, which ends every
+// block at its next barrier, and the solve reports non-convergence.
+// ---------------------------------------------------------------------------
+namespace kp {
+
+constexpr int kLev = 6;                  // levels 0 .. top handled
+constexpr unsigned kSpin = 1u << 22;     // polls of a waiting block (about a second)
+// barrier words in a scratch array of their own, on separate 128-byte lines (the
+// arrival counter, the generation the waiting blocks poll, the abort flag)
+enum { BAR_COUNT = 0, BAR_GEN = 32, BAR_ABORT = 64, BAR_WORDS = 96 };
+
+struct Args {
+    LvT<float> lev[kLev];   // FP32 level descriptors 0 .. top
+    LvT<double> L0;          // the fine level in FP64 (residual and reliable update)
+    int top;
+    int dtx[kLev], dty[kLev];   // down tiles of level l (its coarse tile grid)
+    int utx[kLev], uty[kLev];   // up tiles of level l
+    int ptx, pty;               // operator tiles of the fine level
+    const double* b;
+    double* x;
+    double* r;
+    float* r32;
+    float* u0pre;
+    float* z;
+    float* upre[kLev];
+    float* f[kLev];
+    float* upost[kLev];
+    float* p0;
+    float* p1;
+    float* q;
+    const float* fdm_tab;
+    double* part;               // 3 x gridDim.x partial sums
+    double* scal;
+    int* ictl;
+    unsigned* bar;              // barrier words (BAR_*)
+    double rtol;
+    int max_iter;
+    int vec4;
+    int mean_ready;
+    unsigned arrivals;          // blocks a barrier waits for (gridDim.x)
+    unsigned spin;              // polls before a waiting block gives up
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier.  Every block arrives once; the last one runs fin() with all
+// its threads (the other blocks' partials are visible to it: their arrivals
+// release, its own acquires), then releases the generation word, which the
+// waiting blocks acquire.  Returns false once the solve has been aborted.
+__device__ __forceinline__ void st_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+template <class Fin>
+__device__ __forceinline__ bool barrier(const Args& a, Fin fin) {
+    __shared__ int s_last, s_ok;
+    unsigned* cnt = a.bar + BAR_COUNT;
+    unsigned* gen = a.bar + BAR_GEN;
+    int* abort = reinterpret_cast<int*>(a.bar + BAR_ABORT);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        s_last = 0;
+        const unsigned g0 = ld_acquire_u32(gen);
+        const unsigned arrived = atomic_add_acq_rel_gpu(cnt, 1u);
+        if (arrived == a.arrivals - 1u) {
+            s_last = 1;
+        } else {
+            unsigned n = 0;
+            while (ld_relaxed_u32(gen) == g0) {
+                if ((++n & 255u) == 0u) {
+                    if (ld_relaxed_i32(abort)) {
+                        s_ok = 0;
+                        break;
+                    }
+                    if (n > a.spin) {
+                        atomicExch(abort, 1);
+                        a.ictl[PI_NOCONV] = 1;
+                        a.ictl[PI_DONE] = 1;
+                        s_ok = 0;
+                        break;
+                    }
+                }
+            }
+            fence_acq_rel_gpu();   // the released writes are visible from here on
+        }
+    }
+    __syncthreads();
+    if (s_last) {
+        fin();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *cnt = 0u;
+            fence_acq_rel_gpu();
+            atomicAdd(gen, 1u);
+        }
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void no_fin() {}
+
+// Fast-diagonalisation solve of the top level by one block (all its threads):
+// the table and f staged in shared memory, then the four products.
+__device__ void fdm_block(int nx, int ny, const float* __restrict__ tab, const float* __restrict__ f,
+                          float* __restrict__ u, float* sm) {
+    float* Sx = sm;
+    float* SxT = Sx + nx * nx;
+    float* Sy = SxT + nx * nx;
+    float* SyT = Sy + ny * ny;
+    float* IL = SyT + ny * ny;
+    float* X = IL + nx * ny;
+    float* Y = X + nx * k2::fdm_ldf(ny);
+    const int ntab = 2 * nx * nx + 2 * ny * ny + nx * ny;
+    for (int i = threadIdx.x; i < ntab / 4; i += blockDim.x)
+        reinterpret_cast<float4*>(Sx)[i] = __ldcg(reinterpret_cast<const float4*>(tab) + i);
+    const int ldf = k2::fdm_ldf(ny);
+    for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) {
+        const int y = i / nx, x = i - y * nx;
+        X[x * ldf + y] = __ldcg(f + i);
+    }
+    __syncthreads();
+    k2::mmT(Y, X, ldf, Sx, ny, nx, nx, nullptr, blockDim.x);
+    __syncthreads();
+    k2::mmT(X, Sy, ny, Y, ny, nx, ny, IL, blockDim.x);
+    __syncthreads();
+    k2::mmT(Y, X, nx, SyT, nx, ny, ny, nullptr, blockDim.x);
+    __syncthreads();
+    k2::mmT(u, Y, ny, SxT, ny, nx, nx, nullptr, blockDim.x);
+}
+
+__global__ void __launch_bounds__(k2::NT, 2) k_solve2(const __grid_constant__ Args a) {
+    using namespace k2;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ float sf[SY][32];
+    __shared__ float su[SY][32];
+    __shared__ int srow[SY];
+    __shared__ double red[2 * (NT / 32)];
+    __shared__ float redf[2 * (NT / 32)];
+    const int nb = gridDim.x, bi = blockIdx.x, tid = threadIdx.x;
+    double* P0 = a.part;
+    double* P1 = a.part + nb;
+    double* P2 = a.part + 2 * nb;
+    double* scal = a.scal;
+    int* ictl = a.ictl;
+    const int N = a.L0.N;
+    const int c0 = bi * NT + tid, cs = nb * NT;
+
+    // mean of b (unless the right-hand side's kernel left it)
+    if (!a.mean_ready) {
+        double acc = 0.0;
+        for (int t = c0; t < N; t += cs) acc += a.b[t];
+        acc = block_sum<NT>(acc, red);
+        if (tid == 0) P0[bi] = acc;
+        if (!barrier(a, [&] {
+                const double S = sum_parts_cg<NT>(P0, nb, red);
+                if (tid == 0) scal[PS_MEANB] = S / (double)N;
+            }))
+            return;
+    }
+    // r = -(b - mean b) - A x; ||f||^2, ||r||^2, sum r; the control words
+    {
+        double ff = 0.0, rr = 0.0, sr = 0.0;
+        init_cells<2>(a.L0, a.b, a.x, a.r, a.r32, __ldcg(scal + PS_MEANB), c0, cs, ff, rr, sr);
+        block_sum2_t<NT, double>(ff, rr, red);
+        sr = block_sum<NT>(sr, red);
+        if (tid == 0) {
+            P0[bi] = ff;
+            P1[bi] = rr;
+            P2[bi] = sr;
+        }
+        if (!barrier(a, [&] {
+                double FF, RR;
+                sum_parts2_cg<NT>(P0, P1, nb, red, &FF, &RR);
+                const double SR = sum_parts_cg<NT>(P2, nb, red);
+                if (tid == 0) {
+                    scal[PS_FF] = FF;
+                    scal[PS_RR] = RR;
+                    scal[PS_MEANR] = SR / (double)N;
+                    scal[PS_RZ] = 0.0;
+                    scal[PS_BETA] = 0.0;
+                    scal[PS_ITERS] = 0.0;
+                    ictl[PI_IT] = 0;
+                    ictl[PI_TOTAL] = 0;
+                    ictl[PI_NOCONV] = 0;
+                    const int zero = !(FF > 0.0);
+                    ictl[PI_ZERO] = zero;
+                    int done = zero || (RR <= a.rtol * a.rtol * FF);
+                    scal[PS_RELRES] = zero ? 0.0 : sqrt(RR / FF);
+                    if (!(RR == RR)) {
+                        done = 1;
+                        ictl[PI_NOCONV] = 1;
+                    }
+                    ictl[PI_DONE] = done;
+                }
+            }))
+            return;
+    }
+    for (;;) {
+        if (__ldcg(ictl + PI_DONE)) break;
+        const int it = __ldcg(ictl + PI_IT);
+        const float mr = (float)__ldcg(scal + PS_MEANR);
+        // down sweeps of levels 0 .. top-1
+        for (int l = 0; l < a.top; ++l) {
+            const int nt = a.dtx[l] * a.dty[l];
+            for (int t = bi; t < nt; t += nb) {
+                const int tx = t % a.dtx[l], ty = t / a.dtx[l];
+                if (l == 0)
+                    down_tile<float, float, 2>(a.lev[0], a.lev[1], a.r32, a.u0pre, a.f[1], mr, tx, ty, sf, su, srow);
+                else
+                    down_tile<float, float, 2>(a.lev[l], a.lev[l + 1], a.f[l], a.upre[l], a.f[l + 1], 0.0f, tx, ty,
+                                               sf, su, srow);
+            }
+            if (!barrier(a, no_fin)) return;
+        }
+        // the top level, exactly
+        if (bi == 0)
+            fdm_block(a.lev[a.top].n[0], a.lev[a.top].n[1], a.fdm_tab, a.f[a.top], a.upost[a.top],
+                      reinterpret_cast<float*>(smraw));
+        if (!barrier(a, no_fin)) return;
+        // up sweeps of levels top-1 .. 1
+        for (int l = a.top - 1; l >= 1; --l) {
+            const int nt = a.utx[l] * a.uty[l];
+            float rz = 0.0f, sz = 0.0f;
+            for (int t = bi; t < nt; t += nb) {
+                const int tx = t % a.utx[l], ty = t / a.utx[l];
+                up_tile<float, float, false, 2>(a.lev[l], a.lev[l + 1], a.upre[l], a.f[l], a.upost[l + 1],
+                                                a.upost[l], 0.0f, tx, ty, sf, su, srow, rz, sz);
+            }
+            if (!barrier(a, no_fin)) return;
+        }
+        // the fine level's up sweep with r.z and sum z
+        {
+            const int nt = a.utx[0] * a.uty[0];
+            float rz = 0.0f, sz = 0.0f;
+            for (int t = bi; t < nt; t += nb) {
+                const int tx = t % a.utx[0], ty = t / a.utx[0];
+                up_tile<float, float, true, 2>(a.lev[0], a.lev[1], a.u0pre, a.r32, a.upost[1], a.z, mr, tx, ty, sf,
+                                               su, srow, rz, sz);
+            }
+            double brz, bsz;
+            block_sum2_any<NT>(rz, sz, red, redf, &brz, &bsz);
+            if (tid == 0) {
+                P0[bi] = brz;
+                P1[bi] = bsz;
+            }
+            if (!barrier(a, [&] {
+                    double RZ, SZ;
+                    sum_parts2_cg<NT>(P0, P1, nb, red, &RZ, &SZ);
+                    if (tid == 0) {
+                        scal[PS_BETA] = (it == 0) ? 0.0 : RZ / __ldcg(scal + PS_RZ);
+                        scal[PS_RZ] = RZ;
+                        scal[PS_MEANZ] = SZ / (double)N;
+                    }
+                }))
+                return;
+        }
+        // p = (z - mean z) + beta p_old, q = A p, p.q
+        {
+            const float beta = (float)__ldcg(scal + PS_BETA), mz = (float)__ldcg(scal + PS_MEANZ);
+            const int nt = a.ptx * a.pty;
+            float acc = 0.0f;
+            for (int t = bi; t < nt; t += nb) {
+                const int tx = t % a.ptx, ty = t / a.ptx;
+                pq_tile<float, float>(a.lev[0], a.z, a.p0, a.p1, a.q, it, beta, mz, tx, ty, sf, acc);
+            }
+            const double bacc = block_sum_any<NT>(acc, red, redf);
+            if (tid == 0) P0[bi] = bacc;
+            if (!barrier(a, [&] {
+                    const double PQ = sum_parts_cg<NT>(P0, nb, red);
+                    if (tid == 0) scal[PS_ALPHA] = __ldcg(scal + PS_RZ) / PQ;
+                }))
+                return;
+        }
+        // reliable update: x += e, r64 -= A e (e = alpha p), r32 = r64; the stopping test
+        {
+            const float alpha = (float)__ldcg(scal + PS_ALPHA);
+            const float* p = (it & 1) ? a.p1 : a.p0;
+            double rr = 0.0, sr = 0.0;
+            // each block a contiguous chunk of the cells (quads), so every SM works
+            const int nu = a.vec4 ? (N >> 2) : N, chunk = (nu + nb - 1) / nb;
+            ir_cells<2>(a.L0, a.x, a.r, p, a.r32, alpha, a.vec4, bi * chunk + tid, NT, (bi + 1) * chunk, rr, sr);
+            block_sum2_t<NT, double>(rr, sr, red);
+            if (tid == 0) {
+                P0[bi] = rr;
+                P1[bi] = sr;
+            }
+            if (!barrier(a, [&] {
+                    double RR, SR;
+                    sum_parts2_cg<NT>(P0, P1, nb, red, &RR, &SR);
+                    if (tid == 0) {
+                        scal[PS_MEANR] = SR / (double)N;
+                        const int tot = __ldcg(ictl + PI_TOTAL) + 1;
+                        ictl[PI_IT] = it + 1;
+                        ictl[PI_TOTAL] = tot;
+                        scal[PS_ITERS] = (double)tot;
+                        const double ff = __ldcg(scal + PS_FF);
+                        const int conv = (RR <= a.rtol * a.rtol * ff);
+                        const int bad = !(RR == RR) || !(RR < 1e300);
+                        const int done = conv || bad || (tot >= a.max_iter);
+                        scal[PS_RR] = RR;
+                        scal[PS_RELRES] = sqrt(RR / ff);
+                        ictl[PI_DONE] = done;
+                        if (done && !conv) ictl[PI_NOCONV] = 1;
+                    }
+                }))
+                return;
+        }
+    }
+}
+
+}  // namespace kp
 
 // ---------------------------------------------------------------------------
 // 3D kernels, z-marching ("2.5D"): a block owns a 32-column x 32-row box in
@@ -2739,6 +3135,41 @@ bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const dou
         pl->fdm_smem = sizeof(float) * (size_t)((dim == 3) ? k3::fdm3_smem_floats(nx, ny, nz)
                                                              : k2::fdm_smem_floats(nx, ny));
     }
+    // persistent solve: one 2D system in refinement mode with the fast-diagonalisation
+    // top level, on request (LOWMACH_PERSIST=1).  Measured on GB300 it is slower
+    // than the chain of level kernels: a grid barrier costs 1.8 us, 3.7 us with a
+    // reduction finished by the last block (the L2 round trips of the release and
+    // acquire), against about 1 us per programmatically dependent launch, so the
+    // 256 x 512 step took 1.19 ms against 1.03 ms.
+    pl->persist = 0;
+    pl->persist_grid = 0;
+    {
+        const char* pe = std::getenv("LOWMACH_PERSIST");
+        const bool on = pe && pe[0] == '1';
+        if (on && dim == 2 && nb == 1 && refine_mode && pl->fdm && pl->sweeps == 2 && pl->top >= 1 &&
+            pl->top < kp::kLev) {
+            int dev = 0, nsm = 0, coop = 0, per = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+            cudaFuncSetAttribute(kp::k_solve2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->fdm_smem);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kp::k_solve2, k2::NT, pl->fdm_smem) !=
+                cudaSuccess)
+                per = 0;
+            cudaGetLastError();
+            long long g = (long long)per * nsm;
+            if (g > 2LL * nsm) g = 2LL * nsm;
+            if (const char* e = std::getenv("LOWMACH_PERSIST_GRID")) {
+                const long long v = std::atoll(e);
+                if (v >= 1 && v < g) g = v;
+            }
+            if (g > pl->npart / 3) g = pl->npart / 3;
+            if (coop && g >= 1) {
+                pl->persist = 1;
+                pl->persist_grid = (int)g;
+            }
+        }
+    }
     // tail shared-memory offsets (elements of T)
     {
         int off = 0;
@@ -3194,7 +3625,81 @@ cudaError_t poisson_enqueue_batch_report(PoissonPlan* pl, double* const* rep, in
     return cudaGetLastError();
 }
 
+cudaError_t poisson_enqueue_persistent(PoissonPlan* pl, const double* b, double* x, cudaStream_t s, int mean_ready) {
+    if (!pl->persist) return cudaErrorInvalidValue;
+    kp::Args a;
+    std::memset(&a, 0, sizeof(a));
+    for (int l = 0; l <= pl->top; ++l) a.lev[l] = lv_host<float>(pl, l);
+    a.L0 = make_lv<double>(pl->lev[0], 2);
+    a.top = pl->top;
+    constexpr int CD = k2::cd_of(2), FU = k2::fu_of(2);
+    for (int l = 0; l < pl->top; ++l) {
+        a.dtx[l] = (pl->lev[l + 1].n[0] + CD - 1) / CD;
+        a.dty[l] = (pl->lev[l + 1].n[1] + CD - 1) / CD;
+        a.utx[l] = (pl->lev[l].n[0] + FU - 1) / FU;
+        a.uty[l] = (pl->lev[l].n[1] + FU - 1) / FU;
+        if (l >= 1) {
+            a.upre[l] = (float*)pl->lev[l].upre;
+            a.f[l] = (float*)pl->lev[l].f;
+            a.upost[l] = (float*)pl->lev[l].upost;
+        }
+    }
+    a.f[pl->top] = (float*)pl->lev[pl->top].f;
+    a.upost[pl->top] = (float*)pl->lev[pl->top].upost;
+    a.ptx = (pl->lev[0].n[0] + k2::FP - 1) / k2::FP;
+    a.pty = (pl->lev[0].n[1] + k2::FP - 1) / k2::FP;
+    a.b = b;
+    a.x = x;
+    a.r = pl->r;
+    a.r32 = pl->r32;
+    a.u0pre = (float*)pl->u0pre;
+    a.z = (float*)pl->z;
+    a.p0 = pl->p32[0];
+    a.p1 = pl->p32[1];
+    a.q = pl->q32;
+    a.fdm_tab = pl->fdm_tab;
+    a.part = pl->part0;
+    a.scal = pl->scal;
+    a.ictl = pl->ictl;
+    a.bar = reinterpret_cast<unsigned*>(pl->part2);   // unused by the persistent solve
+    a.rtol = pl->rtol;
+    a.max_iter = pl->max_iter;
+    a.vec4 = (pl->lev[0].n[0] % 4 == 0) && (((uintptr_t)x & 15) == 0);
+    a.mean_ready = mean_ready;
+    a.arrivals = (unsigned)pl->persist_grid;
+    a.spin = kp::kSpin;
+    if (const char* e = std::getenv("LOWMACH_PERSIST_TEST_TIMEOUT")) {
+        // failure injection for the tests: a barrier that waits for one block
+        // more than the grid has, with a short poll limit
+        if (e[0] == '1') {
+            a.arrivals = (unsigned)pl->persist_grid + 1u;
+            a.spin = 1u << 14;
+        }
+    }
+    cudaError_t e = cudaMemsetAsync(pl->part2, 0, kp::BAR_WORDS * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)pl->persist_grid);
+    cfg.blockDim = dim3(k2::NT);
+    cfg.dynamicSmemBytes = pl->fdm_smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kp::k_solve2, a);
+    pl->launches += 1;
+    return e;
+}
+
 cudaError_t poisson_solve_host_loop(PoissonPlan* pl, const double* b, double* x, cudaStream_t s) {
+    if (pl->persist) {
+        cudaError_t e = poisson_enqueue_persistent(pl, b, x, s, 0);
+        if (e != cudaSuccess) return e;
+        return poisson_enqueue_epilogue(pl, x, s, nullptr, nullptr, 0, 1);
+    }
     const PdlScope pdl(pl);
     cudaError_t e = poisson_enqueue_prologue(pl, b, x, s, 0ULL, 0);
     if (e != cudaSuccess) return e;

@@ -60,7 +60,7 @@ enum : int {
 // PI_IT: CG iterations of the solve (its parity selects the search-direction
 // buffer); PI_TOTAL: the same count for the iteration cap.
 enum : int { PI_IT = 0, PI_DONE = 1, PI_NOCONV = 2, PI_ZERO = 3, PI_TOTAL = 5, PI_NINT = 8 };
-constexpr int kNumCounters = 8;          // last-block counters (one per reducing kernel kind)
+constexpr int kNumCounters = 12;         // last-block counters (one per reducing kernel kind), barrier words
 
 struct PoissonPlan {
     int dim;
@@ -118,6 +118,12 @@ struct PoissonPlan {
     int nb;
     int* bdone;
     int prefix;           // CG iterations a graph solve captures ahead of its while node
+    // Persistent solve (one 2D system, FP32 multigrid with reliable updates,
+    // fast-diagonalisation top level): the whole solve in one cooperative
+    // launch of persist_grid blocks (all resident), phases separated by grid
+    // barriers instead of kernel boundaries.
+    int persist;
+    int persist_grid;
     int pdl;              // 1: the solver's kernels launch with programmatic dependent launch
 };
 
@@ -187,6 +193,10 @@ cudaError_t poisson_enqueue_remove_mean(PoissonPlan* pl, double* x, cudaStream_t
 // 3 = coarse-level tail.
 cudaError_t poisson_launch_single(PoissonPlan* pl, int which, cudaStream_t s);
 // Host-driven complete solve (prologue, body until done, epilogue).
+// The whole solve of a persistent plan (pl->persist) in one cooperative launch
+// (after a reset of its barrier words); mean_ready as for the prologue.  The
+// epilogue is enqueued separately.
+cudaError_t poisson_enqueue_persistent(PoissonPlan* pl, const double* b, double* x, cudaStream_t s, int mean_ready);
 cudaError_t poisson_solve_host_loop(PoissonPlan* pl, const double* b, double* x, cudaStream_t s);
 
 }  // namespace lm

@@ -522,7 +522,12 @@ cudaError_t enqueue_poisson(sim_t* s, cudaStream_t st, bool graph, int iter_slot
         const sim_status ss = launch_solve_graph(s, iter_slot == SC_ITERS_PRED ? 0 : 1, st);
         return ss == SIM_OK ? cudaGetLastError() : cudaErrorUnknown;
     }
-    if (!graph) {
+    if (pl->persist) {
+        // the whole solve in one cooperative launch (graph and eager alike)
+        *body_launch = 0;
+        e = poisson_enqueue_persistent(pl, s->b, s->P, st, 1);
+        if (e != cudaSuccess) return e;
+    } else if (!graph) {
         e = poisson_enqueue_prologue(pl, s->b, s->P, st, 0ULL, 1);
         if (e != cudaSuccess) return e;
         int done = 0;

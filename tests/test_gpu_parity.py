@@ -413,6 +413,62 @@ def test_predictor_corrector_difference_matches_table2():
 # ---------------------------------------------------------------------------
 # Execution paths and error handling
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# Persistent 2D solve (one cooperative launch per pressure solve; opt-in,
+# LOWMACH_PERSIST=1)
+# ---------------------------------------------------------------------------
+def _mixed_slot(nx, ny, steps, env, monkeypatch):
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    prm, geo, f = W.slot_burner(nx, ny)
+    prm["precision"] = W.MIXED
+    prm["poisson_rtol"] = 1e-12
+    sim = gpu_run(prm, geo, f, steps)
+    out = {k: sim.get(k) for k in ("U", "V", "Z", "RHO", "P")}
+    its = (sim.query(4), sim.query(5))
+    sim.close()
+    for k in env:
+        monkeypatch.delenv(k)
+    return out, its
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 128), (256, 512), (96, 192)])
+def test_persistent_solve_matches_the_kernel_chain(nx, ny, monkeypatch):
+    """The persistent solve and the chain of level kernels run the same
+    iteration; only the order of the block partial sums differs, so the fields
+    agree to the solver tolerance and the iteration counts to one."""
+    a, ia = _mixed_slot(nx, ny, 12, {"LOWMACH_PERSIST": "1"}, monkeypatch)
+    b, ib = _mixed_slot(nx, ny, 12, {}, monkeypatch)
+    for k in a:
+        assert rel(a[k], b[k]) < 1e-9, (k, rel(a[k], b[k]))
+    assert abs(ia[0] - ib[0]) <= 1 and abs(ia[1] - ib[1]) <= 1, (ia, ib)
+
+
+def test_persistent_solve_graph_and_eager_agree_bitwise(monkeypatch):
+    a, _ = _mixed_slot(64, 128, 9, {"LOWMACH_PERSIST": "1"}, monkeypatch)
+    b, _ = _mixed_slot(64, 128, 9, {"LOWMACH_PERSIST": "1", "LOWMACH_NO_GRAPH": "1"}, monkeypatch)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_persistent_solve_barrier_timeout_is_reported(monkeypatch):
+    """A barrier that waits for one block more than the grid has gives up
+    after its poll limit: every block leaves, the step reports
+    non-convergence, and the context stays usable for the next simulation."""
+    from paper_2603_01727_gb300.lowmach import SimError, SIM_ENOCONV
+    monkeypatch.setenv("LOWMACH_PERSIST", "1")
+    monkeypatch.setenv("LOWMACH_PERSIST_TEST_TIMEOUT", "1")
+    prm, geo, f = W.slot_burner(64, 128)
+    prm["precision"] = W.MIXED
+    with pytest.raises(SimError) as e:
+        gpu_run(prm, geo, f, 1)
+    assert e.value.status == SIM_ENOCONV
+    monkeypatch.delenv("LOWMACH_PERSIST_TEST_TIMEOUT")
+    sim = gpu_run(prm, geo, f, 2)
+    assert sim.query(7) <= 1e-10
+    sim.close()
+
+
 def test_graph_and_eager_paths_agree_bitwise(monkeypatch):
     prm, geo, f = W.slot_burner(32, 64)
     sim_g = gpu_run(prm, geo, f, 9)
