@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -707,7 +708,7 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
         launch_project(g, s->ph, pa, st, L);
         if (D == 3) ghost_v(s, s->vs, st, L);
         // P* kept for the predictor-corrector difference (per-step checks)
-        e = cudaMemcpyAsync(s->Pstar, s->P, sizeof(double) * (size_t)g.ncell, cudaMemcpyDeviceToDevice, st);
+        e = stage_copy(s->P, s->Pstar, g.ncell, st);
         if (e != cudaSuccess) return e;
     }
     if (on(SEC_MID) && s->adj_save) {
@@ -2100,6 +2101,16 @@ struct sim_batch {
     bool gvalid[6];
     std::vector<BatchGroup> groups;
     std::vector<int> group_of;   // member -> group, or -1 (own solves)
+    // Member-batched stage kernels: the grouped members (2D, open systems)
+    // run each stage kernel as one launch over all of them; per phase, the
+    // records of every launch position and their work lists (device).
+    std::vector<int> staged;     // members whose stage kernels are batched
+    StageRec* stab;              // [6 phases][kStagePos][staged] records
+    int* swork;                  // [6 phases][kStagePos][staged + 1] block starts
+    int stage_launches[6];       // batched launches of a phase's graph
+    int last_phase;
+    std::vector<int> stage_blocks;   // host copy of the last tables' block starts
+    std::vector<int> stage_kinds;    // kind of each launch position
     char err[512];
 };
 
@@ -2131,6 +2142,32 @@ std::vector<std::vector<int>> batch_groups(sim_t* const* sims, int n) {
         if (g.size() >= 2) out.push_back(g);
     }
     return out;
+}
+
+constexpr int kStagePos = 16;   // launch positions of one step's stage kernels (at most)
+
+// Members whose stage kernels can run as batched launches: every member that
+// is in a solve group, when all of them are 2D open systems (their stage is
+// the stencil, the fused state relation and fluxes, the right-hand side and
+// the projection); LOWMACH_NO_STAGE_BATCH=1 keeps one launch per member.
+std::vector<int> staged_members(sim_t* const* sims, int n, const std::vector<std::vector<int>>& groups) {
+    std::vector<int> out;
+    const char* e = std::getenv("LOWMACH_NO_STAGE_BATCH");
+    if (e && e[0] == '1') return out;
+    for (const auto& g : groups)
+        for (int k : g) {
+            if (sims[k]->g.dim != 2 || sims[k]->ph.closed || sims[k]->ph.mixed != sims[groups[0][0]]->ph.mixed)
+                return std::vector<int>();
+            out.push_back(k);
+        }
+    std::sort(out.begin(), out.end());
+    return out;
+}
+
+size_t stage_table_bytes(int nstaged) {
+    if (nstaged == 0) return 0;
+    return a256(sizeof(StageRec) * (size_t)6 * kStagePos * nstaged) +
+           a256(sizeof(int) * (size_t)6 * kStagePos * (nstaged + 1));
 }
 
 // Workspace bytes of one group (plan, contiguous b and x, pointer tables).
@@ -2187,9 +2224,66 @@ cudaError_t batch_group_solve(BatchGroup& G, int which) {
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// Records of the staged members' stage kernels for one phase: each member's
+// sections are enqueued with a collector installed (nothing is launched), the
+// records of each launch position are stored side by side with the position's
+// work list (block starts), and both go to the phase's device tables.
+sim_status batch_stage_tables(sim_batch_t* b, int phase, int npos[3]) {
+    const int secs[3][2] = {{SEC_PRED, SEC_PRED}, {SEC_MID, SEC_MID}, {SEC_END, SEC_END}};
+    const int ns = (int)b->staged.size();
+    std::vector<StageRec> all((size_t)kStagePos * ns);
+    std::vector<int> starts((size_t)kStagePos * (ns + 1), 0);
+    std::vector<StageRec> buf(kStagePos);
+    int base = 0;
+    for (int k = 0; k < 3; ++k) {
+        npos[k] = 0;
+        for (int j = 0; j < ns; ++j) {
+            sim_t* s = b->sims[(size_t)b->staged[(size_t)j]];
+            StageCollector col{buf.data(), 0, kStagePos - base, false};
+            set_stage_collector(&col);
+            int L = 0, body = 0;
+            const cudaError_t e = enqueue_step_sections(s, s->nstep, s->cap, true, &L, &body, secs[k][0], secs[k][1]);
+            set_stage_collector(nullptr);
+            if (e != cudaSuccess) return bfail(b, SIM_ECUDA, "stage records: %s", cudaGetErrorString(e));
+            if (col.overflow) return bfail(b, SIM_EINVAL, "stage records: more than %d launches", kStagePos);
+            if (j == 0) npos[k] = col.n;
+            if (col.n != npos[k]) return bfail(b, SIM_EINVAL, "stage records differ between members");
+            for (int i = 0; i < col.n; ++i) {
+                if (j > 0 && buf[(size_t)i].kind != all[(size_t)(base + i) * ns].kind)
+                    return bfail(b, SIM_EINVAL, "stage records differ between members");
+                all[(size_t)(base + i) * ns + j] = buf[(size_t)i];
+            }
+        }
+        for (int i = 0; i < npos[k]; ++i) {
+            int* st = starts.data() + (size_t)(base + i) * (ns + 1);
+            for (int j = 0; j < ns; ++j) st[j + 1] = st[j] + all[(size_t)(base + i) * ns + j].nblocks;
+        }
+        base += npos[k];
+    }
+    StageRec* dtab = b->stab + (size_t)phase * kStagePos * ns;
+    int* dwork = b->swork + (size_t)phase * kStagePos * (ns + 1);
+    BCK(cudaMemcpy(dtab, all.data(), sizeof(StageRec) * (size_t)base * ns, cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(dwork, starts.data(), sizeof(int) * (size_t)base * (ns + 1), cudaMemcpyHostToDevice));
+    b->stage_blocks.assign(starts.begin(), starts.end());
+    b->stage_kinds.assign((size_t)base, 0);
+    for (int i = 0; i < base; ++i) b->stage_kinds[(size_t)i] = all[(size_t)i * ns].kind;
+    return SIM_OK;
+}
+
 // The batch step as one graph: per-member sections on forked streams, joined
 // before and after each stage's batched solves (one forked stream per group).
+// The staged members' stage kernels run as member-batched launches on the
+// capture stream, alongside the other members' sections.
 sim_status batch_capture(sim_batch_t* b, int phase) {
+    const int ns = (int)b->staged.size();
+    int npos[3] = {0, 0, 0};
+    if (ns > 0) {
+        const sim_status st = batch_stage_tables(b, phase, npos);
+        if (st != SIM_OK) return st;
+    }
+    std::vector<char> staged(b->sims.size(), 0);
+    for (int k : b->staged) staged[(size_t)k] = 1;
+    const int mixed = ns > 0 ? b->sims[(size_t)b->staged[0]]->ph.mixed : 0;
     BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
     cudaError_t e = cudaSuccess;
     const int secs[3][2] = {{SEC_PRED, SEC_POIS_PRED}, {SEC_MID, SEC_POIS_CORR}, {SEC_END, SEC_END}};
@@ -2197,9 +2291,12 @@ sim_status batch_capture(sim_batch_t* b, int phase) {
         b->sims[i]->launches_fixed_graph[phase] = 0;
         b->sims[i]->body_launches = 0;
     }
+    b->stage_launches[phase] = 0;
+    int base = 0;
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
         e = cudaEventRecord(b->fork, b->cap);
         for (size_t i = 0; i < b->sims.size() && e == cudaSuccess; ++i) {
+            if (staged[i]) continue;
             sim_t* s = b->sims[i];
             const bool batched = b->group_of[i] >= 0;
             // a batched member leaves its solve to the group
@@ -2212,6 +2309,16 @@ sim_status batch_capture(sim_batch_t* b, int phase) {
             if (e == cudaSuccess) e = cudaEventRecord(b->join[i], s->cap);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[i], 0);
         }
+        // the staged members' stage kernels, one launch per position
+        for (int p = 0; p < npos[k] && e == cudaSuccess; ++p) {
+            const int pos = base + p;
+            const StageRec* recs = b->stab + ((size_t)phase * kStagePos + pos) * ns;
+            const int* work = b->swork + ((size_t)phase * kStagePos + pos) * (ns + 1);
+            const int total = b->stage_blocks[(size_t)pos * (ns + 1) + ns];
+            e = launch_stage_batched(b->stage_kinds[(size_t)pos], 2, mixed, recs, work, ns, total, b->cap);
+            b->stage_launches[phase] += 1;
+        }
+        base += npos[k];
         if (k == 2 || b->groups.empty()) continue;
         if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->cap);
         for (BatchGroup& G : b->groups) {
@@ -2244,11 +2351,13 @@ sim_status sim_batch_workspace_size(sim_t* const* sims, int n, size_t* bytes) {
         if (!sims[i]) return SIM_EINVAL;
     size_t total = 0;
     const char* err = nullptr;
-    for (const auto& g : batch_groups(sims, n)) {
+    const auto groups = batch_groups(sims, n);
+    for (const auto& g : groups) {
         const size_t gb = group_bytes(sims[g[0]], (int)g.size(), &err);
         if (gb == 0) return SIM_EINVAL;
         total += gb;
     }
+    total += stage_table_bytes((int)staged_members(sims, n, groups).size());
     *bytes = total;
     return SIM_OK;
 }
@@ -2336,6 +2445,12 @@ sim_status sim_batch_create(sim_t* const* sims, int n, void* d_workspace, size_t
                 return SIM_ECUDA;
             }
         }
+        b->staged = staged_members(sims, n, batch_groups(sims, n));
+        if (!b->staged.empty()) {
+            const int ns = (int)b->staged.size();
+            b->stab = (StageRec*)cur;
+            b->swork = (int*)(cur + a256(sizeof(StageRec) * (size_t)6 * kStagePos * ns));
+        }
     }
     *out = b;
     return SIM_OK;
@@ -2365,6 +2480,7 @@ sim_status sim_batch_query_launches(sim_batch_t* b, double* out) {
         total += 2.0 * G.fixed_launches +
                  G.body_launches * (poisson_loop_iters(&G.pl, itp) + poisson_loop_iters(&G.pl, itc));
     }
+    total += b->stage_launches[b->last_phase];
     *out = total;
     return SIM_OK;
 }
@@ -2403,6 +2519,7 @@ sim_status sim_batch_step(sim_batch_t* b, int nsteps) {
             if (st != SIM_OK) return st;
         }
         BCK(cudaGraphLaunch(b->gexec[phase], b->stream));
+        b->last_phase = phase;
         for (sim_t* s : b->sims) {
             s->launches_last = -(s->launches_fixed_graph[phase] + 1);
             after_step(s);

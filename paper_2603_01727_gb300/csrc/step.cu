@@ -526,9 +526,10 @@ struct ResidMinBlocks<2, FF> {
     static constexpr int v = 4;
 };
 
+// The stage stencil and combination of the cells of block bx (NT cells).
 template <int DIM, class C>
-__global__ void __launch_bounds__(NT, ResidMinBlocks<DIM, C>::v) k_residual(Geom g, Phys ph, ResidArgs a) {
-    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+__device__ __forceinline__ void residual_body(const Geom& g, const Phys& ph, const ResidArgs& a, int bx) {
+    const long long t = (long long)bx * NT + threadIdx.x;
     if (t >= g.ncell) return;
     const long long c = (DIM == 3) ? pad_index_div64(g, t) : pad_index(g, t);
     const double* Rrd[5];
@@ -583,6 +584,11 @@ __global__ void __launch_bounds__(NT, ResidMinBlocks<DIM, C>::v) k_residual(Geom
     }
 }
 
+template <int DIM, class C>
+__global__ void __launch_bounds__(NT, ResidMinBlocks<DIM, C>::v) k_residual(Geom g, Phys ph, ResidArgs a) {
+    residual_body<DIM, C>(g, ph, a, blockIdx.x);
+}
+
 // ----------------------------------------------------------------------------
 // Interface mass fluxes of the provisional momentum (first term of Eq 3.23) and
 // block partials of the global mass balance (Eq 3.24 + S_m, Eq 3.33).
@@ -607,12 +613,16 @@ __device__ __forceinline__ double flux_cell(const Geom& g, const Phys& ph, const
     int ct[3], q[3];
     interior_coords(g, t, ct);
     padded_coords(g, c, q);
+    // FP64 products and sums explicitly rounded (no contraction), so that the
+    // member-batched launch of this code rounds exactly as the single one
     if (a.correct) {
-        const double drho = (a.bdf_c0 * rho_new_c + a.bdf_c1 * a.rho_n[c] +
-                             (a.bdf_c2 != 0.0 ? a.bdf_c2 * a.rho_prev[c] : 0.0)) * iden;
+        double num = __dadd_rn(__dmul_rn(a.bdf_c0, rho_new_c), __dmul_rn(a.bdf_c1, a.rho_n[c]));
+        if (a.bdf_c2 != 0.0) num = __dadd_rn(num, __dmul_rn(a.bdf_c2, a.rho_prev[c]));
+        const double drho = __dmul_rn(num, iden);
         const double Sm = a.Sm ? a.Sm[c] : 0.0;
-        a.b[t] = drho - Sm;   // completed by k_rhs with the flux divergence
-        acc += (drho - Sm) * g.dV;
+        const double bm = __dsub_rn(drho, Sm);
+        a.b[t] = bm;   // completed by k_rhs with the flux divergence
+        acc = __fma_rn(bm, g.dV, acc);
     }
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
@@ -625,9 +635,10 @@ __device__ __forceinline__ double flux_cell(const Geom& g, const Phys& ph, const
             a.F[j][c] = half_exact(m[cl] + m[c]);
         } else {
             const int kind = bnd.kind[j][0][slab_index(g, j, q)];
-            const double val = (kind == BC_INFLOW) ? rho_in * ph.inflow_v[j] : (kind == BC_OUTFLOW) ? m[c] : 0.0;
+            const double val =
+                (kind == BC_INFLOW) ? __dmul_rn(rho_in, ph.inflow_v[j]) : (kind == BC_OUTFLOW) ? m[c] : 0.0;
             a.F[j][c] = val;
-            acc += -val * dA;
+            acc = __fma_rn(-val, dA, acc);
         }
         if (ct[j] == n - 1) {
             if (g.periodic[j]) {
@@ -635,9 +646,9 @@ __device__ __forceinline__ double flux_cell(const Geom& g, const Phys& ph, const
             } else {
                 const int kind = bnd.kind[j][1][slab_index(g, j, q)];
                 const double val =
-                    (kind == BC_INFLOW) ? rho_in * ph.inflow_v[j] : (kind == BC_OUTFLOW) ? m[c] : 0.0;
+                    (kind == BC_INFLOW) ? __dmul_rn(rho_in, ph.inflow_v[j]) : (kind == BC_OUTFLOW) ? m[c] : 0.0;
                 a.F[j][c + s] = val;
-                acc += val * dA;
+                acc = __fma_rn(val, dA, acc);
             }
         }
     }
@@ -664,39 +675,48 @@ __global__ void k_face_flux(Geom g, Phys ph, Bnd bnd, FluxArgs a) {
 // k_face_flux); the state's sum of 1/T serves only the enclosed system's p0, so
 // the block partials are the mass balance's.
 template <int DIM, bool MIXED>
-__global__ void k_state_flux(Geom g, Phys ph, const double* __restrict__ Z, const double* __restrict__ H,
-                             double* __restrict__ T, double* __restrict__ rho, double* __restrict__ kap,
-                             int* status, double* sc, Bnd bnd, int kap_ghosts, FluxArgs a) {
+__device__ __forceinline__ void state_flux_body(const Geom& g, const Phys& ph, const double* __restrict__ Z,
+                                                const double* __restrict__ H, double* __restrict__ T,
+                                                double* __restrict__ rho, double* __restrict__ kap, int* status,
+                                                double* sc, const Bnd& bnd, int kap_ghosts, const FluxArgs& a,
+                                                int bx, int gx) {
     const GhostJob kj = kappa_job(kap);
     __shared__ double sm[NT / 32];
     const double rho_in = ph.incompressible ? 1.0 : 1.0 / ph.rho_in_T;
     const double iden = 1.0 / a.bdf_den;
     double acc = 0.0;
     int bad = 0;
-    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
+    for (long long t = (long long)bx * NT + threadIdx.x; t < g.ncell; t += (long long)gx * NT) {
         const long long c = pad_index(g, t);
         const double iT = state_cell<MIXED>(g, ph, Z, H, T, rho, kap, bnd, kj, kap_ghosts, c, bad);
         acc += flux_cell<DIM>(g, ph, bnd, a, t, c, iT, rho_in, iden);
     }
     if (bad) atomicOr(status, ST_NAN);
     acc = block_sum<NT>(acc, sm);
-    if (threadIdx.x == 0) a.part[blockIdx.x] = acc;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (threadIdx.x == 0) a.part[bx] = acc;
+    if (bx == 0 && threadIdx.x == 0) {
         sc[a.p0_slot] = 1.0;
         sc[a.p0_slot + SC_INV_OFF] = 1.0;
     }
 }
 
+template <int DIM, bool MIXED>
+__global__ void k_state_flux(Geom g, Phys ph, const double* __restrict__ Z, const double* __restrict__ H,
+                             double* __restrict__ T, double* __restrict__ rho, double* __restrict__ kap,
+                             int* status, double* sc, Bnd bnd, int kap_ghosts, FluxArgs a) {
+    state_flux_body<DIM, MIXED>(g, ph, Z, H, T, rho, kap, status, sc, bnd, kap_ghosts, a, blockIdx.x, gridDim.x);
+}
+
 // Uniform shift of the outflow fluxes closing the mass balance, then
 // b = d_t rho + sum_j delta_1 F_j / delta_1 x_j - S_m  (Eq 3.24 with S_m).
 template <int DIM>
-__global__ void k_rhs(Geom g, Bnd bnd, FluxArgs a, int np) {
+__device__ __forceinline__ void rhs_body(const Geom& g, const Bnd& bnd, const FluxArgs& a, int np, int bx, int gx) {
     __shared__ double sm[NT / 32];
     const double total = sum_partials<NT>(a.part, np, sm);
     const double area = a.sc[SC_OUT_AREA];
     const double shift = (area > 0.0) ? -total / area : 0.0;
     double bsum = 0.0;
-    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
+    for (long long t = (long long)bx * NT + threadIdx.x; t < g.ncell; t += (long long)gx * NT) {
         const long long c = pad_index(g, t);
         int ct[3], q[3];
         interior_coords(g, t, ct);
@@ -706,11 +726,12 @@ __global__ void k_rhs(Geom g, Bnd bnd, FluxArgs a, int np) {
         for (int j = 0; j < DIM; ++j) {
             const long long s = g.s[j];
             if (!g.periodic[j]) {
-                if (ct[j] == 0 && bnd.kind[j][0][slab_index(g, j, q)] == BC_OUTFLOW) a.F[j][c] = a.F[j][c] - shift;
+                if (ct[j] == 0 && bnd.kind[j][0][slab_index(g, j, q)] == BC_OUTFLOW)
+                    a.F[j][c] = __dsub_rn(a.F[j][c], shift);
                 if (ct[j] == g.n[j] - 1 && bnd.kind[j][1][slab_index(g, j, q)] == BC_OUTFLOW)
-                    a.F[j][c + s] = a.F[j][c + s] + shift;
+                    a.F[j][c + s] = __dadd_rn(a.F[j][c + s], shift);
             }
-            b = b + (a.F[j][c + s] - a.F[j][c]) * g.ih[j];
+            b = __fma_rn(__dsub_rn(a.F[j][c + s], a.F[j][c]), g.ih[j], b);
         }
         a.b[t] = b;
         bsum += b;
@@ -719,10 +740,10 @@ __global__ void k_rhs(Geom g, Bnd bnd, FluxArgs a, int np) {
         // mean(b) for the pressure solve, with the block decomposition and the
         // fixed-order sums of the solver's own mean pass (bitwise the same)
         bsum = block_sum<NT>(bsum, sm);
-        if (threadIdx.x == 0) a.mb_part[blockIdx.x] = bsum;
-        if (arrive_last_n(a.mb_cnt, gridDim.x)) {
+        if (threadIdx.x == 0) a.mb_part[bx] = bsum;
+        if (arrive_last_n(a.mb_cnt, gx)) {
             double v = 0.0;
-            for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) v += __ldcg(a.mb_part + i);
+            for (int i = threadIdx.x; i < gx; i += NT) v += __ldcg(a.mb_part + i);
             v = block_sum<NT>(v, sm);
             if (threadIdx.x == 0) {
                 *a.mb_out = v / (double)g.ncell;
@@ -730,6 +751,11 @@ __global__ void k_rhs(Geom g, Bnd bnd, FluxArgs a, int np) {
             }
         }
     }
+}
+
+template <int DIM>
+__global__ void k_rhs(Geom g, Bnd bnd, FluxArgs a, int np) {
+    rhs_body<DIM>(g, bnd, a, np, blockIdx.x, gridDim.x);
 }
 
 // ----------------------------------------------------------------------------
@@ -748,15 +774,16 @@ __device__ __forceinline__ void rotate_p0(double* sc) {
 }
 
 template <int DIM>
-__global__ void k_project(Geom g, Phys ph, ProjArgs a) {
+__device__ __forceinline__ void project_body(const Geom& g, const Phys& ph, const ProjArgs& a, int bx) {
     double vout[3];
-    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+    const long long t = (long long)bx * NT + threadIdx.x;
     if (t >= g.ncell) return;
     const long long c = pad_index(g, t);
     int ct[3];
     interior_coords(g, t, ct);
+    // FP64 products and sums explicitly rounded (no contraction; see flux_cell)
     const double Pc = a.P[t];
-    const double irho = a.T[c] * a.sc[a.p0_slot + SC_INV_OFF];   // 1/rho = T / p0 (Eq 2.49)
+    const double irho = __dmul_rn(a.T[c], a.sc[a.p0_slot + SC_INV_OFF]);   // 1/rho = T / p0 (Eq 2.49)
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
         const long long s = g.s[j];
@@ -766,13 +793,13 @@ __global__ void k_project(Geom g, Phys ph, ProjArgs a) {
         double Pm, Pp;
         if (ct[j] > 0) Pm = a.P[t - st];
         else if (g.periodic[j]) Pm = a.P[t + (long long)(n - 1) * st];
-        else Pm = a.eA * Pc + a.eB * a.P[t + st] + a.eC * a.P[t + 2 * st];
+        else Pm = __fma_rn(a.eC, a.P[t + 2 * st], __fma_rn(a.eB, a.P[t + st], __dmul_rn(a.eA, Pc)));
         if (ct[j] < n - 1) Pp = a.P[t + st];
         else if (g.periodic[j]) Pp = a.P[t - (long long)(n - 1) * st];
-        else Pp = a.eA * Pc + a.eB * a.P[t - st] + a.eC * a.P[t - 2 * st];
-        if (ct[j] > 0 || g.periodic[j]) a.F[j][c] = a.F[j][c] - (Pc - Pm) * ih;
-        if (ct[j] == n - 1 && g.periodic[j]) a.F[j][c + s] = a.F[j][c + s] - (Pp - Pc) * ih;
-        vout[j] = (a.mom[j][c] - (Pp - Pm) * (0.5 * ih)) * irho;
+        else Pp = __fma_rn(a.eC, a.P[t - 2 * st], __fma_rn(a.eB, a.P[t - st], __dmul_rn(a.eA, Pc)));
+        if (ct[j] > 0 || g.periodic[j]) a.F[j][c] = __fma_rn(-__dsub_rn(Pc, Pm), ih, a.F[j][c]);
+        if (ct[j] == n - 1 && g.periodic[j]) a.F[j][c + s] = __fma_rn(-__dsub_rn(Pp, Pc), ih, a.F[j][c + s]);
+        vout[j] = __dmul_rn(__fma_rn(-__dsub_rn(Pp, Pm), __dmul_rn(0.5, ih), a.mom[j][c]), irho);
         a.v[j][c] = vout[j];
     }
     if (a.gj.nf) {   // fused ghost fill of v
@@ -783,6 +810,11 @@ __global__ void k_project(Geom g, Phys ph, ProjArgs a) {
     // the step's last projection rotates the p0 history (it reads only the new
     // p0, which the rotation leaves as it is)
     if (a.rot && t == 0) rotate_p0(a.rot);
+}
+
+template <int DIM>
+__global__ void k_project(Geom g, Phys ph, ProjArgs a) {
+    project_body<DIM>(g, ph, a, blockIdx.x);
 }
 
 __global__ void k_momentum(Geom g, const double* __restrict__ rho, const double* v0, const double* v1,
@@ -1751,7 +1783,139 @@ __global__ void k_profile_spread(Geom g, IbmDev b, const double* __restrict__ co
     grad[k] = acc;
 }
 
+// ----------------------------------------------------------------------------
+// Member-batched stage kernels: block b of the launch belongs to the member m
+// with start[m] <= b < start[m+1] (binary search over the work list), as its
+// member-local block b - start[m]; the member's record is staged in shared
+// memory, then the stage body runs exactly as in the member's own launch.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int member_of_block(const int* __restrict__ start, int nm, int b) {
+    int lo = 0, hi = nm - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Copy of the record into shared memory (8-byte words), then a barrier.
+__device__ __forceinline__ int stage_rec(const StageRec* __restrict__ recs, const int* __restrict__ start, int nm,
+                                         StageRec* srec) {
+    __shared__ int s_m;
+    if (threadIdx.x == 0) s_m = member_of_block(start, nm, blockIdx.x);
+    __syncthreads();
+    const int m = s_m;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(recs + m);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(srec);
+    for (int i = threadIdx.x; i < (int)(sizeof(StageRec) / 8); i += NT) dst[i] = src[i];
+    __syncthreads();
+    return blockIdx.x - start[m];
+}
+
+template <int DIM, class C>
+__global__ void __launch_bounds__(NT, ResidMinBlocks<DIM, C>::v)
+    k_residual_b(const StageRec* __restrict__ recs, const int* __restrict__ start, int nm) {
+    __shared__ __align__(16) StageRec r;
+    const int bx = stage_rec(recs, start, nm, &r);
+    residual_body<DIM, C>(r.g, r.ph, r.u.r, bx);
+}
+
+template <int DIM, bool MIXED>
+__global__ void k_state_flux_b(const StageRec* __restrict__ recs, const int* __restrict__ start, int nm) {
+    __shared__ __align__(16) StageRec r;
+    const int bx = stage_rec(recs, start, nm, &r);
+    const StageSF& q = r.u.sf;
+    state_flux_body<DIM, MIXED>(r.g, r.ph, q.Z, q.H, q.T, q.rho, q.kap, q.status, q.sc, q.bnd, q.kap_ghosts, q.fa,
+                                bx, r.nblocks);
+}
+
+template <int DIM>
+__global__ void k_rhs_b(const StageRec* __restrict__ recs, const int* __restrict__ start, int nm) {
+    __shared__ __align__(16) StageRec r;
+    const int bx = stage_rec(recs, start, nm, &r);
+    rhs_body<DIM>(r.g, r.u.sf.bnd, r.u.sf.fa, r.np, bx, r.nblocks);
+}
+
+template <int DIM>
+__global__ void k_project_b(const StageRec* __restrict__ recs, const int* __restrict__ start, int nm) {
+    __shared__ __align__(16) StageRec r;
+    const int bx = stage_rec(recs, start, nm, &r);
+    project_body<DIM>(r.g, r.ph, r.u.p, bx);
+}
+
+__global__ void k_copy_b(const StageRec* __restrict__ recs, const int* __restrict__ start, int nm) {
+    __shared__ __align__(16) StageRec r;
+    const int bx = stage_rec(recs, start, nm, &r);
+    const StageCopy& q = r.u.cp;
+    const long long t = (long long)bx * NT + threadIdx.x;
+    if (t < q.n) q.dst[t] = q.src[t];
+}
+
+thread_local StageCollector* t_collect = nullptr;
+
+bool collect(const StageRec& rec) {
+    if (!t_collect) return false;
+    if (t_collect->n < t_collect->cap) t_collect->recs[t_collect->n] = rec;
+    else t_collect->overflow = true;
+    ++t_collect->n;
+    return true;
+}
+
 }  // namespace
+
+void set_stage_collector(StageCollector* c) { t_collect = c; }
+
+cudaError_t stage_copy(const double* src, double* dst, long long n, cudaStream_t s) {
+    if (t_collect) {
+        StageRec r;
+        std::memset(&r, 0, sizeof(r));
+        r.kind = SK_COPY;
+        r.nblocks = blocks_for(n);
+        r.u.cp.src = src;
+        r.u.cp.dst = dst;
+        r.u.cp.n = n;
+        collect(r);
+        return cudaSuccess;
+    }
+    return cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+}
+
+cudaError_t launch_stage_batched(int kind, int dim, int mixed, const StageRec* recs, const int* start, int nm,
+                                 int total_blocks, cudaStream_t s) {
+    const dim3 grid((unsigned)total_blocks);
+    switch (kind) {
+        case SK_RESID:
+            if (dim == 3) {
+                if (mixed) k_residual_b<3, FF><<<grid, NT, 0, s>>>(recs, start, nm);
+                else k_residual_b<3, double><<<grid, NT, 0, s>>>(recs, start, nm);
+            } else {
+                if (mixed) k_residual_b<2, FF><<<grid, NT, 0, s>>>(recs, start, nm);
+                else k_residual_b<2, double><<<grid, NT, 0, s>>>(recs, start, nm);
+            }
+            break;
+        case SK_STATE_FLUX:
+            if (dim == 3) {
+                if (mixed) k_state_flux_b<3, true><<<grid, NT, 0, s>>>(recs, start, nm);
+                else k_state_flux_b<3, false><<<grid, NT, 0, s>>>(recs, start, nm);
+            } else {
+                if (mixed) k_state_flux_b<2, true><<<grid, NT, 0, s>>>(recs, start, nm);
+                else k_state_flux_b<2, false><<<grid, NT, 0, s>>>(recs, start, nm);
+            }
+            break;
+        case SK_RHS:
+            if (dim == 3) k_rhs_b<3><<<grid, NT, 0, s>>>(recs, start, nm);
+            else k_rhs_b<2><<<grid, NT, 0, s>>>(recs, start, nm);
+            break;
+        case SK_PROJECT:
+            if (dim == 3) k_project_b<3><<<grid, NT, 0, s>>>(recs, start, nm);
+            else k_project_b<2><<<grid, NT, 0, s>>>(recs, start, nm);
+            break;
+        default:
+            k_copy_b<<<grid, NT, 0, s>>>(recs, start, nm);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_diagnostics(const Geom& g, const DiagArgs& a, cudaStream_t st) {
     long long nb = (g.ncell + NT - 1) / NT;
@@ -1797,6 +1961,18 @@ void launch_state(const Geom& g, const Phys& ph, const double* Z, const double* 
 
 void launch_residual(const Geom& g, const Phys& ph, const ResidArgs& a, cudaStream_t s, int* launches) {
     const int nb = blocks_for(g.ncell);
+    if (t_collect) {
+        StageRec r;
+        std::memset(&r, 0, sizeof(r));
+        r.g = g;
+        r.ph = ph;
+        r.kind = SK_RESID;
+        r.nblocks = nb;
+        r.u.r = a;
+        collect(r);
+        ++*launches;
+        return;
+    }
     // FP64, or float-float (~48 bits on the FP32 pipes) in the mixed path: the
     // pressure is the dt-scaled divergence of the momentum increment and
     // inherits the stencil's relative rounding directly, which plain FP32
@@ -1832,6 +2008,30 @@ void launch_state_flux_rhs(const Geom& g, const Phys& ph, const double* Z, const
                            cudaStream_t s, int* launches) {
     const int rb = reduce_grid(g);
     const int kg = kap_ghosts ? 1 : 0;
+    if (t_collect) {
+        StageRec r;
+        std::memset(&r, 0, sizeof(r));
+        r.g = g;
+        r.ph = ph;
+        r.kind = SK_STATE_FLUX;
+        r.nblocks = rb;
+        r.np = rb;
+        r.u.sf.Z = Z;
+        r.u.sf.H = H;
+        r.u.sf.T = T;
+        r.u.sf.rho = rho;
+        r.u.sf.kap = kap;
+        r.u.sf.status = status;
+        r.u.sf.sc = sc;
+        r.u.sf.bnd = bnd;
+        r.u.sf.kap_ghosts = kg;
+        r.u.sf.fa = a;
+        collect(r);
+        r.kind = SK_RHS;
+        collect(r);
+        *launches += 2;
+        return;
+    }
     if (g.dim == 3) {
         if (ph.mixed) k_state_flux<3, true><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, status, sc, bnd, kg, a);
         else k_state_flux<3, false><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, status, sc, bnd, kg, a);
@@ -1845,6 +2045,18 @@ void launch_state_flux_rhs(const Geom& g, const Phys& ph, const double* Z, const
 }
 
 void launch_project(const Geom& g, const Phys& ph, const ProjArgs& a, cudaStream_t s, int* launches) {
+    if (t_collect) {
+        StageRec r;
+        std::memset(&r, 0, sizeof(r));
+        r.g = g;
+        r.ph = ph;
+        r.kind = SK_PROJECT;
+        r.nblocks = blocks_for(g.ncell);
+        r.u.p = a;
+        collect(r);
+        ++*launches;
+        return;
+    }
     if (g.dim == 3)
         k_project<3><<<blocks_for(g.ncell), NT, 0, s>>>(g, ph, a);
     else

@@ -214,6 +214,62 @@ void launch_store_sum(const double* part, int np, double scale, double* dst, cud
 void launch_copy_scalar(const double* src, double* dst, int n, cudaStream_t s, int* launches);
 void launch_or_status(const int* src_flag, int bit, int* status, cudaStream_t s, int* launches);
 
+// Member-batched stage kernels (a batch of simulations): one launch of a
+// stage kernel covers every member, whatever its grid.  Each member keeps the
+// block decomposition of its own launch (nblocks blocks); a work list of
+// consecutive block ranges (start[m] .. start[m+1]) maps a block of the batched
+// launch to its member and member-local block, so every member computes
+// exactly what its own launch would (bitwise).  The members' arguments are
+// records in device memory.
+enum StageKind : int { SK_RESID = 0, SK_STATE_FLUX = 1, SK_RHS = 2, SK_PROJECT = 3, SK_COPY = 4 };
+struct StageSF {
+    const double* Z;
+    const double* H;
+    double* T;
+    double* rho;
+    double* kap;
+    int* status;
+    double* sc;
+    Bnd bnd;
+    int kap_ghosts;
+    FluxArgs fa;
+};
+struct StageCopy {
+    const double* src;
+    double* dst;
+    long long n;
+};
+struct StageRec {
+    Geom g;
+    Phys ph;
+    int kind;
+    int nblocks;             // blocks of the member's own launch
+    int np;                  // SK_RHS: partials of the mass balance
+    union {
+        ResidArgs r;
+        StageSF sf;          // SK_STATE_FLUX and SK_RHS (FluxArgs, bnd)
+        ProjArgs p;
+        StageCopy cp;
+    } u;
+};
+// Records collected instead of launched: while a collector is installed on the
+// calling thread, launch_residual, launch_state_flux_rhs, launch_project and
+// stage_copy append their member's record (SK_STATE_FLUX then SK_RHS for the
+// state relation with the right-hand side) and launch nothing.
+struct StageCollector {
+    StageRec* recs;
+    int n, cap;
+    bool overflow;
+};
+void set_stage_collector(StageCollector* c);
+// D2D copy of n doubles as a step element (collected like the kernels).
+cudaError_t stage_copy(const double* src, double* dst, long long n, cudaStream_t s);
+// One batched launch of kind k over nm members: recs[m] (device), start[m]
+// the first block of member m (start[nm] = total blocks, device and host
+// copies), dim and mixed as for the members' own launches.
+cudaError_t launch_stage_batched(int kind, int dim, int mixed, const StageRec* recs, const int* start,
+                                 int nm, int total_blocks, cudaStream_t s);
+
 // Immersed body and boundary kinds (set-up time).
 struct IbmDev {
     int kind;
