@@ -341,7 +341,8 @@ def run_gpu_batch(args, precision, world, rank, local, pg):
         key = tuple(prm["n"][:2])
         if key not in tuned:
             tuned[key], tab = autotune.tune(prm, geo, f, copies=8, device=device)
-            tables["x".join(map(str, key))] = {f"sweeps{a}_tail{b}": round(v, 4) for (a, b), v in tab.items()}
+            tables["x".join(map(str, key))] = {f"sweeps{a}_tail{b}_tile{c}": round(v, 4)
+                                               for (a, b, c), v in tab.items()}
     sims = []
     for prm, geo, f in flames:
         s = LM.Simulation(autotune.apply(prm, tuned[tuple(prm["n"][:2])]), geo, device=device, stream=stream)

@@ -100,6 +100,12 @@ typedef struct {
      * through the iteration count (the stopping test is unchanged). */
     int mg_sweeps;
     int mg_tail_cells;
+    /* Cell tile of a block in the projection kernel: 0 = 256 consecutive
+     * interior cells (x fastest); otherwise the x extent TX of a TX x (256/TX)
+     * tile of cells (x by rows of y, z), TX one of 8, 16, 32, 64, 128, 256.
+     * Results do not depend on it (the kernel is cell-local); it sets the
+     * blocks' reuse of P's neighbours. */
+    int stage_tile_x;
 } sim_params_t;
 
 /* Immersed burner (paper Sec. 3.4; Eqs 3.30-3.33, 4.19-4.21).  The mask is the

@@ -56,6 +56,7 @@ struct Geom {
     int periodic[3];
     DivU32 dn0, dn1; // division by n[0], n[1] (interior index maps)
     DivU32 dp0, dp1; // division by p[0], p[1] (padded index maps)
+    int tile_x;      // projection kernel: x extent of a block's cell tile (0: linear)
 };
 
 // Interior linear index t (x fastest over the interior) -> padded index.
@@ -355,6 +356,29 @@ inline int blocks_for(long long n, int nt = kThreads) {
     long long b = (n + nt - 1) / nt;
     if (b < 1) b = 1;
     return (int)b;
+}
+
+// The projection kernel (one thread per interior cell): blocks of the cell
+// map, linear (kThreads consecutive cells) or tiled (tile_x x kThreads/tile_x
+// cells, x by rows of y and z), and the interior index of a thread (-1 when
+// its tile position lies outside the grid).
+inline int cell_blocks(const Geom& g) {
+    if (g.tile_x <= 0) return blocks_for(g.ncell);
+    const long long rows = (long long)g.n[1] * g.n[2];
+    const int ty = kThreads / g.tile_x;
+    return (int)(((g.n[0] + g.tile_x - 1) / g.tile_x) * ((rows + ty - 1) / ty));
+}
+__device__ __forceinline__ long long cell_of_block(const Geom& g, int bx) {
+    if (g.tile_x <= 0) {
+        const long long t = (long long)bx * kThreads + threadIdx.x;
+        return t < g.ncell ? t : -1;
+    }
+    const int tx = g.tile_x, ty = kThreads / tx;
+    const int ntx = (g.n[0] + tx - 1) / tx;
+    const int i = (bx % ntx) * tx + (int)threadIdx.x % tx;
+    const long long row = (long long)(bx / ntx) * ty + (int)threadIdx.x / tx;
+    if (i >= g.n[0] || row >= (long long)g.n[1] * g.n[2]) return -1;
+    return i + (long long)g.n[0] * row;
 }
 
 // Grid-stride launch bounded by the partial-sum capacity.

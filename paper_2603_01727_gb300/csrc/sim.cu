@@ -162,6 +162,7 @@ Geom make_geom(const sim_params_t* p) {
     g.dn1 = make_divu32((unsigned)g.n[1]);
     g.dp0 = make_divu32((unsigned)g.p[0]);
     g.dp1 = make_divu32((unsigned)g.p[1]);
+    g.tile_x = p->stage_tile_x;
     return g;
 }
 
@@ -241,6 +242,9 @@ const char* validate(const sim_params_t* p) {
     if (p->poisson_max_iter < 1) return "poisson_max_iter must be >= 1";
     if (p->mg_sweeps < 0 || p->mg_sweeps > 2) return "mg_sweeps must be 0 (default), 1 or 2";
     if (p->mg_tail_cells < 0) return "mg_tail_cells must be >= 0";
+    if (p->stage_tile_x != 0 && (p->stage_tile_x < 8 || p->stage_tile_x > 256 ||
+                                 (p->stage_tile_x & (p->stage_tile_x - 1)) != 0))
+        return "stage_tile_x must be 0 or a power of two from 8 to 256";
     if (p->precision != SIM_FP64 && p->precision != SIM_MIXED) return "precision must be SIM_FP64 or SIM_MIXED";
     if (p->closed_system) {
         for (int d = 0; d < p->dim; ++d)

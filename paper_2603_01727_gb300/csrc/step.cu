@@ -529,6 +529,8 @@ struct ResidMinBlocks<2, FF> {
 // The stage stencil and combination of the cells of block bx (NT cells).
 template <int DIM, class C>
 __device__ __forceinline__ void residual_body(const Geom& g, const Phys& ph, const ResidArgs& a, int bx) {
+    // the linear cell map: the tiled one (stage_tile_x) costs the register-capped
+    // float-float stencil spills (96 -> 848 bytes in 3D) and gained nothing
     const long long t = (long long)bx * NT + threadIdx.x;
     if (t >= g.ncell) return;
     const long long c = (DIM == 3) ? pad_index_div64(g, t) : pad_index(g, t);
@@ -776,8 +778,8 @@ __device__ __forceinline__ void rotate_p0(double* sc) {
 template <int DIM>
 __device__ __forceinline__ void project_body(const Geom& g, const Phys& ph, const ProjArgs& a, int bx) {
     double vout[3];
-    const long long t = (long long)bx * NT + threadIdx.x;
-    if (t >= g.ncell) return;
+    const long long t = cell_of_block(g, bx);
+    if (t < 0) return;
     const long long c = pad_index(g, t);
     int ct[3];
     interior_coords(g, t, ct);
@@ -2051,16 +2053,16 @@ void launch_project(const Geom& g, const Phys& ph, const ProjArgs& a, cudaStream
         r.g = g;
         r.ph = ph;
         r.kind = SK_PROJECT;
-        r.nblocks = blocks_for(g.ncell);
+        r.nblocks = cell_blocks(g);
         r.u.p = a;
         collect(r);
         ++*launches;
         return;
     }
     if (g.dim == 3)
-        k_project<3><<<blocks_for(g.ncell), NT, 0, s>>>(g, ph, a);
+        k_project<3><<<cell_blocks(g), NT, 0, s>>>(g, ph, a);
     else
-        k_project<2><<<blocks_for(g.ncell), NT, 0, s>>>(g, ph, a);
+        k_project<2><<<cell_blocks(g), NT, 0, s>>>(g, ph, a);
     ++*launches;
 }
 

@@ -49,7 +49,7 @@ class SimParams(ctypes.Structure):
                 ("incompressible", ctypes.c_int), ("dt", ctypes.c_double),
                 ("precision", ctypes.c_int), ("poisson_rtol", ctypes.c_double),
                 ("poisson_max_iter", ctypes.c_int), ("mg_sweeps", ctypes.c_int),
-                ("mg_tail_cells", ctypes.c_int)]
+                ("mg_tail_cells", ctypes.c_int), ("stage_tile_x", ctypes.c_int)]
 
 
 class SimIbm(ctypes.Structure):
@@ -148,6 +148,7 @@ def params_struct(prm):
         setattr(p, k, int(prm[k]))
     p.mg_sweeps = int(prm.get("mg_sweeps", 0))
     p.mg_tail_cells = int(prm.get("mg_tail_cells", 0))
+    p.stage_tile_x = int(prm.get("stage_tile_x", 0))
     return p
 
 

@@ -469,6 +469,23 @@ def test_persistent_solve_barrier_timeout_is_reported(monkeypatch):
     sim.close()
 
 
+@pytest.mark.parametrize("case,tile", [("slot", 16), ("slot", 64), ("sphere", 32)])
+def test_stage_cell_tiles_change_nothing(case, tile):
+    """The cell tile of the projection only changes which block computes a
+    cell: the fields are bitwise those of the linear map."""
+    if case == "slot":
+        prm, geo, f = W.slot_burner(64, 128)
+    else:
+        prm, geo, f = W.sphere_burner(24)
+    prm["precision"] = W.MIXED
+    a = gpu_run(prm, geo, f, 5)
+    b = gpu_run(dict(prm, stage_tile_x=tile), geo, f, 5)
+    for k in ("U", "V", "Z", "H", "RHO", "P"):
+        assert np.array_equal(a.get(k), b.get(k)), k
+    a.close()
+    b.close()
+
+
 def test_graph_and_eager_paths_agree_bitwise(monkeypatch):
     prm, geo, f = W.slot_burner(32, 64)
     sim_g = gpu_run(prm, geo, f, 9)

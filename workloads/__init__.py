@@ -39,7 +39,8 @@ def _base_params():
         Re=100.0, Pr=0.7, inv_Fr2=0.0, Le_F=1.0, Le_O=1.0, gamma=1.4, sigma=0.7,
         Z_st=0.055, density_ratio=7.0, eps_reg=0.5, tol_reg=1e-3,
         closed_system=0, incompressible=0, dt=0.0,
-        precision=FP64, poisson_rtol=1e-10, poisson_max_iter=200, mg_sweeps=0, mg_tail_cells=0)
+        precision=FP64, poisson_rtol=1e-10, poisson_max_iter=200, mg_sweeps=0, mg_tail_cells=0,
+        stage_tile_x=0)
 
 
 def paper_scalars(Z_st, ratio):
