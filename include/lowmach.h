@@ -58,7 +58,9 @@ enum {
                             shifted uniformly to close the global mass balance
                             (text after Eq 4.22)                                      */
     SIM_BC_WALL = 3,     /* no-slip v = 0, zero-gradient Z, H, zero mass flux        */
-    SIM_BC_SLIP = 4      /* symmetry plane (Eqs 4.22a-b): v_n = 0, zero-gradient rest */
+    SIM_BC_SLIP = 4,     /* symmetry plane (Eqs 4.22a-b): v_n = 0, zero-gradient rest */
+    SIM_BC_WALL_T = 5    /* isothermal no-slip wall (Eq 4.16a-b): v = 0, Dirichlet
+                            Z = inflow_Z and H = wall_H of the side, zero mass flux */
 };
 
 enum { SIM_FP64 = 0, SIM_MIXED = 1 };
@@ -78,6 +80,11 @@ typedef struct {
     double Le_F, Le_O;       /* fuel / oxidiser Lewis numbers (Eq 3.35)                 */
     double gamma;            /* ratio of specific heats (zeta, text after Eq 2.45)      */
     double sigma;            /* transport exponent, kappa = T^sigma (Eq 2.50)           */
+    int transport;           /* 0: kappa = T^sigma; 1: Sutherland's law
+                                kappa = T^(3/2) (1 + C) / (T + C) (Eq 4.12)             */
+    double sutherland_C;     /* C of Sutherland's law (its constant over the
+                                reference temperature, e.g. 110.5 K / 600 K)            */
+    double wall_H[3][2];     /* Dirichlet H of SIM_BC_WALL_T sides [direction][side]   */
     double Z_st;             /* stoichiometric conventional mixture fraction: S = 1/Z_st - 1 */
     double density_ratio;    /* flame / ambient temperature: Q = (ratio - 1)(S + 1)     */
     double eps_reg, tol_reg; /* regularisation: k = ln((1-tol)/tol) / (2 eps) (Eq 3.34)  */

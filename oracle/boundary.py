@@ -10,13 +10,17 @@ Boundary kinds of a domain side:
   WALL      no-slip v = 0 (Eq 3.43), zero-gradient Z, H (Eq 3.44); zero mass flux;
   SLIP      symmetry plane: normal velocity 0 (Eq 3.43), tangential velocity and
             Z, H zero-gradient (Eq 3.44), zero mass flux (Eqs 4.22a-b).
+  WALL_T    isothermal no-slip wall (the heated and cooled walls of Eq 4.16):
+            v = 0, Dirichlet Z = Z_in (the inflow value, air) and H = H_wall of
+            that side (Eq 3.43), so kappa takes the wall state's value; zero
+            mass flux.
 An INFLOW face whose adjacent interior cell is inside the immersed body mask is
 a WALL face (the burner foot closes the inlet under it).
 """
 
 import numpy as np
 
-PERIODIC, INFLOW, OUTFLOW, WALL, SLIP = 0, 1, 2, 3, 4
+PERIODIC, INFLOW, OUTFLOW, WALL, SLIP, WALL_T = 0, 1, 2, 3, 4, 5
 
 
 def _slab(a, g, d, idx):
@@ -35,8 +39,11 @@ def _layers(g, d, side):
 class Boundary:
     """Per-face boundary kinds (a full padded slab per side) plus inflow data."""
 
-    def __init__(self, g, bc, inflow_v, inflow_Z, inflow_H, chi=None):
+    def __init__(self, g, bc, inflow_v, inflow_Z, inflow_H, chi=None, wall_H=None):
         self.g = g
+        # Dirichlet H of each side's isothermal wall, [d][side]
+        self.wall_H = [[float(wall_H[d][s]) if wall_H is not None else 0.0 for s in (0, 1)]
+                       for d in range(g.dim)]
         self.bc = [tuple(bc[d]) for d in range(g.dim)]
         self.inflow_v = [float(inflow_v[d]) for d in range(g.dim)]
         self.inflow_Z = float(inflow_Z)
@@ -58,14 +65,15 @@ class Boundary:
         return self.bc[d][0] == PERIODIC
 
     # ------------------------------------------------------------------
-    def fill(self, phi, what, comp=None, kappa_in=None):
+    def fill(self, phi, what, comp=None, kappa_in=None, kappa_wall=None):
         """Fill all ghost cells of ``phi`` in place.
 
         ``what`` is "Z", "H", "kappa" or "v" (then ``comp`` is the velocity
         component).  For "kappa" the Dirichlet value is ``kappa_in``, the
         transport coefficient of the inflow state, so the interface value of kappa
         on an inflow side is kappa_in (Eq 3.43 applied to kappa); other sides take
-        its zero-gradient ghost (Eq 3.44).
+        its zero-gradient ghost (Eq 3.44), and an isothermal wall's side the
+        transport coefficient of the wall state, kappa_wall[d][side].
         Directions are filled in order 0, 1, 2 over full padded slabs, so edge and
         corner ghosts end up consistent with every side they touch."""
         g = self.g
@@ -93,12 +101,20 @@ class Boundary:
                 if what == "v":
                     wall = mirror_zero
                     slip = mirror_zero if comp == d else zero_grad
+                    wall_t = mirror_zero
                 else:
                     wall = zero_grad
                     slip = zero_grad
+                    if what == "Z":
+                        wall_t = mirror_in
+                    elif what == "H":
+                        wall_t = 2.0 * self.wall_H[d][side] - a1
+                    else:
+                        kw = kappa_wall[d][side] if kappa_wall is not None else 0.0
+                        wall_t = 2.0 * kw - a1
                 out = np.select(
-                    [kind == INFLOW, kind == OUTFLOW, kind == WALL, kind == SLIP],
-                    [mirror_in, zero_grad, wall, slip])
+                    [kind == INFLOW, kind == OUTFLOW, kind == WALL, kind == SLIP, kind == WALL_T],
+                    [mirror_in, zero_grad, wall, slip, wall_t])
                 _slab(phi, g, d, ghost)[...] = out
 
     def fill_pressure(self, P):

@@ -66,8 +66,12 @@ def temperature(Z, H, fp):
     return fp["Q"] / (fp["S"] + 1.0) * (F_eps(Z, fp["S"], fp["k"]) + H)
 
 
-def kappa(T, sigma):
-    """kappa = mu = rho D = T^sigma (Eq 2.50)."""
+def kappa(T, sigma, transport=0, C=0.0):
+    """kappa = mu = rho D as a function of T: the power law T^sigma (Eq 2.50),
+    or with transport = 1 Sutherland's law T^(3/2) (1 + C) / (T + C) (Eq 4.12),
+    C the Sutherland constant over the reference temperature."""
+    if transport == 1:
+        return T ** 1.5 * (1.0 + C) / (T + C)
     return T ** sigma
 
 

@@ -40,7 +40,7 @@ import copy
 import numpy as np
 
 from . import flame, poisson
-from .boundary import (Boundary, INFLOW, OUTFLOW, WALL, SLIP, face_end, cell_end)
+from .boundary import (Boundary, INFLOW, OUTFLOW, WALL, SLIP, WALL_T, face_end, cell_end)
 from .ibm import build as build_ibm
 from .operators import (Grid, V, pad, interp_to_faces, diff_to_faces, faces_interp_to_cells,
                         faces_diff_to_cells, diff2, integrate)
@@ -60,7 +60,9 @@ class Problem:
         self.ibm = build_ibm(g, geo)
         chi = self.ibm["chi"] if self.ibm is not None else None
         self.bnd = Boundary(g, prm["bc"][:dim], prm["inflow_v"][:dim], prm["inflow_Z"],
-                            prm["inflow_H"], chi)
+                            prm["inflow_H"], chi, prm.get("wall_H"))
+        self.transport = int(prm.get("transport", 0))
+        self.suth_C = float(prm.get("sutherland_C", 0.0))
         self.periodic = [self.bnd.periodic(d) for d in range(dim)]
         self.incompressible = bool(prm.get("incompressible", 0))
         self.has_inflow = any(prm["bc"][d][s] == INFLOW for d in range(dim) for s in (0, 1))
@@ -79,8 +81,9 @@ class Problem:
         rho = g.zeros()
         V(rho, g)[...] = flame.density(p0, V(T, g))                      # Eq 2.49
         kap = g.zeros()
-        V(kap, g)[...] = flame.kappa(V(T, g), self.prm["sigma"])         # Eq 2.50
-        self.bnd.fill(kap, "kappa", kappa_in=self.inflow_kappa() if self.has_inflow else None)
+        V(kap, g)[...] = self.kappa_of(V(T, g))                          # Eq 2.50 / 4.12
+        self.bnd.fill(kap, "kappa", kappa_in=self.inflow_kappa() if self.has_inflow else None,
+                      kappa_wall=self.wall_kappa())
         return T, rho, kap
 
     def thermo(self, Z, H, mass):
@@ -99,8 +102,25 @@ class Problem:
         return float(flame.temperature(np.array(self.prm["inflow_Z"]),
                                        np.array(self.prm["inflow_H"]), self.fp))
 
+    def kappa_of(self, T):
+        return flame.kappa(T, self.prm["sigma"], self.transport, self.suth_C)
+
     def inflow_kappa(self):
-        return float(flame.kappa(self.inflow_temperature(), self.prm["sigma"]))
+        return float(self.kappa_of(self.inflow_temperature()))
+
+    def wall_kappa(self):
+        """kappa of each isothermal wall's state (Z_in, H_wall of the side), [d][side]."""
+        out = []
+        for d in range(self.g.dim):
+            row = []
+            for s in (0, 1):
+                if self.prm["bc"][d][s] != WALL_T or self.incompressible:
+                    row.append(1.0)
+                    continue
+                T = flame.temperature(np.array(self.prm["inflow_Z"]), np.array(self.bnd.wall_H[d][s]), self.fp)
+                row.append(float(self.kappa_of(T)))
+            out.append(row)
+        return out
 
     def inflow_density(self, p0):
         if self.incompressible:

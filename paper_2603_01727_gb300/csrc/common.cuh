@@ -9,7 +9,7 @@ namespace lm {
 
 constexpr int kMaxDim = 3;
 
-enum BcKind : int { BC_PERIODIC = 0, BC_INFLOW = 1, BC_OUTFLOW = 2, BC_WALL = 3, BC_SLIP = 4 };
+enum BcKind : int { BC_PERIODIC = 0, BC_INFLOW = 1, BC_OUTFLOW = 2, BC_WALL = 3, BC_SLIP = 4, BC_WALL_T = 5 };
 
 // Grid geometry.  Cell fields live in a padded array with one ghost layer on
 // each side of every active direction (ghost index 0 and n+1, interior 1..n),
@@ -89,7 +89,17 @@ struct Phys {
     int incompressible, closed;
     int mixed;                         // 1: FP32 stencil arithmetic and multigrid (SIM_MIXED)
     int sigma_is_07;                   // sigma == 0.7 exactly (paper value, Eq 2.50)
+    int transport;                     // 0: kappa = T^sigma (Eq 2.50); 1: Sutherland (Eq 4.12)
+    double suth_C;                     // Sutherland constant over the reference temperature
+    double wall_H[3][2];               // Dirichlet H of isothermal walls, [direction][side]
+    double kap_wall[3][2];             // kappa of the isothermal walls' states
 };
+
+// Transport coefficient of a temperature, FP64 (Eq 2.50 or Eq 4.12).
+__host__ __device__ inline double kappa_of(const Phys& ph, double T) {
+    if (ph.transport == 1) return pow(T, 1.5) * (1.0 + ph.suth_C) / (T + ph.suth_C);
+    return pow(T, ph.sigma);
+}
 
 // ---------------------------------------------------------------------------
 // Forward-mode dual number (value, derivative): instantiating a cell function

@@ -195,6 +195,8 @@ Phys make_phys(const sim_params_t* p) {
     ph.mixed = (p->precision == SIM_MIXED);
     ph.sigma_is_07 = (p->sigma == 0.7);
     ph.sigma = p->sigma;
+    ph.transport = p->transport;
+    ph.suth_C = p->sutherland_C;
     ph.inv_Fr2 = p->inv_Fr2;
     for (int d = 0; d < 3; ++d) ph.inflow_v[d] = p->inflow_v[d];
     ph.inflow_Z = p->inflow_Z;
@@ -209,11 +211,19 @@ Phys make_phys(const sim_params_t* p) {
         ph.kappa_in = 1.0;
     } else if (inflow) {
         ph.rho_in_T = host_temperature(ph, p->inflow_Z, p->inflow_H);
-        ph.kappa_in = std::pow(ph.rho_in_T, p->sigma);
+        ph.kappa_in = kappa_of(ph, ph.rho_in_T);
     } else {
         ph.rho_in_T = 1.0;
         ph.kappa_in = 1.0;
     }
+    // isothermal walls: Dirichlet H of the side, kappa of the wall state (Z_in, H_wall)
+    for (int d = 0; d < 3; ++d)
+        for (int q = 0; q < 2; ++q) {
+            ph.wall_H[d][q] = p->wall_H[d][q];
+            ph.kap_wall[d][q] = 1.0;
+            if (d < p->dim && p->bc[d][q] == SIM_BC_WALL_T && !p->incompressible)
+                ph.kap_wall[d][q] = kappa_of(ph, host_temperature(ph, p->inflow_Z, p->wall_H[d][q]));
+        }
     return ph;
 }
 
@@ -224,7 +234,7 @@ const char* validate(const sim_params_t* p) {
         if (p->n[d] < 4) return "every extent must be >= 4 cells";
         if (!(p->L[d] > 0.0)) return "domain lengths must be > 0";
         for (int q = 0; q < 2; ++q)
-            if (p->bc[d][q] < SIM_BC_PERIODIC || p->bc[d][q] > SIM_BC_SLIP) return "unknown boundary kind";
+            if (p->bc[d][q] < SIM_BC_PERIODIC || p->bc[d][q] > SIM_BC_WALL_T) return "unknown boundary kind";
         if ((p->bc[d][0] == SIM_BC_PERIODIC) != (p->bc[d][1] == SIM_BC_PERIODIC))
             return "a periodic side needs a periodic partner";
     }
@@ -242,6 +252,8 @@ const char* validate(const sim_params_t* p) {
     if (p->poisson_max_iter < 1) return "poisson_max_iter must be >= 1";
     if (p->mg_sweeps < 0 || p->mg_sweeps > 2) return "mg_sweeps must be 0 (default), 1 or 2";
     if (p->mg_tail_cells < 0) return "mg_tail_cells must be >= 0";
+    if (p->transport != 0 && p->transport != 1) return "transport must be 0 (power law) or 1 (Sutherland)";
+    if (p->transport == 1 && !(p->sutherland_C >= 0.0)) return "sutherland_C must be >= 0";
     if (p->stage_tile_x != 0 && (p->stage_tile_x < 8 || p->stage_tile_x > 256 ||
                                  (p->stage_tile_x & (p->stage_tile_x - 1)) != 0))
         return "stage_tile_x must be 0 or a power of two from 8 to 256";
@@ -1677,6 +1689,10 @@ const char* adj_unsupported(const sim_t* s) {
     if (s->ph.incompressible) return "the adjoint step needs the variable-density model";
     if (s->ph.Le_F != s->ph.Le_O) return "the adjoint step needs Le_F == Le_O";
     if (s->ph.inv_Fr2 != 0.0) return "the adjoint step needs inv_Fr2 == 0";
+    if (s->ph.transport != 0) return "the adjoint step needs the power-law transport (Eq 2.50)";
+    for (int d = 0; d < s->g.dim; ++d)
+        for (int q = 0; q < 2; ++q)
+            if (s->prm.bc[d][q] == SIM_BC_WALL_T) return "the adjoint step has no isothermal walls";
     return nullptr;
 }
 

@@ -43,6 +43,29 @@ __device__ __forceinline__ long long compact_stride(const Geom& g, int d) {
 // ----------------------------------------------------------------------------
 // Ghost cells of one direction d (Eqs 3.43-3.45; kappa: see Bnd docs).
 // ----------------------------------------------------------------------------
+// Ghost value of field `what` across side `side` of direction d (Eqs
+// 3.43-3.45): Dirichlet sides mirror about the prescribed face value (inflow,
+// isothermal wall), zero-gradient sides copy, walls reverse the velocity,
+// symmetry planes its normal component.
+__device__ __forceinline__ double ghost_value(const Phys& ph, int what, int d, int side, int kind, double adj) {
+    const bool vel = what >= GW_V0;
+    const bool normal = vel && (what - GW_V0 == d);
+    if (kind == BC_WALL_T) {
+        if (vel) return -adj;
+        const double dv = (what == GW_Z) ? ph.inflow_Z : (what == GW_H) ? ph.wall_H[d][side] : ph.kap_wall[d][side];
+        return 2.0 * dv - adj;
+    }
+    double dv;
+    if (what == GW_Z) dv = ph.inflow_Z;
+    else if (what == GW_H) dv = ph.inflow_H;
+    else if (what == GW_KAPPA) dv = ph.kappa_in;
+    else dv = ph.inflow_v[what - GW_V0];
+    if (kind == BC_INFLOW) return 2.0 * dv - adj;
+    if (kind == BC_OUTFLOW) return adj;
+    if (kind == BC_WALL) return vel ? -adj : adj;
+    return normal ? -adj : adj;   // BC_SLIP
+}
+
 __global__ void k_ghost(Geom g, Phys ph, const uint8_t* __restrict__ klo, const uint8_t* __restrict__ khi,
                         int d, int periodic, GhostJob job) {
     const int a = (d == 0) ? 1 : 0;
@@ -64,24 +87,11 @@ __global__ void k_ghost(Geom g, Phys ph, const uint8_t* __restrict__ klo, const 
             x[i_gh] = x[i_1];
             continue;
         }
-        double dv;
-        if (what == GW_Z) dv = ph.inflow_Z;
-        else if (what == GW_H) dv = ph.inflow_H;
-        else if (what == GW_KAPPA) dv = ph.kappa_in;
-        else dv = ph.inflow_v[what - GW_V0];
-        const bool vel = what >= GW_V0;
-        const bool normal = vel && (what - GW_V0 == d);
         for (int side = 0; side < 2; ++side) {
             const long long ig = side ? i_gh : i_g0;
             const long long ia = side ? i_n : i_1;
             const int kind = side ? khi[q] : klo[q];
-            const double adj = x[ia];
-            double out;
-            if (kind == BC_INFLOW) out = 2.0 * dv - adj;
-            else if (kind == BC_OUTFLOW) out = adj;
-            else if (kind == BC_WALL) out = vel ? -adj : adj;
-            else out = normal ? -adj : adj;  // BC_SLIP
-            x[ig] = out;
+            x[ig] = ghost_value(ph, what, d, side, kind, x[ia]);
         }
     }
 }
@@ -93,20 +103,6 @@ __global__ void k_ghost(Geom g, Phys ph, const uint8_t* __restrict__ klo, const 
 // from c, composing the per-direction maps in the same order (a corner is the
 // d = 1 map of the d = 0 ghost).  Same formulas, so the same values.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ double ghost_value(const Phys& ph, int what, int d, int kind, double adj) {
-    double dv;
-    if (what == GW_Z) dv = ph.inflow_Z;
-    else if (what == GW_H) dv = ph.inflow_H;
-    else if (what == GW_KAPPA) dv = ph.kappa_in;
-    else dv = ph.inflow_v[what - GW_V0];
-    const bool vel = what >= GW_V0;
-    const bool normal = vel && (what - GW_V0 == d);
-    if (kind == BC_INFLOW) return 2.0 * dv - adj;
-    if (kind == BC_OUTFLOW) return adj;
-    if (kind == BC_WALL) return vel ? -adj : adj;
-    return normal ? -adj : adj;   // BC_SLIP
-}
-
 // vals[f]: the value just written to job.f[f] at interior cell q.
 __device__ __forceinline__ void fill_ghosts_of(const Geom& g, const Phys& ph, const Bnd& bnd, const GhostJob& job,
                                                const int q[3], const double* vals) {
@@ -133,7 +129,8 @@ __device__ __forceinline__ void fill_ghosts_of(const Geom& g, const Phys& ph, co
                     for (int d = 0; d < g.dim; ++d) {
                         if (o[d] == 0) continue;
                         const int side = o[d] - 1;
-                        if (!g.periodic[d]) v = ghost_value(ph, job.what[f], d, bnd.kind[d][side][slab_index(g, d, qq)], v);
+                        if (!g.periodic[d])
+                            v = ghost_value(ph, job.what[f], d, side, bnd.kind[d][side][slab_index(g, d, qq)], v);
                         qq[d] = side ? g.n[d] + 1 : 0;
                     }
                     job.f[f][(long long)qq[0] + (long long)qq[1] * g.s[1] + (long long)qq[2] * g.s[2]] = v;
@@ -198,7 +195,7 @@ __device__ __forceinline__ double recip_newton(double T) {
 // differences at a fraction of an FP64 pow's cost.  Other exponents use the
 // FP64 pow.
 __device__ __forceinline__ double kappa_mixed(const Phys& ph, double T) {
-    if (!ph.sigma_is_07) return pow(T, ph.sigma);
+    if (ph.transport != 0 || !ph.sigma_is_07) return kappa_of(ph, T);
     const FF t(T);
     const float y0 = powf(t.hi, 0.7f);
     const FF t2 = t * t, t4 = t2 * t2, t7 = t4 * t2 * t;
@@ -235,7 +232,7 @@ __device__ __forceinline__ double state_cell(const Geom& g, const Phys& ph, cons
         iT = recip_newton(Tv);
     } else {
         Tv = temperature(ph, Z[c], H[c]);
-        kv = pow(Tv, ph.sigma);
+        kv = kappa_of(ph, Tv);
         iT = 1.0 / Tv;
     }
     T[c] = Tv;

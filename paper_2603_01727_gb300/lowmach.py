@@ -18,7 +18,7 @@ SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ENOCONV, SIM_ENAN, SIM_EUNSTABLE,
     0, -1, -2, -3, -4, -5, -6, -7
 STATUS_NAMES = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ENOMEM", -3: "SIM_ECUDA", -4: "SIM_ENOCONV",
                 -5: "SIM_ENAN", -6: "SIM_EUNSTABLE", -7: "SIM_ESTATE"}
-SIM_BC_PERIODIC, SIM_BC_INFLOW, SIM_BC_OUTFLOW, SIM_BC_WALL, SIM_BC_SLIP = 0, 1, 2, 3, 4
+SIM_BC_PERIODIC, SIM_BC_INFLOW, SIM_BC_OUTFLOW, SIM_BC_WALL, SIM_BC_SLIP, SIM_BC_WALL_T = 0, 1, 2, 3, 4, 5
 SIM_FP64, SIM_MIXED = 0, 1
 SIM_IBM_NONE, SIM_IBM_SLOT, SIM_IBM_SPHERE = 0, 1, 2
 (SIM_FIELD_U, SIM_FIELD_V, SIM_FIELD_W, SIM_FIELD_Z, SIM_FIELD_H, SIM_FIELD_T, SIM_FIELD_RHO,
@@ -43,7 +43,9 @@ class SimParams(ctypes.Structure):
                 ("inflow_Z", ctypes.c_double), ("inflow_H", ctypes.c_double),
                 ("Re", ctypes.c_double), ("Pr", ctypes.c_double), ("inv_Fr2", ctypes.c_double),
                 ("Le_F", ctypes.c_double), ("Le_O", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("sigma", ctypes.c_double), ("Z_st", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("transport", ctypes.c_int),
+                ("sutherland_C", ctypes.c_double), ("wall_H", (ctypes.c_double * 2) * 3),
+                ("Z_st", ctypes.c_double),
                 ("density_ratio", ctypes.c_double), ("eps_reg", ctypes.c_double),
                 ("tol_reg", ctypes.c_double), ("closed_system", ctypes.c_int),
                 ("incompressible", ctypes.c_int), ("dt", ctypes.c_double),
@@ -149,6 +151,12 @@ def params_struct(prm):
     p.mg_sweeps = int(prm.get("mg_sweeps", 0))
     p.mg_tail_cells = int(prm.get("mg_tail_cells", 0))
     p.stage_tile_x = int(prm.get("stage_tile_x", 0))
+    p.transport = int(prm.get("transport", 0))
+    p.sutherland_C = float(prm.get("sutherland_C", 0.0))
+    wall_H = prm.get("wall_H")
+    for d in range(3):
+        for s in range(2):
+            p.wall_H[d][s] = float(wall_H[d][s]) if wall_H is not None and d < len(wall_H) else 0.0
     return p
 
 

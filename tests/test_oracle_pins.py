@@ -717,3 +717,61 @@ def test_marker_body_mask_velocity_and_source(dim, n, spacing):
     owner = nearest_markers(pts, M[:, :dim])
     per = np.bincount(owner, weights=ib["Sm"][chi > 0] * g.dV, minlength=len(M))
     assert np.allclose(per, flow, rtol=1e-13, atol=0.0)
+
+
+def test_sutherland_law_is_the_dimensional_law_over_its_reference_value():
+    """Eq 4.12: kappa(T) = mu(T*)/mu(T_ref) with Sutherland's dimensional law
+    mu(T*) ~ T*^(3/2) / (T* + S), T* = T T_ref, so S enters only through
+    C = S / T_ref; kappa(1) = 1, and C = 0 reduces to the power law T^(1/2)."""
+    S_K, T_ref = 110.5, 600.0
+
+    def mu(Tk):
+        return Tk ** 1.5 / (Tk + S_K)
+
+    T = np.linspace(0.3, 2.5, 23)
+    assert np.allclose(flame.kappa(T, 0.7, transport=1, C=S_K / T_ref), mu(T * T_ref) / mu(T_ref),
+                       rtol=1e-14, atol=0.0)
+    assert flame.kappa(1.0, 0.7, transport=1, C=S_K / T_ref) == pytest.approx(1.0, rel=1e-15)
+    assert np.allclose(flame.kappa(T, 0.7, transport=1, C=0.0), T ** 0.5, rtol=1e-14)
+    assert np.allclose(flame.kappa(T, 0.7), T ** 0.7, rtol=1e-14)
+
+
+def test_isothermal_slab_conducts_to_the_kirchhoff_profile():
+    """The heated cavity's walls (Eq 4.16a-b) with Sutherland transport
+    (Eq 4.12), gravity off and periodic in x_2: a closed slab between T_H and
+    T_C.  Continuity with zero wall flux leaves rho u = 0 at steady state, so
+    the energy equation is d/dx(kappa dT/dx) = 0 and the Kirchhoff transform
+    K(T) = int_1^T kappa is linear in x; the enclosed mass fixes
+    p0 = m / int 1/T (Eq 2.40).  From a linear initial profile, after the
+    transient has decayed, T and p0 converge to them at second order."""
+    from scipy.optimize import brentq
+    eps, C = 0.6, 110.5 / 600.0
+    TH, TC = 1.0 + eps, 1.0 - eps
+
+    def K(T):
+        return quad(lambda s: flame.kappa(s, 0.7, transport=1, C=C), 1.0, T, epsabs=1e-14, epsrel=1e-14)[0]
+
+    KH, KC = K(TH), K(TC)
+
+    def T_exact(xi):
+        return brentq(lambda T: K(T) - (KH + (KC - KH) * xi), TC - 1e-9, TH + 1e-9, xtol=1e-15)
+
+    errT, errp = [], []
+    for n in (12, 24):
+        x, _ = W.cell_centres((n, 4), (1.0, 4.0 / n))
+        T0 = TH + (TC - TH) * x
+        prm, geo, f = W.heated_cavity(n, gravity=False, ny=4, T0=T0)
+        pb = S.Problem(prm, geo)
+        st = S.initial_state(pb, f["v"], f["Z"], f["H"])
+        for _ in range(int(np.ceil(6.0 / prm["dt"]))):
+            st = S.advance(pb, st)
+        T = V(st.T, pb.g)
+        assert np.allclose(T, T[:1, :], rtol=0.0, atol=1e-12)     # uniform along x_2
+        te = np.array([T_exact(xi) for xi in x[0]])
+        errT.append(np.max(np.abs(T[0] - te)))
+        m = np.mean(1.0 / T0)
+        p0e = m / quad(lambda xi: 1.0 / T_exact(xi), 0.0, 1.0, epsabs=1e-12)[0]
+        errp.append(abs(st.p0_hist[0] - p0e))
+    assert errT[1] < 2.5e-3 and errp[1] < 3.5e-3
+    assert np.log2(errT[0] / errT[1]) > 1.6
+    assert np.log2(errp[0] / errp[1]) > 1.6

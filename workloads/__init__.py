@@ -20,11 +20,14 @@ Workloads
   sphere_burner(...)    3D spherical porous burner, 192^3 on [0,1]^3.
   marker_burner(...)    the porous burner (circle in 2D, sphere in 3D) given by
                         surface markers instead of its analytic shape.
+  heated_cavity(...)    the differentially heated square cavity of Sec. 4.3
+                        (Eqs 4.8-4.17): isothermal side walls, adiabatic top and
+                        bottom, Sutherland transport, buoyancy, enclosed.
 """
 
 import numpy as np
 
-PERIODIC, INFLOW, OUTFLOW, WALL, SLIP = 0, 1, 2, 3, 4
+PERIODIC, INFLOW, OUTFLOW, WALL, SLIP, WALL_T = 0, 1, 2, 3, 4, 5
 IBM_NONE, IBM_SLOT, IBM_SPHERE, IBM_MARKERS = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 
@@ -40,7 +43,7 @@ def _base_params():
         Z_st=0.055, density_ratio=7.0, eps_reg=0.5, tol_reg=1e-3,
         closed_system=0, incompressible=0, dt=0.0,
         precision=FP64, poisson_rtol=1e-10, poisson_max_iter=200, mg_sweeps=0, mg_tail_cells=0,
-        stage_tile_x=0)
+        stage_tile_x=0, transport=0, sutherland_C=0.0, wall_H=[[0.0, 0.0], [0.0, 0.0], [0.0, 0.0]])
 
 
 def paper_scalars(Z_st, ratio):
@@ -333,3 +336,39 @@ def marker_burner(n=64, dim=2, spacing=1.5, cfl=0.4, Re=150.0, seed=SEED, rms=0.
         M = circle_markers([0.5, 0.5], R, count)
     geo = dict(geo, kind=IBM_MARKERS, markers=M)
     return prm, geo, f
+
+
+def heated_cavity(n=64, Ra=1e2, eps=0.6, gravity=True, ny=None, cfl=0.4, T0=None):
+    """Differentially heated square cavity (Sec. 4.3): unit square, left wall at
+    T_H = 1 + eps, right wall at T_C = 1 - eps (isothermal no-slip walls,
+    Eq 4.16a-b), adiabatic no-slip top and bottom (Eq 4.16c); Pr = 0.71,
+    gamma = 1.4, Sutherland transport with C = 110.5 K / 600 K (Eq 4.12),
+    Pe = Pr Ra^(1/2) (Eq 4.10, so Re = Ra^(1/2)), Fr = (2 Pr eps)^(1/2)
+    (Eq 4.11); enclosed (p0 from the mass, Eq 4.13).  Air only (Z = 0) with the
+    convenient Q = S + 1, so H = T + 1 (Eq 4.16) and the quiescent initial
+    state at T = 1 has H = 2 (Eq 4.17).  gravity=False and ny > 0 (periodic in
+    x_2) give the one-dimensional conduction slab used as a pin; T0 (an
+    interior array) replaces the uniform initial temperature."""
+    ny = n if ny is None else ny
+    prm = _base_params()
+    Re = Ra ** 0.5
+    Pr = 0.71
+    bc_y = [WALL, WALL] if ny == n and gravity else [PERIODIC, PERIODIC]
+    if not gravity and ny != n:
+        bc_y = [PERIODIC, PERIODIC]
+    prm.update(dim=2, n=[n, ny, 1], L=[1.0, float(ny) / n if bc_y[0] == PERIODIC else 1.0, 1.0],
+               bc=[[WALL_T, WALL_T], bc_y, [PERIODIC, PERIODIC]], Re=Re, Pr=Pr,
+               inv_Fr2=(1.0 / (2.0 * Pr * eps)) if gravity else 0.0, gamma=1.4, transport=1,
+               sutherland_C=110.5 / 600.0, density_ratio=2.0, closed_system=1, inflow_Z=0.0, inflow_H=2.0,
+               wall_H=[[2.0 + eps, 2.0 - eps], [0.0, 0.0], [0.0, 0.0]])
+    x, y = cell_centres((n, ny), (1.0, prm["L"][1]))
+    T = np.ones(x.shape) if T0 is None else np.asarray(T0, dtype=float)
+    fields = dict(v=[np.zeros(x.shape), np.zeros(x.shape)], Z=np.zeros(x.shape), H=T + 1.0)
+    # explicit diffusion limit at the hottest, lightest state: kappa(T_H), rho ~ 1/T_H
+    TH = 1.0 + eps
+    C = prm["sutherland_C"]
+    kap_max = TH ** 1.5 * (1.0 + C) / (TH + C)
+    h = 1.0 / n
+    lim = [h / 1.0, h * h * Re * min(1.0, Pr) * (1.0 / TH) / (4.0 * kap_max)]
+    prm["dt"] = cfl * min(lim)
+    return prm, None, fields
