@@ -25,6 +25,12 @@ def derived_parameters(Z_st, density_ratio, eps, tol, Le_F=1.0, Le_O=1.0, gamma=
     return dict(S=S, Q=Q, k=k, N_F=N_F, N_O=N_O, zeta=zeta, Le_F=Le_F, Le_O=Le_O)
 
 
+def Nprime_eps(Z, fp):
+    """N' of the p0 equation (Eq 2.39), N'_F = -1/S, N'_O = 1, regularised with
+    the same theta_eps as N (Eq 3.35b)."""
+    return (-1.0 / fp["S"] - 1.0) * theta_eps(Z, fp["k"]) + 1.0
+
+
 def theta_eps(Z, k):
     """Regularised Heaviside around the flame Z = 1 (Eq 3.34)."""
     return 0.5 * (1.0 + np.tanh(k * (Z - 1.0)))

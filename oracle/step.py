@@ -27,6 +27,15 @@ the design notes of the package):
    the highest order the stored history allows (0th, 1st, then 2nd order).
  * Enclosed systems take p0 from Eq 2.40 with the initial mass m = int rho^0 dV,
    p0^0 = 1; open systems take p0 = 1 (Eq 2.41).
+ * Semi-enclosed systems (closed_system = 2) advance p0 by the ODE of Eq 2.38
+   with the stages of the scalars: AB2 in the predictor (Euler on step 0),
+   AM2 in the corrector, its right-hand side G evaluated on the level's
+   fields.  The volume integrals are cell sums of the discrete operators the
+   residuals use: div(kappa grad .) as in Eq 3.26b's diffusive part, div v as
+   the sum of the cell-centred delta_2 derivatives (which telescopes to the
+   boundary values of v), and N' regularised like N (Eq 3.35b).  The
+   projection's mass balance is then closed only up to the ODE's truncation
+   error; the mean of b is removed as for every other kind.
  * The outflow interfaces' mass flux is the adjacent cell's provisional
    momentum, shifted by one uniform amount so that the discrete global mass
    balance closes exactly (text after Eq 4.22); the mean of b is then removed
@@ -66,7 +75,8 @@ class Problem:
         self.periodic = [self.bnd.periodic(d) for d in range(dim)]
         self.incompressible = bool(prm.get("incompressible", 0))
         self.has_inflow = any(prm["bc"][d][s] == INFLOW for d in range(dim) for s in (0, 1))
-        self.closed = bool(prm.get("closed_system", 0))
+        self.closed = int(prm.get("closed_system", 0)) == 1
+        self.semi = int(prm.get("closed_system", 0)) == 2 and not self.incompressible
 
     # -- state relation (Sec. 3.5, Eqs 2.49-2.50, 2.40-2.41) ------------------
     def thermo_at(self, Z, H, p0):
@@ -86,12 +96,15 @@ class Problem:
                       kappa_wall=self.wall_kappa())
         return T, rho, kap
 
-    def thermo(self, Z, H, mass):
-        """(T, rho, kappa, p0): p0 from Eq 2.40 (enclosed) or Eq 2.41 (open)."""
+    def thermo(self, Z, H, mass, p0_ode=None):
+        """(T, rho, kappa, p0): p0 from Eq 2.40 (enclosed), Eq 2.41 (open) or
+        the value p0_ode the ODE of Eq 2.38 gave (semi-enclosed)."""
         g = self.g
         if self.incompressible:
             return self.thermo_at(Z, H, 1.0) + (1.0,)
-        if self.closed:
+        if self.semi:
+            p0 = float(p0_ode)
+        elif self.closed:
             T = flame.temperature(V(Z, g), V(H, g), self.fp)
             p0 = flame.closed_p0(mass, T, g.dV)
         else:
@@ -138,6 +151,7 @@ class State:
         self.p0_hist = []    # [p0^n, p0^(n-1), p0^(n-2)]
         self.rho_prev = None
         self.R_prev = None
+        self.G_prev = None   # right-hand side of Eq 2.38 at the previous level
         self.mass = None
         self.nstep = 0
         self.t = 0.0
@@ -338,6 +352,28 @@ def project(pb, mom, rho, drho, p0):
     return P, F, v, b
 
 
+def p0_rate(pb, v, Z, H, kap, p0):
+    """Right-hand side of Eq 2.38,
+    G = gamma / V { Q/(S+1) / Pe int [div(kappa grad H) + N' div(kappa grad Z)] dV
+                    - p0 int div v dV },
+    the integrals as cell sums of the discrete operators (padded inputs with
+    their ghost cells filled)."""
+    g, fp = pb.g, pb.fp
+    dim = g.dim
+    kf = [interp_to_faces(kap, g, j) for j in range(dim)]
+
+    def diffusive(phi):
+        out = np.zeros(V(phi, g).shape)
+        for j in range(dim):
+            out += faces_diff_to_cells(kf[j] * diff_to_faces(phi, g, j), g, j)
+        return out
+
+    heat = integrate(diffusive(H) + flame.Nprime_eps(V(Z, g), fp) * diffusive(Z), g)
+    div = integrate(sum(diff2(v[j], g, j) for j in range(dim)), g)
+    vol = float(np.prod([g.n[d] * g.h[d] for d in range(dim)]))
+    return pb.prm["gamma"] / vol * (fp["Q"] / (fp["S"] + 1.0) / pb.Pe * heat - p0 * div)
+
+
 def _ddt_rho(rho_new, rho_n, rho_prev, dt, n):
     """Backward difference of rho: Eq 3.11 / 3.19 (first order on step 0)."""
     if n == 0:
@@ -385,7 +421,12 @@ def advance(pb, st, return_star=False):
     Hs = pad(V(st.H, g) + dt * cH, g)
     bnd.fill(Zs, "Z")
     bnd.fill(Hs, "H")
-    Ts, rhos, kaps, p0s = pb.thermo(Zs, Hs, st.mass)                    # Eq 3.6
+    p0_ode = None
+    if pb.semi:                                                          # Eq 2.38, AB2
+        G_n = p0_rate(pb, st.v, st.Z, st.H, st.kappa, st.p0_hist[0])
+        cG = G_n if (n == 0 or st.G_prev is None) else 1.5 * G_n - 0.5 * st.G_prev
+        p0_ode = st.p0_hist[0] + dt * cG
+    Ts, rhos, kaps, p0s = pb.thermo(Zs, Hs, st.mass, p0_ode)            # Eq 3.6
     mom_t = [mom_n[i] + dt * cv[i] for i in range(dim)]                 # rho* v~ (Eq 3.10)
     drho = _ddt_rho(V(rhos, g), rho_n, None if st.rho_prev is None else V(st.rho_prev, g), dt, n)
     Ps, Fs, vs, _ = project(pb, mom_t, rhos, drho, p0s)                 # Eqs 3.9, 3.23-3.25
@@ -397,7 +438,10 @@ def advance(pb, st, return_star=False):
     H1 = pad(V(st.H, g) + 0.5 * dt * (Rs["H"] + Rn["H"]), g)            # Eq 3.13
     bnd.fill(Z1, "Z")
     bnd.fill(H1, "H")
-    T1, rho1, kap1, p01 = pb.thermo(Z1, H1, st.mass)                    # Eq 3.15
+    if pb.semi:                                                          # Eq 2.38, AM2
+        G_s = p0_rate(pb, vs, Zs, Hs, kaps, p0s)
+        p0_ode = st.p0_hist[0] + 0.5 * dt * (G_s + G_n)
+    T1, rho1, kap1, p01 = pb.thermo(Z1, H1, st.mass, p0_ode)            # Eq 3.15
     mom_b = [mom_n[i] + 0.5 * dt * (Rs["v"][i] + Rn["v"][i]) for i in range(dim)]  # Eq 3.18
     drho1 = _ddt_rho(V(rho1, g), rho_n, None if st.rho_prev is None else V(st.rho_prev, g), dt, n)
     P1, F1, v1, _ = project(pb, mom_b, rho1, drho1, p01)                # Eqs 3.17, 3.23-3.25
@@ -408,6 +452,7 @@ def advance(pb, st, return_star=False):
     new.p0_hist = ([p01] + st.p0_hist)[:3]
     new.rho_prev = st.rho.copy()
     new.R_prev = Rn
+    new.G_prev = G_n if pb.semi else None
     new.mass = st.mass
     new.nstep = n + 1
     new.t = st.t + dt

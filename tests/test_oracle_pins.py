@@ -775,3 +775,57 @@ def test_isothermal_slab_conducts_to_the_kirchhoff_profile():
     assert errT[1] < 2.5e-3 and errp[1] < 3.5e-3
     assert np.log2(errT[0] / errT[1]) > 1.6
     assert np.log2(errp[0] / errp[1]) > 1.6
+
+
+def _p0_after(prm, geo, f, t_end):
+    pb = S.Problem(prm, geo)
+    st = S.initial_state(pb, f["v"], f["Z"], f["H"])
+    dt = prm["dt"]
+    hist = [1.0]
+    for _ in range(int(np.ceil(t_end / dt))):
+        st = S.advance(pb, st)
+        hist.append(st.p0_hist[0])
+    return pb, st, np.array(hist)
+
+
+def test_semi_enclosed_p0_ode_converges_to_the_mass_constraint_in_a_closed_box():
+    """In a box that exchanges nothing with the outside, the ODE of Eq 2.38
+    (integrated by the stages) and the mass constraint of Eq 2.40 describe the
+    same p0(t): the heat released at the flame enters the ODE only through
+    N' div(kappa grad Z) (the boundary integrals vanish), the mass constraint
+    only through T.  Their difference after a burning period falls at second
+    order under refinement (dt scaling with the grid)."""
+    diff = []
+    for n in (16, 32):
+        p = {}
+        for cs in (1, 2):
+            prm, geo, f = W.periodic_blobs(n)
+            prm.update(closed_system=cs, poisson_rtol=1e-12)
+            p[cs] = _p0_after(prm, geo, f, 0.1)[2][-1]
+        assert p[1] > 1.05                                # the flame raises p0 substantially
+        diff.append(abs(p[2] - p[1]))
+    assert diff[1] < 3e-3
+    assert np.log2(diff[0] / diff[1]) > 1.8
+
+
+def test_semi_enclosed_p0_ode_follows_the_mass_inventory_of_a_filling_chamber():
+    """A chamber filled through its bottom side, with no outlet: the ODE of
+    Eq 2.38 sees the inflow only through p0 int div v = -p0 U_in A, while the
+    mass inventory m(t) = m(0) + int rho_in U_in A dt (rho_in = p0 / T_in)
+    gives p0 = m / int 1/T dV (Eq 2.40 with a growing mass).  The two agree at
+    second order under refinement."""
+    from oracle.operators import integrate
+    diff = []
+    for n in (16, 32):
+        prm, geo, f = W.filling_chamber(n)
+        prm["poisson_rtol"] = 1e-12
+        pb, st, hist = _p0_after(prm, geo, f, 0.1)
+        g = pb.g
+        T_in, U_in = pb.inflow_temperature(), prm["inflow_v"][1]
+        m0 = integrate(1.0 / V(S.initial_state(pb, f["v"], f["Z"], f["H"]).T, g), g)
+        inflow = np.sum(0.5 * (hist[1:] + hist[:-1])) * prm["dt"] * U_in * 1.0 / T_in
+        p_inv = (m0 + inflow) / integrate(1.0 / V(st.T, g), g)
+        assert hist[-1] > 1.5
+        diff.append(abs(hist[-1] - p_inv))
+    assert diff[1] < 1e-2
+    assert np.log2(diff[0] / diff[1]) > 1.8
