@@ -88,7 +88,11 @@ typedef struct {
     double Z_st;             /* stoichiometric conventional mixture fraction: S = 1/Z_st - 1 */
     double density_ratio;    /* flame / ambient temperature: Q = (ratio - 1)(S + 1)     */
     double eps_reg, tol_reg; /* regularisation: k = ln((1-tol)/tol) / (2 eps) (Eq 3.34)  */
-    int closed_system;       /* 1: p0 from the mass constraint (Eq 2.40); 0: p0 = 1 (Eq 2.41) */
+    int closed_system;       /* 0: open, p0 = 1 (Eq 2.41); 1: enclosed, p0 from the mass
+                                constraint (Eq 2.40), no inflow or outflow sides;
+                                2: semi-enclosed, p0 advanced by the ODE of Eq 2.38
+                                (AB2 predictor, AM2 corrector), inflow sides allowed,
+                                no outflow sides and no immersed body               */
     int incompressible;      /* 1: T = rho = kappa = p0 = 1 (constant-density runs)     */
     double dt;               /* fixed time step (> 0)                                   */
     int precision;           /* SIM_FP64: every kernel in FP64.  SIM_MIXED: the stage

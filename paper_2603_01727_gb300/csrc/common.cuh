@@ -86,7 +86,10 @@ struct Phys {
     double inflow_v[3], inflow_Z, inflow_H;
     double cA, cB, cT;                 // T = cT (cA (|x| + log1p(e^-2|x|)) + cB (Z - 1) + H), Eq 3.42
     double iPe, iLePe;                 // 1/Pe, 1/(Le Pe) (uniform Le)
-    int incompressible, closed;
+    int incompressible, closed;        // closed: p0 != 1 (enclosed, Eq 2.40, or semi-enclosed)
+    int semi;                          // semi-enclosed: p0 from the ODE of Eq 2.38
+    double NpF, NpO;                   // N'_F = -1/S, N'_O = 1 (Eq 2.39)
+    double ode_gV, ode_heat;           // gamma / V and Q / ((S + 1) Pe) of Eq 2.38
     int mixed;                         // 1: FP32 stencil arithmetic and multigrid (SIM_MIXED)
     int sigma_is_07;                   // sigma == 0.7 exactly (paper value, Eq 2.50)
     int transport;                     // 0: kappa = T^sigma (Eq 2.50); 1: Sutherland (Eq 4.12)

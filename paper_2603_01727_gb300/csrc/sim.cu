@@ -76,6 +76,7 @@ struct sim {
     double* diag;          // per-step check partials and results
     double* part;
     double* part2;
+    double* ode_part;                     // block partials of Eq 2.38's sums (semi-enclosed)
     double* sc;
     double* profile;
     int* status;
@@ -202,7 +203,16 @@ Phys make_phys(const sim_params_t* p) {
     ph.inflow_Z = p->inflow_Z;
     ph.inflow_H = p->inflow_H;
     ph.incompressible = p->incompressible;
-    ph.closed = p->closed_system && !p->incompressible;
+    ph.closed = p->closed_system != 0 && !p->incompressible;
+    ph.semi = p->closed_system == 2 && !p->incompressible;
+    ph.NpF = -1.0 / ph.S;                                        // Eq 2.39
+    ph.NpO = 1.0;
+    {
+        double vol = 1.0;
+        for (int d = 0; d < p->dim; ++d) vol *= p->L[d];
+        ph.ode_gV = p->gamma / vol;                              // Eq 2.38
+        ph.ode_heat = ph.Q / ((ph.S + 1.0) * ph.Pe);
+    }
     bool inflow = false;
     for (int d = 0; d < p->dim; ++d)
         for (int q = 0; q < 2; ++q) inflow |= (p->bc[d][q] == SIM_BC_INFLOW);
@@ -258,11 +268,19 @@ const char* validate(const sim_params_t* p) {
                                  (p->stage_tile_x & (p->stage_tile_x - 1)) != 0))
         return "stage_tile_x must be 0 or a power of two from 8 to 256";
     if (p->precision != SIM_FP64 && p->precision != SIM_MIXED) return "precision must be SIM_FP64 or SIM_MIXED";
-    if (p->closed_system) {
+    if (p->closed_system < 0 || p->closed_system > 2)
+        return "closed_system must be 0 (open), 1 (enclosed) or 2 (semi-enclosed)";
+    if (p->closed_system == 1) {
         for (int d = 0; d < p->dim; ++d)
             for (int q = 0; q < 2; ++q)
                 if (p->bc[d][q] == SIM_BC_INFLOW || p->bc[d][q] == SIM_BC_OUTFLOW)
                     return "an enclosed system cannot have inflow or outflow sides";
+    }
+    if (p->closed_system == 2) {
+        for (int d = 0; d < p->dim; ++d)
+            for (int q = 0; q < 2; ++q)
+                if (p->bc[d][q] == SIM_BC_OUTFLOW)
+                    return "a semi-enclosed system has no outflow sides (its outflow would close the mass balance)";
     }
     return nullptr;
 }
@@ -333,6 +351,8 @@ size_t layout(const sim_params_t* p, sim_t* s, char* base) {
         if (s) s->part = q;
         q = (double*)take(sizeof(double) * kMaxPartials);
         if (s) s->part2 = q;
+        q = (double*)take(sizeof(double) * 2 * kMaxPartials);
+        if (s) s->ode_part = q;
         q = (double*)take(sizeof(double) * kMaxProfile);
         if (s) s->profile = q;
         uint8_t* c = (uint8_t*)take((size_t)g.npad);
@@ -435,6 +455,8 @@ cudaError_t enqueue_init(sim_t* s, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     double ones[3] = {1.0, 1.0, 1.0};
     e = cudaMemcpyAsync(s->sc + SC_P0_NM1, ones, sizeof(double) * 2, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(s->sc + SC_G_N, 0, sizeof(double) * 2, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(s->status, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -686,6 +708,10 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     // an open system (p0 = 1) forms its state and face fluxes in one kernel
     const bool fuse = !s->ph.closed;
     if (on(SEC_PRED)) {
+        // semi-enclosed: p0* from Eq 2.38 on level n's fields
+        if (s->ph.semi)
+            launch_p0_ode(g, s->ph, s->Z, s->H, s->kap, s->v, s->ode_part, s->sc,
+                          n == 0 ? ODE_PRED_EULER : ODE_PRED_AB2, dt, SC_P0_STAR, st, L);
         launch_residual(g, s->ph, a, st, L);
         if (D == 3) ghost(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}}, st, L);
         if (fuse) {
@@ -726,6 +752,11 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
         // P* kept for the predictor-corrector difference (per-step checks)
         e = stage_copy(s->P, s->Pstar, g.ncell, st);
         if (e != cudaSuccess) return e;
+        // semi-enclosed: p0^{n+1} from Eq 2.38 on the predicted fields
+        // (kappa* is overwritten by the corrector's state relation)
+        if (s->ph.semi)
+            launch_p0_ode(g, s->ph, s->Zs, s->Hs, s->kap, s->vs, s->ode_part, s->sc, ODE_CORR, dt, SC_P0_NEW,
+                          st, L);
     }
     if (on(SEC_MID) && s->adj_save) {
         // predictor values read by the reverse pass (overwritten by the corrector)
@@ -989,6 +1020,9 @@ sim_status sim_set_ibm_geometry(sim_t* s, const sim_ibm_t* geo) {
     }
     if (geo->kind != SIM_IBM_SLOT && geo->kind != SIM_IBM_SPHERE && geo->kind != SIM_IBM_MARKERS)
         return fail(s, SIM_EINVAL, "unknown body kind %d", geo->kind);
+    if (s->ph.semi)
+        return fail(s, SIM_EINVAL, "a semi-enclosed system takes no immersed body (Eq 2.38 has no penalisation "
+                                   "or mass-source terms)");
     const int mk_stride = 2 * s->g.dim + 2;
     if (geo->kind == SIM_IBM_MARKERS &&
         (geo->n_markers < 1 || !geo->markers || (long long)geo->n_markers * mk_stride > s->g.npad))

@@ -338,19 +338,87 @@ __global__ void __launch_bounds__(NT) k_diag_final(Geom g, DiagArgs a, int nb) {
 }
 
 // Enclosed system: p0 = m / (sum(1/T) dV) (Eq 2.40), rho = p0 / T (Eq 2.49).
+// Semi-enclosed (semi): p0 is the value the ODE of Eq 2.38 left in the slot.
 __global__ void k_density(Geom g, const double* __restrict__ T, double* __restrict__ rho,
-                          const double* __restrict__ part, int np, double* sc, int p0_slot, int mixed) {
+                          const double* __restrict__ part, int np, double* sc, int p0_slot, int mixed, int semi) {
     __shared__ double sm[NT / 32];
-    const double s = sum_partials<NT>(part, np, sm);
-    const double p0 = sc[SC_MASS] / (s * g.dV);
+    double p0;
+    if (semi) {
+        p0 = sc[p0_slot];
+    } else {
+        const double s = sum_partials<NT>(part, np, sm);
+        p0 = sc[SC_MASS] / (s * g.dV);
+    }
     for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
         const long long c = pad_index(g, t);
         rho[c] = mixed ? p0 * recip_newton(T[c]) : p0 / T[c];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !semi) {
         sc[p0_slot] = p0;
         sc[p0_slot + SC_INV_OFF] = 1.0 / p0;
     }
+}
+
+// Semi-enclosed system, Eq 2.38: block partials of the two volume sums of
+//   G = gamma / V { Q / ((S+1) Pe) sum [div(kappa grad H) + N' div(kappa grad Z)] dV - p0 sum div v dV },
+// div(kappa grad .) as the residuals' diffusion (kappa on the faces by the
+// mean of Eq 3.20, delta_1 across them), N' = (N'_F - N'_O) theta_eps(Z - 1)
+// + N'_O regularised like N (Eq 3.35b), and div v the cell-centred delta_2
+// divergence.  One FP64 pass over Z, H, kappa and v.
+template <int DIM>
+__global__ void __launch_bounds__(NT) k_p0_rate(Geom g, Phys ph, const double* __restrict__ Z,
+                                                const double* __restrict__ H, const double* __restrict__ kap,
+                                                const double* __restrict__ v0, const double* __restrict__ v1,
+                                                const double* __restrict__ v2, double* __restrict__ part) {
+    __shared__ double sm[NT / 32];
+    const double* v[3] = {v0, v1, v2};
+    double heat = 0.0, div = 0.0;
+    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < g.ncell; t += (long long)gridDim.x * NT) {
+        const long long c = pad_index(g, t);
+        const double kc = kap[c], Zc = Z[c], Hc = H[c];
+        double dH = 0.0, dZ = 0.0, dv = 0.0;
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+            const long long s = g.s[j];
+            const double kp = 0.5 * (kc + kap[c + s]), km = 0.5 * (kc + kap[c - s]);
+            dH += (kp * (H[c + s] - Hc) - km * (Hc - H[c - s])) * g.ih[j] * g.ih[j];
+            dZ += (kp * (Z[c + s] - Zc) - km * (Zc - Z[c - s])) * g.ih[j] * g.ih[j];
+            dv += (v[j][c + s] - v[j][c - s]) * (0.5 * g.ih[j]);
+        }
+        const double th = 0.5 * (1.0 + tanh(ph.k * (Zc - 1.0)));
+        heat += dH + ((ph.NpF - ph.NpO) * th + ph.NpO) * dZ;
+        div += dv;
+    }
+    heat = block_sum<NT>(heat, sm);
+    div = block_sum<NT>(div, sm);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = heat;
+        part[gridDim.x + blockIdx.x] = div;
+    }
+}
+
+// One block: the sums in index order, G, and the stage's p0 (AB2 predictor,
+// AM2 corrector, as for Z and H in Eqs 3.1-3.3 and 3.12-3.13).  The
+// predictor rotates the G history (SC_G_N -> SC_G_NM1).
+__global__ void k_p0_ode(Geom g, Phys ph, const double* __restrict__ part, int np, double* sc, int stage, double dt,
+                         int out_slot) {
+    __shared__ double sm[NT / 32];
+    const double heat = sum_partials<NT>(part, np, sm) * g.dV;
+    const double div = sum_partials<NT>(part + np, np, sm) * g.dV;
+    if (threadIdx.x != 0) return;
+    const double p0_level = (stage == ODE_CORR) ? sc[SC_P0_STAR] : sc[SC_P0_N];
+    const double G = ph.ode_gV * (ph.ode_heat * heat - p0_level * div);
+    double p0;
+    if (stage == ODE_CORR) {
+        p0 = sc[SC_P0_N] + 0.5 * dt * (G + sc[SC_G_N]);
+    } else {
+        const double Gp = sc[SC_G_N];
+        sc[SC_G_NM1] = Gp;
+        sc[SC_G_N] = G;
+        p0 = sc[SC_P0_N] + dt * ((stage == ODE_PRED_AB2) ? 1.5 * G - 0.5 * Gp : G);
+    }
+    sc[out_slot] = p0;
+    sc[out_slot + SC_INV_OFF] = 1.0 / p0;
 }
 
 // ----------------------------------------------------------------------------
@@ -1953,9 +2021,20 @@ void launch_state(const Geom& g, const Phys& ph, const double* Z, const double* 
         k_state<false><<<rb, NT, 0, s>>>(g, ph, Z, H, T, rho, kap, part, status, sc, p0_slot, b, kg);
     ++*launches;
     if (ph.closed) {
-        k_density<<<rb, NT, 0, s>>>(g, T, rho, part, rb, sc, p0_slot, ph.mixed);
+        k_density<<<rb, NT, 0, s>>>(g, T, rho, part, rb, sc, p0_slot, ph.mixed, ph.semi);
         ++*launches;
     }
+}
+
+void launch_p0_ode(const Geom& g, const Phys& ph, const double* Z, const double* H, const double* kap,
+                   double* const* v, double* part, double* sc, int stage, double dt, int out_slot, cudaStream_t s,
+                   int* launches) {
+    const int rb = reduce_grid(g);
+    const double* v2 = (g.dim == 3) ? v[2] : v[0];
+    if (g.dim == 3) k_p0_rate<3><<<rb, NT, 0, s>>>(g, ph, Z, H, kap, v[0], v[1], v2, part);
+    else k_p0_rate<2><<<rb, NT, 0, s>>>(g, ph, Z, H, kap, v[0], v[1], v2, part);
+    k_p0_ode<<<1, NT, 0, s>>>(g, ph, part, rb, sc, stage, dt, out_slot);
+    *launches += 2;
 }
 
 void launch_residual(const Geom& g, const Phys& ph, const ResidArgs& a, cudaStream_t s, int* launches) {

@@ -14,6 +14,7 @@ enum : int {
     SC_P0_N = 0, SC_P0_NM1 = 1, SC_P0_NM2 = 2, SC_P0_STAR = 3, SC_P0_NEW = 4,
     SC_MASS = 5, SC_OUT_AREA = 6,
     SC_ITERS_PRED = 8, SC_RELRES_PRED = 9, SC_ITERS_CORR = 10, SC_RELRES_CORR = 11,
+    SC_G_N = 12, SC_G_NM1 = 13,   // right-hand side of Eq 2.38 at levels n, n-1 (semi-enclosed)
     SC_INV_OFF = 16,      // slot p0_slot + SC_INV_OFF holds 1 / p0 of that slot (slots 16..20)
     SC_NSCAL = 32
 };
@@ -210,6 +211,14 @@ void launch_project(const Geom& g, const Phys& ph, const ProjArgs& a, cudaStream
 void launch_momentum(const Geom& g, const double* rho, double* const v[3], double* mom[3], cudaStream_t s,
                      int* launches);
 void launch_sum(const Geom& g, const double* x, double* part, cudaStream_t s, int* launches);
+// Semi-enclosed system: G of Eq 2.38 on one level's fields (padded, ghosts
+// filled; v[d] for d < dim) and the stage update of p0 it feeds: stage 0 the
+// predictor's Euler step (step 0), 1 its AB2 step, 2 the corrector's AM2 step.
+// Writes p0 (and 1/p0) into out_slot; part holds 2 * reduce_grid(g) doubles.
+enum { ODE_PRED_EULER = 0, ODE_PRED_AB2 = 1, ODE_CORR = 2 };
+void launch_p0_ode(const Geom& g, const Phys& ph, const double* Z, const double* H, const double* kap,
+                   double* const* v, double* part, double* sc, int stage, double dt, int out_slot, cudaStream_t s,
+                   int* launches);
 void launch_store_sum(const double* part, int np, double scale, double* dst, cudaStream_t s, int* launches);
 void launch_copy_scalar(const double* src, double* dst, int n, cudaStream_t s, int* launches);
 void launch_or_status(const int* src_flag, int bit, int* status, cudaStream_t s, int* launches);

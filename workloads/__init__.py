@@ -148,24 +148,29 @@ def periodic_blobs(n=64, seed=SEED, cfl=0.4, nblobs=8):
     return prm, None, fields
 
 
-def filling_chamber(n=64, U_in=0.1, cfl=0.4, closed_system=2):
-    """2D semi-enclosed chamber (Eq 2.38): [0,1]^2, periodic in x, air (Z = 0,
-    H = H_inf) entering through the whole bottom side at v = (0, U_in), a
-    no-slip wall on top, no outlet, so that p0 rises as the chamber fills.  It
-    holds a Gaussian fuel blob (peak Z = Z_fuel, width 0.1, centre (0.5, 0.6))
-    burning in air at rest; Z_st = 0.055, density ratio 7, Le = 1, Re = 100,
-    Pr = 0.7."""
+def filling_chamber(n=64, U_in=0.1, cfl=0.4, closed_system=2, dim=2):
+    """Semi-enclosed chamber (Eq 2.38): the unit square (cube), periodic in x
+    (and z), air (Z = 0, H = H_inf) entering through the whole bottom side at
+    v_2 = U_in, a no-slip wall on top, no outlet, so that p0 rises as the
+    chamber fills.  It holds a Gaussian fuel blob (peak Z = Z_fuel, width 0.1,
+    centre (0.5, 0.6[, 0.5])) burning in air moving at v_2 = U_in;
+    Z_st = 0.055, density ratio 7, Le = 1, Re = 100, Pr = 0.7."""
     prm = _base_params()
-    prm.update(dim=2, n=[n, n, 1], L=[1.0, 1.0, 1.0], Re=100.0, Pr=0.7,
-               bc=[[PERIODIC, PERIODIC], [INFLOW, WALL], [PERIODIC, PERIODIC]],
+    bc = [[PERIODIC, PERIODIC], [INFLOW, WALL], [PERIODIC, PERIODIC]]
+    prm.update(dim=dim, n=[n, n, n if dim == 3 else 1], L=[1.0, 1.0, 1.0], Re=100.0, Pr=0.7, bc=bc,
                inflow_v=[0.0, U_in, 0.0], closed_system=closed_system)
     S, Q, H_inf, Z_fuel = paper_scalars(prm["Z_st"], prm["density_ratio"])
     prm.update(inflow_Z=0.0, inflow_H=H_inf)
-    x, y = cell_centres((n, n), (1.0, 1.0))
-    Z = Z_fuel * np.exp(-((x - 0.5) ** 2 + (y - 0.6) ** 2) / (2.0 * 0.1 ** 2))
-    prm["dt"] = stable_dt((n, n), (1.0, 1.0), prm["Re"], prm["Pr"], prm["density_ratio"], prm["sigma"],
-                          max(U_in, 0.1), cfl)
-    fields = dict(v=[np.zeros(x.shape), np.full(x.shape, U_in)], Z=Z, H=np.full(x.shape, H_inf))
+    shape = (n,) * dim
+    xs = cell_centres(shape, (1.0,) * dim)
+    centre = (0.5, 0.6, 0.5)
+    r2 = sum((xs[d] - centre[d]) ** 2 for d in range(dim))
+    Z = Z_fuel * np.exp(-r2 / (2.0 * 0.1 ** 2))
+    prm["dt"] = stable_dt(shape, (1.0,) * dim, prm["Re"], prm["Pr"], prm["density_ratio"], prm["sigma"],
+                          max(U_in, 0.1), cfl, dim=dim)
+    v = [np.zeros(Z.shape) for _ in range(dim)]
+    v[1][...] = U_in
+    fields = dict(v=v, Z=Z, H=np.full(Z.shape, H_inf))
     return prm, None, fields
 
 
