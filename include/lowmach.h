@@ -64,7 +64,7 @@ enum {
 };
 
 enum { SIM_FP64 = 0, SIM_MIXED = 1 };
-enum { SIM_IBM_NONE = 0, SIM_IBM_SLOT = 1, SIM_IBM_SPHERE = 2, SIM_IBM_MARKERS = 3 };
+enum { SIM_IBM_NONE = 0, SIM_IBM_SLOT = 1, SIM_IBM_SPHERE = 2, SIM_IBM_MARKERS = 3, SIM_IBM_COUETTE = 4 };
 
 /* Run parameters (paper notation, Eqs 2.42-2.50). */
 typedef struct {
@@ -137,12 +137,19 @@ typedef struct {
  * uniformly over the N_m masked interior cells matched with it,
  * S_m = rho_b U_m A_m / (N_m dV); SIM_EINVAL if some N_m = 0 (markers denser
  * than the cells) or if 2 dim + 2 times n_markers exceeds the padded cell
- * count.  center, half, radius, U_b and the profile are unused. */
+ * count.  center, half, radius, U_b and the profile are unused.
+ * COUETTE (the Taylor-Couette flow of Sec. 4.2.3): coaxial cylinders along
+ * x_3 through center, inner radius R_1 = radius turning rigidly with surface
+ * speed U_b (counter-clockwise about +x_3), outer radius R_2 = half[0] at
+ * rest; with r the distance in the x_1-x_2 plane, the mask is r - R_1 <= s or
+ * R_2 - r <= s (s = sqrt(Da_ib)), v_ib = (U_b/R_1)(-(x_2-c_2), x_1-c_1) in the
+ * inner body and 0 in the outer, S_m = 0.  SIM_EINVAL unless
+ * 0 < radius < half[0]. */
 typedef struct {
     int kind;                /* SIM_IBM_*                                              */
     double center[3];
-    double half[3];          /* SLOT half-sizes                                        */
-    double radius;           /* SPHERE radius                                          */
+    double half[3];          /* SLOT half-sizes; COUETTE: half[0] = outer radius R_2    */
+    double radius;           /* SPHERE radius; COUETTE: inner radius R_1               */
     double Da_ib;            /* immersed-boundary Darcy number (> 0)                   */
     double rho_b, U_b;       /* ejected density and velocity scale                     */
     double Z_ib, H_ib;       /* body targets in the paper's variables (Eq 4.21)        */

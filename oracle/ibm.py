@@ -27,13 +27,21 @@ H_ib, and mass source S_m.
   S_m = rho_b U_m A_m / (N_m dV), so the discrete integral of S_m equals the
   total sum_m rho_b U_m A_m exactly; every marker needs N_m >= 1 (markers no
   denser than the cells).
+* Coaxial cylinders (the Taylor-Couette flow of Sec. 4.2.3), axis along x_3
+  through the centre: the inner cylinder r <= R_1 turns rigidly with surface
+  speed U_b (counter-clockwise about +x_3), the outer body r >= R_2 is at
+  rest, the fluid fills the gap.  With r the distance in the x_1-x_2 plane,
+  each solid is extended into the gap by s: chi = 1 iff r - R_1 <= s or
+  R_2 - r <= s; v_ib = (U_b / R_1)(-(x_2 - c_2), x_1 - c_1) in the inner
+  body, 0 in the outer; no mass source.  r is formed with explicitly
+  rounded squares and sum (the mask is an integer decision).
 """
 
 import numpy as np
 
 from .operators import V
 
-NONE, SLOT, SPHERE, MARKERS = 0, 1, 2, 3
+NONE, SLOT, SPHERE, MARKERS, COUETTE = 0, 1, 2, 3, 4
 
 
 def nearest_markers(pts, X):
@@ -132,6 +140,15 @@ def build(g, geo):
         Sm_int = chi_int * (rho_b * Um[mi] * Am[mi] / (counts[mi] * g.dV))
         Sm_full = g.zeros()
         V(Sm_full, g)[...] = Sm_int
+    elif geo["kind"] == COUETTE:
+        R1, R2 = float(geo["radius"]), float(geo["half"][0])
+        dx, dy = x[0] - c[0], x[1] - c[1]
+        r = np.sqrt(dx * dx + dy * dy)
+        inner = r - R1 <= s
+        chi = (inner | (R2 - r <= s)).astype(float)
+        w = np.where(inner, U_b / R1, 0.0)
+        vib[0] = -w * dy
+        vib[1] = w * dx
     else:
         raise ValueError("unknown body kind")
 

@@ -1018,8 +1018,11 @@ sim_status sim_set_ibm_geometry(sim_t* s, const sim_ibm_t* geo) {
         CK(cudaGetLastError());
         return SIM_OK;
     }
-    if (geo->kind != SIM_IBM_SLOT && geo->kind != SIM_IBM_SPHERE && geo->kind != SIM_IBM_MARKERS)
+    if (geo->kind != SIM_IBM_SLOT && geo->kind != SIM_IBM_SPHERE && geo->kind != SIM_IBM_MARKERS &&
+        geo->kind != SIM_IBM_COUETTE)
         return fail(s, SIM_EINVAL, "unknown body kind %d", geo->kind);
+    if (geo->kind == SIM_IBM_COUETTE && !(geo->radius > 0.0 && geo->half[0] > geo->radius))
+        return fail(s, SIM_EINVAL, "coaxial cylinders need 0 < radius < half[0]");
     if (s->ph.semi)
         return fail(s, SIM_EINVAL, "a semi-enclosed system takes no immersed body (Eq 2.38 has no penalisation "
                                    "or mass-source terms)");

@@ -946,6 +946,18 @@ __global__ void k_ibm_cells(Geom g, IbmDev b, uint8_t* chi, double* vib0, double
         for (int d = 0; d < g.dim; ++d) vib[d][c] = m * b.U_b * (x[d] - b.c[d]) / rs;
         Sm[c] = interior ? m * (double)(g.dim - 1) * b.rho_b * b.U_b / rs : 0.0;
         U[c] = 0.0;
+    } else if (b.kind == 4) {  // coaxial cylinders: inner turns rigidly, outer at rest
+        const double dx = x[0] - b.c[0], dy = x[1] - b.c[1];
+        const double r = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+        const bool inner = (r - b.radius <= b.s);
+        const bool m = inner || (b.half[0] - r <= b.s);
+        const double w = inner ? b.U_b / b.radius : 0.0;
+        chi[c] = (uint8_t)m;
+        vib[0][c] = -w * dy;
+        vib[1][c] = w * dx;
+        if (g.dim == 3) vib[2][c] = 0.0;
+        Sm[c] = 0.0;
+        U[c] = 0.0;
     } else {  // slot ejecting through its +x_2 face
         double qd[3], out2 = 0.0, qmax = -1e300;
         for (int d = 0; d < g.dim; ++d) {

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ENOMEM", -3: "SIM_ECUDA"
                 -5: "SIM_ENAN", -6: "SIM_EUNSTABLE", -7: "SIM_ESTATE"}
 SIM_BC_PERIODIC, SIM_BC_INFLOW, SIM_BC_OUTFLOW, SIM_BC_WALL, SIM_BC_SLIP, SIM_BC_WALL_T = 0, 1, 2, 3, 4, 5
 SIM_FP64, SIM_MIXED = 0, 1
-SIM_IBM_NONE, SIM_IBM_SLOT, SIM_IBM_SPHERE = 0, 1, 2
+SIM_IBM_NONE, SIM_IBM_SLOT, SIM_IBM_SPHERE, SIM_IBM_MARKERS, SIM_IBM_COUETTE = 0, 1, 2, 3, 4
 (SIM_FIELD_U, SIM_FIELD_V, SIM_FIELD_W, SIM_FIELD_Z, SIM_FIELD_H, SIM_FIELD_T, SIM_FIELD_RHO,
  SIM_FIELD_P, SIM_FIELD_FX, SIM_FIELD_FY, SIM_FIELD_FZ, SIM_FIELD_CHI, SIM_FIELD_SM,
  SIM_FIELD_KAPPA) = range(14)

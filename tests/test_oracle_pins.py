@@ -829,3 +829,36 @@ def test_semi_enclosed_p0_ode_follows_the_mass_inventory_of_a_filling_chamber():
         diff.append(abs(hist[-1] - p_inv))
     assert diff[1] < 1e-2
     assert np.log2(diff[0] / diff[1]) > 1.8
+
+
+def test_coaxial_cylinder_mask_areas_and_rigid_rotation():
+    """Coaxial-cylinder body (Sec. 4.2.3): the masked area approaches the
+    analytic area of the two shifted solids, pi (R_1 + s)^2 plus the box
+    outside r = R_2 - s, within a perimeter's worth of cells; v_ib is a rigid
+    rotation in the inner body (its delta_2 curl is exactly 2 U_b / R_1 and
+    its divergence zero wherever the whole stencil is inside) and zero in the
+    outer body; there is no mass source."""
+    from oracle.ibm import build
+    for n in (64, 128):
+        prm, geo, _ = W.taylor_couette(n, Da_ib=1e-2)
+        g = Grid(prm["n"][:2], prm["L"][:2])
+        ib = build(g, geo)
+        s = np.sqrt(geo["Da_ib"])
+        L, h = prm["L"][0], g.h[0]
+        area = np.pi * (1.0 + s) ** 2 + L * L - np.pi * (2.0 - s) ** 2
+        masked = np.sum(V(ib["chi"], g)) * g.dV
+        assert abs(masked - area) < 2.0 * np.pi * (1.0 + 2.0) * h * h * 2.0
+        assert np.all(ib["Sm"] == 0.0)
+        x = [V(g.centres(d), g) for d in range(2)]
+        r = np.sqrt((x[0] - 2.5) ** 2 + (x[1] - 2.5) ** 2)
+        u, v = ib["vib"]
+        curl = (V(v, g, off=[1, 0]) - V(v, g, off=[-1, 0])) / (2 * h) - \
+               (V(u, g, off=[0, 1]) - V(u, g, off=[0, -1])) / (2 * h)
+        div = (V(u, g, off=[1, 0]) - V(u, g, off=[-1, 0])) / (2 * h) + \
+              (V(v, g, off=[0, 1]) - V(v, g, off=[0, -1])) / (2 * h)
+        deep = r < 1.0 + s - 2.0 * h
+        assert np.allclose(curl[deep], 2.0 * geo["U_b"] / geo["radius"], rtol=1e-12, atol=0.0)
+        assert np.allclose(div[deep], 0.0, atol=1e-12)
+        outer = r > 2.0 - s
+        assert np.all(V(u, g)[outer] == 0.0) and np.all(V(v, g)[outer] == 0.0)
+        assert np.all(V(ib["chi"], g)[(r > 1.0 + s + 1e-9) & (r < 2.0 - s - 1e-9)] == 0.0)

@@ -28,7 +28,7 @@ Workloads
 import numpy as np
 
 PERIODIC, INFLOW, OUTFLOW, WALL, SLIP, WALL_T = 0, 1, 2, 3, 4, 5
-IBM_NONE, IBM_SLOT, IBM_SPHERE, IBM_MARKERS = 0, 1, 2, 3
+IBM_NONE, IBM_SLOT, IBM_SPHERE, IBM_MARKERS, IBM_COUETTE = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
 
 SEED = 20260101
@@ -328,6 +328,40 @@ def sphere_markers(center, R, count, U_b=1.0):
     A = np.full(count, 4.0 * np.pi * R * R / count)
     return np.stack([center[0] + R * nx, center[1] + R * ny, center[2] + R * nz, nx, ny, nz,
                      np.full(count, U_b), A], axis=1)
+
+
+def taylor_couette_exact(x, y, c=(0.0, 0.0)):
+    """Exact Taylor-Couette velocity for R_2 = 2 R_1 = 2 (Sec. 4.2.3):
+    v_theta = (4 - r^2)/(3 r) in the gap 1 <= r <= 2, rigid rotation
+    v_theta = r inside the inner cylinder, rest outside the outer one."""
+    dx, dy = x - c[0], y - c[1]
+    r = np.sqrt(dx * dx + dy * dy)
+    rs = np.where(r > 0.0, r, 1.0)
+    vt = np.where(r < 1.0, r, np.where(r <= 2.0, (4.0 - r * r) / (3.0 * rs), 0.0))
+    return -vt * dy / rs, vt * dx / rs
+
+
+def taylor_couette(n=128, Re=1.0, Da_ib=1e-3, L=5.0, cfl=0.4, dim=2, nz=8):
+    """Taylor-Couette flow (Sec. 4.2.3): constant density, coaxial cylinders of
+    radii 1 and 2 (eta = 1/2) centred in the periodic box [0, L]^2 (times
+    nz cells of the same spacing along the axis x_3 in 3D), the inner one
+    turning with unit surface speed, the outer one at rest; penalised with
+    the shifted mask at Da_ib.  The initial velocity is the exact solution
+    (rigid rotation in the inner body, rest in the outer)."""
+    prm = _base_params()
+    h = L / n
+    nn = [n, n, nz if dim == 3 else 1]
+    Ls = [L, L, h * nz if dim == 3 else 1.0]
+    prm.update(dim=dim, n=nn, L=Ls, Re=Re, Pr=1.0, incompressible=1)
+    c = [0.5 * L, 0.5 * L, 0.5 * Ls[2]]
+    geo = dict(kind=IBM_COUETTE, center=c[:dim], half=[2.0, 0.0, 0.0], radius=1.0, Da_ib=Da_ib,
+               rho_b=1.0, U_b=1.0, Z_ib=0.0, H_ib=0.0)
+    xs = cell_centres(tuple(nn[:dim]), tuple(Ls[:dim]))
+    u, v = taylor_couette_exact(xs[0], xs[1], c)
+    vel = [u, v] + ([np.zeros(u.shape)] if dim == 3 else [])
+    prm["dt"] = cfl * min(h / 1.0, h * h * Re / (2.0 * dim), Re * Da_ib)
+    fields = dict(v=vel, Z=np.zeros(u.shape), H=np.zeros(u.shape))
+    return prm, geo, fields
 
 
 def marker_burner(n=64, dim=2, spacing=1.5, cfl=0.4, Re=150.0, seed=SEED, rms=0.01):
