@@ -2638,6 +2638,323 @@ __global__ void __launch_bounds__(FT3) fdm(int nx, int ny, int nz, const float* 
 
 }  // namespace k3
 
+// ---------------------------------------------------------------------------
+// Colour-sweep kernels of the large 3D levels: the same smoother, residual and
+// transfers as the z-marching kernels (red from zero, black, residual,
+// restriction; prolongation-add, black, red), one whole-level pass each, so
+// that a pass costs its memory traffic instead of a chain of per-plane
+// barriers.  A thread owns an x-pair of cells (one of each colour) of a row;
+// a block of 32 x 8 pairs (256 threads, x fastest) walks zc consecutive
+// planes, so a plane's z-neighbours are the rows it read one step before and
+// reads one step after (L1).  Indices are 32-bit (levels under 2^31 cells).
+// ---------------------------------------------------------------------------
+namespace k3s {
+
+constexpr int BX = 32, BY = 8, NT = BX * BY;
+constexpr int kZC = 4;  // consecutive planes per block (default)
+
+// The x coordinate of this thread's cell of colour `color` ((x + y + z) & 1).
+__device__ __forceinline__ int pair_x(int y, int z, int color) {
+    const int x0 = 2 * (int)(blockIdx.x * BX + (threadIdx.x & (BX - 1)));
+    return x0 + ((color + x0 + y + z) & 1);
+}
+__device__ __forceinline__ int row_y() { return (int)(blockIdx.y * BY + threadIdx.x / BX); }
+
+__device__ __forceinline__ int cls_of(int g, int n, int per) { return per ? 2 : (int)(g > 0) + (int)(g < n - 1); }
+
+// A cell's index, its six neighbours' (-1 outside a non-periodic level) and
+// its class index (the diagonal's and the inverse diagonal's).
+struct Nb {
+    int i, xm, xp, ym, yp, zm, zp, cls;
+};
+template <class T>
+__device__ __forceinline__ Nb nbr(const LvT<T>& L, int x, int y, int z) {
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2], sy = nx, sz = nx * ny;
+    Nb b;
+    b.i = x + sy * y + sz * z;
+    if (x > 0 && x < nx - 1 && y > 0 && y < ny - 1 && z > 0 && z < nz - 1) {
+        b.xm = b.i - 1;
+        b.xp = b.i + 1;
+        b.ym = b.i - sy;
+        b.yp = b.i + sy;
+        b.zm = b.i - sz;
+        b.zp = b.i + sz;
+        b.cls = 26;
+        return b;
+    }
+    b.xm = (x > 0) ? b.i - 1 : (L.per[0] ? b.i + (nx - 1) : -1);
+    b.xp = (x < nx - 1) ? b.i + 1 : (L.per[0] ? b.i - (nx - 1) : -1);
+    b.ym = (y > 0) ? b.i - sy : (L.per[1] ? b.i + sy * (ny - 1) : -1);
+    b.yp = (y < ny - 1) ? b.i + sy : (L.per[1] ? b.i - sy * (ny - 1) : -1);
+    b.zm = (z > 0) ? b.i - sz : (L.per[2] ? b.i + sz * (nz - 1) : -1);
+    b.zp = (z < nz - 1) ? b.i + sz : (L.per[2] ? b.i - sz * (nz - 1) : -1);
+    b.cls = cls_of(x, nx, L.per[0]) + 3 * cls_of(y, ny, L.per[1]) + 9 * cls_of(z, nz, L.per[2]);
+    return b;
+}
+
+template <class T>
+__device__ __forceinline__ T at(const T* u, int j) {
+    return j < 0 ? (T)0 : u[j];
+}
+
+// The off-diagonal sum of the z-marching kernels' off3, in its order.
+template <class T>
+__device__ __forceinline__ T off7(const LvT<T>& L, const Nb& b, const T* u) {
+    T off = L.w[0] * (at(u, b.xm) + at(u, b.xp)) + L.w[1] * (at(u, b.ym) + at(u, b.yp));
+    off += L.w[2] * (at(u, b.zm) + at(u, b.zp));
+    return off;
+}
+
+// Red cells from a zero guess: u = f invd.
+template <class T, class TF>
+__global__ void __launch_bounds__(NT) red0(LvT<T> L, const TF* __restrict__ f, T* __restrict__ u,
+                                           const double* __restrict__ scal_r, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const TF mr = scal_r ? (TF)scal_r[PS_MEANR] : (TF)0;
+    const int y = row_y();
+    const int z1 = min((int)(blockIdx.z + 1) * zc, L.n[2]);
+    if (y >= L.n[1]) return;
+    for (int z = blockIdx.z * zc; z < z1; ++z) {
+        const int x = pair_x(y, z, 0);
+        if (x >= L.n[0]) continue;
+        const Nb b = nbr(L, x, y, z);
+        u[b.i] = (T)(f[b.i] - mr) * L.invd[b.cls];
+    }
+}
+
+// One colour of a Gauss-Seidel sweep in place (the other colour is read).
+template <class T, class TF>
+__global__ void __launch_bounds__(NT) sweep(LvT<T> L, const TF* __restrict__ f, T* u, int color,
+                                            const double* __restrict__ scal_r, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const TF mr = scal_r ? (TF)scal_r[PS_MEANR] : (TF)0;
+    const int y = row_y();
+    const int z1 = min((int)(blockIdx.z + 1) * zc, L.n[2]);
+    if (y >= L.n[1]) return;
+    for (int z = blockIdx.z * zc; z < z1; ++z) {
+        const int x = pair_x(y, z, color);
+        if (x >= L.n[0]) continue;
+        const Nb b = nbr(L, x, y, z);
+        u[b.i] = ((T)(f[b.i] - mr) + off7<T>(L, b, u)) * L.invd[b.cls];
+    }
+}
+
+// Residual r = f - A u at every cell.
+template <class T, class TF>
+__global__ void __launch_bounds__(NT) resid(LvT<T> L, const TF* __restrict__ f, const T* __restrict__ u,
+                                            T* __restrict__ r, const double* __restrict__ scal_r, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const TF mr = scal_r ? (TF)scal_r[PS_MEANR] : (TF)0;
+    const int y = row_y();
+    const int z1 = min((int)(blockIdx.z + 1) * zc, L.n[2]);
+    if (y >= L.n[1]) return;
+    for (int z = blockIdx.z * zc; z < z1; ++z) {
+#pragma unroll
+        for (int color = 0; color < 2; ++color) {
+            const int x = pair_x(y, z, color);
+            if (x >= L.n[0]) continue;
+            const Nb b = nbr(L, x, y, z);
+            r[b.i] = (T)(f[b.i] - mr) - (L.diag[b.cls] * u[b.i] - off7<T>(L, b, u));
+        }
+    }
+}
+
+// Restriction fc = R r (R = P^T / 2 per direction, times 1/8 overall),
+// separable through shared memory: a block owns a coarse tile of
+// RX x RY x RZ cells, stages its fine footprint (2 RX + 2) x (2 RY + 2) x
+// (2 RZ + 2) of r (zero outside a non-periodic level), then sums along x, y
+// and z with the 1D weights.
+constexpr int RX = 32, RY = 8, RZ = 4;
+constexpr int FX = 2 * RX + 2, FY = 2 * RY + 2, FZ = 2 * RZ + 2;
+constexpr size_t kRestrictSmem = sizeof(float) * (size_t)(FX * FY * FZ + RX * FY * FZ + RX * RY * FZ);
+
+template <class T>
+__global__ void __launch_bounds__(NT) restrict3(LvT<T> L, LvT<T> C, const T* __restrict__ r, T* __restrict__ fc) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sr = reinterpret_cast<T*>(smraw);          // [FZ][FY][FX]
+    T* sx = sr + FX * FY * FZ;                     // [FZ][FY][RX]
+    T* sy = sx + RX * FY * FZ;                     // [FZ][RY][RX]
+    __shared__ T wt[(RX + RY + RZ) * 4];           // 1D weights of the tile's coarse indices
+    const int I0 = blockIdx.x * RX, J0 = blockIdx.y * RY, K0 = blockIdx.z * RZ;
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    {
+        const int t = threadIdx.x;
+        if (t < RX) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) wt[4 * t + a] = (T)rweight(a, I0 + t, C.n[0], C.per[0]);
+        } else if (t < RX + RY) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) wt[4 * t + a] = (T)rweight(a, J0 + t - RX, C.n[1], C.per[1]);
+        } else if (t < RX + RY + RZ) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) wt[4 * t + a] = (T)rweight(a, K0 + t - RX - RY, C.n[2], C.per[2]);
+        }
+    }
+    // the fine footprint, one row of FX per warp step (lanes over x), zero
+    // outside a non-periodic level
+    constexpr int MX = (FX + 31) / 32;
+    int gx[MX];
+    bool okx[MX];
+#pragma unroll
+    for (int m = 0; m < MX; ++m) {
+        int g = 2 * I0 - 1 + lane + 32 * m;
+        bool ok = lane + 32 * m < FX;
+        if (g < 0 || g >= nx) {
+            ok = ok && L.per[0];
+            g = g < 0 ? g + nx : g - nx;
+        }
+        okx[m] = ok && g >= 0 && g < nx;
+        gx[m] = g;
+    }
+#pragma unroll 2
+    for (int row = warp; row < FY * FZ; row += NT / 32) {
+        const int b = row % FY, c = row / FY;
+        int gy = 2 * J0 - 1 + b, gz = 2 * K0 - 1 + c;
+        bool ok = true;
+        if (gy < 0 || gy >= ny) {
+            ok = ok && L.per[1];
+            gy = gy < 0 ? gy + ny : gy - ny;
+        }
+        if (gz < 0 || gz >= nz) {
+            ok = ok && L.per[2];
+            gz = gz < 0 ? gz + nz : gz - nz;
+        }
+        ok = ok && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+        const T* src = r + (long long)nx * (gy + (long long)ny * gz);
+        T v[MX];
+#pragma unroll
+        for (int m = 0; m < MX; ++m) v[m] = (ok && okx[m]) ? __ldg(src + gx[m]) : (T)0;
+#pragma unroll
+        for (int m = 0; m < MX; ++m)
+            if (lane + 32 * m < FX) sr[row * FX + lane + 32 * m] = v[m];
+    }
+    __syncthreads();
+    // x: lane = coarse column i (NT and RX are multiples of 32)
+    {
+        const T w0 = wt[4 * lane], w1 = wt[4 * lane + 1], w2 = wt[4 * lane + 2], w3 = wt[4 * lane + 3];
+        for (int q = warp; q < FY * FZ; q += NT / 32) {
+            const T* rowp = sr + q * FX + 2 * lane;
+            T v = (T)0;
+            v += w0 * rowp[0];
+            v += w1 * rowp[1];
+            v += w2 * rowp[2];
+            v += w3 * rowp[3];
+            sx[q * RX + lane] = v;
+        }
+    }
+    __syncthreads();
+    for (int q = warp; q < RY * FZ; q += NT / 32) {
+        const int j = q % RY, c = q / RY;
+        const T* wy = wt + 4 * (RX + j);
+        T v = (T)0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) v += wy[b] * sx[(c * FY + 2 * j + b) * RX + lane];
+        sy[q * RX + lane] = v;
+    }
+    __syncthreads();
+    for (int q = warp; q < RY * RZ; q += NT / 32) {
+        const int j = q % RY, k = q / RY;
+        const int I = I0 + lane, J = J0 + j, K = K0 + k;
+        if (I >= C.n[0] || J >= C.n[1] || K >= C.n[2]) continue;
+        const T* wz = wt + 4 * (RX + RY + k);
+        T v = (T)0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v += wz[c] * sy[((2 * k + c) * RY + j) * RX + lane];
+        fc[I + C.n[0] * (J + C.n[1] * K)] = v * (T)0.125;
+    }
+}
+
+// u += P uc at every cell (in place).
+template <class T>
+__global__ void __launch_bounds__(NT) prolong_add(LvT<T> L, LvT<T> C, const T* __restrict__ uc, T* u, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const int y = row_y();
+    const int z1 = min((int)(blockIdx.z + 1) * zc, L.n[2]);
+    if (y >= L.n[1]) return;
+    for (int z = blockIdx.z * zc; z < z1; ++z) {
+#pragma unroll
+        for (int color = 0; color < 2; ++color) {
+            const int x = pair_x(y, z, color);
+            if (x >= L.n[0]) continue;
+            const int gw[3] = {x, y, z};
+            const int i = x + L.n[0] * (y + L.n[1] * z);
+            u[i] = u[i] + prolong_at<T, 3>(C, uc, gw);
+        }
+    }
+}
+
+// The red half of the post-smoothing, reading u_in (black already swept),
+// writing every cell of u_out; on the fine level also r.z and sum z, whose
+// last block forms beta, r.z and mean z as the z-marching up does.
+template <class T, class TF, bool FINE>
+__global__ void __launch_bounds__(NT) red_out(LvT<T> L, const TF* __restrict__ f, const T* __restrict__ u_in,
+                                              T* __restrict__ u_out, double* part_rz, double* part_sz, double* scal,
+                                              const int* ictl, unsigned int* cnt, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const TF mr = FINE ? (TF)scal[PS_MEANR] : (TF)0;
+    TF rz = (TF)0, sz = (TF)0;
+    const int y = row_y();
+    const int z1 = min((int)(blockIdx.z + 1) * zc, L.n[2]);
+    if (y < L.n[1]) {
+        for (int z = blockIdx.z * zc; z < z1; ++z) {
+#pragma unroll
+            for (int color = 0; color < 2; ++color) {
+                const int x = pair_x(y, z, color);
+                if (x >= L.n[0]) continue;
+                const Nb b = nbr(L, x, y, z);
+                const TF fv = f[b.i] - mr;
+                const T u = (color == 0) ? ((T)fv + off7<T>(L, b, u_in)) * L.invd[b.cls] : u_in[b.i];
+                u_out[b.i] = u;
+                if (FINE) {
+                    rz = fma(fv, (TF)u, rz);
+                    sz += (TF)u;
+                }
+            }
+        }
+    }
+    if (FINE) {
+        __shared__ double red[2 * (NT / 32)];
+        __shared__ float redf[2 * (NT / 32)];
+        double brz, bsz;
+        block_sum2_any<NT>(rz, sz, red, redf, &brz, &bsz);
+        const int nb = gridDim.x * gridDim.y * gridDim.z;
+        const int bl = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        if (threadIdx.x == 0) {
+            part_rz[bl] = brz;
+            part_sz[bl] = bsz;
+        }
+        if (arrive_last_n(cnt, (unsigned int)nb)) {
+            double RZ, SZ;
+            sum_parts2_cg<NT>(part_rz, part_sz, nb, red, &RZ, &SZ);
+            if (threadIdx.x == 0) {
+                const int it = ictl[PI_IT];
+                scal[PS_BETA] = (it == 0) ? 0.0 : RZ / scal[PS_RZ];
+                scal[PS_RZ] = RZ;
+                scal[PS_MEANZ] = SZ / (double)L.N;
+                *cnt = 0u;
+            }
+        }
+    }
+}
+
+inline dim3 grid_of(const int n[3], int zc = kZC) {
+    const int npx = (n[0] + 1) / 2;
+    return dim3((unsigned)((npx + BX - 1) / BX), (unsigned)((n[1] + BY - 1) / BY), (unsigned)((n[2] + zc - 1) / zc));
+}
+inline dim3 restrict_grid(const int nc[3]) {
+    return dim3((unsigned)((nc[0] + RX - 1) / RX), (unsigned)((nc[1] + RY - 1) / RY), (unsigned)((nc[2] + RZ - 1) / RZ));
+}
+
+}  // namespace k3s
+
 // ------------------------------ host helpers --------------------------------
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -2750,9 +3067,10 @@ dim3 k3_tile_grid(const int n[3], int tile) {
     return dim3((n[0] + tile - 1) / tile, (n[1] + tile - 1) / tile, (n[2] + k3::ZU - 1) / k3::ZU);
 }
 long long k3_blocks(const int n[3]) {
-    const dim3 a = k3_tile_grid(n, k3::FU), b = k3_tile_grid(n, k3::FP);
-    const long long na = (long long)a.x * a.y * a.z, nb = (long long)b.x * b.y * b.z;
-    return na > nb ? na : nb;
+    const dim3 a = k3_tile_grid(n, k3::FU), b = k3_tile_grid(n, k3::FP), c = k3s::grid_of(n, 1);
+    const long long na = (long long)a.x * a.y * a.z, nb = (long long)b.x * b.y * b.z,
+                    nc = (long long)c.x * c.y * c.z;
+    return std::max(na, std::max(nb, nc));
 }
 
 template <int DIM>
@@ -2941,6 +3259,8 @@ void set_smem_attrs() {
                          2 * pl3 * (int)sizeof(T));
     cudaFuncSetAttribute(k3::up<T, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pl3 * (int)sizeof(T));
     cudaFuncSetAttribute(k3::pq<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl3 * (int)sizeof(double));
+    cudaFuncSetAttribute(k3s::restrict3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(k3s::kRestrictSmem * (sizeof(T) / 4)));
     cudaFuncSetAttribute(k2::fdm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
     cudaFuncSetAttribute(k3::fdm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
 }
@@ -3077,6 +3397,14 @@ bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const dou
         // levels below this many cells keep the cube tiles (too few z-marching blocks)
         const char* m = std::getenv("LOWMACH_MG3_MIN_CELLS");
         pl->mg3_min_cells = (m && std::atoll(m) >= 0) ? std::atoll(m) : kMg3MinCells;
+        // those levels on whole-level colour-sweep passes (LOWMACH_MG3_SWEEPS=0:
+        // the z-marching kernels, which read each array once but serialise a
+        // block's planes behind barriers; C3 192^3 mixed 16.77 -> 15.60 ms,
+        // FP64 57.6 -> 48.0 ms per step)
+        const char* w = std::getenv("LOWMACH_MG3_SWEEPS");
+        pl->mg3_sweeps = (w && w[0] == '0') ? 0 : 1;
+        const char* zc = std::getenv("LOWMACH_K3S_ZC");
+        pl->k3s_zc = (zc && std::atoi(zc) >= 1 && std::atoi(zc) <= 64) ? std::atoi(zc) : k3s::kZC;
     }
     pl->nb = nb;
     pl->r = (double*)take(B * sizeof(double) * pl->N);
@@ -3315,6 +3643,34 @@ void enqueue_down(PoissonPlan* pl, int l, cudaStream_t s) {
             }
         }
         enqueue_down2<T, 1>(pl, l, L, C, fc, s);
+    } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells && pl->mg3_sweeps && pl->nb == 1) {
+        // colour-sweep passes; the residual goes through z (not live during the
+        // down pass: the previous iteration's z was consumed by its pq)
+        const int zc = pl->k3s_zc;
+        const dim3 grid = k3s::grid_of(L.n, zc);
+        T* u = (l == 0) ? (T*)pl->u0pre : (T*)pl->lev[l].upre;
+        T* r = (T*)pl->z;
+        const double* sr = pl->scal;
+        if (l == 0 && ir) {
+            const float* f = pl->r32;
+            launch(k3s::red0<T, float>, grid, k3s::NT, 0, s, L, f, u, sr, zc);
+            launch(k3s::sweep<T, float>, grid, k3s::NT, 0, s, L, f, u, 1, sr, zc);
+            launch(k3s::resid<T, float>, grid, k3s::NT, 0, s, L, f, (const T*)u, r, sr, zc);
+        } else if (l == 0) {
+            const double* f = pl->r;
+            launch(k3s::red0<T, double>, grid, k3s::NT, 0, s, L, f, u, sr, zc);
+            launch(k3s::sweep<T, double>, grid, k3s::NT, 0, s, L, f, u, 1, sr, zc);
+            launch(k3s::resid<T, double>, grid, k3s::NT, 0, s, L, f, (const T*)u, r, sr, zc);
+        } else {
+            const T* f = (const T*)pl->lev[l].f;
+            const double* nsr = nullptr;
+            launch(k3s::red0<T, T>, grid, k3s::NT, 0, s, L, f, u, nsr, zc);
+            launch(k3s::sweep<T, T>, grid, k3s::NT, 0, s, L, f, u, 1, nsr, zc);
+            launch(k3s::resid<T, T>, grid, k3s::NT, 0, s, L, f, (const T*)u, r, nsr, zc);
+        }
+        launch(k3s::restrict3<T>, k3s::restrict_grid(C.n), k3s::NT, k3s::kRestrictSmem * (sizeof(T) / 4), s, L, C,
+               (const T*)r, fc);
+        pl->launches += 3;
     } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells) {
         const dim3 grid = k3_down_grid(pl->lev[l + 1].n);
         const size_t smem = 3 * k3::RING * k3::SB * k3::SB * sizeof(T);
@@ -3355,6 +3711,27 @@ void enqueue_up(PoissonPlan* pl, int l, cudaStream_t s) {
             }
         }
         enqueue_up2<T, 1>(pl, l, L, C, uc, s);
+    } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells && pl->mg3_sweeps && pl->nb == 1) {
+        const int zc = pl->k3s_zc;
+        const dim3 grid = k3s::grid_of(L.n, zc);
+        T* u = (l == 0) ? (T*)pl->u0pre : (T*)pl->lev[l].upre;
+        launch(k3s::prolong_add<T>, grid, k3s::NT, 0, s, L, C, uc, u, zc);
+        if (l == 0 && ir) {
+            launch(k3s::sweep<T, float>, grid, k3s::NT, 0, s, L, (const float*)pl->r32, u, 1, (const double*)pl->scal, zc);
+            launch(k3s::red_out<T, float, true>, grid, k3s::NT, 0, s, L, (const float*)pl->r32, (const T*)u,
+                   (T*)pl->z, pl->part0, pl->part1, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_UP0, zc);
+        } else if (l == 0) {
+            launch(k3s::sweep<T, double>, grid, k3s::NT, 0, s, L, (const double*)pl->r, u, 1, (const double*)pl->scal, zc);
+            launch(k3s::red_out<T, double, true>, grid, k3s::NT, 0, s, L, (const double*)pl->r, (const T*)u,
+                   (T*)pl->z, pl->part0, pl->part1, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_UP0, zc);
+        } else {
+            const T* f = (const T*)pl->lev[l].f;
+            launch(k3s::sweep<T, T>, grid, k3s::NT, 0, s, L, f, u, 1, (const double*)nullptr, zc);
+            launch(k3s::red_out<T, T, false>, grid, k3s::NT, 0, s, L, f, (const T*)u, (T*)pl->lev[l].upost,
+                   (double*)nullptr, (double*)nullptr, (double*)nullptr, (const int*)nullptr,
+                   (unsigned int*)nullptr, zc);
+        }
+        pl->launches += 2;
     } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells) {
         const dim3 grid = k3_tile_grid(pl->lev[l].n, k3::FU);
         const size_t smem = 2 * k3::RING * k3::SB * k3::SB * sizeof(T);

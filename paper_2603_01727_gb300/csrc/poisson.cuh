@@ -70,6 +70,8 @@ struct PoissonPlan {
     int sweeps;           // red-black sweeps per pre / post smoothing (2D kernels)
     int mg3_tiles;        // 1: cube-tile 3D level kernels instead of the z-marching ones
     long long mg3_min_cells;  // 3D levels with fewer cells use the cube tiles
+    int mg3_sweeps;       // 1: those levels on whole-level colour-sweep passes instead of z-marching
+    int k3s_zc;           // consecutive planes per block of the colour-sweep passes
     MgLevel lev[kMaxLevels];
     long long N;          // fine cells
     double* r;            // FP64 Krylov vectors on the fine level

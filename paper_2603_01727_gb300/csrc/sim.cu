@@ -77,6 +77,7 @@ struct sim {
     double* part;
     double* part2;
     double* ode_part;                     // block partials of Eq 2.38's sums (semi-enclosed)
+    float2* ffs;                          // 3D mixed: float-float images of the stencil inputs (or null)
     double* sc;
     double* profile;
     int* status;
@@ -338,6 +339,12 @@ size_t layout(const sim_params_t* p, sim_t* s, char* base) {
     for (int d = 0; d < D; ++d) F(&t->vib[d]);
     F(&t->Sm);
     F(&t->U);
+    {
+        // 3D mixed path: the stage stencil's float-float input images
+        float2* im = nullptr;
+        if (D == 3 && p->precision == SIM_MIXED) im = (float2*)take(sizeof(float2) * 6 * (size_t)g.npad);
+        if (s) s->ffs = im;
+    }
     {
         double* q = (double*)take(fcmp);
         if (s) s->Pstar = q;
@@ -628,6 +635,14 @@ ResidArgs resid_common(sim_t* s) {
     return a;
 }
 
+// The 3D mixed stage stencil reads float-float images of its inputs (one
+// split per value instead of one per use); LOWMACH_FF_IMAGES=0 splits on load.
+bool use_ff_images(const sim_t* s) {
+    if (!s->ffs) return false;
+    const char* e = std::getenv("LOWMACH_FF_IMAGES");
+    return !(e && e[0] == '0');
+}
+
 // Sections of a step, in order: SEC_PRED (predictor up to the right-hand
 // side), SEC_POIS_PRED (its pressure solve), SEC_MID (predictor projection to
 // the corrector's right-hand side), SEC_POIS_CORR, SEC_END (corrector
@@ -681,6 +696,7 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     // ghost cells of Z*, H*, kappa, v are filled by the kernels that write them
     a.bnd = s->bnd;
     a.gj = job_of(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}});
+    a.ffs = use_ff_images(s) ? s->ffs : nullptr;
     if (D == 3) a.gj.nf = 0;   // 3D: separate ghost fills (the 3D kernels run faster without)
     FluxArgs fa;
     std::memset(&fa, 0, sizeof(fa));
@@ -712,6 +728,10 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
         if (s->ph.semi)
             launch_p0_ode(g, s->ph, s->Z, s->H, s->kap, s->v, s->ode_part, s->sc,
                           n == 0 ? ODE_PRED_EULER : ODE_PRED_AB2, dt, SC_P0_STAR, st, L);
+        if (a.ffs) {
+            const double* src[6] = {s->v[0], s->v[1], D == 3 ? s->v[2] : nullptr, s->Z, s->H, s->kap};
+            launch_ff_images(g, src, s->ffs, st, L);
+        }
         launch_residual(g, s->ph, a, st, L);
         if (D == 3) ghost(s, {{s->Zs, GW_Z}, {s->Hs, GW_H}}, st, L);
         if (fuse) {
@@ -804,9 +824,14 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     c.iwden = 1.0 / c.wden;
     c.bnd = s->bnd;
     c.gj = job_of(s, {{s->Z, GW_Z}, {s->H, GW_H}});
+    c.ffs = a.ffs;
     if (D == 3) c.gj.nf = 0;
     fa.p0_slot = SC_P0_NEW;
     if (on(SEC_MID)) {
+        if (c.ffs) {
+            const double* src[6] = {s->vs[0], s->vs[1], D == 3 ? s->vs[2] : nullptr, s->Zs, s->Hs, s->kap};
+            launch_ff_images(g, src, s->ffs, st, L);
+        }
         launch_residual(g, s->ph, c, st, L);
         if (D == 3) ghost(s, {{s->Z, GW_Z}, {s->H, GW_H}}, st, L);
         if (fuse) {

@@ -452,6 +452,39 @@ struct PlainLoad {
     }
 };
 
+// Float-float loads with the six stencil fields read from their split
+// images (launch_ff_images), which the stencil reads up to 19 times per cell:
+// the same values as splitting on load, without the integer split per use.
+struct ImageLoad {
+    const ResidArgs* a;
+    long long np;
+    __device__ __forceinline__ FF operator()(int f, long long i) const {
+        int p;
+        switch (f) {
+            case RF_V0: p = 0; break;
+            case RF_V1: p = 1; break;
+            case RF_V2: p = 2; break;
+            case RF_Z: p = 3; break;
+            case RF_H: p = 4; break;
+            case RF_KAP: p = 5; break;
+            default: return FF(PlainLoad{a}(f, i));
+        }
+        const float2 w = __ldg(a->ffs + (long long)p * np + i);
+        return FF(w.x, w.y);
+    }
+};
+
+__global__ void k_ff_images(long long npad, int nf, FFSrc src, float2* __restrict__ dst) {
+    for (long long p = (long long)blockIdx.x * NT + threadIdx.x; p < npad; p += (long long)gridDim.x * NT) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            if (!src.f[f]) continue;
+            const FF w(src.f[f][p]);
+            dst[(long long)f * npad + p] = make_float2(w.hi, w.lo);
+        }
+    }
+}
+
 // Stage residuals at padded cell c (Eqs 3.1-3.4, 3.7-3.8, 3.26, 3.30-3.32):
 // R[i] = Res_v,i + f_v,i + F_v,i (i < DIM), R[3] = Res_Z, R[4] = Res_H.  C is
 // the arithmetic type (double, or a dual number for the adjoint); ld(f, i)
@@ -591,8 +624,9 @@ struct ResidMinBlocks<2, FF> {
     static constexpr int v = 4;
 };
 
-// The stage stencil and combination of the cells of block bx (NT cells).
-template <int DIM, class C>
+// The stage stencil and combination of the cells of block bx (NT cells);
+// IMG: float-float stencil inputs from their split images.
+template <int DIM, class C, bool IMG = false>
 __device__ __forceinline__ void residual_body(const Geom& g, const Phys& ph, const ResidArgs& a, int bx) {
     // the linear cell map: the tiled one (stage_tile_x) costs the register-capped
     // float-float stencil spills (96 -> 848 bytes in 3D) and gained nothing
@@ -610,7 +644,8 @@ __device__ __forceinline__ void residual_body(const Geom& g, const Phys& ph, con
     const double p0dot = (a.wden != 0.0) ? (a.w0 * a.sc[a.p0a] + a.w1 * a.sc[a.p0b] + a.w2 * a.sc[a.p0c]) * a.iwden
                                          : 0.0;
     C Rall[5];
-    residual_cell<DIM, C>(g, ph, a, c, p0dot, PlainLoad{&a}, Rall);
+    if constexpr (IMG) residual_cell<DIM, C>(g, ph, a, c, p0dot, ImageLoad{&a, g.npad}, Rall);
+    else residual_cell<DIM, C>(g, ph, a, c, p0dot, PlainLoad{&a}, Rall);
     double Rv[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) Rv[i] = (double)Rall[i];
@@ -651,9 +686,9 @@ __device__ __forceinline__ void residual_body(const Geom& g, const Phys& ph, con
     }
 }
 
-template <int DIM, class C>
+template <int DIM, class C, bool IMG = false>
 __global__ void __launch_bounds__(NT, ResidMinBlocks<DIM, C>::v) k_residual(Geom g, Phys ph, ResidArgs a) {
-    residual_body<DIM, C>(g, ph, a, blockIdx.x);
+    residual_body<DIM, C, IMG>(g, ph, a, blockIdx.x);
 }
 
 // ----------------------------------------------------------------------------
@@ -2038,6 +2073,15 @@ void launch_state(const Geom& g, const Phys& ph, const double* Z, const double* 
     }
 }
 
+void launch_ff_images(const Geom& g, const double* const src[6], float2* dst, cudaStream_t s, int* launches) {
+    FFSrc fs;
+    for (int f = 0; f < 6; ++f) fs.f[f] = (f == 2 && g.dim == 2) ? nullptr : src[f];
+    long long nb = (g.npad + NT - 1) / NT;
+    if (nb > 8 * 152) nb = 8 * 152;
+    k_ff_images<<<(int)nb, NT, 0, s>>>(g.npad, 6, fs, dst);
+    ++*launches;
+}
+
 void launch_p0_ode(const Geom& g, const Phys& ph, const double* Z, const double* H, const double* kap,
                    double* const* v, double* part, double* sc, int stage, double dt, int out_slot, cudaStream_t s,
                    int* launches) {
@@ -2068,8 +2112,13 @@ void launch_residual(const Geom& g, const Phys& ph, const ResidArgs& a, cudaStre
     // inherits the stencil's relative rounding directly, which plain FP32
     // (24 bits) leaves above 1e-6
     if (ph.mixed) {
-        if (g.dim == 3) k_residual<3, FF><<<nb, NT, 0, s>>>(g, ph, a);
-        else k_residual<2, FF><<<nb, NT, 0, s>>>(g, ph, a);
+        if (g.dim == 3) {
+            if (a.ffs) k_residual<3, FF, true><<<nb, NT, 0, s>>>(g, ph, a);
+            else k_residual<3, FF><<<nb, NT, 0, s>>>(g, ph, a);
+        } else {
+            if (a.ffs) k_residual<2, FF, true><<<nb, NT, 0, s>>>(g, ph, a);
+            else k_residual<2, FF><<<nb, NT, 0, s>>>(g, ph, a);
+        }
     } else {
         if (g.dim == 3) k_residual<3, double><<<nb, NT, 0, s>>>(g, ph, a);
         else k_residual<2, double><<<nb, NT, 0, s>>>(g, ph, a);

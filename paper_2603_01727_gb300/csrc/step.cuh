@@ -99,6 +99,10 @@ struct ResidArgs {
     double iwden;             // 1 / wden
     int mode;
     double dt;
+    // mixed path: float-float images (hi, lo) of v0, v1, v2, Z, H and kappa,
+    // six planes of npad float2 written by launch_ff_images (null: the
+    // stencil splits each double as it loads it)
+    const float2* ffs;
 };
 
 struct FluxArgs {
@@ -211,6 +215,13 @@ void launch_project(const Geom& g, const Phys& ph, const ProjArgs& a, cudaStream
 void launch_momentum(const Geom& g, const double* rho, double* const v[3], double* mom[3], cudaStream_t s,
                      int* launches);
 void launch_sum(const Geom& g, const double* x, double* part, cudaStream_t s, int* launches);
+struct FFSrc {
+    const double* f[6];
+};
+// Float-float images of a stage's stencil inputs (padded, ghosts included):
+// dst plane f (npad float2) = the (hi, lo) split of src[f], f = v0, v1, v2,
+// Z, H, kappa (src[2] unused in 2D).
+void launch_ff_images(const Geom& g, const double* const src[6], float2* dst, cudaStream_t s, int* launches);
 // Semi-enclosed system: G of Eq 2.38 on one level's fields (padded, ghosts
 // filled; v[d] for d < dim) and the stage update of p0 it feeds: stage 0 the
 // predictor's Euler step (step 0), 1 its AB2 step, 2 the corrector's AM2 step.

@@ -690,12 +690,15 @@ def test_step_before_fields_is_a_state_error():
     assert e.value.status == SIM_ESTATE
 
 
+@pytest.mark.parametrize("path", ["sweeps", "zmarch"])
 @pytest.mark.parametrize("n,periodic_x,precision", [(48, False, W.MIXED), (48, False, W.FP64), (32, True, W.FP64),
                                                     (32, True, W.MIXED)])
-def test_z_marching_3d_multigrid_matches_cube_tiles(n, periodic_x, precision, monkeypatch):
-    """The z-marching 3D level kernels apply the same smoother, residual,
-    restriction and prolongation as the cube-tile kernels (LOWMACH_MG3_TILES=1):
-    same iteration counts and the same fields to solver tolerance."""
+def test_large_level_3d_multigrid_matches_cube_tiles(n, periodic_x, precision, path, monkeypatch):
+    """The large-level 3D multigrid kernels -- the whole-level colour-sweep
+    passes (default) and the z-marching ones (LOWMACH_MG3_SWEEPS=0) -- apply
+    the same smoother, residual, restriction and prolongation as the
+    cube-tile kernels (LOWMACH_MG3_TILES=1): same iteration counts and the
+    same fields to solver tolerance, with every level on the kernels tested."""
     from paper_2603_01727_gb300.lowmach import SIM_Q_ITERS_PRED, SIM_Q_ITERS_CORR
     prm, geo, f = W.sphere_burner(n)
     prm["precision"] = precision
@@ -703,7 +706,8 @@ def test_z_marching_3d_multigrid_matches_cube_tiles(n, periodic_x, precision, mo
     if periodic_x:
         prm["bc"] = [[W.PERIODIC, W.PERIODIC]] + prm["bc"][1:]
     out = {}
-    monkeypatch.setenv("LOWMACH_MG3_MIN_CELLS", "0")     # every level on the z-marching kernels
+    monkeypatch.setenv("LOWMACH_MG3_MIN_CELLS", "0")     # every level on the large-level kernels
+    monkeypatch.setenv("LOWMACH_MG3_SWEEPS", "1" if path == "sweeps" else "0")
     for tiles in ("0", "1"):
         monkeypatch.setenv("LOWMACH_MG3_TILES", tiles)
         sim = gpu_run(prm, geo, f, 4)
