@@ -2767,7 +2767,7 @@ __global__ void __launch_bounds__(NT) resid(LvT<T> L, const TF* __restrict__ f, 
 // RX x RY x RZ cells, stages its fine footprint (2 RX + 2) x (2 RY + 2) x
 // (2 RZ + 2) of r (zero outside a non-periodic level), then sums along x, y
 // and z with the 1D weights.
-constexpr int RX = 32, RY = 8, RZ = 4;
+constexpr int RX = 32, RY = 4, RZ = 4;
 constexpr int FX = 2 * RX + 2, FY = 2 * RY + 2, FZ = 2 * RZ + 2;
 constexpr size_t kRestrictSmem = sizeof(float) * (size_t)(FX * FY * FZ + RX * FY * FZ + RX * RY * FZ);
 

@@ -837,6 +837,16 @@ __device__ __forceinline__ void rhs_body(const Geom& g, const Bnd& bnd, const Fl
         }
         a.b[t] = b;
         bsum += b;
+        if (a.guess != GUESS_NONE) {
+            const double p = a.P[t];
+            if (a.guess == GUESS_SHIFT) {
+                a.P[t] = __dadd_rn(p, a.Pd[t]);
+            } else {
+                const double pm = a.Pm1[t];
+                a.Pm1[t] = p;
+                if (a.guess == GUESS_EXTRAP) a.P[t] = __fma_rn(2.0, p, -pm);
+            }
+        }
     }
     if (a.mb_out) {
         // mean(b) for the pressure solve, with the block decomposition and the
@@ -909,6 +919,7 @@ __device__ __forceinline__ void project_body(const Geom& g, const Phys& ph, cons
         padded_coords(g, c, q);
         fill_ghosts_of(g, ph, a.bnd, a.gj, q, vout);
     }
+    if (a.Pd) a.Pd[t] = __dsub_rn(Pc, a.Pstar[t]);
     // the step's last projection rotates the p0 history (it reads only the new
     // p0, which the rotation leaves as it is)
     if (a.rot && t == 0) rotate_p0(a.rot);

@@ -123,7 +123,16 @@ struct FluxArgs {
     double* mb_part;
     unsigned int* mb_cnt;
     double* mb_out;
+    // initial guess of the stage's pressure solve, formed in place in P
+    // (compact) by k_rhs: GUESS_COPY keeps P in Pm1; GUESS_EXTRAP also sets
+    // P = 2 P - Pm1 (linear extrapolation from the last two steps' pressures);
+    // GUESS_SHIFT adds Pd (the last step's P - P*) to the predictor's P*
+    int guess;
+    double* P;
+    double* Pm1;
+    const double* Pd;
 };
+enum { GUESS_NONE = 0, GUESS_COPY = 1, GUESS_EXTRAP = 2, GUESS_SHIFT = 3 };
 
 struct ProjArgs {
     double* F[3];
@@ -138,6 +147,8 @@ struct ProjArgs {
     Bnd bnd;                 // boundary kinds for the fused ghost fill of v
     GhostJob gj;             // v components to ghost-fill in the kernel (nf = 0: none)
     double* rot;             // not null: rotate the p0 history in these scalars (the step's end)
+    double* Pd;              // not null: Pd = P - Pstar (the corrector's projection)
+    const double* Pstar;
 };
 
 // Fields read by the stage stencil, by loader id.
