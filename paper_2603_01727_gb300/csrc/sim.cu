@@ -1431,6 +1431,9 @@ sim_status sim_time_kernel(sim_t* s, int kernel, int reps) {
                 a.p0r = SC_P0_N;
                 a.w0 = 3.0; a.w1 = -4.0; a.w2 = 1.0; a.wden = 2.0 * s->prm.dt;
                 a.iwden = 1.0 / a.wden;
+                // the stencil variant the step runs (its inputs' images as the
+                // last stage left them)
+                a.ffs = use_ff_images(s) ? s->ffs : nullptr;
                 launch_residual(g, s->ph, a, s->stream, &L);
                 break;
             }
