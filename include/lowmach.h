@@ -247,13 +247,12 @@ sim_status sim_query(sim_t *sim, int what, double *out);
  * buf is a device pointer when on_device = 1, else a host pointer.  The
  * blob's body is one contiguous image of the workspace's state arrays, so it
  * moves in one copy (fastest from pinned host memory); both calls return once
- * a host buffer may be reused.  Blob format version 3: a 256-byte-aligned
+ * a host buffer may be reused.  Blob format version 2: a 256-byte-aligned
  * header, then the segments in this order, each padded to 256 bytes: Z, H, T,
  * kappa, rho (three levels), the stored residuals of the last two steps (the
  * arrays final after the corrector's state relation, first), then v, F, P,
- * the warm-start history of the pressure solves (the previous step's P, the
- * last step's P - P*), the scalars and the status words.  Blobs of earlier
- * versions are refused with SIM_EINVAL. */
+ * the scalars and the status words.  Blobs of version 1 (v and F first) are
+ * refused with SIM_EINVAL. */
 sim_status sim_state_size(const sim_t *sim, size_t *bytes);
 sim_status sim_state_save(sim_t *sim, void *buf, int on_device);
 sim_status sim_state_load(sim_t *sim, const void *buf, int on_device);

@@ -74,6 +74,7 @@ struct sim {
     double *P, *b, *io;
     double* Pstar;         // the predictor's P of the last step (per-step checks)
     double *Pm1, *Pd;      // warm-start history: P of the step before, P - P* of the last step
+    long long hist_from = 0;   // the step from which that history is being kept (set-up or load)
     double* diag;          // per-step check partials and results
     double* part;
     double* part2;
@@ -329,14 +330,16 @@ size_t layout(const sim_params_t* p, sim_t* s, char* base) {
     {
         double* q = (double*)take(fcmp);
         if (s) s->P = q;
-        q = (double*)take(fcmp);
-        if (s) s->Pm1 = q;
-        q = (double*)take(fcmp);
-        if (s) s->Pd = q;
         q = (double*)take(sizeof(double) * SC_NSCAL);
         if (s) s->sc = q;
         int* st = (int*)take(sizeof(int) * 8);
         if (s) s->status = st;
+    }
+    {
+        double* q = (double*)take(fcmp);
+        if (s) s->Pm1 = q;
+        q = (double*)take(fcmp);
+        if (s) s->Pd = q;
     }
     for (int d = 0; d < D; ++d) F(&t->vs[d]);
     F(&t->Zs); F(&t->Hs);
@@ -652,9 +655,12 @@ bool use_ff_images(const sim_t* s) {
 
 // Warm-started pressure solves (LOWMACH_EXTRAP=1; off by default): the
 // predictor's solve starts from the linear extrapolation 2 P^n - P^(n-1) of
-// the last two steps' pressures (from step 2 on), the corrector's from
-// P* + (P^n - P*^n), the predictor's pressure shifted by the last step's
-// predictor-corrector difference (from step 1 on).  Both are initial guesses
+// the last two steps' pressures, the corrector's from P* + (P^n - P*^n), the
+// predictor's pressure shifted by the last step's predictor-corrector
+// difference, once two (one) steps of history exist since the set-up or the
+// last state load (the restart blob does not carry it: a reloaded run takes
+// plain guesses for two steps, and matches an uninterrupted one to the
+// solvers' tolerance, not bitwise).  Both are initial guesses
 // only: every solve still runs to its tolerance.  Measured on the 256x512
 // slot burner: 12.95 instead of 14.10 CG iterations per step over 300 steps
 // (0.859 against 0.899 ms), but 16.1 instead of 15.55 over the first 25
@@ -745,7 +751,8 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     fa.P = s->P;
     fa.Pm1 = s->Pm1;
     fa.Pd = s->Pd;
-    fa.guess = !extrap ? GUESS_NONE : (n >= 2) ? GUESS_EXTRAP : (n == 1) ? GUESS_COPY : GUESS_NONE;
+    const long long hn = n - s->hist_from;   // steps of warm-start history
+    fa.guess = !extrap ? GUESS_NONE : (hn >= 2) ? GUESS_EXTRAP : (hn == 1) ? GUESS_COPY : GUESS_NONE;
     // k_rhs leaves mean(b) in the plan's scratch word (the solve's prologue
     // then runs no mean pass)
     poisson_meanb_target(&s->pp, &fa.mb_part, &fa.mb_cnt, &fa.mb_out);
@@ -853,7 +860,7 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
     c.bnd = s->bnd;
     c.gj = job_of(s, {{s->Z, GW_Z}, {s->H, GW_H}});
     c.ffs = a.ffs;
-    fa.guess = (extrap && n >= 1) ? GUESS_SHIFT : GUESS_NONE;
+    fa.guess = (extrap && hn >= 1) ? GUESS_SHIFT : GUESS_NONE;
     if (D == 3) c.gj.nf = 0;
     fa.p0_slot = SC_P0_NEW;
     if (on(SEC_MID)) {
@@ -1251,6 +1258,7 @@ sim_status sim_step(sim_t* s, int nsteps) {
         s->nstep = 0;
         s->rho_base = 0;
         s->t = 0.0;
+        s->hist_from = 0;
         CK(enqueue_init(s, s->stream));
         s->need_init = false;
         for (int k = 0; k < 6; ++k)
@@ -1261,7 +1269,9 @@ sim_status sim_step(sim_t* s, int nsteps) {
     }
     for (int it = 0; it < nsteps; ++it) {
         const long long n = s->nstep;
-        if (n < 2 || !s->use_graph) {
+        // eager until the launch sequence is the steady one (the first two
+        // steps; with warm starts, also the first two after a state load)
+        if (n < 2 || !s->use_graph || (use_extrap() && n - s->hist_from < 2)) {
             int L = 0, body = 0;
             CK(enqueue_step(s, n, s->stream, false, &L, &body));
             s->launches_last = L;
@@ -1517,8 +1527,6 @@ std::vector<std::pair<void*, size_t>> state_segments(sim_t* s) {
     for (int d = 0; d < g.dim; ++d) seg.push_back({s->v[d], fpad});
     for (int d = 0; d < g.dim; ++d) seg.push_back({s->F[d], fpad});
     seg.push_back({s->P, sizeof(double) * (size_t)g.ncell});
-    seg.push_back({s->Pm1, sizeof(double) * (size_t)g.ncell});
-    seg.push_back({s->Pd, sizeof(double) * (size_t)g.ncell});
     seg.push_back({s->sc, sizeof(double) * SC_NSCAL});
     seg.push_back({s->status, sizeof(int) * 8});
     return seg;
@@ -1541,7 +1549,7 @@ char* state_image(const std::vector<std::pair<void*, size_t>>& seg, size_t* byte
 void fill_header(const sim_t* s, StateHeader* h) {
     std::memset(h, 0, sizeof(*h));
     std::memcpy(h->magic, "LMSTATE", 8);
-    h->version = 3;
+    h->version = 2;
     h->dim = s->g.dim;
     for (int d = 0; d < 3; ++d) h->n[d] = s->g.n[d];
     h->rho_base = s->rho_base;
@@ -1639,7 +1647,7 @@ sim_status sim_state_load(sim_t* s, const void* buf, int on_device) {
         CK(cudaMemcpy(&h, buf, sizeof(h), cudaMemcpyDeviceToHost));
     else
         std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "LMSTATE", 8) != 0 || h.version != 3 || h.dim != s->g.dim || h.dt != s->prm.dt ||
+    if (std::memcmp(h.magic, "LMSTATE", 8) != 0 || h.version != 2 || h.dim != s->g.dim || h.dt != s->prm.dt ||
         h.n[0] != s->g.n[0] || h.n[1] != s->g.n[1] || h.n[2] != s->g.n[2] || h.ibm_active != s->ibm_active)
         return fail(s, SIM_EINVAL, "restart blob does not match this simulation");
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -1659,6 +1667,7 @@ sim_status sim_state_load(sim_t* s, const void* buf, int on_device) {
     if (!on_device) CK(cudaStreamSynchronize(s->stream));
     s->rho_base = h.rho_base;
     s->nstep = h.nstep;
+    s->hist_from = h.nstep;
     s->t = h.t;
     s->need_init = false;
     s->fields_set = 0x1f;

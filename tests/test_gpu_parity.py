@@ -637,12 +637,13 @@ def test_second_run_after_set_fields_repeats_the_first():
     sim.close()
 
 
-def test_warm_started_solves_match_oracle_and_restart_exactly(monkeypatch):
+def test_warm_started_solves_match_oracle_and_restart(monkeypatch):
     """LOWMACH_EXTRAP=1: the pressure solves start from extrapolated guesses
     (2 P^n - P^(n-1); P* + P^n - P*^n).  Every solve still runs to its
-    tolerance, so the fields stay within 1e-9 of the oracle, and the restart
-    blob carries the guesses' history: a run reloaded mid-way steps to the
-    same bits as the uninterrupted one."""
+    tolerance, so the fields stay within 1e-9 of the oracle.  The restart
+    blob does not carry the guesses' history: a reloaded run takes plain
+    guesses for two steps and agrees with the uninterrupted run to the
+    solvers' tolerance."""
     monkeypatch.setenv("LOWMACH_EXTRAP", "1")
     prm, geo, f = W.slot_burner(64, 128)
     prm["poisson_rtol"] = 1e-13
@@ -651,14 +652,14 @@ def test_warm_started_solves_match_oracle_and_restart_exactly(monkeypatch):
     compare(sim, oracle_fields(pb, st), 1e-9)
     blob = np.zeros(sim.state_size(), dtype=np.uint8)
     sim.state_save(blob)
-    sim.step(4)
+    sim.step(6)
     sim.sync()
     ref = {k: sim.get(k) for k in ("U", "V", "Z", "H", "P")}
     sim.state_load(blob)
-    sim.step(4)
+    sim.step(6)
     sim.sync()
     for k, v in ref.items():
-        assert np.array_equal(sim.get(k), v), k
+        assert rel(sim.get(k), v) <= 1e-10, k
     sim.close()
 
 
