@@ -3716,20 +3716,23 @@ void enqueue_up(PoissonPlan* pl, int l, cudaStream_t s) {
         const dim3 grid = k3s::grid_of(L.n, zc);
         T* u = (l == 0) ? (T*)pl->u0pre : (T*)pl->lev[l].upre;
         launch(k3s::prolong_add<T>, grid, k3s::NT, 0, s, L, C, uc, u, zc);
+        // the reducing pass keeps the default plane chunk (its last block sums
+        // one partial per block)
+        const dim3 rgrid = k3s::grid_of(L.n, k3s::kZC);
         if (l == 0 && ir) {
             launch(k3s::sweep<T, float>, grid, k3s::NT, 0, s, L, (const float*)pl->r32, u, 1, (const double*)pl->scal, zc);
-            launch(k3s::red_out<T, float, true>, grid, k3s::NT, 0, s, L, (const float*)pl->r32, (const T*)u,
-                   (T*)pl->z, pl->part0, pl->part1, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_UP0, zc);
+            launch(k3s::red_out<T, float, true>, rgrid, k3s::NT, 0, s, L, (const float*)pl->r32, (const T*)u,
+                   (T*)pl->z, pl->part0, pl->part1, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_UP0, k3s::kZC);
         } else if (l == 0) {
             launch(k3s::sweep<T, double>, grid, k3s::NT, 0, s, L, (const double*)pl->r, u, 1, (const double*)pl->scal, zc);
-            launch(k3s::red_out<T, double, true>, grid, k3s::NT, 0, s, L, (const double*)pl->r, (const T*)u,
-                   (T*)pl->z, pl->part0, pl->part1, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_UP0, zc);
+            launch(k3s::red_out<T, double, true>, rgrid, k3s::NT, 0, s, L, (const double*)pl->r, (const T*)u,
+                   (T*)pl->z, pl->part0, pl->part1, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_UP0, k3s::kZC);
         } else {
             const T* f = (const T*)pl->lev[l].f;
             launch(k3s::sweep<T, T>, grid, k3s::NT, 0, s, L, f, u, 1, (const double*)nullptr, zc);
-            launch(k3s::red_out<T, T, false>, grid, k3s::NT, 0, s, L, f, (const T*)u, (T*)pl->lev[l].upost,
+            launch(k3s::red_out<T, T, false>, rgrid, k3s::NT, 0, s, L, f, (const T*)u, (T*)pl->lev[l].upost,
                    (double*)nullptr, (double*)nullptr, (double*)nullptr, (const int*)nullptr,
-                   (unsigned int*)nullptr, zc);
+                   (unsigned int*)nullptr, k3s::kZC);
         }
         pl->launches += 2;
     } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells) {
