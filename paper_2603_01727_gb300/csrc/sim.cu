@@ -1796,7 +1796,6 @@ const char* adj_unsupported(const sim_t* s) {
     if (s->prm.precision != SIM_FP64) return "the adjoint step needs precision SIM_FP64";
     if (s->ph.closed) return "the adjoint step needs an open system (p0 = 1)";
     if (s->ph.incompressible) return "the adjoint step needs the variable-density model";
-    if (s->ph.Le_F != s->ph.Le_O) return "the adjoint step needs Le_F == Le_O";
     if (s->ph.inv_Fr2 != 0.0) return "the adjoint step needs inv_Fr2 == 0";
     if (s->ph.transport != 0) return "the adjoint step needs the power-law transport (Eq 2.50)";
     for (int d = 0; d < s->g.dim; ++d)
@@ -1911,8 +1910,11 @@ sim_status sim_adjoint_begin(sim_t* s, void* d_workspace, size_t workspace_bytes
     s->adj.i_rho = 0;
     s->adj.i_prev = 1;
     {
+        // the hand-written reverse sweep of the stage stencil covers Le_F ==
+        // Le_O; differential diffusion (the regularised Le_eps(Z), N_eps(Z) of
+        // Eq 3.35) takes the exact dual-number gather
         const char* dual = std::getenv("LOWMACH_ADJ_DUAL");
-        s->adj.use_dual = (dual && dual[0] == '1') ? 1 : 0;
+        s->adj.use_dual = ((dual && dual[0] == '1') || s->ph.Le_F != s->ph.Le_O) ? 1 : 0;
     }
     CK(cudaMemsetAsync(s->adj.lam_base, 0, s->adj.lam_bytes, s->stream));
     CK(cudaStreamSynchronize(s->stream));
