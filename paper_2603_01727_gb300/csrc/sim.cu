@@ -348,9 +348,9 @@ size_t layout(const sim_params_t* p, sim_t* s, char* base) {
     F(&t->Sm);
     F(&t->U);
     {
-        // 3D mixed path: the stage stencil's float-float input images
+        // mixed path: the stage stencil's float-float input images
         float2* im = nullptr;
-        if (D == 3 && p->precision == SIM_MIXED) im = (float2*)take(sizeof(float2) * 6 * (size_t)g.npad);
+        if (p->precision == SIM_MIXED) im = (float2*)take(sizeof(float2) * 6 * (size_t)g.npad);
         if (s) s->ffs = im;
     }
     {
@@ -645,8 +645,9 @@ ResidArgs resid_common(sim_t* s) {
     return a;
 }
 
-// The 3D mixed stage stencil reads float-float images of its inputs (one
-// split per value instead of one per use); LOWMACH_FF_IMAGES=0 splits on load.
+// The mixed stage stencil reads float-float images of its inputs (one split
+// per value instead of one per use); LOWMACH_FF_IMAGES=0 splits on load (the
+// same bits: the stencil converts each value as it loads it).
 bool use_ff_images(const sim_t* s) {
     if (!s->ffs) return false;
     const char* e = std::getenv("LOWMACH_FF_IMAGES");

@@ -492,10 +492,14 @@ __global__ void k_ff_images(long long npad, int nf, FFSrc src, float2* __restric
 template <int DIM, class C, class LD>
 __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, const ResidArgs& a, long long c,
                                               double p0dot, const LD& ld, C R[5]) {
+    // every input converted to the arithmetic type as it is loaded, so that
+    // differences of loaded values are taken in C (the same bits whichever
+    // loader supplies a float-float value: split on load, or its image)
+    auto ldc = [&](int f, long long i) -> C { return C(ld(f, i)); };
     const C half = (C)0.5;
-    const C rho_c = ld(RF_RHO, c);
-    const C kap_c = ld(RF_KAP, c);
-    const C Zc = ld(RF_Z, c), Hc = ld(RF_H, c);
+    const C rho_c = ldc(RF_RHO, c);
+    const C kap_c = ldc(RF_KAP, c);
+    const C Zc = ldc(RF_Z, c), Hc = ldc(RF_H, c);
 
     // scalar convection (Eq 3.26b) and diffusion div(kappa grad .)
     C convZ = 0.0, convH = 0.0, difZ = 0.0, difH = 0.0;
@@ -504,11 +508,11 @@ __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, con
     for (int j = 0; j < DIM; ++j) {
         const long long s = g.s[j];
         const C ih = (C)g.ih[j];
-        const C Flo = ld(RF_F0 + j, c), Fhi = ld(RF_F0 + j, c + s);
-        kf_lo[j] = half * (ld(RF_KAP, c - s) + kap_c);
-        kf_hi[j] = half * (kap_c + ld(RF_KAP, c + s));
-        const C dZlo = (Zc - ld(RF_Z, c - s)) * ih, dZhi = (ld(RF_Z, c + s) - Zc) * ih;
-        const C dHlo = (Hc - ld(RF_H, c - s)) * ih, dHhi = (ld(RF_H, c + s) - Hc) * ih;
+        const C Flo = ldc(RF_F0 + j, c), Fhi = ldc(RF_F0 + j, c + s);
+        kf_lo[j] = half * (ldc(RF_KAP, c - s) + kap_c);
+        kf_hi[j] = half * (kap_c + ldc(RF_KAP, c + s));
+        const C dZlo = (Zc - ldc(RF_Z, c - s)) * ih, dZhi = (ldc(RF_Z, c + s) - Zc) * ih;
+        const C dHlo = (Hc - ldc(RF_H, c - s)) * ih, dHhi = (ldc(RF_H, c + s) - Hc) * ih;
         convZ += half * (Flo * dZlo + Fhi * dZhi);
         convH += half * (Flo * dHlo + Fhi * dHhi);
         difZ += (kf_hi[j] * dZhi - kf_lo[j] * dZlo) * ih;
@@ -524,8 +528,8 @@ __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, con
         for (int j = 0; j < DIM; ++j) {
             const long long s = g.s[j];
             const C ih = (C)g.ih[j];
-            const C Flo = ld(RF_F0 + j, c), Fhi = ld(RF_F0 + j, c + s);
-            const C vl = ld(RF_V0 + i, c - s), vc = ld(RF_V0 + i, c), vh = ld(RF_V0 + i, c + s);
+            const C Flo = ldc(RF_F0 + j, c), Fhi = ldc(RF_F0 + j, c + s);
+            const C vl = ldc(RF_V0 + i, c - s), vc = ldc(RF_V0 + i, c), vh = ldc(RF_V0 + i, c + s);
             conv += (Fhi * (half * (vc + vh)) - Flo * (half * (vl + vc))) * ih;
             C tau_f[2];
 #pragma unroll
@@ -540,8 +544,8 @@ __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, con
                 } else {
                     const long long si = g.s[i];
                     const C hi2 = (C)(0.5 * g.ih[i]);
-                    const C da = (ld(RF_V0 + j, ca + si) - ld(RF_V0 + j, ca - si)) * hi2;
-                    const C db = (ld(RF_V0 + j, cb + si) - ld(RF_V0 + j, cb - si)) * hi2;
+                    const C da = (ldc(RF_V0 + j, ca + si) - ldc(RF_V0 + j, ca - si)) * hi2;
+                    const C db = (ldc(RF_V0 + j, cb + si) - ldc(RF_V0 + j, cb - si)) * hi2;
                     dvj = half * (da + db);
                 }
                 C tau = kf * (dvi + dvj);
@@ -552,8 +556,8 @@ __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, con
                         if (k == j) continue;
                         const long long sk = g.s[k];
                         const C hk2 = (C)(0.5 * g.ih[k]);
-                        const C da = (ld(RF_V0 + k, ca + sk) - ld(RF_V0 + k, ca - sk)) * hk2;
-                        const C db = (ld(RF_V0 + k, cb + sk) - ld(RF_V0 + k, cb - sk)) * hk2;
+                        const C da = (ldc(RF_V0 + k, ca + sk) - ldc(RF_V0 + k, ca - sk)) * hk2;
+                        const C db = (ldc(RF_V0 + k, cb + sk) - ldc(RF_V0 + k, cb - sk)) * hk2;
                         div = div + half * (da + db);
                     }
                     tau = tau - two3 * kf * div;
@@ -565,7 +569,7 @@ __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, con
         C Rm = -conv + (C)ph.PrPe * visc;
         if (i == 1 && ph.inv_Fr2 != 0.0) Rm = Rm + (C)ph.inv_Fr2 * ((C)1.0 - rho_c);                  // Eq 3.8b
         if (a.ibm && a.chi[c])
-            Rm = Rm - (C)(ph.PrPe * a.inv_Da) * kap_c * (ld(RF_V0 + i, c) - ld(RF_VIB0 + i, c));    // Eq 3.30
+            Rm = Rm - (C)(ph.PrPe * a.inv_Da) * kap_c * (ldc(RF_V0 + i, c) - ldc(RF_VIB0 + i, c));    // Eq 3.30
         R[i] = Rm;
     }
 
@@ -586,7 +590,7 @@ __device__ __forceinline__ void residual_cell(const Geom& g, const Phys& ph, con
         bH = bH - kap_c * (Hc - (C)a.H_ib) * iPe * iDa;                                     // Eq 3.32
     }
     // 1/rho = T / p0 (Eq 2.49)
-    const C irho = ld(RF_T, c) * (C)a.sc[a.p0r + SC_INV_OFF];
+    const C irho = ldc(RF_T, c) * (C)a.sc[a.p0r + SC_INV_OFF];
     R[3] = bZ * irho;
     R[4] = bH * irho;
 }
@@ -641,8 +645,11 @@ __device__ __forceinline__ void residual_body(const Geom& g, const Phys& ph, con
         Rst[k] = reinterpret_cast<double*>(a.Rst[k]);
     }
     // dp0/dt for the H source (Eqs 3.5, 3.14)
-    const double p0dot = (a.wden != 0.0) ? (a.w0 * a.sc[a.p0a] + a.w1 * a.sc[a.p0b] + a.w2 * a.sc[a.p0c]) * a.iwden
-                                         : 0.0;
+    const double p0dot =
+        (a.wden != 0.0) ? __dmul_rn(__dadd_rn(__dadd_rn(__dmul_rn(a.w0, a.sc[a.p0a]), __dmul_rn(a.w1, a.sc[a.p0b])),
+                                              __dmul_rn(a.w2, a.sc[a.p0c])),
+                                    a.iwden)
+                        : 0.0;
     C Rall[5];
     if constexpr (IMG) residual_cell<DIM, C>(g, ph, a, c, p0dot, ImageLoad{&a, g.npad}, Rall);
     else residual_cell<DIM, C>(g, ph, a, c, p0dot, PlainLoad{&a}, Rall);
@@ -658,23 +665,26 @@ __device__ __forceinline__ void residual_body(const Geom& g, const Phys& ph, con
     if (a.mode == MODE_CORR) {
         const double hdt = 0.5 * dt;
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) a.mo[i][c] = fma(hdt, Rv[i] + Rrd[i][c], rb * a.vb[i][c]);
-        zo = fma(hdt, RZ + Rrd[3][c], a.Zb[c]);
-        ho = fma(hdt, RH + Rrd[4][c], a.Hb[c]);
+        for (int i = 0; i < DIM; ++i)
+            a.mo[i][c] = __fma_rn(hdt, __dadd_rn(Rv[i], Rrd[i][c]), __dmul_rn(rb, a.vb[i][c]));
+        zo = __fma_rn(hdt, __dadd_rn(RZ, Rrd[3][c]), a.Zb[c]);
+        ho = __fma_rn(hdt, __dadd_rn(RH, Rrd[4][c]), a.Hb[c]);
     } else {
         const bool ab2 = (a.mode == MODE_PRED_AB2);
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
-            const double cv = ab2 ? (1.5 * Rv[i] - 0.5 * Rrd[i][c]) : Rv[i];
+            // explicitly rounded (the same bits in every instantiation of this
+            // body, whatever contraction the compiler would choose)
+            const double cv = ab2 ? __fma_rn(1.5, Rv[i], __dmul_rn(-0.5, Rrd[i][c])) : Rv[i];
             Rst[i][c] = Rv[i];
-            a.mo[i][c] = fma(dt, cv, rb * a.vb[i][c]);
+            a.mo[i][c] = __fma_rn(dt, cv, __dmul_rn(rb, a.vb[i][c]));
         }
-        const double cZ = ab2 ? (1.5 * RZ - 0.5 * Rrd[3][c]) : RZ;
-        const double cH = ab2 ? (1.5 * RH - 0.5 * Rrd[4][c]) : RH;
+        const double cZ = ab2 ? __fma_rn(1.5, RZ, __dmul_rn(-0.5, Rrd[3][c])) : RZ;
+        const double cH = ab2 ? __fma_rn(1.5, RH, __dmul_rn(-0.5, Rrd[4][c])) : RH;
         Rst[3][c] = RZ;
         Rst[4][c] = RH;
-        zo = fma(dt, cZ, a.Zb[c]);
-        ho = fma(dt, cH, a.Hb[c]);
+        zo = __fma_rn(dt, cZ, a.Zb[c]);
+        ho = __fma_rn(dt, cH, a.Hb[c]);
     }
     a.Zo[c] = zo;
     a.Ho[c] = ho;
@@ -1969,6 +1979,28 @@ __global__ void k_project_b(const StageRec* __restrict__ recs, const int* __rest
     project_body<DIM>(r.g, r.ph, r.u.p, bx);
 }
 
+template <int DIM, class C>
+__global__ void __launch_bounds__(NT, ResidMinBlocks<DIM, C>::v)
+    k_residual_img_b(const StageRec* __restrict__ recs, const int* __restrict__ start, int nm) {
+    __shared__ __align__(16) StageRec r;
+    const int bx = stage_rec(recs, start, nm, &r);
+    residual_body<DIM, C, true>(r.g, r.ph, r.u.r, bx);
+}
+
+__global__ void k_ff_images_b(const StageRec* __restrict__ recs, const int* __restrict__ start, int nm) {
+    __shared__ __align__(16) StageRec r;
+    const int bx = stage_rec(recs, start, nm, &r);
+    const StageImg& q = r.u.im;
+    const long long p = (long long)bx * NT + threadIdx.x;
+    if (p >= q.npad) return;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        if (!q.src.f[f]) continue;
+        const FF w(q.src.f[f][p]);
+        q.dst[(long long)f * q.npad + p] = make_float2(w.hi, w.lo);
+    }
+}
+
 __global__ void k_copy_b(const StageRec* __restrict__ recs, const int* __restrict__ start, int nm) {
     __shared__ __align__(16) StageRec r;
     const int bx = stage_rec(recs, start, nm, &r);
@@ -1990,6 +2022,7 @@ bool collect(const StageRec& rec) {
 }  // namespace
 
 void set_stage_collector(StageCollector* c) { t_collect = c; }
+bool stage_collecting() { return t_collect != nullptr; }
 
 cudaError_t stage_copy(const double* src, double* dst, long long n, cudaStream_t s) {
     if (t_collect) {
@@ -2035,6 +2068,13 @@ cudaError_t launch_stage_batched(int kind, int dim, int mixed, const StageRec* r
         case SK_PROJECT:
             if (dim == 3) k_project_b<3><<<grid, NT, 0, s>>>(recs, start, nm);
             else k_project_b<2><<<grid, NT, 0, s>>>(recs, start, nm);
+            break;
+        case SK_IMAGES:
+            k_ff_images_b<<<grid, NT, 0, s>>>(recs, start, nm);
+            break;
+        case SK_RESID_IMG:   // the float-float stencil reading its inputs' images
+            if (dim == 3) k_residual_img_b<3, FF><<<grid, NT, 0, s>>>(recs, start, nm);
+            else k_residual_img_b<2, FF><<<grid, NT, 0, s>>>(recs, start, nm);
             break;
         default:
             k_copy_b<<<grid, NT, 0, s>>>(recs, start, nm);
@@ -2087,6 +2127,19 @@ void launch_state(const Geom& g, const Phys& ph, const double* Z, const double* 
 void launch_ff_images(const Geom& g, const double* const src[6], float2* dst, cudaStream_t s, int* launches) {
     FFSrc fs;
     for (int f = 0; f < 6; ++f) fs.f[f] = (f == 2 && g.dim == 2) ? nullptr : src[f];
+    if (t_collect) {
+        StageRec r;
+        std::memset(&r, 0, sizeof(r));
+        r.g = g;
+        r.kind = SK_IMAGES;
+        r.nblocks = blocks_for(g.npad);
+        r.u.im.src = fs;
+        r.u.im.dst = dst;
+        r.u.im.npad = g.npad;
+        collect(r);
+        ++*launches;
+        return;
+    }
     long long nb = (g.npad + NT - 1) / NT;
     if (nb > 8 * 152) nb = 8 * 152;
     k_ff_images<<<(int)nb, NT, 0, s>>>(g.npad, 6, fs, dst);
@@ -2111,7 +2164,7 @@ void launch_residual(const Geom& g, const Phys& ph, const ResidArgs& a, cudaStre
         std::memset(&r, 0, sizeof(r));
         r.g = g;
         r.ph = ph;
-        r.kind = SK_RESID;
+        r.kind = (a.ffs && ph.mixed) ? SK_RESID_IMG : SK_RESID;
         r.nblocks = nb;
         r.u.r = a;
         collect(r);

@@ -252,7 +252,8 @@ void launch_or_status(const int* src_flag, int bit, int* status, cudaStream_t s,
 // launch to its member and member-local block, so every member computes
 // exactly what its own launch would (bitwise).  The members' arguments are
 // records in device memory.
-enum StageKind : int { SK_RESID = 0, SK_STATE_FLUX = 1, SK_RHS = 2, SK_PROJECT = 3, SK_COPY = 4 };
+enum StageKind : int { SK_RESID = 0, SK_STATE_FLUX = 1, SK_RHS = 2, SK_PROJECT = 3, SK_COPY = 4, SK_IMAGES = 5,
+                       SK_RESID_IMG = 6 };
 struct StageSF {
     const double* Z;
     const double* H;
@@ -270,6 +271,11 @@ struct StageCopy {
     double* dst;
     long long n;
 };
+struct StageImg {
+    FFSrc src;
+    float2* dst;
+    long long npad;
+};
 struct StageRec {
     Geom g;
     Phys ph;
@@ -281,6 +287,7 @@ struct StageRec {
         StageSF sf;          // SK_STATE_FLUX and SK_RHS (FluxArgs, bnd)
         ProjArgs p;
         StageCopy cp;
+        StageImg im;
     } u;
 };
 // Records collected instead of launched: while a collector is installed on the
@@ -293,6 +300,8 @@ struct StageCollector {
     bool overflow;
 };
 void set_stage_collector(StageCollector* c);
+// True while a collector is installed on the calling thread.
+bool stage_collecting();
 // D2D copy of n doubles as a step element (collected like the kernels).
 cudaError_t stage_copy(const double* src, double* dst, long long n, cudaStream_t s);
 // One batched launch of kind k over nm members: recs[m] (device), start[m]

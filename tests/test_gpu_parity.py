@@ -663,6 +663,24 @@ def test_warm_started_solves_match_oracle_and_restart(monkeypatch):
     sim.close()
 
 
+@pytest.mark.parametrize("case", ["slot", "sphere"])
+def test_stencil_input_images_change_nothing(case, monkeypatch):
+    """The mixed stage stencil reads float-float images of v, Z, H and kappa,
+    split once per stage; LOWMACH_FF_IMAGES=0 splits each value as it is
+    loaded.  Every value enters the stencil's arithmetic as the same
+    float-float pair either way, so the runs agree bit for bit."""
+    prm, geo, f = W.slot_burner(64, 128) if case == "slot" else W.sphere_burner(24)
+    prm["precision"] = W.MIXED
+    out = {}
+    for img in ("1", "0"):
+        monkeypatch.setenv("LOWMACH_FF_IMAGES", img)
+        sim = gpu_run(prm, geo, f, 5)
+        out[img] = {k: sim.get(k) for k in ("U", "V", "Z", "H", "P")}
+        sim.close()
+    for k in out["1"]:
+        assert np.array_equal(out["1"][k], out["0"][k]), k
+
+
 def test_repeat_runs_are_bitwise_deterministic():
     prm, geo, f = W.periodic_blobs(48)
     a = gpu_run(prm, geo, f, 12)
