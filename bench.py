@@ -553,7 +553,7 @@ def roofline(res, peaks, precision):
     if top == "residual" and precision == "mixed":
         # float-float stencil on the FP32 pipes: bound by instruction issue
         # (4 warp instructions / clk / SM); warp instructions per cell measured
-        # by ncu (smsp__inst_executed.sum / cells on 128x256 and 192^3)
+        # by ncu (smsp__inst_executed.sum / cells on 256x512 and 192^3)
         dim = res["prm"]["dim"]
         wi = RESIDUAL_FF_WARP_INSTR_PER_CELL[dim] * res["ncell"]
         pk = ISSUE_PEAK_WARP_INSTR / 1e12
@@ -593,9 +593,9 @@ def roofline(res, peaks, precision):
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12    # 1.26 TFLOP/s
 ISSUE_PEAK_WARP_INSTR = 152 * 4 * 2.07e9           # warp instructions / s
-# float-float stage stencil: smsp__inst_executed.sum / cells (ncu; 2D 128x256; 3D 192^3, the
-# variant reading its inputs' float-float images)
-RESIDUAL_FF_WARP_INSTR_PER_CELL = {2: 129.8, 3: 213.6}
+# float-float stage stencil reading its inputs' float-float images: smsp__inst_executed.sum /
+# cells (ncu; 2D 256x512, 3D 192^3)
+RESIDUAL_FF_WARP_INSTR_PER_CELL = {2: 114.0, 3: 213.6}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 80.5 TFLOP/s
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel, by
 # (grid, precision, kernel); entries are removed when the kernel changes.
