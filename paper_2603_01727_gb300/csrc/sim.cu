@@ -46,6 +46,7 @@ struct AdjWs {
     double* F0[3];
     double* m0[3];          // predictor values: provisional momentum, T*, kappa*, P*, F*
     double *Ts, *kaps, *Ps;
+    double* rhos;           // rho* (read by the buoyancy term of the corrector's stencil)
     double* Fs[3];
     double *col, *grad, *obj, *rep, *part;
     double* cont;           // scratch of the reverse stencil sweep (slots x padded cells)
@@ -822,6 +823,7 @@ cudaError_t enqueue_step_sections(sim_t* s, long long n, cudaStream_t st, bool g
             if (e == cudaSuccess) e = cudaMemcpyAsync(s->adj.Fs[d], s->F[d], fp, cudaMemcpyDeviceToDevice, st);
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(s->adj.Ts, s->T, fp, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s->adj.rhos, r.rho_new, fp, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(s->adj.kaps, s->kap, fp, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(s->adj.Ps, s->P, sizeof(double) * (size_t)g.ncell, cudaMemcpyDeviceToDevice, st);
@@ -954,8 +956,8 @@ sim_status check_device_status(sim_t* s) {
 // adjoint helpers (defined with the adjoint entry points below)
 namespace {
 ResidArgs adj_resid_args(sim_t* s, double* const* v, const double* Z, const double* H, const double* kap,
-                         double* const* F, const double* T);
-AdjIn adj_in(sim_t* s, double* const* lv, double* lZ, double* lH);
+                         double* const* F, const double* T, const double* rho);
+AdjIn adj_in(sim_t* s, double* const* lv, double* lZ, double* lH, double* lrho);
 }  // namespace
 
 // ============================== C ABI ========================================
@@ -1485,8 +1487,9 @@ sim_status sim_time_kernel(sim_t* s, int kernel, int reps) {
                 AdjWs& A = s->adj;
                 AdjR lr;
                 for (int k = 0; k < 5; ++k) lr.R[k] = A.LR[k];
-                const ResidArgs a = adj_resid_args(s, s->v, s->Z, s->H, s->kap, s->F, s->T);
-                launch_residual_adj(g, s->ph, a, 0.0, lr, adj_in(s, A.Lv, A.LZ, A.LH), A.use_dual ? nullptr : A.cont,
+                const ResidArgs a = adj_resid_args(s, s->v, s->Z, s->H, s->kap, s->F, s->T, r.rho_n);
+                launch_residual_adj(g, s->ph, a, 0.0, lr, adj_in(s, A.Lv, A.LZ, A.LH, nullptr),
+                                    A.use_dual ? nullptr : A.cont,
                                     s->stream);
                 L += 2;
                 break;
@@ -1778,7 +1781,7 @@ size_t adj_layout(const sim_t* s, AdjWs* A, char* base) {
     a.Z0 = take(fpad); a.H0 = take(fpad); a.T0 = take(fpad); a.kap0 = take(fpad); a.rho0 = take(fpad);
     for (int d = 0; d < D; ++d) a.F0[d] = take(fpad);
     for (int d = 0; d < D; ++d) a.m0[d] = take(fpad);
-    a.Ts = take(fpad); a.kaps = take(fpad);
+    a.Ts = take(fpad); a.kaps = take(fpad); a.rhos = take(fpad);
     a.Ps = take(fcmp);
     for (int d = 0; d < D; ++d) a.Fs[d] = take(fpad);
     a.col = take(sizeof(double) * (size_t)g.n[0]);
@@ -1797,7 +1800,6 @@ const char* adj_unsupported(const sim_t* s) {
     if (s->prm.precision != SIM_FP64) return "the adjoint step needs precision SIM_FP64";
     if (s->ph.closed) return "the adjoint step needs an open system (p0 = 1)";
     if (s->ph.incompressible) return "the adjoint step needs the variable-density model";
-    if (s->ph.inv_Fr2 != 0.0) return "the adjoint step needs inv_Fr2 == 0";
     if (s->ph.transport != 0) return "the adjoint step needs the power-law transport (Eq 2.50)";
     for (int d = 0; d < s->g.dim; ++d)
         for (int q = 0; q < 2; ++q)
@@ -1849,7 +1851,7 @@ cudaError_t adj_poisson(sim_t* s, const double* lP, double* lb, cudaStream_t st)
 }
 
 ResidArgs adj_resid_args(sim_t* s, double* const* v, const double* Z, const double* H, const double* kap,
-                         double* const* F, const double* T) {
+                         double* const* F, const double* T, const double* rho) {
     ResidArgs a = resid_common(s);
     for (int d = 0; d < s->g.dim; ++d) {
         a.v[d] = v[d];
@@ -1859,12 +1861,12 @@ ResidArgs adj_resid_args(sim_t* s, double* const* v, const double* Z, const doub
     a.H = H;
     a.kap = kap;
     a.T = T;
-    a.rho = s->adj.rho0;     // read by the buoyancy term only, which the adjoint excludes
+    a.rho = rho;             // the stage's input density (read by the buoyancy term only)
     a.p0r = SC_P0_N;         // open system: p0 = 1 in every slot
     return a;
 }
 
-AdjIn adj_in(sim_t* s, double* const* lv, double* lZ, double* lH) {
+AdjIn adj_in(sim_t* s, double* const* lv, double* lZ, double* lH, double* lrho) {
     AdjWs& A = s->adj;
     AdjIn li;
     std::memset(&li, 0, sizeof(li));
@@ -1877,6 +1879,7 @@ AdjIn adj_in(sim_t* s, double* const* lv, double* lZ, double* lH) {
     li.out[RF_H] = lH;
     li.out[RF_KAP] = A.Lkap;
     li.out[RF_T] = A.LT;
+    li.out[RF_RHO] = lrho;   // buoyancy only (null without gravity)
     return li;
 }
 
@@ -1912,10 +1915,12 @@ sim_status sim_adjoint_begin(sim_t* s, void* d_workspace, size_t workspace_bytes
     s->adj.i_prev = 1;
     {
         // the hand-written reverse sweep of the stage stencil covers Le_F ==
-        // Le_O; differential diffusion (the regularised Le_eps(Z), N_eps(Z) of
-        // Eq 3.35) takes the exact dual-number gather
+        // Le_O without gravity; differential diffusion (the regularised
+        // Le_eps(Z), N_eps(Z) of Eq 3.35) and buoyancy (Eq 3.8b, through the
+        // stage's density) take the exact dual-number gather
         const char* dual = std::getenv("LOWMACH_ADJ_DUAL");
-        s->adj.use_dual = ((dual && dual[0] == '1') || s->ph.Le_F != s->ph.Le_O) ? 1 : 0;
+        s->adj.use_dual =
+            ((dual && dual[0] == '1') || s->ph.Le_F != s->ph.Le_O || s->ph.inv_Fr2 != 0.0) ? 1 : 0;
     }
     CK(cudaMemsetAsync(s->adj.lam_base, 0, s->adj.lam_bytes, s->stream));
     CK(cudaStreamSynchronize(s->stream));
@@ -1983,6 +1988,7 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
         La += 1;
     }
 
+    const bool grav = ph.inv_Fr2 != 0.0;
     for (int stage = 1; stage >= 0; --stage) {   // corrector, then predictor
         const bool corr = stage == 1;
         double* const* lv = corr ? A.Lv : A.Lvs;
@@ -2067,12 +2073,16 @@ sim_status sim_adjoint_step(sim_t* s, double objective_weight, double* dJ_dprofi
             for (int d = 0; d < D; ++d) CK(cudaMemsetAsync(A.Lvs[d], 0, fpad, st));
             CK(cudaMemsetAsync(A.LZs, 0, fpad, st));
             CK(cudaMemsetAsync(A.LHs, 0, fpad, st));
-            const ResidArgs a = adj_resid_args(s, s->vs, s->Zs, s->Hs, A.kaps, A.Fs, A.Ts);
-            launch_residual_adj(g, ph, a, 0.0, lr, adj_in(s, A.Lvs, A.LZs, A.LHs), A.use_dual ? nullptr : A.cont,
-                                st);
+            // the stencil read rho* (buoyancy): its lambda joins Lrho, which the
+            // corrector's state relation^T has consumed and zeroed and the
+            // predictor's flux and state relation^T use next as lambda rho*
+            const ResidArgs a = adj_resid_args(s, s->vs, s->Zs, s->Hs, A.kaps, A.Fs, A.Ts, A.rhos);
+            launch_residual_adj(g, ph, a, 0.0, lr, adj_in(s, A.Lvs, A.LZs, A.LHs, grav ? Lrho : nullptr),
+                                A.use_dual ? nullptr : A.cont, st);
         } else {
-            const ResidArgs a = adj_resid_args(s, A.v0, A.Z0, A.H0, A.kap0, A.F0, A.T0);
-            launch_residual_adj(g, ph, a, 0.0, lr, adj_in(s, A.Lv, A.LZ, A.LH), A.use_dual ? nullptr : A.cont, st);
+            const ResidArgs a = adj_resid_args(s, A.v0, A.Z0, A.H0, A.kap0, A.F0, A.T0, A.rho0);
+            launch_residual_adj(g, ph, a, 0.0, lr, adj_in(s, A.Lv, A.LZ, A.LH, grav ? Lrn : nullptr),
+                                A.use_dual ? nullptr : A.cont, st);
         }
         La += A.use_dual ? 1 : 2;
     }
