@@ -301,9 +301,9 @@ void sim_destroy(sim_t *sim);
  *            aligned, live until end) for the adjoint state lambda and the
  *            recomputed step's values.  begin zeroes lambda and the accumulated
  *            forcing adjoints.  Supported: dim 2, SIM_FP64, open system, no
- *            incompressible switch, power-law transport, no isothermal walls
- *            (SIM_EINVAL else); Le_F != Le_O and inv_Fr2 != 0 transpose the
- *            stage stencil by its exact dual-number gather.
+ *            incompressible switch (SIM_EINVAL else); Le_F != Le_O and
+ *            inv_Fr2 != 0 transpose the stage stencil by its exact
+ *            dual-number gather.
  *   adjoint_step: the simulation must hold the state of some level n (e.g. from
  *            sim_state_load).  Recomputes step n (the simulation ends at level
  *            n+1), adds objective_weight * d(objective at n+1)/d(state n+1) to

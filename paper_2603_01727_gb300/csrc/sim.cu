@@ -1800,10 +1800,6 @@ const char* adj_unsupported(const sim_t* s) {
     if (s->prm.precision != SIM_FP64) return "the adjoint step needs precision SIM_FP64";
     if (s->ph.closed) return "the adjoint step needs an open system (p0 = 1)";
     if (s->ph.incompressible) return "the adjoint step needs the variable-density model";
-    if (s->ph.transport != 0) return "the adjoint step needs the power-law transport (Eq 2.50)";
-    for (int d = 0; d < s->g.dim; ++d)
-        for (int q = 0; q < 2; ++q)
-            if (s->prm.bc[d][q] == SIM_BC_WALL_T) return "the adjoint step has no isothermal walls";
     return nullptr;
 }
 

@@ -1566,7 +1566,7 @@ __global__ void k_ghost_adj(Geom g, const uint8_t* __restrict__ klo, const uint8
             const long long ia = side ? i_n : i_1;
             const int kind = side ? khi[q] : klo[q];
             double sg;
-            if (kind == BC_INFLOW) sg = -1.0;
+            if (kind == BC_INFLOW || kind == BC_WALL_T) sg = -1.0;   // mirrors about a fixed value
             else if (kind == BC_OUTFLOW) sg = 1.0;
             else if (kind == BC_WALL) sg = vel ? -1.0 : 1.0;
             else sg = normal ? -1.0 : 1.0;
@@ -1576,10 +1576,11 @@ __global__ void k_ghost_adj(Geom g, const uint8_t* __restrict__ klo, const uint8
     }
 }
 
-// State relation transposed (FP64 path, open system: rho = 1/T, kappa = T^sigma,
-// T = cT (cA (|x| + log1p(e^-2|x|)) + cB (Z - 1) + H), x = k (Z - 1)):
-// dT/dZ = cT (cA k tanh(x) + cB), dT/dH = cT, drho/dT = -1/T^2,
-// dkappa/dT = sigma kappa / T.
+// State relation transposed (FP64 path, open system: rho = 1/T, kappa = T^sigma
+// or Sutherland's law, T = cT (cA (|x| + log1p(e^-2|x|)) + cB (Z - 1) + H),
+// x = k (Z - 1)): dT/dZ = cT (cA k tanh(x) + cB), dT/dH = cT, drho/dT =
+// -1/T^2, dkappa/dT = sigma kappa / T (power law) or kappa (3/(2T) - 1/(T + C))
+// (Eq 4.12).
 __global__ void k_state_adj(Geom g, Phys ph, const double* __restrict__ Z, const double* __restrict__ T,
                             const double* __restrict__ kap, double* lT, double* lrho, double* lkap, double* lZ,
                             double* lH) {
@@ -1587,7 +1588,8 @@ __global__ void k_state_adj(Geom g, Phys ph, const double* __restrict__ Z, const
     if (t >= g.ncell) return;
     const long long c = pad_index(g, t);
     const double Tv = T[c];
-    const double lt = lT[c] - lrho[c] / (Tv * Tv) + lkap[c] * ph.sigma * kap[c] / Tv;
+    const double dk = (ph.transport == 1) ? kap[c] * (1.5 / Tv - 1.0 / (Tv + ph.suth_C)) : ph.sigma * kap[c] / Tv;
+    const double lt = lT[c] - lrho[c] / (Tv * Tv) + lkap[c] * dk;
     const double x = ph.k * (Z[c] - 1.0);
     lZ[c] += lt * ph.cT * (ph.cA * ph.k * tanh(x) + ph.cB);
     lH[c] += lt * ph.cT;
