@@ -2646,7 +2646,8 @@ __global__ void __launch_bounds__(FT3) fdm(int nx, int ny, int nz, const float* 
 // barriers.  A thread owns an x-pair of cells (one of each colour) of a row;
 // a block of 32 x 8 pairs (256 threads, x fastest) walks zc consecutive
 // planes, so a plane's z-neighbours are the rows it read one step before and
-// reads one step after (L1).  Indices are 32-bit (levels under 2^31 cells).
+// reads one step after (L1).  Indices are 32-bit: larger levels keep the
+// z-marching kernels.
 // ---------------------------------------------------------------------------
 namespace k3s {
 
@@ -3643,7 +3644,8 @@ void enqueue_down(PoissonPlan* pl, int l, cudaStream_t s) {
             }
         }
         enqueue_down2<T, 1>(pl, l, L, C, fc, s);
-    } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells && pl->mg3_sweeps && pl->nb == 1) {
+    } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells && pl->mg3_sweeps && pl->nb == 1 &&
+               pl->lev[l].N < (1LL << 31)) {
         // colour-sweep passes; the residual goes through z (not live during the
         // down pass: the previous iteration's z was consumed by its pq)
         const int zc = pl->k3s_zc;
@@ -3711,7 +3713,8 @@ void enqueue_up(PoissonPlan* pl, int l, cudaStream_t s) {
             }
         }
         enqueue_up2<T, 1>(pl, l, L, C, uc, s);
-    } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells && pl->mg3_sweeps && pl->nb == 1) {
+    } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells && pl->mg3_sweeps && pl->nb == 1 &&
+               pl->lev[l].N < (1LL << 31)) {
         const int zc = pl->k3s_zc;
         const dim3 grid = k3s::grid_of(L.n, zc);
         T* u = (l == 0) ? (T*)pl->u0pre : (T*)pl->lev[l].upre;
