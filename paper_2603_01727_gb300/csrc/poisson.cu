@@ -3860,7 +3860,9 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
     if (ir) {
         // four x-consecutive cells per thread step when nx % 4 == 0 and x (the
         // caller's array) is 16-byte aligned
-        const int vec4 = (pl->lev[0].n[0] % 4 == 0) && (((uintptr_t)x & 15) == 0);
+        // (LOWMACH_IR_VEC4=0: one cell per thread step)
+        const char* v4 = std::getenv("LOWMACH_IR_VEC4");
+        const int vec4 = (pl->lev[0].n[0] % 4 == 0) && (((uintptr_t)x & 15) == 0) && !(v4 && v4[0] == '0');
         const dim3 rbr(vec4 ? reduce_blocks(pl->N / 4) : reduce_blocks(pl->N), pl->nb);
         launch(k_ir_step<DIM>, rbr, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r, (const float*)pl->p32[0],
                (const float*)pl->p32[1], pl->r32, pl->part1, pl->part2, pl->scal, pl->ictl, pl->cnt + CNT_REF,
