@@ -624,96 +624,112 @@ __global__ void __launch_bounds__(NTV)
 // operations, so that only three FP64 operations per cell (two additions, the
 // squared norm) use the 1/64-rate FP64 pipe.  The FP32 search direction and
 // r.z are kept.
+// W x-consecutive cells per thread step of the reliable-update CG step.
+template <int DIM, int W>
+__device__ __forceinline__ void ir_vec(const LvT<double>& L, double* __restrict__ x, double* __restrict__ r64,
+                                       const float* __restrict__ p, float* __restrict__ r32, float alpha,
+                                       const FF* wd, int i0, int stride, int iend, double& rr, double& sr) {
+    constexpr int G = W / 4;   // float4 groups per step
+    auto ld1 = [&](int i) -> float { return fmaf(alpha, p[i], 0.0f); };
+    auto ldw = [&](int i, float* out) {
+#pragma unroll
+        for (int g4 = 0; g4 < G; ++g4) {
+            const float4 v = *reinterpret_cast<const float4*>(p + i + 4 * g4);
+            out[4 * g4 + 0] = fmaf(alpha, v.x, 0.0f);
+            out[4 * g4 + 1] = fmaf(alpha, v.y, 0.0f);
+            out[4 * g4 + 2] = fmaf(alpha, v.z, 0.0f);
+            out[4 * g4 + 3] = fmaf(alpha, v.w, 0.0f);
+        }
+    };
+    const int nx = L.n[0], ny = L.n[1];
+    const int NW = L.N / W;
+    for (int q = i0; q < min(NW, iend); q += stride) {
+        const int t0 = W * q;
+        int c[3];
+        coords(L, t0, c);
+        float ev[W];
+        ldw(t0, ev);
+        float el = 0.0f, er = 0.0f;
+        if (c[0] > 0) el = ld1(t0 - 1);
+        else if (L.per[0]) el = ld1(t0 + nx - 1);
+        if (c[0] + W < nx) er = ld1(t0 + W);
+        else if (L.per[0]) er = ld1(t0 + W - nx);
+        float nb[2][2][W];   // [y, z][low, high] neighbour rows
+        int clo = 0, p3 = 3;
+#pragma unroll
+        for (int d = 1; d < DIM; ++d) {
+            const int n = L.n[d];
+            const int sd = (d == 1) ? nx : nx * ny;
+#pragma unroll
+            for (int i = 0; i < W; ++i) nb[d - 1][0][i] = nb[d - 1][1][i] = 0.0f;
+            if (c[d] > 0) ldw(t0 - sd, nb[d - 1][0]);
+            else if (L.per[d]) ldw(t0 + (n - 1) * sd, nb[d - 1][0]);
+            if (c[d] < n - 1) ldw(t0 + sd, nb[d - 1][1]);
+            else if (L.per[d]) ldw(t0 - (n - 1) * sd, nb[d - 1][1]);
+            clo += (L.per[d] ? 2 : (int)(c[d] > 0) + (int)(c[d] < n - 1)) * p3;
+            p3 *= 3;
+        }
+        double rin[W], xin[W];
+#pragma unroll
+        for (int h = 0; h < W / 2; ++h) {
+            const double2 ra = *reinterpret_cast<const double2*>(r64 + t0 + 2 * h);
+            const double2 xa = *reinterpret_cast<const double2*>(x + t0 + 2 * h);
+            rin[2 * h] = ra.x;
+            rin[2 * h + 1] = ra.y;
+            xin[2 * h] = xa.x;
+            xin[2 * h + 1] = xa.y;
+        }
+        double rout[W], xout[W];
+        float r32o[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const float a0 = (i == 0) ? el : ev[i - 1];
+            const float b0 = (i == W - 1) ? er : ev[i + 1];
+            FF off;
+            off += wd[0] * (FF(a0, 0.0f) + FF(b0, 0.0f));
+#pragma unroll
+            for (int d = 1; d < DIM; ++d) off += wd[d] * (FF(nb[d - 1][0][i], 0.0f) + FF(nb[d - 1][1][i], 0.0f));
+            const int xg = c[0] + i;
+            const int cl = (L.per[0] ? 2 : (int)(xg > 0) + (int)(xg < nx - 1)) + clo;
+            const FF Ae = FF(L.diag[cl]) * FF(ev[i], 0.0f) - off;
+            const FF rv = FF(rin[i]) - Ae;
+            xout[i] = xin[i] + f2d_bits(ev[i]);
+            rout[i] = f2d_bits(rv.hi) + f2d_bits(rv.lo);
+            r32o[i] = rv.hi;
+            rr = fma(rout[i], rout[i], rr);
+            sr += rout[i];
+        }
+#pragma unroll
+        for (int h = 0; h < W / 2; ++h) {
+            *reinterpret_cast<double2*>(x + t0 + 2 * h) = make_double2(xout[2 * h], xout[2 * h + 1]);
+            *reinterpret_cast<double2*>(r64 + t0 + 2 * h) = make_double2(rout[2 * h], rout[2 * h + 1]);
+        }
+#pragma unroll
+        for (int g4 = 0; g4 < G; ++g4)
+            *reinterpret_cast<float4*>(r32 + t0 + 4 * g4) =
+                make_float4(r32o[4 * g4], r32o[4 * g4 + 1], r32o[4 * g4 + 2], r32o[4 * g4 + 3]);
+    }
+}
+
 // The cells of the reliable-update CG step handled by one thread: compact
-// indices (quads of four x-consecutive cells when vec4) from i0 by stride,
-// below iend; adds ||r||^2 and sum r of the new residual to rr, sr.
-template <int DIM>
+// indices (groups of vec4 = 4 or 8 x-consecutive cells, else single cells)
+// from i0 by stride, below iend; adds ||r||^2 and sum r of the new residual
+// to rr, sr.
+template <int DIM, int W = 4>
 __device__ __forceinline__ void ir_cells(const LvT<double>& L, double* __restrict__ x, double* __restrict__ r64,
                                          const float* __restrict__ p, float* __restrict__ r32, float alpha,
                                          int vec4, int i0, int stride, int iend, double& rr, double& sr) {
     // the correction e = alpha p at compact index i (the product rounded once)
     auto ld1 = [&](int i) -> float { return fmaf(alpha, p[i], 0.0f); };
-    auto ld4 = [&](int i) -> float4 {
-        float4 v = *reinterpret_cast<const float4*>(p + i);
-        v.x = fmaf(alpha, v.x, 0.0f);
-        v.y = fmaf(alpha, v.y, 0.0f);
-        v.z = fmaf(alpha, v.z, 0.0f);
-        v.w = fmaf(alpha, v.w, 0.0f);
-        return v;
-    };
     FF wd[3];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) wd[d] = FF(L.w[d]);
     if (vec4) {
-        // four x-consecutive cells per thread step (nx % 4 == 0, x 16-byte
-        // aligned; the launch is sized by N / 4): one coordinate map, 16-byte
+        // W x-consecutive cells per thread step (nx % W == 0, x 16-byte
+        // aligned; the launch is sized by N / W): one coordinate map, 16-byte
         // loads of p's rows (e = alpha p) and of x, r64; each cell's
         // arithmetic is the scalar path's, in its order
-        const int nx = L.n[0], ny = L.n[1];
-        const int N4 = L.N >> 2;
-        for (int q = i0; q < min(N4, iend); q += stride) {
-            const int t0 = 4 * q;
-            int c[3];
-            coords(L, t0, c);
-            const float4 ec = ld4(t0);
-            float el = 0.0f, er = 0.0f;
-            if (c[0] > 0) el = ld1(t0 - 1);
-            else if (L.per[0]) el = ld1(t0 + nx - 1);
-            if (c[0] + 4 < nx) er = ld1(t0 + 4);
-            else if (L.per[0]) er = ld1(t0 + 4 - nx);
-            float4 nb[2][2];   // [y, z][low, high] neighbour rows
-            int clo = 0, p3 = 3;
-#pragma unroll
-            for (int d = 1; d < DIM; ++d) {
-                const int n = L.n[d];
-                const int stride = (d == 1) ? nx : nx * ny;
-                nb[d - 1][0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                nb[d - 1][1] = nb[d - 1][0];
-                if (c[d] > 0) nb[d - 1][0] = ld4(t0 - stride);
-                else if (L.per[d]) nb[d - 1][0] = ld4(t0 + (n - 1) * stride);
-                if (c[d] < n - 1) nb[d - 1][1] = ld4(t0 + stride);
-                else if (L.per[d]) nb[d - 1][1] = ld4(t0 - (n - 1) * stride);
-                clo += (L.per[d] ? 2 : (int)(c[d] > 0) + (int)(c[d] < n - 1)) * p3;
-                p3 *= 3;
-            }
-            const double2 ra = *reinterpret_cast<const double2*>(r64 + t0);
-            const double2 rb = *reinterpret_cast<const double2*>(r64 + t0 + 2);
-            const double2 xa = *reinterpret_cast<const double2*>(x + t0);
-            const double2 xb = *reinterpret_cast<const double2*>(x + t0 + 2);
-            const float ev[4] = {ec.x, ec.y, ec.z, ec.w};
-            const double rin[4] = {ra.x, ra.y, rb.x, rb.y};
-            const double xin[4] = {xa.x, xa.y, xb.x, xb.y};
-            double rout[4], xout[4];
-            float r32o[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float a0 = (i == 0) ? el : ev[i - 1];
-                const float b0 = (i == 3) ? er : ev[i + 1];
-                FF off;
-                off += wd[0] * (FF(a0, 0.0f) + FF(b0, 0.0f));
-#pragma unroll
-                for (int d = 1; d < DIM; ++d) {
-                    const float4 lo = nb[d - 1][0], hi = nb[d - 1][1];
-                    const float a = (i == 0) ? lo.x : (i == 1) ? lo.y : (i == 2) ? lo.z : lo.w;
-                    const float b = (i == 0) ? hi.x : (i == 1) ? hi.y : (i == 2) ? hi.z : hi.w;
-                    off += wd[d] * (FF(a, 0.0f) + FF(b, 0.0f));
-                }
-                const int xg = c[0] + i;
-                const int cl = (L.per[0] ? 2 : (int)(xg > 0) + (int)(xg < nx - 1)) + clo;
-                const FF Ae = FF(L.diag[cl]) * FF(ev[i], 0.0f) - off;
-                const FF rv = FF(rin[i]) - Ae;
-                xout[i] = xin[i] + f2d_bits(ev[i]);
-                rout[i] = f2d_bits(rv.hi) + f2d_bits(rv.lo);
-                r32o[i] = rv.hi;
-                rr = fma(rout[i], rout[i], rr);
-                sr += rout[i];
-            }
-            *reinterpret_cast<double2*>(x + t0) = make_double2(xout[0], xout[1]);
-            *reinterpret_cast<double2*>(x + t0 + 2) = make_double2(xout[2], xout[3]);
-            *reinterpret_cast<double2*>(r64 + t0) = make_double2(rout[0], rout[1]);
-            *reinterpret_cast<double2*>(r64 + t0 + 2) = make_double2(rout[2], rout[3]);
-            *reinterpret_cast<float4*>(r32 + t0) = make_float4(r32o[0], r32o[1], r32o[2], r32o[3]);
-        }
+        ir_vec<DIM, W>(L, x, r64, p, r32, alpha, wd, i0, stride, iend, rr, sr);
     }
     for (int t = vec4 ? L.N : i0; t < min(L.N, iend); t += stride) {
         int c[3];
@@ -745,7 +761,7 @@ __device__ __forceinline__ void ir_cells(const LvT<double>& L, double* __restric
     }
 }
 
-template <int DIM>
+template <int DIM, int W>
 __global__ void __launch_bounds__(NTV)
     k_ir_step(LvT<double> L, double* __restrict__ x, double* __restrict__ r64, const float* p0, const float* p1,
               float* __restrict__ r32, double* part, double* part_s, double* scal, int* ictl, unsigned int* cnt,
@@ -766,7 +782,7 @@ __global__ void __launch_bounds__(NTV)
     part += (long long)fb * gridDim.x;
     part_s += (long long)fb * gridDim.x;
     double rr = 0.0, sr = 0.0;
-    ir_cells<DIM>(L, x, r64, p, r32, alpha, vec4, blockIdx.x * NTV + threadIdx.x, gridDim.x * NTV, INT_MAX, rr,
+    ir_cells<DIM, W>(L, x, r64, p, r32, alpha, vec4, blockIdx.x * NTV + threadIdx.x, gridDim.x * NTV, INT_MAX, rr,
                   sr);
     __shared__ double red[2 * (NTV / 32)];
     block_sum2_t<NTV, double>(rr, sr, red);
@@ -3860,14 +3876,19 @@ void body(PoissonPlan* pl, double* x, cudaStream_t s, cudaGraphConditionalHandle
     if (ir) {
         // four x-consecutive cells per thread step when nx % 4 == 0 and x (the
         // caller's array) is 16-byte aligned
-        // (LOWMACH_IR_VEC4=0: one cell per thread step)
+        // (LOWMACH_IR_VEC4=0: one cell per thread step; =8: eight when nx % 8 == 0)
         const char* v4 = std::getenv("LOWMACH_IR_VEC4");
-        const int vec4 = (pl->lev[0].n[0] % 4 == 0) && (((uintptr_t)x & 15) == 0) && !(v4 && v4[0] == '0');
-        const dim3 rbr(vec4 ? reduce_blocks(pl->N / 4) : reduce_blocks(pl->N), pl->nb);
-        launch(k_ir_step<DIM>, rbr, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r, (const float*)pl->p32[0],
-               (const float*)pl->p32[1], pl->r32, pl->part1, pl->part2, pl->scal, pl->ictl, pl->cnt + CNT_REF,
-               pl->rtol,
-               pl->max_iter, h, ug, vec4);
+        int vec4 = ((pl->lev[0].n[0] % 4 == 0) && (((uintptr_t)x & 15) == 0) && !(v4 && v4[0] == '0')) ? 4 : 0;
+        if (vec4 && v4 && v4[0] == '8' && pl->lev[0].n[0] % 8 == 0) vec4 = 8;
+        const dim3 rbr(vec4 ? reduce_blocks(pl->N / vec4) : reduce_blocks(pl->N), pl->nb);
+        if (vec4 == 8)
+            launch(k_ir_step<DIM, 8>, rbr, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r,
+                   (const float*)pl->p32[0], (const float*)pl->p32[1], pl->r32, pl->part1, pl->part2, pl->scal,
+                   pl->ictl, pl->cnt + CNT_REF, pl->rtol, pl->max_iter, h, ug, vec4);
+        else
+            launch(k_ir_step<DIM, 4>, rbr, NTV, 0, s, make_lv<double>(pl->lev[0], DIM), x, pl->r,
+                   (const float*)pl->p32[0], (const float*)pl->p32[1], pl->r32, pl->part1, pl->part2, pl->scal,
+                   pl->ictl, pl->cnt + CNT_REF, pl->rtol, pl->max_iter, h, ug, vec4);
         pl->launches += 1;
     } else {
         // the update runs two cells per thread step when N is even and x (the
