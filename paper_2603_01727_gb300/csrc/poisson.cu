@@ -2962,6 +2962,72 @@ __global__ void __launch_bounds__(NT) red_out(LvT<T> L, const TF* __restrict__ f
     }
 }
 
+// CG direction in a whole-level pass: p = (z - mean z) + beta p_old (no
+// neighbours), then the operator pass q = A p with the partial sums of p.q,
+// whose last block forms alpha = r.z / p.q as the z-marching pq does.
+template <class T, class V>
+__global__ void __launch_bounds__(NT) pdir(LvT<V> L, const T* __restrict__ z, V* p0, V* p1, const double* scal,
+                                           const int* ictl, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const int it = ictl[PI_IT];
+    const V* __restrict__ pold = (it & 1) ? p0 : p1;
+    V* __restrict__ pnew = (it & 1) ? p1 : p0;
+    const V beta = (V)scal[PS_BETA], mz = (V)scal[PS_MEANZ];
+    const int y = row_y();
+    const int z1 = min((int)(blockIdx.z + 1) * zc, L.n[2]);
+    if (y >= L.n[1]) return;
+    for (int zz = blockIdx.z * zc; zz < z1; ++zz) {
+#pragma unroll
+        for (int color = 0; color < 2; ++color) {
+            const int x = pair_x(y, zz, color);
+            if (x >= L.n[0]) continue;
+            const int i = x + L.n[0] * (y + L.n[1] * zz);
+            V pv = (V)z[i] - mz;
+            if (it > 0) pv = fma(beta, pold[i], pv);
+            pnew[i] = pv;
+        }
+    }
+}
+
+template <class V>
+__global__ void __launch_bounds__(NT) qop(LvT<V> L, const V* p0, const V* p1, V* __restrict__ q, double* part,
+                                          double* scal, const int* ictl, unsigned int* cnt, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const int it = ictl[PI_IT];
+    const V* __restrict__ p = (it & 1) ? p1 : p0;
+    V acc = (V)0;
+    const int y = row_y();
+    const int z1 = min((int)(blockIdx.z + 1) * zc, L.n[2]);
+    if (y < L.n[1]) {
+        for (int zz = blockIdx.z * zc; zz < z1; ++zz) {
+#pragma unroll
+            for (int color = 0; color < 2; ++color) {
+                const int x = pair_x(y, zz, color);
+                if (x >= L.n[0]) continue;
+                const Nb b = nbr(L, x, y, zz);
+                const V pv = p[b.i];
+                const V qv = L.diag[b.cls] * pv - off7<V>(L, b, p);
+                q[b.i] = qv;
+                acc = fma(pv, qv, acc);
+            }
+        }
+    }
+    __shared__ double red[NT / 32];
+    __shared__ float redf[NT / 32];
+    const double bacc = block_sum_any<NT>(acc, red, redf);
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (threadIdx.x == 0) part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = bacc;
+    if (arrive_last_n(cnt, (unsigned int)nb)) {
+        const double PQ = sum_parts_cg<NT>(part, nb, red);
+        if (threadIdx.x == 0) {
+            scal[PS_ALPHA] = scal[PS_RZ] / PQ;
+            *cnt = 0u;
+        }
+    }
+}
+
 inline dim3 grid_of(const int n[3], int zc = kZC) {
     const int npx = (n[0] + 1) / 2;
     return dim3((unsigned)((npx + BX - 1) / BX), (unsigned)((n[1] + BY - 1) / BY), (unsigned)((n[2] + zc - 1) / zc));
@@ -3816,6 +3882,17 @@ void enqueue_tail(PoissonPlan* pl, cudaStream_t s) {
     pl->launches += 1;
 }
 
+// The large 3D fine level's CG direction and operator as two whole-level
+// passes (FP64 vectors; 192^3: 46.3-46.4 -> 45.3 ms per step) or the
+// z-marching pq, which stages p once per plane (FP32 vectors of the
+// refinement mode: 15.04-15.14 against 15.39 ms for the passes).
+// LOWMACH_PQ_PASSES=0 / 1 forces either.
+bool pq_passes(bool fp32_vectors) {
+    const char* e = std::getenv("LOWMACH_PQ_PASSES");
+    if (e && (e[0] == '0' || e[0] == '1')) return e[0] == '1';
+    return !fp32_vectors;
+}
+
 // CG direction update + operator application: FP64 vectors, or the FP32
 // inner vectors in refinement mode.
 template <class T, int DIM>
@@ -3831,6 +3908,23 @@ void enqueue_pq(PoissonPlan* pl, cudaStream_t s) {
             launch(k2::pq<T, double>, grid, k2::NT, 0, s, make_lv<double>(pl->lev[0], DIM), (const T*)pl->z, pl->p[0],
                                                       pl->p[1], pl->q, pl->part2, pl->scal, pl->ictl,
                                                       pl->cnt + CNT_PQ);
+    } else if (!pl->mg3_tiles && pl->lev[0].N >= pl->mg3_min_cells && pl->mg3_sweeps && pl->nb == 1 &&
+               pq_passes(ir)) {
+        const dim3 grid = k3s::grid_of(pl->lev[0].n, k3s::kZC);
+        if (ir) {
+            launch(k3s::pdir<T, float>, grid, k3s::NT, 0, s, make_lv<float>(pl->lev[0], DIM), (const T*)pl->z,
+                   pl->p32[0], pl->p32[1], (const double*)pl->scal, (const int*)pl->ictl, k3s::kZC);
+            launch(k3s::qop<float>, grid, k3s::NT, 0, s, make_lv<float>(pl->lev[0], DIM), (const float*)pl->p32[0],
+                   (const float*)pl->p32[1], pl->q32, pl->part2, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_PQ,
+                   k3s::kZC);
+        } else {
+            launch(k3s::pdir<T, double>, grid, k3s::NT, 0, s, make_lv<double>(pl->lev[0], DIM), (const T*)pl->z,
+                   pl->p[0], pl->p[1], (const double*)pl->scal, (const int*)pl->ictl, k3s::kZC);
+            launch(k3s::qop<double>, grid, k3s::NT, 0, s, make_lv<double>(pl->lev[0], DIM), (const double*)pl->p[0],
+                   (const double*)pl->p[1], pl->q, pl->part2, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_PQ,
+                   k3s::kZC);
+        }
+        pl->launches += 1;
     } else if (!pl->mg3_tiles && pl->lev[0].N >= pl->mg3_min_cells) {
         const dim3 grid = k3_tile_grid(pl->lev[0].n, k3::FP);
         const size_t pl3 = (size_t)k3::RING * k3::SB * k3::SB;
