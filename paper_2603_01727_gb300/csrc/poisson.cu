@@ -85,6 +85,7 @@ constexpr long long kTailCellsF32 = 4096;   // largest level handled by the tail
 constexpr long long kTailCellsF64 = 128;    // (FP64: one SM's FP64 rate is 1/64 of FP32)
 constexpr size_t kTailSmemMax = 200 * 1024;
 constexpr long long kMg3MinCells = 1LL << 20;   // smallest 3D level on the z-marching kernels
+constexpr long long kMg3SweepMinCells = 1LL << 17;   // ... on the colour-sweep passes
 
 template <int DIM>
 struct Tile;
@@ -3477,15 +3478,20 @@ bool poisson_plan_init_batch(PoissonPlan* pl, int dim, const int n[3], const dou
         // LOWMACH_MG3_TILES=1: the cube-tile 3D kernels instead of the z-marching ones
         const char* e = std::getenv("LOWMACH_MG3_TILES");
         pl->mg3_tiles = (e && e[0] == '1') ? 1 : 0;
-        // levels below this many cells keep the cube tiles (too few z-marching blocks)
-        const char* m = std::getenv("LOWMACH_MG3_MIN_CELLS");
-        pl->mg3_min_cells = (m && std::atoll(m) >= 0) ? std::atoll(m) : kMg3MinCells;
-        // those levels on whole-level colour-sweep passes (LOWMACH_MG3_SWEEPS=0:
+        // large levels on whole-level colour-sweep passes (LOWMACH_MG3_SWEEPS=0:
         // the z-marching kernels, which read each array once but serialise a
         // block's planes behind barriers; C3 192^3 mixed 16.77 -> 15.60 ms,
         // FP64 57.6 -> 48.0 ms per step)
         const char* w = std::getenv("LOWMACH_MG3_SWEEPS");
         pl->mg3_sweeps = (w && w[0] == '0') ? 0 : 1;
+        // levels below this many cells keep the cube tiles: 2^17 for the
+        // colour sweeps (the 96^3 level of a 192^3 grid on them too: mixed
+        // 15.06-15.13 -> 14.89 ms, FP64 45.3 -> 44.0 ms), 2^20 for the
+        // z-marching kernels (fewer planes per block would leave them too few
+        // blocks)
+        const char* m = std::getenv("LOWMACH_MG3_MIN_CELLS");
+        pl->mg3_min_cells = (m && std::atoll(m) >= 0) ? std::atoll(m)
+                                                      : (pl->mg3_sweeps ? kMg3SweepMinCells : kMg3MinCells);
         const char* zc = std::getenv("LOWMACH_K3S_ZC");
         pl->k3s_zc = (zc && std::atoi(zc) >= 1 && std::atoi(zc) <= 64) ? std::atoi(zc) : k3s::kZC;
     }
