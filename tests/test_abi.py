@@ -81,3 +81,29 @@ def test_invalid_parameters_rejected_without_gpu(lib_path):
     assert lib.sim_workspace_size(ctypes.byref(L.params_struct(bad)), ctypes.byref(sz)) == L.SIM_EINVAL
     h = ctypes.c_void_p()
     assert lib.sim_create(ctypes.byref(p), None, 0, None, ctypes.byref(h)) == L.SIM_ENOMEM
+
+
+def test_variant_parameters_validated_without_gpu(lib_path):
+    """The semi-enclosed system, the transport law and the isothermal walls are
+    checked by the host before any CUDA call."""
+    import workloads as W
+    from paper_2603_01727_gb300 import lowmach as L
+    lib = L.load()
+    sz = ctypes.c_size_t()
+
+    def status(prm):
+        return lib.sim_workspace_size(ctypes.byref(L.params_struct(prm)), ctypes.byref(sz))
+
+    chamber, _, _ = W.filling_chamber(16)
+    assert status(chamber) == L.SIM_OK                                   # inlet, no outlet
+    slot, _, _ = W.slot_burner(32, 64)
+    assert status(dict(slot, closed_system=2)) == L.SIM_EINVAL           # semi-enclosed with an outlet
+    assert status(dict(slot, closed_system=3)) == L.SIM_EINVAL
+    assert status(dict(chamber, closed_system=1)) == L.SIM_EINVAL        # enclosed with an inlet
+    cavity, _, _ = W.heated_cavity(16)
+    assert status(cavity) == L.SIM_OK                                    # isothermal walls, Sutherland
+    assert status(dict(cavity, transport=2)) == L.SIM_EINVAL
+    assert status(dict(cavity, sutherland_C=-0.1)) == L.SIM_EINVAL
+    assert status(dict(cavity, bc=[[6, 6], [3, 3], [0, 0]])) == L.SIM_EINVAL   # unknown kind
+    tc, _, _ = W.taylor_couette(32)
+    assert status(tc) == L.SIM_OK
