@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -2670,6 +2671,7 @@ namespace k3s {
 
 constexpr int BX = 32, BY = 8, NT = BX * BY;
 constexpr int kZC = 4;  // consecutive planes per block (default)
+constexpr int kZC8 = 2; // ... of the eight-cell passes
 
 // The x coordinate of this thread's cell of colour `color` ((x + y + z) & 1).
 __device__ __forceinline__ int pair_x(int y, int z, int color) {
@@ -2961,6 +2963,164 @@ __global__ void __launch_bounds__(NT) red_out(LvT<T> L, const TF* __restrict__ f
             }
         }
     }
+}
+
+// ---- eight x-consecutive cells per thread (nx % 8 == 0): 16-byte loads of the
+// cells' row segment and of the four neighbour rows, scalar loads of the two
+// x-neighbours at the ends.  A thread owns segment (x0 .. x0 + 7, y) of the
+// planes of its block's z-chunk; threads run along x, then y.
+template <class T>
+__device__ __forceinline__ void ld8(const T* __restrict__ p, T* o) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+        o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+    } else {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const double2 a = *reinterpret_cast<const double2*>(p + 2 * h);
+            o[2 * h] = a.x;
+            o[2 * h + 1] = a.y;
+        }
+    }
+}
+template <class T>
+__device__ __forceinline__ void st8(T* __restrict__ p, const T* o) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4*>(p + 4) = make_float4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) *reinterpret_cast<double2*>(p + 2 * h) = make_double2(o[2 * h], o[2 * h + 1]);
+    }
+}
+
+// Row-uniform data of a thread's segment: its y, the offsets to the y and z
+// neighbour rows (0 when outside a non-periodic level), the x-end offsets.
+struct Seg {
+    int x0, y, valid;
+    int dym, dyp, cy;   // y neighbour rows (offsets from the segment) and class
+    int dxm, dxp;       // x neighbours of the first / last cell (offsets from the segment's start)
+    bool hym, hyp, hxm, hxp;   // whether each neighbour exists (inside or periodic)
+};
+template <class T>
+__device__ __forceinline__ Seg seg_of(const LvT<T>& L) {
+    Seg g;
+    const int nx = L.n[0], ny = L.n[1], nseg = nx >> 3;
+    const int gid = (int)(blockIdx.x * NT + threadIdx.x);
+    g.valid = gid < nseg * ny;
+    const int sxi = gid % nseg;
+    g.y = gid / nseg;
+    g.x0 = 8 * sxi;
+    g.hym = g.y > 0 || L.per[1];
+    g.hyp = g.y < ny - 1 || L.per[1];
+    g.dym = (g.y > 0) ? -nx : nx * (ny - 1);
+    g.dyp = (g.y < ny - 1) ? nx : -nx * (ny - 1);
+    g.cy = cls_of(g.y, ny, L.per[1]);
+    g.hxm = g.x0 > 0 || L.per[0];
+    g.hxp = g.x0 + 8 < nx || L.per[0];
+    g.dxm = (g.x0 > 0) ? -1 : nx - 1;
+    g.dxp = (g.x0 + 8 < nx) ? 8 : 8 - nx;
+    return g;
+}
+
+// The segment's cells and neighbour rows of plane z (zeros outside).
+template <class T>
+struct Rows8 {
+    T c[8], ym[8], yp[8], zm[8], zp[8];
+    T xm, xp;
+    int cz;
+};
+template <class T>
+__device__ __forceinline__ void rows8(const LvT<T>& L, const Seg& g, const T* __restrict__ u, int z, int base,
+                                      Rows8<T>& R) {
+    const int nz = L.n[2], sz = L.n[0] * L.n[1];
+    const bool hzm = z > 0 || L.per[2], hzp = z < nz - 1 || L.per[2];
+    const int dzm = (z > 0) ? -sz : sz * (nz - 1);
+    const int dzp = (z < nz - 1) ? sz : -sz * (nz - 1);
+    R.cz = cls_of(z, nz, L.per[2]);
+    ld8(u + base, R.c);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) R.ym[i] = R.yp[i] = R.zm[i] = R.zp[i] = (T)0;
+    if (g.hym) ld8(u + base + g.dym, R.ym);
+    if (g.hyp) ld8(u + base + g.dyp, R.yp);
+    if (hzm) ld8(u + base + dzm, R.zm);
+    if (hzp) ld8(u + base + dzp, R.zp);
+    R.xm = g.hxm ? u[base + g.dxm] : (T)0;
+    R.xp = g.hxp ? u[base + g.dxp] : (T)0;
+}
+
+// The off-diagonal sum of cell i of the segment, in off7's order.
+template <class T>
+__device__ __forceinline__ T off8(const LvT<T>& L, const Rows8<T>& R, int i) {
+    const T left = (i > 0) ? R.c[i - 1] : R.xm;
+    const T right = (i < 7) ? R.c[i + 1] : R.xp;
+    T off = L.w[0] * (left + right) + L.w[1] * (R.ym[i] + R.yp[i]);
+    off += L.w[2] * (R.zm[i] + R.zp[i]);
+    return off;
+}
+
+template <class T>
+__device__ __forceinline__ int cls8(const LvT<T>& L, const Seg& g, const Rows8<T>& R, int i) {
+    return cls_of(g.x0 + i, L.n[0], L.per[0]) + 3 * g.cy + 9 * R.cz;
+}
+
+// One colour of a Gauss-Seidel sweep in place, eight cells per thread: the
+// segment is written back whole, the other colour's values unchanged (the
+// pass reads them only), so a concurrent reader sees the same values.
+template <class T, class TF>
+__global__ void __launch_bounds__(NT) sweep8(LvT<T> L, const TF* __restrict__ f, T* u, int color,
+                                             const double* __restrict__ scal_r, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const TF mr = scal_r ? (TF)scal_r[PS_MEANR] : (TF)0;
+    const Seg g = seg_of(L);
+    if (!g.valid) return;
+    const int z1 = min((int)(blockIdx.y + 1) * zc, L.n[2]);
+    for (int z = blockIdx.y * zc; z < z1; ++z) {
+        const int base = g.x0 + L.n[0] * (g.y + L.n[1] * z);
+        Rows8<T> R;
+        rows8(L, g, u, z, base, R);
+        TF fv[8];
+        ld8(f + base, fv);
+        T out[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            out[i] = R.c[i];
+            if (((g.x0 + i + g.y + z) & 1) == color)
+                out[i] = ((T)(fv[i] - mr) + off8(L, R, i)) * L.invd[cls8(L, g, R, i)];
+        }
+        st8(u + base, out);
+    }
+}
+
+// Residual r = f - A u, eight cells per thread.
+template <class T, class TF>
+__global__ void __launch_bounds__(NT) resid8(LvT<T> L, const TF* __restrict__ f, const T* __restrict__ u,
+                                             T* __restrict__ r, const double* __restrict__ scal_r, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const TF mr = scal_r ? (TF)scal_r[PS_MEANR] : (TF)0;
+    const Seg g = seg_of(L);
+    if (!g.valid) return;
+    const int z1 = min((int)(blockIdx.y + 1) * zc, L.n[2]);
+    for (int z = blockIdx.y * zc; z < z1; ++z) {
+        const int base = g.x0 + L.n[0] * (g.y + L.n[1] * z);
+        Rows8<T> R;
+        rows8(L, g, u, z, base, R);
+        TF fv[8];
+        ld8(f + base, fv);
+        T out[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            out[i] = (T)(fv[i] - mr) - (L.diag[cls8(L, g, R, i)] * R.c[i] - off8(L, R, i));
+        st8(r + base, out);
+    }
+}
+
+inline dim3 grid8(const int n[3], int zc) {
+    const long long segs = (long long)(n[0] / 8) * n[1];
+    return dim3((unsigned)((segs + NT - 1) / NT), (unsigned)((n[2] + zc - 1) / zc));
 }
 
 // CG direction in a whole-level pass: p = (z - mean z) + beta p_old (no
@@ -3716,6 +3876,17 @@ void enqueue_up2(PoissonPlan* pl, int l, const LvT<T>& L, const LvT<T>& C, const
                (unsigned int*)nullptr);
 }
 
+// Eight cells per thread in the colour sweeps and residual of the large 3D
+// levels (nx % 8 == 0): FP32 levels (192^3 mixed 14.89 -> 14.58 ms); the FP64
+// levels keep the cell pairs (44.07 against 47.48 ms: 128 registers).
+// LOWMACH_K3S_V8=0 / 1 forces either.
+bool k3s_v8(const int n[3], bool fp32) {
+    if (n[0] % 8 != 0) return false;
+    const char* e = std::getenv("LOWMACH_K3S_V8");
+    if (e && (e[0] == '0' || e[0] == '1')) return e[0] == '1';
+    return fp32;
+}
+
 // Right-hand side of the fine multigrid level: the FP64 CG residual, or the
 // FP32 inner residual in refinement mode.
 template <class T, int DIM>
@@ -3741,23 +3912,22 @@ void enqueue_down(PoissonPlan* pl, int l, cudaStream_t s) {
         T* u = (l == 0) ? (T*)pl->u0pre : (T*)pl->lev[l].upre;
         T* r = (T*)pl->z;
         const double* sr = pl->scal;
-        if (l == 0 && ir) {
-            const float* f = pl->r32;
-            launch(k3s::red0<T, float>, grid, k3s::NT, 0, s, L, f, u, sr, zc);
-            launch(k3s::sweep<T, float>, grid, k3s::NT, 0, s, L, f, u, 1, sr, zc);
-            launch(k3s::resid<T, float>, grid, k3s::NT, 0, s, L, f, (const T*)u, r, sr, zc);
-        } else if (l == 0) {
-            const double* f = pl->r;
-            launch(k3s::red0<T, double>, grid, k3s::NT, 0, s, L, f, u, sr, zc);
-            launch(k3s::sweep<T, double>, grid, k3s::NT, 0, s, L, f, u, 1, sr, zc);
-            launch(k3s::resid<T, double>, grid, k3s::NT, 0, s, L, f, (const T*)u, r, sr, zc);
-        } else {
-            const T* f = (const T*)pl->lev[l].f;
-            const double* nsr = nullptr;
-            launch(k3s::red0<T, T>, grid, k3s::NT, 0, s, L, f, u, nsr, zc);
-            launch(k3s::sweep<T, T>, grid, k3s::NT, 0, s, L, f, u, 1, nsr, zc);
-            launch(k3s::resid<T, T>, grid, k3s::NT, 0, s, L, f, (const T*)u, r, nsr, zc);
-        }
+        const bool v8 = k3s_v8(L.n, sizeof(T) == 4);
+        const dim3 g8 = k3s::grid8(L.n, k3s::kZC8);
+        auto down_passes = [&](auto f, const double* srr) {
+            using TFp = std::remove_cv_t<std::remove_pointer_t<decltype(f)>>;
+            launch(k3s::red0<T, TFp>, grid, k3s::NT, 0, s, L, f, u, srr, zc);
+            if (v8) {
+                launch(k3s::sweep8<T, TFp>, g8, k3s::NT, 0, s, L, f, u, 1, srr, k3s::kZC8);
+                launch(k3s::resid8<T, TFp>, g8, k3s::NT, 0, s, L, f, (const T*)u, r, srr, k3s::kZC8);
+            } else {
+                launch(k3s::sweep<T, TFp>, grid, k3s::NT, 0, s, L, f, u, 1, srr, zc);
+                launch(k3s::resid<T, TFp>, grid, k3s::NT, 0, s, L, f, (const T*)u, r, srr, zc);
+            }
+        };
+        if (l == 0 && ir) down_passes((const float*)pl->r32, sr);
+        else if (l == 0) down_passes((const double*)pl->r, sr);
+        else down_passes((const T*)pl->lev[l].f, (const double*)nullptr);
         launch(k3s::restrict3<T>, k3s::restrict_grid(C.n), k3s::NT, k3s::kRestrictSmem * (sizeof(T) / 4), s, L, C,
                (const T*)r, fc);
         pl->launches += 3;
@@ -3810,17 +3980,32 @@ void enqueue_up(PoissonPlan* pl, int l, cudaStream_t s) {
         // the reducing pass keeps the default plane chunk (its last block sums
         // one partial per block)
         const dim3 rgrid = k3s::grid_of(L.n, k3s::kZC);
+        const bool v8 = k3s_v8(L.n, sizeof(T) == 4);
+        const dim3 g8 = k3s::grid8(L.n, k3s::kZC8);
         if (l == 0 && ir) {
-            launch(k3s::sweep<T, float>, grid, k3s::NT, 0, s, L, (const float*)pl->r32, u, 1, (const double*)pl->scal, zc);
+            if (v8)
+                launch(k3s::sweep8<T, float>, g8, k3s::NT, 0, s, L, (const float*)pl->r32, u, 1,
+                       (const double*)pl->scal, k3s::kZC8);
+            else
+                launch(k3s::sweep<T, float>, grid, k3s::NT, 0, s, L, (const float*)pl->r32, u, 1,
+                       (const double*)pl->scal, zc);
             launch(k3s::red_out<T, float, true>, rgrid, k3s::NT, 0, s, L, (const float*)pl->r32, (const T*)u,
                    (T*)pl->z, pl->part0, pl->part1, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_UP0, k3s::kZC);
         } else if (l == 0) {
-            launch(k3s::sweep<T, double>, grid, k3s::NT, 0, s, L, (const double*)pl->r, u, 1, (const double*)pl->scal, zc);
+            if (v8)
+                launch(k3s::sweep8<T, double>, g8, k3s::NT, 0, s, L, (const double*)pl->r, u, 1,
+                       (const double*)pl->scal, k3s::kZC8);
+            else
+                launch(k3s::sweep<T, double>, grid, k3s::NT, 0, s, L, (const double*)pl->r, u, 1,
+                       (const double*)pl->scal, zc);
             launch(k3s::red_out<T, double, true>, rgrid, k3s::NT, 0, s, L, (const double*)pl->r, (const T*)u,
                    (T*)pl->z, pl->part0, pl->part1, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_UP0, k3s::kZC);
         } else {
             const T* f = (const T*)pl->lev[l].f;
-            launch(k3s::sweep<T, T>, grid, k3s::NT, 0, s, L, f, u, 1, (const double*)nullptr, zc);
+            if (v8)
+                launch(k3s::sweep8<T, T>, g8, k3s::NT, 0, s, L, f, u, 1, (const double*)nullptr, k3s::kZC8);
+            else
+                launch(k3s::sweep<T, T>, grid, k3s::NT, 0, s, L, f, u, 1, (const double*)nullptr, zc);
             launch(k3s::red_out<T, T, false>, rgrid, k3s::NT, 0, s, L, f, (const T*)u, (T*)pl->lev[l].upost,
                    (double*)nullptr, (double*)nullptr, (double*)nullptr, (const int*)nullptr,
                    (unsigned int*)nullptr, k3s::kZC);
