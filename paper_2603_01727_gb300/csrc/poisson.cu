@@ -3118,6 +3118,63 @@ __global__ void __launch_bounds__(NT) resid8(LvT<T> L, const TF* __restrict__ f,
     }
 }
 
+// The red half of the post-smoothing, eight cells per thread (as red_out).
+template <class T, class TF, bool FINE>
+__global__ void __launch_bounds__(NT) red_out8(LvT<T> L, const TF* __restrict__ f, const T* __restrict__ u_in,
+                                               T* __restrict__ u_out, double* part_rz, double* part_sz,
+                                               double* scal, const int* ictl, unsigned int* cnt, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const TF mr = FINE ? (TF)scal[PS_MEANR] : (TF)0;
+    TF rz = (TF)0, sz = (TF)0;
+    const Seg g = seg_of(L);
+    if (g.valid) {
+        const int z1 = min((int)(blockIdx.y + 1) * zc, L.n[2]);
+        for (int z = blockIdx.y * zc; z < z1; ++z) {
+            const int base = g.x0 + L.n[0] * (g.y + L.n[1] * z);
+            Rows8<T> R;
+            rows8(L, g, u_in, z, base, R);
+            TF fv[8];
+            ld8(f + base, fv);
+            T out[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const TF fi = fv[i] - mr;
+                out[i] = (((g.x0 + i + g.y + z) & 1) == 0) ? ((T)fi + off8(L, R, i)) * L.invd[cls8(L, g, R, i)]
+                                                           : R.c[i];
+                if (FINE) {
+                    rz = fma(fi, (TF)out[i], rz);
+                    sz += (TF)out[i];
+                }
+            }
+            st8(u_out + base, out);
+        }
+    }
+    if (FINE) {
+        __shared__ double red[2 * (NT / 32)];
+        __shared__ float redf[2 * (NT / 32)];
+        double brz, bsz;
+        block_sum2_any<NT>(rz, sz, red, redf, &brz, &bsz);
+        const int nb = gridDim.x * gridDim.y;
+        const int bl = blockIdx.x + gridDim.x * blockIdx.y;
+        if (threadIdx.x == 0) {
+            part_rz[bl] = brz;
+            part_sz[bl] = bsz;
+        }
+        if (arrive_last_n(cnt, (unsigned int)nb)) {
+            double RZ, SZ;
+            sum_parts2_cg<NT>(part_rz, part_sz, nb, red, &RZ, &SZ);
+            if (threadIdx.x == 0) {
+                const int it = ictl[PI_IT];
+                scal[PS_BETA] = (it == 0) ? 0.0 : RZ / scal[PS_RZ];
+                scal[PS_RZ] = RZ;
+                scal[PS_MEANZ] = SZ / (double)L.N;
+                *cnt = 0u;
+            }
+        }
+    }
+}
+
 inline dim3 grid8(const int n[3], int zc) {
     const long long segs = (long long)(n[0] / 8) * n[1];
     return dim3((unsigned)((segs + NT - 1) / NT), (unsigned)((n[2] + zc - 1) / zc));
@@ -3989,8 +4046,14 @@ void enqueue_up(PoissonPlan* pl, int l, cudaStream_t s) {
             else
                 launch(k3s::sweep<T, float>, grid, k3s::NT, 0, s, L, (const float*)pl->r32, u, 1,
                        (const double*)pl->scal, zc);
-            launch(k3s::red_out<T, float, true>, rgrid, k3s::NT, 0, s, L, (const float*)pl->r32, (const T*)u,
-                   (T*)pl->z, pl->part0, pl->part1, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_UP0, k3s::kZC);
+            if (v8)
+                launch(k3s::red_out8<T, float, true>, g8, k3s::NT, 0, s, L, (const float*)pl->r32, (const T*)u,
+                       (T*)pl->z, pl->part0, pl->part1, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_UP0,
+                       k3s::kZC8);
+            else
+                launch(k3s::red_out<T, float, true>, rgrid, k3s::NT, 0, s, L, (const float*)pl->r32, (const T*)u,
+                       (T*)pl->z, pl->part0, pl->part1, pl->scal, (const int*)pl->ictl, pl->cnt + CNT_UP0,
+                       k3s::kZC);
         } else if (l == 0) {
             if (v8)
                 launch(k3s::sweep8<T, double>, g8, k3s::NT, 0, s, L, (const double*)pl->r, u, 1,
@@ -4006,9 +4069,14 @@ void enqueue_up(PoissonPlan* pl, int l, cudaStream_t s) {
                 launch(k3s::sweep8<T, T>, g8, k3s::NT, 0, s, L, f, u, 1, (const double*)nullptr, k3s::kZC8);
             else
                 launch(k3s::sweep<T, T>, grid, k3s::NT, 0, s, L, f, u, 1, (const double*)nullptr, zc);
-            launch(k3s::red_out<T, T, false>, rgrid, k3s::NT, 0, s, L, f, (const T*)u, (T*)pl->lev[l].upost,
-                   (double*)nullptr, (double*)nullptr, (double*)nullptr, (const int*)nullptr,
-                   (unsigned int*)nullptr, k3s::kZC);
+            if (v8)
+                launch(k3s::red_out8<T, T, false>, g8, k3s::NT, 0, s, L, f, (const T*)u, (T*)pl->lev[l].upost,
+                       (double*)nullptr, (double*)nullptr, (double*)nullptr, (const int*)nullptr,
+                       (unsigned int*)nullptr, k3s::kZC8);
+            else
+                launch(k3s::red_out<T, T, false>, rgrid, k3s::NT, 0, s, L, f, (const T*)u, (T*)pl->lev[l].upost,
+                       (double*)nullptr, (double*)nullptr, (double*)nullptr, (const int*)nullptr,
+                       (unsigned int*)nullptr, k3s::kZC);
         }
         pl->launches += 2;
     } else if (!pl->mg3_tiles && pl->lev[l].N >= pl->mg3_min_cells) {
