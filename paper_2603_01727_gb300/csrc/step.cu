@@ -10,6 +10,7 @@
 // Poisson right-hand side b are compact interior arrays.
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "step.cuh"
@@ -2142,8 +2143,9 @@ void launch_ff_images(const Geom& g, const double* const src[6], float2* dst, cu
         ++*launches;
         return;
     }
-    long long nb = (g.npad + NT - 1) / NT;
-    if (nb > 8 * 152) nb = 8 * 152;
+    // one padded cell per thread (192^3: 14.49 -> 14.43 ms per step against a
+    // grid-stride loop over 8 x 152 blocks)
+    const long long nb = (g.npad + NT - 1) / NT;
     k_ff_images<<<(int)nb, NT, 0, s>>>(g.npad, 6, fs, dst);
     ++*launches;
 }
