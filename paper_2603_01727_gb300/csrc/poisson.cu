@@ -3118,6 +3118,53 @@ __global__ void __launch_bounds__(NT) resid8(LvT<T> L, const TF* __restrict__ f,
     }
 }
 
+// Red cells from a zero guess, eight cells per thread (the segment's black
+// cells get 0: the black sweep that follows writes them before any read).
+template <class T, class TF>
+__global__ void __launch_bounds__(NT) red0_8(LvT<T> L, const TF* __restrict__ f, T* __restrict__ u,
+                                             const double* __restrict__ scal_r, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const TF mr = scal_r ? (TF)scal_r[PS_MEANR] : (TF)0;
+    const Seg g = seg_of(L);
+    if (!g.valid) return;
+    const int z1 = min((int)(blockIdx.y + 1) * zc, L.n[2]);
+    for (int z = blockIdx.y * zc; z < z1; ++z) {
+        const int base = g.x0 + L.n[0] * (g.y + L.n[1] * z);
+        const int cz = cls_of(z, L.n[2], L.per[2]);
+        TF fv[8];
+        ld8(f + base, fv);
+        T out[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int cls = cls_of(g.x0 + i, L.n[0], L.per[0]) + 3 * g.cy + 9 * cz;
+            out[i] = (((g.x0 + i + g.y + z) & 1) == 0) ? (T)(fv[i] - mr) * L.invd[cls] : (T)0;
+        }
+        st8(u + base, out);
+    }
+}
+
+// u += P uc, eight cells per thread.
+template <class T>
+__global__ void __launch_bounds__(NT) prolong_add8(LvT<T> L, LvT<T> C, const T* __restrict__ uc, T* u, int zc) {
+    pdl_wait();
+    pdl_trigger();
+    const Seg g = seg_of(L);
+    if (!g.valid) return;
+    const int z1 = min((int)(blockIdx.y + 1) * zc, L.n[2]);
+    for (int z = blockIdx.y * zc; z < z1; ++z) {
+        const int base = g.x0 + L.n[0] * (g.y + L.n[1] * z);
+        T v[8];
+        ld8(u + base, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int gw[3] = {g.x0 + i, g.y, z};
+            v[i] = v[i] + prolong_at<T, 3>(C, uc, gw);
+        }
+        st8(u + base, v);
+    }
+}
+
 // The red half of the post-smoothing, eight cells per thread (as red_out).
 template <class T, class TF, bool FINE>
 __global__ void __launch_bounds__(NT) red_out8(LvT<T> L, const TF* __restrict__ f, const T* __restrict__ u_in,
@@ -3973,7 +4020,8 @@ void enqueue_down(PoissonPlan* pl, int l, cudaStream_t s) {
         const dim3 g8 = k3s::grid8(L.n, k3s::kZC8);
         auto down_passes = [&](auto f, const double* srr) {
             using TFp = std::remove_cv_t<std::remove_pointer_t<decltype(f)>>;
-            launch(k3s::red0<T, TFp>, grid, k3s::NT, 0, s, L, f, u, srr, zc);
+            if (v8) launch(k3s::red0_8<T, TFp>, g8, k3s::NT, 0, s, L, f, u, srr, k3s::kZC8);
+            else launch(k3s::red0<T, TFp>, grid, k3s::NT, 0, s, L, f, u, srr, zc);
             if (v8) {
                 launch(k3s::sweep8<T, TFp>, g8, k3s::NT, 0, s, L, f, u, 1, srr, k3s::kZC8);
                 launch(k3s::resid8<T, TFp>, g8, k3s::NT, 0, s, L, f, (const T*)u, r, srr, k3s::kZC8);
@@ -4033,12 +4081,13 @@ void enqueue_up(PoissonPlan* pl, int l, cudaStream_t s) {
         const int zc = pl->k3s_zc;
         const dim3 grid = k3s::grid_of(L.n, zc);
         T* u = (l == 0) ? (T*)pl->u0pre : (T*)pl->lev[l].upre;
-        launch(k3s::prolong_add<T>, grid, k3s::NT, 0, s, L, C, uc, u, zc);
         // the reducing pass keeps the default plane chunk (its last block sums
         // one partial per block)
         const dim3 rgrid = k3s::grid_of(L.n, k3s::kZC);
         const bool v8 = k3s_v8(L.n, sizeof(T) == 4);
         const dim3 g8 = k3s::grid8(L.n, k3s::kZC8);
+        if (v8) launch(k3s::prolong_add8<T>, g8, k3s::NT, 0, s, L, C, uc, u, k3s::kZC8);
+        else launch(k3s::prolong_add<T>, grid, k3s::NT, 0, s, L, C, uc, u, zc);
         if (l == 0 && ir) {
             if (v8)
                 launch(k3s::sweep8<T, float>, g8, k3s::NT, 0, s, L, (const float*)pl->r32, u, 1,
