@@ -887,3 +887,19 @@ def test_taylor_couette_penalised_flow_approaches_the_exact_profile():
         h = prm["L"][0] / n
         errs.append(float(np.sqrt(np.sum((V(st.v[1], pb.g) - ve)[fluid] ** 2) * h * h)))
     assert errs[1] < errs[0] and errs[1] < 2.5e-2, errs
+
+
+def test_nprime_of_the_p0_ode_is_the_slope_of_the_flame_sheet_at_unit_lewis():
+    """Eq 2.39 regularised like Eq 3.35b: with Le = 1 the coefficient N' of
+    Eq 2.38 equals dF_eps/dZ, the Z-derivative of the regularised flame-sheet
+    function of the state relation (T = Q/(S+1)(F_eps(Z) + H)), which is what
+    makes the ODE and the mass constraint agree; its limits are N'_O = 1
+    (oxidiser side) and N'_F = -1/S (fuel side)."""
+    fp = flame.derived_parameters(0.055, 7.0, 0.5, 1e-3)
+    S, k = fp["S"], fp["k"]
+    Z = np.linspace(0.0, S + 1.0, 4001)
+    h = 1e-6
+    slope = (flame.F_eps(Z + h, S, k) - flame.F_eps(Z - h, S, k)) / (2.0 * h)
+    assert np.allclose(flame.Nprime_eps(Z, fp), slope, rtol=0.0, atol=1e-8)
+    assert flame.Nprime_eps(np.array(-5.0), fp) == pytest.approx(1.0, abs=1e-12)
+    assert flame.Nprime_eps(np.array(S + 5.0), fp) == pytest.approx(-1.0 / S, abs=1e-12)
