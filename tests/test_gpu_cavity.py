@@ -1,7 +1,7 @@
 """Differentially heated cavity (Sec. 4.3): isothermal walls (Eq 4.16a-b) and
 Sutherland transport (Eq 4.12) on the GPU, against the oracle and against the
 paper's converged hydrodynamic pressure and Nusselt numbers at Ra = 1e2
-(Tables 4 and 5).
+(Tables 3 and 5).
 """
 
 import numpy as np
@@ -91,7 +91,7 @@ def _nusselt_middle(T, KAPPA, FX, prm, eps):
 
 def test_heated_cavity_ra1e2_steady_state_matches_table5():
     """Ra = 1e2, eps = 0.6 run to steady state on 48^2 and 72^2 uniform grids
-    (refinement ratio 1.5, as in the grid study of Table 4), then Richardson
+    (refinement ratio 1.5, as in the grid study of Table 3), then Richardson
     extrapolated at second order: p0 within 3e-5 of both the paper's value
     (0.95738) and its reference value (0.95736) of Table 5, and the mid-line
     Nusselt number within 2e-4 of theirs (0.9787)."""
@@ -108,6 +108,6 @@ def test_heated_cavity_ra1e2_steady_state_matches_table5():
     p_inf = p0[1] + (p0[1] - p0[0]) / (r2 - 1.0)
     nu_inf = nu[1] + (nu[1] - nu[0]) / (r2 - 1.0)
     print("p0", p0, "extrapolated", p_inf, "Nu_M", nu, "extrapolated", nu_inf)
-    assert p0[0] > p0[1] > p_inf                     # monotone approach from above, as in Table 4
+    assert p0[0] > p0[1] > p_inf                     # monotone approach from above, as in Table 3
     assert abs(p_inf - 0.95738) < 3e-5 and abs(p_inf - 0.95736) < 3e-5
     assert abs(nu_inf - 0.9787) < 2e-4
