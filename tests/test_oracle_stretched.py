@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import stretched as G
+from conftest import golden
 
 
 def _axis(n, alpha):
@@ -61,6 +62,23 @@ def test_alpha_hits_the_requested_spacing_ratio(n, ratio):
     assert G.spacing_ratio(n, a) == pytest.approx(ratio, rel=1e-10)
     assert a == pytest.approx(2.0 * np.arccosh(np.sqrt(ratio)), rel=0.05)
     assert G.alpha_for_ratio(n, 1.0) == 0.0
+
+
+def test_stretched_grids_have_the_printed_largest_spacing():
+    """Tables 3 and 4 print max(dx_i) of every stretched grid of the cavity's
+    grid studies.  Eq 4.18 on the faces i/n, with alpha solved for
+    max(dx) = m min(dx), gives all eight within one unit of the last printed
+    digit (the table truncates some and rounds others).  A uniform grid misses
+    them by far more, and a one-sided tanh clustering with the same ratio
+    misses the first (0.019533 on 64 cells)."""
+    rows = golden("cavity_grid_spacing_tables3_4.txt")
+    assert len(rows) == 8
+    for m, n, want in rows:
+        m, n, want = float(m), int(n), float(want)
+        dx = np.diff(G.tanh_faces(n, G.alpha_for_ratio(n, m)))
+        assert abs(dx.max() - want) < 1e-5, (m, n, dx.max(), want)
+        assert dx.max() / dx.min() == pytest.approx(m, rel=1e-10)
+        assert abs(1.0 / n - want) > 0.15 * want                # far from the uniform width
 
 
 def test_alpha_grows_with_the_ratio():
