@@ -17,11 +17,16 @@ mass-flux immersed boundary method" (arXiv 2603.01727):
 * ``poisson``    -- exact solve of the compact pressure Poisson equation (Eqs 3.9, 3.17, 3.24)
 * ``step``       -- predictor-corrector step (Eqs 3.1-3.19, 3.23-3.26)
 * ``convergence``-- observed order and GCI (Eqs 4.1-4.3)
+* ``stretched``  -- the tanh grid map (Eq 4.18) and 1D non-uniform operators
+  (Eqs 3.20-3.24) used to check the stretched path of ``operators``
+* ``objective``  -- integrated heat release (the adjoint's objective)
 
 Everything is float64 numpy; the only library primitives used as steps are the
-FFT / DCT of ``scipy.fft`` (Poisson solve) and dense linear algebra of
+FFT / DCT of ``scipy.fft`` (Poisson solve on a uniform grid), the sparse LU of
+``scipy.sparse.linalg`` (Poisson solve on a stretched grid), a bracketing root
+finder of ``scipy.optimize`` (the alpha of Eq 4.18) and dense linear algebra of
 ``numpy.linalg`` (brute-force checks).  There is no blocking, fusion or
 reordering beyond what the equations state.
 """
 
-from . import operators, flame, boundary, ibm, poisson, step, convergence  # noqa: F401
+from . import operators, flame, boundary, ibm, poisson, step, convergence, stretched  # noqa: F401

@@ -129,7 +129,10 @@ class Boundary:
                 continue
             for side in (0, 1):
                 i0, i1, i2, i3 = _layers(g, d, side)
-                x0, x1, x2, x3 = [(i - 0.5) * g.h[d] for i in (i0, i1, i2, i3)]
+                if g.uniform:
+                    x0, x1, x2, x3 = [(i - 0.5) * g.h[d] for i in (i0, i1, i2, i3)]
+                else:                                                # stretched: the centres
+                    x0, x1, x2, x3 = [g.xc[d][i] for i in (i0, i1, i2, i3)]
                 A = (x2 - x0) * (x3 - x0) / ((x2 - x1) * (x3 - x1))
                 B = (x1 - x0) * (x3 - x0) / ((x1 - x2) * (x3 - x2))
                 C = (x1 - x0) * (x2 - x0) / ((x1 - x3) * (x2 - x3))

@@ -87,5 +87,8 @@ def density(p0, T):
 
 
 def closed_p0(mass, T_interior, dV):
-    """Enclosed system: p0 * int(1/T) dV = m (Eq 2.40, midpoint rule Eq 3.22)."""
-    return mass / (np.sum(1.0 / T_interior) * dV)
+    """Enclosed system: p0 * int(1/T) dV = m (Eq 2.40, midpoint rule Eq 3.22);
+    dV is the cell volume, or an array of them on a stretched grid."""
+    if np.ndim(dV) == 0:
+        return mass / (np.sum(1.0 / T_interior) * dV)
+    return mass / np.sum(dV / T_interior)

@@ -17,10 +17,20 @@ eigenvalue of mode k along d is -(2 - 2 cos theta_k)/h_d^2 with
 theta_k = 2 pi k / n_d (periodic) or pi k / n_d (Neumann).  ``dense_solve`` is the
 brute-force check: it assembles L column by column from ``apply`` and solves
 the augmented system [L 1; 1^T 0].
+
+On a stretched grid (Eq 4.18) L is no longer diagonalised by those bases.
+There ``solve`` assembles L as a sum of Kronecker products of the 1D
+operators delta_1(delta_1 . / delta_1 x_d) / delta_1 x_d and factors, once
+per grid, the augmented system [W L, w; w^T, 0] (W the cell volumes, w their
+vector): W L is symmetric (the volume-weighted sum of L P is the net
+boundary flux, zero here), and the border row selects the solution with zero
+volume-weighted mean.
 """
 
 import numpy as np
 import scipy.fft as sfft
+import scipy.sparse as sp
+from scipy.sparse.linalg import splu
 
 from .operators import V, diff_to_faces, faces_diff_to_cells
 
@@ -67,8 +77,54 @@ def eigenvalues(g, periodic):
     return lam
 
 
+def _operator_1d(g, d, periodic):
+    """delta_1(delta_1 P / delta_1 x_d) / delta_1 x_d along direction d of a
+    stretched grid (n_d x n_d, zero flux through non-periodic ends)."""
+    n = g.n[d]
+    xc, dx = g.xc[d], g.dx[d][1:-1]
+    G = sp.lil_matrix((n + 1, n))              # interface gradients, faces 0..n
+    for f in range(1, n):
+        G[f, f] = 1.0 / (xc[f + 1] - xc[f])
+        G[f, f - 1] = -1.0 / (xc[f + 1] - xc[f])
+    if periodic[d]:
+        for f in (0, n):                       # the same interface seen from both ends
+            G[f, 0] = 1.0 / (xc[1] - xc[0])
+            G[f, n - 1] = -1.0 / (xc[1] - xc[0])
+    D = sp.lil_matrix((n, n + 1))
+    for c in range(n):
+        D[c, c + 1] = 1.0 / dx[c]
+        D[c, c] = -1.0 / dx[c]
+    return (D.tocsr() @ G.tocsr()).tocsr()
+
+
+def _stretched_factor(g, periodic):
+    key = tuple(bool(p) for p in periodic)
+    cache = g.__dict__.setdefault("_poisson_lu", {})
+    if key not in cache:
+        L = None
+        for d in range(g.dim):
+            term = sp.identity(1, format="csr")
+            for dd in reversed(range(g.dim)):           # x is the fastest index
+                term = sp.kron(term, _operator_1d(g, dd, periodic) if dd == d
+                               else sp.identity(g.n[dd], format="csr"), format="csr")
+            L = term if L is None else L + term
+        w = np.asarray(g.dV * np.ones(tuple(g.n[d] for d in reversed(range(g.dim))))).ravel()
+        WL = sp.diags(w) @ L
+        M = sp.bmat([[WL, sp.csr_matrix(w[:, None])], [sp.csr_matrix(w[None, :]), None]], format="csc")
+        cache[key] = (splu(M), w, L)
+    return cache[key]
+
+
 def solve(b, g, periodic):
-    """Zero-mean P with L P = b - mean(b) (exact, transform-diagonalised)."""
+    """Zero-mean P with L P = b - mean(b) (exact: transform-diagonalised on a
+    uniform grid, a sparse LU factorisation on a stretched one, where both
+    means are volume-weighted)."""
+    if not g.uniform:
+        lu, w, _ = _stretched_factor(g, periodic)
+        r = np.asarray(b, dtype=np.float64).ravel()
+        r = r - np.dot(w, r) / np.sum(w)
+        sol = lu.solve(np.concatenate([w * r, [0.0]]))
+        return sol[:-1].reshape(np.asarray(b).shape)
     X = np.asarray(b, dtype=np.float64).astype(np.complex128)
     for d in range(g.dim):
         a = g.ax(d)

@@ -42,6 +42,11 @@ the design notes of the package):
    (augmented-matrix solution, Sec. 3.3).
  * ``incompressible``: T = rho = kappa = p0 = 1 regardless of Z, H -- the
    constant-density runs of Secs 4.2-4.3 (Re = Pe/Pr in the viscous term).
+ * ``stretch`` (alpha of Eq 4.18 per direction, 0 for uniform) gives the
+   tanh-stretched grids of the cavity (Sec. 4.3.1): every operator takes the
+   non-uniform weights of Eqs 3.20-3.22, the mean of b and of P is
+   volume-weighted, and the Poisson equation is solved by a sparse
+   factorisation.  Immersed bodies are not built on stretched grids.
 """
 
 import copy
@@ -49,10 +54,11 @@ import copy
 import numpy as np
 
 from . import flame, poisson
-from .boundary import (Boundary, INFLOW, OUTFLOW, WALL, SLIP, WALL_T, face_end, cell_end)
+from .boundary import (Boundary, PERIODIC, INFLOW, OUTFLOW, WALL, SLIP, WALL_T, face_end, cell_end)
 from .ibm import build as build_ibm
 from .operators import (Grid, V, pad, interp_to_faces, diff_to_faces, faces_interp_to_cells,
                         faces_diff_to_cells, diff2, integrate)
+from .stretched import tanh_faces
 
 
 class Problem:
@@ -61,7 +67,15 @@ class Problem:
     def __init__(self, prm, geo=None):
         self.prm = dict(prm)
         dim = int(prm["dim"])
-        self.g = Grid(prm["n"][:dim], prm["L"][:dim])
+        alpha = [float(a) for a in prm.get("stretch", [0.0] * dim)[:dim]]
+        if any(a != 0.0 for a in alpha):
+            if geo is not None:
+                raise NotImplementedError("immersed bodies on stretched grids are not built")
+            faces = [prm["L"][d] * tanh_faces(prm["n"][d], alpha[d]) for d in range(dim)]
+            per = [prm["bc"][d][0] == PERIODIC for d in range(dim)]
+            self.g = Grid(prm["n"][:dim], prm["L"][:dim], faces=faces, periodic=per)
+        else:
+            self.g = Grid(prm["n"][:dim], prm["L"][:dim])
         g = self.g
         self.fp = flame.derived_parameters(prm["Z_st"], prm["density_ratio"], prm["eps_reg"],
                                            prm["tol_reg"], prm["Le_F"], prm["Le_O"], prm["gamma"])
@@ -311,12 +325,16 @@ def project(pb, mom, rho, drho, p0):
     for j in range(dim):
         if bnd.periodic(j):
             continue
-        dA = g.dV / g.h[j]
+        dA = g.face_area(j)
         for side in (0, 1):
             sign = -1.0 if side == 0 else 1.0
-            total += sign * float(np.sum(face_end(Ft[j], g, j, side))) * dA
             kind = bnd.face_kind_view(j, side)
-            out_area += float(np.sum(kind == OUTFLOW)) * dA
+            if g.uniform:
+                total += sign * float(np.sum(face_end(Ft[j], g, j, side))) * dA
+                out_area += float(np.sum(kind == OUTFLOW)) * dA
+            else:
+                total += sign * float(np.sum(face_end(Ft[j], g, j, side) * dA))
+                out_area += float(np.sum((kind == OUTFLOW) * dA))
     if out_area > 0.0:
         c = -total / out_area
         for j in range(dim):
@@ -331,7 +349,7 @@ def project(pb, mom, rho, drho, p0):
     b = drho - Sm
     for j in range(dim):
         b = b + faces_diff_to_cells(Ft[j], g, j)
-    b = b - b.mean()
+    b = b - g.mean(b)
     P_int = poisson.solve(b, g, pb.periodic)
     P = pad(P_int, g)
     bnd.fill_pressure(P)
@@ -370,7 +388,7 @@ def p0_rate(pb, v, Z, H, kap, p0):
 
     heat = integrate(diffusive(H) + flame.Nprime_eps(V(Z, g), fp) * diffusive(Z), g)
     div = integrate(sum(diff2(v[j], g, j) for j in range(dim)), g)
-    vol = float(np.prod([g.n[d] * g.h[d] for d in range(dim)]))
+    vol = g.volume()
     return pb.prm["gamma"] / vol * (fp["Q"] / (fp["S"] + 1.0) / pb.Pe * heat - p0 * div)
 
 

@@ -135,6 +135,9 @@ class SimError(RuntimeError):
 
 
 def params_struct(prm):
+    if any(float(a) != 0.0 for a in prm.get("stretch", [])):
+        # the kernels read one spacing per direction
+        raise ValueError("stretched grids (Eq 4.18) are not supported by the CUDA path")
     p = SimParams()
     p.dim = int(prm["dim"])
     for d in range(3):

@@ -107,3 +107,8 @@ def test_variant_parameters_validated_without_gpu(lib_path):
     assert status(dict(cavity, bc=[[6, 6], [3, 3], [0, 0]])) == L.SIM_EINVAL   # unknown kind
     tc, _, _ = W.taylor_couette(32)
     assert status(tc) == L.SIM_OK
+    # the tanh-stretched grids of Eq 4.18 exist in the oracle only: the binding
+    # refuses them instead of running a uniform grid
+    assert status(dict(cavity, stretch=[0.0, 0.0])) == L.SIM_OK
+    with pytest.raises(ValueError, match="stretched"):
+        L.params_struct(dict(cavity, stretch=[1.8, 1.8]))

@@ -1,0 +1,191 @@
+"""Pins for the oracle's time step on tanh-stretched grids (Eq 4.18): the
+general-coordinate operators against the uniform ones and against the 1D
+operators of ``oracle.stretched``, the ghost cells, the sparse Poisson solve,
+the whole step against the uniform step in the uniform limit, and exact
+discrete continuity and mass conservation on a strongly stretched cavity."""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import poisson
+from oracle import step as S
+from oracle import stretched as G
+from oracle.boundary import Boundary, PERIODIC, WALL, WALL_T
+from oracle.operators import (Grid, V, pad, interp_to_faces, diff_to_faces, faces_interp_to_cells,
+                              faces_diff_to_cells, diff2, integrate)
+
+
+def _faces(n, alpha, L=1.0):
+    return L * G.tanh_faces(n, alpha)
+
+
+# -------------------------------------------------------------- operators
+
+@pytest.mark.parametrize("dim,periodic", [(2, (True, False)), (3, (False, True, False))])
+def test_general_operators_on_uniform_faces_equal_the_uniform_ones(dim, periodic):
+    n, L = [6, 5, 4][:dim], [1.0, 2.0, 0.5][:dim]
+    gu = Grid(n, L)
+    gs = Grid(n, L, faces=[np.linspace(0.0, L[d], n[d] + 1) for d in range(dim)], periodic=periodic)
+    rng = np.random.default_rng(7)
+    phi = rng.standard_normal(gu.shape)
+    for d in range(dim):
+        if periodic[d]:                     # ghosts one period away: the copy of Eq 3.45
+            sl0 = [slice(None)] * dim
+            sl1 = [slice(None)] * dim
+            sl0[gu.ax(d)], sl1[gu.ax(d)] = 0, n[d]
+            phi[tuple(sl0)] = phi[tuple(sl1)]
+            sl0[gu.ax(d)], sl1[gu.ax(d)] = n[d] + 1, 1
+            phi[tuple(sl0)] = phi[tuple(sl1)]
+    for j in range(dim):
+        np.testing.assert_allclose(interp_to_faces(phi, gs, j), interp_to_faces(phi, gu, j), atol=1e-14)
+        np.testing.assert_allclose(diff_to_faces(phi, gs, j), diff_to_faces(phi, gu, j), rtol=1e-12, atol=1e-12)
+        fv = rng.standard_normal(interp_to_faces(phi, gu, j).shape)
+        np.testing.assert_allclose(faces_interp_to_cells(fv, gs, j), faces_interp_to_cells(fv, gu, j), atol=1e-14)
+        np.testing.assert_allclose(faces_diff_to_cells(fv, gs, j), faces_diff_to_cells(fv, gu, j),
+                                   rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(diff2(phi, gs, j), diff2(phi, gu, j), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(gs.dV, gu.dV, rtol=1e-13)
+    assert integrate(V(phi, gs), gs) == pytest.approx(integrate(V(phi, gu), gu), rel=1e-12, abs=1e-13)
+    assert gs.volume() == pytest.approx(gu.volume(), rel=1e-14)
+
+
+def test_padded_operators_equal_the_one_dimensional_ones():
+    """Interior faces and cells of a grid stretched in x and y: the padded
+    operators against the interior-array ones of ``oracle.stretched``."""
+    ax_x, ax_y = G.Axis(_faces(9, 3.0)), G.Axis(_faces(7, 1.5, L=2.0))
+    g = Grid((9, 7), (1.0, 2.0), faces=[ax_x.xf, ax_y.xf], periodic=(False, False))
+    phi = np.random.default_rng(8).standard_normal(g.shape)
+    inner = V(phi, g)
+    np.testing.assert_allclose(interp_to_faces(phi, g, 0)[:, 1:-1], G.interp_to_faces(inner, ax_x, 1),
+                               rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(interp_to_faces(phi, g, 1)[1:-1, :], G.interp_to_faces(inner, ax_y, 0),
+                               rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(diff_to_faces(phi, g, 0)[:, 1:-1], G.diff_to_faces(inner, ax_x, 1), rtol=1e-13)
+    np.testing.assert_allclose(diff_to_faces(phi, g, 1)[1:-1, :], G.diff_to_faces(inner, ax_y, 0), rtol=1e-13)
+    np.testing.assert_allclose(diff2(phi, g, 0)[:, 1:-1], G.diff2(inner, ax_x, 1), rtol=1e-13)
+    fv = np.random.default_rng(9).standard_normal((7, 10))
+    np.testing.assert_allclose(faces_diff_to_cells(fv, g, 0), G.faces_diff_to_cells(fv, ax_x, 1), rtol=1e-13)
+    np.testing.assert_allclose(faces_interp_to_cells(fv, g, 0), 0.5 * (fv[:, 1:] + fv[:, :-1]), atol=1e-14)
+    assert integrate(inner, g) == pytest.approx(G.integrate(inner, [ax_x, ax_y]), rel=1e-13)
+
+
+def test_ghosts_give_the_boundary_value_and_extrapolate_quadratics():
+    """On a stretched grid the mirror ghosts put the isothermal wall's value
+    and a zero gradient on the boundary faces (Eqs 3.43-3.44), and the P
+    ghosts of Eqs 3.27-3.28 reproduce any quadratic in the wall-normal
+    coordinate exactly."""
+    n = (8, 6)
+    g = Grid(n, (1.0, 1.0), faces=[_faces(8, 4.0), _faces(6, 2.0)], periodic=(False, False))
+    bnd = Boundary(g, [[WALL_T, WALL_T], [WALL, WALL]], [0.0, 0.0], 0.0, 2.0,
+                   wall_H=[[2.6, 1.4], [0.0, 0.0]])
+    H = pad(np.random.default_rng(10).uniform(1.5, 2.5, (6, 8)), g)
+    bnd.fill(H, "H")
+    Hf = interp_to_faces(H, g, 0)
+    np.testing.assert_allclose(Hf[:, 0], 2.6, rtol=1e-14)
+    np.testing.assert_allclose(Hf[:, -1], 1.4, rtol=1e-14)
+    gy = diff_to_faces(H, g, 1)
+    assert np.max(np.abs(gy[0, :])) == 0.0 and np.max(np.abs(gy[-1, :])) == 0.0
+    xc, yc = g.centres(0), g.centres(1)
+    P = 0.3 - 1.1 * xc + 2.5 * xc ** 2 + 0.7 * yc - 1.9 * yc ** 2
+    Q = pad(V(P, g), g)
+    bnd.fill_pressure(Q)
+    np.testing.assert_allclose(Q[1:-1, 0], P[1:-1, 0], rtol=1e-12)
+    np.testing.assert_allclose(Q[1:-1, -1], P[1:-1, -1], rtol=1e-12)
+    np.testing.assert_allclose(Q[0, 1:-1], P[0, 1:-1], rtol=1e-12)
+    np.testing.assert_allclose(Q[-1, 1:-1], P[-1, 1:-1], rtol=1e-12)
+
+
+# ------------------------------------------------------------------ Poisson
+
+@pytest.mark.parametrize("dim,periodic", [(2, (False, False)), (2, (True, False)), (3, (False, True, False))])
+def test_stretched_poisson_solve(dim, periodic):
+    """L P = b - mean(b) with the volume-weighted mean, through the operator
+    the step uses (``poisson.apply``); P has zero volume-weighted mean."""
+    n = [7, 6, 5][:dim]
+    faces = [_faces(n[d], [3.0, 1.0, 2.0][d]) for d in range(dim)]
+    g = Grid(n, [1.0] * dim, faces=faces, periodic=periodic)
+    b = np.random.default_rng(11).standard_normal(tuple(reversed(n)))
+    P = poisson.solve(b, g, periodic)
+    np.testing.assert_allclose(poisson.apply(P, g, periodic), b - g.mean(b), atol=1e-10)
+    assert abs(g.mean(P)) < 1e-13
+
+
+def test_stretched_poisson_solve_on_uniform_faces_equals_the_transform_solve():
+    n = (8, 6)
+    periodic = (True, False)
+    gu = Grid(n, (1.0, 1.5))
+    gs = Grid(n, (1.0, 1.5), faces=[np.linspace(0, 1.0, 9), np.linspace(0, 1.5, 7)], periodic=periodic)
+    b = np.random.default_rng(12).standard_normal((6, 8))
+    np.testing.assert_allclose(poisson.solve(b, gs, periodic), poisson.solve(b, gu, periodic), atol=1e-12)
+
+
+# --------------------------------------------------------------------- step
+
+def _fields(pb, st):
+    g = pb.g
+    out = dict(Z=V(st.Z, g), H=V(st.H, g), T=V(st.T, g), P=V(st.P, g) - g.mean(V(st.P, g)))
+    for d in range(g.dim):
+        out["v%d" % d] = V(st.v[d], g)
+        out["F%d" % d] = V(st.F[d], g, face=d)
+    return out
+
+
+def _channel():
+    """The filling chamber opened at the top: an outflow side, open system."""
+    prm, geo, f = W.filling_chamber(16, closed_system=0)
+    prm["bc"] = [list(prm["bc"][0]), [W.INFLOW, W.OUTFLOW], list(prm["bc"][2])]
+    return prm, geo, f
+
+
+@pytest.mark.parametrize("case", ["blobs", "cavity", "chamber3d", "channel"])
+def test_stretched_step_tends_to_the_uniform_step(case):
+    """alpha = 1e-7 leaves the faces uniform to about 1e-15 while every operator,
+    ghost, mean, the outflow shift's face areas and the Poisson solve take the
+    general path: after a few steps every field and p0 agree with the uniform
+    oracle to round-off."""
+    prm, geo, f = {"blobs": lambda: W.periodic_blobs(24), "cavity": lambda: W.heated_cavity(16),
+                   "chamber3d": lambda: W.filling_chamber(8, dim=3), "channel": _channel}[case]()
+    steps = 4
+    res = []
+    for stretch in (None, [1e-7] * prm["dim"]):
+        p = dict(prm) if stretch is None else dict(prm, stretch=stretch)
+        pb = S.Problem(p, geo)
+        st = S.initial_state(pb, f["v"], f["Z"], f["H"])
+        for _ in range(steps):
+            st = S.advance(pb, st)
+        res.append((_fields(pb, st), st.p0_hist[0], pb.g.uniform))
+    (a, pa, ua), (b, pb_, ub) = res
+    assert ua and not ub
+    assert pb_ == pytest.approx(pa, rel=1e-14)
+    for k in a:
+        assert np.max(np.abs(a[k] - b[k])) <= 1e-10 * np.max(np.abs(a[k])), k
+
+
+def test_stretched_cavity_keeps_discrete_continuity_and_mass():
+    """The cavity on a 21:1 grid (the clustering of Table 4): after every
+    projection d_t rho + delta_1 F_j / delta_1 x_j = 0 (Eq 3.24) to
+    round-off, the boundary faces carry no flux, and the enclosed mass stays
+    the initial one (Eq 2.40)."""
+    n = 12
+    a = G.alpha_for_ratio(n, 21.0)
+    hmin = np.diff(G.tanh_faces(n, a)).min()
+    prm, geo, f = W.heated_cavity(n, h_min=hmin, cfl=0.7)
+    prm["stretch"] = [a, a]
+    pb = S.Problem(prm, geo)
+    g = pb.g
+    st = S.initial_state(pb, f["v"], f["Z"], f["H"])
+    m0 = integrate(V(st.rho, g), g)
+    dt = prm["dt"]
+    for k in range(40):
+        prev = st
+        st = S.advance(pb, st)
+        rho1, rho0 = V(st.rho, g), V(prev.rho, g)
+        drho = (rho1 - rho0) / dt if k == 0 else (3 * rho1 - 4 * rho0 + V(prev.rho_prev, g)) / (2 * dt)
+        div = sum(faces_diff_to_cells(V(st.F[j], g, face=j), g, j) for j in range(2))
+        scale = np.max(np.abs(div)) + np.max(np.abs(drho))
+        assert np.max(np.abs(drho + div)) < 1e-10 * scale, k
+        for j in range(2):
+            Fj = V(st.F[j], g, face=j)
+            assert np.all(np.take(Fj, [0, n], axis=g.ax(j)) == 0.0)
+        assert integrate(V(st.rho, g), g) == pytest.approx(m0, rel=1e-13)

@@ -398,7 +398,7 @@ def marker_burner(n=64, dim=2, spacing=1.5, cfl=0.4, Re=150.0, seed=SEED, rms=0.
     return prm, geo, f
 
 
-def heated_cavity(n=64, Ra=1e2, eps=0.6, gravity=True, ny=None, cfl=0.4, T0=None):
+def heated_cavity(n=64, Ra=1e2, eps=0.6, gravity=True, ny=None, cfl=0.4, T0=None, h_min=None):
     """Differentially heated square cavity (Sec. 4.3): unit square, left wall at
     T_H = 1 + eps, right wall at T_C = 1 - eps (isothermal no-slip walls,
     Eq 4.16a-b), adiabatic no-slip top and bottom (Eq 4.16c); Pr = 0.71,
@@ -408,7 +408,9 @@ def heated_cavity(n=64, Ra=1e2, eps=0.6, gravity=True, ny=None, cfl=0.4, T0=None
     convenient Q = S + 1, so H = T + 1 (Eq 4.16) and the quiescent initial
     state at T = 1 has H = 2 (Eq 4.17).  gravity=False and ny > 0 (periodic in
     x_2) give the one-dimensional conduction slab used as a pin; T0 (an
-    interior array) replaces the uniform initial temperature."""
+    interior array) replaces the uniform initial temperature; h_min (the
+    smallest cell width of a stretched grid) sets the explicit limits of dt
+    instead of 1/n."""
     ny = n if ny is None else ny
     prm = _base_params()
     Re = Ra ** 0.5
@@ -428,7 +430,7 @@ def heated_cavity(n=64, Ra=1e2, eps=0.6, gravity=True, ny=None, cfl=0.4, T0=None
     TH = 1.0 + eps
     C = prm["sutherland_C"]
     kap_max = TH ** 1.5 * (1.0 + C) / (TH + C)
-    h = 1.0 / n
+    h = 1.0 / n if h_min is None else float(h_min)
     lim = [h / 1.0, h * h * Re * min(1.0, Pr) * (1.0 / TH) / (4.0 * kap_max)]
     prm["dt"] = cfl * min(lim)
     return prm, None, fields
