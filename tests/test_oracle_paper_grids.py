@@ -7,7 +7,7 @@ import os
 
 import pytest
 
-from test_oracle_stretched_step import _stretched_cavity_p0
+from test_oracle_stretched_step import _stretched_cavity, _stretched_cavity_p0
 
 pytestmark = [pytest.mark.slow,
               pytest.mark.skipif(os.environ.get("LOWMACH_LONG_ORACLE") != "1",
@@ -16,11 +16,15 @@ pytestmark = [pytest.mark.slow,
 
 def test_ra1e2_finer_stretched_pair_extrapolates_to_table5():
     """Ra = 1e2, 2:1 grids of 24^2 and 32^2 to t = 8, extrapolated at second
-    order: 0.957384 (p0 0.9588163 and 0.9581899), against the paper's 0.95738
-    and the reference value 0.95736 of Table 5.  About 4 minutes."""
-    p24, p32 = (_stretched_cavity_p0(n, 2.0, 1e2, 8.0) for n in (24, 32))
-    p_inf = p32 + (p32 - p24) / ((32.0 / 24.0) ** 2 - 1.0)
+    order: p0 0.957384 (0.9588163 and 0.9581899), against the paper's 0.95738
+    and the reference value 0.95736 of Table 5; mid-line Nusselt number
+    0.978671 (0.9779182 and 0.9782475), against 0.9787.  About 4 minutes."""
+    (p24, nu24), (p32, nu32) = (_stretched_cavity(n, 2.0, 1e2, 8.0) for n in (24, 32))
+    r = (32.0 / 24.0) ** 2 - 1.0
+    p_inf = p32 + (p32 - p24) / r
+    nu_inf = nu32 + (nu32 - nu24) / r
     assert abs(p_inf - 0.95738) < 1e-5 and abs(p_inf - 0.95736) < 3e-5, (p24, p32, p_inf)
+    assert abs(nu_inf - 0.9787) < 5e-5, (nu24, nu32, nu_inf)
 
 
 def test_ra1e2_on_the_64_grid_of_table3():
@@ -38,8 +42,11 @@ def test_ra1e2_on_the_64_grid_of_table3():
 
 def test_ra1e7_on_a_21_to_1_grid_reaches_table5():
     """Ra = 1e7 on a 32^2 grid with the 21:1 clustering of Table 4, to t = 300
-    (p0 then moves by under 5e-6 per 50 time units): 0.9225092, within 1e-4
-    of the paper's 0.92245 (216^2) and 2e-4 of the reference value 0.92263
-    (Table 5).  About 10 minutes."""
-    p = _stretched_cavity_p0(32, 21.0, 1e7, 300.0)
+    (p0 then moves by under 5e-6 per 50 time units): p0 0.9225092, within
+    1e-4 of the paper's 0.92245 (216^2) and 2e-4 of the reference value
+    0.92263 (Table 5); mid-line Nusselt number 16.256, within 0.03 (0.2 %) of
+    16.241, the paper's and the reference value (Table 5).  About 10
+    minutes."""
+    p, nu = _stretched_cavity(32, 21.0, 1e7, 300.0)
     assert abs(p - 0.92245) < 1e-4 and abs(p - 0.92263) < 2e-4, p
+    assert abs(nu - 16.241) < 0.03, nu
