@@ -252,7 +252,8 @@ def test_stretched_cavity_ra1e2_converges_to_the_papers_p0():
     second order: p0 0.957419, within 5e-5 of the paper's converged 0.95738
     (Tables 3 and 5), approached from above as in Table 3; the mid-line
     Nusselt number 0.978665, within 1e-4 of 0.9787 (Table 5)."""
-    (p16, nu16), (p24, nu24) = (_stretched_cavity(n, 2.0, 1e2, 6.0) for n in (16, 24))
+    from test_oracle_pins import two_runs
+    (p16, nu16), (p24, nu24) = two_runs(_stretched_cavity, [(16, 2.0, 1e2, 6.0), (24, 2.0, 1e2, 6.0)])
     r = 1.5 ** 2 - 1.0
     p_inf = p24 + (p24 - p16) / r
     nu_inf = nu24 + (nu24 - nu16) / r
