@@ -96,7 +96,8 @@ def build(g, geo):
         prof = np.maximum(prof, 0.0)
         samples = geo.get("profile")
         if samples is not None and len(samples) > 0:
-            samples = np.asarray(samples, dtype=float)
+            samples = np.asarray(samples)
+            samples = samples.astype(complex if np.iscomplexobj(samples) else float)
             lo, hi = c[0] - a[0] - s, c[0] + a[0] + s
             xs = np.linspace(lo, hi, len(samples))
             prof = prof * np.interp(x[0], xs, samples)
@@ -108,7 +109,7 @@ def build(g, geo):
         n_col = np.sum(chi_int, axis=g.ax(1), keepdims=True)
         n_col_safe = np.where(n_col > 0, n_col, 1.0)
         Sm_int = chi_int * rho_b * V(U, g) / (n_col_safe * g.h[1])
-        Sm_full = g.zeros()
+        Sm_full = g.zeros(Sm_int.dtype)
         V(Sm_full, g)[...] = Sm_int
     elif geo["kind"] == MARKERS:
         M = np.asarray(geo["markers"], dtype=float).reshape(-1, 2 * dim + 2)

@@ -16,6 +16,15 @@ Eq 3.22), with grad Z by the centred difference delta_2 (Eq 3.21, n = 2).
 Pinned (tests/test_oracle_pins.py): F_eps'' against second differences of
 Eq 3.41 itself, omega against -d^2T/dZ^2 kappa |grad Z|^2 / Pe of the state
 relation, delta_2 of a linear field.
+
+The oracle's derivative of J is taken by the complex step (Squire and Trapp,
+SIAM Review 40, 1998): for a map that is real-analytic in its input,
+Im J(c + i h e) / h is dJ/dc . e up to O(h^2) with no subtraction, so any
+h far below the rounding scale gives it to rounding.  Every operation of the
+step on the path from the burner profile to J is analytic (products, sums,
+powers of T, log cosh and tanh of Z, the linear Poisson solve), and the
+oracle's arrays take the dtype of their values, so the perturbation travels
+through the step.  Pinned against central differences of J.
 """
 
 import numpy as np
@@ -51,3 +60,11 @@ def objective(pb, st, nsteps, advance):
         st = advance(pb, st)
         J += dt * heat_release(pb, st)
     return J
+
+
+def complex_step_derivative(J, c, e, h=1e-20):
+    """dJ/dc . e at c for a real-analytic objective J evaluated on complex
+    input: Im J(c + i h e) / h."""
+    c = np.asarray(c, dtype=float)
+    e = np.asarray(e, dtype=float)
+    return float(np.imag(J(c + 1j * h * e))) / h

@@ -79,8 +79,8 @@ class Grid:
         shp[self.ax(d)] = len(x)
         return np.asarray(x).reshape(shp)
 
-    def zeros(self):
-        return np.zeros(self.shape)
+    def zeros(self, dtype=float):
+        return np.zeros(self.shape, dtype=dtype)
 
     def centres(self, d):
         """Cell-centre coordinate of direction d on the padded array (ghosts included)."""
@@ -140,9 +140,15 @@ def V(a, g, off=None, face=None):
     return a[tuple(sl)]
 
 
+def dtype_of(*arrays):
+    """float64, or complex128 when any argument is complex (the oracle then
+    carries a complex-step perturbation through the step)."""
+    return np.result_type(np.float64, *[np.asarray(a).dtype for a in arrays])
+
+
 def pad(interior_values, g):
     """New padded array with the given interior values and zero ghosts."""
-    a = g.zeros()
+    a = g.zeros(dtype_of(interior_values))
     V(a, g)[...] = interior_values
     return a
 
@@ -221,6 +227,5 @@ def diff2(phi, g, j, off=None, face=None):
 # Eq 3.22: midpoint-rule integration over the interior cells.
 # ---------------------------------------------------------------------------
 def integrate(phi_interior, g):
-    if g.uniform:
-        return float(np.sum(phi_interior) * g.dV)
-    return float(np.sum(phi_interior * g.dV))
+    r = np.sum(phi_interior) * g.dV if g.uniform else np.sum(phi_interior * g.dV)
+    return complex(r) if np.iscomplexobj(r) else float(r)

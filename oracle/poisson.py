@@ -118,7 +118,10 @@ def _stretched_factor(g, periodic):
 def solve(b, g, periodic):
     """Zero-mean P with L P = b - mean(b) (exact: transform-diagonalised on a
     uniform grid, a sparse LU factorisation on a stretched one, where both
-    means are volume-weighted)."""
+    means are volume-weighted).  A complex b (a complex-step perturbation)
+    is solved part by part: L is real."""
+    if np.iscomplexobj(b):
+        return solve(b.real, g, periodic) + 1j * solve(b.imag, g, periodic)
     if not g.uniform:
         lu, w, _ = _stretched_factor(g, periodic)
         r = np.asarray(b, dtype=np.float64).ravel()

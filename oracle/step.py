@@ -56,7 +56,7 @@ import numpy as np
 from . import flame, poisson
 from .boundary import (Boundary, PERIODIC, INFLOW, OUTFLOW, WALL, SLIP, WALL_T, face_end, cell_end)
 from .ibm import build as build_ibm
-from .operators import (Grid, V, pad, interp_to_faces, diff_to_faces, faces_interp_to_cells,
+from .operators import (Grid, V, pad, dtype_of, interp_to_faces, diff_to_faces, faces_interp_to_cells,
                         faces_diff_to_cells, diff2, integrate)
 from .stretched import tanh_faces
 
@@ -100,12 +100,9 @@ class Problem:
         if self.incompressible:
             one = np.ones(g.shape)
             return one, one.copy(), one.copy()
-        T = g.zeros()
-        V(T, g)[...] = flame.temperature(V(Z, g), V(H, g), self.fp)     # Eq 3.42
-        rho = g.zeros()
-        V(rho, g)[...] = flame.density(p0, V(T, g))                      # Eq 2.49
-        kap = g.zeros()
-        V(kap, g)[...] = self.kappa_of(V(T, g))                          # Eq 2.50 / 4.12
+        T = pad(flame.temperature(V(Z, g), V(H, g), self.fp), g)        # Eq 3.42
+        rho = pad(flame.density(p0, V(T, g)), g)                         # Eq 2.49
+        kap = pad(self.kappa_of(V(T, g)), g)                             # Eq 2.50 / 4.12
         self.bnd.fill(kap, "kappa", kappa_in=self.inflow_kappa() if self.has_inflow else None,
                       kappa_wall=self.wall_kappa())
         return T, rho, kap
@@ -195,7 +192,7 @@ def initial_state(pb, v0, Z0, H0):
     Ft = _provisional_fluxes(pb, mom, 1.0)
     st.F = []
     for j in range(g.dim):
-        Fj = g.zeros()
+        Fj = g.zeros(dtype_of(Ft[j]))
         V(Fj, g, face=j)[...] = Ft[j]
         st.F.append(Fj)
     return st
@@ -217,11 +214,12 @@ def residuals(pb, v, Z, H, rho, kap, F, p0dot):
     ibm = pb.ibm
     Fv = [V(F[j], g, face=j) for j in range(dim)]
     kf = [interp_to_faces(kap, g, j) for j in range(dim)]
+    dt_ = dtype_of(*v, Z, H, rho, kap, *F)
 
     Rv = []
     for i in range(dim):
-        conv = np.zeros(rho_c.shape)
-        visc = np.zeros(rho_c.shape)
+        conv = np.zeros(rho_c.shape, dtype=dt_)
+        visc = np.zeros(rho_c.shape, dtype=dt_)
         for j in range(dim):
             # Eq 3.26a: delta_1 (F_j bar(v_i)^{1x_j}) / delta_1 x_j
             conv += faces_diff_to_cells(Fv[j] * interp_to_faces(v[i], g, j), g, j)
@@ -250,13 +248,13 @@ def residuals(pb, v, Z, H, rho, kap, F, p0dot):
         Rv.append(R)
 
     def convective(phi):                                             # Eq 3.26b
-        out = np.zeros(rho_c.shape)
+        out = np.zeros(rho_c.shape, dtype=dt_)
         for j in range(dim):
             out += faces_interp_to_cells(Fv[j] * diff_to_faces(phi, g, j), g, j)
         return out
 
     def diffusive(phi):                                              # div(kappa grad phi)
-        out = np.zeros(rho_c.shape)
+        out = np.zeros(rho_c.shape, dtype=dt_)
         for j in range(dim):
             out += faces_diff_to_cells(kf[j] * diff_to_faces(phi, g, j), g, j)
         return out
@@ -330,10 +328,10 @@ def project(pb, mom, rho, drho, p0):
             sign = -1.0 if side == 0 else 1.0
             kind = bnd.face_kind_view(j, side)
             if g.uniform:
-                total += sign * float(np.sum(face_end(Ft[j], g, j, side))) * dA
+                total += sign * np.sum(face_end(Ft[j], g, j, side)) * dA
                 out_area += float(np.sum(kind == OUTFLOW)) * dA
             else:
-                total += sign * float(np.sum(face_end(Ft[j], g, j, side) * dA))
+                total += sign * np.sum(face_end(Ft[j], g, j, side) * dA)
                 out_area += float(np.sum((kind == OUTFLOW) * dA))
     if out_area > 0.0:
         c = -total / out_area
@@ -359,7 +357,7 @@ def project(pb, mom, rho, drho, p0):
         if not bnd.periodic(j):
             for side in (0, 1):
                 face_end(Fj_face, g, j, side)[...] = face_end(Ft[j], g, j, side)
-        Fj = g.zeros()
+        Fj = g.zeros(dtype_of(Fj_face))
         V(Fj, g, face=j)[...] = Fj_face
         F.append(Fj)
     v = []
@@ -381,7 +379,7 @@ def p0_rate(pb, v, Z, H, kap, p0):
     kf = [interp_to_faces(kap, g, j) for j in range(dim)]
 
     def diffusive(phi):
-        out = np.zeros(V(phi, g).shape)
+        out = np.zeros(V(phi, g).shape, dtype=dtype_of(phi, kap))
         for j in range(dim):
             out += faces_diff_to_cells(kf[j] * diff_to_faces(phi, g, j), g, j)
         return out

@@ -648,6 +648,37 @@ def test_heat_release_rate_is_the_temperature_curvature_times_dissipation():
     assert np.all(om >= 0.0)
 
 
+def test_complex_step_derivative_of_the_objective_matches_central_differences():
+    """The oracle's derivative of J by the complex step, on the slot burner
+    whose profile is a sum of 6 Gaussian bumps (24x48, 6 steps): equal to
+    the Richardson-combined central differences (4 D(h) - D(2h)) / 3 at
+    h = 1e-2 to 1e-7 relative, along a random direction and along single
+    coefficients; the real part of J(c + i h e) is J(c).  No complex value is
+    cast to float on the way (that warning is an error here)."""
+    import warnings
+    from oracle import objective as O
+    prm, geo, f, A, c = W.slot_bumps(24, 48, n_bumps=6, n_profile=32, Da_ib=(2.0 / 24) ** 2)
+    prm["poisson_rtol"] = 1e-13
+
+    def J(cc):
+        p = S.Problem(prm, dict(geo, profile=list(A @ cc)))
+        st = S.initial_state(p, f["v"], f["Z"], f["H"])
+        return O.objective(p, st, 6, S.advance)
+
+    e = np.random.Generator(np.random.PCG64(5)).standard_normal(len(c))
+    e /= np.linalg.norm(e)
+    complex_warning = getattr(getattr(np, "exceptions", np), "ComplexWarning")
+    J0 = J(c)
+    for d in (e, np.eye(len(c))[0], np.eye(len(c))[3]):
+        with warnings.catch_warnings():
+            warnings.simplefilter("error", complex_warning)
+            cs = O.complex_step_derivative(J, c, d)
+            assert np.real(J(c + 1e-20j * d)) == pytest.approx(J0, rel=1e-14)
+        D = [(J(c + h * d) - J(c - h * d)) / (2.0 * h) for h in (1e-2, 2e-2)]
+        rich = (4.0 * D[0] - D[1]) / 3.0
+        assert abs(rich - cs) <= 1e-7 * abs(cs), (rich, cs)
+
+
 def test_heat_release_vanishes_for_uniform_mixture():
     """Z uniform and equal to the inflow value: every delta_2 Z is zero (the
     Dirichlet and zero-gradient ghosts agree with the interior)."""
