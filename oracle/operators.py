@@ -157,14 +157,20 @@ def pad(interior_values, g):
 # Eq 3.20 / Eq 3.21 with n = 1 (odd operators), centre -> interface.
 # On a uniform grid the weights of Eq 3.20 are 1/2, 1/2.
 # ---------------------------------------------------------------------------
-def interp_to_faces(phi, g, j):
-    """bar(phi)^{1x_j} on every j-interface (needs the ghost cells along j)."""
-    lo, hi = V(phi, g, off=g.unit(j, -1), face=j), V(phi, g, face=j)
+def centres_to_faces(lo, hi, g, j):
+    """Eq 3.20 with n = 1 at every j-interface from the values ``lo`` and
+    ``hi`` at the centres on either side of it (face views of the cells
+    f - 1 and f along j)."""
     if g.uniform:
         return 0.5 * (lo + hi)
     xl, xr = g._along(j, g.xc[j][:-1]), g._along(j, g.xc[j][1:])
     xf = g._along(j, g.xf[j])
     return ((xf - xl) * hi + (xr - xf) * lo) / (xr - xl)
+
+
+def interp_to_faces(phi, g, j):
+    """bar(phi)^{1x_j} on every j-interface (needs the ghost cells along j)."""
+    return centres_to_faces(V(phi, g, off=g.unit(j, -1), face=j), V(phi, g, face=j), g, j)
 
 
 def diff_to_faces(phi, g, j):

@@ -16,9 +16,9 @@ the design notes of the package):
    projection that produced v^n; at t = 0, F^0 = bar(rho^0 v^0) (P = 0).
  * Viscous stress (Eq 2.46) on the j-interface: kappa by Eq 3.20; d v_i/d x_j by
    delta_1 across the interface; tangential derivatives d v_j / d x_i (i != j) and
-   the divergence's tangential parts by the interface average of the cell-centred
-   delta_2 derivatives; then delta_1 across the cell (a composition of odd
-   operators, text after Eq 3.26).
+   the divergence's tangential parts by the interface average (Eq 3.20: 1/2 and
+   1/2 on a uniform grid) of the cell-centred delta_2 derivatives; then delta_1
+   across the cell (a composition of odd operators, text after Eq 3.26).
  * Penalisation terms (Eqs 3.30-3.32) join the other forcing terms of their
    equation (Z, H: inside the 1/rho bracket of Eqs 3.2/3.4) and get the same
    AB2 / AM2 treatment.
@@ -56,8 +56,8 @@ import numpy as np
 from . import flame, poisson
 from .boundary import (Boundary, PERIODIC, INFLOW, OUTFLOW, WALL, SLIP, WALL_T, face_end, cell_end)
 from .ibm import build as build_ibm
-from .operators import (Grid, V, pad, dtype_of, interp_to_faces, diff_to_faces, faces_interp_to_cells,
-                        faces_diff_to_cells, diff2, integrate)
+from .operators import (Grid, V, pad, dtype_of, centres_to_faces, interp_to_faces, diff_to_faces,
+                        faces_interp_to_cells, faces_diff_to_cells, diff2, integrate)
 from .stretched import tanh_faces
 
 
@@ -228,15 +228,15 @@ def residuals(pb, v, Z, H, rho, kap, F, p0dot):
             if i == j:
                 dvj_dxi = dvi_dxj
             else:
-                dvj_dxi = 0.5 * (diff2(v[j], g, i, off=g.unit(j, -1), face=j)
-                                 + diff2(v[j], g, i, face=j))
+                dvj_dxi = centres_to_faces(diff2(v[j], g, i, off=g.unit(j, -1), face=j),
+                                           diff2(v[j], g, i, face=j), g, j)
             tau = kf[j] * (dvi_dxj + dvj_dxi)
             if i == j:
                 div = diff_to_faces(v[j], g, j)
                 for k in range(dim):
                     if k != j:
-                        div = div + 0.5 * (diff2(v[k], g, k, off=g.unit(j, -1), face=j)
-                                           + diff2(v[k], g, k, face=j))
+                        div = div + centres_to_faces(diff2(v[k], g, k, off=g.unit(j, -1), face=j),
+                                                     diff2(v[k], g, k, face=j), g, j)
                 tau = tau - (2.0 / 3.0) * kf[j] * div
             visc += faces_diff_to_cells(tau, g, j)
         R = -conv + PrPe * visc
