@@ -249,7 +249,7 @@ def _stretched_cavity_p0(n, ratio, Ra, t_end, cfl=0.7):
 def test_stretched_cavity_ra1e2_converges_to_the_papers_p0():
     """The cavity at Ra = 1e2 on the 2:1 grids of Table 3, 16^2 and 24^2, run
     to t = 6 (p0 then moves by under 2e-6 per time unit) and extrapolated at
-    second order: p0 0.957419, within 5e-5 of the paper's converged 0.95738
+    second order: p0 0.957420, within 5e-5 of the paper's converged 0.95738
     (Tables 3 and 5), approached from above as in Table 3; the mid-line
     Nusselt number 0.978665, within 1e-4 of 0.9787 (Table 5)."""
     from test_oracle_pins import two_runs
